@@ -1,0 +1,348 @@
+"""Throughput benchmark of the fast guided filter on GB300.
+
+Workload (one step): the 12 MP fast guided filter -- gray 4000 x 3000 FP32 guide I (synthetic scene,
+seed 0), 3-channel FP32 input p = I + N(0, 0.1^2) noise clipped to [0, 1] (seed 1), r = 16, eps = 1e-3,
+s = 4, bilinear subsampling -- through ``gf_filter`` with the inputs resident in HBM.  The metric is
+output megapixels per second (H * W per filter; the three channels of q are not counted separately).
+
+Also reported on the same line: the same workload at s = 1 (the plain guided filter) and s = 8, the
+per-kernel durations from CUDA events and the roofline of the dominant kernel, the end-to-end rate through
+``gf_filter_host`` (host buffers, copies timed), SM clocks sampled during the timed region, and the FP64
+CPU oracle timed on a bounded sample of the same workload.
+
+Launch: ``python bench.py [--gpus N --steps K --warmup W]``; for N > 1 under torchrun every rank filters
+its own image (weak scaling, no collective on the data path; the timing is max-reduced over ranks).
+``--impl reference`` times the FP64 CPU oracle on the same workload instead (rank 0 only).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "output MP/s at 12MP r=16 s=4 vs s=1; % HBM peak; serving p50/p99 latency"
+H, W, C, R, EPS, S, MODE = 3000, 4000, 3, 16, 1e-3, 4, "bilinear"
+WORKLOAD = "fast guided filter, 12 MP 4000x3000 FP32 gray guide, 3-channel FP32 p, r=16, eps=1e-3, s=4 bilinear"
+L2_BYTES = 129 * 2**20
+FALLBACK_HBM_GBS = 6800.0
+STAGES = ["k_subsample", "k_sweep_stats_coef", "k_sweep_mean_ab", "k_upsample_output"]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-graph", action="store_true", help="launch every step eagerly instead of graph replay")
+    ap.add_argument("--no-extras", action="store_true", help="skip the s sweep, e2e, cpu baseline")
+    return ap.parse_args()
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback (6.8 TB/s, no MEASURED_PEAKS.json)"
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if one exists for this workload."""
+    path = os.path.join(ROOT, "profiles", "%s_12mp_s4.md" % kernel)
+    try:
+        for line in open(path):
+            if line.startswith("dram_bytes_per_launch:"):
+                return int(float(line.split(":", 1)[1].strip()))
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(rank):
+    import synth
+    I = synth.make_scene(H, W, seed=0)
+    p = synth.rgb_noisy_input(I, seed=1, channels=C)
+    return I, p
+
+
+# --------------------------------------------------------------------------------------------------------
+# native arm
+# --------------------------------------------------------------------------------------------------------
+
+def time_steps(fn, steps, warmup, world, graph_steps, use_graph, stream):
+    """Warm up, then time exactly `steps` calls of fn on `stream` (graph replay of `graph_steps` calls at a
+    time when use_graph).  Returns milliseconds per step (max over ranks)."""
+    for _ in range(max(warmup, 1)):
+        fn()
+    torch.cuda.synchronize()
+    graph = None
+    if use_graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            for _ in range(graph_steps):
+                fn()
+        for _ in range(max(1, warmup // graph_steps)):
+            graph.replay()
+        torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        start.record(stream)
+        if graph is not None:
+            full, rem = divmod(steps, graph_steps)
+            for _ in range(full):
+                graph.replay()
+            for _ in range(rem):
+                fn()
+        else:
+            for _ in range(steps):
+                fn()
+        end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = start.elapsed_time(end) / steps
+    return max_over_ranks(ms, world)
+
+
+def run_native(args, world, rank, local):
+    import paper_1505_00996_gb300 as gf
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    I_np, p_np = make_inputs(rank)
+    I = torch.from_numpy(I_np).to(dev)
+    p = torch.from_numpy(p_np).to(dev)
+    q = torch.empty((1, C, H, W), dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = gf.default_context(local)
+    mp = H * W / 1e6
+
+    def filt(s):
+        return lambda: gf.fast_guided_filter(I, p, R, EPS, s, MODE, out=q, stream=stream, ctx=ctx)
+
+    use_graph = not args.no_graph
+    graph_steps = 10
+    # make the context arena large enough for every s before any capture
+    for s in (1, 4, 8):
+        filt(s)()
+    torch.cuda.synchronize()
+
+    # ---- headline: s = 4, exactly K steps, clocks sampled during the timed region
+    with ClockSampler(local) as clk:
+        ms = time_steps(filt(S), args.steps, args.warmup, world, graph_steps, use_graph, stream)
+    clocks = clk.summary()
+    value = world * mp / (ms / 1e3)
+
+    # ---- per-kernel durations from events recorded around each kernel of the same call
+    n_ev = min(args.steps, 200)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * gf.GF_MAX_STAGES)] for _ in range(n_ev)]
+    torch.cuda.synchronize()
+    for k in range(n_ev):
+        gf.fast_guided_filter(I, p, R, EPS, S, MODE, out=q, stream=stream, ctx=ctx, kernel_events=evs[k])
+    torch.cuda.synchronize()
+    stage_ms = {name: statistics.mean(e[2 * j].elapsed_time(e[2 * j + 1]) for e in evs)
+                for j, name in enumerate(STAGES)}
+    h, w, rl = gf.lowres_geometry(H, W, S, R)
+    # algorithmic bytes per launch of the output kernel: read I, read mean_a / mean_b (low res), write q
+    alg_bytes = H * W * 4 + 2 * C * h * w * 4 + C * H * W * 4
+    peak, peak_src = measured_hbm_peak()
+    achieved = alg_bytes / (stage_ms["k_upsample_output"] / 1e3) / 1e9
+    roofline = {"kernel": "k_upsample_output", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": profiled_traffic("k_upsample_output"),
+                "algorithmic_bytes": alg_bytes, "peak_source": peak_src,
+                "stage_us": {k: round(v * 1e3, 2) for k, v in stage_ms.items()}}
+
+    out = {"metric": METRIC, "value": round(value, 1), "unit": "MP/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "H": H, "W": W, "C": C, "r": R, "eps": EPS, "s": S, "mode": MODE,
+                      "global_batch": world, "parallelism": "replicas" if world > 1 else "single",
+                      "l2": "inputs larger than L2 (%.0f MB read+written per step > 129 MB L2); no flush" %
+                            ((I.numel() + p.numel() + q.numel()) * 4 / 2**20),
+                      "cuda_graph": use_graph},
+           "gpu_launches": 4 * args.steps, "roofline": roofline, "clocks": clocks}
+
+    if not args.no_extras:
+        sweep = {}
+        k_sweep = max(20, args.steps // 10)
+        for s in (1, 8):
+            ms_s = time_steps(filt(s), k_sweep, args.warmup, world, graph_steps, use_graph, stream)
+            sweep[str(s)] = {"ms_per_step": round(ms_s, 5), "mp_per_s": round(world * mp / (ms_s / 1e3), 1),
+                             "steps": k_sweep}
+        sweep["4"] = {"ms_per_step": round(ms, 5), "mp_per_s": round(value, 1), "steps": args.steps}
+        out["s_sweep"] = sweep
+        out["speedup_s4_vs_s1"] = round(sweep["1"]["ms_per_step"] / ms, 3)
+
+        # ---- end to end through the host-buffer entry point: copies in, filter, copy out, every step
+        I_h = torch.from_numpy(I_np).pin_memory()
+        p_h = torch.from_numpy(p_np).pin_memory()
+        q_h = torch.empty((1, C, H, W), dtype=torch.float32).pin_memory()
+        k_e2e = min(args.steps, 20)
+        for _ in range(3):
+            gf.fast_guided_filter_host(I_h, p_h, R, EPS, S, MODE, out=q_h, stream=stream, ctx=ctx)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            gf.fast_guided_filter_host(I_h, p_h, R, EPS, S, MODE, out=q_h, stream=stream, ctx=ctx)
+        dt = max_over_ranks((time.perf_counter() - t0) / k_e2e, world)
+        out["e2e"] = {"value": round(world * mp / dt, 1), "unit": "MP/s",
+                      "h2d_bytes_per_step": (I_h.numel() + p_h.numel()) * 4, "d2h_bytes_per_step": q_h.numel() * 4,
+                      "steps": k_e2e, "api": "gf_filter_host"}
+        if rank == 0:
+            out["cpu_baseline"] = cpu_baseline(I_np, p_np)
+    return out
+
+
+# --------------------------------------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# --------------------------------------------------------------------------------------------------------
+
+def _oracle_once(I_np, p_np, rows):
+    import oracle
+    Ic = I_np[None, None, :rows].astype(np.float64)
+    pc = p_np[None, :, :rows].astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.fast_guided_filter(Ic, pc, R, EPS, S, oracle.SUB_BILINEAR)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(I_np, p_np, budget_s=12.0):
+    """The FP64 oracle (single-threaded C, as it stands) on the full 12 MP workload, repeated for about
+    `budget_s` seconds."""
+    reps, total = 0, 0.0
+    while total < budget_s and reps < 50:
+        total += _oracle_once(I_np, p_np, H)
+        reps += 1
+    return {"value": round(reps * H * W / 1e6 / total, 3), "unit": "MP/s", "cores": 1, "kind": "oracle",
+            "sample": "%d full 12 MP filters (s=4 bilinear, C=3) in %.1f s, FP64 single-threaded C" % (reps, total)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    I_np, p_np = make_inputs(0)
+    # one step = the oracle on a band of full-width rows, sized so the whole run stays near a minute
+    t_full = _oracle_once(I_np, p_np, 400) * H / 400
+    total_steps = args.steps + args.warmup
+    rows = int(H * min(1.0, 60.0 / max(total_steps * t_full, 1e-9)))
+    rows = max(4 * S, rows // S * S)
+    for _ in range(args.warmup):
+        _oracle_once(I_np, p_np, rows)
+    t = sum(_oracle_once(I_np, p_np, rows) for _ in range(args.steps))
+    value = args.steps * rows * W / 1e6 / t
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "MP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "H": H, "W": W, "C": C, "r": R, "eps": EPS, "s": S, "mode": MODE},
+            "cpu_baseline": {"value": round(value, 3), "unit": "MP/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step: oracle on %d full-width rows of the 12 MP workload" % rows},
+            "e2e": {"value": round(value, 3), "unit": "MP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        out = run_reference(args, world, rank)
+    else:
+        out = run_native(args, world, rank, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,149 @@
+/*
+ * gf.h -- C ABI of the GB300 (sm_103a) fast guided filter library, libgf.so.
+ *
+ * Method: K. He and J. Sun, "Fast Guided Filter" (arXiv:1505.00996, 2015).  The library evaluates
+ * Algorithm 2 of the paper: subsample the guide I and the input p by a ratio s, compute the box
+ * statistics of I', p', I'.*I', I'.*p' at the low-res radius r', form the coefficients a (Eq. 2) and
+ * b (Eq. 3), box-average them, bilinearly upsample the averages, and output q = mean_a .* I + mean_b
+ * (Eq. 4) on the FULL-resolution guide.  With s = 1 the same call is the guided filter of Algorithm 1.
+ *
+ * Conventions (the paper leaves these open; the library and its tests fix them):
+ *   - f_mean(x, r): mean over the window of radius r clipped to the image, divided by the number of
+ *     in-image pixels of that window.
+ *   - Low-res size h = ceil(H/s), w = ceil(W/s); r' = r/s rounded half up and raised to 1 when r >= 1
+ *     (s = 1 gives r' = r), unless gf_opts.r_low >= 0 sets r' directly.
+ *   - Nearest subsample takes full-res (floor((j+1/2)s), floor((i+1/2)s)); bilinear subsample and
+ *     upsample use half-pixel centres without antialiasing, with coordinates clamped to the image;
+ *     box subsample (not in the paper) averages each s x s block clipped to the image.
+ *   - I has 1 channel (shared by every channel of p) or C channels (channel c guides channel c).
+ *
+ * Memory: every image pointer is caller-owned DEVICE memory, dense row-major planes, batch-major
+ * (N x channels x rows x cols).  The library never frees caller memory.  Calls are asynchronous on the
+ * caller's CUDA stream (a cudaStream_t passed as void*, NULL = legacy default stream) unless stated.
+ *
+ * Errors: every entry point returns a gf_status.  Argument errors return GF_EINVAL before anything is
+ * launched; gf_last_error() then returns a message for the calling thread.  GF_ECUDA reports a failed
+ * CUDA call (launch or allocation); the message names it.
+ */
+#ifndef GF_H
+#define GF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GF_ABI_VERSION 1
+#define GF_MAX_STAGES 8 /* kernel stages one gf_filter call can launch (for gf_opts.kernel_events) */
+
+typedef enum gf_status {
+    GF_OK = 0,
+    GF_PENDING = 1,     /* gf_poll: the request has not finished yet */
+    GF_EINVAL = -1,     /* invalid argument; nothing was launched */
+    GF_ENOMEM = -2,     /* a device allocation failed or the request can never fit the memory budget */
+    GF_ECUDA = -3,      /* a CUDA runtime call failed */
+    GF_ETIMEOUT = -4,   /* gf_poll: not finished within the timeout */
+    GF_EBUSY = -5,      /* the serving queue is full */
+    GF_ECANCELED = -6,  /* the request was cancelled */
+    GF_ENOTFOUND = -7   /* unknown ticket */
+} gf_status;
+
+typedef enum gf_subsample_mode { GF_SUB_NEAREST = 0, GF_SUB_BILINEAR = 1, GF_SUB_BOX = 2 } gf_subsample_mode;
+
+typedef enum gf_dtype { GF_F32 = 0, GF_F16 = 1, GF_U8 = 2 } gf_dtype;
+
+typedef struct gf_ctx gf_ctx;
+
+/*
+ * Options of one filter call.  Fill with gf_opts_init() and change what you need.
+ *   batch           N >= 1 images.
+ *   guide_channels  CI: 1 (one gray guide for all channels of p) or C (depthwise guide).  0 means 1.
+ *   r_low           >= 0: the low-res radius r'; < 0: derive r' from r and s (see above).
+ *   p_lowres        nonzero: p is already at low resolution (N x C x h x w) and is not subsampled.
+ *   dtype_in        storage of I and p: GF_F32, GF_F16 (FP32 arithmetic), or GF_U8 (values k/255;
+ *                   window sums are exact integers; nearest or bilinear subsample only).
+ *   dtype_out       storage of q: GF_F32 or GF_F16 (GF_U8 input always gives GF_F32 or GF_F16 out).
+ *   a_out, b_out, mean_a_out, mean_b_out
+ *                   optional device buffers (FP32, N x C x h x w) that receive a, b of Eq. (2)-(3) and
+ *                   their box means before upsampling.  NULL skips them.
+ *   stats_out       optional device buffer, N x C x 4 x h x w: for float input the window means
+ *                   mean_I, corr_I, mean_p, corr_Ip (FP32); for GF_U8 input the exact window SUMS
+ *                   (uint32) of J, J*J, P, J*P where J, P are the subsampled values in units of 1/(255k),
+ *                   k = 4 for bilinear subsampling at even s and 1 otherwise.
+ *   workspace, workspace_bytes
+ *                   optional caller-owned device scratch of at least gf_workspace_size() bytes; NULL
+ *                   makes the call use (and grow) the context's own arena.
+ *   kernel_events   optional array of 2*GF_MAX_STAGES cudaEvent_t (as void*): event 2k is recorded
+ *                   before and 2k+1 after the k-th kernel the call launches (unused ones untouched).
+ */
+typedef struct gf_opts {
+    int batch;
+    int guide_channels;
+    int r_low;
+    int p_lowres;
+    gf_dtype dtype_in;
+    gf_dtype dtype_out;
+    float *a_out;
+    float *b_out;
+    float *mean_a_out;
+    float *mean_b_out;
+    void *stats_out;
+    void *workspace;
+    size_t workspace_bytes;
+    void **kernel_events;
+} gf_opts;
+
+/* Default options: batch 1, gray guide, derived r', full-res p, FP32 in and out, nothing optional. */
+void gf_opts_init(gf_opts *opts);
+
+/* ABI version of the loaded library (GF_ABI_VERSION it was built with). */
+int gf_abi_version(void);
+
+/* Message describing the last error returned to the calling thread ("" if none).  Owned by the
+ * library; valid until the next call on the same thread. */
+const char *gf_last_error(void);
+
+/* Low-res geometry of a call: h = ceil(H/s), w = ceil(W/s), and the radius r' used on that grid
+ * (Algorithm 2 sets r' = r/s).  Host-only; returns GF_EINVAL for H, W, s < 1 or r < 0. */
+gf_status gf_lowres_geometry(int H, int W, int s, int r, int r_low, int *h, int *w, int *r_prime);
+
+/* Bytes of device scratch one gf_filter call with these arguments needs (host-only). */
+gf_status gf_workspace_size(int H, int W, int C, int s, const gf_opts *opts, size_t *bytes);
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device memory the serving loop
+ * may hold for admitted requests (0 = no cap beyond what cudaMalloc grants).  flags: reserved, 0.
+ * The context owns a growable scratch arena and the serving state; it does not own any stream. */
+gf_status gf_create(gf_ctx **out, int device, size_t hbm_budget_bytes, unsigned flags);
+
+/* Wait for the context's own in-flight work, then free everything it owns. */
+gf_status gf_destroy(gf_ctx *ctx);
+
+/*
+ * Fast guided filter, Algorithm 2 (and Algorithm 1 when s = 1).
+ *   I: N x CI x H x W guide; p: N x C x H x W input (N x C x h x w if opts->p_lowres);
+ *   q: N x C x H x W output, dtype opts->dtype_out.  All device pointers, dense.
+ *   r >= 0 full-res radius; eps >= 0 regulariser added to var(I) (data on the [0,1] scale for the
+ *   paper's eps values); s >= 1 subsampling ratio; mode: subsample mode.
+ *   opts may be NULL (defaults).  cuda_stream: the stream the kernels run on.
+ * Without a caller workspace the call uses the context arena; growing it is synchronous, and two
+ * calls that share a context arena must not run concurrently on different streams.
+ * Returns GF_OK once the kernels are enqueued.
+ */
+gf_status gf_filter(gf_ctx *ctx, const void *I, const void *p, void *q, int H, int W, int C, int r, float eps,
+                    int s, gf_subsample_mode mode, const gf_opts *opts, void *cuda_stream);
+
+/*
+ * Same filter on HOST buffers: copies I and p to the device, filters, copies q back and waits for the
+ * stream.  Staging memory comes from the context.  Host buffers may be pageable or pinned (pinned is
+ * faster).  Synchronous.
+ */
+gf_status gf_filter_host(gf_ctx *ctx, const void *I_host, const void *p_host, void *q_host, int H, int W, int C,
+                         int r, float eps, int s, gf_subsample_mode mode, const gf_opts *opts, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GF_H */

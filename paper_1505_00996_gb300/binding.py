@@ -1,0 +1,270 @@
+"""ctypes binding of libgf.so: the names of include/gf.h, with torch tensors for device memory and streams.
+
+This module only marshals arguments; every step of the filter runs in the library's CUDA kernels.  If the
+library cannot be loaded the calls raise -- there is no CPU fallback.
+"""
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import _build
+
+GF_OK, GF_PENDING, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_ETIMEOUT, GF_EBUSY, GF_ECANCELED, GF_ENOTFOUND = \
+    0, 1, -1, -2, -3, -4, -5, -6, -7
+GF_SUB_NEAREST, GF_SUB_BILINEAR, GF_SUB_BOX = 0, 1, 2
+GF_F32, GF_F16, GF_U8 = 0, 1, 2
+GF_MAX_STAGES = 8
+
+MODES = {"nearest": GF_SUB_NEAREST, "bilinear": GF_SUB_BILINEAR, "box": GF_SUB_BOX}
+_DTYPES = {torch.float32: GF_F32, torch.float16: GF_F16, torch.uint8: GF_U8}
+_STATUS_NAMES = {0: "GF_OK", 1: "GF_PENDING", -1: "GF_EINVAL", -2: "GF_ENOMEM", -3: "GF_ECUDA",
+                 -4: "GF_ETIMEOUT", -5: "GF_EBUSY", -6: "GF_ECANCELED", -7: "GF_ENOTFOUND"}
+
+
+class GFError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (_STATUS_NAMES.get(status, str(status)), message))
+        self.status = status
+
+
+class GFOpts(ctypes.Structure):
+    _fields_ = [
+        ("batch", ctypes.c_int),
+        ("guide_channels", ctypes.c_int),
+        ("r_low", ctypes.c_int),
+        ("p_lowres", ctypes.c_int),
+        ("dtype_in", ctypes.c_int),
+        ("dtype_out", ctypes.c_int),
+        ("a_out", ctypes.c_void_p),
+        ("b_out", ctypes.c_void_p),
+        ("mean_a_out", ctypes.c_void_p),
+        ("mean_b_out", ctypes.c_void_p),
+        ("stats_out", ctypes.c_void_p),
+        ("workspace", ctypes.c_void_p),
+        ("workspace_bytes", ctypes.c_size_t),
+        ("kernel_events", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def library_path():
+    return _build.LIB_PATH
+
+
+def load_library(build_if_missing=True):
+    """Load libgf.so (building it first if it is missing and ``build_if_missing``).  Raises if it cannot
+    be loaded: callers never fall back to another implementation."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB_PATH
+        if build_if_missing and _build.needs_build():
+            _build.build_library()
+        if not os.path.exists(path):
+            raise RuntimeError("libgf.so is not built (%s); run __graft_entry__.build()" % path)
+        lib = ctypes.CDLL(path)
+        vp, i, f, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
+        P = ctypes.POINTER
+        lib.gf_opts_init.argtypes = [P(GFOpts)]
+        lib.gf_opts_init.restype = None
+        lib.gf_abi_version.restype = i
+        lib.gf_last_error.restype = ctypes.c_char_p
+        lib.gf_lowres_geometry.argtypes = [i, i, i, i, i, P(i), P(i), P(i)]
+        lib.gf_lowres_geometry.restype = i
+        lib.gf_workspace_size.argtypes = [i, i, i, i, P(GFOpts), P(sz)]
+        lib.gf_workspace_size.restype = i
+        lib.gf_create.argtypes = [P(vp), i, sz, ctypes.c_uint]
+        lib.gf_create.restype = i
+        lib.gf_destroy.argtypes = [vp]
+        lib.gf_destroy.restype = i
+        lib.gf_filter.argtypes = [vp, vp, vp, vp, i, i, i, i, f, i, i, P(GFOpts), vp]
+        lib.gf_filter.restype = i
+        lib.gf_filter_host.argtypes = [vp, vp, vp, vp, i, i, i, i, f, i, i, P(GFOpts), vp]
+        lib.gf_filter_host.restype = i
+        _lib = lib
+        return lib
+
+
+def check(status):
+    if status != GF_OK:
+        msg = load_library(False).gf_last_error().decode(errors="replace")
+        raise GFError(status, msg)
+    return status
+
+
+def opts_init():
+    o = GFOpts()
+    load_library().gf_opts_init(ctypes.byref(o))
+    return o
+
+
+def lowres_geometry(H, W, s, r, r_low=-1):
+    h, w, rp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(load_library().gf_lowres_geometry(int(H), int(W), int(s), int(r), int(r_low), ctypes.byref(h),
+                                            ctypes.byref(w), ctypes.byref(rp)))
+    return h.value, w.value, rp.value
+
+
+class Context:
+    """Owns a gf_ctx (scratch arena, serving state) on one CUDA device."""
+
+    def __init__(self, device=None, hbm_budget_bytes=0):
+        lib = load_library()
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        self._ptr = ctypes.c_void_p()
+        check(lib.gf_create(ctypes.byref(self._ptr), self.device, int(hbm_budget_bytes), 0))
+
+    @property
+    def handle(self):
+        return self._ptr
+
+    def close(self):
+        if self._ptr:
+            check(load_library().gf_destroy(self._ptr))
+            self._ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_contexts = {}
+
+
+def default_context(device=None):
+    if device is None:
+        device = torch.cuda.current_device()
+    device = int(device)
+    if device not in _contexts:
+        _contexts[device] = Context(device)
+    return _contexts[device]
+
+
+def _nchw(x, name):
+    if x.dim() == 2:
+        return x[None, None], 2
+    if x.dim() == 3:
+        return x[None], 3
+    if x.dim() == 4:
+        return x, 4
+    raise ValueError("%s must have 2, 3 or 4 dimensions" % name)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowres=False, out_dtype=None,
+                       out=None, a_out=None, b_out=None, mean_a_out=None, mean_b_out=None, stats_out=None,
+                       workspace=None, kernel_events=None, stream=None, ctx=None):
+    """Fast guided filter (Algorithm 2; Algorithm 1 at s = 1) on CUDA tensors, via ``gf_filter``.
+
+    I: (H, W), (CI, H, W) or (N, CI, H, W); p: the same rank with C channels (at low resolution when
+    ``p_lowres``).  CI is 1 or C.  dtypes: float32, float16 or uint8 (I and p alike).  Returns q shaped like
+    p at full resolution, float32 (float16 for float16 input unless ``out_dtype`` says otherwise).
+    """
+    if not (I.is_cuda and p.is_cuda):
+        raise ValueError("I and p must be CUDA tensors")
+    if I.dtype != p.dtype or I.dtype not in _DTYPES:
+        raise ValueError("I and p must share one of float32, float16, uint8")
+    I4, _ = _nchw(I, "I")
+    p4, prank = _nchw(p, "p")
+    N, CI, H, W = I4.shape
+    C = p4.shape[1]
+    if p4.shape[0] != N:
+        raise ValueError("I and p must have the same batch size")
+    if out_dtype is None:
+        out_dtype = torch.float16 if I.dtype == torch.float16 else torch.float32
+    if out_dtype not in (torch.float32, torch.float16):
+        raise ValueError("out_dtype must be float32 or float16")
+    qshape = (N, C, H, W)
+    if out is None:
+        out = torch.empty(qshape, dtype=out_dtype, device=I.device)
+    elif tuple(out.shape) != qshape or out.dtype != out_dtype or not out.is_contiguous():
+        raise ValueError("out must be a contiguous %s tensor of shape %s" % (out_dtype, qshape))
+    if min(N, C, H, W) == 0 or p4.numel() == 0:
+        return out.reshape(p.shape[:-2] + (H, W)) if prank < 4 else out
+    I4 = I4.contiguous()
+    p4 = p4.contiguous()
+    o = opts_init()
+    o.batch = N
+    o.guide_channels = CI
+    o.r_low = -1 if r_low is None else int(r_low)
+    o.p_lowres = int(bool(p_lowres))
+    o.dtype_in = _DTYPES[I.dtype]
+    o.dtype_out = _DTYPES[out_dtype]
+    for name, t in (("a_out", a_out), ("b_out", b_out), ("mean_a_out", mean_a_out),
+                    ("mean_b_out", mean_b_out), ("stats_out", stats_out)):
+        if t is not None:
+            if not t.is_contiguous():
+                raise ValueError("%s must be contiguous" % name)
+            setattr(o, name, t.data_ptr())
+    if workspace is not None:
+        o.workspace = workspace.data_ptr()
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    ev_arr = None
+    if kernel_events is not None:
+        if len(kernel_events) != 2 * GF_MAX_STAGES:
+            raise ValueError("kernel_events needs %d events" % (2 * GF_MAX_STAGES))
+        st = stream if stream is not None else torch.cuda.current_stream()
+        for e in kernel_events:
+            if not e.cuda_event:  # torch creates the CUDA event on its first record
+                e.record(st)
+        ev_arr = (ctypes.c_void_p * (2 * GF_MAX_STAGES))(*[e.cuda_event for e in kernel_events])
+        o.kernel_events = ctypes.cast(ev_arr, ctypes.c_void_p)
+    ctx = ctx or default_context(I.device.index)
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    with torch.cuda.device(I.device):
+        check(load_library().gf_filter(ctx.handle, _ptr(I4), _ptr(p4), _ptr(out), H, W, C, int(r), float(eps),
+                                       int(s), m, ctypes.byref(o), _stream_handle(stream)))
+    if prank == 2:
+        return out[0, 0]
+    if prank == 3:
+        return out[0]
+    return out
+
+
+def fast_guided_filter_host(I, p, r, eps, s=4, mode="bilinear", *, out=None, out_dtype=None, r_low=None,
+                            stream=None, ctx=None, device=None):
+    """Same filter on HOST (CPU) tensors through ``gf_filter_host``: the library copies the inputs to the
+    device, filters and copies q back before returning."""
+    if I.is_cuda or p.is_cuda:
+        raise ValueError("gf_filter_host takes host tensors")
+    I4, _ = _nchw(I, "I")
+    p4, prank = _nchw(p, "p")
+    N, CI, H, W = I4.shape
+    C = p4.shape[1]
+    if out_dtype is None:
+        out_dtype = torch.float16 if I.dtype == torch.float16 else torch.float32
+    if out is None:
+        out = torch.empty((N, C, H, W), dtype=out_dtype)
+    o = opts_init()
+    o.batch = N
+    o.guide_channels = CI
+    o.r_low = -1 if r_low is None else int(r_low)
+    o.dtype_in = _DTYPES[I.dtype]
+    o.dtype_out = _DTYPES[out_dtype]
+    ctx = ctx or default_context(device)
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    I4 = I4.contiguous()
+    p4 = p4.contiguous()
+    with torch.cuda.device(ctx.device):
+        check(load_library().gf_filter_host(ctx.handle, _ptr(I4), _ptr(p4), _ptr(out), H, W, C, int(r),
+                                            float(eps), int(s), m, ctypes.byref(o), _stream_handle(stream)))
+    return out.reshape(p.shape[:-2] + (H, W)) if prank < 4 else out

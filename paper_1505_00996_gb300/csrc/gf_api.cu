@@ -1,0 +1,307 @@
+// gf_api.cu -- the extern "C" entry points of libgf.so declared in include/gf.h: argument checking,
+// the context and its scratch arena, and the host-buffer wrapper.  All arithmetic runs in the kernels of
+// gf_forward.cu.
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+
+#include "gf_internal.cuh"
+
+static thread_local std::string g_last_error;
+
+void gf_set_error(const std::string &msg) { g_last_error = msg; }
+
+struct gf_ctx {
+    int device = 0;
+    size_t budget = 0;
+    std::mutex mu;
+    void *arena = nullptr;  // scratch for calls without a caller workspace
+    size_t arena_bytes = 0;
+    void *stage = nullptr;  // device copies of host buffers (gf_filter_host)
+    size_t stage_bytes = 0;
+};
+
+namespace {
+
+gf_status fail(gf_status st, const std::string &msg)
+{
+    gf_set_error(msg);
+    return st;
+}
+
+gf_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(GF_ECUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+// Grow a device buffer to at least `need` bytes.  Growing waits for the device so that no queued kernel
+// still reads the old buffer.
+gf_status grow(void **buf, size_t *have, size_t need, const char *what)
+{
+    if (*have >= need) return GF_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize before growing scratch");
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    size_t bytes = need + need / 8;
+    e = cudaMalloc(buf, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GF_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes for " + what +
+                                   " failed: " + cudaGetErrorString(e));
+    }
+    *have = bytes;
+    return GF_OK;
+}
+
+int lowres_radius(int r, int s)
+{
+    if (s == 1) return r;
+    int rl = (2 * r + s) / (2 * s);  // r/s rounded half up
+    if (r >= 1 && rl < 1) rl = 1;
+    return rl;
+}
+
+struct Resolved {
+    int N, C, CI, H, W, h, w, s, r_low, mode, dt_in, dt_out;
+    bool p_lowres, dense_lowres, int_stats;
+    float eps, int_scale;
+    size_t lps;  // low-res plane stride in floats
+};
+
+// Check every argument of a forward call and derive its geometry.  No CUDA call.
+gf_status resolve(int H, int W, int C, int r, float eps, int s, int mode, const gf_opts *o, Resolved &R)
+{
+    gf_opts def;
+    gf_opts_init(&def);
+    if (!o) o = &def;
+    if (H < 1 || W < 1 || C < 1) return fail(GF_EINVAL, "H, W and C must be >= 1");
+    if (s < 1) return fail(GF_EINVAL, "subsampling ratio s must be >= 1");
+    if (r < 0) return fail(GF_EINVAL, "radius r must be >= 0");
+    if (!(eps >= 0.0f) || !isfinite(eps)) return fail(GF_EINVAL, "eps must be finite and >= 0");
+    if (mode < GF_SUB_NEAREST || mode > GF_SUB_BOX) return fail(GF_EINVAL, "unknown subsample mode");
+    if (o->batch < 1) return fail(GF_EINVAL, "batch must be >= 1");
+    const int CI = o->guide_channels == 0 ? 1 : o->guide_channels;
+    if (CI != 1 && CI != C) return fail(GF_EINVAL, "guide_channels must be 1 or C");
+    if (o->dtype_in < GF_F32 || o->dtype_in > GF_U8) return fail(GF_EINVAL, "unknown dtype_in");
+    if (o->dtype_out != GF_F32 && o->dtype_out != GF_F16) return fail(GF_EINVAL, "dtype_out must be GF_F32 or GF_F16");
+    if ((long long)H * W > (1LL << 31) - 1) return fail(GF_EINVAL, "H * W must be < 2^31");
+    R.N = o->batch; R.C = C; R.CI = CI; R.H = H; R.W = W; R.s = s; R.mode = mode;
+    R.h = (H + s - 1) / s;
+    R.w = (W + s - 1) / s;
+    R.r_low = o->r_low >= 0 ? o->r_low : lowres_radius(r, s);
+    if (R.r_low > 496) return fail(GF_EINVAL, "low-res radius r' > 496 is not supported");
+    R.eps = eps;
+    R.dt_in = o->dtype_in;
+    R.dt_out = o->dtype_out;
+    R.p_lowres = o->p_lowres != 0;
+    R.int_stats = (o->dtype_in == GF_U8);
+    R.int_scale = 255.0f;
+    if (R.int_stats) {
+        if (mode == GF_SUB_BOX && s > 1) return fail(GF_EINVAL, "uint8 input supports nearest or bilinear subsampling");
+        if (R.p_lowres) return fail(GF_EINVAL, "uint8 input does not support a low-res p");
+        const int k = (mode == GF_SUB_BILINEAR && s > 1 && (s % 2 == 0)) ? 4 : 1;
+        R.int_scale = 255.0f * (float)k;
+        // window sums of J*J and J*P must fit in 32 bits: (2r'+1)^2 (255k)^2 <= 2^32 - 1
+        const double side = 2.0 * R.r_low + 1.0, top = 255.0 * k;
+        if (side * side * top * top > 4294967295.0)
+            return fail(GF_EINVAL, "uint8 input: (2r'+1)^2 * (255k)^2 exceeds 32-bit window sums");
+    }
+    if (R.h > 65535) return fail(GF_EINVAL, "low-res height ceil(H/s) must be <= 65535");
+    const long long planes = (long long)R.N * (R.CI + C);
+    if (planes > 65535) return fail(GF_EINVAL, "batch * (guide channels + C) must be <= 65535");
+    R.dense_lowres = (o->a_out || o->b_out || o->mean_a_out || o->mean_b_out);
+    R.lps = R.dense_lowres ? (size_t)R.h * R.w : gfk::plane_stride_f32((size_t)R.h * R.w);
+    return GF_OK;
+}
+
+struct Layout {
+    size_t off_Il, off_pl, off_a, off_b, off_ma, off_mb, total;
+};
+
+Layout layout_of(const Resolved &R, const gf_opts *o)
+{
+    const size_t pb = R.lps * sizeof(float);
+    const size_t nc = (size_t)R.N * R.C * pb;
+    Layout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off += (bytes + 255) & ~size_t(255); return at; };
+    const bool sub = R.s > 1 || R.p_lowres;
+    L.off_Il = take(sub ? (size_t)R.N * R.CI * pb : 0);
+    L.off_pl = take(sub ? nc : 0);
+    L.off_a = take((o && o->a_out) ? 0 : nc);
+    L.off_b = take((o && o->b_out) ? 0 : nc);
+    L.off_ma = take((o && o->mean_a_out) ? 0 : nc);
+    L.off_mb = take((o && o->mean_b_out) ? 0 : nc);
+    L.total = off;
+    return L;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard()
+    {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+void gf_opts_init(gf_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->batch = 1;
+    o->guide_channels = 1;
+    o->r_low = -1;
+    o->dtype_in = GF_F32;
+    o->dtype_out = GF_F32;
+}
+
+int gf_abi_version(void) { return GF_ABI_VERSION; }
+
+const char *gf_last_error(void) { return g_last_error.c_str(); }
+
+gf_status gf_lowres_geometry(int H, int W, int s, int r, int r_low, int *h, int *w, int *r_prime)
+{
+    if (H < 1 || W < 1 || s < 1 || r < 0) return fail(GF_EINVAL, "H, W, s must be >= 1 and r >= 0");
+    if (h) *h = (H + s - 1) / s;
+    if (w) *w = (W + s - 1) / s;
+    if (r_prime) *r_prime = r_low >= 0 ? r_low : lowres_radius(r, s);
+    return GF_OK;
+}
+
+gf_status gf_workspace_size(int H, int W, int C, int s, const gf_opts *opts, size_t *bytes)
+{
+    if (!bytes) return fail(GF_EINVAL, "bytes is NULL");
+    Resolved R;
+    gf_status st = resolve(H, W, C, 0, 0.0f, s, GF_SUB_BILINEAR, opts, R);
+    if (st != GF_OK) return st;
+    *bytes = layout_of(R, opts).total;
+    return GF_OK;
+}
+
+gf_status gf_create(gf_ctx **out, int device, size_t hbm_budget_bytes, unsigned flags)
+{
+    if (!out) return fail(GF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (flags != 0) return fail(GF_EINVAL, "flags must be 0");
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(GF_EINVAL, "no such CUDA device");
+    gf_ctx *c = new gf_ctx();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    *out = c;
+    return GF_OK;
+}
+
+gf_status gf_destroy(gf_ctx *ctx)
+{
+    if (!ctx) return fail(GF_EINVAL, "ctx is NULL");
+    {
+        DeviceGuard g(ctx->device);
+        cudaDeviceSynchronize();
+        if (ctx->arena) cudaFree(ctx->arena);
+        if (ctx->stage) cudaFree(ctx->stage);
+    }
+    delete ctx;
+    return GF_OK;
+}
+
+gf_status gf_filter(gf_ctx *ctx, const void *I, const void *p, void *q, int H, int W, int C, int r, float eps, int s,
+                    gf_subsample_mode mode, const gf_opts *opts, void *cuda_stream)
+{
+    if (!ctx) return fail(GF_EINVAL, "ctx is NULL");
+    if (!I || !p || !q) return fail(GF_EINVAL, "I, p and q must be device pointers");
+    Resolved R;
+    gf_status st = resolve(H, W, C, r, eps, s, (int)mode, opts, R);
+    if (st != GF_OK) return st;
+    const Layout L = layout_of(R, opts);
+
+    DeviceGuard guard(ctx->device);
+    std::unique_lock<std::mutex> lock(ctx->mu, std::defer_lock);
+    char *ws = nullptr;
+    if (opts && opts->workspace) {
+        if (opts->workspace_bytes < L.total)
+            return fail(GF_EINVAL, "workspace_bytes is smaller than gf_workspace_size()");
+        ws = (char *)opts->workspace;
+    } else {
+        lock.lock();
+        st = grow(&ctx->arena, &ctx->arena_bytes, L.total, "the scratch arena");
+        if (st != GF_OK) return st;
+        ws = (char *)ctx->arena;
+    }
+
+    gfk::FwdPlan P;
+    P.N = R.N; P.C = R.C; P.CI = R.CI; P.H = R.H; P.W = R.W; P.h = R.h; P.w = R.w; P.s = R.s;
+    P.r_low = R.r_low; P.mode = R.mode; P.eps = R.eps; P.dt_in = R.dt_in; P.dt_out = R.dt_out;
+    P.p_lowres = R.p_lowres;
+    P.I = I; P.p = p; P.q = q;
+    P.lps = R.lps;
+    const bool sub = R.s > 1 || R.p_lowres;
+    P.Il = sub ? (float *)(ws + L.off_Il) : nullptr;
+    P.pl = sub ? (float *)(ws + L.off_pl) : nullptr;
+    P.a = (opts && opts->a_out) ? opts->a_out : (float *)(ws + L.off_a);
+    P.b = (opts && opts->b_out) ? opts->b_out : (float *)(ws + L.off_b);
+    P.ma = (opts && opts->mean_a_out) ? opts->mean_a_out : (float *)(ws + L.off_ma);
+    P.mb = (opts && opts->mean_b_out) ? opts->mean_b_out : (float *)(ws + L.off_mb);
+    P.stats = opts ? opts->stats_out : nullptr;
+    P.int_stats = R.int_stats;
+    P.int_scale = R.int_scale;
+    P.events = (opts && opts->kernel_events) ? (cudaEvent_t *)opts->kernel_events : nullptr;
+
+    cudaError_t e = gfk::launch_forward(P, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch in gf_filter");
+    return GF_OK;
+}
+
+gf_status gf_filter_host(gf_ctx *ctx, const void *I_host, const void *p_host, void *q_host, int H, int W, int C,
+                         int r, float eps, int s, gf_subsample_mode mode, const gf_opts *opts, void *cuda_stream)
+{
+    if (!ctx) return fail(GF_EINVAL, "ctx is NULL");
+    if (!I_host || !p_host || !q_host) return fail(GF_EINVAL, "I, p and q must be host pointers");
+    Resolved R;
+    gf_status st = resolve(H, W, C, r, eps, s, (int)mode, opts, R);
+    if (st != GF_OK) return st;
+    const size_t esz = gfk::dtype_size(R.dt_in);
+    const size_t plane = (size_t)R.H * R.W;
+    const size_t bI = (size_t)R.N * R.CI * plane * esz;
+    const size_t bp = (size_t)R.N * R.C * (R.p_lowres ? (size_t)R.h * R.w : plane) * esz;
+    const size_t bq = (size_t)R.N * R.C * plane * gfk::dtype_size(R.dt_out);
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    DeviceGuard guard(ctx->device);
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    char *base;
+    {
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        st = grow(&ctx->stage, &ctx->stage_bytes, al(bI) + al(bp) + al(bq), "host-call staging");
+        if (st != GF_OK) return st;
+        base = (char *)ctx->stage;
+    }
+    void *dI = base, *dp = base + al(bI), *dq = base + al(bI) + al(bp);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(dI, I_host, bI, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync of I");
+    if ((e = cudaMemcpyAsync(dp, p_host, bp, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync of p");
+    st = gf_filter(ctx, dI, dp, dq, H, W, C, r, eps, s, mode, opts, cuda_stream);
+    if (st != GF_OK) return st;
+    if ((e = cudaMemcpyAsync(q_host, dq, bq, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync of q");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return GF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+// gf_internal.cuh -- types and launcher declarations shared by the libgf translation units.
+// Nothing here is part of the public ABI (include/gf.h is).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gf.h"
+
+namespace gfk {
+
+// Element type of an input plane.
+enum DType { F32 = GF_F32, F16 = GF_F16, U8 = GF_U8 };
+
+inline size_t dtype_size(int dt) { return dt == F32 ? 4 : (dt == F16 ? 2 : 1); }
+
+// Low-res planes in the workspace start on 256-byte boundaries.
+inline size_t plane_stride_f32(size_t elems) { return (elems + 63) & ~size_t(63); }
+
+// Everything one forward call needs, resolved on the host.
+struct FwdPlan {
+    int N, C, CI, H, W, h, w, s, r_low, mode;
+    float eps;
+    int dt_in, dt_out;
+    bool p_lowres;
+    // inputs / outputs (device)
+    const void *I, *p;
+    void *q;
+    // low-res planes (FP32, plane stride `lps` elements)
+    size_t lps;
+    float *Il, *pl;      // subsampled guide (N*CI planes) and input (N*C planes); NULL when not needed
+    float *a, *b;        // N*C planes each
+    float *ma, *mb;      // N*C planes each
+    void *stats;         // optional N*C*4 planes (dense h*w each)
+    bool int_stats;      // exact integer window sums (uint8 input)
+    float int_scale;     // 255 * k: J = int_scale * I' (uint8 path)
+    cudaEvent_t *events; // 2*GF_MAX_STAGES or NULL
+};
+
+// Launch the forward chain on `stream`.  Returns cudaSuccess or the first launch error.
+cudaError_t launch_forward(const FwdPlan &P, cudaStream_t stream);
+
+}  // namespace gfk
+
+// Thread-local error message used by every entry point.
+void gf_set_error(const std::string &msg);

@@ -1,0 +1,107 @@
+"""CPU-only checks of the C ABI: the library builds for sm_103a, loads, exports every function that
+include/gf.h declares, and its host-only entry points (defaults, geometry, workspace size, argument
+checks) behave as documented.  No kernel is launched here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gf.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1505_00996_gb300 import _build, binding
+    _build.build_library()
+    return binding.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gf_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("gf_create", "gf_destroy", "gf_filter", "gf_filter_host", "gf_last_error"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib._name], capture_output=True, text=True).stdout
+    exported = set(line.split()[-1] for line in out.splitlines() if line.strip())
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        getattr(lib, n)
+
+
+def test_opts_defaults(lib):
+    from paper_1505_00996_gb300 import binding
+    o = binding.opts_init()
+    assert (o.batch, o.guide_channels, o.r_low, o.p_lowres, o.dtype_in, o.dtype_out) == (1, 1, -1, 0, 0, 0)
+    assert not o.workspace and not o.kernel_events
+    assert lib.gf_abi_version() == 1
+
+
+@pytest.mark.parametrize("H,W,s,r", [(3000, 4000, 4, 16), (3000, 4000, 8, 16), (3000, 4000, 1, 16), (10, 13, 4, 6),
+                                     (7, 7, 8, 3), (512, 512, 4, 8), (1, 1, 3, 0)])
+def test_lowres_geometry_matches_oracle_rule(lib, H, W, s, r):
+    from paper_1505_00996_gb300 import binding
+    h, w, rp = binding.lowres_geometry(H, W, s, r)
+    assert (h, w) == oracle.lowres_shape(H, W, s)
+    assert rp == oracle.lowres_radius(r, s)
+    assert binding.lowres_geometry(H, W, s, r, r_low=5)[2] == 5
+
+
+def test_workspace_size(lib):
+    from paper_1505_00996_gb300 import binding
+    o = binding.opts_init()
+    n = ctypes.c_size_t()
+    binding.check(lib.gf_workspace_size(3000, 4000, 3, 4, ctypes.byref(o), ctypes.byref(n)))
+    # low-res 750 x 1000: I', 3 x p', 3 x (a, b, mean_a, mean_b) planes of FP32
+    assert n.value >= (1 + 3 + 12) * 750 * 1000 * 4
+    n1 = ctypes.c_size_t()
+    binding.check(lib.gf_workspace_size(3000, 4000, 3, 1, ctypes.byref(o), ctypes.byref(n1)))
+    assert n1.value >= 12 * 3000 * 4000 * 4
+
+
+def test_argument_errors_are_reported_without_launching(lib):
+    from paper_1505_00996_gb300 import binding
+    o = binding.opts_init()
+    n = ctypes.c_size_t()
+    assert lib.gf_workspace_size(0, 10, 1, 4, ctypes.byref(o), ctypes.byref(n)) == binding.GF_EINVAL
+    assert b"H, W and C" in lib.gf_last_error()
+    assert lib.gf_workspace_size(10, 10, 1, 0, ctypes.byref(o), ctypes.byref(n)) == binding.GF_EINVAL
+    o.guide_channels = 2
+    assert lib.gf_workspace_size(10, 10, 3, 2, ctypes.byref(o), ctypes.byref(n)) == binding.GF_EINVAL
+    o = binding.opts_init()
+    o.dtype_in = binding.GF_U8
+    o.r_low = 40  # (2*40+1)^2 * 1020^2 > 2^32 at s = 4 bilinear
+    assert lib.gf_workspace_size(400, 400, 1, 4, ctypes.byref(o), ctypes.byref(n)) == binding.GF_EINVAL
+    assert lib.gf_filter(None, None, None, None, 8, 8, 1, 1, 0.1, 1, 1, None, None) == binding.GF_EINVAL
+    assert lib.gf_lowres_geometry(0, 1, 1, 1, -1, None, None, None) == binding.GF_EINVAL
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_1505_00996_gb300 import _build, binding
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(_build, "LIB_PATH", str(tmp_path / "missing" / "libgf.so"))
+    with pytest.raises(RuntimeError):
+        binding.load_library(build_if_missing=False)
+
+
+def test_product_package_does_not_use_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1505_00996_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle", text, flags=re.M), f
+                assert "gf_oracle" not in text and "libgforacle" not in text, f

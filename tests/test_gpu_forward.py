@@ -1,0 +1,243 @@
+"""GPU parity of the forward path (libgf.so through the C ABI) against the FP64 oracle.
+
+Every case runs the CUDA kernels through ``gf_filter`` and compares element by element with the oracle on
+the same seeded inputs: tiny, ragged and multi-tile shapes, every subsample mode and ratio, batch and
+depthwise guides, the 512 x 512 and 12 MP workloads, and the intermediates (a, b, their means, the window
+statistics).  Tolerance: max-abs 1e-4 on [0, 1] data for FP32 (2e-3 for FP16 storage).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_helpers import TOL_F16, TOL_F32, max_abs, oracle_q, oracle_rows
+
+pytestmark = pytest.mark.gpu
+
+MODE_NAMES = {0: "nearest", 1: "bilinear", 2: "box"}
+
+
+@pytest.fixture(scope="module")
+def gf(cuda_device):
+    import paper_1505_00996_gb300 as gf
+    gf.load_library()
+    return gf
+
+
+def _rand(shape, seed):
+    return np.random.default_rng(seed).uniform(0.0, 1.0, shape).astype(np.float32)
+
+
+def _run(gf, I, p, r, eps, s, mode, **kw):
+    q = gf.fast_guided_filter(torch.from_numpy(I).cuda(), torch.from_numpy(p).cuda(), r, eps, s, MODE_NAMES[mode], **kw)
+    torch.cuda.synchronize()
+    return q.float().cpu().numpy()
+
+
+CASES = [
+    # (N, CI, C, H, W, r, eps, s, mode)
+    (1, 1, 1, 1, 1, 1, 1e-2, 1, 1),
+    (1, 1, 1, 1, 37, 3, 1e-2, 1, 1),
+    (1, 1, 1, 29, 1, 3, 1e-2, 2, 0),
+    (1, 1, 2, 5, 7, 8, 1e-2, 1, 1),         # r' larger than the image
+    (1, 1, 1, 9, 13, 0, 1e-2, 1, 1),        # r' = 0
+    (1, 1, 3, 37, 53, 4, 1e-2, 2, 1),
+    (1, 1, 1, 61, 43, 6, 1e-3, 3, 0),       # odd s, ragged
+    (1, 1, 1, 61, 43, 6, 1e-3, 3, 1),
+    (1, 1, 2, 66, 70, 8, 1e-3, 4, 2),       # box mode, ragged
+    (1, 1, 3, 300, 701, 8, 1e-3, 2, 1),     # scalar path (W % 4 != 0), several strips and chunks
+    (1, 1, 3, 300, 704, 16, 1e-3, 4, 1),    # vector path
+    (1, 1, 3, 257, 1030, 16, 1e-3, 8, 0),
+    (2, 1, 3, 96, 128, 8, 1e-2, 4, 1),      # batch
+    (2, 3, 3, 96, 128, 8, 1e-2, 4, 2),      # depthwise guide
+    (1, 1, 1, 200, 300, 16, 1e-3, 1, 1),    # plain guided filter, r = 16
+    (1, 1, 1, 150, 420, 120, 1e-3, 1, 1),   # r' > 112: wide-span sweep variant
+    (1, 1, 2, 40, 1024, 60, 1e-6, 4, 1),    # paper's feathering radius (r' = 15), tiny eps
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "N%dCI%dC%d_%dx%d_r%d_s%d_m%d" % (c[0], c[1], c[2], c[3], c[4], c[5], c[7], c[8]))
+def test_fp32_parity(gf, case):
+    N, CI, C, H, W, r, eps, s, mode = case
+    I = _rand((N, CI, H, W), 1 + H + W)
+    p = _rand((N, C, H, W), 2 + H * W)
+    q = _run(gf, I, p, r, eps, s, mode)
+    ref = oracle_q(I, p, r, eps, s, mode)
+    assert q.shape == ref.shape
+    err = max_abs(q, ref)
+    assert err <= TOL_F32, "max-abs error %.3g" % err
+
+
+def test_intermediates_match_oracle(gf):
+    N, C, H, W, r, eps, s, mode = 1, 3, 120, 260, 8, 1e-2, 4, 1
+    I = synth.make_scene(H, W, seed=5)[None, None]
+    p = synth.rgb_noisy_input(I[0, 0], seed=6)[None]
+    h, w, rl = gf.lowres_geometry(H, W, s, r)
+    dev = torch.device("cuda")
+    a = torch.empty((N, C, h, w), device=dev)
+    b = torch.empty_like(a)
+    ma = torch.empty_like(a)
+    mb = torch.empty_like(a)
+    st = torch.empty((N, C, 4, h, w), device=dev)
+    q = gf.fast_guided_filter(torch.from_numpy(I).cuda(), torch.from_numpy(p).cuda(), r, eps, s, "bilinear",
+                              a_out=a, b_out=b, mean_a_out=ma, mean_b_out=mb, stats_out=st)
+    torch.cuda.synchronize()
+    ref_q, inter = oracle.fast_guided_filter(I.astype(np.float64), p.astype(np.float64), r, eps, s, mode,
+                                             intermediates=True)
+    assert max_abs(q.cpu(), ref_q) <= TOL_F32
+    assert max_abs(st.cpu(), inter["stats"]) <= 2e-6
+    # a = cov / (var + eps): an absolute error e in var/cov moves a by about e / eps
+    assert max_abs(a.cpu(), inter["a"]) <= 2e-6 / eps * 10
+    assert max_abs(b.cpu(), inter["b"]) <= 2e-6 / eps * 10
+    assert max_abs(ma.cpu(), inter["mean_a"]) <= 2e-6 / eps * 10
+    assert max_abs(mb.cpu(), inter["mean_b"]) <= 2e-6 / eps * 10
+
+
+def test_config0_512(gf):
+    """512 x 512 scene (seed 0), p = I, r = 8, eps = 0.01, s = 4 nearest, and s = 1 on the same inputs."""
+    I = synth.make_scene(512, 512, seed=0)
+    for s, mode in ((4, 0), (1, 0)):
+        q = _run(gf, I, I, 8, 0.01, s, mode)
+        err = max_abs(q, oracle_q(I, I, 8, 0.01, s, mode))
+        assert err <= TOL_F32, "s=%d err %.3g" % (s, err)
+
+
+@pytest.fixture(scope="module")
+def scene12mp():
+    I = synth.make_scene(3000, 4000, seed=0)
+    p = synth.rgb_noisy_input(I, seed=1)
+    return I[None, None], p[None]
+
+
+@pytest.mark.parametrize("s", [4, 8])
+def test_config1_12mp_full_oracle(gf, scene12mp, s):
+    """12 MP (4000 x 3000) gray guide, 3-channel noisy p, r = 16, eps = 1e-3, bilinear: every output."""
+    I, p = scene12mp
+    q = _run(gf, I, p, 16, 1e-3, s, 1)
+    err = max_abs(q, oracle_q(I, p, 16, 1e-3, s, 1))
+    assert err <= TOL_F32, "err %.3g" % err
+
+
+def test_config1_12mp_s1_row_bands(gf, scene12mp):
+    """12 MP at s = 1 (plain guided filter, r = 16): bands of rows at the top, middle and bottom, each
+    compared exactly with the oracle run on a crop with enough margin."""
+    I, p = scene12mp
+    q = _run(gf, I, p, 16, 1e-3, 1, 1)
+    H = I.shape[-2]
+    for Y0, Y1 in ((0, 40), (1480, 1530), (H - 40, H)):
+        ref = oracle_rows(I, p, Y0, Y1, 16, 1e-3, 1, 1)
+        err = max_abs(q[..., Y0:Y1, :], ref)
+        assert err <= TOL_F32, "rows %d-%d err %.3g" % (Y0, Y1, err)
+
+
+def test_output_guard_band(gf):
+    """No write lands outside q: q is a view into a larger buffer whose margins hold a sentinel."""
+    N, C, H, W = 1, 3, 50, 61
+    I = _rand((N, 1, H, W), 3)
+    p = _rand((N, C, H, W), 4)
+    n = N * C * H * W
+    big = torch.full((n + 2048,), 12345.0, device="cuda")
+    out = big[1024:1024 + n].view(N, C, H, W)
+    gf.fast_guided_filter(torch.from_numpy(I).cuda(), torch.from_numpy(p).cuda(), 4, 1e-2, 2, "bilinear", out=out)
+    torch.cuda.synchronize()
+    assert torch.all(big[:1024] == 12345.0) and torch.all(big[1024 + n:] == 12345.0)
+    assert max_abs(out.cpu(), oracle_q(I, p, 4, 1e-2, 2, 1)) <= TOL_F32
+
+
+def test_fp16_storage(gf):
+    I = synth.to_f16_values(synth.make_scene(600, 800, seed=7))
+    p = synth.to_f16_values(synth.rgb_noisy_input(I.astype(np.float32), seed=8))
+    q = gf.fast_guided_filter(torch.from_numpy(I).cuda(), torch.from_numpy(p).cuda(), 16, 1e-3, 4, "bilinear")
+    torch.cuda.synchronize()
+    assert q.dtype == torch.float16
+    ref = oracle_q(I.astype(np.float64), p.astype(np.float64), 16, 1e-3, 4, 1)
+    assert max_abs(q.float().cpu(), ref) <= TOL_F16
+
+
+@pytest.mark.parametrize("s,mode", [(4, 1), (4, 0), (1, 1), (3, 1), (8, 1)])
+def test_uint8_exact_window_sums(gf, s, mode):
+    """uint8 storage: the window sums of J, J^2, P, J P are exact integers (compared bit for bit with the
+    oracle's sums of the subsampled values, which are exact in FP64), and q matches the oracle run on the
+    dequantised values."""
+    H, W, C, r, eps = 240, 328, 3, 16, 1e-3
+    I8 = synth.quantize_u8(synth.make_scene(H, W, seed=9))
+    p8 = synth.quantize_u8(synth.rgb_noisy_input(I8 / 255.0, seed=10))
+    h, w, rl = gf.lowres_geometry(H, W, s, r)
+    k = 4 if (mode == 1 and s > 1 and s % 2 == 0) else 1
+    st = torch.zeros((1, C, 4, h, w), dtype=torch.int32, device="cuda")
+    q = gf.fast_guided_filter(torch.from_numpy(I8).cuda(), torch.from_numpy(p8).cuda(), r, eps, s,
+                              MODE_NAMES[mode], stats_out=st)
+    torch.cuda.synchronize()
+    got = st.cpu().numpy().view(np.uint32).astype(np.int64)
+    J = k * oracle.subsample(I8.astype(np.float64), s, mode)
+    assert np.all(J == np.round(J))
+    for c in range(C):
+        P = k * oracle.subsample(p8[c].astype(np.float64), s, mode)
+        ref = [oracle.box_sum(J, rl), oracle.box_sum(J * J, rl), oracle.box_sum(P, rl), oracle.box_sum(J * P, rl)]
+        for qi in range(4):
+            np.testing.assert_array_equal(got[0, c, qi], ref[qi].astype(np.int64))
+    ref_q = oracle_q(I8 / 255.0, p8 / 255.0, r, eps, s, mode)
+    assert max_abs(q.cpu(), ref_q) <= TOL_F32
+
+
+def test_lowres_p_box_depthwise(gf):
+    """Trainable-layer shape: 3-channel guide guiding each channel of a low-res p (box subsample, r' = 2)."""
+    I, p = synth.trainable_layer_batch(batch=2, channels=3, size=128, s=4)
+    q = gf.fast_guided_filter(torch.from_numpy(I).cuda(), torch.from_numpy(p).cuda(), 0, 1e-2, 4, "box",
+                              r_low=2, p_lowres=True)
+    torch.cuda.synchronize()
+    ref = oracle_q(I, p, 0, 1e-2, 4, 2, r_low=2, p_lowres=True)
+    assert max_abs(q.cpu(), ref) <= TOL_F32
+
+
+def test_host_buffers_match_device_call(gf):
+    I = _rand((1, 1, 90, 130), 11)
+    p = _rand((1, 3, 90, 130), 12)
+    q_dev = _run(gf, I, p, 8, 1e-2, 4, 1)
+    q_host = gf.fast_guided_filter_host(torch.from_numpy(I), torch.from_numpy(p), 8, 1e-2, 4, "bilinear").numpy()
+    np.testing.assert_array_equal(q_host, q_dev)
+
+
+def test_caller_workspace(gf):
+    import ctypes
+    I = _rand((1, 1, 70, 90), 13)
+    p = _rand((1, 2, 70, 90), 14)
+    o = gf.opts_init()
+    nbytes = ctypes.c_size_t()
+    gf.binding.check(gf.load_library().gf_workspace_size(70, 90, 2, 4, ctypes.byref(o), ctypes.byref(nbytes)))
+    ws = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+    q1 = _run(gf, I, p, 8, 1e-2, 4, 1, workspace=ws)
+    q2 = _run(gf, I, p, 8, 1e-2, 4, 1)
+    np.testing.assert_array_equal(q1, q2)
+    with pytest.raises(gf.GFError) as ei:
+        _run(gf, I, p, 8, 1e-2, 4, 1, workspace=ws[:16])
+    assert ei.value.status == gf.GF_EINVAL
+
+
+def test_invalid_arguments_rejected(gf):
+    I = torch.rand(1, 2, 16, 16, device="cuda")
+    p = torch.rand(1, 3, 16, 16, device="cuda")
+    with pytest.raises(gf.GFError) as ei:
+        gf.fast_guided_filter(I, p, 2, 1e-2, 2)        # 2 guide channels for 3 input channels
+    assert ei.value.status == gf.GF_EINVAL
+    with pytest.raises(gf.GFError):
+        gf.fast_guided_filter(I[:, :1], p, 2, -1.0, 2)  # eps < 0
+    I8 = torch.zeros(16, 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(gf.GFError):
+        gf.fast_guided_filter(I8, I8, 2, 1e-2, 2, "box")  # uint8 supports nearest / bilinear only
+
+
+def test_empty_input_returns_empty(gf):
+    I = torch.rand(1, 1, 0, 16, device="cuda")
+    p = torch.rand(1, 3, 0, 16, device="cuda")
+    q = gf.fast_guided_filter(I, p, 2, 1e-2, 2)
+    assert q.shape == (1, 3, 0, 16)
+
+
+def test_kernel_events_recorded(gf):
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * gf.GF_MAX_STAGES)]
+    I = _rand((1, 1, 256, 256), 15)
+    _run(gf, I, I, 8, 1e-2, 4, 1, kernel_events=ev)
+    for k in range(4):  # subsample, statistics + coefficients, box means of a and b, upsample + output
+        assert ev[2 * k].elapsed_time(ev[2 * k + 1]) >= 0.0
