@@ -33,7 +33,7 @@ H, W, C, R, EPS, S, MODE = 3000, 4000, 3, 16, 1e-3, 4, "bilinear"
 WORKLOAD = "fast guided filter, 12 MP 4000x3000 FP32 gray guide, 3-channel FP32 p, r=16, eps=1e-3, s=4 bilinear"
 L2_BYTES = 129 * 2**20
 FALLBACK_HBM_GBS = 6800.0
-STAGES = ["k_subsample", "k_sweep_stats_coef", "k_sweep_mean_ab", "k_upsample_output"]
+STAGES = ["k_subsample", "k_box_tile_stats_coef", "k_box_tile_mean_ab", "k_upsample_output"]
 
 
 def parse_args():
@@ -227,9 +227,15 @@ def run_native(args, world, rank, local):
     # ---- per-kernel durations from events recorded around each kernel of the same call
     n_ev = min(args.steps, 200)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * gf.GF_MAX_STAGES)] for _ in range(n_ev)]
+    for e in (e for row in evs for e in row):
+        e.record(stream)
     torch.cuda.synchronize()
-    for k in range(n_ev):
-        gf.fast_guided_filter(I, p, R, EPS, S, MODE, out=q, stream=stream, ctx=ctx, kernel_events=evs[k])
+    with torch.cuda.stream(stream):
+        # hold the stream with a spin kernel while the host enqueues every step, so that no kernel of the
+        # measured steps waits for the host between the events around it
+        torch.cuda._sleep(int(0.05 * 2.0e9))
+        for k in range(n_ev):
+            gf.fast_guided_filter(I, p, R, EPS, S, MODE, out=q, stream=stream, ctx=ctx, kernel_events=evs[k])
     torch.cuda.synchronize()
     stage_ms = {name: statistics.mean(e[2 * j].elapsed_time(e[2 * j + 1]) for e in evs)
                 for j, name in enumerate(STAGES)}

@@ -11,7 +11,7 @@
  *   - f_mean(x, r): mean over the window of radius r clipped to the image, divided by the number of
  *     in-image pixels of that window.
  *   - Low-res size h = ceil(H/s), w = ceil(W/s); r' = r/s rounded half up and raised to 1 when r >= 1
- *     (s = 1 gives r' = r), unless gf_opts.r_low >= 0 sets r' directly.
+ *     (s = 1 gives r' = r), unless gf_opts.r_low >= 0 sets r' directly.  r' <= 128 is supported.
  *   - Nearest subsample takes full-res (floor((j+1/2)s), floor((i+1/2)s)); bilinear subsample and
  *     upsample use half-pixel centres without antialiasing, with coordinates clamped to the image;
  *     box subsample (not in the paper) averages each s x s block clipped to the image.

@@ -93,7 +93,7 @@ gf_status resolve(int H, int W, int C, int r, float eps, int s, int mode, const 
     R.h = (H + s - 1) / s;
     R.w = (W + s - 1) / s;
     R.r_low = o->r_low >= 0 ? o->r_low : lowres_radius(r, s);
-    if (R.r_low > 496) return fail(GF_EINVAL, "low-res radius r' > 496 is not supported");
+    if (R.r_low > gfk::MAX_LOWRES_RADIUS) return fail(GF_EINVAL, "low-res radius r' > 128 is not supported");
     R.eps = eps;
     R.dt_in = o->dtype_in;
     R.dt_out = o->dtype_out;

@@ -1,19 +1,28 @@
 // gf_forward.cu -- sm_103a kernels of the fast guided filter forward pass (Algorithm 2 of He and Sun,
 // "Fast Guided Filter", 2015) and the host launcher that chains them.
 //
-//   k_subsample   Algorithm 2 first step: I' = f_subsample(I, s), p' = f_subsample(p, s) into FP32 low-res
-//                 planes (nearest, bilinear or box; see gf.h for the conventions).
-//   k_sweep       KIND 0/1: the box statistics of I', p', I'.*I', I'.*p' at radius r' fused with the
+//   k_subsample / k_subsample_vec
+//                 Algorithm 2 first step: I' = f_subsample(I, s), p' = f_subsample(p, s) into FP32 low-res
+//                 planes (nearest, bilinear or box; see gf.h for the conventions).  Each thread produces a
+//                 column of low-res pixels so that all of its full-res loads are in flight together; the
+//                 _vec form reads aligned FP32 rows with 64/128-bit loads for s = 2, 4, 8.
+//   k_box_tile    KIND 0/1: the box statistics of I', p', I'.*I', I'.*p' at radius r' fused with the
 //                 variance/covariance and the coefficients a (Eq. 2) and b (Eq. 3).
 //                 KIND 2: the box means of a and b.
-//                 One CTA owns a strip of output columns and a run of rows; it sweeps down the rows keeping
-//                 compensated running column sums in registers (O(1) work per pixel for any r'), then does
-//                 the horizontal window sums from shared memory with sliding sums.
-//   k_upsample_output
+//                 One CTA owns a 32 x 64 tile of outputs of one channel.  Phase 1: each thread slides a
+//                 vertical window down a segment of one column (loads straight from global memory, sums in
+//                 registers) and writes the column sums into a transposed shared tile.  Phase 2: each thread
+//                 slides a horizontal window along a segment of one row of that tile and applies the
+//                 epilogue.  Phase 3 writes the tile out coalesced.  Work per pixel is O(1) in r'.
+//   k_upsample_output_s4x / k_upsample_output
 //                 Algorithm 2 last two steps fused: bilinear upsampling of mean_a, mean_b (never written at
-//                 full resolution) and q = mean_a .* I + mean_b (Eq. 4) on the full-resolution guide.  Each
-//                 thread owns 4 adjacent columns and a run of rows, reads I once and writes q once with
-//                 128-bit streaming accesses, and caches the horizontally interpolated low-res rows.
+//                 full resolution) and q = mean_a .* I + mean_b (Eq. 4) on the full-resolution guide.  A CTA
+//                 stages the low-res taps of its 512-pixel-wide band in shared memory; each thread owns 4
+//                 adjacent columns, reads I with 128-bit streaming loads (several rows in flight) and
+//                 writes q once with streaming stores.  The _s4x form (s = 4, 8) walks the rows in the
+//                 s-row runs that share one pair of low-res tap rows, with the vertical weights as
+//                 compile-time constants: three FMAs per output value.
+//   k_output_s1   the s = 1 form of the last step (no resampling).
 #include <algorithm>
 
 #include "gf_internal.cuh"
@@ -35,6 +44,9 @@ __device__ __forceinline__ float ldv<uint8_t>(const uint8_t *p) { return (float)
 // ------------------------------------------------------------------------------------------------------
 // k_subsample
 // ------------------------------------------------------------------------------------------------------
+constexpr int SUB_NT = 128;  // threads per CTA (one low-res column each)
+constexpr int SUB_JB = 4;    // low-res rows per thread
+
 struct SubJob {
     const void *src;
     float *dst;
@@ -48,21 +60,12 @@ struct SubParams {
 };
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_subsample(SubParams P)
+__device__ __forceinline__ float subsample_one(const T *src, int H, int W, int s, int j, int i)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    if (i >= P.w) return;
-    int z = blockIdx.z;
-    const SubJob &J = (z < P.job[0].planes) ? P.job[0] : P.job[1];
-    if (z >= P.job[0].planes) z -= P.job[0].planes;
-    const T *src = (const T *)J.src + (size_t)z * J.sps;
-    const int H = J.H, W = J.W, s = J.s;
-    float v;
     if (MODE == GF_SUB_NEAREST || s == 1) {
         const int sy = min(((2 * j + 1) * s) >> 1, H - 1);  // floor((j + 1/2) s)
         const int sx = min(((2 * i + 1) * s) >> 1, W - 1);
-        v = ldv(src + (size_t)sy * W + sx);
+        return ldv(src + (size_t)sy * W + sx);
     } else if (MODE == GF_SUB_BILINEAR) {
         // source coordinate (j + 1/2) s - 1/2 = ((2j+1)s - 1) / 2, clamped to [0, H-1]
         const int ny = (2 * j + 1) * s - 1, nx = (2 * i + 1) * s - 1;
@@ -74,269 +77,341 @@ __global__ void __launch_bounds__(256) k_subsample(SubParams P)
         const T *r0 = src + (size_t)y0 * W, *r1 = src + (size_t)y1 * W;
         const float top = (1.0f - fx) * ldv(r0 + x0) + fx * ldv(r0 + x1);
         const float bot = (1.0f - fx) * ldv(r1 + x0) + fx * ldv(r1 + x1);
-        v = (1.0f - fy) * top + fy * bot;
+        return (1.0f - fy) * top + fy * bot;
     } else {  // box: mean of the s x s block clipped to the image
         const int ya = j * s, yb = min(ya + s, H), xa = i * s, xb = min(xa + s, W);
         float acc = 0.0f;
         for (int yy = ya; yy < yb; ++yy)
             for (int xx = xa; xx < xb; ++xx) acc += ldv(src + (size_t)yy * W + xx);
-        v = acc / (float)((yb - ya) * (xb - xa));
+        return acc / (float)((yb - ya) * (xb - xa));
     }
-    J.dst[(size_t)z * J.dps + (size_t)j * P.w + i] = v * P.scale;
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(SUB_NT) k_subsample(SubParams P)
+{
+    const int i = blockIdx.x * SUB_NT + threadIdx.x;
+    const int j0 = blockIdx.y * SUB_JB;
+    if (i >= P.w) return;
+    int z = blockIdx.z;
+    const SubJob &J = (z < P.job[0].planes) ? P.job[0] : P.job[1];
+    if (z >= P.job[0].planes) z -= P.job[0].planes;
+    const T *src = (const T *)J.src + (size_t)z * J.sps;
+    float v[SUB_JB];
+#pragma unroll
+    for (int u = 0; u < SUB_JB; ++u) {
+        const int j = min(j0 + u, P.h - 1);
+        v[u] = subsample_one<T, MODE>(src, J.H, J.W, J.s, j, i);
+    }
+    float *dst = J.dst + (size_t)z * J.dps + i;
+#pragma unroll
+    for (int u = 0; u < SUB_JB; ++u)
+        if (j0 + u < P.h) dst[(size_t)(j0 + u) * P.w] = v[u] * P.scale;
+}
+
+// Aligned FP32 fast path of k_subsample for s = 2, 4, 8 with H and W multiples of s (so no sample is
+// clamped): the two (bilinear) or one (nearest) source columns of a low-res pixel lie in one 8- or 16-byte
+// chunk (two for s = 8), read with one vector load per source row.
+template <int MODE, int S>
+__global__ void __launch_bounds__(SUB_NT) k_subsample_vec(SubParams P)
+{
+    constexpr int JB = (S == 8) ? 4 : 8;
+    const int i = blockIdx.x * SUB_NT + threadIdx.x;
+    const int j0 = blockIdx.y * JB;
+    if (i >= P.w) return;
+    int z = blockIdx.z;
+    const SubJob &J = (z < P.job[0].planes) ? P.job[0] : P.job[1];
+    if (z >= P.job[0].planes) z -= P.job[0].planes;
+    const float *src = (const float *)J.src + (size_t)z * J.sps;
+    const int W = J.W;
+    // source row pair (bilinear) or row (nearest) of low-res row j, and the two source columns' chunk
+    auto row_val = [&](int y) -> float2 {  // returns the two columns around the sample (bilinear) / the sample twice
+        const float *rp = src + (size_t)y * W + (size_t)i * S;
+        if (S == 2) {
+            const float2 t = __ldcs(reinterpret_cast<const float2 *>(rp));
+            return MODE == GF_SUB_BILINEAR ? t : make_float2(t.y, t.y);
+        } else if (S == 4) {
+            const float4 t = __ldcs(reinterpret_cast<const float4 *>(rp));
+            return MODE == GF_SUB_BILINEAR ? make_float2(t.y, t.z) : make_float2(t.z, t.z);
+        } else {
+            const float4 b = __ldcs(reinterpret_cast<const float4 *>(rp + 4));
+            if (MODE == GF_SUB_NEAREST) return make_float2(b.x, b.x);
+            const float4 a = __ldcs(reinterpret_cast<const float4 *>(rp));
+            return make_float2(a.w, b.x);
+        }
+    };
+    float2 top[JB], bot[JB];
+#pragma unroll
+    for (int u = 0; u < JB; ++u) {
+        const int j = min(j0 + u, P.h - 1);
+        if (MODE == GF_SUB_BILINEAR) {
+            top[u] = row_val(S * j + S / 2 - 1);
+            bot[u] = row_val(S * j + S / 2);
+        } else {
+            top[u] = row_val(S * j + S / 2);
+        }
+    }
+    float *dst = J.dst + (size_t)z * J.dps + i;
+#pragma unroll
+    for (int u = 0; u < JB; ++u) {
+        if (j0 + u >= P.h) break;
+        float v;
+        if (MODE == GF_SUB_BILINEAR)
+            v = 0.5f * (0.5f * top[u].x + 0.5f * top[u].y) + 0.5f * (0.5f * bot[u].x + 0.5f * bot[u].y);
+        else
+            v = top[u].x;
+        dst[(size_t)(j0 + u) * P.w] = v * P.scale;
+    }
 }
 
 // ------------------------------------------------------------------------------------------------------
-// k_sweep
+// k_box_tile
 // ------------------------------------------------------------------------------------------------------
-constexpr int SW_NT = 128;  // threads per CTA
-constexpr int SW_D = 4;     // rows whose loads are issued together
+constexpr int BT_NT = 256;  // threads per CTA
+constexpr int BT_TH = 32;   // output rows per tile
+constexpr int BT_TW = 64;   // output columns per tile
+constexpr int BT_VP = BT_TH + 1;  // pitch of the transposed column-sum tile (odd: no bank conflicts)
+constexpr int BT_OP = BT_TW + 1;  // pitch of the output staging tile
 
 enum { KIND_STATS_F = 0, KIND_STATS_INT = 1, KIND_MEAN2 = 2 };
 
-struct SweepParams {
+struct BoxParams {
     const void *X, *Y;  // KIND 0/1: guide I' and input p' planes; KIND 2: a and b planes
     size_t xps, yps;    // plane strides (elements)
     int CX, C;          // X planes per image (1 or C), Y planes per image (C)
     float *out0, *out1; // KIND 0/1: a, b.  KIND 2: mean of X, mean of Y.
     size_t ops;         // output plane stride
     void *stats;        // optional, KIND 0/1: 4 dense h*w planes per (n, c)
-    int h, w, r, TW, TH, G;
+    int h, w, r;
     float eps;
     float int_scale;    // KIND 1: 255 * k (values are integers J = int_scale * I')
 };
 
-// Neumaier-compensated accumulation: s + c carries the running sum to about one rounding of its value,
-// however many rows have entered and left the window.
-__device__ __forceinline__ void kadd(float &s, float &c, float v)
+inline size_t box_tile_smem(int nq, int r)
 {
-    const float t = s + v;
-    c += (fabsf(s) >= fabsf(v)) ? ((s - t) + v) : ((v - t) + s);
-    s = t;
+    return ((size_t)nq * (BT_TW + 2 * r) * BT_VP + 2 * BT_TH * BT_OP) * sizeof(float);
 }
 
-template <typename T, int KIND, int COLS>
-__global__ void __launch_bounds__(SW_NT) k_sweep(SweepParams P)
+// Window-sum accumulation.  With COMP the sum is Neumaier-compensated (s + c carries it to about one
+// rounding of its value); used for large radii, where a window holds hundreds of terms.  For r' <= 16 the
+// shifted FP32 sums of at most a few dozen terms stay well inside the error budget without it.
+template <bool COMP>
+__device__ __forceinline__ void kadd(float &s, float &c, float v)
 {
-    constexpr int NQ = (KIND == KIND_MEAN2) ? 2 : 4;
-    constexpr int SPANMAX = SW_NT * COLS;
-    extern __shared__ float smf[];
-    uint32_t *smu = reinterpret_cast<uint32_t *>(smf);
+    if (COMP) {
+        const float t = s + v;
+        c += (fabsf(s) >= fabsf(v)) ? ((s - t) + v) : ((v - t) + s);
+        s = t;
+    } else {
+        s += v;
+    }
+}
 
+template <int KIND>
+struct Quant {
+    static constexpr int NQ = (KIND == KIND_MEAN2) ? 2 : 4;
+    // the quantities whose window sums the kernel needs, from one (X, Y) sample
+    __device__ __forceinline__ static void of(float x, float y, float cx, float cy, float *q)
+    {
+        if (KIND == KIND_MEAN2) {
+            q[0] = x - cx;
+            q[1] = y - cy;
+        } else {
+            const float dx = x - cx, dy = y - cy;
+            q[0] = dx; q[1] = dx * dx; q[2] = dy; q[3] = dx * dy;
+        }
+    }
+    __device__ __forceinline__ static void of_int(float x, float y, uint32_t *q)
+    {
+        const uint32_t J = (uint32_t)x, Pv = (uint32_t)y;
+        q[0] = J; q[1] = J * J; q[2] = Pv; q[3] = J * Pv;
+    }
+};
+
+template <typename T, int KIND, bool COMP, int BT_RV, int BT_RH>
+__global__ void __launch_bounds__(BT_NT) k_box_tile(BoxParams P)
+{
+    using Q = Quant<KIND>;
+    constexpr int NQ = Q::NQ;
+    constexpr bool INT = (KIND == KIND_STATS_INT);
+    extern __shared__ float smf[];
     const int tid = threadIdx.x;
     const int h = P.h, w = P.w, r = P.r;
-    const int x0 = blockIdx.x * P.TW;
-    const int y0 = blockIdx.y * P.TH;
+    const int span = BT_TW + 2 * r;
+    float *Vt = smf;                        // [NQ][span][BT_VP] column sums, transposed
+    uint32_t *Vu = reinterpret_cast<uint32_t *>(smf);
+    float *Ot = smf + (size_t)NQ * span * BT_VP;  // [2][BT_TH][BT_OP] outputs
+    const int x0 = blockIdx.x * BT_TW, y0 = blockIdx.y * BT_TH;
     const int plane = blockIdx.z;  // n * C + c
     const int n = plane / P.C, c = plane - n * P.C;
     const T *Xp = (const T *)P.X + (size_t)(n * P.CX + (P.CX == 1 ? 0 : c)) * P.xps;
     const T *Yp = (const T *)P.Y + (size_t)plane * P.yps;
-    const int y_end = min(y0 + P.TH, h);
-    const int nout = min(P.TW, w - x0);
-    const int xs = x0 - r;          // global column of span index 0
-    const int span = nout + 2 * r;  // <= SPANMAX (host guarantees)
 
-    // shift for the float statistics: one value of the tile, so that sums of squares stay small
+    // shift of the float sums: one sample of the tile, so that the sums of squares stay small
     float cx = 0.0f, cy = 0.0f;
-    if (KIND != KIND_STATS_INT) {
+    if (!INT) {
         cx = ldv(Xp + (size_t)y0 * w + x0);
         cy = ldv(Yp + (size_t)y0 * w + x0);
     }
 
-    float V[COLS][NQ], Vc[COLS][NQ];
-    uint32_t U[COLS][NQ];
+    // ---- phase 1: vertical window sums of every tile column (halo columns included)
+    constexpr int NSEG_V = BT_TH / BT_RV;
+    for (int item = tid; item < span * NSEG_V; item += BT_NT) {
+        const int xc = item % span, seg = item / span;
+        const int gx = x0 - r + xc;
+        const int ya = y0 + seg * BT_RV;
+        const int vrow = seg * BT_RV;
+        if (gx < 0 || gx >= w || ya >= h) {
 #pragma unroll
-    for (int k = 0; k < COLS; ++k)
+            for (int i = 0; i < BT_RV; ++i)
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) { V[k][q] = 0.0f; Vc[k][q] = 0.0f; U[k][q] = 0u; }
-
-    int colx[COLS];
-    bool colv[COLS];
+                for (int q = 0; q < NQ; ++q) Vt[((size_t)q * span + xc) * BT_VP + vrow + i] = 0.0f;
+            continue;
+        }
+        const T *xcol = Xp + gx, *ycol = Yp + gx;
+        float S[NQ], Sc[NQ];
+        uint32_t U[NQ];
 #pragma unroll
-    for (int k = 0; k < COLS; ++k) {
-        const int j = tid + k * SW_NT;
-        colx[k] = xs + j;
-        colv[k] = (j < span) && (colx[k] >= 0) && (colx[k] < w);
-    }
-
-    const int t_begin = y0 - r, t_end = y_end + r;
-    const int t_add_min = max(0, y0 - r);
-    constexpr int D = (COLS > 2) ? 1 : SW_D;
-
-    for (int tg = t_begin; tg < t_end; tg += D) {
-        // ---- issue the loads of D rows entering and D rows leaving the window
-        float xn[D][COLS], yn[D][COLS], xo[D][COLS], yo[D][COLS];
+        for (int q = 0; q < NQ; ++q) { S[q] = 0.0f; Sc[q] = 0.0f; U[q] = 0u; }
+        auto add_row = [&](int yy, bool sub) {
+            const float xv = ldv(xcol + (size_t)yy * w), yv = ldv(ycol + (size_t)yy * w);
+            if (INT) {
+                uint32_t qv[4];
+                Q::of_int(xv, yv, qv);
 #pragma unroll
-        for (int u = 0; u < D; ++u) {
-            const int t = tg + u, to = t - 2 * r - 1;
-            const bool addv = (t >= 0) && (t < h) && (t < t_end);
-            const bool subv = (to >= t_add_min) && (to < h) && (t < t_end);
+                for (int q = 0; q < NQ; ++q) U[q] = sub ? U[q] - qv[q] : U[q] + qv[q];
+            } else {
+                float qv[NQ];
+                Q::of(xv, yv, cx, cy, qv);
 #pragma unroll
-            for (int k = 0; k < COLS; ++k) {
-                xn[u][k] = yn[u][k] = xo[u][k] = yo[u][k] = 0.0f;
-                if (colv[k] && addv) {
-                    xn[u][k] = ldv(Xp + (size_t)t * w + colx[k]);
-                    yn[u][k] = ldv(Yp + (size_t)t * w + colx[k]);
-                }
-                if (colv[k] && subv) {
-                    xo[u][k] = ldv(Xp + (size_t)to * w + colx[k]);
-                    yo[u][k] = ldv(Yp + (size_t)to * w + colx[k]);
-                }
+                for (int q = 0; q < NQ; ++q) kadd<COMP>(S[q], Sc[q], sub ? -qv[q] : qv[q]);
+            }
+        };
+        const int lo = max(0, ya - r), hi = min(h - 1, ya + r);
+#pragma unroll 4
+        for (int yy = lo; yy <= hi; ++yy) add_row(yy, false);
+#pragma unroll
+        for (int i = 0; i < BT_RV; ++i) {
+            const int y = ya + i;
+            if (i > 0) {
+                if (y + r < h) add_row(y + r, false);
+                if (y - r - 1 >= 0) add_row(y - r - 1, true);
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const size_t vi = ((size_t)q * span + xc) * BT_VP + vrow + i;
+                if (INT) Vu[vi] = U[q];
+                else Vt[vi] = S[q] + Sc[q];
             }
         }
-        // ---- process them one row at a time
+    }
+    __syncthreads();
+
+    // ---- phase 2: horizontal window sums along each tile row, then the epilogue
+    constexpr int NSEG_H = BT_TW / BT_RH;
+    for (int item = tid; item < BT_TH * NSEG_H; item += BT_NT) {
+        const int yr = item % BT_TH, seg = item / BT_TH;
+        const int y = y0 + yr;
+        const int xa = seg * BT_RH;
+        if (y >= h || x0 + xa >= w) continue;
+        const int ny = min(h - 1, y + r) - max(0, y - r) + 1;
+        float S[NQ], Sc[NQ];
+        uint32_t U[NQ];
 #pragma unroll
-        for (int u = 0; u < D; ++u) {
-            const int t = tg + u;
-            if (t >= t_end) break;  // uniform over the CTA
-            const int to = t - 2 * r - 1;
-            const bool addv = (t >= 0) && (t < h);
-            const bool subv = (to >= t_add_min) && (to < h);
+        for (int q = 0; q < NQ; ++q) { S[q] = 0.0f; Sc[q] = 0.0f; U[q] = 0u; }
+        auto vget = [&](int q, int col) -> size_t { return ((size_t)q * span + col) * BT_VP + yr; };
+        // window of tile column xa covers span columns [xa, xa + 2r]; out-of-image columns hold zeros
+        for (int k = 0; k <= 2 * r; ++k) {
 #pragma unroll
-            for (int k = 0; k < COLS; ++k) {
-                if (KIND == KIND_STATS_INT) {
-                    if (addv) {
-                        const uint32_t J = (uint32_t)xn[u][k], Pv = (uint32_t)yn[u][k];
-                        U[k][0] += J; U[k][1] += J * J; U[k][2] += Pv; U[k][3] += J * Pv;
-                    }
-                    if (subv) {
-                        const uint32_t J = (uint32_t)xo[u][k], Pv = (uint32_t)yo[u][k];
-                        U[k][0] -= J; U[k][1] -= J * J; U[k][2] -= Pv; U[k][3] -= J * Pv;
-                    }
-                } else if (KIND == KIND_STATS_F) {
-                    if (addv && colv[k]) {
-                        const float dx = xn[u][k] - cx, dy = yn[u][k] - cy;
-                        kadd(V[k][0], Vc[k][0], dx);
-                        kadd(V[k][1], Vc[k][1], dx * dx);
-                        kadd(V[k][2], Vc[k][2], dy);
-                        kadd(V[k][3], Vc[k][3], dx * dy);
-                    }
-                    if (subv && colv[k]) {
-                        const float dx = xo[u][k] - cx, dy = yo[u][k] - cy;
-                        kadd(V[k][0], Vc[k][0], -dx);
-                        kadd(V[k][1], Vc[k][1], -(dx * dx));
-                        kadd(V[k][2], Vc[k][2], -dy);
-                        kadd(V[k][3], Vc[k][3], -(dx * dy));
-                    }
-                } else {
-                    if (addv && colv[k]) {
-                        kadd(V[k][0], Vc[k][0], xn[u][k] - cx);
-                        kadd(V[k][1], Vc[k][1], yn[u][k] - cy);
-                    }
-                    if (subv && colv[k]) {
-                        kadd(V[k][0], Vc[k][0], -(xo[u][k] - cx));
-                        kadd(V[k][1], Vc[k][1], -(yo[u][k] - cy));
-                    }
-                }
+            for (int q = 0; q < NQ; ++q) {
+                if (INT) U[q] += Vu[vget(q, xa + k)];
+                else kadd<COMP>(S[q], Sc[q], Vt[vget(q, xa + k)]);
             }
-            const int yrow = t - r;  // output row whose vertical window is now complete
-            if (yrow < y0) continue; // uniform
-            // ---- stage the column sums of this row in shared memory
+        }
 #pragma unroll
-            for (int k = 0; k < COLS; ++k) {
-                const int j = tid + k * SW_NT;
-                if (j < span) {
+        for (int i = 0; i < BT_RH; ++i) {
+            const int xt = xa + i, x = x0 + xt;
+            if (x >= w) break;
+            if (i > 0) {
 #pragma unroll
-                    for (int q = 0; q < NQ; ++q) {
-                        if (KIND == KIND_STATS_INT)
-                            smu[q * SPANMAX + j] = colv[k] ? U[k][q] : 0u;
-                        else
-                            smf[q * SPANMAX + j] = colv[k] ? (V[k][q] + Vc[k][q]) : 0.0f;
-                    }
-                }
-            }
-            __syncthreads();
-            // ---- horizontal window sums: G adjacent output columns per thread, sliding
-            const int ny = min(h - 1, yrow + r) - max(0, yrow - r) + 1;
-            const size_t orow = (size_t)plane * P.ops + (size_t)yrow * w;
-            for (int base = tid * P.G; base < nout; base += SW_NT * P.G) {
-                const int xb = x0 + base;
-                float Sf[NQ];
-                uint32_t Su[NQ];
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) { Sf[q] = 0.0f; Su[q] = 0u; }
-                const int lo = max(0, xb - r), hi = min(w - 1, xb + r);
-                for (int xc = lo; xc <= hi; ++xc) {
-#pragma unroll
-                    for (int q = 0; q < NQ; ++q) {
-                        if (KIND == KIND_STATS_INT) Su[q] += smu[q * SPANMAX + xc - xs];
-                        else Sf[q] += smf[q * SPANMAX + xc - xs];
-                    }
-                }
-                const int gmax = min(P.G, nout - base);
-                for (int g = 0; g < gmax; ++g) {
-                    const int xg = xb + g;
-                    if (g > 0) {
-                        const int ad = xg + r, rm = xg - r - 1;
-#pragma unroll
-                        for (int q = 0; q < NQ; ++q) {
-                            if (KIND == KIND_STATS_INT) {
-                                if (ad < w) Su[q] += smu[q * SPANMAX + ad - xs];
-                                if (rm >= 0) Su[q] -= smu[q * SPANMAX + rm - xs];
-                            } else {
-                                if (ad < w) Sf[q] += smf[q * SPANMAX + ad - xs];
-                                if (rm >= 0) Sf[q] -= smf[q * SPANMAX + rm - xs];
-                            }
-                        }
-                    }
-                    const int nx = min(w - 1, xg + r) - max(0, xg - r) + 1;
-                    const int cnt = nx * ny;
-                    const size_t oi = orow + xg;
-                    if (KIND == KIND_STATS_F) {
-                        const float inv = 1.0f / (float)cnt;
-                        const float mI = Sf[0] * inv, mp = Sf[2] * inv;   // shifted means
-                        const float eII = Sf[1] * inv, eIp = Sf[3] * inv;
-                        const float var = fmaxf(eII - mI * mI, 0.0f);     // Algorithm 2: var_I
-                        const float cov = eIp - mI * mp;                  // Algorithm 2: cov_Ip
-                        const float a = cov / (var + P.eps);              // Eq. (2)
-                        const float b = (mp + cy) - a * (mI + cx);        // Eq. (3)
-                        P.out0[oi] = a;
-                        P.out1[oi] = b;
-                        if (P.stats) {
-                            float *st = (float *)P.stats + (size_t)plane * 4 * h * w + (size_t)yrow * w + xg;
-                            const size_t ps = (size_t)h * w;
-                            st[0] = mI + cx;
-                            st[ps] = eII + cx * (2.0f * mI + cx);
-                            st[2 * ps] = mp + cy;
-                            st[3 * ps] = eIp + cx * mp + cy * mI + cx * cy;
-                        }
-                    } else if (KIND == KIND_STATS_INT) {
-                        const long long nn = cnt;
-                        // exact integer numerators of var and cov (times n^2 (255k)^2)
-                        const long long vnum = nn * (long long)Su[1] - (long long)Su[0] * (long long)Su[0];
-                        const long long cnum = nn * (long long)Su[3] - (long long)Su[0] * (long long)Su[2];
-                        const float den = (float)vnum + P.eps * ((float)nn * (float)nn) * (P.int_scale * P.int_scale);
-                        const float a = (float)cnum / den;                                        // Eq. (2)
-                        const float b = ((float)Su[2] - a * (float)Su[0]) / ((float)cnt * P.int_scale); // Eq. (3)
-                        P.out0[oi] = a;
-                        P.out1[oi] = b;
-                        if (P.stats) {
-                            uint32_t *st = (uint32_t *)P.stats + (size_t)plane * 4 * h * w + (size_t)yrow * w + xg;
-                            const size_t ps = (size_t)h * w;
-                            st[0] = Su[0]; st[ps] = Su[1]; st[2 * ps] = Su[2]; st[3 * ps] = Su[3];
-                        }
+                for (int q = 0; q < NQ; ++q) {
+                    if (INT) {
+                        U[q] += Vu[vget(q, xt + 2 * r)];
+                        U[q] -= Vu[vget(q, xt - 1)];
                     } else {
-                        const float inv = 1.0f / (float)cnt;
-                        P.out0[oi] = Sf[0] * inv + cx;
-                        P.out1[oi] = Sf[1] * inv + cy;
+                        kadd<COMP>(S[q], Sc[q], Vt[vget(q, xt + 2 * r)]);
+                        kadd<COMP>(S[q], Sc[q], -Vt[vget(q, xt - 1)]);
                     }
                 }
             }
-            __syncthreads();
+            const int nx = min(w - 1, x + r) - max(0, x - r) + 1;
+            const int cnt = nx * ny;
+            float o0, o1;
+            if (KIND == KIND_STATS_F) {
+                const float inv = __fdividef(1.0f, (float)cnt);
+                const float mI = (S[0] + Sc[0]) * inv, mp = (S[2] + Sc[2]) * inv;  // shifted means
+                const float eII = (S[1] + Sc[1]) * inv, eIp = (S[3] + Sc[3]) * inv;
+                const float var = fmaxf(eII - mI * mI, 0.0f);  // var_I
+                const float cov = eIp - mI * mp;               // cov_Ip
+                o0 = __fdividef(cov, var + P.eps);             // a, Eq. (2)
+                o1 = (mp + cy) - o0 * (mI + cx);               // b, Eq. (3)
+                if (P.stats) {
+                    const size_t ps = (size_t)h * w;
+                    float *st = (float *)P.stats + (size_t)plane * 4 * ps + (size_t)y * w + x;
+                    st[0] = mI + cx;
+                    st[ps] = eII + cx * (2.0f * mI + cx);
+                    st[2 * ps] = mp + cy;
+                    st[3 * ps] = eIp + cx * mp + cy * mI + cx * cy;
+                }
+            } else if (KIND == KIND_STATS_INT) {
+                const long long nn = cnt;
+                // exact integer numerators of var and cov, scaled by n^2 (255k)^2
+                const long long vnum = nn * (long long)U[1] - (long long)U[0] * (long long)U[0];
+                const long long cnum = nn * (long long)U[3] - (long long)U[0] * (long long)U[2];
+                const float den = (float)vnum + P.eps * ((float)nn * (float)nn) * (P.int_scale * P.int_scale);
+                o0 = __fdividef((float)cnum, den);                                              // a, Eq. (2)
+                o1 = __fdividef((float)U[2] - o0 * (float)U[0], (float)cnt * P.int_scale);      // b, Eq. (3)
+                if (P.stats) {
+                    const size_t ps = (size_t)h * w;
+                    uint32_t *st = (uint32_t *)P.stats + (size_t)plane * 4 * ps + (size_t)y * w + x;
+                    st[0] = U[0]; st[ps] = U[1]; st[2 * ps] = U[2]; st[3 * ps] = U[3];
+                }
+            } else {
+                const float inv = __fdividef(1.0f, (float)cnt);
+                o0 = (S[0] + Sc[0]) * inv + cx;
+                o1 = (S[1] + Sc[1]) * inv + cy;
+            }
+            Ot[yr * BT_OP + xt] = o0;
+            Ot[BT_TH * BT_OP + yr * BT_OP + xt] = o1;
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 3: coalesced write of the tile
+    const size_t obase = (size_t)plane * P.ops;
+    for (int idx = tid; idx < BT_TH * BT_TW; idx += BT_NT) {
+        const int yr = idx / BT_TW, xt = idx - yr * BT_TW;
+        const int y = y0 + yr, x = x0 + xt;
+        if (y < h && x < w) {
+            P.out0[obase + (size_t)y * w + x] = Ot[yr * BT_OP + xt];
+            P.out1[obase + (size_t)y * w + x] = Ot[BT_TH * BT_OP + yr * BT_OP + xt];
         }
     }
 }
 
 // ------------------------------------------------------------------------------------------------------
-// k_upsample_output
+// k_upsample_output / k_output_s1
 // ------------------------------------------------------------------------------------------------------
-constexpr int UP_NT = 128;
+constexpr int UP_NT = 128;            // threads per CTA, 4 columns each
+constexpr int UP_BAND = UP_NT * 4;    // full-res columns per CTA
 
 struct UpParams {
     const void *I;
     const float *ma, *mb;
     void *q;
-    int C, CI, H, W, h, w, s, R, CG;  // CG: channel groups per image
+    int C, CI, H, W, h, w, s, R, CG;  // R: full-res rows per CTA; CG: channel groups per image
     size_t lps;                       // low-res plane stride
+    int LRmax, LCmax;                 // staged low-res tile bounds (rows, columns)
 };
 
 // Upsampling taps along one axis: full-res index X samples position (X + 1/2)/s - 1/2 = (2X + 1 - s)/(2s),
@@ -418,114 +493,274 @@ __device__ __forceinline__ void st4<__half>(__half *p, bool vec, int valid, cons
     }
 }
 
-template <typename TI, typename TQ, int CC, bool VEC, bool S1>
+template <typename TI, typename TQ, int CC, bool VEC>
 __global__ void __launch_bounds__(UP_NT) k_upsample_output(UpParams P)
 {
-    const int gx = blockIdx.x * UP_NT + threadIdx.x;
-    const int X0 = gx * 4;
+    extern __shared__ float tap[];  // [CC][2][LRmax][LCmax] low-res tap tile (mean_a, mean_b)
+    const int Xb = blockIdx.x * UP_BAND;
+    const int Yb = blockIdx.y * P.R, Ye = min(Yb + P.R, P.H);
+    const int n = blockIdx.z / P.CG, c0 = (blockIdx.z - n * P.CG) * CC;
+    const int ncc = min(CC, P.C - c0);
+    const size_t HW = (size_t)P.H * P.W;
+
+    // low-res rows / columns this CTA samples
+    int ly0, ly1, lx0, lx1, t0, t1;
+    float ft;
+    up_taps(Yb, P.s, P.h, ly0, t0, ft);
+    up_taps(Ye - 1, P.s, P.h, t0, ly1, ft);
+    up_taps(Xb, P.s, P.w, lx0, t1, ft);
+    up_taps(min(Xb + UP_BAND, P.W) - 1, P.s, P.w, t1, lx1, ft);
+    const int LR = ly1 - ly0 + 1, LC = lx1 - lx0 + 1;
+    const int tile = P.LRmax * P.LCmax;
+    for (int mr = 0; mr < CC * 2 * LR; ++mr) {  // (map, row) pairs; mc = cc * 2 + map
+        const int mc = mr / LR, row = mr - mc * LR;
+        const int c = min(c0 + (mc >> 1), P.C - 1);
+        const float *src = ((mc & 1) ? P.mb : P.ma) + (size_t)(n * P.C + c) * P.lps + (size_t)(ly0 + row) * P.w + lx0;
+        float *dst = tap + mc * tile + row * P.LCmax;
+        for (int col = threadIdx.x; col < LC; col += UP_NT) dst[col] = __ldg(src + col);
+    }
+    __syncthreads();
+
+    const int X0 = Xb + threadIdx.x * 4;
     if (X0 >= P.W) return;
     const int valid = min(4, P.W - X0);
     const bool vec = VEC && (valid == 4);
-    const int Yb = blockIdx.y * P.R, Ye = min(Yb + P.R, P.H);
-    const int n = blockIdx.z / P.CG, c0 = (blockIdx.z - n * P.CG) * CC;
-    const size_t HW = (size_t)P.H * P.W;
 
-    const float *MA[CC], *MB[CC];
-    TQ *Q[CC];
     const TI *Ig[CC];
+    TQ *Qp[CC];
 #pragma unroll
     for (int cc = 0; cc < CC; ++cc) {
         const int c = min(c0 + cc, P.C - 1);
-        MA[cc] = P.ma + (size_t)(n * P.C + c) * P.lps;
-        MB[cc] = P.mb + (size_t)(n * P.C + c) * P.lps;
-        Q[cc] = (TQ *)P.q + (size_t)(n * P.C + c) * HW;
+        Qp[cc] = (TQ *)P.q + (size_t)(n * P.C + c) * HW;
         Ig[cc] = (const TI *)P.I + (size_t)(n * P.CI + (P.CI == 1 ? 0 : c)) * HW;
     }
-    const int ncc = min(CC, P.C - c0);
 
-    if constexpr (S1) {
-        // s = 1: no resampling, mean_a and mean_b are already full resolution
-        for (int Y = Yb; Y < Ye; ++Y) {
-            float iv[4];
-            if (P.CI == 1) ld4<TI>(Ig[0] + (size_t)Y * P.W + X0, vec, valid, iv);
-#pragma unroll
-            for (int cc = 0; cc < CC; ++cc) {
-                if (cc >= ncc) break;
-                if (P.CI != 1) ld4<TI>(Ig[cc] + (size_t)Y * P.W + X0, vec, valid, iv);
-                float A[4], B[4], out[4];
-                ld4<float>(MA[cc] + (size_t)Y * P.W + X0, vec, valid, A);
-                ld4<float>(MB[cc] + (size_t)Y * P.W + X0, vec, valid, B);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) out[k] = fmaf(A[k], iv[k], B[k]);
-                st4<TQ>(Q[cc] + (size_t)Y * P.W + X0, vec, valid, out);
-            }
-        }
-    } else {
     int xa[4], xb[4];
     float fx[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) up_taps(min(X0 + k, P.W - 1), P.s, P.w, xa[k], xb[k], fx[k]);
+    for (int k = 0; k < 4; ++k) {
+        up_taps(min(X0 + k, P.W - 1), P.s, P.w, xa[k], xb[k], fx[k]);
+        xa[k] -= lx0;
+        xb[k] -= lx0;
+    }
 
-    // horizontally interpolated low-res rows: slot 0 = upper tap row, slot 1 = lower tap row
+    // horizontally interpolated tap rows: slot 0 = upper tap row, slot 1 = lower tap row
     float ha[CC][2][4], hb[CC][2][4];
     int cur0 = -1, cur1 = -1;
     auto load_row = [&](int yy, int slot) {
 #pragma unroll
         for (int cc = 0; cc < CC; ++cc) {
-            const float *ra = MA[cc] + (size_t)yy * P.w, *rb = MB[cc] + (size_t)yy * P.w;
+            const float *ra = tap + (cc * 2) * tile + (yy - ly0) * P.LCmax;
+            const float *rb = ra + tile;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float a0 = __ldg(ra + xa[k]), a1 = __ldg(ra + xb[k]);
-                const float b0 = __ldg(rb + xa[k]), b1 = __ldg(rb + xb[k]);
+                const float a0 = ra[xa[k]], a1 = ra[xb[k]];
+                const float b0 = rb[xa[k]], b1 = rb[xb[k]];
                 ha[cc][slot][k] = fmaf(fx[k], a1 - a0, a0);
                 hb[cc][slot][k] = fmaf(fx[k], b1 - b0, b0);
             }
         }
     };
 
+    for (int Yg = Yb; Yg < Ye; Yg += 4) {
+        float iv[4][4];
+        if (P.CI == 1) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (Yg + u < Ye) ld4<TI>(Ig[0] + (size_t)(Yg + u) * P.W + X0, vec, valid, iv[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int Y = Yg + u;
+            if (Y >= Ye) break;
+            int ya, yb;
+            float fy;
+            up_taps(Y, P.s, P.h, ya, yb, fy);
+            if (ya != cur0) {
+                if (ya == cur1) {
+#pragma unroll
+                    for (int cc = 0; cc < CC; ++cc)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) { ha[cc][0][k] = ha[cc][1][k]; hb[cc][0][k] = hb[cc][1][k]; }
+                } else {
+                    load_row(ya, 0);
+                }
+                cur0 = ya;
+                cur1 = -1;
+            }
+            if (yb != cur1) {
+                if (yb == cur0) {
+#pragma unroll
+                    for (int cc = 0; cc < CC; ++cc)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) { ha[cc][1][k] = ha[cc][0][k]; hb[cc][1][k] = hb[cc][0][k]; }
+                } else {
+                    load_row(yb, 1);
+                }
+                cur1 = yb;
+            }
+#pragma unroll
+            for (int cc = 0; cc < CC; ++cc) {
+                if (cc >= ncc) break;
+                float ivc[4];
+                if (P.CI == 1) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) ivc[k] = iv[u][k];
+                } else {
+                    ld4<TI>(Ig[cc] + (size_t)Y * P.W + X0, vec, valid, ivc);
+                }
+                float out[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float A = fmaf(fy, ha[cc][1][k] - ha[cc][0][k], ha[cc][0][k]);  // upsampled mean_a
+                    const float B = fmaf(fy, hb[cc][1][k] - hb[cc][0][k], hb[cc][0][k]);  // upsampled mean_b
+                    out[k] = fmaf(A, ivc[k], B);                                           // Eq. (4)
+                }
+                st4<TQ>(Qp[cc] + (size_t)Y * P.W + X0, vec, valid, out);
+            }
+        }
+    }
+}
+
+// s = 4 or 8, one guide channel, 4-aligned rows.  Full-res row S*j + S/2 + k (k = 0 .. S-1) samples low-res
+// rows j and j+1 with weight (2k + 1)/(2S) on row j+1, so the rows are walked in such S-row runs: one pair of
+// horizontally interpolated tap rows (and their difference) serves the whole run.  Columns: pixels 4t .. 4t+3
+// sample low-res columns i-1, i, i+1 (S = 4) or one adjacent pair of them (S = 8) with fixed weights.  Taps
+// beyond the image are clamped copies, which gives the same value as clamping the sample position.
+template <typename TI, typename TQ, int CC, int S>
+__global__ void __launch_bounds__(UP_NT) k_upsample_output_s4x(UpParams P)
+{
+    extern __shared__ float tap[];  // [CC][2][LRmax][LCmax]: low-res rows jb-1 .. jb+nb, clamped
+    const int nb = P.R / S;         // low-res rows (bands) per CTA
+    const int jb = blockIdx.y * nb;
+    const int Xb = blockIdx.x * UP_BAND;
+    const int Yb = jb * S, Ye = min(Yb + P.R, P.H);
+    const int n = blockIdx.z / P.CG, c0 = (blockIdx.z - n * P.CG) * CC;
+    const int ncc = min(CC, P.C - c0);
+    const int ly0 = jb - 1, lx0 = Xb / S - 1;
+    const int LR = P.LRmax, LC = P.LCmax, tile = LR * LC;
+    for (int mr = 0; mr < CC * 2 * LR; ++mr) {  // (map, row) pairs; mc = cc * 2 + map
+        const int mc = mr / LR, row = mr - mc * LR;
+        const int c = min(c0 + (mc >> 1), P.C - 1);
+        const int gy = min(max(ly0 + row, 0), P.h - 1);
+        const float *src = ((mc & 1) ? P.mb : P.ma) + (size_t)(n * P.C + c) * P.lps + (size_t)gy * P.w;
+        float *dst = tap + mc * tile + row * LC;
+        for (int col = threadIdx.x; col < LC; col += UP_NT) dst[col] = __ldg(src + min(max(lx0 + col, 0), P.w - 1));
+    }
+    __syncthreads();
+
+    const int X0 = Xb + threadIdx.x * 4;
+    if (X0 >= P.W) return;
+    const int ti = X0 / S - lx0;  // tile column of the low-res column that holds pixel X0 (>= 1)
+    const int g = (S == 8) ? ((X0 >> 2) & 1) : 0;
+
+    // horizontally interpolated tap row `tr` for the thread's 4 pixels, all maps
+    auto hrow = [&](int tr, float (&o)[CC][2][4]) {
+#pragma unroll
+        for (int mc = 0; mc < CC * 2; ++mc) {
+            const float *row = tap + mc * tile + tr * LC;
+            if (S == 4) {
+                const float a = row[ti - 1], b = row[ti], c = row[ti + 1];
+                o[mc >> 1][mc & 1][0] = fmaf(0.625f, b - a, a);
+                o[mc >> 1][mc & 1][1] = fmaf(0.875f, b - a, a);
+                o[mc >> 1][mc & 1][2] = fmaf(0.125f, c - b, b);
+                o[mc >> 1][mc & 1][3] = fmaf(0.375f, c - b, b);
+            } else {
+                const int lo = g ? ti : ti - 1;
+                const float a = row[lo], b = row[lo + 1];
+                const float f0 = g ? 0.0625f : 0.5625f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) o[mc >> 1][mc & 1][k] = fmaf(f0 + 0.125f * k, b - a, a);
+            }
+        }
+    };
+
+    const TI *Irow0 = (const TI *)P.I + (size_t)n * P.H * P.W + X0;
+    TQ *Qrow0[CC];
+#pragma unroll
+    for (int cc = 0; cc < CC; ++cc)
+        Qrow0[cc] = (TQ *)P.q + (size_t)(n * P.C + min(c0 + cc, P.C - 1)) * P.H * P.W + X0;
+
+    float lo[CC][2][4], d[CC][2][4];
+    hrow(0, lo);  // low-res row jb - 1
+    // run j covers full-res rows S*j + S/2 .. S*j + S/2 + S - 1 and samples low-res rows j, j+1
+    for (int t = 0; t <= nb; ++t) {
+        const int j = jb - 1 + t;
+        const int Yr = S * j + S / 2;
+        if (Yr >= Ye) break;
+        float iv[S][4];
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            const int Y = Yr + k;
+            if (Y >= Yb && Y < Ye) ld4<TI>(Irow0 + (size_t)Y * P.W, true, 4, iv[k]);
+        }
+        float hi[CC][2][4];
+        hrow(t + 1, hi);
+#pragma unroll
+        for (int cc = 0; cc < CC; ++cc)
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) d[cc][m][k] = hi[cc][m][k] - lo[cc][m][k];
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            const int Y = Yr + k;
+            if (Y < Yb || Y >= Ye) continue;
+            const float fy = (2.0f * k + 1.0f) / (2.0f * S);  // compile-time constant
+#pragma unroll
+            for (int cc = 0; cc < CC; ++cc) {
+                if (cc >= ncc) break;
+                float out[4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const float A = fmaf(fy, d[cc][0][x], lo[cc][0][x]);  // upsampled mean_a
+                    const float B = fmaf(fy, d[cc][1][x], lo[cc][1][x]);  // upsampled mean_b
+                    out[x] = fmaf(A, iv[k][x], B);                        // Eq. (4)
+                }
+                st4<TQ>(Qrow0[cc] + (size_t)Y * P.W, true, 4, out);
+            }
+        }
+#pragma unroll
+        for (int cc = 0; cc < CC; ++cc)
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) lo[cc][m][k] = hi[cc][m][k];
+    }
+}
+
+template <typename TI, typename TQ, int CC, bool VEC>
+__global__ void __launch_bounds__(UP_NT) k_output_s1(UpParams P)
+{
+    const int X0 = (blockIdx.x * UP_NT + threadIdx.x) * 4;
+    if (X0 >= P.W) return;
+    const int valid = min(4, P.W - X0);
+    const bool vec = VEC && (valid == 4);
+    const int Yb = blockIdx.y * P.R, Ye = min(Yb + P.R, P.H);
+    const int n = blockIdx.z / P.CG, c0 = (blockIdx.z - n * P.CG) * CC;
+    const int ncc = min(CC, P.C - c0);
+    const size_t HW = (size_t)P.H * P.W;
     for (int Y = Yb; Y < Ye; ++Y) {
-        int ya, yb;
-        float fy;
-        up_taps(Y, P.s, P.h, ya, yb, fy);
-        if (ya != cur0) {
-            if (ya == cur1) {
-#pragma unroll
-                for (int cc = 0; cc < CC; ++cc)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) { ha[cc][0][k] = ha[cc][1][k]; hb[cc][0][k] = hb[cc][1][k]; }
-            } else {
-                load_row(ya, 0);
-            }
-            cur0 = ya;
-            cur1 = -1;
-        }
-        if (yb != cur1) {
-            if (yb == cur0) {
-#pragma unroll
-                for (int cc = 0; cc < CC; ++cc)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) { ha[cc][1][k] = ha[cc][0][k]; hb[cc][1][k] = hb[cc][0][k]; }
-            } else {
-                load_row(yb, 1);
-            }
-            cur1 = yb;
-        }
         float iv[4];
-        if (P.CI == 1) ld4<TI>(Ig[0] + (size_t)Y * P.W + X0, vec, valid, iv);
+        if (P.CI == 1) ld4<TI>((const TI *)P.I + (size_t)n * HW + (size_t)Y * P.W + X0, vec, valid, iv);
+        float A[CC][4], B[CC][4];
 #pragma unroll
         for (int cc = 0; cc < CC; ++cc) {
             if (cc >= ncc) break;
-            if (P.CI != 1) ld4<TI>(Ig[cc] + (size_t)Y * P.W + X0, vec, valid, iv);
+            const size_t lo = (size_t)(n * P.C + c0 + cc) * P.lps + (size_t)Y * P.W + X0;
+            ld4<float>(P.ma + lo, vec, valid, A[cc]);
+            ld4<float>(P.mb + lo, vec, valid, B[cc]);
+        }
+#pragma unroll
+        for (int cc = 0; cc < CC; ++cc) {
+            if (cc >= ncc) break;
+            const int c = c0 + cc;
+            if (P.CI != 1) ld4<TI>((const TI *)P.I + (size_t)(n * P.CI + c) * HW + (size_t)Y * P.W + X0, vec, valid, iv);
             float out[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float A = fmaf(fy, ha[cc][1][k] - ha[cc][0][k], ha[cc][0][k]);  // upsampled mean_a
-                const float B = fmaf(fy, hb[cc][1][k] - hb[cc][0][k], hb[cc][0][k]);  // upsampled mean_b
-                out[k] = fmaf(A, iv[k], B);                                            // Eq. (4)
-            }
-            st4<TQ>(Q[cc] + (size_t)Y * P.W + X0, vec, valid, out);
+            for (int k = 0; k < 4; ++k) out[k] = fmaf(A[cc][k], iv[k], B[cc][k]);  // Eq. (4), s = 1
+            st4<TQ>((TQ *)P.q + (size_t)(n * P.C + c) * HW + (size_t)Y * P.W + X0, vec, valid, out);
         }
-    }
     }
 }
 
@@ -546,66 +781,71 @@ template <typename T>
 void launch_sub_t(const SubParams &sp, dim3 grid, cudaStream_t st)
 {
     switch (sp.mode) {
-    case GF_SUB_NEAREST: k_subsample<T, GF_SUB_NEAREST><<<grid, 256, 0, st>>>(sp); break;
-    case GF_SUB_BILINEAR: k_subsample<T, GF_SUB_BILINEAR><<<grid, 256, 0, st>>>(sp); break;
-    default: k_subsample<T, GF_SUB_BOX><<<grid, 256, 0, st>>>(sp); break;
+    case GF_SUB_NEAREST: k_subsample<T, GF_SUB_NEAREST><<<grid, SUB_NT, 0, st>>>(sp); break;
+    case GF_SUB_BILINEAR: k_subsample<T, GF_SUB_BILINEAR><<<grid, SUB_NT, 0, st>>>(sp); break;
+    default: k_subsample<T, GF_SUB_BOX><<<grid, SUB_NT, 0, st>>>(sp); break;
     }
 }
 
-int next_pow2(int v)
+template <typename T, int KIND, bool COMP, int RV, int RH>
+cudaError_t launch_box_v(const BoxParams &bp, int planes, cudaStream_t st)
 {
-    int p = 1;
-    while (p < v) p <<= 1;
-    return p;
-}
-
-// Tile geometry of a sweep launch.
-void sweep_geometry(int h, int w, int r, int planes, int &cols, int &TW, int &TH, int &G, dim3 &grid)
-{
-    cols = (32 + 2 * r <= SW_NT * 2) ? 2 : 8;
-    const int spanmax = SW_NT * cols;
-    TW = std::min(128, spanmax - 2 * r);
-    TW = std::min(TW, ((w + 31) / 32) * 32);
-    G = (r <= 1) ? 1 : std::min(16, next_pow2(r));
-    const int strips = (w + TW - 1) / TW;
-    const int target = 152 * 8;
-    int chunks = std::max(1, (target + strips * planes - 1) / (strips * planes));
-    TH = (h + chunks - 1) / chunks;
-    TH = std::max(TH, std::max(8, 2 * r));
-    TH = std::min(TH, h);
-    chunks = (h + TH - 1) / TH;
-    grid = dim3(strips, chunks, planes);
-}
-
-template <typename T, int KIND>
-cudaError_t launch_sweep_t(SweepParams sp, int planes, cudaStream_t st)
-{
-    int cols, TW, TH, G;
-    dim3 grid;
-    sweep_geometry(sp.h, sp.w, sp.r, planes, cols, TW, TH, G, grid);
-    sp.TW = TW; sp.TH = TH; sp.G = G;
     const int nq = (KIND == KIND_MEAN2) ? 2 : 4;
-    const size_t smem = (size_t)nq * SW_NT * cols * sizeof(float);
-    if (cols == 2)
-        k_sweep<T, KIND, 2><<<grid, SW_NT, smem, st>>>(sp);
-    else
-        k_sweep<T, KIND, 8><<<grid, SW_NT, smem, st>>>(sp);
+    const size_t smem = box_tile_smem(nq, bp.r);
+    static size_t configured = 0;  // largest dynamic shared memory opted in so far for this instantiation
+    if (smem > 48 * 1024 && smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_box_tile<T, KIND, COMP, RV, RH>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    dim3 grid((bp.w + BT_TW - 1) / BT_TW, (bp.h + BT_TH - 1) / BT_TH, planes);
+    k_box_tile<T, KIND, COMP, RV, RH><<<grid, BT_NT, smem, st>>>(bp);
     return cudaGetLastError();
 }
 
-template <typename TI, typename TQ>
-void launch_up_t(const UpParams &up, int N, int CC, bool vec, bool s1, cudaStream_t st)
+// Segment lengths grow with the radius (a segment pays 2r'+1 loads to open its window); compensated
+// sums for windows of more than 33 x 33 terms.
+template <typename T, int KIND>
+cudaError_t launch_box_t(const BoxParams &bp, int planes, cudaStream_t st)
 {
-    const int groups = (up.W + 3) / 4;
-    dim3 grid((groups + UP_NT - 1) / UP_NT, (up.H + up.R - 1) / up.R, N * up.CG);
-#define GF_UP(cc, v, one) k_upsample_output<TI, TQ, cc, v, one><<<grid, UP_NT, 0, st>>>(up)
-    if (CC == 3) {
-        if (vec) { if (s1) GF_UP(3, true, true); else GF_UP(3, true, false); }
-        else { if (s1) GF_UP(3, false, true); else GF_UP(3, false, false); }
-    } else {
-        if (vec) { if (s1) GF_UP(1, true, true); else GF_UP(1, true, false); }
-        else { if (s1) GF_UP(1, false, true); else GF_UP(1, false, false); }
+    if (bp.r <= 8) return launch_box_v<T, KIND, false, 8, 8>(bp, planes, st);
+    if (bp.r <= 16) return launch_box_v<T, KIND, false, 16, 16>(bp, planes, st);
+    return launch_box_v<T, KIND, true, 16, 16>(bp, planes, st);
+}
+
+template <typename TI, typename TQ>
+void launch_up_t(UpParams up, int N, int CC, bool vec, cudaStream_t st)
+{
+    const bool s1 = (up.s == 1);
+    const int bands = (up.W + UP_BAND - 1) / UP_BAND;
+    if (s1) {
+        dim3 grid(bands, (up.H + up.R - 1) / up.R, N * up.CG);
+#define GF_S1(cc, v) k_output_s1<TI, TQ, cc, v><<<grid, UP_NT, 0, st>>>(up)
+        if (CC == 3) { if (vec) GF_S1(3, true); else GF_S1(3, false); }
+        else { if (vec) GF_S1(1, true); else GF_S1(1, false); }
+#undef GF_S1
+        return;
     }
+    if (vec && up.CI == 1 && (up.s == 4 || up.s == 8)) {
+        up.R = 4 * up.s;  // 4 low-res rows per CTA
+        up.LRmax = up.R / up.s + 2;
+        up.LCmax = UP_BAND / up.s + 2;
+        dim3 grid(bands, (up.H + up.R - 1) / up.R, N * up.CG);
+        const size_t smem = (size_t)CC * 2 * up.LRmax * up.LCmax * sizeof(float);
+#define GF_UPX(cc, ss) k_upsample_output_s4x<TI, TQ, cc, ss><<<grid, UP_NT, smem, st>>>(up)
+        if (up.s == 4) { if (CC == 3) GF_UPX(3, 4); else GF_UPX(1, 4); }
+        else { if (CC == 3) GF_UPX(3, 8); else GF_UPX(1, 8); }
+#undef GF_UPX
+        return;
+    }
+    up.LRmax = (up.R + up.s - 1) / up.s + 2;
+    up.LCmax = (UP_BAND + up.s - 1) / up.s + 2;
+    dim3 grid(bands, (up.H + up.R - 1) / up.R, N * up.CG);
+    const size_t smem = (size_t)CC * 2 * up.LRmax * up.LCmax * sizeof(float);
+#define GF_UP(cc, v) k_upsample_output<TI, TQ, cc, v><<<grid, UP_NT, smem, st>>>(up)
+    if (CC == 3) { if (vec) GF_UP(3, true); else GF_UP(3, false); }
+    else { if (vec) GF_UP(1, true); else GF_UP(1, false); }
 #undef GF_UP
 }
 
@@ -622,62 +862,63 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
     // ---- Algorithm 2, first step: subsample I and p (skipped at s = 1)
     const void *Xsrc = P.I, *Ysrc = P.p;
     int src_dt = P.dt_in;
-    if (P.s > 1 || P.p_lowres) {
+    if (P.s > 1) {
         SubParams sp;
         sp.h = P.h; sp.w = P.w; sp.mode = P.mode;
-        sp.scale = 1.0f;
         // uint8 path: carry the subsampled values as exact integers J = k * (value in 1/255 units)
-        if (P.int_stats) sp.scale = P.int_scale / 255.0f;
-        int nz = 0;
-        if (P.s > 1) {
-            sp.job[0] = SubJob{P.I, P.Il, P.N * P.CI, P.H, P.W, P.s, (size_t)P.H * P.W, P.lps};
-            nz = P.N * P.CI;
-            if (!P.p_lowres) {
-                sp.job[1] = SubJob{P.p, P.pl, planesNC, P.H, P.W, P.s, (size_t)P.H * P.W, P.lps};
-                nz += planesNC;
+        sp.scale = P.int_stats ? P.int_scale / 255.0f : 1.0f;
+        sp.job[0] = SubJob{P.I, P.Il, P.N * P.CI, P.H, P.W, P.s, (size_t)P.H * P.W, P.lps};
+        if (!P.p_lowres)
+            sp.job[1] = SubJob{P.p, P.pl, planesNC, P.H, P.W, P.s, (size_t)P.H * P.W, P.lps};
+        else  // a low-res p is only copied into the FP32 workspace
+            sp.job[1] = SubJob{P.p, P.pl, planesNC, P.h, P.w, 1, (size_t)P.h * P.w, P.lps};
+        const int nz = P.N * P.CI + planesNC;
+        const bool vec_ok = (P.dt_in == F32) && !P.p_lowres && (P.mode != GF_SUB_BOX) &&
+                            (P.s == 2 || P.s == 4 || P.s == 8) && (P.H % P.s == 0) && (P.W % P.s == 0) &&
+                            (P.W % 4 == 0) && aligned16(P.I) && aligned16(P.p);
+        tm.before();
+        if (vec_ok) {
+            const int jb = (P.s == 8) ? 4 : 8;
+            dim3 grid((P.w + SUB_NT - 1) / SUB_NT, (P.h + jb - 1) / jb, nz);
+#define GF_SV(m, ss) k_subsample_vec<m, ss><<<grid, SUB_NT, 0, st>>>(sp)
+            if (P.mode == GF_SUB_BILINEAR) {
+                if (P.s == 2) GF_SV(GF_SUB_BILINEAR, 2); else if (P.s == 4) GF_SV(GF_SUB_BILINEAR, 4); else GF_SV(GF_SUB_BILINEAR, 8);
             } else {
-                sp.job[1] = SubJob{P.p, P.pl, planesNC, P.h, P.w, 1, (size_t)P.h * P.w, P.lps};
-                nz += planesNC;
+                if (P.s == 2) GF_SV(GF_SUB_NEAREST, 2); else if (P.s == 4) GF_SV(GF_SUB_NEAREST, 4); else GF_SV(GF_SUB_NEAREST, 8);
             }
+#undef GF_SV
         } else {
-            // s = 1 with a low-res p is the same grid: nothing to resample
-            sp.job[0] = SubJob{P.p, P.pl, 0, P.h, P.w, 1, (size_t)P.h * P.w, P.lps};
-            sp.job[1] = sp.job[0];
-            nz = 0;
-        }
-        if (nz > 0) {
-            dim3 grid((P.w + 255) / 256, P.h, nz);
-            tm.before();
+            dim3 grid((P.w + SUB_NT - 1) / SUB_NT, (P.h + SUB_JB - 1) / SUB_JB, nz);
             if (P.dt_in == F32) launch_sub_t<float>(sp, grid, st);
             else if (P.dt_in == F16) launch_sub_t<__half>(sp, grid, st);
             else launch_sub_t<uint8_t>(sp, grid, st);
-            tm.after();
-            if ((err = cudaGetLastError()) != cudaSuccess) return err;
-            Xsrc = P.Il;
-            Ysrc = P.pl;
-            src_dt = F32;
         }
+        tm.after();
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        Xsrc = P.Il;
+        Ysrc = P.pl;
+        src_dt = F32;
     }
 
     // ---- Algorithm 2, box statistics + var/cov + coefficients a, b (Eq. 2-3)
     {
-        SweepParams sp{};
-        sp.X = Xsrc; sp.Y = Ysrc;
-        const bool lowres_src = (src_dt == F32 && (P.s > 1));
-        sp.xps = lowres_src ? P.lps : (size_t)P.h * P.w;
-        sp.yps = lowres_src ? P.lps : (size_t)P.h * P.w;
-        sp.CX = P.CI; sp.C = P.C;
-        sp.out0 = P.a; sp.out1 = P.b; sp.ops = P.lps;
-        sp.stats = P.stats;
-        sp.h = P.h; sp.w = P.w; sp.r = P.r_low; sp.eps = P.eps;
-        sp.int_scale = P.int_scale;
+        BoxParams bp{};
+        bp.X = Xsrc; bp.Y = Ysrc;
+        const bool lowres_src = (P.s > 1);
+        bp.xps = lowres_src ? P.lps : (size_t)P.h * P.w;
+        bp.yps = lowres_src ? P.lps : (size_t)P.h * P.w;
+        bp.CX = P.CI; bp.C = P.C;
+        bp.out0 = P.a; bp.out1 = P.b; bp.ops = P.lps;
+        bp.stats = P.stats;
+        bp.h = P.h; bp.w = P.w; bp.r = P.r_low; bp.eps = P.eps;
+        bp.int_scale = P.int_scale;
         tm.before();
         if (P.int_stats) {
-            if (src_dt == F32) err = launch_sweep_t<float, KIND_STATS_INT>(sp, planesNC, st);
-            else err = launch_sweep_t<uint8_t, KIND_STATS_INT>(sp, planesNC, st);
+            if (src_dt == F32) err = launch_box_t<float, KIND_STATS_INT>(bp, planesNC, st);
+            else err = launch_box_t<uint8_t, KIND_STATS_INT>(bp, planesNC, st);
         } else {
-            if (src_dt == F32) err = launch_sweep_t<float, KIND_STATS_F>(sp, planesNC, st);
-            else err = launch_sweep_t<__half, KIND_STATS_F>(sp, planesNC, st);
+            if (src_dt == F32) err = launch_box_t<float, KIND_STATS_F>(bp, planesNC, st);
+            else err = launch_box_t<__half, KIND_STATS_F>(bp, planesNC, st);
         }
         tm.after();
         if (err != cudaSuccess) return err;
@@ -685,41 +926,41 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
 
     // ---- Algorithm 2, box means of a and b
     {
-        SweepParams sp{};
-        sp.X = P.a; sp.Y = P.b;
-        sp.xps = P.lps; sp.yps = P.lps;
-        sp.CX = P.C; sp.C = P.C;
-        sp.out0 = P.ma; sp.out1 = P.mb; sp.ops = P.lps;
-        sp.h = P.h; sp.w = P.w; sp.r = P.r_low;
+        BoxParams bp{};
+        bp.X = P.a; bp.Y = P.b;
+        bp.xps = P.lps; bp.yps = P.lps;
+        bp.CX = P.C; bp.C = P.C;
+        bp.out0 = P.ma; bp.out1 = P.mb; bp.ops = P.lps;
+        bp.h = P.h; bp.w = P.w; bp.r = P.r_low;
         tm.before();
-        err = launch_sweep_t<float, KIND_MEAN2>(sp, planesNC, st);
+        err = launch_box_t<float, KIND_MEAN2>(bp, planesNC, st);
         tm.after();
         if (err != cudaSuccess) return err;
     }
 
     // ---- Algorithm 2, bilinear upsample of mean_a, mean_b fused with q = mean_a .* I + mean_b
     {
-        UpParams up;
+        UpParams up{};
         up.I = P.I; up.ma = P.ma; up.mb = P.mb; up.q = P.q;
         up.C = P.C; up.CI = P.CI; up.H = P.H; up.W = P.W; up.h = P.h; up.w = P.w; up.s = P.s;
         up.lps = P.lps;
         const int CC = (P.C % 3 == 0) ? 3 : 1;
         up.CG = P.C / CC;
         const bool s1 = (P.s == 1);
-        up.R = s1 ? 8 : 4 * P.s;
+        up.R = s1 ? 8 : std::max(8, 4 * P.s);
         // 4-wide vector accesses need every row of every plane to start on the vector boundary
         const bool vec = (P.W % 4 == 0) && aligned16(P.I) && aligned16(P.q) &&
                          (!s1 || ((P.lps % 4 == 0) && aligned16(P.ma) && aligned16(P.mb)));
         tm.before();
         if (P.dt_in == F32) {
-            if (P.dt_out == F32) launch_up_t<float, float>(up, P.N, CC, vec, s1, st);
-            else launch_up_t<float, __half>(up, P.N, CC, vec, s1, st);
+            if (P.dt_out == F32) launch_up_t<float, float>(up, P.N, CC, vec, st);
+            else launch_up_t<float, __half>(up, P.N, CC, vec, st);
         } else if (P.dt_in == F16) {
-            if (P.dt_out == F32) launch_up_t<__half, float>(up, P.N, CC, vec, s1, st);
-            else launch_up_t<__half, __half>(up, P.N, CC, vec, s1, st);
+            if (P.dt_out == F32) launch_up_t<__half, float>(up, P.N, CC, vec, st);
+            else launch_up_t<__half, __half>(up, P.N, CC, vec, st);
         } else {
-            if (P.dt_out == F32) launch_up_t<uint8_t, float>(up, P.N, CC, vec, s1, st);
-            else launch_up_t<uint8_t, __half>(up, P.N, CC, vec, s1, st);
+            if (P.dt_out == F32) launch_up_t<uint8_t, float>(up, P.N, CC, vec, st);
+            else launch_up_t<uint8_t, __half>(up, P.N, CC, vec, st);
         }
         tm.after();
         if ((err = cudaGetLastError()) != cudaSuccess) return err;

@@ -15,6 +15,9 @@ namespace gfk {
 // Element type of an input plane.
 enum DType { F32 = GF_F32, F16 = GF_F16, U8 = GF_U8 };
 
+// Largest low-res radius r' the box kernels support (their shared tile grows with r').
+constexpr int MAX_LOWRES_RADIUS = 128;
+
 inline size_t dtype_size(int dt) { return dt == F32 ? 4 : (dt == F16 ? 2 : 1); }
 
 // Low-res planes in the workspace start on 256-byte boundaries.

@@ -52,8 +52,16 @@ CASES = [
     (2, 1, 3, 96, 128, 8, 1e-2, 4, 1),      # batch
     (2, 3, 3, 96, 128, 8, 1e-2, 4, 2),      # depthwise guide
     (1, 1, 1, 200, 300, 16, 1e-3, 1, 1),    # plain guided filter, r = 16
-    (1, 1, 1, 150, 420, 120, 1e-3, 1, 1),   # r' > 112: wide-span sweep variant
+    (1, 1, 1, 150, 420, 120, 1e-3, 1, 1),   # r = 120: large radius, compensated sums
     (1, 1, 2, 40, 1024, 60, 1e-6, 4, 1),    # paper's feathering radius (r' = 15), tiny eps
+    (1, 1, 2, 203, 408, 16, 1e-3, 8, 1),    # s = 8 fast output path with a ragged last band
+    (1, 1, 3, 120, 200, 8, 1e-3, 8, 1),     # s = 8 vector subsample + fast output, W % 8 == 0
+    (1, 1, 3, 124, 204, 8, 1e-3, 8, 0),     # s = 8, W % 8 == 4: last 4-pixel group is a half cell
+    (1, 1, 1, 64, 36, 4, 1e-2, 4, 0),       # narrower than one 512-pixel band
+    (1, 1, 3, 128, 260, 6, 1e-2, 2, 1),     # s = 2 vector subsample
+    (1, 1, 3, 130, 262, 6, 1e-2, 2, 0),     # s = 2, W % 4 != 0: generic paths
+    (1, 1, 3, 97, 1300, 9, 1e-3, 4, 1),     # s = 4 fast output, H % 4 != 0, several bands across
+    (1, 1, 1, 2000, 48, 40, 1e-3, 1, 1),    # s = 1, r = 40: compensated box sums
 ]
 
 
