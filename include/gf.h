@@ -142,6 +142,25 @@ gf_status gf_filter(gf_ctx *ctx, const void *I, const void *p, void *q, int H, i
 gf_status gf_filter_host(gf_ctx *ctx, const void *I_host, const void *p_host, void *q_host, int H, int W, int C,
                          int r, float eps, int s, gf_subsample_mode mode, const gf_opts *opts, void *cuda_stream);
 
+/*
+ * gf_filter without any device allocation.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc -- a plugin whose host application owns every device allocation
+ * through its own pool or budget, code that must not take the allocator's locks or its implicit
+ * synchronisation on a latency-critical path, or a C caller with no context object to own an arena.
+ *
+ * Same arguments and results as gf_filter (no ctx; opts->workspace must be NULL).  The scratch is one
+ * fixed array of 64 MiB compiled into the library, which every GPU that loads the library holds until the
+ * process exits; a call whose scratch (gf_workspace_size) exceeds 64 MiB returns GF_EINVAL with a message
+ * (a 12 MP, 3-channel FP32 call at s = 4 needs about 48 MB; s = 1 at that size does not fit).  Runs on the
+ * current CUDA device.  The first call on each device looks up that device's address of the array; make
+ * that first call before any stream capture.  Every call shares the one array, which keeps the last
+ * call's contents (the filter writes each scratch plane before reading it, so nothing needs clearing):
+ * calls whose kernels overlap on the GPU -- on different streams, or from different threads -- race on
+ * it and must be serialised by the caller.  No cudaMalloc, cudaFree or other allocating call is made.
+ */
+gf_status gf_filter_noalloc(const void *I, const void *p, void *q, int H, int W, int C, int r, float eps, int s,
+                            gf_subsample_mode mode, const gf_opts *opts, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

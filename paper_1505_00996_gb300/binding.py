@@ -87,6 +87,8 @@ def load_library(build_if_missing=True):
         lib.gf_filter.restype = i
         lib.gf_filter_host.argtypes = [vp, vp, vp, vp, i, i, i, i, f, i, i, P(GFOpts), vp]
         lib.gf_filter_host.restype = i
+        lib.gf_filter_noalloc.argtypes = [vp, vp, vp, i, i, i, i, f, i, i, P(GFOpts), vp]
+        lib.gf_filter_noalloc.restype = i
         _lib = lib
         return lib
 

@@ -65,12 +65,22 @@ int lowres_radius(int r, int s)
     return rl;
 }
 
-struct Resolved {
-    int N, C, CI, H, W, h, w, s, r_low, mode, dt_in, dt_out;
-    bool p_lowres, dense_lowres, int_stats;
-    float eps, int_scale;
-    size_t lps;  // low-res plane stride in floats
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard()
+    {
+        if (changed) cudaSetDevice(prev);
+    }
 };
+
+}  // namespace
+
+namespace gfk {
 
 // Check every argument of a forward call and derive its geometry.  No CUDA call.
 gf_status resolve(int H, int W, int C, int r, float eps, int s, int mode, const gf_opts *o, Resolved &R)
@@ -118,10 +128,6 @@ gf_status resolve(int H, int W, int C, int r, float eps, int s, int mode, const 
     return GF_OK;
 }
 
-struct Layout {
-    size_t off_Il, off_pl, off_a, off_b, off_ma, off_mb, total;
-};
-
 Layout layout_of(const Resolved &R, const gf_opts *o)
 {
     const size_t pb = R.lps * sizeof(float);
@@ -140,20 +146,12 @@ Layout layout_of(const Resolved &R, const gf_opts *o)
     return L;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    bool changed = false;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = (cudaSetDevice(dev) == cudaSuccess);
-    }
-    ~DeviceGuard()
-    {
-        if (changed) cudaSetDevice(prev);
-    }
-};
+}  // namespace gfk
 
-}  // namespace
+using gfk::Layout;
+using gfk::Resolved;
+using gfk::layout_of;
+using gfk::resolve;
 
 extern "C" {
 

@@ -43,6 +43,23 @@ struct FwdPlan {
     cudaEvent_t *events; // 2*GF_MAX_STAGES or NULL
 };
 
+// A forward call's arguments, checked and resolved on the host (gf_api.cu).
+struct Resolved {
+    int N, C, CI, H, W, h, w, s, r_low, mode, dt_in, dt_out;
+    bool p_lowres, dense_lowres, int_stats;
+    float eps, int_scale;
+    size_t lps;  // low-res plane stride in floats
+};
+// Check every argument of a forward call and derive its geometry (no CUDA call).  On error the thread's
+// gf_last_error() message is set.
+gf_status resolve(int H, int W, int C, int r, float eps, int s, int mode, const gf_opts *o, Resolved &R);
+
+// Byte offsets of a forward call's low-res planes in its scratch.
+struct Layout {
+    size_t off_Il, off_pl, off_a, off_b, off_ma, off_mb, total;
+};
+Layout layout_of(const Resolved &R, const gf_opts *o);
+
 // Launch the forward chain on `stream`.  Returns cudaSuccess or the first launch error.
 cudaError_t launch_forward(const FwdPlan &P, cudaStream_t stream);
 
