@@ -143,6 +143,21 @@ gf_status gf_filter_host(gf_ctx *ctx, const void *I_host, const void *p_host, vo
                          int r, float eps, int s, gf_subsample_mode mode, const gf_opts *opts, void *cuda_stream);
 
 /*
+ * Backward pass of gf_filter: the exact derivative of Algorithm 2 (the paper gives none; it is derived by
+ * the chain rule through every step, with the transposed box mean sum_{k: i in w_k} y_k / n_k at borders).
+ *   dq: dL/dq, N x C x H x W.  Outputs (overwritten): dI (N x CI x H x W), dp (same shape as p: full
+ *   resolution, or N x C x h x w when opts->p_lowres), and, if d_eps is not NULL, the device scalar
+ *   dL/d eps (summed over every channel, pixel and batch element).  All FP32 (opts->dtype_in and dtype_out
+ *   must be GF_F32); the other arguments are those of the forward call.  The forward statistics are
+ *   recomputed.  Scratch: the context arena, or opts->workspace of gf_backward_workspace_size() bytes.
+ *   Asynchronous on cuda_stream; deterministic (no atomics).
+ */
+gf_status gf_backward_workspace_size(int H, int W, int C, int s, const gf_opts *opts, size_t *bytes);
+gf_status gf_filter_backward(gf_ctx *ctx, const void *I, const void *p, const void *dq, void *dI, void *dp, float *d_eps,
+                             int H, int W, int C, int r, float eps, int s, gf_subsample_mode mode, const gf_opts *opts,
+                             void *cuda_stream);
+
+/*
  * gf_filter without any device allocation.  The paper has no counterpart: this entry point exists for
  * callers that cannot call cudaMalloc -- a plugin whose host application owns every device allocation
  * through its own pool or budget, code that must not take the allocator's locks or its implicit

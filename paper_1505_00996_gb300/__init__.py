@@ -7,5 +7,6 @@ from .binding import (  # noqa: F401
     GF_OK, GF_PENDING, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_ETIMEOUT, GF_EBUSY, GF_ECANCELED, GF_ENOTFOUND,
     GF_SUB_NEAREST, GF_SUB_BILINEAR, GF_SUB_BOX, GF_F32, GF_F16, GF_U8, GF_MAX_STAGES, MODES, GFError, GFOpts,
     Context, default_context, fast_guided_filter, fast_guided_filter_host, load_library, library_path,
-    lowres_geometry, opts_init,
+    lowres_geometry, opts_init, fast_guided_filter_backward,
 )
+from .autograd import FastGuidedFilter, FastGuidedFilterFn  # noqa: F401

@@ -89,6 +89,10 @@ def load_library(build_if_missing=True):
         lib.gf_filter_host.restype = i
         lib.gf_filter_noalloc.argtypes = [vp, vp, vp, i, i, i, i, f, i, i, P(GFOpts), vp]
         lib.gf_filter_noalloc.restype = i
+        lib.gf_backward_workspace_size.argtypes = [i, i, i, i, P(GFOpts), P(sz)]
+        lib.gf_backward_workspace_size.restype = i
+        lib.gf_filter_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, i, i, i, f, i, i, P(GFOpts), vp]
+        lib.gf_filter_backward.restype = i
         _lib = lib
         return lib
 
@@ -270,3 +274,37 @@ def fast_guided_filter_host(I, p, r, eps, s=4, mode="bilinear", *, out=None, out
         check(load_library().gf_filter_host(ctx.handle, _ptr(I4), _ptr(p4), _ptr(out), H, W, C, int(r),
                                             float(eps), int(s), m, ctypes.byref(o), _stream_handle(stream)))
     return out.reshape(p.shape[:-2] + (H, W)) if prank < 4 else out
+
+
+def fast_guided_filter_backward(I, p, dq, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowres=False,
+                                need_eps=True, stream=None, ctx=None):
+    """Backward pass of ``fast_guided_filter`` via ``gf_filter_backward`` (FP32 CUDA tensors).
+
+    dq has the shape of q.  Returns (dI, dp, deps): dI shaped like I, dp shaped like p, deps a 0-dim
+    device tensor (or None when ``need_eps`` is False)."""
+    if not (I.is_cuda and p.is_cuda and dq.is_cuda):
+        raise ValueError("I, p and dq must be CUDA tensors")
+    if I.dtype != torch.float32 or p.dtype != torch.float32 or dq.dtype != torch.float32:
+        raise ValueError("the backward pass takes float32 tensors")
+    I4, irank = _nchw(I, "I")
+    p4, prank = _nchw(p, "p")
+    N, CI, H, W = I4.shape
+    C = p4.shape[1]
+    dq4 = dq.reshape(N, C, H, W).contiguous()
+    I4 = I4.contiguous()
+    p4 = p4.contiguous()
+    dI = torch.empty_like(I4)
+    dp = torch.empty_like(p4)
+    deps = torch.empty((), dtype=torch.float32, device=I.device) if need_eps else None
+    o = opts_init()
+    o.batch = N
+    o.guide_channels = CI
+    o.r_low = -1 if r_low is None else int(r_low)
+    o.p_lowres = int(bool(p_lowres))
+    ctx = ctx or default_context(I.device.index)
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    with torch.cuda.device(I.device):
+        check(load_library().gf_filter_backward(ctx.handle, _ptr(I4), _ptr(p4), _ptr(dq4), _ptr(dI), _ptr(dp),
+                                                _ptr(deps), H, W, C, int(r), float(eps), int(s), m, ctypes.byref(o),
+                                                _stream_handle(stream)))
+    return dI.reshape(I.shape), dp.reshape(p.shape), deps

@@ -146,12 +146,48 @@ Layout layout_of(const Resolved &R, const gf_opts *o)
     return L;
 }
 
+// Scratch of a backward call: the forward planes, the dense window statistics, and the adjoint planes.
+struct BwdLayout {
+    Layout fwd;
+    size_t off_stats, off_dma, off_dmb, off_gq[4], off_dIl, off_dpl, off_eps, total;
+};
+
+BwdLayout bwd_layout_of(const Resolved &R)
+{
+    BwdLayout B;
+    B.fwd = layout_of(R, nullptr);
+    size_t off = B.fwd.total;
+    auto take = [&](size_t bytes) { size_t at = off; off += (bytes + 255) & ~size_t(255); return at; };
+    const size_t nc = (size_t)R.N * R.C * R.lps * sizeof(float);
+    B.off_stats = take((size_t)R.N * R.C * 4 * R.h * R.w * sizeof(float));
+    B.off_dma = take(nc);
+    B.off_dmb = take(nc);
+    for (int k = 0; k < 4; ++k) B.off_gq[k] = take(nc);
+    B.off_dIl = take(nc);
+    B.off_dpl = take(nc);
+    B.off_eps = take(bwd_eps_partials(R.N, R.C, R.h, R.w) * sizeof(float));
+    B.total = off;
+    return B;
+}
+
+// Extra checks of a backward call (FP32 only; launch-grid limits of the full-resolution kernel).
+gf_status check_backward(const Resolved &R)
+{
+    if (R.dt_in != GF_F32 || R.dt_out != GF_F32) return fail(GF_EINVAL, "the backward pass takes FP32 I, p and dq");
+    if (R.H > 65535) return fail(GF_EINVAL, "the backward pass needs H <= 65535");
+    if (R.N > 65535) return fail(GF_EINVAL, "the backward pass needs batch <= 65535");
+    return GF_OK;
+}
+
 }  // namespace gfk
 
 using gfk::Layout;
 using gfk::Resolved;
 using gfk::layout_of;
 using gfk::resolve;
+using gfk::BwdLayout;
+using gfk::bwd_layout_of;
+using gfk::check_backward;
 
 extern "C" {
 
@@ -299,6 +335,78 @@ gf_status gf_filter_host(gf_ctx *ctx, const void *I_host, const void *p_host, vo
     if ((e = cudaMemcpyAsync(q_host, dq, bq, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpyAsync of q");
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return GF_OK;
+}
+
+gf_status gf_backward_workspace_size(int H, int W, int C, int s, const gf_opts *opts, size_t *bytes)
+{
+    if (!bytes) return fail(GF_EINVAL, "bytes is NULL");
+    Resolved R;
+    gf_status st = resolve(H, W, C, 0, 0.0f, s, GF_SUB_BILINEAR, opts, R);
+    if (st != GF_OK) return st;
+    R.lps = gfk::plane_stride_f32((size_t)R.h * R.w);
+    *bytes = bwd_layout_of(R).total;
+    return GF_OK;
+}
+
+gf_status gf_filter_backward(gf_ctx *ctx, const void *I, const void *p, const void *dq, void *dI, void *dp, float *d_eps,
+                             int H, int W, int C, int r, float eps, int s, gf_subsample_mode mode, const gf_opts *opts,
+                             void *cuda_stream)
+{
+    if (!ctx) return fail(GF_EINVAL, "ctx is NULL");
+    if (!I || !p || !dq || !dI || !dp) return fail(GF_EINVAL, "I, p, dq, dI and dp must be device pointers");
+    Resolved R;
+    gf_status st = resolve(H, W, C, r, eps, s, (int)mode, opts, R);
+    if (st != GF_OK) return st;
+    if ((st = check_backward(R)) != GF_OK) return st;
+    R.lps = gfk::plane_stride_f32((size_t)R.h * R.w);  // optional low-res outputs are not produced here
+    const BwdLayout L = bwd_layout_of(R);
+
+    DeviceGuard guard(ctx->device);
+    std::unique_lock<std::mutex> lock(ctx->mu, std::defer_lock);
+    char *ws = nullptr;
+    if (opts && opts->workspace) {
+        if (opts->workspace_bytes < L.total)
+            return fail(GF_EINVAL, "workspace_bytes is smaller than gf_backward_workspace_size()");
+        ws = (char *)opts->workspace;
+    } else {
+        lock.lock();
+        st = grow(&ctx->arena, &ctx->arena_bytes, L.total, "the scratch arena");
+        if (st != GF_OK) return st;
+        ws = (char *)ctx->arena;
+    }
+
+    gfk::BwdPlan B;
+    gfk::FwdPlan &P = B.fwd;
+    P.N = R.N; P.C = R.C; P.CI = R.CI; P.H = R.H; P.W = R.W; P.h = R.h; P.w = R.w; P.s = R.s;
+    P.r_low = R.r_low; P.mode = R.mode; P.eps = R.eps; P.dt_in = R.dt_in; P.dt_out = R.dt_out;
+    P.p_lowres = R.p_lowres;
+    P.I = I; P.p = p; P.q = nullptr;
+    P.lps = R.lps;
+    const bool sub = R.s > 1 || R.p_lowres;
+    P.Il = sub ? (float *)(ws + L.fwd.off_Il) : nullptr;
+    P.pl = sub ? (float *)(ws + L.fwd.off_pl) : nullptr;
+    P.a = (float *)(ws + L.fwd.off_a);
+    P.b = (float *)(ws + L.fwd.off_b);
+    P.ma = (float *)(ws + L.fwd.off_ma);
+    P.mb = (float *)(ws + L.fwd.off_mb);
+    P.stats = ws + L.off_stats;
+    P.int_stats = false;
+    P.int_scale = 255.0f;
+    P.events = nullptr;
+    P.skip_output = true;
+    B.dq = (const float *)dq;
+    B.dI = (float *)dI;
+    B.dp = (float *)dp;
+    B.d_eps = d_eps;
+    B.dma = (float *)(ws + L.off_dma);
+    B.dmb = (float *)(ws + L.off_dmb);
+    for (int k = 0; k < 4; ++k) B.gq[k] = (float *)(ws + L.off_gq[k]);
+    B.dIl = (float *)(ws + L.off_dIl);
+    B.dpl = (float *)(ws + L.off_dpl);
+    B.eps_partial = (float *)(ws + L.off_eps);
+    cudaError_t e = gfk::launch_backward(B, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch in gf_filter_backward");
     return GF_OK;
 }
 

@@ -1,0 +1,511 @@
+// gf_backward.cu -- sm_103a kernels of the backward pass (the exact derivative) of Algorithm 2 of He and Sun,
+// "Fast Guided Filter" (2015).  The paper has no backward pass; this is the adjoint of the forward chain in
+// gf_forward.cu, operator by operator.  With g = dL/dq for channel c and guide channel I_g:
+//
+//   q = U(mean_a) .* I + U(mean_b)          -> dI += g .* U(mean_a);  dMA = U^T(g .* I);  dMB = U^T(g)
+//   mean_a = B(a), mean_b = B(b)            -> da = B^T(dMA),  db = B^T(dMB)
+//   b = mean_p - a .* mean_I                -> dmp = db;  da -= mean_I .* db;  dmI = -a .* db
+//   a = cov / (var + eps)                   -> dcov = da / (var+eps);  dvar = -da .* a / (var+eps);  deps += sum dvar
+//   var = corr_I - mean_I.^2, cov = corr_Ip - mean_I .* mean_p
+//                                           -> dcII = dvar;  dcIp = dcov;  dmI -= 2 mean_I dvar + mean_p dcov;
+//                                              dmp -= mean_I dcov
+//   mean_I = B(I'), mean_p = B(p'), corr_I = B(I'.*I'), corr_Ip = B(I'.*p')
+//                                           -> dI' = B^T(dmI) + 2 I' B^T(dcII) + p' B^T(dcIp);
+//                                              dp' = B^T(dmp) + I' B^T(dcIp)
+//   I' = D(I), p' = D(p)                    -> dI += D^T(dI');  dp = D^T(dp')
+//
+// B^T of the border-normalised box mean is B^T(y)_i = sum over windows k containing i of y_k / n_k, i.e. the
+// box SUM of y ./ n (n_k: in-image pixel count of window k) -- not B itself at the borders.  U^T and D^T are
+// the transposed bilinear / subsample maps, evaluated as gathers (no atomics).
+//
+//   k_bwd_upsample_T   dMA, dMB: per low-res tile, a horizontal gather of g.*I and g into a shared table of
+//                      full-res rows x low-res columns, then a vertical gather.
+//   k_bwd_box_T        B^T of 2 maps with the chain epilogue (4 maps out, per-CTA partial sums of deps), or
+//                      B^T of 4 maps with the final combination into dI', dp'.  Same tiling as k_box_tile.
+//   k_bwd_full         full-res: dI = sum_c g_c U(mean_a_c) + D^T(dI'), dp = D^T(dp').
+//   k_reduce_eps       deterministic sum of the per-CTA deps partials (FP64 accumulation).
+#include <algorithm>
+
+#include "gf_device.cuh"
+#include "gf_internal.cuh"
+
+namespace gfk {
+
+// ------------------------------------------------------------------------------------------------------
+// k_bwd_upsample_T
+// ------------------------------------------------------------------------------------------------------
+constexpr int UT_NT = 256;
+constexpr int UT_TI = 32;  // low-res columns per tile
+
+struct UpTParams {
+    const float *g;   // dL/dq, N x C x H x W
+    const float *I;   // guide, N x CI x H x W
+    float *dma, *dmb; // out: N x C planes of stride lps
+    int C, CI, H, W, h, w, s, TJ;
+    size_t lps;
+};
+
+__device__ __forceinline__ float up_weight(int X, int i, int s, int n)
+{
+    int i0, i1;
+    float f;
+    up_taps(X, s, n, i0, i1, f);
+    return (i0 == i ? 1.0f - f : 0.0f) + (i1 == i ? f : 0.0f);
+}
+
+__global__ void __launch_bounds__(UT_NT) k_bwd_upsample_T(UpTParams P)
+{
+    extern __shared__ float sm[];
+    const int s = P.s, TJ = P.TJ;
+    const int i0 = blockIdx.x * UT_TI, j0 = blockIdx.y * TJ;
+    const int plane = blockIdx.z, n = plane / P.C, c = plane - n * P.C;
+    const size_t HW = (size_t)P.H * P.W;
+    const float *g = P.g + (size_t)plane * HW;
+    const float *I = P.I + (size_t)(n * P.CI + (P.CI == 1 ? 0 : c)) * HW;
+    const int ncand = 3 * s;                 // candidate full-res positions per low-res index
+    const int Y0 = max(0, s * (j0 - 1)), Y1 = min(P.H, s * (j0 + TJ + 1));
+    const int NR = Y1 - Y0;
+    float *Tga = sm;                         // [NR][UT_TI] horizontal gathers of g .* I
+    float *Tg = Tga + (size_t)NR * UT_TI;    // [NR][UT_TI] horizontal gathers of g
+    float *wx = Tg + (size_t)NR * UT_TI;     // [UT_TI][ncand] weights of X = s(i-1) + t onto column i
+    float *wy = wx + UT_TI * ncand;          // [TJ][ncand] weights of Y = s(j-1) + t onto row j
+    for (int k = threadIdx.x; k < UT_TI * ncand; k += UT_NT) {
+        const int il = k / ncand, t = k - il * ncand;
+        const int i = i0 + il, X = s * (i - 1) + t;
+        wx[k] = (i < P.w && X >= 0 && X < P.W) ? up_weight(X, i, s, P.w) : 0.0f;
+    }
+    for (int k = threadIdx.x; k < TJ * ncand; k += UT_NT) {
+        const int jl = k / ncand, t = k - jl * ncand;
+        const int j = j0 + jl, Y = s * (j - 1) + t;
+        wy[k] = (j < P.h && Y >= 0 && Y < P.H) ? up_weight(Y, j, s, P.h) : 0.0f;
+    }
+    __syncthreads();
+    // horizontal gather: T[y][i] = sum_X wx(X -> i) v(y, X)
+    for (int k = threadIdx.x; k < NR * UT_TI; k += UT_NT) {
+        const int yl = k / UT_TI, il = k - yl * UT_TI;
+        const int i = i0 + il;
+        float sga = 0.0f, sg = 0.0f;
+        if (i < P.w) {
+            const size_t ro = (size_t)(Y0 + yl) * P.W;
+            const int xb = s * (i - 1);
+            for (int t = 0; t < ncand; ++t) {
+                const float wgt = wx[il * ncand + t];
+                if (wgt != 0.0f) {
+                    const float gv = __ldg(g + ro + xb + t);
+                    sg = fmaf(wgt, gv, sg);
+                    sga = fmaf(wgt, gv * __ldg(I + ro + xb + t), sga);
+                }
+            }
+        }
+        Tga[k] = sga;
+        Tg[k] = sg;
+    }
+    __syncthreads();
+    // vertical gather: dM[j][i] = sum_y wy(y -> j) T[y][i]
+    for (int k = threadIdx.x; k < TJ * UT_TI; k += UT_NT) {
+        const int jl = k / UT_TI, il = k - jl * UT_TI;
+        const int j = j0 + jl, i = i0 + il;
+        if (j >= P.h || i >= P.w) continue;
+        float sa = 0.0f, sb = 0.0f;
+        const int yb = s * (j - 1);
+        for (int t = 0; t < ncand; ++t) {
+            const float wgt = wy[jl * ncand + t];
+            if (wgt != 0.0f) {
+                const int yl = yb + t - Y0;
+                sa = fmaf(wgt, Tga[yl * UT_TI + il], sa);
+                sb = fmaf(wgt, Tg[yl * UT_TI + il], sb);
+            }
+        }
+        const size_t o = (size_t)plane * P.lps + (size_t)j * P.w + i;
+        P.dma[o] = sa;
+        P.dmb[o] = sb;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// k_bwd_box_T
+// ------------------------------------------------------------------------------------------------------
+constexpr int BB_NT = 256;
+constexpr int BB_TH = 32;
+constexpr int BB_TW = 64;
+constexpr int BB_RV = 8;
+constexpr int BB_RH = 8;
+constexpr int BB_VP = BB_TH + 1;
+constexpr int BB_OP = BB_TW + 1;
+
+enum { EPI_CHAIN = 0, EPI_COMBINE = 1 };
+
+struct BoxTParams {
+    const float *in[4];  // input maps (N x C planes of stride lps each)
+    float *out[4];       // output maps (N x C planes of stride lps each)
+    size_t lps;
+    int C, CI, h, w, r;
+    float eps;
+    // chain epilogue: forward statistics (dense h*w planes, 4 per (n, c)) and a (stride lps)
+    const float *stats, *a;
+    float *eps_partial;  // one partial sum of dvar per CTA
+    // combine epilogue: I' (plane index n*CI + guide) and p' (plane index n*C + c), plane stride xps / yps
+    const float *Il, *pl;
+    size_t xps, yps;
+};
+
+__device__ __forceinline__ int win_count(int k, int r, int n) { return min(n - 1, k + r) - max(0, k - r) + 1; }
+
+template <int NIN, int EPI, bool COMP>
+__global__ void __launch_bounds__(BB_NT) k_bwd_box_T(BoxTParams P)
+{
+    constexpr int NOUT = (EPI == EPI_CHAIN) ? 4 : 2;
+    extern __shared__ float smf[];
+    __shared__ float red[BB_NT / 32];
+    const int tid = threadIdx.x;
+    const int h = P.h, w = P.w, r = P.r;
+    const int span = BB_TW + 2 * r;
+    float *Vt = smf;                                 // [NIN][span][BB_VP]
+    float *Ot = smf + (size_t)NIN * span * BB_VP;     // [NOUT][BB_TH][BB_OP]
+    const int x0 = blockIdx.x * BB_TW, y0 = blockIdx.y * BB_TH;
+    const int plane = blockIdx.z;
+    const size_t pbase = (size_t)plane * P.lps;
+
+    // ---- phase 1: vertical sums of in ./ n (n: pixel count of the window centred at each pixel)
+    for (int item = tid; item < span * (BB_TH / BB_RV); item += BB_NT) {
+        const int xc = item % span, seg = item / span;
+        const int gx = x0 - r + xc, ya = y0 + seg * BB_RV, vrow = seg * BB_RV;
+        float S[NIN], Sc[NIN];
+#pragma unroll
+        for (int q = 0; q < NIN; ++q) { S[q] = 0.0f; Sc[q] = 0.0f; }
+        if (gx >= 0 && gx < w && ya < h) {
+            const float inx = __fdividef(1.0f, (float)win_count(gx, r, w));
+            auto add_row = [&](int yy, float sign) {
+                const float sc = sign * inx * __fdividef(1.0f, (float)win_count(yy, r, h));
+                const size_t o = pbase + (size_t)yy * w + gx;
+#pragma unroll
+                for (int q = 0; q < NIN; ++q) {
+                    const float v = sc * __ldg(P.in[q] + o);
+                    if (COMP) {
+                        const float t = S[q] + v;
+                        Sc[q] += (fabsf(S[q]) >= fabsf(v)) ? ((S[q] - t) + v) : ((v - t) + S[q]);
+                        S[q] = t;
+                    } else {
+                        S[q] += v;
+                    }
+                }
+            };
+            for (int yy = max(0, ya - r); yy <= min(h - 1, ya + r); ++yy) add_row(yy, 1.0f);
+#pragma unroll
+            for (int i = 0; i < BB_RV; ++i) {
+                const int y = ya + i;
+                if (i > 0) {
+                    if (y + r < h) add_row(y + r, 1.0f);
+                    if (y - r - 1 >= 0) add_row(y - r - 1, -1.0f);
+                }
+#pragma unroll
+                for (int q = 0; q < NIN; ++q) Vt[((size_t)q * span + xc) * BB_VP + vrow + i] = S[q] + Sc[q];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < BB_RV; ++i)
+#pragma unroll
+                for (int q = 0; q < NIN; ++q) Vt[((size_t)q * span + xc) * BB_VP + vrow + i] = 0.0f;
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 2: horizontal sums and the epilogue
+    float eps_acc = 0.0f;
+    const int n = plane / P.C, c = plane - n * P.C;
+    for (int item = tid; item < BB_TH * (BB_TW / BB_RH); item += BB_NT) {
+        const int yr = item % BB_TH, seg = item / BB_TH;
+        const int y = y0 + yr, xa = seg * BB_RH;
+        if (y >= h || x0 + xa >= w) continue;
+        float S[NIN], Sc[NIN];
+#pragma unroll
+        for (int q = 0; q < NIN; ++q) { S[q] = 0.0f; Sc[q] = 0.0f; }
+        auto vacc = [&](int col, float sign) {
+#pragma unroll
+            for (int q = 0; q < NIN; ++q) {
+                const float v = sign * Vt[((size_t)q * span + col) * BB_VP + yr];
+                if (COMP) {
+                    const float t = S[q] + v;
+                    Sc[q] += (fabsf(S[q]) >= fabsf(v)) ? ((S[q] - t) + v) : ((v - t) + S[q]);
+                    S[q] = t;
+                } else {
+                    S[q] += v;
+                }
+            }
+        };
+        for (int k = 0; k <= 2 * r; ++k) vacc(xa + k, 1.0f);
+#pragma unroll
+        for (int i = 0; i < BB_RH; ++i) {
+            const int xt = xa + i, x = x0 + xt;
+            if (x >= w) break;
+            if (i > 0) {
+                vacc(xt + 2 * r, 1.0f);
+                vacc(xt - 1, -1.0f);
+            }
+            const size_t pix = (size_t)y * w + x;
+            float o[NOUT];
+            if (EPI == EPI_CHAIN) {
+                const float da0 = S[0] + Sc[0], db = S[1] + Sc[1];  // B^T(dMA), B^T(dMB)
+                const size_t ps = (size_t)h * w;
+                const float *st = P.stats + (size_t)plane * 4 * ps + pix;
+                const float mI = st[0], cI = st[ps], mp = st[2 * ps];
+                const float a = P.a[pbase + pix];
+                const float var = fmaxf(cI - mI * mI, 0.0f);
+                const float inv = 1.0f / (var + P.eps);
+                const float da = da0 - mI * db;          // through b = mean_p - a mean_I
+                const float dcov = da * inv;              // through a = cov / (var + eps)
+                const float dvar = -da * a * inv;
+                eps_acc += dvar;
+                o[0] = -a * db - 2.0f * mI * dvar - mp * dcov;  // d mean_I
+                o[1] = dvar;                                    // d corr_I
+                o[2] = dcov;                                    // d corr_Ip
+                o[3] = db - mI * dcov;                          // d mean_p
+            } else {
+                const float tmI = S[0] + Sc[0], tcII = S[1] + Sc[1], tcIp = S[2] + Sc[2], tmp = S[3] + Sc[3];
+                const float Iv = P.Il[(size_t)(n * P.CI + (P.CI == 1 ? 0 : c)) * P.xps + pix];
+                const float pv = P.pl[(size_t)plane * P.yps + pix];
+                o[0] = tmI + 2.0f * Iv * tcII + pv * tcIp;  // dI'
+                o[1] = tmp + Iv * tcIp;                     // dp'
+            }
+#pragma unroll
+            for (int q = 0; q < NOUT; ++q) Ot[(q * BB_TH + yr) * BB_OP + xt] = o[q];
+        }
+    }
+    if (EPI == EPI_CHAIN) {
+        // deterministic CTA reduction of the deps contributions
+        for (int off = 16; off > 0; off >>= 1) eps_acc += __shfl_xor_sync(0xffffffffu, eps_acc, off);
+        if ((tid & 31) == 0) red[tid >> 5] = eps_acc;
+    }
+    __syncthreads();
+    if (EPI == EPI_CHAIN && tid == 0) {
+        float t = 0.0f;
+        for (int k = 0; k < BB_NT / 32; ++k) t += red[k];
+        P.eps_partial[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
+    }
+
+    // ---- phase 3: coalesced write-out
+    for (int idx = tid; idx < BB_TH * BB_TW; idx += BB_NT) {
+        const int yr = idx / BB_TW, xt = idx - yr * BB_TW;
+        const int y = y0 + yr, x = x0 + xt;
+        if (y < h && x < w) {
+#pragma unroll
+            for (int q = 0; q < NOUT; ++q) P.out[q][pbase + (size_t)y * w + x] = Ot[(q * BB_TH + yr) * BB_OP + xt];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// k_bwd_full
+// ------------------------------------------------------------------------------------------------------
+constexpr int BF_NT = 256;
+
+struct FullParams {
+    const float *g;            // N x C x H x W
+    const float *ma;           // mean_a, N x C planes of stride lps
+    const float *dIl, *dpl;    // dI', dp' per channel, N x C planes of stride lps
+    float *dI;                 // N x CI x H x W
+    float *dp;                 // N x C x H x W, or NULL when p is low-res
+    int C, CI, H, W, h, w, s, mode;
+    size_t lps;
+};
+
+// Weights with which full-res index Y receives from low-res indices j in {Y/s - 1, Y/s, Y/s + 1} under the
+// transposed subsample (the gather form of D^T).
+__device__ __forceinline__ void sub_adjoint(int Y, int s, int H, int h, int mode, int j[3], float wgt[3])
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int jj = Y / s - 1 + k;
+        j[k] = min(max(jj, 0), h - 1);
+        float wv = 0.0f;
+        if (jj >= 0 && jj < h) {
+            if (mode == GF_SUB_BOX && s > 1) {
+                const int a = jj * s, b = min(a + s, H);
+                wv = (Y >= a && Y < b) ? 1.0f / (float)(b - a) : 0.0f;
+            } else {
+                int t0, t1;
+                float f;
+                sub_taps(jj, s, H, mode, t0, t1, f);
+                wv = (t0 == Y ? 1.0f - f : 0.0f) + (t1 == Y ? f : 0.0f);
+            }
+        }
+        wgt[k] = wv;
+    }
+}
+
+__global__ void __launch_bounds__(BF_NT) k_bwd_full(FullParams P)
+{
+    const int X = blockIdx.x * BF_NT + threadIdx.x, Y = blockIdx.y, n = blockIdx.z;
+    if (X >= P.W) return;
+    const size_t HW = (size_t)P.H * P.W, pix = (size_t)Y * P.W + X;
+    int ya, yb, xa, xb;
+    float fy, fx;
+    up_taps(Y, P.s, P.h, ya, yb, fy);
+    up_taps(X, P.s, P.w, xa, xb, fx);
+    int jy[3], ix[3];
+    float wy[3], wx[3];
+    sub_adjoint(Y, P.s, P.H, P.h, P.mode, jy, wy);
+    sub_adjoint(X, P.s, P.W, P.w, P.mode, ix, wx);
+    float dI_shared = 0.0f;
+    for (int c = 0; c < P.C; ++c) {
+        const size_t lp = (size_t)(n * P.C + c) * P.lps;
+        const float *ma = P.ma + lp;
+        const float A0 = fmaf(fx, __ldg(ma + (size_t)ya * P.w + xb) - __ldg(ma + (size_t)ya * P.w + xa), __ldg(ma + (size_t)ya * P.w + xa));
+        const float A1 = fmaf(fx, __ldg(ma + (size_t)yb * P.w + xb) - __ldg(ma + (size_t)yb * P.w + xa), __ldg(ma + (size_t)yb * P.w + xa));
+        const float A = fmaf(fy, A1 - A0, A0);                        // U(mean_a)
+        const float gv = __ldg(P.g + (size_t)(n * P.C + c) * HW + pix);
+        float tI = 0.0f, tp = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (wy[a] == 0.0f) continue;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (wx[b] == 0.0f) continue;
+                const size_t o = lp + (size_t)jy[a] * P.w + ix[b];
+                const float wv = wy[a] * wx[b];
+                tI = fmaf(wv, __ldg(P.dIl + o), tI);
+                if (P.dp) tp = fmaf(wv, __ldg(P.dpl + o), tp);
+            }
+        }
+        const float dIc = fmaf(gv, A, tI);                            // direct term + D^T(dI')
+        if (P.CI == 1) dI_shared += dIc;
+        else P.dI[(size_t)(n * P.CI + c) * HW + pix] = dIc;
+        if (P.dp) P.dp[(size_t)(n * P.C + c) * HW + pix] = tp;        // D^T(dp')
+    }
+    if (P.CI == 1) P.dI[(size_t)n * HW + pix] = dI_shared;
+}
+
+// ------------------------------------------------------------------------------------------------------
+// k_reduce_eps
+// ------------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_reduce_eps(const float *partial, int n, float *out)
+{
+    __shared__ double red[256];
+    double t = 0.0;
+    for (int k = threadIdx.x; k < n; k += 256) t += (double)partial[k];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = (float)red[0];
+}
+
+// ------------------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------------------
+namespace {
+
+template <int NIN, int EPI>
+cudaError_t launch_box_T(const BoxTParams &bp, int planes, cudaStream_t st)
+{
+    const size_t smem = ((size_t)NIN * (BB_TW + 2 * bp.r) * BB_VP + (size_t)((EPI == EPI_CHAIN) ? 4 : 2) * BB_TH * BB_OP) *
+                        sizeof(float);
+    dim3 grid((bp.w + BB_TW - 1) / BB_TW, (bp.h + BB_TH - 1) / BB_TH, planes);
+    if (bp.r > 16) {
+        static size_t conf = 0;
+        if (smem > 48 * 1024 && smem > conf) {
+            cudaError_t e = cudaFuncSetAttribute(k_bwd_box_T<NIN, EPI, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            conf = smem;
+        }
+        k_bwd_box_T<NIN, EPI, true><<<grid, BB_NT, smem, st>>>(bp);
+    } else {
+        static size_t conf = 0;
+        if (smem > 48 * 1024 && smem > conf) {
+            cudaError_t e = cudaFuncSetAttribute(k_bwd_box_T<NIN, EPI, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            conf = smem;
+        }
+        k_bwd_box_T<NIN, EPI, false><<<grid, BB_NT, smem, st>>>(bp);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t bwd_eps_partials(int N, int C, int h, int w)
+{
+    return (size_t)N * C * ((h + BB_TH - 1) / BB_TH) * ((w + BB_TW - 1) / BB_TW);
+}
+
+cudaError_t launch_backward(const BwdPlan &B, cudaStream_t st)
+{
+    cudaError_t err;
+    const FwdPlan &F = B.fwd;
+    const int planes = F.N * F.C;
+    // ---- forward recomputation: low-res planes, statistics, a, mean_a
+    if ((err = launch_forward(F, st)) != cudaSuccess) return err;
+
+    // ---- dMA = U^T(g .* I), dMB = U^T(g)
+    {
+        UpTParams up;
+        up.g = B.dq; up.I = (const float *)F.I; up.dma = B.dma; up.dmb = B.dmb;
+        up.C = F.C; up.CI = F.CI; up.H = F.H; up.W = F.W; up.h = F.h; up.w = F.w; up.s = F.s;
+        up.TJ = F.s <= 8 ? 8 : (F.s <= 16 ? 4 : 2);
+        up.lps = F.lps;
+        const int NRmax = F.s * (up.TJ + 2);
+        const size_t smem = ((size_t)2 * NRmax * UT_TI + (size_t)UT_TI * 3 * F.s + (size_t)up.TJ * 3 * F.s) * sizeof(float);
+        static size_t conf = 0;
+        if (smem > 48 * 1024 && smem > conf) {
+            if ((err = cudaFuncSetAttribute(k_bwd_upsample_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+                return err;
+            conf = smem;
+        }
+        dim3 grid((F.w + UT_TI - 1) / UT_TI, (F.h + up.TJ - 1) / up.TJ, planes);
+        k_bwd_upsample_T<<<grid, UT_NT, smem, st>>>(up);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+
+    // ---- da, db = B^T(dMA), B^T(dMB) with the chain epilogue -> d mean_I, d corr_I, d corr_Ip, d mean_p
+    {
+        BoxTParams bp{};
+        bp.in[0] = B.dma; bp.in[1] = B.dmb;
+        for (int k = 0; k < 4; ++k) bp.out[k] = B.gq[k];
+        bp.lps = F.lps; bp.C = F.C; bp.CI = F.CI; bp.h = F.h; bp.w = F.w; bp.r = F.r_low; bp.eps = F.eps;
+        bp.stats = (const float *)F.stats; bp.a = F.a; bp.eps_partial = B.eps_partial;
+        if ((err = launch_box_T<2, EPI_CHAIN>(bp, planes, st)) != cudaSuccess) return err;
+    }
+
+    // ---- dI', dp' = B^T of the four maps, combined with I', p'
+    {
+        BoxTParams bp{};
+        for (int k = 0; k < 4; ++k) bp.in[k] = B.gq[k];
+        bp.out[0] = B.dIl; bp.out[1] = B.dpl;
+        bp.lps = F.lps; bp.C = F.C; bp.CI = F.CI; bp.h = F.h; bp.w = F.w; bp.r = F.r_low; bp.eps = F.eps;
+        const bool sub = F.s > 1;
+        bp.Il = sub ? F.Il : (const float *)F.I;
+        bp.pl = sub ? F.pl : (const float *)F.p;
+        bp.xps = sub ? F.lps : (size_t)F.h * F.w;
+        bp.yps = sub ? F.lps : (size_t)F.h * F.w;
+        if ((err = launch_box_T<4, EPI_COMBINE>(bp, planes, st)) != cudaSuccess) return err;
+    }
+
+    // ---- full resolution: dI (direct term + D^T(dI')), dp = D^T(dp')
+    {
+        FullParams fp;
+        fp.g = B.dq; fp.ma = F.ma; fp.dIl = B.dIl; fp.dpl = B.dpl; fp.dI = B.dI;
+        fp.dp = F.p_lowres ? nullptr : B.dp;
+        fp.C = F.C; fp.CI = F.CI; fp.H = F.H; fp.W = F.W; fp.h = F.h; fp.w = F.w; fp.s = F.s; fp.mode = F.mode;
+        fp.lps = F.lps;
+        dim3 grid((F.W + BF_NT - 1) / BF_NT, F.H, F.N);
+        k_bwd_full<<<grid, BF_NT, 0, st>>>(fp);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        if (F.p_lowres) {  // p was given at low resolution: dp = dp' (dense copy out of the strided workspace)
+            if ((err = cudaMemcpy2DAsync(B.dp, (size_t)F.h * F.w * sizeof(float), B.dpl, F.lps * sizeof(float),
+                                         (size_t)F.h * F.w * sizeof(float), planes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+                return err;
+        }
+    }
+
+    // ---- deps
+    if (B.d_eps) {
+        const int np = (int)bwd_eps_partials(F.N, F.C, F.h, F.w);
+        k_reduce_eps<<<1, 256, 0, st>>>(B.eps_partial, np, B.d_eps);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace gfk

@@ -1,0 +1,62 @@
+// gf_device.cuh -- device helpers shared by the forward and backward kernels: typed loads, the
+// resampling tap arithmetic of the library's conventions (see gf.h), and cp.async.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gf.h"
+
+namespace gfk {
+
+// ------------------------------------------------------------------------------------------------------
+// element loads
+// ------------------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ float ldv(const T *p);
+template <>
+__device__ __forceinline__ float ldv<float>(const float *p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float ldv<__half>(const __half *p) { return __half2float(__ldg(p)); }
+template <>
+__device__ __forceinline__ float ldv<uint8_t>(const uint8_t *p) { return (float)__ldg(p); }
+
+// 4-byte asynchronous global -> shared copy (sm_80+ cp.async): many can be in flight per thread, and
+// they complete without holding registers.
+__device__ __forceinline__ void cp_async4(float *smem_dst, const float *gmem_src)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Upsampling taps along one axis: full-res index X samples position (X + 1/2)/s - 1/2 = (2X + 1 - s)/(2s),
+// clamped to [0, n-1].  Integer arithmetic keeps the taps exact.
+__device__ __forceinline__ void up_taps(int X, int s, int n, int &i0, int &i1, float &f)
+{
+    const int num = 2 * X + 1 - s, den = 2 * s;
+    if (num <= 0) { i0 = 0; i1 = 0; f = 0.0f; return; }
+    const int qt = num / den, rem = num - qt * den;
+    if (qt >= n - 1) { i0 = n - 1; i1 = n - 1; f = 0.0f; return; }
+    i0 = qt; i1 = qt + 1; f = (float)rem / (float)den;
+}
+
+// Subsampling taps along one axis for low-res index j (Algorithm 2 first step, gf.h conventions): the
+// full-res positions t0, t1 that the sample reads and the weight f of t1 (nearest: t0 = t1, f = 0).  Box mode
+// is handled by the callers (it averages a whole block).
+__device__ __forceinline__ void sub_taps(int j, int s, int n, int mode, int &t0, int &t1, float &f)
+{
+    if (mode == GF_SUB_NEAREST || s == 1) {
+        t0 = t1 = min(((2 * j + 1) * s) >> 1, n - 1);
+        f = 0.0f;
+        return;
+    }
+    const int nn = (2 * j + 1) * s - 1;  // twice the source coordinate
+    t0 = nn >> 1;
+    f = (nn & 1) ? 0.5f : 0.0f;
+    if (t0 >= n - 1) { t0 = n - 1; f = 0.0f; }
+    t1 = min(t0 + 1, n - 1);
+}
+
+}  // namespace gfk

@@ -25,21 +25,10 @@
 //   k_output_s1   the s = 1 form of the last step (no resampling).
 #include <algorithm>
 
+#include "gf_device.cuh"
 #include "gf_internal.cuh"
 
 namespace gfk {
-
-// ------------------------------------------------------------------------------------------------------
-// element loads
-// ------------------------------------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ float ldv(const T *p);
-template <>
-__device__ __forceinline__ float ldv<float>(const float *p) { return __ldg(p); }
-template <>
-__device__ __forceinline__ float ldv<__half>(const __half *p) { return __half2float(__ldg(p)); }
-template <>
-__device__ __forceinline__ float ldv<uint8_t>(const uint8_t *p) { return (float)__ldg(p); }
 
 // ------------------------------------------------------------------------------------------------------
 // k_subsample
@@ -167,7 +156,7 @@ __global__ void __launch_bounds__(SUB_NT) k_subsample_vec(SubParams P)
 // ------------------------------------------------------------------------------------------------------
 // k_box_tile
 // ------------------------------------------------------------------------------------------------------
-constexpr int BT_NT = 256;  // threads per CTA
+constexpr int BT_NT_MAX = 320;  // largest CTA (the launch sizes it to the phase-1 work, a multiple of 32)
 constexpr int BT_TH = 32;   // output rows per tile
 constexpr int BT_TW = 64;   // output columns per tile
 constexpr int BT_VP = BT_TH + 1;  // pitch of the transposed column-sum tile (odd: no bank conflicts)
@@ -229,8 +218,9 @@ struct Quant {
 };
 
 template <typename T, int KIND, bool COMP, int BT_RV, int BT_RH>
-__global__ void __launch_bounds__(BT_NT) k_box_tile(BoxParams P)
+__global__ void __launch_bounds__(BT_NT_MAX) k_box_tile(BoxParams P)
 {
+    const int BT_NT = blockDim.x;
     using Q = Quant<KIND>;
     constexpr int NQ = Q::NQ;
     constexpr bool INT = (KIND == KIND_STATS_INT);
@@ -274,7 +264,8 @@ __global__ void __launch_bounds__(BT_NT) k_box_tile(BoxParams P)
 #pragma unroll
         for (int q = 0; q < NQ; ++q) { S[q] = 0.0f; Sc[q] = 0.0f; U[q] = 0u; }
         auto add_row = [&](int yy, bool sub) {
-            const float xv = ldv(xcol + (size_t)yy * w), yv = ldv(ycol + (size_t)yy * w);
+            const size_t off = (size_t)yy * w;
+            const float xv = ldv(xcol + off), yv = ldv(ycol + off);
             if (INT) {
                 uint32_t qv[4];
                 Q::of_int(xv, yv, qv);
@@ -414,17 +405,6 @@ struct UpParams {
     int LRmax, LCmax;                 // staged low-res tile bounds (rows, columns)
 };
 
-// Upsampling taps along one axis: full-res index X samples position (X + 1/2)/s - 1/2 = (2X + 1 - s)/(2s),
-// clamped to [0, n-1].  Integer arithmetic keeps the taps exact.
-__device__ __forceinline__ void up_taps(int X, int s, int n, int &i0, int &i1, float &f)
-{
-    const int num = 2 * X + 1 - s, den = 2 * s;
-    if (num <= 0) { i0 = 0; i1 = 0; f = 0.0f; return; }
-    const int qt = num / den, rem = num - qt * den;
-    if (qt >= n - 1) { i0 = n - 1; i1 = n - 1; f = 0.0f; return; }
-    i0 = qt; i1 = qt + 1; f = (float)rem / (float)den;
-}
-
 template <typename T>
 __device__ __forceinline__ void ld4(const T *p, bool vec, int valid, float v[4]);
 template <>
@@ -517,8 +497,9 @@ __global__ void __launch_bounds__(UP_NT) k_upsample_output(UpParams P)
         const int c = min(c0 + (mc >> 1), P.C - 1);
         const float *src = ((mc & 1) ? P.mb : P.ma) + (size_t)(n * P.C + c) * P.lps + (size_t)(ly0 + row) * P.w + lx0;
         float *dst = tap + mc * tile + row * P.LCmax;
-        for (int col = threadIdx.x; col < LC; col += UP_NT) dst[col] = __ldg(src + col);
+        for (int col = threadIdx.x; col < LC; col += UP_NT) cp_async4(dst + col, src + col);
     }
+    cp_async_wait_all();
     __syncthreads();
 
     const int X0 = Xb + threadIdx.x * 4;
@@ -627,105 +608,120 @@ __global__ void __launch_bounds__(UP_NT) k_upsample_output(UpParams P)
 // horizontally interpolated tap rows (and their difference) serves the whole run.  Columns: pixels 4t .. 4t+3
 // sample low-res columns i-1, i, i+1 (S = 4) or one adjacent pair of them (S = 8) with fixed weights.  Taps
 // beyond the image are clamped copies, which gives the same value as clamping the sample position.
-template <typename TI, typename TQ, int CC, int S>
-__global__ void __launch_bounds__(UP_NT) k_upsample_output_s4x(UpParams P)
+// One channel per CTA; the channel is the fastest-varying block index, so the CTAs of one band of I run
+// side by side and share I through L2.
+template <typename TI, typename TQ, int S>
+__global__ void __launch_bounds__(UP_NT, 8) k_upsample_output_s4x(UpParams P)
 {
-    extern __shared__ float tap[];  // [CC][2][LRmax][LCmax]: low-res rows jb-1 .. jb+nb, clamped
+    extern __shared__ float tap[];  // [2][LRmax][LCmax]: mean_a, mean_b at low-res rows jb-1 .. jb+nb, clamped
     const int nb = P.R / S;         // low-res rows (bands) per CTA
     const int jb = blockIdx.y * nb;
-    const int Xb = blockIdx.x * UP_BAND;
+    const int c = blockIdx.x % P.C, band = blockIdx.x / P.C;
+    const int n = blockIdx.z;
+    const int Xb = band * UP_BAND;
     const int Yb = jb * S, Ye = min(Yb + P.R, P.H);
-    const int n = blockIdx.z / P.CG, c0 = (blockIdx.z - n * P.CG) * CC;
-    const int ncc = min(CC, P.C - c0);
     const int ly0 = jb - 1, lx0 = Xb / S - 1;
     const int LR = P.LRmax, LC = P.LCmax, tile = LR * LC;
-    for (int mr = 0; mr < CC * 2 * LR; ++mr) {  // (map, row) pairs; mc = cc * 2 + map
-        const int mc = mr / LR, row = mr - mc * LR;
-        const int c = min(c0 + (mc >> 1), P.C - 1);
-        const int gy = min(max(ly0 + row, 0), P.h - 1);
-        const float *src = ((mc & 1) ? P.mb : P.ma) + (size_t)(n * P.C + c) * P.lps + (size_t)gy * P.w;
-        float *dst = tap + mc * tile + row * LC;
-        for (int col = threadIdx.x; col < LC; col += UP_NT) dst[col] = __ldg(src + min(max(lx0 + col, 0), P.w - 1));
+    {
+        // asynchronous fill of the tap tile; each thread owns at most two tile columns
+        const int c0 = threadIdx.x, c1 = threadIdx.x + UP_NT;
+        const int g0 = min(max(lx0 + c0, 0), P.w - 1), g1 = min(max(lx0 + c1, 0), P.w - 1);
+        const float *pa = P.ma + (size_t)(n * P.C + c) * P.lps, *pb = P.mb + (size_t)(n * P.C + c) * P.lps;
+        for (int row = 0; row < LR; ++row) {
+            const size_t go = (size_t)min(max(ly0 + row, 0), P.h - 1) * P.w;
+            float *da = tap + row * LC, *db = da + tile;
+            if (c0 < LC) { cp_async4(da + c0, pa + go + g0); cp_async4(db + c0, pb + go + g0); }
+            if (c1 < LC) { cp_async4(da + c1, pa + go + g1); cp_async4(db + c1, pb + go + g1); }
+        }
+        cp_async_wait_all();
+        __syncthreads();
     }
-    __syncthreads();
 
     const int X0 = Xb + threadIdx.x * 4;
     if (X0 >= P.W) return;
     const int ti = X0 / S - lx0;  // tile column of the low-res column that holds pixel X0 (>= 1)
     const int g = (S == 8) ? ((X0 >> 2) & 1) : 0;
 
-    // horizontally interpolated tap row `tr` for the thread's 4 pixels, all maps
-    auto hrow = [&](int tr, float (&o)[CC][2][4]) {
+    // horizontally interpolated tap row `tr` for the thread's 4 pixels, both maps
+    auto hrow = [&](int tr, float (&o)[2][4]) {
 #pragma unroll
-        for (int mc = 0; mc < CC * 2; ++mc) {
-            const float *row = tap + mc * tile + tr * LC;
+        for (int m = 0; m < 2; ++m) {
+            const float *row = tap + m * tile + tr * LC;
             if (S == 4) {
-                const float a = row[ti - 1], b = row[ti], c = row[ti + 1];
-                o[mc >> 1][mc & 1][0] = fmaf(0.625f, b - a, a);
-                o[mc >> 1][mc & 1][1] = fmaf(0.875f, b - a, a);
-                o[mc >> 1][mc & 1][2] = fmaf(0.125f, c - b, b);
-                o[mc >> 1][mc & 1][3] = fmaf(0.375f, c - b, b);
+                const float a = row[ti - 1], b = row[ti], cc = row[ti + 1];
+                o[m][0] = fmaf(0.625f, b - a, a);
+                o[m][1] = fmaf(0.875f, b - a, a);
+                o[m][2] = fmaf(0.125f, cc - b, b);
+                o[m][3] = fmaf(0.375f, cc - b, b);
             } else {
                 const int lo = g ? ti : ti - 1;
                 const float a = row[lo], b = row[lo + 1];
                 const float f0 = g ? 0.0625f : 0.5625f;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) o[mc >> 1][mc & 1][k] = fmaf(f0 + 0.125f * k, b - a, a);
+                for (int k = 0; k < 4; ++k) o[m][k] = fmaf(f0 + 0.125f * k, b - a, a);
             }
         }
     };
 
-    const TI *Irow0 = (const TI *)P.I + (size_t)n * P.H * P.W + X0;
-    TQ *Qrow0[CC];
-#pragma unroll
-    for (int cc = 0; cc < CC; ++cc)
-        Qrow0[cc] = (TQ *)P.q + (size_t)(n * P.C + min(c0 + cc, P.C - 1)) * P.H * P.W + X0;
+    const size_t HW = (size_t)P.H * P.W;
+    const TI *Ip = (const TI *)P.I + (size_t)n * HW + X0;
+    TQ *Qp = (TQ *)P.q + (size_t)(n * P.C + c) * HW + X0;
 
-    float lo[CC][2][4], d[CC][2][4];
-    hrow(0, lo);  // low-res row jb - 1
-    // run j covers full-res rows S*j + S/2 .. S*j + S/2 + S - 1 and samples low-res rows j, j+1
-    for (int t = 0; t <= nb; ++t) {
-        const int j = jb - 1 + t;
-        const int Yr = S * j + S / 2;
-        if (Yr >= Ye) break;
-        float iv[S][4];
+    // Run j covers full-res rows S*j + S/2 .. S*j + S/2 + S - 1 and samples low-res rows j and j+1 (tile
+    // rows t and t+1 for t = j - jb + 1).  Runs are walked in quads of 4 rows; the I rows of the next quad
+    // are requested before the current quad is computed (two register buffers used in turn).
+    constexpr int QPR = S / 4;  // quads per run
+    const int nquads = (nb + 1) * QPR;
+    float lo[2][4], d[2][4];
+    float ivA[4][4], ivB[4][4];
+    auto load_quad = [&](int u, float (&dst)[4][4]) {
+        const int Yq = S * (jb - 1 + u / QPR) + S / 2 + 4 * (u % QPR);
 #pragma unroll
-        for (int k = 0; k < S; ++k) {
-            const int Y = Yr + k;
-            if (Y >= Yb && Y < Ye) ld4<TI>(Irow0 + (size_t)Y * P.W, true, 4, iv[k]);
+        for (int k = 0; k < 4; ++k) {
+            const int Y = Yq + k;
+            if (Y >= Yb && Y < Ye) ld4<TI>(Ip + (size_t)Y * P.W, true, 4, dst[k]);
         }
-        float hi[CC][2][4];
-        hrow(t + 1, hi);
+    };
+    auto do_quad = [&](int u, const float (&iv)[4][4]) {
+        const int t = u / QPR, sub = u % QPR;
+        const int Yq = S * (jb - 1 + t) + S / 2 + 4 * sub;
+        if (sub == 0) {
+            if (t > 0) {  // the previous run's lower tap row becomes this run's upper one
 #pragma unroll
-        for (int cc = 0; cc < CC; ++cc)
+                for (int m = 0; m < 2; ++m)
 #pragma unroll
-            for (int m = 0; m < 2; ++m)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) d[cc][m][k] = hi[cc][m][k] - lo[cc][m][k];
-#pragma unroll
-        for (int k = 0; k < S; ++k) {
-            const int Y = Yr + k;
-            if (Y < Yb || Y >= Ye) continue;
-            const float fy = (2.0f * k + 1.0f) / (2.0f * S);  // compile-time constant
-#pragma unroll
-            for (int cc = 0; cc < CC; ++cc) {
-                if (cc >= ncc) break;
-                float out[4];
-#pragma unroll
-                for (int x = 0; x < 4; ++x) {
-                    const float A = fmaf(fy, d[cc][0][x], lo[cc][0][x]);  // upsampled mean_a
-                    const float B = fmaf(fy, d[cc][1][x], lo[cc][1][x]);  // upsampled mean_b
-                    out[x] = fmaf(A, iv[k][x], B);                        // Eq. (4)
-                }
-                st4<TQ>(Qrow0[cc] + (size_t)Y * P.W, true, 4, out);
+                    for (int x = 0; x < 4; ++x) lo[m][x] += d[m][x];
             }
-        }
-#pragma unroll
-        for (int cc = 0; cc < CC; ++cc)
+            hrow(t + 1, d);
 #pragma unroll
             for (int m = 0; m < 2; ++m)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) lo[cc][m][k] = hi[cc][m][k];
+                for (int x = 0; x < 4; ++x) d[m][x] -= lo[m][x];
+        }
+        const float fy0 = (S == 4) ? 0.125f : (sub ? 0.5625f : 0.0625f);  // (8 sub + 1) / (2S)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int Y = Yq + k;
+            if (Y < Yb || Y >= Ye) continue;
+            const float fy = fy0 + (float)k / (float)S;
+            float out[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                const float A = fmaf(fy, d[0][x], lo[0][x]);  // upsampled mean_a
+                const float B = fmaf(fy, d[1][x], lo[1][x]);  // upsampled mean_b
+                out[x] = fmaf(A, iv[k][x], B);                // Eq. (4)
+            }
+            st4<TQ>(Qp + (size_t)Y * P.W, true, 4, out);
+        }
+    };
+    hrow(0, lo);  // low-res row jb - 1
+    load_quad(0, ivA);
+    for (int u = 0; u < nquads; u += 2) {
+        if (u + 1 < nquads) load_quad(u + 1, ivB);
+        do_quad(u, ivA);
+        if (u + 1 >= nquads) break;
+        if (u + 2 < nquads) load_quad(u + 2, ivA);
+        do_quad(u + 1, ivB);
     }
 }
 
@@ -800,7 +796,10 @@ cudaError_t launch_box_v(const BoxParams &bp, int planes, cudaStream_t st)
         configured = smem;
     }
     dim3 grid((bp.w + BT_TW - 1) / BT_TW, (bp.h + BT_TH - 1) / BT_TH, planes);
-    k_box_tile<T, KIND, COMP, RV, RH><<<grid, BT_NT, smem, st>>>(bp);
+    // one phase-1 item (column segment) per thread when it fits; phase 2 needs BT_TH * BT_TW / RH <= 256
+    const int items = (BT_TW + 2 * bp.r) * (BT_TH / RV);
+    const int nt = std::min(BT_NT_MAX, std::max(256, (items + 31) / 32 * 32));
+    k_box_tile<T, KIND, COMP, RV, RH><<<grid, nt, smem, st>>>(bp);
     return cudaGetLastError();
 }
 
@@ -828,15 +827,13 @@ void launch_up_t(UpParams up, int N, int CC, bool vec, cudaStream_t st)
         return;
     }
     if (vec && up.CI == 1 && (up.s == 4 || up.s == 8)) {
-        up.R = 4 * up.s;  // 4 low-res rows per CTA
+        up.R = 8 * up.s;  // 8 low-res rows per CTA
         up.LRmax = up.R / up.s + 2;
         up.LCmax = UP_BAND / up.s + 2;
-        dim3 grid(bands, (up.H + up.R - 1) / up.R, N * up.CG);
-        const size_t smem = (size_t)CC * 2 * up.LRmax * up.LCmax * sizeof(float);
-#define GF_UPX(cc, ss) k_upsample_output_s4x<TI, TQ, cc, ss><<<grid, UP_NT, smem, st>>>(up)
-        if (up.s == 4) { if (CC == 3) GF_UPX(3, 4); else GF_UPX(1, 4); }
-        else { if (CC == 3) GF_UPX(3, 8); else GF_UPX(1, 8); }
-#undef GF_UPX
+        dim3 grid(bands * up.C, (up.H + up.R - 1) / up.R, N);
+        const size_t smem = (size_t)2 * up.LRmax * up.LCmax * sizeof(float);
+        if (up.s == 4) k_upsample_output_s4x<TI, TQ, 4><<<grid, UP_NT, smem, st>>>(up);
+        else k_upsample_output_s4x<TI, TQ, 8><<<grid, UP_NT, smem, st>>>(up);
         return;
     }
     up.LRmax = (up.R + up.s - 1) / up.s + 2;
@@ -937,6 +934,8 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         tm.after();
         if (err != cudaSuccess) return err;
     }
+
+    if (P.skip_output) return cudaSuccess;
 
     // ---- Algorithm 2, bilinear upsample of mean_a, mean_b fused with q = mean_a .* I + mean_b
     {

@@ -41,7 +41,23 @@ struct FwdPlan {
     bool int_stats;      // exact integer window sums (uint8 input)
     float int_scale;     // 255 * k: J = int_scale * I' (uint8 path)
     cudaEvent_t *events; // 2*GF_MAX_STAGES or NULL
+    bool skip_output = false;  // stop after the low-res stages (the backward's forward recomputation)
 };
+
+// Everything one backward call needs (gf_backward.cu).  `fwd` describes the forward recomputation; it must
+// write the window statistics (fwd.stats), a, mean_a and the low-res I', p' into the workspace.
+struct BwdPlan {
+    FwdPlan fwd;
+    const float *dq;      // dL/dq, N x C x H x W
+    float *dI, *dp;       // outputs: N x CI x H x W; like p (full or low resolution)
+    float *d_eps;         // device scalar or NULL
+    float *dma, *dmb;     // U^T(g .* I), U^T(g): N x C planes of stride fwd.lps
+    float *gq[4];         // d mean_I, d corr_I, d corr_Ip, d mean_p
+    float *dIl, *dpl;     // dI', dp'
+    float *eps_partial;   // bwd_eps_partials() floats
+};
+size_t bwd_eps_partials(int N, int C, int h, int w);
+cudaError_t launch_backward(const BwdPlan &B, cudaStream_t stream);
 
 // A forward call's arguments, checked and resolved on the host (gf_api.cu).
 struct Resolved {
