@@ -287,7 +287,83 @@ def run_native(args, world, rank, local):
                       "steps": k_e2e, "api": "gf_filter_host"}
         if rank == 0:
             out["cpu_baseline"] = cpu_baseline(I_np, p_np)
+        out["serving"] = run_serving(local)
     return out
+
+
+# --------------------------------------------------------------------------------------------------------
+# serving workload
+# --------------------------------------------------------------------------------------------------------
+
+def run_serving(local, n_requests=512, slots=4):
+    """Seeded Poisson stream of mixed requests (0.3-24 MP, aspect 4:3 / 16:9 / 1:1, 1 or 3 channels,
+    r = round(0.004 max(H, W)), eps in {1e-4, 1e-2}, s in {4, 8}, FP16 storage) through gf_submit/gf_poll:
+    one-at-a-time launches (gf_filter, each waited for) give the capacity; the loop is then fed all requests
+    at once (saturated) and as Poisson arrivals at 0.5, 0.8 and 1.0 x that capacity."""
+    import paper_1505_00996_gb300 as gf
+    import synth
+    dev = torch.device("cuda", local)
+    reqs = synth.serving_stream(n_requests=n_requests, seed=2, rate_per_s=1.0)
+    maxpix = max(rq["H"] * rq["W"] for rq in reqs)
+    side = int(np.ceil(np.sqrt(maxpix)))
+    base = synth.make_scene(side, side, seed=2)
+    Ibuf = torch.from_numpy(base).to(torch.float16).to(dev).reshape(-1)[:maxpix]
+    pbuf = torch.from_numpy(synth.rgb_noisy_input(base, seed=3)).to(torch.float16).to(dev).reshape(-1)[:3 * maxpix]
+    views = []
+    for rq in reqs:
+        H, W, C = rq["H"], rq["W"], rq["C"]
+        I = Ibuf[:H * W].view(H, W)
+        p = pbuf[:C * H * W].view(C, H, W)
+        q = torch.empty((C, H, W), dtype=torch.float16, device=dev)
+        views.append((I, p, q))
+    total_mp = sum(rq["H"] * rq["W"] for rq in reqs) / 1e6
+
+    # one at a time: plain gf_filter launches, each waited for
+    stream = torch.cuda.Stream(device=dev)
+    for rq, (I, p, q) in list(zip(reqs, views))[:8]:
+        gf.fast_guided_filter(I, p, rq["r"], rq["eps"], rq["s"], "bilinear", out=q, stream=stream)
+    torch.cuda.synchronize()
+    service = []
+    for rq, (I, p, q) in zip(reqs, views):
+        t0 = time.perf_counter()
+        gf.fast_guided_filter(I, p, rq["r"], rq["eps"], rq["s"], "bilinear", out=q, stream=stream)
+        stream.synchronize()
+        service.append(time.perf_counter() - t0)
+    one_total = sum(service)
+    capacity = n_requests / one_total  # requests per second
+
+    srv = gf.Server(device=local, hbm_budget_bytes=8 << 30, slots=slots)
+
+    def run_stream(arrivals):
+        tickets = []
+        t_start = srv.clock()
+        for a, rq, (I, p, q) in zip(arrivals, reqs, views):
+            while srv.clock() - t_start < a:
+                pass
+            tickets.append(srv.submit(I, p, q, rq["r"], rq["eps"], rq["s"], "bilinear"))
+        res = [srv.poll(t) for t in tickets]
+        assert all(r["status"] == gf.GF_OK for r in res)
+        lat = np.array([r["t_done"] - r["t_submit"] for r in res]) * 1e3
+        span = max(r["t_done"] for r in res) - t_start
+        return {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "mp_per_s": round(total_mp / span, 1)}
+
+    run_stream([0.0] * 16)  # warm the loop
+    saturated = run_stream([0.0] * n_requests)
+    gaps = np.array([rq["arrival_s"] for rq in reqs])
+    loads = []
+    for frac in (0.5, 0.8, 1.0):
+        lam = frac * capacity
+        r = run_stream(list(gaps / lam))
+        r["load"] = frac
+        r["arrival_rate_per_s"] = round(lam, 1)
+        loads.append(r)
+    srv.close()
+    svc_ms = np.array(service) * 1e3
+    return {"requests": n_requests, "slots": slots, "storage": "f16", "total_mp": round(total_mp, 1),
+            "one_at_a_time": {"mp_per_s": round(total_mp / one_total, 1), "p50_ms": round(float(np.percentile(svc_ms, 50)), 3),
+                              "p99_ms": round(float(np.percentile(svc_ms, 99)), 3), "capacity_req_per_s": round(capacity, 1)},
+            "saturated": saturated, "poisson": loads}
 
 
 # --------------------------------------------------------------------------------------------------------

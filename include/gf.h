@@ -113,7 +113,7 @@ gf_status gf_lowres_geometry(int H, int W, int s, int r, int r_low, int *h, int 
 gf_status gf_workspace_size(int H, int W, int C, int s, const gf_opts *opts, size_t *bytes);
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device memory the serving loop
- * may hold for admitted requests (0 = no cap beyond what cudaMalloc grants).  flags: reserved, 0.
+ * holds for admitted requests' scratch (0 = 2 GiB).  flags: reserved, 0.
  * The context owns a growable scratch arena and the serving state; it does not own any stream. */
 gf_status gf_create(gf_ctx **out, int device, size_t hbm_budget_bytes, unsigned flags);
 
@@ -156,6 +156,68 @@ gf_status gf_backward_workspace_size(int H, int W, int C, int s, const gf_opts *
 gf_status gf_filter_backward(gf_ctx *ctx, const void *I, const void *p, const void *dq, void *dI, void *dp, float *d_eps,
                              int H, int W, int C, int r, float eps, int s, gf_subsample_mode mode, const gf_opts *opts,
                              void *cuda_stream);
+
+/* ---- Serving: continuous batching of filter requests -------------------------------------------------
+ *
+ * gf_submit queues a request and returns at once with a ticket.  A scheduler thread owned by the context
+ * admits queued requests in arrival order as soon as one of its stream slots is free and the request's
+ * low-res scratch fits in the context's HBM budget (gf_create's hbm_budget_bytes; 0 means 2 GiB), taken
+ * from one device arena the context allocates on the first submit.  Admitted requests run on separate
+ * streams, so requests that arrive while others are on the GPU overlap with them.  gf_poll returns the
+ * outcome.  The per-pixel arithmetic is that of gf_filter, so a request's q is the same whether it ran alone
+ * or among others.  I, p and q stay caller-owned and must remain valid until gf_poll reports a terminal
+ * status (GF_OK, GF_ECANCELED or an error).  Times are seconds on gf_clock().
+ */
+typedef struct gf_request {
+    const void *I, *p;  /* device inputs, as for gf_filter */
+    void *q;            /* device output */
+    int H, W, C, r;
+    float eps;
+    int s;
+    gf_subsample_mode mode;
+    gf_opts opts;       /* batch, guide_channels, r_low, p_lowres, dtype_in/out; other fields are ignored */
+    void *user;         /* caller's tag, returned in gf_result */
+} gf_request;
+
+typedef struct gf_result {
+    gf_status status;   /* GF_OK, GF_ECANCELED, or the error the request failed with */
+    uint64_t ticket;
+    void *user;
+    double t_submit, t_admit, t_done;  /* gf_clock() at submission, admission and completion on the GPU */
+    size_t scratch_bytes;              /* the request's HBM footprint in the serving arena */
+} gf_result;
+
+typedef struct gf_serve_stats {
+    int queued, running, slots;
+    size_t budget_bytes, scratch_in_use;
+} gf_serve_stats;
+
+/* Monotonic clock of the serving timestamps, in seconds. */
+double gf_clock(void);
+
+/* Stream slots (concurrent requests, default 4, at most 64) and queue limit (default 4096) of the serving
+ * loop.  Only before the first gf_submit on the context (GF_EBUSY afterwards). */
+gf_status gf_serve_config(gf_ctx *ctx, int slots, size_t queue_limit);
+
+/* Queue a request.  GF_EINVAL for bad arguments, GF_ENOMEM if its scratch can never fit the budget,
+ * GF_EBUSY if the queue is full; otherwise GF_OK and *ticket. */
+gf_status gf_submit(gf_ctx *ctx, const gf_request *req, uint64_t *ticket);
+
+/* Outcome of a request.  timeout_us = 0: check and return GF_PENDING if not finished; > 0: wait at most that
+ * long, then GF_ETIMEOUT; < 0: wait until it finishes.  On a terminal status the result is written to *out
+ * (if not NULL) and the ticket is retired: GF_OK, GF_ECANCELED, or the request's error.  GF_ENOTFOUND for an
+ * unknown or already retired ticket. */
+gf_status gf_poll(gf_ctx *ctx, uint64_t ticket, int64_t timeout_us, gf_result *out);
+
+/* Cancel a request that is still queued (GF_OK); GF_EBUSY once it has been admitted to the GPU. */
+gf_status gf_cancel(gf_ctx *ctx, uint64_t ticket);
+
+/* Hold (paused != 0) or resume admission.  Held requests stay queued (and cancellable); requests already on
+ * the GPU run to completion.  Lets a host drain or stage work. */
+gf_status gf_serve_pause(gf_ctx *ctx, int paused);
+
+/* Queue depth, running requests and scratch in use of the serving loop. */
+gf_status gf_serve_stats_get(gf_ctx *ctx, gf_serve_stats *out);
 
 /*
  * gf_filter without any device allocation.  The paper has no counterpart: this entry point exists for

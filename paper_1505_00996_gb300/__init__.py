@@ -10,3 +10,4 @@ from .binding import (  # noqa: F401
     lowres_geometry, opts_init, fast_guided_filter_backward,
 )
 from .autograd import FastGuidedFilter, FastGuidedFilterFn  # noqa: F401
+from .serving import Server  # noqa: F401

@@ -48,6 +48,30 @@ class GFOpts(ctypes.Structure):
     ]
 
 
+class GFRequest(ctypes.Structure):
+    _fields_ = [
+        ("I", ctypes.c_void_p), ("p", ctypes.c_void_p), ("q", ctypes.c_void_p),
+        ("H", ctypes.c_int), ("W", ctypes.c_int), ("C", ctypes.c_int), ("r", ctypes.c_int),
+        ("eps", ctypes.c_float), ("s", ctypes.c_int), ("mode", ctypes.c_int),
+        ("opts", GFOpts), ("user", ctypes.c_void_p),
+    ]
+
+
+class GFResult(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("ticket", ctypes.c_uint64), ("user", ctypes.c_void_p),
+        ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+        ("scratch_bytes", ctypes.c_size_t),
+    ]
+
+
+class GFServeStats(ctypes.Structure):
+    _fields_ = [
+        ("queued", ctypes.c_int), ("running", ctypes.c_int), ("slots", ctypes.c_int),
+        ("budget_bytes", ctypes.c_size_t), ("scratch_in_use", ctypes.c_size_t),
+    ]
+
+
 _lib = None
 _lib_lock = threading.Lock()
 
@@ -93,6 +117,19 @@ def load_library(build_if_missing=True):
         lib.gf_backward_workspace_size.restype = i
         lib.gf_filter_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, i, i, i, f, i, i, P(GFOpts), vp]
         lib.gf_filter_backward.restype = i
+        lib.gf_clock.restype = ctypes.c_double
+        lib.gf_serve_config.argtypes = [vp, i, sz]
+        lib.gf_serve_config.restype = i
+        lib.gf_serve_pause.argtypes = [vp, i]
+        lib.gf_serve_pause.restype = i
+        lib.gf_submit.argtypes = [vp, P(GFRequest), P(ctypes.c_uint64)]
+        lib.gf_submit.restype = i
+        lib.gf_poll.argtypes = [vp, ctypes.c_uint64, ctypes.c_int64, P(GFResult)]
+        lib.gf_poll.restype = i
+        lib.gf_cancel.argtypes = [vp, ctypes.c_uint64]
+        lib.gf_cancel.restype = i
+        lib.gf_serve_stats_get.argtypes = [vp, P(GFServeStats)]
+        lib.gf_serve_stats_get.restype = i
         _lib = lib
         return lib
 
@@ -200,12 +237,15 @@ def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowr
     if out_dtype not in (torch.float32, torch.float16):
         raise ValueError("out_dtype must be float32 or float16")
     qshape = (N, C, H, W)
+    given = out is not None
     if out is None:
         out = torch.empty(qshape, dtype=out_dtype, device=I.device)
-    elif tuple(out.shape) != qshape or out.dtype != out_dtype or not out.is_contiguous():
-        raise ValueError("out must be a contiguous %s tensor of shape %s" % (out_dtype, qshape))
+    elif out.numel() != N * C * H * W or out.dtype != out_dtype or not out.is_contiguous() or not out.is_cuda:
+        raise ValueError("out must be a contiguous CUDA %s tensor of %d elements" % (out_dtype, N * C * H * W))
+    result = out
+    out = out.view(qshape)
     if min(N, C, H, W) == 0 or p4.numel() == 0:
-        return out.reshape(p.shape[:-2] + (H, W)) if prank < 4 else out
+        return result if given else (out.reshape(p.shape[:-2] + (H, W)) if prank < 4 else out)
     I4 = I4.contiguous()
     p4 = p4.contiguous()
     o = opts_init()
@@ -239,6 +279,8 @@ def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowr
     with torch.cuda.device(I.device):
         check(load_library().gf_filter(ctx.handle, _ptr(I4), _ptr(p4), _ptr(out), H, W, C, int(r), float(eps),
                                        int(s), m, ctypes.byref(o), _stream_handle(stream)))
+    if given:
+        return result
     if prank == 2:
         return out[0, 0]
     if prank == 3:

@@ -21,6 +21,7 @@ struct gf_ctx {
     size_t arena_bytes = 0;
     void *stage = nullptr;  // device copies of host buffers (gf_filter_host)
     size_t stage_bytes = 0;
+    gfk::Server *server = nullptr;  // serving loop, created with the context, started on first submit
 };
 
 namespace {
@@ -237,6 +238,7 @@ gf_status gf_create(gf_ctx **out, int device, size_t hbm_budget_bytes, unsigned 
     gf_ctx *c = new gf_ctx();
     c->device = device;
     c->budget = hbm_budget_bytes;
+    c->server = gfk::server_create(device, hbm_budget_bytes);
     *out = c;
     return GF_OK;
 }
@@ -244,6 +246,7 @@ gf_status gf_create(gf_ctx **out, int device, size_t hbm_budget_bytes, unsigned 
 gf_status gf_destroy(gf_ctx *ctx)
 {
     if (!ctx) return fail(GF_EINVAL, "ctx is NULL");
+    gfk::server_destroy(ctx->server);
     {
         DeviceGuard g(ctx->device);
         cudaDeviceSynchronize();
@@ -408,6 +411,45 @@ gf_status gf_filter_backward(gf_ctx *ctx, const void *I, const void *p, const vo
     cudaError_t e = gfk::launch_backward(B, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch in gf_filter_backward");
     return GF_OK;
+}
+
+double gf_clock(void) { return gfk::now_seconds(); }
+
+gf_status gf_serve_config(gf_ctx *ctx, int slots, size_t queue_limit)
+{
+    if (!ctx) return fail(GF_EINVAL, "ctx is NULL");
+    return gfk::server_config(ctx->server, slots, queue_limit);
+}
+
+gf_status gf_submit(gf_ctx *ctx, const gf_request *req, uint64_t *ticket)
+{
+    if (!ctx) return fail(GF_EINVAL, "ctx is NULL");
+    DeviceGuard guard(ctx->device);
+    return gfk::server_submit(ctx->server, req, ticket);
+}
+
+gf_status gf_poll(gf_ctx *ctx, uint64_t ticket, int64_t timeout_us, gf_result *out)
+{
+    if (!ctx) return fail(GF_EINVAL, "ctx is NULL");
+    return gfk::server_poll(ctx->server, ticket, timeout_us, out);
+}
+
+gf_status gf_cancel(gf_ctx *ctx, uint64_t ticket)
+{
+    if (!ctx) return fail(GF_EINVAL, "ctx is NULL");
+    return gfk::server_cancel(ctx->server, ticket);
+}
+
+gf_status gf_serve_pause(gf_ctx *ctx, int paused)
+{
+    if (!ctx) return fail(GF_EINVAL, "ctx is NULL");
+    return gfk::server_pause(ctx->server, paused);
+}
+
+gf_status gf_serve_stats_get(gf_ctx *ctx, gf_serve_stats *out)
+{
+    if (!ctx || !out) return fail(GF_EINVAL, "ctx and out must not be NULL");
+    return gfk::server_stats(ctx->server, out);
 }
 
 }  // extern "C"

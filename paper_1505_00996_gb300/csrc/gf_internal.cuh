@@ -59,6 +59,18 @@ struct BwdPlan {
 size_t bwd_eps_partials(int N, int C, int h, int w);
 cudaError_t launch_backward(const BwdPlan &B, cudaStream_t stream);
 
+// Serving loop (gf_serve.cu).
+struct Server;
+double now_seconds();
+Server *server_create(int device, size_t budget);
+void server_destroy(Server *s);
+gf_status server_config(Server *s, int slots, size_t queue_limit);
+gf_status server_submit(Server *s, const gf_request *req, uint64_t *ticket);
+gf_status server_poll(Server *s, uint64_t ticket, int64_t timeout_us, gf_result *out);
+gf_status server_cancel(Server *s, uint64_t ticket);
+gf_status server_stats(Server *s, gf_serve_stats *out);
+gf_status server_pause(Server *s, int paused);
+
 // A forward call's arguments, checked and resolved on the host (gf_api.cu).
 struct Resolved {
     int N, C, CI, H, W, h, w, s, r_low, mode, dt_in, dt_out;

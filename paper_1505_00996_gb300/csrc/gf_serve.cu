@@ -1,0 +1,428 @@
+// gf_serve.cu -- the serving loop behind gf_submit / gf_poll / gf_cancel: continuous batching of fast guided
+// filter requests of mixed sizes on one GPU.
+//
+// Requests enter a FIFO queue.  A scheduler thread per context admits the head of the queue as soon as a
+// stream slot is free and the request's low-res scratch (its HBM footprint: the I', p', a, b, mean_a,
+// mean_b planes) fits in the context's budget; the scratch comes from one device arena carved by a
+// first-fit allocator.  Each admitted request runs the forward kernels on its slot's stream, so requests
+// that arrive while others are on the GPU overlap with them on the device.  A host callback enqueued after
+// the kernels timestamps the completion and wakes the scheduler, which frees the slot and the scratch and
+// admits more work.  The per-pixel arithmetic does not depend on what else is running, so a request's
+// result is the same alone and in a mix.
+//
+// Failure handling is host-side: a failed launch marks its request GF_ECUDA and the loop carries on; the
+// environment variable GF_FAULT=launch:<k> makes the k-th admitted launch report failure without launching
+// anything (used by the tests); waits in gf_poll are bounded by the caller's timeout.
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "gf_internal.cuh"
+
+namespace gfk {
+
+double now_seconds()
+{
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+namespace {
+
+// First-fit allocator over [0, size) with coalescing free list; offsets are 256-byte aligned.
+class ArenaAllocator {
+public:
+    explicit ArenaAllocator(size_t size = 0) { reset(size); }
+    void reset(size_t size)
+    {
+        free_.clear();
+        if (size) free_[0] = size;
+        size_ = size;
+    }
+    bool alloc(size_t bytes, size_t *off)
+    {
+        bytes = (bytes + 255) & ~size_t(255);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes, at = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                in_use_ += bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes)
+    {
+        bytes = (bytes + 255) & ~size_t(255);
+        in_use_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t size() const { return size_; }
+    size_t in_use() const { return in_use_; }
+
+private:
+    std::map<size_t, size_t> free_;  // offset -> length
+    size_t size_ = 0, in_use_ = 0;
+};
+
+enum ReqState { QUEUED, RUNNING, DONE, FAILED, CANCELED };
+
+struct Request {
+    uint64_t ticket;
+    gf_request req;
+    Resolved R;
+    Layout L;
+    ReqState state = QUEUED;
+    gf_status status = GF_OK;
+    size_t off = 0;
+    int slot = -1;
+    double t_submit = 0, t_admit = 0;
+    std::atomic<double> t_done{0.0};
+    std::atomic<int> finished{0};  // set by the stream callback
+    struct Server *srv = nullptr;
+};
+
+}  // namespace
+
+struct Server {
+    int device = 0;
+    size_t budget = 0;
+    int nslots = 4;
+    size_t queue_limit = 4096;
+    void *arena = nullptr;
+    ArenaAllocator alloc;
+    std::vector<cudaStream_t> streams;
+    std::vector<uint64_t> slot_owner;  // ticket running on each slot, 0 = free
+    std::mutex mu;
+    std::condition_variable cv_sched, cv_done;
+    std::deque<uint64_t> queue;
+    std::map<uint64_t, std::shared_ptr<Request>> reqs;
+    uint64_t next_ticket = 1;
+    bool stop = false, started = false;
+    std::thread thread;
+    long long launches = 0, fault_launch = -1;
+    bool paused = false;  // admission held (requests stay queued)
+};
+
+namespace {
+
+void CUDART_CB on_done(void *arg)
+{
+    Request *r = static_cast<Request *>(arg);
+    r->t_done.store(now_seconds());
+    r->finished.store(1, std::memory_order_release);
+    Server *s = r->srv;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->cv_sched.notify_all();
+}
+
+// Enqueue the request's kernels on its slot (called with the lock held).  Returns the launch status.
+gf_status launch_request(Server *s, Request &r)
+{
+    if (s->fault_launch >= 0 && s->launches++ == s->fault_launch) {
+        gf_set_error("injected launch failure (GF_FAULT)");
+        return GF_ECUDA;
+    }
+    char *ws = (char *)s->arena + r.off;
+    FwdPlan P;
+    const Resolved &R = r.R;
+    P.N = R.N; P.C = R.C; P.CI = R.CI; P.H = R.H; P.W = R.W; P.h = R.h; P.w = R.w; P.s = R.s;
+    P.r_low = R.r_low; P.mode = R.mode; P.eps = R.eps; P.dt_in = R.dt_in; P.dt_out = R.dt_out;
+    P.p_lowres = R.p_lowres;
+    P.I = r.req.I; P.p = r.req.p; P.q = r.req.q;
+    P.lps = R.lps;
+    const bool sub = R.s > 1 || R.p_lowres;
+    P.Il = sub ? (float *)(ws + r.L.off_Il) : nullptr;
+    P.pl = sub ? (float *)(ws + r.L.off_pl) : nullptr;
+    P.a = (float *)(ws + r.L.off_a);
+    P.b = (float *)(ws + r.L.off_b);
+    P.ma = (float *)(ws + r.L.off_ma);
+    P.mb = (float *)(ws + r.L.off_mb);
+    P.stats = nullptr;
+    P.int_stats = R.int_stats;
+    P.int_scale = R.int_scale;
+    P.events = nullptr;
+    cudaStream_t st = s->streams[r.slot];
+    cudaError_t e = launch_forward(P, st);
+    if (e == cudaSuccess) e = cudaLaunchHostFunc(st, on_done, &r);
+    if (e != cudaSuccess) {
+        gf_set_error(std::string("serving launch: ") + cudaGetErrorString(e));
+        return GF_ECUDA;
+    }
+    return GF_OK;
+}
+
+void scheduler(Server *s)
+{
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lock(s->mu);
+    while (true) {
+        // retire finished requests: free their slot and scratch
+        for (int k = 0; k < s->nslots; ++k) {
+            const uint64_t t = s->slot_owner[k];
+            if (!t) continue;
+            auto &r = *s->reqs[t];
+            if (r.finished.load(std::memory_order_acquire)) {
+                r.state = DONE;
+                s->alloc.release(r.off, r.L.total);
+                s->slot_owner[k] = 0;
+                s->cv_done.notify_all();
+            }
+        }
+        // admit from the head of the queue while a slot is free and the scratch fits
+        while (!s->paused && !s->queue.empty()) {
+            const uint64_t t = s->queue.front();
+            auto it = s->reqs.find(t);
+            if (it == s->reqs.end() || it->second->state != QUEUED) {
+                s->queue.pop_front();
+                continue;
+            }
+            Request &r = *it->second;
+            int slot = -1;
+            for (int k = 0; k < s->nslots; ++k)
+                if (!s->slot_owner[k]) { slot = k; break; }
+            if (slot < 0) break;
+            size_t off;
+            if (!s->alloc.alloc(r.L.total, &off)) break;  // wait for memory to free up
+            s->queue.pop_front();
+            r.off = off;
+            r.slot = slot;
+            r.t_admit = now_seconds();
+            r.state = RUNNING;
+            s->slot_owner[slot] = t;
+            const gf_status st = launch_request(s, r);
+            if (st != GF_OK) {
+                cudaStreamSynchronize(s->streams[slot]);  // nothing of the request may still use its scratch
+                cudaGetLastError();
+                r.state = FAILED;
+                r.status = st;
+                r.t_done.store(now_seconds());
+                s->alloc.release(r.off, r.L.total);
+                s->slot_owner[slot] = 0;
+                s->cv_done.notify_all();
+            }
+        }
+        bool running = false;
+        for (int k = 0; k < s->nslots; ++k) running |= (s->slot_owner[k] != 0);
+        if (s->stop && !running) break;
+        s->cv_sched.wait_for(lock, std::chrono::milliseconds(50));
+    }
+}
+
+gf_status server_start(Server *s)
+{
+    if (s->started) return GF_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(s->device);
+    cudaError_t e = cudaMalloc(&s->arena, s->budget);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaSetDevice(prev);
+        s->arena = nullptr;
+        gf_set_error(std::string("serving arena of ") + std::to_string(s->budget) + " bytes: " + cudaGetErrorString(e));
+        return GF_ENOMEM;
+    }
+    s->alloc.reset(s->budget);
+    s->streams.resize(s->nslots);
+    s->slot_owner.assign(s->nslots, 0);
+    for (int k = 0; k < s->nslots; ++k) cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking);
+    cudaSetDevice(prev);
+    s->thread = std::thread(scheduler, s);
+    s->started = true;
+    return GF_OK;
+}
+
+}  // namespace
+
+Server *server_create(int device, size_t budget)
+{
+    Server *s = new Server();
+    s->device = device;
+    s->budget = budget ? budget : (size_t(2) << 30);
+    if (const char *f = getenv("GF_FAULT")) {
+        if (strncmp(f, "launch:", 7) == 0) s->fault_launch = atoll(f + 7);
+    }
+    return s;
+}
+
+void server_destroy(Server *s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
+        for (auto &kv : s->reqs)
+            if (kv.second->state == QUEUED) kv.second->state = CANCELED;
+        s->queue.clear();
+        s->cv_sched.notify_all();
+    }
+    if (s->thread.joinable()) s->thread.join();
+    if (s->started) {
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaSetDevice(s->device);
+        for (auto st : s->streams) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
+        if (s->arena) cudaFree(s->arena);
+        cudaSetDevice(prev);
+    }
+    delete s;
+}
+
+gf_status server_config(Server *s, int slots, size_t queue_limit)
+{
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->started) {
+        gf_set_error("gf_serve_config must be called before the first gf_submit");
+        return GF_EBUSY;
+    }
+    if (slots < 1 || slots > 64) {
+        gf_set_error("slots must be in [1, 64]");
+        return GF_EINVAL;
+    }
+    s->nslots = slots;
+    if (queue_limit) s->queue_limit = queue_limit;
+    return GF_OK;
+}
+
+gf_status server_submit(Server *s, const gf_request *req, uint64_t *ticket)
+{
+    if (!req || !ticket) {
+        gf_set_error("req and ticket must not be NULL");
+        return GF_EINVAL;
+    }
+    if (!req->I || !req->p || !req->q) {
+        gf_set_error("request I, p and q must be device pointers");
+        return GF_EINVAL;
+    }
+    auto r = std::make_shared<Request>();
+    r->req = *req;
+    r->req.opts.workspace = nullptr;
+    r->req.opts.kernel_events = nullptr;
+    r->req.opts.a_out = r->req.opts.b_out = r->req.opts.mean_a_out = r->req.opts.mean_b_out = nullptr;
+    r->req.opts.stats_out = nullptr;
+    gf_status st = resolve(req->H, req->W, req->C, req->r, req->eps, req->s, (int)req->mode, &r->req.opts, r->R);
+    if (st != GF_OK) return st;
+    r->L = layout_of(r->R, &r->req.opts);
+    r->srv = s;
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (r->L.total > s->budget) {
+        gf_set_error("request scratch of " + std::to_string(r->L.total) + " bytes can never fit the serving budget of " +
+                     std::to_string(s->budget) + " bytes");
+        return GF_ENOMEM;
+    }
+    if (s->queue.size() >= s->queue_limit) {
+        gf_set_error("serving queue is full");
+        return GF_EBUSY;
+    }
+    if ((st = server_start(s)) != GF_OK) return st;
+    r->ticket = s->next_ticket++;
+    r->t_submit = now_seconds();
+    s->reqs[r->ticket] = r;
+    s->queue.push_back(r->ticket);
+    *ticket = r->ticket;
+    s->cv_sched.notify_all();
+    return GF_OK;
+}
+
+gf_status server_poll(Server *s, uint64_t ticket, int64_t timeout_us, gf_result *out)
+{
+    std::unique_lock<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) {
+        gf_set_error("unknown ticket");
+        return GF_ENOTFOUND;
+    }
+    std::shared_ptr<Request> r = it->second;
+    auto terminal = [&] { return r->state == DONE || r->state == FAILED || r->state == CANCELED; };
+    if (!terminal() && timeout_us != 0) {
+        if (timeout_us < 0)
+            s->cv_done.wait(lock, terminal);
+        else
+            s->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), terminal);
+    }
+    if (!terminal()) return timeout_us == 0 ? GF_PENDING : GF_ETIMEOUT;
+    if (out) {
+        out->status = r->state == CANCELED ? GF_ECANCELED : r->status;
+        out->ticket = r->ticket;
+        out->user = r->req.user;
+        out->t_submit = r->t_submit;
+        out->t_admit = r->t_admit;
+        out->t_done = r->t_done.load();
+        out->scratch_bytes = r->L.total;
+    }
+    const gf_status st = r->state == CANCELED ? GF_ECANCELED : r->status;
+    s->reqs.erase(it);  // a terminal result is delivered once
+    if (st != GF_OK) gf_set_error(st == GF_ECANCELED ? "request was cancelled" : "request failed");
+    return st;
+}
+
+gf_status server_cancel(Server *s, uint64_t ticket)
+{
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) {
+        gf_set_error("unknown ticket");
+        return GF_ENOTFOUND;
+    }
+    if (it->second->state != QUEUED) {
+        gf_set_error("request is already running or finished");
+        return GF_EBUSY;
+    }
+    it->second->state = CANCELED;
+    s->cv_done.notify_all();
+    return GF_OK;
+}
+
+gf_status server_pause(Server *s, int paused)
+{
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->paused = paused != 0;
+    s->cv_sched.notify_all();
+    return GF_OK;
+}
+
+gf_status server_stats(Server *s, gf_serve_stats *out)
+{
+    std::lock_guard<std::mutex> lock(s->mu);
+    out->queued = 0;
+    out->running = 0;
+    for (auto &kv : s->reqs) {
+        if (kv.second->state == QUEUED) ++out->queued;
+        if (kv.second->state == RUNNING) ++out->running;
+    }
+    out->budget_bytes = s->budget;
+    out->scratch_in_use = s->alloc.in_use();
+    out->slots = s->nslots;
+    return GF_OK;
+}
+
+}  // namespace gfk
