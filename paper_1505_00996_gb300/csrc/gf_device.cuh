@@ -30,6 +30,15 @@ __device__ __forceinline__ void cp_async4(float *smem_dst, const float *gmem_src
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// 16-byte form (L2 only, both addresses 16-byte aligned), and per-thread group bookkeeping.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // Upsampling taps along one axis: full-res index X samples position (X + 1/2)/s - 1/2 = (2X + 1 - s)/(2s),
 // clamped to [0, n-1].  Integer arithmetic keeps the taps exact.

@@ -394,6 +394,7 @@ __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile(BoxParams P)
 // k_upsample_output / k_output_s1
 // ------------------------------------------------------------------------------------------------------
 constexpr int UP_NT = 128;            // threads per CTA, 4 columns each
+constexpr int UP_NST = 4;             // quads of I rows in the s = 4, 8 kernel's shared ring
 constexpr int UP_BAND = UP_NT * 4;    // full-res columns per CTA
 
 struct UpParams {
@@ -442,6 +443,41 @@ __device__ __forceinline__ void ld4<uint8_t>(const uint8_t *p, bool vec, int val
 #pragma unroll
         for (int k = 0; k < 4; ++k) v[k] = (k < valid) ? (float)p[k] / 255.0f : 0.0f;
     }
+}
+
+// 4 pixels of I from the thread's shared ring slot, as floats.
+template <typename T>
+__device__ __forceinline__ void ld4_shared(const void *p, float v[4]);
+template <>
+__device__ __forceinline__ void ld4_shared<float>(const void *p, float v[4])
+{
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+template <>
+__device__ __forceinline__ void ld4_shared<__half>(const void *p, float v[4])
+{
+    const uint2 t = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+template <>
+__device__ __forceinline__ void ld4_shared<uint8_t>(const void *p, float v[4])
+{
+    const uint32_t t = *reinterpret_cast<const uint32_t *>(p);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (float)((t >> (8 * k)) & 0xffu) / 255.0f;
+}
+// 8-byte (FP16) and 4-byte (uint8) forms of the ring copy.
+template <typename T>
+__device__ __forceinline__ void ld_async_small(void *smem_dst, const T *gmem_src)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if (sizeof(T) == 2)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem_src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem_src) : "memory");
 }
 
 template <typename T>
@@ -668,23 +704,39 @@ __global__ void __launch_bounds__(UP_NT, 8) k_upsample_output_s4x(UpParams P)
     TQ *Qp = (TQ *)P.q + (size_t)(n * P.C + c) * HW + X0;
 
     // Run j covers full-res rows S*j + S/2 .. S*j + S/2 + S - 1 and samples low-res rows j and j+1 (tile
-    // rows t and t+1 for t = j - jb + 1).  Runs are walked in quads of 4 rows; the I rows of the next quad
-    // are requested before the current quad is computed (two register buffers used in turn).
+    // rows t and t+1 for t = j - jb + 1).  Runs are walked in quads of 4 rows.  The I values of the next
+    // UP_NST - 1 quads are in flight at any time: each thread copies its own 4 pixels of every row into its
+    // slots of a shared ring with 16-byte cp.async and reads back only what it copied itself, so the only
+    // synchronisation is the thread's own cp.async group wait.
     constexpr int QPR = S / 4;  // quads per run
+    constexpr int VB = 4 * (int)sizeof(TI);  // bytes of one row's 4 pixels
     const int nquads = (nb + 1) * QPR;
-    float lo[2][4], d[2][4];
-    float ivA[4][4], ivB[4][4];
-    auto load_quad = [&](int u, float (&dst)[4][4]) {
-        const int Yq = S * (jb - 1 + u / QPR) + S / 2 + 4 * (u % QPR);
+    unsigned char *ring = reinterpret_cast<unsigned char *>(tap + 2 * tile);  // [UP_NST][4 rows][UP_NT][VB]
+    auto slot = [&](int stage, int k) { return ring + ((size_t)(stage * 4 + k) * UP_NT + threadIdx.x) * VB; };
+    auto issue_quad = [&](int u) {
+        if (u < nquads) {
+            const int Yq = S * (jb - 1 + u / QPR) + S / 2 + 4 * (u % QPR);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int Y = Yq + k;
-            if (Y >= Yb && Y < Ye) ld4<TI>(Ip + (size_t)Y * P.W, true, 4, dst[k]);
+            for (int k = 0; k < 4; ++k) {
+                const int Y = Yq + k;
+                if (Y >= Yb && Y < Ye) {
+                    if (VB == 16) cp_async16(slot(u % UP_NST, k), Ip + (size_t)Y * P.W);
+                    else ld_async_small<TI>(slot(u % UP_NST, k), Ip + (size_t)Y * P.W);
+                }
+            }
         }
+        cp_async_commit();  // one group per quad, empty past the end, so the group count stays uniform
     };
-    auto do_quad = [&](int u, const float (&iv)[4][4]) {
+    float lo[2][4], d[2][4];
+    hrow(0, lo);  // low-res row jb - 1
+#pragma unroll
+    for (int u = 0; u < UP_NST - 1; ++u) issue_quad(u);
+    for (int u = 0; u < nquads; ++u) {
+        issue_quad(u + UP_NST - 1);
+        cp_async_wait_group<UP_NST - 1>();  // this thread's copies of quad u have landed
         const int t = u / QPR, sub = u % QPR;
         const int Yq = S * (jb - 1 + t) + S / 2 + 4 * sub;
+        if (Yq >= Ye) break;
         if (sub == 0) {
             if (t > 0) {  // the previous run's lower tap row becomes this run's upper one
 #pragma unroll
@@ -703,26 +755,20 @@ __global__ void __launch_bounds__(UP_NT, 8) k_upsample_output_s4x(UpParams P)
         for (int k = 0; k < 4; ++k) {
             const int Y = Yq + k;
             if (Y < Yb || Y >= Ye) continue;
+            float iv[4];
+            ld4_shared<TI>(slot(u % UP_NST, k), iv);
             const float fy = fy0 + (float)k / (float)S;
             float out[4];
 #pragma unroll
             for (int x = 0; x < 4; ++x) {
                 const float A = fmaf(fy, d[0][x], lo[0][x]);  // upsampled mean_a
                 const float B = fmaf(fy, d[1][x], lo[1][x]);  // upsampled mean_b
-                out[x] = fmaf(A, iv[k][x], B);                // Eq. (4)
+                out[x] = fmaf(A, iv[x], B);                   // Eq. (4)
             }
             st4<TQ>(Qp + (size_t)Y * P.W, true, 4, out);
         }
-    };
-    hrow(0, lo);  // low-res row jb - 1
-    load_quad(0, ivA);
-    for (int u = 0; u < nquads; u += 2) {
-        if (u + 1 < nquads) load_quad(u + 1, ivB);
-        do_quad(u, ivA);
-        if (u + 1 >= nquads) break;
-        if (u + 2 < nquads) load_quad(u + 2, ivA);
-        do_quad(u + 1, ivB);
     }
+    cp_async_wait_all();
 }
 
 template <typename TI, typename TQ, int CC, bool VEC>
@@ -830,8 +876,9 @@ void launch_up_t(UpParams up, int N, int CC, bool vec, cudaStream_t st)
         up.R = 8 * up.s;  // 8 low-res rows per CTA
         up.LRmax = up.R / up.s + 2;
         up.LCmax = UP_BAND / up.s + 2;
+        up.LCmax = (up.LCmax + 1) & ~1;  // 2 * LRmax * LCmax floats is then a multiple of 16 bytes
         dim3 grid(bands * up.C, (up.H + up.R - 1) / up.R, N);
-        const size_t smem = (size_t)2 * up.LRmax * up.LCmax * sizeof(float);
+        const size_t smem = (size_t)2 * up.LRmax * up.LCmax * sizeof(float) + (size_t)UP_NST * 4 * UP_NT * 4 * sizeof(TI);
         if (up.s == 4) k_upsample_output_s4x<TI, TQ, 4><<<grid, UP_NT, smem, st>>>(up);
         else k_upsample_output_s4x<TI, TQ, 8><<<grid, UP_NT, smem, st>>>(up);
         return;
