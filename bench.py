@@ -33,6 +33,7 @@ H, W, C, R, EPS, S, MODE = 3000, 4000, 3, 16, 1e-3, 4, "bilinear"
 WORKLOAD = "fast guided filter, 12 MP 4000x3000 FP32 gray guide, 3-channel FP32 p, r=16, eps=1e-3, s=4 bilinear"
 L2_BYTES = 129 * 2**20
 FALLBACK_HBM_GBS = 6800.0
+# kernel stages of one call
 STAGES = ["k_subsample", "k_box_tile_stats_coef", "k_box_tile_mean_ab", "k_upsample_output"]
 
 
@@ -263,6 +264,7 @@ def run_native(args, world, rank, local):
     stage_ms = {name: statistics.mean(e[2 * j].elapsed_time(e[2 * j + 1]) for e in evs)
                 for j, name in enumerate(STAGES)}
     h, w, rl = gf.lowres_geometry(H, W, S, R)
+    kernels_per_call = gf.load_library().gf_filter_kernel_count(H, W, C, S, gf.MODES[MODE], None)
     # algorithmic bytes per launch of the output kernel: read I, read mean_a / mean_b (low res), write q
     alg_bytes = H * W * 4 + 2 * C * h * w * 4 + C * H * W * 4
     peak, peak_src = measured_hbm_peak()
@@ -282,7 +284,7 @@ def run_native(args, world, rank, local):
                             ((I.numel() + p.numel() + q.numel()) * 4 / 2**20),
                       "cuda_graph": use_graph, "streams": len(lanes),
                       "inputs": "each stream filters its own copy of I and p (no input shared through L2)"},
-           "gpu_launches": 4 * args.steps, "roofline": roofline, "clocks": clocks}
+           "gpu_launches": kernels_per_call * args.steps, "roofline": roofline, "clocks": clocks}
 
     if not args.no_extras:
         sweep = {}

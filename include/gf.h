@@ -109,6 +109,11 @@ const char *gf_last_error(void);
  * (Algorithm 2 sets r' = r/s).  Host-only; returns GF_EINVAL for H, W, s < 1 or r < 0. */
 gf_status gf_lowres_geometry(int H, int W, int s, int r, int r_low, int *h, int *w, int *r_prime);
 
+/* Number of kernels one gf_filter call with these arguments launches (host-only; -1 for invalid
+ * arguments): 4 when s > 1 (subsample, statistics + coefficients, box means of a and b, upsample + output),
+ * 3 when s = 1 (no subsample). */
+int gf_filter_kernel_count(int H, int W, int C, int s, gf_subsample_mode mode, const gf_opts *opts);
+
 /* Bytes of device scratch one gf_filter call with these arguments needs (host-only). */
 gf_status gf_workspace_size(int H, int W, int C, int s, const gf_opts *opts, size_t *bytes);
 

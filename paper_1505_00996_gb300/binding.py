@@ -103,6 +103,8 @@ def load_library(build_if_missing=True):
         lib.gf_lowres_geometry.restype = i
         lib.gf_workspace_size.argtypes = [i, i, i, i, P(GFOpts), P(sz)]
         lib.gf_workspace_size.restype = i
+        lib.gf_filter_kernel_count.argtypes = [i, i, i, i, i, P(GFOpts)]
+        lib.gf_filter_kernel_count.restype = i
         lib.gf_create.argtypes = [P(vp), i, sz, ctypes.c_uint]
         lib.gf_create.restype = i
         lib.gf_destroy.argtypes = [vp]

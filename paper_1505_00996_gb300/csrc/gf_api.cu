@@ -398,6 +398,7 @@ gf_status gf_filter_backward(gf_ctx *ctx, const void *I, const void *p, const vo
     P.int_scale = 255.0f;
     P.events = nullptr;
     P.skip_output = true;
+    P.need_lowres = true;
     B.dq = (const float *)dq;
     B.dI = (float *)dI;
     B.dp = (float *)dp;
@@ -450,6 +451,13 @@ gf_status gf_serve_stats_get(gf_ctx *ctx, gf_serve_stats *out)
 {
     if (!ctx || !out) return fail(GF_EINVAL, "ctx and out must not be NULL");
     return gfk::server_stats(ctx->server, out);
+}
+
+int gf_filter_kernel_count(int H, int W, int C, int s, gf_subsample_mode mode, const gf_opts *opts)
+{
+    Resolved R;
+    if (resolve(H, W, C, 0, 0.0f, s, (int)mode, opts, R) != GF_OK) return -1;
+    return gfk::forward_kernel_count(R);
 }
 
 }  // extern "C"

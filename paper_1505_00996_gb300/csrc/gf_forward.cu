@@ -237,11 +237,13 @@ __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile(BoxParams P)
     const T *Xp = (const T *)P.X + (size_t)(n * P.CX + (P.CX == 1 ? 0 : c)) * P.xps;
     const T *Yp = (const T *)P.Y + (size_t)plane * P.yps;
 
+    auto xval = [&](int y, int x) -> float { return ldv(Xp + (size_t)y * w + x); };
+    auto yval = [&](int y, int x) -> float { return ldv(Yp + (size_t)y * w + x); };
     // shift of the float sums: one sample of the tile, so that the sums of squares stay small
     float cx = 0.0f, cy = 0.0f;
     if (!INT) {
-        cx = ldv(Xp + (size_t)y0 * w + x0);
-        cy = ldv(Yp + (size_t)y0 * w + x0);
+        cx = xval(y0, x0);
+        cy = yval(y0, x0);
     }
 
     // ---- phase 1: vertical window sums of every tile column (halo columns included)
@@ -258,14 +260,12 @@ __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile(BoxParams P)
                 for (int q = 0; q < NQ; ++q) Vt[((size_t)q * span + xc) * BT_VP + vrow + i] = 0.0f;
             continue;
         }
-        const T *xcol = Xp + gx, *ycol = Yp + gx;
         float S[NQ], Sc[NQ];
         uint32_t U[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) { S[q] = 0.0f; Sc[q] = 0.0f; U[q] = 0u; }
         auto add_row = [&](int yy, bool sub) {
-            const size_t off = (size_t)yy * w;
-            const float xv = ldv(xcol + off), yv = ldv(ycol + off);
+            const float xv = xval(yy, gx), yv = yval(yy, gx);
             if (INT) {
                 uint32_t qv[4];
                 Q::of_int(xv, yv, qv);
@@ -895,6 +895,20 @@ void launch_up_t(UpParams up, int N, int CC, bool vec, cudaStream_t st)
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// FP32 input at s = 2, 4, 8 (bilinear or nearest, full-res p) whose rows are 16-byte aligned and whose size
+// is a multiple of s: every subsample reads one or two whole vectors per source row and nothing is clamped.
+bool aligned_fp32_subsample(const FwdPlan &P)
+{
+    return (P.dt_in == F32) && !P.p_lowres && (P.mode != GF_SUB_BOX) && (P.s == 2 || P.s == 4 || P.s == 8) &&
+           (P.H % P.s == 0) && (P.W % P.s == 0) && (P.W % 4 == 0) && aligned16(P.I) && aligned16(P.p);
+}
+
+}  // namespace
+
+int forward_kernel_count(const Resolved &R) { return 3 + (R.s > 1 ? 1 : 0); }
+
+namespace {
+
 }  // namespace
 
 cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
@@ -917,9 +931,7 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         else  // a low-res p is only copied into the FP32 workspace
             sp.job[1] = SubJob{P.p, P.pl, planesNC, P.h, P.w, 1, (size_t)P.h * P.w, P.lps};
         const int nz = P.N * P.CI + planesNC;
-        const bool vec_ok = (P.dt_in == F32) && !P.p_lowres && (P.mode != GF_SUB_BOX) &&
-                            (P.s == 2 || P.s == 4 || P.s == 8) && (P.H % P.s == 0) && (P.W % P.s == 0) &&
-                            (P.W % 4 == 0) && aligned16(P.I) && aligned16(P.p);
+        const bool vec_ok = aligned_fp32_subsample(P);
         tm.before();
         if (vec_ok) {
             const int jb = (P.s == 8) ? 4 : 8;

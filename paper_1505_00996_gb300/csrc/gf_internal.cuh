@@ -42,6 +42,7 @@ struct FwdPlan {
     float int_scale;     // 255 * k: J = int_scale * I' (uint8 path)
     cudaEvent_t *events; // 2*GF_MAX_STAGES or NULL
     bool skip_output = false;  // stop after the low-res stages (the backward's forward recomputation)
+    bool need_lowres = false;  // keep I', p' in the workspace (no fused subsample); the backward reads them
 };
 
 // Everything one backward call needs (gf_backward.cu).  `fwd` describes the forward recomputation; it must
@@ -87,6 +88,9 @@ struct Layout {
     size_t off_Il, off_pl, off_a, off_b, off_ma, off_mb, total;
 };
 Layout layout_of(const Resolved &R, const gf_opts *o);
+
+// Kernels one forward call launches for these arguments (host-side, assuming 16-byte aligned buffers).
+int forward_kernel_count(const Resolved &R);
 
 // Launch the forward chain on `stream`.  Returns cudaSuccess or the first launch error.
 cudaError_t launch_forward(const FwdPlan &P, cudaStream_t stream);

@@ -141,10 +141,12 @@ void CUDART_CB on_done(void *arg)
     s->cv_sched.notify_all();
 }
 
-// Enqueue the request's kernels on its slot (called with the lock held).  Returns the launch status.
-gf_status launch_request(Server *s, Request &r)
+// Enqueue the request's kernels on its slot (called with the lock held).  Returns the launch status;
+// *launched_some tells whether any kernel was enqueued before a failure.
+gf_status launch_request(Server *s, Request &r, bool *launched_some)
 {
-    if (s->fault_launch >= 0 && s->launches++ == s->fault_launch) {
+    *launched_some = false;
+    if (s->fault_launch >= 0 && s->launches++ == s->fault_launch) {  // injected: nothing is launched
         gf_set_error("injected launch failure (GF_FAULT)");
         return GF_ECUDA;
     }
@@ -168,6 +170,7 @@ gf_status launch_request(Server *s, Request &r)
     P.int_scale = R.int_scale;
     P.events = nullptr;
     cudaStream_t st = s->streams[r.slot];
+    *launched_some = true;
     cudaError_t e = launch_forward(P, st);
     if (e == cudaSuccess) e = cudaLaunchHostFunc(st, on_done, &r);
     if (e != cudaSuccess) {
@@ -215,10 +218,19 @@ void scheduler(Server *s)
             r.t_admit = now_seconds();
             r.state = RUNNING;
             s->slot_owner[slot] = t;
-            const gf_status st = launch_request(s, r);
+            bool launched_some = false;
+            const gf_status st = launch_request(s, r, &launched_some);
             if (st != GF_OK) {
-                cudaStreamSynchronize(s->streams[slot]);  // nothing of the request may still use its scratch
-                cudaGetLastError();
+                if (launched_some) {
+                    // Kernels of the request may still be running: wait for them before the scratch is reused.
+                    // Never with the lock held: an earlier request's completion callback on this stream may be
+                    // waiting for it.
+                    auto keep = it->second;
+                    lock.unlock();
+                    cudaStreamSynchronize(s->streams[slot]);
+                    cudaGetLastError();
+                    lock.lock();
+                }
                 r.state = FAILED;
                 r.status = st;
                 r.t_done.store(now_seconds());

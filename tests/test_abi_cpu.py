@@ -105,3 +105,12 @@ def test_product_package_does_not_use_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", text, flags=re.M), f
                 assert "gf_oracle" not in text and "libgforacle" not in text, f
+
+
+def test_kernel_count(lib):
+    from paper_1505_00996_gb300 import binding
+    o = binding.opts_init()
+    count = lambda H, W, s, mode: lib.gf_filter_kernel_count(H, W, 3, s, mode, ctypes.byref(o))
+    assert count(3000, 4000, 4, binding.GF_SUB_BILINEAR) == 4
+    assert count(3000, 4000, 1, binding.GF_SUB_BILINEAR) == 3   # s = 1: no subsample stage
+    assert count(0, 4000, 4, binding.GF_SUB_BILINEAR) == -1
