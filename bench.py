@@ -315,6 +315,37 @@ def run_native(args, world, rank, local):
         out["e2e"] = {"value": round(world * mp / dt, 1), "unit": "MP/s",
                       "h2d_bytes_per_step": (I_h.numel() + p_h.numel()) * 4, "d2h_bytes_per_step": q_h.numel() * 4,
                       "steps": k_e2e, "api": "gf_filter_host"}
+        # ---- storage precision: the same 12 MP s = 4 workload stored as FP16, and as uint8
+        prec = {"f32": {"ms_per_step": round(ms_serial, 5), "mp_per_s": round(world * mp / (ms_serial / 1e3), 1)}}
+        for name, dt in (("f16", torch.float16), ("u8", torch.uint8)):
+            if dt == torch.uint8:
+                Iv = (lanes[0]["I"] * 255.0).round().clamp(0, 255).to(torch.uint8)
+                pv = (lanes[0]["p"] * 255.0).round().clamp(0, 255).to(torch.uint8)
+            else:
+                Iv, pv = lanes[0]["I"].to(dt), lanes[0]["p"].to(dt)
+            qv = torch.empty((1, C, H, W), dtype=torch.float16 if dt == torch.float16 else torch.float32, device=dev)
+            call = (lambda Iv=Iv, pv=pv, qv=qv: gf.fast_guided_filter(Iv, pv, R, EPS, S, MODE, out=qv, stream=stream,
+                                                                       ctx=ctx))
+            ms_v = time_steps([(stream, call)], max(20, args.steps // 10), args.warmup, world, 10, use_graph)
+            prec[name] = {"ms_per_step": round(ms_v, 5), "mp_per_s": round(world * mp / (ms_v / 1e3), 1)}
+        out["precision"] = prec
+
+        # ---- trainable layer: batch 16 x 3 x 1024^2 guide, low-res p 16 x 3 x 256^2, s = 4 box, r' = 2, eps = 1e-2
+        Ib = torch.rand((16, 3, 1024, 1024), device=dev)
+        pb = torch.rand((16, 3, 256, 256), device=dev)
+        gq = torch.rand_like(Ib) * 2.0 - 1.0
+        qb = torch.empty_like(Ib)
+        fwd = lambda: gf.fast_guided_filter(Ib, pb, 0, 1e-2, 4, "box", r_low=2, p_lowres=True, out=qb, stream=stream,
+                                            ctx=ctx)
+        bwd = lambda: gf.fast_guided_filter_backward(Ib, pb, gq, 0, 1e-2, 4, "box", r_low=2, p_lowres=True,
+                                                     stream=stream, ctx=ctx)
+        k_tr = max(5, args.steps // 200)
+        ms_f = time_steps([(stream, fwd)], k_tr, 3, world, 1, False)
+        ms_b = time_steps([(stream, bwd)], k_tr, 3, world, 1, False)
+        out["training"] = {"workload": "trainable layer, batch 16 x 3 x 1024^2, s=4 box, r'=2, eps=1e-2, low-res p",
+                           "forward_ms": round(ms_f, 4), "backward_ms": round(ms_b, 4),
+                           "mp_per_s_fwd_bwd": round(world * 16 * 1.048576 / ((ms_f + ms_b) / 1e3), 1), "steps": k_tr}
+        del Ib, pb, gq, qb
         if rank == 0:
             out["cpu_baseline"] = cpu_baseline(I_np, p_np)
         out["serving"] = run_serving(local)

@@ -249,3 +249,31 @@ def test_kernel_events_recorded(gf):
     _run(gf, I, I, 8, 1e-2, 4, 1, kernel_events=ev)
     for k in range(4):  # subsample, statistics + coefficients, box means of a and b, upsample + output
         assert ev[2 * k].elapsed_time(ev[2 * k + 1]) >= 0.0
+
+
+def test_precision_variants_at_12mp(gf, scene12mp):
+    """Storage precision at 12 MP (r = 16, eps = 1e-3, s = 4 bilinear): FP32, FP16 storage (FP32 arithmetic)
+    and uint8 storage (exact integer window sums), each against the FP64 oracle run on the values actually
+    stored.  Prints max-abs / RMS per variant (and the FP16 / uint8 distance from the FP32-input result)."""
+    I, p = scene12mp
+    r, eps, s = 16, 1e-3, 4
+    ref32 = oracle_q(I, p, r, eps, s, 1)
+    report = {}
+    q32 = _run(gf, I, p, r, eps, s, 1)
+    report["f32"] = (max_abs(q32, ref32), float(np.sqrt(np.mean((q32 - ref32) ** 2))))
+    I16, p16 = synth.to_f16_values(I), synth.to_f16_values(p)
+    q16 = gf.fast_guided_filter(torch.from_numpy(I16).cuda(), torch.from_numpy(p16).cuda(), r, eps, s, "bilinear")
+    torch.cuda.synchronize()
+    q16 = q16.float().cpu().numpy().astype(np.float64)
+    ref16 = oracle_q(I16.astype(np.float64), p16.astype(np.float64), r, eps, s, 1)
+    report["f16"] = (max_abs(q16, ref16), float(np.sqrt(np.mean((q16 - ref16) ** 2))), max_abs(q16, ref32))
+    I8, p8 = synth.quantize_u8(I), synth.quantize_u8(p)
+    q8 = gf.fast_guided_filter(torch.from_numpy(I8).cuda(), torch.from_numpy(p8).cuda(), r, eps, s, "bilinear")
+    torch.cuda.synchronize()
+    q8 = q8.cpu().numpy().astype(np.float64)
+    ref8 = oracle_q(I8 / 255.0, p8 / 255.0, r, eps, s, 1)
+    report["u8"] = (max_abs(q8, ref8), float(np.sqrt(np.mean((q8 - ref8) ** 2))), max_abs(q8, ref32))
+    print("precision report (max-abs, rms[, max-abs vs FP32-input oracle]):", report)
+    assert report["f32"][0] <= TOL_F32
+    assert report["f16"][0] <= TOL_F16
+    assert report["u8"][0] <= TOL_F32
