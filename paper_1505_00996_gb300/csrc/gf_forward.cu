@@ -390,6 +390,180 @@ __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile(BoxParams P)
     }
 }
 
+// Packed form of k_box_tile for the FP32 kinds (KIND 0 and 2) at r' <= 16: the window sums travel as float2
+// pairs -- (dx, dy) and (dx^2, dx dy) for the statistics, (a, b) for the means -- through registers, a float2
+// column-sum tile (64-bit shared accesses) and the sliding updates, so every add, subtract and product
+// covers two quantities in one f32x2 instruction.  Same tiling, phases and epilogue as k_box_tile.
+template <typename T, int KIND, int BT_RV, int BT_RH, int RC = 0>
+__global__ void __launch_bounds__(BT_NT_MAX) k_box_tile_x2(BoxParams P)
+{
+    constexpr int NP = (KIND == KIND_MEAN2) ? 1 : 2;  // float2 pairs
+    extern __shared__ float smf[];
+    const int BT_NT = blockDim.x;
+    const int tid = threadIdx.x;
+    const int h = P.h, w = P.w;
+    const int r = RC > 0 ? RC : P.r;  // compile-time for the common small radii
+    const int span = BT_TW + 2 * r;
+    float2 *Vt = reinterpret_cast<float2 *>(smf);           // [NP][span][BT_VP]
+    float *Ot = smf + (size_t)2 * NP * span * BT_VP;         // [2][BT_TH][BT_OP]
+    const int x0 = blockIdx.x * BT_TW, y0 = blockIdx.y * BT_TH;
+    const int plane = blockIdx.z;
+    const int n = plane / P.C, c = plane - n * P.C;
+    const T *Xp = (const T *)P.X + (size_t)(n * P.CX + (P.CX == 1 ? 0 : c)) * P.xps;
+    const T *Yp = (const T *)P.Y + (size_t)plane * P.yps;
+    const float2 shift = make_float2(ldv(Xp + (size_t)y0 * w + x0), ldv(Yp + (size_t)y0 * w + x0));
+
+    // ---- phase 1: vertical window sums
+    constexpr int NSEG_V = BT_TH / BT_RV;
+    for (int item = tid; item < span * NSEG_V; item += BT_NT) {
+        const int xc = item % span, seg = item / span;
+        const int gx = x0 - r + xc;
+        const int ya = y0 + seg * BT_RV, vrow = seg * BT_RV;
+        float2 S[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) S[k] = make_float2(0.0f, 0.0f);
+        if constexpr (RC > 0) {
+            // radius known at compile time: the RV + 2 RC rows of the segment's window span are requested at
+            // once into registers; rows outside the image contribute nothing
+            constexpr int NR = BT_RV + 2 * RC;
+            float2 v[NR];
+            bool ok[NR];
+            if (gx >= 0 && gx < w && ya < h) {
+                const T *xc_p = Xp + gx, *yc_p = Yp + gx;
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    const int yy = ya - RC + k;
+                    ok[k] = (yy >= 0) && (yy < h);
+                    v[k] = ok[k] ? make_float2(ldv(xc_p + yy * w), ldv(yc_p + yy * w)) : shift;
+                }
+                auto acc = [&](int k, bool sub) {
+                    const float2 d = sub2(v[k], shift);  // zero for rows outside the image
+                    if (sub) S[0] = sub2(S[0], d); else S[0] = add2(S[0], d);
+                    if (NP == 2) {
+                        const float2 pr = mul2(make_float2(d.x, d.x), d);  // (dx^2, dx dy)
+                        if (sub) S[NP - 1] = sub2(S[NP - 1], pr); else S[NP - 1] = add2(S[NP - 1], pr);
+                    }
+                };
+#pragma unroll
+                for (int k = 0; k <= 2 * RC; ++k) acc(k, false);
+#pragma unroll
+                for (int i = 0; i < BT_RV; ++i) {
+                    if (i > 0) {
+                        acc(i + 2 * RC, false);
+                        acc(i - 1, true);
+                    }
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) Vt[((size_t)k * span + xc) * BT_VP + vrow + i] = S[k];
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < BT_RV; ++i)
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) Vt[((size_t)k * span + xc) * BT_VP + vrow + i] = S[k];
+            }
+            continue;
+        }
+        if (gx >= 0 && gx < w && ya < h) {
+            const T *xc_p = Xp + gx, *yc_p = Yp + gx;
+            auto row = [&](int yy, bool sub) {
+                const int off = yy * w;
+                const float2 d = sub2(make_float2(ldv(xc_p + off), ldv(yc_p + off)), shift);
+                if (sub) S[0] = sub2(S[0], d); else S[0] = add2(S[0], d);
+                if (NP == 2) {
+                    const float2 pr = mul2(make_float2(d.x, d.x), d);  // (dx^2, dx dy)
+                    if (sub) S[NP - 1] = sub2(S[NP - 1], pr); else S[NP - 1] = add2(S[NP - 1], pr);
+                }
+            };
+            const int lo = max(0, ya - r), hi = min(h - 1, ya + r);
+#pragma unroll 4
+            for (int yy = lo; yy <= hi; ++yy) row(yy, false);
+#pragma unroll
+            for (int i = 0; i < BT_RV; ++i) {
+                const int y = ya + i;
+                if (i > 0) {
+                    if (y + r < h) row(y + r, false);
+                    if (y - r - 1 >= 0) row(y - r - 1, true);
+                }
+#pragma unroll
+                for (int k = 0; k < NP; ++k) Vt[((size_t)k * span + xc) * BT_VP + vrow + i] = S[k];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < BT_RV; ++i)
+#pragma unroll
+                for (int k = 0; k < NP; ++k) Vt[((size_t)k * span + xc) * BT_VP + vrow + i] = S[k];
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 2: horizontal window sums and the epilogue
+    constexpr int NSEG_H = BT_TW / BT_RH;
+    const size_t kstride = (size_t)span * BT_VP;  // between the pair planes of Vt
+    for (int item = tid; item < BT_TH * NSEG_H; item += BT_NT) {
+        const int yr = item % BT_TH, seg = item / BT_TH;
+        const int y = y0 + yr, xa = seg * BT_RH;
+        if (y >= h || x0 + xa >= w) continue;
+        const int ny = min(h - 1, y + r) - max(0, y - r) + 1;
+        const float2 *col = Vt + yr;  // column k of pair plane q at col[q * kstride + k * BT_VP]
+        float2 S[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) S[k] = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int k = 0; k <= 2 * r; ++k) {
+#pragma unroll
+            for (int q = 0; q < NP; ++q) S[q] = add2(S[q], col[q * kstride + (size_t)(xa + k) * BT_VP]);
+        }
+#pragma unroll
+        for (int i = 0; i < BT_RH; ++i) {
+            const int xt = xa + i, x = x0 + xt;
+            if (x >= w) break;
+            if (i > 0) {
+#pragma unroll
+                for (int q = 0; q < NP; ++q)
+                    S[q] = sub2(add2(S[q], col[q * kstride + (size_t)(xt + 2 * r) * BT_VP]),
+                                col[q * kstride + (size_t)(xt - 1) * BT_VP]);
+            }
+            const int nx = min(w - 1, x + r) - max(0, x - r) + 1;
+            const float inv = __fdividef(1.0f, (float)(nx * ny));
+            float o0, o1;
+            if (KIND == KIND_STATS_F) {
+                const float mI = S[0].x * inv, mp = S[0].y * inv;    // shifted means
+                const float eII = S[1].x * inv, eIp = S[1].y * inv;
+                const float var = fmaxf(eII - mI * mI, 0.0f);      // var_I
+                const float cov = eIp - mI * mp;                   // cov_Ip
+                o0 = __fdividef(cov, var + P.eps);                 // a, Eq. (2)
+                o1 = (mp + shift.y) - o0 * (mI + shift.x);         // b, Eq. (3)
+                if (P.stats) {
+                    const size_t ps = (size_t)h * w;
+                    float *st = (float *)P.stats + (size_t)plane * 4 * ps + (size_t)y * w + x;
+                    const float cx = shift.x, cy = shift.y;
+                    st[0] = mI + cx;
+                    st[ps] = eII + cx * (2.0f * mI + cx);
+                    st[2 * ps] = mp + cy;
+                    st[3 * ps] = eIp + cx * mp + cy * mI + cx * cy;
+                }
+            } else {
+                o0 = S[0].x * inv + shift.x;
+                o1 = S[0].y * inv + shift.y;
+            }
+            Ot[yr * BT_OP + xt] = o0;
+            Ot[BT_TH * BT_OP + yr * BT_OP + xt] = o1;
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 3: coalesced write of the tile
+    const size_t obase = (size_t)plane * P.ops;
+    for (int idx = tid; idx < BT_TH * BT_TW; idx += BT_NT) {
+        const int yr = idx / BT_TW, xt = idx - yr * BT_TW;
+        const int y = y0 + yr, x = x0 + xt;
+        if (y < h && x < w) {
+            P.out0[obase + (size_t)y * w + x] = Ot[yr * BT_OP + xt];
+            P.out1[obase + (size_t)y * w + x] = Ot[BT_TH * BT_OP + yr * BT_OP + xt];
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------------------------
 // k_upsample_output / k_output_s1
 // ------------------------------------------------------------------------------------------------------
@@ -851,9 +1025,40 @@ cudaError_t launch_box_v(const BoxParams &bp, int planes, cudaStream_t st)
 
 // Segment lengths grow with the radius (a segment pays 2r'+1 loads to open its window); compensated
 // sums for windows of more than 33 x 33 terms.
+template <typename T, int KIND, int RV, int RH, int RC = 0>
+cudaError_t launch_box_x2(const BoxParams &bp, int planes, cudaStream_t st)
+{
+    const int nq = (KIND == KIND_MEAN2) ? 2 : 4;
+    const size_t smem = box_tile_smem(nq, bp.r);
+    static size_t configured = 0;
+    if (smem > 48 * 1024 && smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_box_tile_x2<T, KIND, RV, RH, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    dim3 grid((bp.w + BT_TW - 1) / BT_TW, (bp.h + BT_TH - 1) / BT_TH, planes);
+    const int items = (BT_TW + 2 * bp.r) * (BT_TH / RV);
+    const int nt = std::min(BT_NT_MAX, std::max(256, (items + 31) / 32 * 32));
+    k_box_tile_x2<T, KIND, RV, RH, RC><<<grid, nt, smem, st>>>(bp);
+    return cudaGetLastError();
+}
+
 template <typename T, int KIND>
 cudaError_t launch_box_t(const BoxParams &bp, int planes, cudaStream_t st)
 {
+    if constexpr (KIND != KIND_STATS_INT) {
+        switch (bp.r) {  // common small radii with the radius known at compile time
+        case 1: return launch_box_x2<T, KIND, 8, 8, 1>(bp, planes, st);
+        case 2: return launch_box_x2<T, KIND, 8, 8, 2>(bp, planes, st);
+        case 3: return launch_box_x2<T, KIND, 8, 8, 3>(bp, planes, st);
+        case 4: return launch_box_x2<T, KIND, 8, 8, 4>(bp, planes, st);
+        default: break;
+        }
+        if (bp.r <= 8) return launch_box_x2<T, KIND, 8, 8>(bp, planes, st);
+        if (bp.r <= 16) return launch_box_x2<T, KIND, 16, 16>(bp, planes, st);
+        return launch_box_v<T, KIND, true, 16, 16>(bp, planes, st);
+    }
     if (bp.r <= 8) return launch_box_v<T, KIND, false, 8, 8>(bp, planes, st);
     if (bp.r <= 16) return launch_box_v<T, KIND, false, 16, 16>(bp, planes, st);
     return launch_box_v<T, KIND, true, 16, 16>(bp, planes, st);
