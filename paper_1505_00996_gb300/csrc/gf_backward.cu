@@ -404,20 +404,12 @@ cudaError_t launch_box_T(const BoxTParams &bp, int planes, cudaStream_t st)
                         sizeof(float);
     dim3 grid((bp.w + BB_TW - 1) / BB_TW, (bp.h + BB_TH - 1) / BB_TH, planes);
     if (bp.r > 16) {
-        static size_t conf = 0;
-        if (smem > 48 * 1024 && smem > conf) {
-            cudaError_t e = cudaFuncSetAttribute(k_bwd_box_T<NIN, EPI, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            conf = smem;
-        }
+        cudaError_t e = opt_in_smem(k_bwd_box_T<NIN, EPI, true>, smem);
+        if (e != cudaSuccess) return e;
         k_bwd_box_T<NIN, EPI, true><<<grid, BB_NT, smem, st>>>(bp);
     } else {
-        static size_t conf = 0;
-        if (smem > 48 * 1024 && smem > conf) {
-            cudaError_t e = cudaFuncSetAttribute(k_bwd_box_T<NIN, EPI, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            conf = smem;
-        }
+        cudaError_t e = opt_in_smem(k_bwd_box_T<NIN, EPI, false>, smem);
+        if (e != cudaSuccess) return e;
         k_bwd_box_T<NIN, EPI, false><<<grid, BB_NT, smem, st>>>(bp);
     }
     return cudaGetLastError();
@@ -447,12 +439,7 @@ cudaError_t launch_backward(const BwdPlan &B, cudaStream_t st)
         up.lps = F.lps;
         const int NRmax = F.s * (up.TJ + 2);
         const size_t smem = ((size_t)2 * NRmax * UT_TI + (size_t)UT_TI * 3 * F.s + (size_t)up.TJ * 3 * F.s) * sizeof(float);
-        static size_t conf = 0;
-        if (smem > 48 * 1024 && smem > conf) {
-            if ((err = cudaFuncSetAttribute(k_bwd_upsample_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-                return err;
-            conf = smem;
-        }
+        if ((err = opt_in_smem(k_bwd_upsample_T, smem)) != cudaSuccess) return err;
         dim3 grid((F.w + UT_TI - 1) / UT_TI, (F.h + up.TJ - 1) / up.TJ, planes);
         k_bwd_upsample_T<<<grid, UT_NT, smem, st>>>(up);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;

@@ -24,6 +24,9 @@
 //                 compile-time constants: three FMAs per output value.
 //   k_output_s1   the s = 1 form of the last step (no resampling).
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "gf_device.cuh"
 #include "gf_internal.cuh"
@@ -983,6 +986,22 @@ __global__ void __launch_bounds__(UP_NT) k_output_s1(UpParams P)
 // ------------------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------------------
+cudaError_t opt_in_smem(const void *func, size_t smem)
+{
+    if (smem <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> done;  // (kernel, device) -> bytes opted in
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &have = done[{func, dev}];
+    if (smem <= have) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) have = smem;
+    return e;
+}
+
 namespace {
 
 struct StageTimer {
@@ -1008,13 +1027,8 @@ cudaError_t launch_box_v(const BoxParams &bp, int planes, cudaStream_t st)
 {
     const int nq = (KIND == KIND_MEAN2) ? 2 : 4;
     const size_t smem = box_tile_smem(nq, bp.r);
-    static size_t configured = 0;  // largest dynamic shared memory opted in so far for this instantiation
-    if (smem > 48 * 1024 && smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_box_tile<T, KIND, COMP, RV, RH>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    cudaError_t e = opt_in_smem(k_box_tile<T, KIND, COMP, RV, RH>, smem);
+    if (e != cudaSuccess) return e;
     dim3 grid((bp.w + BT_TW - 1) / BT_TW, (bp.h + BT_TH - 1) / BT_TH, planes);
     // one phase-1 item (column segment) per thread when it fits; phase 2 needs BT_TH * BT_TW / RH <= 256
     const int items = (BT_TW + 2 * bp.r) * (BT_TH / RV);
@@ -1030,13 +1044,8 @@ cudaError_t launch_box_x2(const BoxParams &bp, int planes, cudaStream_t st)
 {
     const int nq = (KIND == KIND_MEAN2) ? 2 : 4;
     const size_t smem = box_tile_smem(nq, bp.r);
-    static size_t configured = 0;
-    if (smem > 48 * 1024 && smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_box_tile_x2<T, KIND, RV, RH, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    cudaError_t e = opt_in_smem(k_box_tile_x2<T, KIND, RV, RH, RC>, smem);
+    if (e != cudaSuccess) return e;
     dim3 grid((bp.w + BT_TW - 1) / BT_TW, (bp.h + BT_TH - 1) / BT_TH, planes);
     const int items = (BT_TW + 2 * bp.r) * (BT_TH / RV);
     const int nt = std::min(BT_NT_MAX, std::max(256, (items + 31) / 32 * 32));

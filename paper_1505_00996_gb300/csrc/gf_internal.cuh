@@ -89,6 +89,12 @@ struct Layout {
 };
 Layout layout_of(const Resolved &R, const gf_opts *o);
 
+// Opt kernel `func` in to `smem` bytes of dynamic shared memory on the current device when that is above the
+// 48 KB default.  Thread-safe; the attribute is set once per kernel, device and larger size.
+cudaError_t opt_in_smem(const void *func, size_t smem);
+template <typename F>
+cudaError_t opt_in_smem(F *func, size_t smem) { return opt_in_smem(reinterpret_cast<const void *>(func), smem); }
+
 // Kernels one forward call launches for these arguments (host-side, assuming 16-byte aligned buffers).
 int forward_kernel_count(const Resolved &R);
 

@@ -62,6 +62,11 @@ CASES = [
     (1, 1, 3, 130, 262, 6, 1e-2, 2, 0),     # s = 2, W % 4 != 0: generic paths
     (1, 1, 3, 97, 1300, 9, 1e-3, 4, 1),     # s = 4 fast output, H % 4 != 0, several bands across
     (1, 1, 1, 2000, 48, 40, 1e-3, 1, 1),    # s = 1, r = 40: compensated box sums
+    # s = 4, 8 fast output path at its edges
+    (1, 1, 3, 33, 68, 32, 1e-3, 4, 1),      # r' = 8, window wider than the image
+    (1, 1, 1, 3, 4, 0, 1e-2, 4, 1),         # r' = 0, H < s, a single 4-pixel column
+    (2, 1, 2, 130, 1028, 64, 1e-3, 8, 2),   # s = 8, r' = 8, box subsample, batch, ragged last band
+    (1, 1, 3, 1000, 2052, 20, 1e-2, 4, 0),  # r' = 5, five bands, ragged
 ]
 
 
