@@ -346,10 +346,44 @@ def run_native(args, world, rank, local):
                            "forward_ms": round(ms_f, 4), "backward_ms": round(ms_b, 4),
                            "mp_per_s_fwd_bwd": round(world * 16 * 1.048576 / ((ms_f + ms_b) / 1e3), 1), "steps": k_tr}
         del Ib, pb, gq, qb
+        out["applications"] = run_applications(dev, stream, ctx, world, max(20, args.steps // 10), args.warmup,
+                                               use_graph)
         if rank == 0:
             out["cpu_baseline"] = cpu_baseline(I_np, p_np)
         out["serving"] = run_serving(local)
     return out
+
+
+# --------------------------------------------------------------------------------------------------------
+# the paper's applications (Figs. 1-4) at 12 MP, s = 4
+# --------------------------------------------------------------------------------------------------------
+
+def run_applications(dev, stream, ctx, world, steps, warmup, use_graph):
+    """Edge-preserving smoothing (r = 4, eps = 0.2^2), detail enhancement (r = 16, eps = 0.1^2, q + 5 (I - q)),
+    flash / no-flash denoising (r = 8, eps = 0.02^2) and guided feathering (r = 60, eps = 0.001^2) with the
+    parameters of the paper's figures, s = 4 bilinear, on 12 MP synthetic stand-ins: a 3-channel colour
+    scene as its own (depthwise) guide, the clean scene guiding a noisy copy, and a gray scene guiding a
+    blocky binary mask.  One filter call per step; output MP/s."""
+    import paper_1505_00996_gb300 as gf
+    import synth
+    Hh, Ww = H, W
+    col = torch.from_numpy(synth.make_color_scene(Hh, Ww, seed=5)).to(dev)
+    noisy = (col + 0.1 * torch.randn(col.shape, generator=torch.Generator(device=dev).manual_seed(8), device=dev)
+             ).clamp_(0.0, 1.0)
+    gray = torch.from_numpy(synth.make_scene(Hh, Ww, seed=9)).to(dev)[None]
+    mask = torch.from_numpy(synth.feather_mask(Hh, Ww, seed=10)).to(dev)[None]
+    apps = {"smoothing": (col, col, 4, 0.2 ** 2, 0.0), "detail_x5": (col, col, 16, 0.1 ** 2, 5.0),
+            "flash_no_flash": (col, noisy, 8, 0.02 ** 2, 0.0), "feathering": (gray, mask, 60, 0.001 ** 2, 0.0)}
+    res = {}
+    for name, (Ia, pa, r, eps, gain) in apps.items():
+        qa = torch.empty_like(pa)
+        call = (lambda Ia=Ia, pa=pa, qa=qa, r=r, eps=eps, gain=gain:
+                gf.fast_guided_filter(Ia, pa, r, eps, 4, "bilinear", out=qa, stream=stream, ctx=ctx, detail_gain=gain))
+        ms_a = time_steps([(stream, call)], steps, warmup, world, 10, use_graph)
+        res[name] = {"C": int(pa.shape[0]), "guide_channels": int(Ia.shape[0]), "r": r, "eps": eps,
+                     "detail_gain": gain, "ms_per_step": round(ms_a, 5),
+                     "mp_per_s": round(world * Hh * Ww / 1e6 / (ms_a / 1e3), 1)}
+    return res
 
 
 # --------------------------------------------------------------------------------------------------------

@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define GF_ABI_VERSION 1
+#define GF_ABI_VERSION 2
 #define GF_MAX_STAGES 8 /* kernel stages one gf_filter call can launch (for gf_opts.kernel_events) */
 
 typedef enum gf_status {
@@ -77,6 +77,10 @@ typedef struct gf_ctx gf_ctx;
  *                   makes the call use (and grow) the context's own arena.
  *   kernel_events   optional array of 2*GF_MAX_STAGES cudaEvent_t (as void*): event 2k is recorded
  *                   before and 2k+1 after the k-th kernel the call launches (unused ones untouched).
+ *   detail_gain     k (finite; default 0): the output becomes q + k (I - q) instead of q, with I the
+ *                   guide channel of each output channel -- with p = I, the detail enhancement of the
+ *                   paper's Fig. 2 (k = 5 there).  Applied in the output kernel; forward only
+ *                   (gf_filter_backward returns GF_EINVAL for k != 0).
  */
 typedef struct gf_opts {
     int batch;
@@ -93,6 +97,7 @@ typedef struct gf_opts {
     void *workspace;
     size_t workspace_bytes;
     void **kernel_events;
+    float detail_gain;
 } gf_opts;
 
 /* Default options: batch 1, gray guide, derived r', full-res p, FP32 in and out, nothing optional. */

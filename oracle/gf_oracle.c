@@ -14,6 +14,8 @@
  *     "Algorithm 2 with s = 1 equals Algorithm 1" is a check between two codings.
  *   - The adjoint (backward pass) of Algorithm 2, written operator by operator as scatters of the forward
  *     maps (the paper has no backward pass; it is the exact derivative of the forward above).
+ *   - The detail-enhancement application of the paper's Fig. 2: q + k (I - q), the guide's detail layer
+ *     I - q amplified by k over the filtered base layer q.
  *
  * Readings of points the paper leaves open (each is a parameter of the tests):
  *   R1 box mean: f_mean(x, r)_k = (1/|w_k n Omega|) * sum of x over the window w_k of radius r clipped to
@@ -513,5 +515,21 @@ int gfo_fast_guided_filter_backward(const double *I, const double *p, const doub
     free(Il); free(pl); free(t); free(mean_I); free(mean_p); free(corr_I); free(corr_Ip); free(var);
     free(a); free(mean_a); free(up_a); free(gfull); free(d_ma); free(d_mb); free(da); free(db);
     free(dmI); free(dmp); free(dcI); free(dcIp); free(tI); free(tp); free(dIl); free(dpl); free(dfull);
+    return 0;
+}
+
+/* Detail enhancement (Fig. 2 application: the smoothed base layer q plus k times the detail layer I - q).
+ * q: N x C x H x W; I: N x CI x H x W (channel c uses guide channel c, or channel 0 when CI = 1). */
+int gfo_detail_enhance(const double *I, const double *q, int N, int CI, int C, int H, int W, double k, double *out)
+{
+    if (N < 1 || C < 1 || H < 1 || W < 1 || (CI != 1 && CI != C)) return -1;
+    const size_t HW = (size_t)H * W;
+    for (int n = 0; n < N; ++n)
+        for (int c = 0; c < C; ++c) {
+            const double *Ic = I + ((size_t)n * CI + (CI == 1 ? 0 : c)) * HW;
+            const double *qc = q + ((size_t)n * C + c) * HW;
+            double *oc = out + ((size_t)n * C + c) * HW;
+            for (size_t i = 0; i < HW; ++i) oc[i] = qc[i] + k * (Ic[i] - qc[i]);
+        }
     return 0;
 }

@@ -51,6 +51,8 @@ def _load():
             lib.gfo_guided_filter.restype = i
             lib.gfo_fast_guided_filter_backward.argtypes = [D, D, D, i, i, i, i, i, i, d, i, i, i, i, D, D, D]
             lib.gfo_fast_guided_filter_backward.restype = i
+            lib.gfo_detail_enhance.argtypes = [D, D, i, i, i, i, i, d, D]
+            lib.gfo_detail_enhance.restype = i
             _lib = lib
     return _lib
 
@@ -160,6 +162,19 @@ def fast_guided_filter(I, p, r, eps, s, mode=SUB_BILINEAR, r_low=None, p_lowres=
         if inter:
             inter = {k: v[0] for k, v in inter.items()}
     return (q, inter) if intermediates else q
+
+
+def detail_enhance(I, q, k):
+    """q + k (I - q) (Fig. 2's detail enhancement; I is the guide, one channel shared or one per channel).
+    I: (N, CI, H, W) or lower rank like q; returns an array shaped like q."""
+    I4, _ = _as_nchw(I)
+    q4, qrank = _as_nchw(q)
+    N, CI, H, W = I4.shape
+    C = q4.shape[1]
+    out = np.empty_like(q4)
+    if _load().gfo_detail_enhance(_ptr(I4), _ptr(q4), N, CI, C, H, W, float(k), _ptr(out)) != 0:
+        raise ValueError("oracle rejected the arguments")
+    return out.reshape(np.shape(q))
 
 
 def guided_filter(I, p, r, eps):

@@ -45,6 +45,7 @@ class GFOpts(ctypes.Structure):
         ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
         ("kernel_events", ctypes.c_void_p),
+        ("detail_gain", ctypes.c_float),
     ]
 
 
@@ -217,12 +218,13 @@ def _stream_handle(stream):
 
 def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowres=False, out_dtype=None,
                        out=None, a_out=None, b_out=None, mean_a_out=None, mean_b_out=None, stats_out=None,
-                       workspace=None, kernel_events=None, stream=None, ctx=None):
+                       workspace=None, kernel_events=None, stream=None, ctx=None, detail_gain=0.0):
     """Fast guided filter (Algorithm 2; Algorithm 1 at s = 1) on CUDA tensors, via ``gf_filter``.
 
     I: (H, W), (CI, H, W) or (N, CI, H, W); p: the same rank with C channels (at low resolution when
     ``p_lowres``).  CI is 1 or C.  dtypes: float32, float16 or uint8 (I and p alike).  Returns q shaped like
     p at full resolution, float32 (float16 for float16 input unless ``out_dtype`` says otherwise).
+    ``detail_gain`` k != 0 returns q + k (I - q) instead (detail enhancement when p is I).
     """
     if not (I.is_cuda and p.is_cuda):
         raise ValueError("I and p must be CUDA tensors")
@@ -257,6 +259,7 @@ def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowr
     o.p_lowres = int(bool(p_lowres))
     o.dtype_in = _DTYPES[I.dtype]
     o.dtype_out = _DTYPES[out_dtype]
+    o.detail_gain = float(detail_gain)
     for name, t in (("a_out", a_out), ("b_out", b_out), ("mean_a_out", mean_a_out),
                     ("mean_b_out", mean_b_out), ("stats_out", stats_out)):
         if t is not None:

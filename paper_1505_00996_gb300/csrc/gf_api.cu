@@ -106,6 +106,8 @@ gf_status resolve(int H, int W, int C, int r, float eps, int s, int mode, const 
     R.r_low = o->r_low >= 0 ? o->r_low : lowres_radius(r, s);
     if (R.r_low > gfk::MAX_LOWRES_RADIUS) return fail(GF_EINVAL, "low-res radius r' > 128 is not supported");
     R.eps = eps;
+    if (!isfinite(o->detail_gain)) return fail(GF_EINVAL, "detail_gain must be finite");
+    R.detail = o->detail_gain;
     R.dt_in = o->dtype_in;
     R.dt_out = o->dtype_out;
     R.p_lowres = o->p_lowres != 0;
@@ -177,6 +179,7 @@ gf_status check_backward(const Resolved &R)
     if (R.dt_in != GF_F32 || R.dt_out != GF_F32) return fail(GF_EINVAL, "the backward pass takes FP32 I, p and dq");
     if (R.H > 65535) return fail(GF_EINVAL, "the backward pass needs H <= 65535");
     if (R.N > 65535) return fail(GF_EINVAL, "the backward pass needs batch <= 65535");
+    if (R.detail != 0.0f) return fail(GF_EINVAL, "detail_gain is forward only");
     return GF_OK;
 }
 
@@ -298,6 +301,7 @@ gf_status gf_filter(gf_ctx *ctx, const void *I, const void *p, void *q, int H, i
     P.int_stats = R.int_stats;
     P.int_scale = R.int_scale;
     P.events = (opts && opts->kernel_events) ? (cudaEvent_t *)opts->kernel_events : nullptr;
+    P.detail = R.detail;
 
     cudaError_t e = gfk::launch_forward(P, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch in gf_filter");

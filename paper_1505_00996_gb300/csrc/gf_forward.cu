@@ -581,7 +581,18 @@ struct UpParams {
     int C, CI, H, W, h, w, s, R, CG;  // R: full-res rows per CTA; CG: channel groups per image
     size_t lps;                       // low-res plane stride
     int LRmax, LCmax;                 // staged low-res tile bounds (rows, columns)
+    float detail;                     // detail gain k: output q + k (I - q) (0: q itself)
 };
+
+// Detail-enhancement epilogue (the application of the paper's Fig. 2): q + k (I - q), the guide's detail
+// I - q scaled by k on top of the filtered image.  k = 0 leaves q as it is.
+__device__ __forceinline__ void detail_epilogue(float k, const float iv[4], float out[4])
+{
+    if (k != 0.0f) {
+#pragma unroll
+        for (int x = 0; x < 4; ++x) out[x] = fmaf(k, iv[x] - out[x], out[x]);
+    }
+}
 
 template <typename T>
 __device__ __forceinline__ void ld4(const T *p, bool vec, int valid, float v[4]);
@@ -810,6 +821,7 @@ __global__ void __launch_bounds__(UP_NT) k_upsample_output(UpParams P)
                     const float B = fmaf(fy, hb[cc][1][k] - hb[cc][0][k], hb[cc][0][k]);  // upsampled mean_b
                     out[k] = fmaf(A, ivc[k], B);                                           // Eq. (4)
                 }
+                detail_epilogue(P.detail, ivc, out);
                 st4<TQ>(Qp[cc] + (size_t)Y * P.W + X0, vec, valid, out);
             }
         }
@@ -942,6 +954,7 @@ __global__ void __launch_bounds__(UP_NT, 8) k_upsample_output_s4x(UpParams P)
                 const float B = fmaf(fy, d[1][x], lo[1][x]);  // upsampled mean_b
                 out[x] = fmaf(A, iv[x], B);                   // Eq. (4)
             }
+            detail_epilogue(P.detail, iv, out);
             st4<TQ>(Qp + (size_t)Y * P.W, true, 4, out);
         }
     }
@@ -978,6 +991,7 @@ __global__ void __launch_bounds__(UP_NT) k_output_s1(UpParams P)
             float out[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) out[k] = fmaf(A[cc][k], iv[k], B[cc][k]);  // Eq. (4), s = 1
+            detail_epilogue(P.detail, iv, out);
             st4<TQ>((TQ *)P.q + (size_t)(n * P.C + c) * HW + (size_t)Y * P.W + X0, vec, valid, out);
         }
     }
@@ -1214,6 +1228,7 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
     {
         UpParams up{};
         up.I = P.I; up.ma = P.ma; up.mb = P.mb; up.q = P.q;
+        up.detail = P.detail;
         up.C = P.C; up.CI = P.CI; up.H = P.H; up.W = P.W; up.h = P.h; up.w = P.w; up.s = P.s;
         up.lps = P.lps;
         const int CC = (P.C % 3 == 0) ? 3 : 1;

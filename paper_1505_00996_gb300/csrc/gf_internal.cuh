@@ -41,6 +41,7 @@ struct FwdPlan {
     bool int_stats;      // exact integer window sums (uint8 input)
     float int_scale;     // 255 * k: J = int_scale * I' (uint8 path)
     cudaEvent_t *events; // 2*GF_MAX_STAGES or NULL
+    float detail = 0.0f; // detail gain of the output epilogue (0: plain q)
     bool skip_output = false;  // stop after the low-res stages (the backward's forward recomputation)
     bool need_lowres = false;  // keep I', p' in the workspace (no fused subsample); the backward reads them
 };
@@ -77,6 +78,7 @@ struct Resolved {
     int N, C, CI, H, W, h, w, s, r_low, mode, dt_in, dt_out;
     bool p_lowres, dense_lowres, int_stats;
     float eps, int_scale;
+    float detail;  // detail gain (gf_opts.detail_gain)
     size_t lps;  // low-res plane stride in floats
 };
 // Check every argument of a forward call and derive its geometry (no CUDA call).  On error the thread's

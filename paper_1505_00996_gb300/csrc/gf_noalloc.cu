@@ -99,6 +99,7 @@ extern "C" gf_status gf_filter_noalloc(const void *I, const void *p, void *q, in
     P.int_stats = R.int_stats;
     P.int_scale = R.int_scale;
     P.events = (opts && opts->kernel_events) ? (cudaEvent_t *)opts->kernel_events : nullptr;
+    P.detail = R.detail;
 
     cudaError_t e = gfk::launch_forward(P, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) {

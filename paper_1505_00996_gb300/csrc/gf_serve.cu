@@ -169,6 +169,7 @@ gf_status launch_request(Server *s, Request &r, bool *launched_some)
     P.int_stats = R.int_stats;
     P.int_scale = R.int_scale;
     P.events = nullptr;
+    P.detail = R.detail;
     cudaStream_t st = s->streams[r.slot];
     *launched_some = true;
     cudaError_t e = launch_forward(P, st);

@@ -32,6 +32,43 @@ def make_scene(H, W, seed=0, n_rects=20, noise_sigma=0.05):
     return np.clip(img, 0.0, 1.0).astype(np.float32)
 
 
+def make_color_scene(H, W, seed=0, n_rects=20, noise_sigma=0.05):
+    """3 x H x W colour stand-in for the paper's application images: the recipe of ``make_scene`` with a
+    colour per rectangle.  Draws, in order: per rectangle its colour (3 x U[0, 1]), width, height and
+    top-left corner as in ``make_scene``; then N(0, noise_sigma^2) noise for the 3 planes."""
+    rng = np.random.default_rng(seed)
+    ys = np.arange(H, dtype=np.float64)[:, None] / max(H - 1, 1)
+    xs = np.arange(W, dtype=np.float64)[None, :] / max(W - 1, 1)
+    img = np.repeat((0.5 * (xs + ys))[None], 3, axis=0)
+    for _ in range(n_rects):
+        col = rng.uniform(0.0, 1.0, size=3)
+        rw = max(1, int(round(rng.uniform(0.05, 0.5) * W)))
+        rh = max(1, int(round(rng.uniform(0.05, 0.5) * H)))
+        x0 = int(rng.integers(0, W))
+        y0 = int(rng.integers(0, H))
+        img[:, y0:y0 + rh, x0:x0 + rw] = col[:, None, None]
+    img = img + rng.normal(0.0, noise_sigma, size=img.shape)
+    return np.clip(img, 0.0, 1.0).astype(np.float32)
+
+
+def feather_mask(H, W, seed=4, n_shapes=3, block=16):
+    """Coarse binary mask (float32 0 / 1), the input of guided feathering (the paper's Fig. 4): the union
+    of ``n_shapes`` ellipses (centre uniform over the middle half of the image, semi-axes U[0.1, 0.3] x
+    (W, H)), then made blocky by taking the value at the centre of each ``block`` x ``block`` cell -- a
+    rough mask whose edges the guide is meant to refine."""
+    rng = np.random.default_rng(seed)
+    ys = np.arange(H, dtype=np.float64)[:, None]
+    xs = np.arange(W, dtype=np.float64)[None, :]
+    yc = (np.floor(ys / block) * block + block / 2.0).clip(0, H - 1)
+    xc = (np.floor(xs / block) * block + block / 2.0).clip(0, W - 1)
+    m = np.zeros((H, W), bool)
+    for _ in range(n_shapes):
+        cx, cy = rng.uniform(0.25, 0.75) * W, rng.uniform(0.25, 0.75) * H
+        ax, ay = rng.uniform(0.1, 0.3) * W, rng.uniform(0.1, 0.3) * H
+        m |= ((xc - cx) / ax) ** 2 + ((yc - cy) / ay) ** 2 <= 1.0
+    return m.astype(np.float32)
+
+
 def rgb_noisy_input(I, seed=1, channels=3, sigma=0.1):
     """p = I replicated per channel + independent N(0, sigma^2) noise, clipped to [0, 1] (float32)."""
     rng = np.random.default_rng(seed)

@@ -309,6 +309,31 @@ def test_depthwise_guide_channels():
 
 
 # ---------------------------------------------------------------------------------------------------------
+# Detail enhancement (the application of Fig. 2: base layer q plus k times the detail layer I - q)
+# ---------------------------------------------------------------------------------------------------------
+
+def test_detail_enhance_special_gains():
+    rng = _rng(16)
+    I = rng.uniform(0, 1, (1, 3, 20, 24))
+    q = rng.uniform(0, 1, (1, 3, 20, 24))
+    out = lambda k, I_=I: oracle.detail_enhance(I_, q, k)
+    np.testing.assert_array_equal(out(0.0), q)               # no detail: the base layer
+    np.testing.assert_allclose(out(1.0), I, atol=1e-15)      # all of the detail: the guide itself
+    np.testing.assert_allclose(out(5.0) - q, 5.0 * (out(1.0) - q), atol=1e-13)  # the detail scales with k
+    # a gray guide serves every channel
+    Ig = I[:, :1]
+    np.testing.assert_array_equal(out(2.0, Ig)[0, 2], oracle.detail_enhance(Ig[0, 0], q[0, 2], 2.0))
+
+
+def test_detail_enhance_of_constant_image_is_the_image():
+    # a constant image filtered with itself as guide is returned unchanged (a = 0, b = c), so its
+    # enhanced version at any gain is the image again
+    I = np.full((24, 32), 0.375)
+    q = oracle.fast_guided_filter(I, I, 8, 1e-2, 4, oracle.SUB_BILINEAR)
+    np.testing.assert_array_equal(oracle.detail_enhance(I, q, 5.0), I)
+
+
+# ---------------------------------------------------------------------------------------------------------
 # Backward pass
 # ---------------------------------------------------------------------------------------------------------
 
