@@ -81,6 +81,16 @@ typedef struct gf_ctx gf_ctx;
  *                   guide channel of each output channel -- with p = I, the detail enhancement of the
  *                   paper's Fig. 2 (k = 5 there).  Applied in the output kernel; forward only
  *                   (gf_filter_backward returns GF_EINVAL for k != 0).
+ *   row_begin, row_end
+ *                   0 <= row_begin < row_end <= H: compute and write only output rows [row_begin, row_end)
+ *                   of every plane of q (other rows of q are left untouched); 0, 0 = all rows.  I, p and q
+ *                   still describe the whole image.  The call filters the band of complete s-row blocks
+ *                   that reaches 2 r' low-res rows beyond the tap rows of the range (the rows whose clipped
+ *                   windows could differ from the whole image's are never used), so each strip equals the
+ *                   same rows of the whole-image call up to FP32 rounding order.  This is how one image is
+ *                   split across GPUs: each filters its own rows from the (replicated) input, and no data
+ *                   is exchanged.  Not combined with a_out, b_out, mean_a_out, mean_b_out or stats_out;
+ *                   forward only.
  */
 typedef struct gf_opts {
     int batch;
@@ -98,6 +108,8 @@ typedef struct gf_opts {
     size_t workspace_bytes;
     void **kernel_events;
     float detail_gain;
+    int row_begin;
+    int row_end;
 } gf_opts;
 
 /* Default options: batch 1, gray guide, derived r', full-res p, FP32 in and out, nothing optional. */
@@ -113,6 +125,12 @@ const char *gf_last_error(void);
 /* Low-res geometry of a call: h = ceil(H/s), w = ceil(W/s), and the radius r' used on that grid
  * (Algorithm 2 sets r' = r/s).  Host-only; returns GF_EINVAL for H, W, s < 1 or r < 0. */
 gf_status gf_lowres_geometry(int H, int W, int s, int r, int r_low, int *h, int *w, int *r_prime);
+
+/* The band of rows a call restricted to output rows [row_begin, row_end) filters (gf_opts.row_begin /
+ * row_end): full-res rows [*row0, *row0 + *rows) of I and p -- the only input rows it reads (rows
+ * [*row0 / s, (*row0 + *rows + s - 1) / s) of a low-res p).  r_low < 0 derives r' from r.  Host-only;
+ * GF_EINVAL for invalid arguments. */
+gf_status gf_row_band(int H, int W, int s, int r, int r_low, int row_begin, int row_end, int *row0, int *rows);
 
 /* Number of kernels one gf_filter call with these arguments launches (host-only; -1 for invalid
  * arguments): 4 when s > 1 (subsample, statistics + coefficients, box means of a and b, upsample + output),

@@ -46,6 +46,8 @@ class GFOpts(ctypes.Structure):
         ("workspace_bytes", ctypes.c_size_t),
         ("kernel_events", ctypes.c_void_p),
         ("detail_gain", ctypes.c_float),
+        ("row_begin", ctypes.c_int),
+        ("row_end", ctypes.c_int),
     ]
 
 
@@ -104,6 +106,8 @@ def load_library(build_if_missing=True):
         lib.gf_lowres_geometry.restype = i
         lib.gf_workspace_size.argtypes = [i, i, i, i, P(GFOpts), P(sz)]
         lib.gf_workspace_size.restype = i
+        lib.gf_row_band.argtypes = [i, i, i, i, i, i, i, P(i), P(i)]
+        lib.gf_row_band.restype = i
         lib.gf_filter_kernel_count.argtypes = [i, i, i, i, i, P(GFOpts)]
         lib.gf_filter_kernel_count.restype = i
         lib.gf_create.argtypes = [P(vp), i, sz, ctypes.c_uint]
@@ -155,6 +159,26 @@ def lowres_geometry(H, W, s, r, r_low=-1):
     check(load_library().gf_lowres_geometry(int(H), int(W), int(s), int(r), int(r_low), ctypes.byref(h),
                                             ctypes.byref(w), ctypes.byref(rp)))
     return h.value, w.value, rp.value
+
+
+def row_band(H, W, s, r, row_begin, row_end, r_low=-1):
+    """(row0, rows): the full-res input rows a call restricted to output rows [row_begin, row_end) reads."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    check(load_library().gf_row_band(int(H), int(W), int(s), int(r), int(r_low), int(row_begin), int(row_end),
+                                     ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def row_strips(H, parts, align=1):
+    """Split rows [0, H) into `parts` contiguous strips of nearly equal height whose inner boundaries are
+    multiples of `align` (one strip per device of a row-sharded filter).  Returns [(row_begin, row_end)]."""
+    if parts < 1 or H < 1:
+        raise ValueError("parts and H must be >= 1")
+    cuts = [0]
+    for k in range(1, parts):
+        cuts.append(min(H, max(cuts[-1], int(round(k * H / parts / align)) * align)))
+    cuts.append(H)
+    return [(cuts[k], cuts[k + 1]) for k in range(parts)]
 
 
 class Context:
@@ -218,13 +242,15 @@ def _stream_handle(stream):
 
 def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowres=False, out_dtype=None,
                        out=None, a_out=None, b_out=None, mean_a_out=None, mean_b_out=None, stats_out=None,
-                       workspace=None, kernel_events=None, stream=None, ctx=None, detail_gain=0.0):
+                       workspace=None, kernel_events=None, stream=None, ctx=None, detail_gain=0.0, rows=None):
     """Fast guided filter (Algorithm 2; Algorithm 1 at s = 1) on CUDA tensors, via ``gf_filter``.
 
     I: (H, W), (CI, H, W) or (N, CI, H, W); p: the same rank with C channels (at low resolution when
     ``p_lowres``).  CI is 1 or C.  dtypes: float32, float16 or uint8 (I and p alike).  Returns q shaped like
     p at full resolution, float32 (float16 for float16 input unless ``out_dtype`` says otherwise).
     ``detail_gain`` k != 0 returns q + k (I - q) instead (detail enhancement when p is I).
+    ``rows=(row_begin, row_end)`` computes only those output rows of q (needs ``out``, the whole q, whose
+    other rows are left as they are): one strip of an image split across devices or streams.
     """
     if not (I.is_cuda and p.is_cuda):
         raise ValueError("I and p must be CUDA tensors")
@@ -260,6 +286,10 @@ def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowr
     o.dtype_in = _DTYPES[I.dtype]
     o.dtype_out = _DTYPES[out_dtype]
     o.detail_gain = float(detail_gain)
+    if rows is not None:
+        if not given:
+            raise ValueError("rows needs out= (the whole q; rows outside the range are not written)")
+        o.row_begin, o.row_end = int(rows[0]), int(rows[1])
     for name, t in (("a_out", a_out), ("b_out", b_out), ("mean_a_out", mean_a_out),
                     ("mean_b_out", mean_b_out), ("stats_out", stats_out)):
         if t is not None:

@@ -4,6 +4,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -123,12 +125,66 @@ gf_status resolve(int H, int W, int C, int r, float eps, int s, int mode, const 
         if (side * side * top * top > 4294967295.0)
             return fail(GF_EINVAL, "uint8 input: (2r'+1)^2 * (255k)^2 exceeds 32-bit window sums");
     }
+    R.row0 = 0;
+    R.Yw0 = 0;
+    R.Yw1 = H;
+    R.fps = (size_t)H * W;
+    R.lpin = (size_t)R.h * R.w;
+    if (o->row_begin != 0 || o->row_end != 0) {
+        if (o->row_begin < 0 || o->row_end > H || o->row_begin >= o->row_end)
+            return fail(GF_EINVAL, "row range must satisfy 0 <= row_begin < row_end <= H");
+        if (o->a_out || o->b_out || o->mean_a_out || o->mean_b_out || o->stats_out)
+            return fail(GF_EINVAL, "a row range does not produce the low-res intermediates");
+        // Output row Y samples low-res rows floor((Y + 1/2)/s - 1/2) and the one below (clamped, R7); those
+        // box means need a, b within r' of them, which need statistics within r' more.  Keeping 2 r' low-res
+        // rows beyond the tap rows keeps every window that could end at the band's cut out of the result.
+        auto tap_row = [&](int Y) { return (int)std::floor((2.0 * Y + 1.0 - s) / (2.0 * s)); };
+        const int lo = std::max(0, tap_row(o->row_begin));
+        const int hi = std::min(R.h - 1, tap_row(o->row_end - 1) + (s > 1 ? 1 : 0));
+        const int c0 = std::max(0, lo - 2 * R.r_low), c1 = std::min(R.h, hi + 2 * R.r_low + 1);
+        R.row0 = s * c0;
+        R.H = std::min(H, s * c1) - R.row0;  // complete s-row blocks, or the image's own last rows
+        R.h = c1 - c0;
+        R.Yw0 = o->row_begin - R.row0;
+        R.Yw1 = o->row_end - R.row0;
+    }
     if (R.h > 65535) return fail(GF_EINVAL, "low-res height ceil(H/s) must be <= 65535");
     const long long planes = (long long)R.N * (R.CI + C);
     if (planes > 65535) return fail(GF_EINVAL, "batch * (guide channels + C) must be <= 65535");
     R.dense_lowres = (o->a_out || o->b_out || o->mean_a_out || o->mean_b_out);
     R.lps = R.dense_lowres ? (size_t)R.h * R.w : gfk::plane_stride_f32((size_t)R.h * R.w);
     return GF_OK;
+}
+
+FwdPlan make_plan(const Resolved &R, const Layout &L, const void *I, const void *p, void *q, char *ws,
+                  const gf_opts *opts)
+{
+    FwdPlan P;
+    P.N = R.N; P.C = R.C; P.CI = R.CI; P.H = R.H; P.W = R.W; P.h = R.h; P.w = R.w; P.s = R.s;
+    P.r_low = R.r_low; P.mode = R.mode; P.eps = R.eps; P.dt_in = R.dt_in; P.dt_out = R.dt_out;
+    P.p_lowres = R.p_lowres;
+    const size_t row_off = (size_t)R.row0 * R.W;  // first element of the filtered band in each plane
+    P.I = (const char *)I + row_off * dtype_size(R.dt_in);
+    P.p = (const char *)p + (R.p_lowres ? (size_t)(R.row0 / R.s) * R.w : row_off) * dtype_size(R.dt_in);
+    P.q = q ? (void *)((char *)q + row_off * dtype_size(R.dt_out)) : nullptr;
+    P.fps = R.fps;
+    P.lpin = R.lpin;
+    P.Yw0 = R.Yw0;
+    P.Yw1 = R.Yw1;
+    P.lps = R.lps;
+    const bool sub = R.s > 1 || R.p_lowres;
+    P.Il = sub ? (float *)(ws + L.off_Il) : nullptr;
+    P.pl = sub ? (float *)(ws + L.off_pl) : nullptr;
+    P.a = (opts && opts->a_out) ? opts->a_out : (float *)(ws + L.off_a);
+    P.b = (opts && opts->b_out) ? opts->b_out : (float *)(ws + L.off_b);
+    P.ma = (opts && opts->mean_a_out) ? opts->mean_a_out : (float *)(ws + L.off_ma);
+    P.mb = (opts && opts->mean_b_out) ? opts->mean_b_out : (float *)(ws + L.off_mb);
+    P.stats = opts ? opts->stats_out : nullptr;
+    P.int_stats = R.int_stats;
+    P.int_scale = R.int_scale;
+    P.events = (opts && opts->kernel_events) ? (cudaEvent_t *)opts->kernel_events : nullptr;
+    P.detail = R.detail;
+    return P;
 }
 
 Layout layout_of(const Resolved &R, const gf_opts *o)
@@ -180,6 +236,7 @@ gf_status check_backward(const Resolved &R)
     if (R.H > 65535) return fail(GF_EINVAL, "the backward pass needs H <= 65535");
     if (R.N > 65535) return fail(GF_EINVAL, "the backward pass needs batch <= 65535");
     if (R.detail != 0.0f) return fail(GF_EINVAL, "detail_gain is forward only");
+    if (R.Yw1 - R.Yw0 != R.H) return fail(GF_EINVAL, "a row range is forward only");
     return GF_OK;
 }
 
@@ -284,25 +341,7 @@ gf_status gf_filter(gf_ctx *ctx, const void *I, const void *p, void *q, int H, i
         ws = (char *)ctx->arena;
     }
 
-    gfk::FwdPlan P;
-    P.N = R.N; P.C = R.C; P.CI = R.CI; P.H = R.H; P.W = R.W; P.h = R.h; P.w = R.w; P.s = R.s;
-    P.r_low = R.r_low; P.mode = R.mode; P.eps = R.eps; P.dt_in = R.dt_in; P.dt_out = R.dt_out;
-    P.p_lowres = R.p_lowres;
-    P.I = I; P.p = p; P.q = q;
-    P.lps = R.lps;
-    const bool sub = R.s > 1 || R.p_lowres;
-    P.Il = sub ? (float *)(ws + L.off_Il) : nullptr;
-    P.pl = sub ? (float *)(ws + L.off_pl) : nullptr;
-    P.a = (opts && opts->a_out) ? opts->a_out : (float *)(ws + L.off_a);
-    P.b = (opts && opts->b_out) ? opts->b_out : (float *)(ws + L.off_b);
-    P.ma = (opts && opts->mean_a_out) ? opts->mean_a_out : (float *)(ws + L.off_ma);
-    P.mb = (opts && opts->mean_b_out) ? opts->mean_b_out : (float *)(ws + L.off_mb);
-    P.stats = opts ? opts->stats_out : nullptr;
-    P.int_stats = R.int_stats;
-    P.int_scale = R.int_scale;
-    P.events = (opts && opts->kernel_events) ? (cudaEvent_t *)opts->kernel_events : nullptr;
-    P.detail = R.detail;
-
+    const gfk::FwdPlan P = gfk::make_plan(R, L, I, p, q, ws, opts);
     cudaError_t e = gfk::launch_forward(P, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch in gf_filter");
     return GF_OK;
@@ -384,23 +423,9 @@ gf_status gf_filter_backward(gf_ctx *ctx, const void *I, const void *p, const vo
     }
 
     gfk::BwdPlan B;
+    B.fwd = gfk::make_plan(R, L.fwd, I, p, nullptr, ws, nullptr);
     gfk::FwdPlan &P = B.fwd;
-    P.N = R.N; P.C = R.C; P.CI = R.CI; P.H = R.H; P.W = R.W; P.h = R.h; P.w = R.w; P.s = R.s;
-    P.r_low = R.r_low; P.mode = R.mode; P.eps = R.eps; P.dt_in = R.dt_in; P.dt_out = R.dt_out;
-    P.p_lowres = R.p_lowres;
-    P.I = I; P.p = p; P.q = nullptr;
-    P.lps = R.lps;
-    const bool sub = R.s > 1 || R.p_lowres;
-    P.Il = sub ? (float *)(ws + L.fwd.off_Il) : nullptr;
-    P.pl = sub ? (float *)(ws + L.fwd.off_pl) : nullptr;
-    P.a = (float *)(ws + L.fwd.off_a);
-    P.b = (float *)(ws + L.fwd.off_b);
-    P.ma = (float *)(ws + L.fwd.off_ma);
-    P.mb = (float *)(ws + L.fwd.off_mb);
     P.stats = ws + L.off_stats;
-    P.int_stats = false;
-    P.int_scale = 255.0f;
-    P.events = nullptr;
     P.skip_output = true;
     P.need_lowres = true;
     B.dq = (const float *)dq;
@@ -455,6 +480,22 @@ gf_status gf_serve_stats_get(gf_ctx *ctx, gf_serve_stats *out)
 {
     if (!ctx || !out) return fail(GF_EINVAL, "ctx and out must not be NULL");
     return gfk::server_stats(ctx->server, out);
+}
+
+gf_status gf_row_band(int H, int W, int s, int r, int r_low, int row_begin, int row_end, int *row0, int *rows)
+{
+    if (!row0 || !rows) return fail(GF_EINVAL, "row0 and rows must not be NULL");
+    gf_opts o;
+    gf_opts_init(&o);
+    o.r_low = r_low;
+    o.row_begin = row_begin;
+    o.row_end = row_end;
+    Resolved R;
+    gf_status st = resolve(H, W, 1, r, 0.0f, s, GF_SUB_BILINEAR, &o, R);
+    if (st != GF_OK) return st;
+    *row0 = R.row0;
+    *rows = R.H;
+    return GF_OK;
 }
 
 int gf_filter_kernel_count(int H, int W, int C, int s, gf_subsample_mode mode, const gf_opts *opts)

@@ -582,6 +582,8 @@ struct UpParams {
     size_t lps;                       // low-res plane stride
     int LRmax, LCmax;                 // staged low-res tile bounds (rows, columns)
     float detail;                     // detail gain k: output q + k (I - q) (0: q itself)
+    size_t fps;                       // plane stride of the full-res I and q (elements)
+    int Yw0, Yw1;                     // rows written: [Yw0, Yw1) of the H rows
 };
 
 // Detail-enhancement epilogue (the application of the paper's Fig. 2): q + k (I - q), the guide's detail
@@ -702,10 +704,11 @@ __global__ void __launch_bounds__(UP_NT) k_upsample_output(UpParams P)
 {
     extern __shared__ float tap[];  // [CC][2][LRmax][LCmax] low-res tap tile (mean_a, mean_b)
     const int Xb = blockIdx.x * UP_BAND;
-    const int Yb = blockIdx.y * P.R, Ye = min(Yb + P.R, P.H);
+    const int Yb = max(blockIdx.y * P.R, P.Yw0), Ye = min(min(blockIdx.y * P.R + P.R, P.H), P.Yw1);
+    if (Yb >= Ye) return;  // the whole CTA is outside the written rows
     const int n = blockIdx.z / P.CG, c0 = (blockIdx.z - n * P.CG) * CC;
     const int ncc = min(CC, P.C - c0);
-    const size_t HW = (size_t)P.H * P.W;
+    const size_t HW = P.fps;
 
     // low-res rows / columns this CTA samples
     int ly0, ly1, lx0, lx1, t0, t1;
@@ -828,13 +831,13 @@ __global__ void __launch_bounds__(UP_NT) k_upsample_output(UpParams P)
     }
 }
 
-// s = 4 or 8, one guide channel, 4-aligned rows.  Full-res row S*j + S/2 + k (k = 0 .. S-1) samples low-res
+// s = 4 or 8, 4-aligned rows (one guide channel for all of p, or one per channel).  Full-res row S*j + S/2 + k (k = 0 .. S-1) samples low-res
 // rows j and j+1 with weight (2k + 1)/(2S) on row j+1, so the rows are walked in such S-row runs: one pair of
 // horizontally interpolated tap rows (and their difference) serves the whole run.  Columns: pixels 4t .. 4t+3
 // sample low-res columns i-1, i, i+1 (S = 4) or one adjacent pair of them (S = 8) with fixed weights.  Taps
 // beyond the image are clamped copies, which gives the same value as clamping the sample position.
-// One channel per CTA; the channel is the fastest-varying block index, so the CTAs of one band of I run
-// side by side and share I through L2.
+// One channel per CTA; the channel is the fastest-varying block index, so with one guide channel the CTAs
+// of one band of I run side by side and share I through L2.
 template <typename TI, typename TQ, int S>
 __global__ void __launch_bounds__(UP_NT, 8) k_upsample_output_s4x(UpParams P)
 {
@@ -844,7 +847,8 @@ __global__ void __launch_bounds__(UP_NT, 8) k_upsample_output_s4x(UpParams P)
     const int c = blockIdx.x % P.C, band = blockIdx.x / P.C;
     const int n = blockIdx.z;
     const int Xb = band * UP_BAND;
-    const int Yb = jb * S, Ye = min(Yb + P.R, P.H);
+    const int Yb = max(jb * S, P.Yw0), Ye = min(min(jb * S + P.R, P.H), P.Yw1);  // rows written by this CTA
+    if (Yb >= Ye) return;
     const int ly0 = jb - 1, lx0 = Xb / S - 1;
     const int LR = P.LRmax, LC = P.LCmax, tile = LR * LC;
     {
@@ -888,8 +892,8 @@ __global__ void __launch_bounds__(UP_NT, 8) k_upsample_output_s4x(UpParams P)
         }
     };
 
-    const size_t HW = (size_t)P.H * P.W;
-    const TI *Ip = (const TI *)P.I + (size_t)n * HW + X0;
+    const size_t HW = P.fps;
+    const TI *Ip = (const TI *)P.I + (size_t)(n * P.CI + (P.CI == 1 ? 0 : c)) * HW + X0;
     TQ *Qp = (TQ *)P.q + (size_t)(n * P.C + c) * HW + X0;
 
     // Run j covers full-res rows S*j + S/2 .. S*j + S/2 + S - 1 and samples low-res rows j and j+1 (tile
@@ -968,10 +972,10 @@ __global__ void __launch_bounds__(UP_NT) k_output_s1(UpParams P)
     if (X0 >= P.W) return;
     const int valid = min(4, P.W - X0);
     const bool vec = VEC && (valid == 4);
-    const int Yb = blockIdx.y * P.R, Ye = min(Yb + P.R, P.H);
+    const int Yb = max(blockIdx.y * P.R, P.Yw0), Ye = min(min(blockIdx.y * P.R + P.R, P.H), P.Yw1);
     const int n = blockIdx.z / P.CG, c0 = (blockIdx.z - n * P.CG) * CC;
     const int ncc = min(CC, P.C - c0);
-    const size_t HW = (size_t)P.H * P.W;
+    const size_t HW = P.fps;
     for (int Y = Yb; Y < Ye; ++Y) {
         float iv[4];
         if (P.CI == 1) ld4<TI>((const TI *)P.I + (size_t)n * HW + (size_t)Y * P.W + X0, vec, valid, iv);
@@ -1100,7 +1104,7 @@ void launch_up_t(UpParams up, int N, int CC, bool vec, cudaStream_t st)
 #undef GF_S1
         return;
     }
-    if (vec && up.CI == 1 && (up.s == 4 || up.s == 8)) {
+    if (vec && (up.s == 4 || up.s == 8)) {
         up.R = 8 * up.s;  // 8 low-res rows per CTA
         up.LRmax = up.R / up.s + 2;
         up.LCmax = UP_BAND / up.s + 2;
@@ -1148,17 +1152,20 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
     // ---- Algorithm 2, first step: subsample I and p (skipped at s = 1)
     const void *Xsrc = P.I, *Ysrc = P.p;
     int src_dt = P.dt_in;
+    // A self-guided call (p is I, one guide channel per channel) subsamples once and uses I' as p'; the
+    // backward keeps its own p' plane, so its forward recomputation subsamples both.
+    const bool self_guided = (P.I == P.p) && (P.CI == P.C) && !P.p_lowres && !P.need_lowres;
     if (P.s > 1) {
         SubParams sp;
         sp.h = P.h; sp.w = P.w; sp.mode = P.mode;
         // uint8 path: carry the subsampled values as exact integers J = k * (value in 1/255 units)
         sp.scale = P.int_stats ? P.int_scale / 255.0f : 1.0f;
-        sp.job[0] = SubJob{P.I, P.Il, P.N * P.CI, P.H, P.W, P.s, (size_t)P.H * P.W, P.lps};
+        sp.job[0] = SubJob{P.I, P.Il, P.N * P.CI, P.H, P.W, P.s, P.fps, P.lps};
         if (!P.p_lowres)
-            sp.job[1] = SubJob{P.p, P.pl, planesNC, P.H, P.W, P.s, (size_t)P.H * P.W, P.lps};
+            sp.job[1] = SubJob{P.p, P.pl, planesNC, P.H, P.W, P.s, P.fps, P.lps};
         else  // a low-res p is only copied into the FP32 workspace
-            sp.job[1] = SubJob{P.p, P.pl, planesNC, P.h, P.w, 1, (size_t)P.h * P.w, P.lps};
-        const int nz = P.N * P.CI + planesNC;
+            sp.job[1] = SubJob{P.p, P.pl, planesNC, P.h, P.w, 1, P.lpin, P.lps};
+        const int nz = P.N * P.CI + (self_guided ? 0 : planesNC);
         const bool vec_ok = aligned_fp32_subsample(P);
         tm.before();
         if (vec_ok) {
@@ -1180,7 +1187,7 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         tm.after();
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         Xsrc = P.Il;
-        Ysrc = P.pl;
+        Ysrc = self_guided ? P.Il : P.pl;
         src_dt = F32;
     }
 
@@ -1189,8 +1196,8 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         BoxParams bp{};
         bp.X = Xsrc; bp.Y = Ysrc;
         const bool lowres_src = (P.s > 1);
-        bp.xps = lowres_src ? P.lps : (size_t)P.h * P.w;
-        bp.yps = lowres_src ? P.lps : (size_t)P.h * P.w;
+        bp.xps = lowres_src ? P.lps : P.fps;  // s = 1: I and p themselves (h = H, w = W)
+        bp.yps = lowres_src ? P.lps : (P.p_lowres ? P.lpin : P.fps);
         bp.CX = P.CI; bp.C = P.C;
         bp.out0 = P.a; bp.out1 = P.b; bp.ops = P.lps;
         bp.stats = P.stats;
@@ -1229,6 +1236,9 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         UpParams up{};
         up.I = P.I; up.ma = P.ma; up.mb = P.mb; up.q = P.q;
         up.detail = P.detail;
+        up.fps = P.fps;
+        up.Yw0 = P.Yw0;
+        up.Yw1 = P.Yw1;
         up.C = P.C; up.CI = P.CI; up.H = P.H; up.W = P.W; up.h = P.h; up.w = P.w; up.s = P.s;
         up.lps = P.lps;
         const int CC = (P.C % 3 == 0) ? 3 : 1;

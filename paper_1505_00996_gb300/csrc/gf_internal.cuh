@@ -42,6 +42,9 @@ struct FwdPlan {
     float int_scale;     // 255 * k: J = int_scale * I' (uint8 path)
     cudaEvent_t *events; // 2*GF_MAX_STAGES or NULL
     float detail = 0.0f; // detail gain of the output epilogue (0: plain q)
+    size_t fps = 0;      // plane stride (elements) of the full-res I, p and q (H * W of the whole image)
+    size_t lpin = 0;     // plane stride of a low-res p given by the caller (h * w of the whole image)
+    int Yw0 = 0, Yw1 = 0;  // output rows written, [Yw0, Yw1) of the H rows the plan covers
     bool skip_output = false;  // stop after the low-res stages (the backward's forward recomputation)
     bool need_lowres = false;  // keep I', p' in the workspace (no fused subsample); the backward reads them
 };
@@ -80,6 +83,11 @@ struct Resolved {
     float eps, int_scale;
     float detail;  // detail gain (gf_opts.detail_gain)
     size_t lps;  // low-res plane stride in floats
+    // Row band (gf_opts.row_begin / row_end): H and h above are those of the band of complete s-row blocks
+    // that is filtered; it starts at full-res row row0 of the whole image, and the output rows written are
+    // [Yw0, Yw1) of the band.  Without a row range: row0 = 0, Yw0 = 0, Yw1 = H.
+    int row0, Yw0, Yw1;
+    size_t fps, lpin;  // plane strides of the whole image's full-res planes and of a caller's low-res p
 };
 // Check every argument of a forward call and derive its geometry (no CUDA call).  On error the thread's
 // gf_last_error() message is set.
@@ -90,6 +98,11 @@ struct Layout {
     size_t off_Il, off_pl, off_a, off_b, off_ma, off_mb, total;
 };
 Layout layout_of(const Resolved &R, const gf_opts *o);
+
+// The forward plan of a call: geometry from R, the caller's buffers (advanced to the first row of the
+// filtered band), scratch planes carved from ws as L says, optional outputs and events from opts.
+FwdPlan make_plan(const Resolved &R, const Layout &L, const void *I, const void *p, void *q, char *ws,
+                  const gf_opts *opts);
 
 // Opt kernel `func` in to `smem` bytes of dynamic shared memory on the current device when that is above the
 // 48 KB default.  Thread-safe; the attribute is set once per kernel, device and larger size.

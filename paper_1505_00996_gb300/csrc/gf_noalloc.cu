@@ -82,25 +82,7 @@ extern "C" gf_status gf_filter_noalloc(const void *I, const void *p, void *q, in
 
     // Every low-res plane is written by the kernel that produces it before any kernel reads it, so no part
     // of the shared scratch has to start at zero.
-    gfk::FwdPlan P;
-    P.N = R.N; P.C = R.C; P.CI = R.CI; P.H = R.H; P.W = R.W; P.h = R.h; P.w = R.w; P.s = R.s;
-    P.r_low = R.r_low; P.mode = R.mode; P.eps = R.eps; P.dt_in = R.dt_in; P.dt_out = R.dt_out;
-    P.p_lowres = R.p_lowres;
-    P.I = I; P.p = p; P.q = q;
-    P.lps = R.lps;
-    const bool sub = R.s > 1 || R.p_lowres;
-    P.Il = sub ? (float *)(ws + L.off_Il) : nullptr;
-    P.pl = sub ? (float *)(ws + L.off_pl) : nullptr;
-    P.a = (opts && opts->a_out) ? opts->a_out : (float *)(ws + L.off_a);
-    P.b = (opts && opts->b_out) ? opts->b_out : (float *)(ws + L.off_b);
-    P.ma = (opts && opts->mean_a_out) ? opts->mean_a_out : (float *)(ws + L.off_ma);
-    P.mb = (opts && opts->mean_b_out) ? opts->mean_b_out : (float *)(ws + L.off_mb);
-    P.stats = opts ? opts->stats_out : nullptr;
-    P.int_stats = R.int_stats;
-    P.int_scale = R.int_scale;
-    P.events = (opts && opts->kernel_events) ? (cudaEvent_t *)opts->kernel_events : nullptr;
-    P.detail = R.detail;
-
+    const gfk::FwdPlan P = gfk::make_plan(R, L, I, p, q, ws, opts);
     cudaError_t e = gfk::launch_forward(P, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) {
         gf_set_error(std::string("kernel launch in gf_filter_noalloc: ") + cudaGetErrorString(e));

@@ -151,25 +151,7 @@ gf_status launch_request(Server *s, Request &r, bool *launched_some)
         return GF_ECUDA;
     }
     char *ws = (char *)s->arena + r.off;
-    FwdPlan P;
-    const Resolved &R = r.R;
-    P.N = R.N; P.C = R.C; P.CI = R.CI; P.H = R.H; P.W = R.W; P.h = R.h; P.w = R.w; P.s = R.s;
-    P.r_low = R.r_low; P.mode = R.mode; P.eps = R.eps; P.dt_in = R.dt_in; P.dt_out = R.dt_out;
-    P.p_lowres = R.p_lowres;
-    P.I = r.req.I; P.p = r.req.p; P.q = r.req.q;
-    P.lps = R.lps;
-    const bool sub = R.s > 1 || R.p_lowres;
-    P.Il = sub ? (float *)(ws + r.L.off_Il) : nullptr;
-    P.pl = sub ? (float *)(ws + r.L.off_pl) : nullptr;
-    P.a = (float *)(ws + r.L.off_a);
-    P.b = (float *)(ws + r.L.off_b);
-    P.ma = (float *)(ws + r.L.off_ma);
-    P.mb = (float *)(ws + r.L.off_mb);
-    P.stats = nullptr;
-    P.int_stats = R.int_stats;
-    P.int_scale = R.int_scale;
-    P.events = nullptr;
-    P.detail = R.detail;
+    const FwdPlan P = make_plan(r.R, r.L, r.req.I, r.req.p, r.req.q, ws, nullptr);
     cudaStream_t st = s->streams[r.slot];
     *launched_some = true;
     cudaError_t e = launch_forward(P, st);

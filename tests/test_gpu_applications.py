@@ -105,3 +105,20 @@ def test_detail_gain_is_forward_only(gf):
     st = gf.load_library().gf_filter_backward(ctx.handle, ptr(I), ptr(I), ptr(I), ptr(g), ptr(g), None, 32, 32, 1,
                                               4, 1e-2, 4, gf.GF_SUB_BILINEAR, ctypes.byref(o), None)
     assert st == gf.GF_EINVAL
+
+
+@pytest.mark.parametrize("s,mode,dtype", [(4, "bilinear", torch.float32), (2, "nearest", torch.float32),
+                                          (8, "box", torch.float16), (4, "bilinear", torch.uint8),
+                                          (1, "bilinear", torch.float32)])
+def test_self_guided_call_equals_separate_copy(gf, s, mode, dtype):
+    """p passed as the guide tensor itself (subsampled once, I' reused as p') gives exactly the result of
+    passing a separate copy of it."""
+    I = torch.from_numpy(synth.make_color_scene(200, 328, seed=11)).cuda()
+    if dtype == torch.uint8:
+        I = (I * 255.0).round().to(torch.uint8)
+    else:
+        I = I.to(dtype)
+    q_same = gf.fast_guided_filter(I, I, 8, 1e-2, s, mode)
+    q_copy = gf.fast_guided_filter(I, I.clone(), 8, 1e-2, s, mode)
+    torch.cuda.synchronize()
+    assert torch.equal(q_same, q_copy)
