@@ -47,6 +47,9 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip the s sweep, e2e, cpu baseline")
     ap.add_argument("--streams", type=int, default=2,
                     help="independent images in flight, one stream (own scratch, own input copy) each")
+    ap.add_argument("--shard", choices=["images", "rows"], default="images",
+                    help="N > 1: every rank filters its own image (weak scaling), or one image split into row "
+                         "strips, one per rank (strong scaling; no data exchanged)")
     return ap.parse_args()
 
 
@@ -211,6 +214,12 @@ def time_steps(fns, steps, warmup, world, graph_steps, use_graph):
     return max_over_ranks(ms, world)
 
 
+def rank_rows(world, rank):
+    """Output rows of the 12 MP image that `rank` filters when one image is split into row strips."""
+    from paper_1505_00996_gb300.binding import row_strips
+    return row_strips(H, world, align=8 * S)[rank]
+
+
 def run_native(args, world, rank, local):
     import paper_1505_00996_gb300 as gf
 
@@ -226,9 +235,12 @@ def run_native(args, world, rank, local):
                       "q": torch.empty((1, C, H, W), dtype=torch.float32, device=dev)})
     I, p, q, stream, ctx = lanes[0]["I"], lanes[0]["p"], lanes[0]["q"], lanes[0]["stream"], lanes[0]["ctx"]
 
+    strip = rank_rows(world, rank) if args.shard == "rows" else None
+    share = 1.0 / world if strip is not None else 1.0  # one image per step across all ranks
+
     def filt(s, lane=lanes[0]):
         return lambda: gf.fast_guided_filter(lane["I"], lane["p"], R, EPS, s, MODE, out=lane["q"],
-                                             stream=lane["stream"], ctx=lane["ctx"])
+                                             stream=lane["stream"], ctx=lane["ctx"], rows=strip)
 
     def fns(s, nl=len(lanes)):
         return [(ln["stream"], filt(s, ln)) for ln in lanes[:nl]]
@@ -245,7 +257,7 @@ def run_native(args, world, rank, local):
     with ClockSampler(local) as clk:
         ms = time_steps(fns(S), args.steps, args.warmup, world, graph_steps, use_graph)
     clocks = clk.summary()
-    value = world * mp / (ms / 1e3)
+    value = world * share * mp / (ms / 1e3)
     ms_serial = time_steps(fns(S, 1), args.steps, args.warmup, world, 10, use_graph)
 
     # ---- per-kernel durations from events recorded around each kernel of the same call
@@ -267,6 +279,8 @@ def run_native(args, world, rank, local):
     kernels_per_call = gf.load_library().gf_filter_kernel_count(H, W, C, S, gf.MODES[MODE], None)
     # algorithmic bytes per launch of the output kernel: read I, read mean_a / mean_b (low res), write q
     alg_bytes = H * W * 4 + 2 * C * h * w * 4 + C * H * W * 4
+    if strip is not None:  # this rank's output kernel covers its strip's rows
+        alg_bytes = int(alg_bytes * (strip[1] - strip[0]) / H)
     peak, peak_src = measured_hbm_peak()
     achieved = alg_bytes / (stage_ms["k_upsample_output"] / 1e3) / 1e9
     roofline = {"kernel": "k_upsample_output", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
@@ -276,17 +290,20 @@ def run_native(args, world, rank, local):
 
     out = {"metric": METRIC, "value": round(value, 1), "unit": "MP/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms, 5), "serial_ms_per_step": round(ms_serial, 5),
-           "higher_is_better": True, "scaling": "weak",
+           "higher_is_better": True, "scaling": "strong" if strip is not None else "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "H": H, "W": W, "C": C, "r": R, "eps": EPS, "s": S, "mode": MODE,
-                      "global_batch": world, "parallelism": "replicas" if world > 1 else "single",
+                      "global_batch": 1 if strip is not None else world,
+                      "parallelism": ("row strips" if strip is not None else "replicas") if world > 1 else "single",
                       "l2": "inputs larger than L2 (%.0f MB read+written per step > 129 MB L2); no flush" %
                             ((I.numel() + p.numel() + q.numel()) * 4 / 2**20),
                       "cuda_graph": use_graph, "streams": len(lanes),
                       "inputs": "each stream filters its own copy of I and p (no input shared through L2)"},
            "gpu_launches": kernels_per_call * args.steps, "roofline": roofline, "clocks": clocks}
 
-    if not args.no_extras:
+    if strip is not None:
+        out["config"]["rows_per_rank"] = strip[1] - strip[0]
+    if not args.no_extras and strip is None:  # the extras describe whole images
         sweep = {}
         k_sweep = max(20, args.steps // 10)
         for s in (1, 8):

@@ -1,5 +1,6 @@
 """Multi-rank host logic of bench.py on CPU (gloo, world size 2): rendezvous, barrier, the max-over-ranks
-timing reduction, and that only rank 0 runs and reports the reference arm."""
+timing reduction, that only rank 0 runs and reports the reference arm, and the row strips of the
+row-sharded mode (one image split across ranks)."""
 import os
 import socket
 import sys
@@ -27,8 +28,17 @@ def _worker(rank, world, port, out):
     slowest = bench.max_over_ranks(0.5 + rank, w)  # each rank's own step time
     bench.barrier(w)
     ref = bench.run_reference(types.SimpleNamespace(steps=1, warmup=0), w, r) if r != 0 else "rank0-skipped"
-    out.put((r, w, slowest, ref))
+    # row-sharded mode: every rank's strip, gathered
+    strips = [None] * w
+    dist.all_gather_object(strips, bench.rank_rows(w, r))
+    out.put((r, w, slowest, ref, strips))
     dist.destroy_process_group()
+
+
+def bench_H():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench.H
 
 
 def test_two_gloo_ranks_reduce_timing_and_only_rank0_reports():
@@ -45,3 +55,7 @@ def test_two_gloo_ranks_reduce_timing_and_only_rank0_reports():
     assert [r[1] for r in results] == [2, 2]
     assert all(r[2] == 1.5 for r in results)  # max over ranks of 0.5 and 1.5
     assert results[1][3] is None              # rank 1 runs no reference work and prints nothing
+    # the two ranks' row strips tile the image's rows without overlap, the same on both ranks
+    strips = results[0][4]
+    assert strips == results[1][4]
+    assert strips[0][0] == 0 and strips[0][1] == strips[1][0] and strips[1][1] == bench_H()
