@@ -34,6 +34,10 @@
  *   R8 channels: the guide has CI = 1 channel shared by all C channels of p, or CI = C channels with
  *      channel c guiding channel c; each channel of p is filtered independently.
  *   R9 eps is added to var(I) as given (no rescaling); R10 q is not clamped.
+ *   R11 antialiased bilinear subsample (a fourth mode; the paper names only "bilinear", and this is the
+ *      form a shrinking resize takes when it low-passes first): a triangle filter of half-width s centred
+ *      on the low-res pixel centre, so source pixel x has weight max(0, 1 - |x + 1/2 - (i + 1/2) s| / s)
+ *      along each axis; taps outside the image are dropped and the remaining weights renormalised.
  *
  * Layout: all images are dense row-major planes; a batch is N x channels x rows x cols.
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared -o libgforacle.so gf_oracle.c -lm
@@ -43,7 +47,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { GFO_SUB_NEAREST = 0, GFO_SUB_BILINEAR = 1, GFO_SUB_BOX = 2 };
+enum { GFO_SUB_NEAREST = 0, GFO_SUB_BILINEAR = 1, GFO_SUB_BOX = 2, GFO_SUB_BILINEAR_AA = 3 };
 
 static int imin(int a, int b) { return a < b ? a : b; }
 static int imax(int a, int b) { return a > b ? a : b; }
@@ -76,7 +80,14 @@ static void axis_taps(double t, int n, int *i0, int *i1, double *f)
     *f = t - (double)a;
 }
 
-/* f_subsample(x, s), Algorithm 2 first step; modes R2/R3/R4.  y is ceil(H/s) x ceil(W/s). */
+/* R11: triangle weight of source pixel x for low-res pixel i at ratio s. */
+static double aa_weight(int x, int i, int s)
+{
+    double d = fabs((x + 0.5) - (i + 0.5) * s) / s;
+    return d < 1.0 ? 1.0 - d : 0.0;
+}
+
+/* f_subsample(x, s), Algorithm 2 first step; modes R2/R3/R4/R11.  y is ceil(H/s) x ceil(W/s). */
 void gfo_subsample(const double *x, int H, int W, int s, int mode, double *y)
 {
     int h, w;
@@ -96,6 +107,20 @@ void gfo_subsample(const double *x, int H, int W, int s, int mode, double *y)
                 double top = (1.0 - fx) * x[(size_t)y0 * W + x0] + fx * x[(size_t)y0 * W + x1];
                 double bot = (1.0 - fx) * x[(size_t)y1 * W + x0] + fx * x[(size_t)y1 * W + x1];
                 v = (1.0 - fy) * top + fy * bot;
+            } else if (mode == GFO_SUB_BILINEAR_AA) {
+                /* every source pixel within s of the centre, weighted, over the sum of the weights used */
+                double acc = 0.0, wsum = 0.0;
+                for (int yy = imax(0, j * s - s); yy <= imin(H - 1, j * s + 2 * s); ++yy) {
+                    double wy = aa_weight(yy, j, s);
+                    if (wy == 0.0) continue;
+                    for (int xx = imax(0, i * s - s); xx <= imin(W - 1, i * s + 2 * s); ++xx) {
+                        double wx = aa_weight(xx, i, s);
+                        if (wx == 0.0) continue;
+                        acc += wy * wx * x[(size_t)yy * W + xx];
+                        wsum += wy * wx;
+                    }
+                }
+                v = acc / wsum;
             } else { /* GFO_SUB_BOX */
                 int ya = j * s, yb = imin((j + 1) * s, H);
                 int xa = i * s, xb = imin((i + 1) * s, W);
@@ -207,6 +232,7 @@ int gfo_fast_guided_filter(const double *I, const double *p, int N, int CI, int 
                            double *b_out, double *ma_out, double *mb_out, double *stats_out)
 {
     if (N < 1 || C < 1 || H < 1 || W < 1 || s < 1 || r_low < 0 || !(eps >= 0.0)) return -1;
+    if (mode < GFO_SUB_NEAREST || mode > GFO_SUB_BILINEAR_AA) return -1;
     if (CI != 1 && CI != C) return -1;
     int h, w;
     gfo_lowres_shape(H, W, s, &h, &w);
@@ -417,6 +443,7 @@ int gfo_fast_guided_filter_backward(const double *I, const double *p, const doub
                                     int brute, double *dI, double *dp, double *deps)
 {
     if (N < 1 || C < 1 || H < 1 || W < 1 || s < 1 || r_low < 0 || !(eps >= 0.0)) return -1;
+    if (mode < GFO_SUB_NEAREST || mode > GFO_SUB_BOX) return -1; /* the adjoint covers R2-R4 */
     if (CI != 1 && CI != C) return -1;
     int h, w;
     gfo_lowres_shape(H, W, s, &h, &w);

@@ -10,7 +10,7 @@ import threading
 
 import numpy as np
 
-SUB_NEAREST, SUB_BILINEAR, SUB_BOX = 0, 1, 2
+SUB_NEAREST, SUB_BILINEAR, SUB_BOX, SUB_BILINEAR_AA = 0, 1, 2, 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gf_oracle.c")

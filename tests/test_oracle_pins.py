@@ -90,7 +90,7 @@ def test_box_sum_integer_exact():
 # Subsample / upsample conventions (R2-R5, R7)
 # ---------------------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("mode", [oracle.SUB_NEAREST, oracle.SUB_BILINEAR, oracle.SUB_BOX])
+@pytest.mark.parametrize("mode", [oracle.SUB_NEAREST, oracle.SUB_BILINEAR, oracle.SUB_BOX, oracle.SUB_BILINEAR_AA])
 @pytest.mark.parametrize("s", [2, 3, 4, 8])
 def test_subsample_matches_torch_divisible(mode, s):
     H, W = 5 * s, 3 * s
@@ -118,7 +118,29 @@ def test_subsample_ragged_conventions():
     assert bil[2, 0] == pytest.approx(x[9, 1:3].mean())
 
 
-@pytest.mark.parametrize("mode", [oracle.SUB_NEAREST, oracle.SUB_BILINEAR, oracle.SUB_BOX])
+def test_antialiased_subsample_hand_weights():
+    # R11 at s = 4 along y on an image constant along x: interior rows take the taps 4j-2 .. 4j+5 with
+    # weights (1, 3, 5, 7, 7, 5, 3, 1) / 32; the top row loses taps -2, -1 and renormalises the rest,
+    # (5, 7, 7, 5, 3, 1) / 28; the bottom row of a 13-row image keeps only its taps 10, 11, 12: (1, 3, 5) / 9.
+    rows = np.array([2.0, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41])
+    x = np.repeat(rows[:, None], 8, axis=1)
+    y = oracle.subsample(x, 4, oracle.SUB_BILINEAR_AA)
+    assert y.shape == (4, 2)
+    assert y[1, 0] == pytest.approx(np.dot([1, 3, 5, 7, 7, 5, 3, 1], rows[2:10]) / 32, abs=1e-14)
+    assert y[0, 0] == pytest.approx(np.dot([5, 7, 7, 5, 3, 1], rows[0:6]) / 28, abs=1e-14)
+    assert y[3, 1] == pytest.approx(np.dot([1, 3, 5], rows[10:13]) / 9, abs=1e-14)
+    # odd s: s = 3 interior taps 3j-1 .. 3j+3 with weights (1, 2, 3, 2, 1) / 9
+    y3 = oracle.subsample(x[:12], 3, oracle.SUB_BILINEAR_AA)
+    assert y3[2, 0] == pytest.approx(np.dot([1, 2, 3, 2, 1], rows[5:10]) / 9, abs=1e-14)
+
+
+def test_antialiased_subsample_keeps_constants():
+    x = np.full((11, 14), 0.3)
+    for s in (2, 3, 4, 8):
+        np.testing.assert_allclose(oracle.subsample(x, s, oracle.SUB_BILINEAR_AA), 0.3, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("mode", [oracle.SUB_NEAREST, oracle.SUB_BILINEAR, oracle.SUB_BOX, oracle.SUB_BILINEAR_AA])
 def test_s1_subsample_is_identity(mode):
     x = _rng(5).standard_normal((6, 9))
     np.testing.assert_array_equal(oracle.subsample(x, 1, mode), x)
@@ -206,7 +228,8 @@ def test_s1_equals_separately_coded_guided_filter(seed, H, W, r, eps):
         np.testing.assert_allclose(q_fgf, oracle.guided_filter(I, p, r, eps), rtol=1e-12, atol=1e-12)
 
 
-@pytest.mark.parametrize("s,mode,CI", [(2, 0, 1), (4, 1, 1), (4, 2, 3), (8, 1, 3), (3, 0, 3), (1, 1, 1)])
+@pytest.mark.parametrize("s,mode,CI", [(2, 0, 1), (4, 1, 1), (4, 2, 3), (8, 1, 3), (3, 0, 3), (1, 1, 1), (4, 3, 1),
+                                       (3, 3, 3)])
 def test_fgf_matches_torch_restatement(s, mode, CI):
     rng = _rng(s * 10 + mode)
     N, C, H, W = 2, 3, 6 * s, 5 * s

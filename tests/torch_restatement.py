@@ -35,6 +35,8 @@ def subsample(x, s, mode):
         y = F.interpolate(x4, size=(h, w), mode="nearest-exact")
     elif mode == 1:
         y = F.interpolate(x4, size=(h, w), mode="bilinear", align_corners=False, antialias=False)
+    elif mode == 3:  # antialiased bilinear (divisible sizes: torch's scale is then exactly s)
+        y = F.interpolate(x4, size=(h, w), mode="bilinear", align_corners=False, antialias=True)
     else:
         y = F.avg_pool2d(x4, kernel_size=s, stride=s, ceil_mode=True)
     return y.reshape(*shp[:-2], h, w)
