@@ -346,6 +346,13 @@ def run_native(args, world, rank, local):
             ms_v = time_steps([(stream, call)], max(20, args.steps // 10), args.warmup, world, 10, use_graph)
             prec[name] = {"ms_per_step": round(ms_v, 5), "mp_per_s": round(world * mp / (ms_v / 1e3), 1)}
         out["precision"] = prec
+        # ---- subsample modes on the same workload (bilinear is the headline)
+        modes = {}
+        for mname in ("nearest", "box", "bilinear_aa"):
+            call = (lambda mname=mname: gf.fast_guided_filter(I, p, R, EPS, S, mname, out=q, stream=stream, ctx=ctx))
+            ms_m = time_steps([(stream, call)], max(20, args.steps // 10), args.warmup, world, 10, use_graph)
+            modes[mname] = {"ms_per_step": round(ms_m, 5), "mp_per_s": round(world * mp / (ms_m / 1e3), 1)}
+        out["subsample_modes"] = modes
 
         # ---- trainable layer: batch 16 x 3 x 1024^2 guide, low-res p 16 x 3 x 256^2, s = 4 box, r' = 2, eps = 1e-2
         Ib = torch.rand((16, 3, 1024, 1024), device=dev)

@@ -14,7 +14,9 @@
  *     (s = 1 gives r' = r), unless gf_opts.r_low >= 0 sets r' directly.  r' <= 128 is supported.
  *   - Nearest subsample takes full-res (floor((j+1/2)s), floor((i+1/2)s)); bilinear subsample and
  *     upsample use half-pixel centres without antialiasing, with coordinates clamped to the image;
- *     box subsample (not in the paper) averages each s x s block clipped to the image.
+ *     box subsample (not in the paper) averages each s x s block clipped to the image; antialiased
+ *     bilinear subsample weights source pixel x by max(0, 1 - |x + 1/2 - (i + 1/2) s| / s) along each
+ *     axis (a triangle filter of half-width s) and renormalises over the taps inside the image.
  *   - I has 1 channel (shared by every channel of p) or C channels (channel c guides channel c).
  *
  * Memory: every image pointer is caller-owned DEVICE memory, dense row-major planes, batch-major
@@ -50,7 +52,12 @@ typedef enum gf_status {
     GF_ENOTFOUND = -7   /* unknown ticket */
 } gf_status;
 
-typedef enum gf_subsample_mode { GF_SUB_NEAREST = 0, GF_SUB_BILINEAR = 1, GF_SUB_BOX = 2 } gf_subsample_mode;
+typedef enum gf_subsample_mode {
+    GF_SUB_NEAREST = 0,
+    GF_SUB_BILINEAR = 1,
+    GF_SUB_BOX = 2,
+    GF_SUB_BILINEAR_AA = 3  /* antialiased bilinear; float input, forward only */
+} gf_subsample_mode;
 
 typedef enum gf_dtype { GF_F32 = 0, GF_F16 = 1, GF_U8 = 2 } gf_dtype;
 
@@ -130,7 +137,8 @@ gf_status gf_lowres_geometry(int H, int W, int s, int r, int r_low, int *h, int 
  * row_end): full-res rows [*row0, *row0 + *rows) of I and p -- the only input rows it reads (rows
  * [*row0 / s, (*row0 + *rows + s - 1) / s) of a low-res p).  r_low < 0 derives r' from r.  Host-only;
  * GF_EINVAL for invalid arguments. */
-gf_status gf_row_band(int H, int W, int s, int r, int r_low, int row_begin, int row_end, int *row0, int *rows);
+gf_status gf_row_band(int H, int W, int s, int r, int r_low, gf_subsample_mode mode, int row_begin, int row_end,
+                      int *row0, int *rows);
 
 /* Number of kernels one gf_filter call with these arguments launches (host-only; -1 for invalid
  * arguments): 4 when s > 1 (subsample, statistics + coefficients, box means of a and b, upsample + output),

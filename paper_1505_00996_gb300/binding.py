@@ -13,11 +13,12 @@ from . import _build
 
 GF_OK, GF_PENDING, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_ETIMEOUT, GF_EBUSY, GF_ECANCELED, GF_ENOTFOUND = \
     0, 1, -1, -2, -3, -4, -5, -6, -7
-GF_SUB_NEAREST, GF_SUB_BILINEAR, GF_SUB_BOX = 0, 1, 2
+GF_SUB_NEAREST, GF_SUB_BILINEAR, GF_SUB_BOX, GF_SUB_BILINEAR_AA = 0, 1, 2, 3
 GF_F32, GF_F16, GF_U8 = 0, 1, 2
 GF_MAX_STAGES = 8
 
-MODES = {"nearest": GF_SUB_NEAREST, "bilinear": GF_SUB_BILINEAR, "box": GF_SUB_BOX}
+MODES = {"nearest": GF_SUB_NEAREST, "bilinear": GF_SUB_BILINEAR, "box": GF_SUB_BOX,
+         "bilinear_aa": GF_SUB_BILINEAR_AA}
 _DTYPES = {torch.float32: GF_F32, torch.float16: GF_F16, torch.uint8: GF_U8}
 _STATUS_NAMES = {0: "GF_OK", 1: "GF_PENDING", -1: "GF_EINVAL", -2: "GF_ENOMEM", -3: "GF_ECUDA",
                  -4: "GF_ETIMEOUT", -5: "GF_EBUSY", -6: "GF_ECANCELED", -7: "GF_ENOTFOUND"}
@@ -106,7 +107,7 @@ def load_library(build_if_missing=True):
         lib.gf_lowres_geometry.restype = i
         lib.gf_workspace_size.argtypes = [i, i, i, i, P(GFOpts), P(sz)]
         lib.gf_workspace_size.restype = i
-        lib.gf_row_band.argtypes = [i, i, i, i, i, i, i, P(i), P(i)]
+        lib.gf_row_band.argtypes = [i, i, i, i, i, i, i, i, P(i), P(i)]
         lib.gf_row_band.restype = i
         lib.gf_filter_kernel_count.argtypes = [i, i, i, i, i, P(GFOpts)]
         lib.gf_filter_kernel_count.restype = i
@@ -161,10 +162,11 @@ def lowres_geometry(H, W, s, r, r_low=-1):
     return h.value, w.value, rp.value
 
 
-def row_band(H, W, s, r, row_begin, row_end, r_low=-1):
+def row_band(H, W, s, r, row_begin, row_end, r_low=-1, mode="bilinear"):
     """(row0, rows): the full-res input rows a call restricted to output rows [row_begin, row_end) reads."""
     a, b = ctypes.c_int(), ctypes.c_int()
-    check(load_library().gf_row_band(int(H), int(W), int(s), int(r), int(r_low), int(row_begin), int(row_end),
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    check(load_library().gf_row_band(int(H), int(W), int(s), int(r), int(r_low), m, int(row_begin), int(row_end),
                                      ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
 

@@ -95,7 +95,7 @@ gf_status resolve(int H, int W, int C, int r, float eps, int s, int mode, const 
     if (s < 1) return fail(GF_EINVAL, "subsampling ratio s must be >= 1");
     if (r < 0) return fail(GF_EINVAL, "radius r must be >= 0");
     if (!(eps >= 0.0f) || !isfinite(eps)) return fail(GF_EINVAL, "eps must be finite and >= 0");
-    if (mode < GF_SUB_NEAREST || mode > GF_SUB_BOX) return fail(GF_EINVAL, "unknown subsample mode");
+    if (mode < GF_SUB_NEAREST || mode > GF_SUB_BILINEAR_AA) return fail(GF_EINVAL, "unknown subsample mode");
     if (o->batch < 1) return fail(GF_EINVAL, "batch must be >= 1");
     const int CI = o->guide_channels == 0 ? 1 : o->guide_channels;
     if (CI != 1 && CI != C) return fail(GF_EINVAL, "guide_channels must be 1 or C");
@@ -116,7 +116,8 @@ gf_status resolve(int H, int W, int C, int r, float eps, int s, int mode, const 
     R.int_stats = (o->dtype_in == GF_U8);
     R.int_scale = 255.0f;
     if (R.int_stats) {
-        if (mode == GF_SUB_BOX && s > 1) return fail(GF_EINVAL, "uint8 input supports nearest or bilinear subsampling");
+        if ((mode == GF_SUB_BOX || mode == GF_SUB_BILINEAR_AA) && s > 1)
+            return fail(GF_EINVAL, "uint8 input supports nearest or bilinear subsampling");
         if (R.p_lowres) return fail(GF_EINVAL, "uint8 input does not support a low-res p");
         const int k = (mode == GF_SUB_BILINEAR && s > 1 && (s % 2 == 0)) ? 4 : 1;
         R.int_scale = 255.0f * (float)k;
@@ -141,7 +142,10 @@ gf_status resolve(int H, int W, int C, int r, float eps, int s, int mode, const 
         auto tap_row = [&](int Y) { return (int)std::floor((2.0 * Y + 1.0 - s) / (2.0 * s)); };
         const int lo = std::max(0, tap_row(o->row_begin));
         const int hi = std::min(R.h - 1, tap_row(o->row_end - 1) + (s > 1 ? 1 : 0));
-        const int c0 = std::max(0, lo - 2 * R.r_low), c1 = std::min(R.h, hi + 2 * R.r_low + 1);
+        // An antialiased subsample also reads s/2 rows into the neighbouring blocks, so the band's edge
+        // low-res rows are themselves inexact: one more row of margin on each side.
+        const int m = 2 * R.r_low + ((mode == GF_SUB_BILINEAR_AA && s > 1) ? 1 : 0);
+        const int c0 = std::max(0, lo - m), c1 = std::min(R.h, hi + m + 1);
         R.row0 = s * c0;
         R.H = std::min(H, s * c1) - R.row0;  // complete s-row blocks, or the image's own last rows
         R.h = c1 - c0;
@@ -236,6 +240,7 @@ gf_status check_backward(const Resolved &R)
     if (R.H > 65535) return fail(GF_EINVAL, "the backward pass needs H <= 65535");
     if (R.N > 65535) return fail(GF_EINVAL, "the backward pass needs batch <= 65535");
     if (R.detail != 0.0f) return fail(GF_EINVAL, "detail_gain is forward only");
+    if (R.mode == GF_SUB_BILINEAR_AA && R.s > 1) return fail(GF_EINVAL, "antialiased subsampling is forward only");
     if (R.Yw1 - R.Yw0 != R.H) return fail(GF_EINVAL, "a row range is forward only");
     return GF_OK;
 }
@@ -482,7 +487,8 @@ gf_status gf_serve_stats_get(gf_ctx *ctx, gf_serve_stats *out)
     return gfk::server_stats(ctx->server, out);
 }
 
-gf_status gf_row_band(int H, int W, int s, int r, int r_low, int row_begin, int row_end, int *row0, int *rows)
+gf_status gf_row_band(int H, int W, int s, int r, int r_low, gf_subsample_mode mode, int row_begin, int row_end,
+                      int *row0, int *rows)
 {
     if (!row0 || !rows) return fail(GF_EINVAL, "row0 and rows must not be NULL");
     gf_opts o;
@@ -491,7 +497,7 @@ gf_status gf_row_band(int H, int W, int s, int r, int r_low, int row_begin, int 
     o.row_begin = row_begin;
     o.row_end = row_end;
     Resolved R;
-    gf_status st = resolve(H, W, 1, r, 0.0f, s, GF_SUB_BILINEAR, &o, R);
+    gf_status st = resolve(H, W, 1, r, 0.0f, s, (int)mode, &o, R);
     if (st != GF_OK) return st;
     *row0 = R.row0;
     *rows = R.H;

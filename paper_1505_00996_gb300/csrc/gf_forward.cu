@@ -101,6 +101,59 @@ __global__ void __launch_bounds__(SUB_NT) k_subsample(SubParams P)
         if (j0 + u < P.h) dst[(size_t)(j0 + u) * P.w] = v[u] * P.scale;
 }
 
+// Antialiased bilinear subsample: along each axis, source pixel x weighs n(x) = 2s - |2x + 1 - (2i + 1)s|
+// (twice s times the triangle weight) for low-res pixel i, over the 2s (even s) or 2s - 1 (odd s) taps with
+// n > 0 that lie in the image, divided by the sum of those n.  Each thread owns one low-res column and
+// SUB_JB consecutive low-res rows; it walks the source rows they cover once, forming the horizontal
+// weighted sum of each row and adding it to the (at most two) low-res rows whose taps include that row.
+template <typename T>
+__global__ void __launch_bounds__(SUB_NT) k_subsample_aa(SubParams P)
+{
+    const int i = blockIdx.x * SUB_NT + threadIdx.x;
+    const int j0 = blockIdx.y * SUB_JB;
+    if (i >= P.w) return;
+    int z = blockIdx.z;
+    const SubJob &J = (z < P.job[0].planes) ? P.job[0] : P.job[1];
+    if (z >= P.job[0].planes) z -= P.job[0].planes;
+    const T *src = (const T *)J.src + (size_t)z * J.sps;
+    float *dst = J.dst + (size_t)z * J.dps + i;
+    const int s = J.s, H = J.H, W = J.W;
+    if (s == 1) {  // a low-res p given by the caller: copied
+        for (int u = 0; u < SUB_JB && j0 + u < P.h; ++u) dst[(size_t)(j0 + u) * P.w] = ldv(src + (size_t)(j0 + u) * W + i);
+        return;
+    }
+    // taps of column i: n(x) > 0 for x in [xa, xb], clipped to the image
+    const int cx = (2 * i + 1) * s;
+    const int xa = max(0, ((cx - 2 * s - 1) >> 1) + 1), xb = min(W - 1, ((cx + 2 * s) >> 1) - 1);
+    int nx = 0;
+    for (int x = xa; x <= xb; ++x) nx += 2 * s - abs(2 * x + 1 - cx);
+    const int jl = min(j0 + SUB_JB, P.h) - 1;  // last low-res row of the block
+    const int ya = max(0, ((2 * j0 - 1) * s - 1 >> 1) + 1), yb = min(H - 1, ((2 * jl + 3) * s >> 1) - 1);
+    float acc[SUB_JB];
+#pragma unroll
+    for (int u = 0; u < SUB_JB; ++u) acc[u] = 0.0f;
+    for (int y = ya; y <= yb; ++y) {
+        const T *row = src + (size_t)y * W;
+        float hs = 0.0f;
+        for (int x = xa; x <= xb; ++x) hs = fmaf((float)(2 * s - abs(2 * x + 1 - cx)), ldv(row + x), hs);
+#pragma unroll
+        for (int u = 0; u < SUB_JB; ++u) {
+            const int ny = 2 * s - abs(2 * y + 1 - (2 * (j0 + u) + 1) * s);
+            if (ny > 0) acc[u] = fmaf((float)ny, hs, acc[u]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < SUB_JB; ++u) {
+        const int j = j0 + u;
+        if (j >= P.h) break;
+        const int cy = (2 * j + 1) * s;
+        const int ja = max(0, ((cy - 2 * s - 1) >> 1) + 1), jb = min(H - 1, ((cy + 2 * s) >> 1) - 1);
+        int ny = 0;
+        for (int y = ja; y <= jb; ++y) ny += 2 * s - abs(2 * y + 1 - cy);
+        dst[(size_t)j * P.w] = acc[u] / ((float)nx * (float)ny) * P.scale;
+    }
+}
+
 // Aligned FP32 fast path of k_subsample for s = 2, 4, 8 with H and W multiples of s (so no sample is
 // clamped): the two (bilinear) or one (nearest) source columns of a low-res pixel lie in one 8- or 16-byte
 // chunk (two for s = 8), read with one vector load per source row.
@@ -1036,7 +1089,8 @@ void launch_sub_t(const SubParams &sp, dim3 grid, cudaStream_t st)
     switch (sp.mode) {
     case GF_SUB_NEAREST: k_subsample<T, GF_SUB_NEAREST><<<grid, SUB_NT, 0, st>>>(sp); break;
     case GF_SUB_BILINEAR: k_subsample<T, GF_SUB_BILINEAR><<<grid, SUB_NT, 0, st>>>(sp); break;
-    default: k_subsample<T, GF_SUB_BOX><<<grid, SUB_NT, 0, st>>>(sp); break;
+    case GF_SUB_BOX: k_subsample<T, GF_SUB_BOX><<<grid, SUB_NT, 0, st>>>(sp); break;
+    default: k_subsample_aa<T><<<grid, SUB_NT, 0, st>>>(sp); break;
     }
 }
 
@@ -1131,7 +1185,8 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 // is a multiple of s: every subsample reads one or two whole vectors per source row and nothing is clamped.
 bool aligned_fp32_subsample(const FwdPlan &P)
 {
-    return (P.dt_in == F32) && !P.p_lowres && (P.mode != GF_SUB_BOX) && (P.s == 2 || P.s == 4 || P.s == 8) &&
+    return (P.dt_in == F32) && !P.p_lowres && (P.mode == GF_SUB_NEAREST || P.mode == GF_SUB_BILINEAR) &&
+           (P.s == 2 || P.s == 4 || P.s == 8) &&
            (P.H % P.s == 0) && (P.W % P.s == 0) && (P.W % 4 == 0) && aligned16(P.I) && aligned16(P.p);
 }
 

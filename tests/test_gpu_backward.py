@@ -19,7 +19,7 @@ import torch_restatement as tr
 
 pytestmark = pytest.mark.gpu
 
-MODE_NAMES = {0: "nearest", 1: "bilinear", 2: "box"}
+MODE_NAMES = {0: "nearest", 1: "bilinear", 2: "box", 3: "bilinear_aa"}
 
 
 @pytest.fixture(scope="module")
@@ -164,3 +164,10 @@ def test_backward_is_deterministic(gf):
     torch.cuda.synchronize()
     for x, y in zip(a, b):
         assert torch.equal(x, y)
+
+
+def test_antialiased_subsample_is_forward_only(gf):
+    I = torch.rand(1, 1, 32, 32, device="cuda")
+    with pytest.raises(gf.GFError) as ei:
+        gf.fast_guided_filter_backward(I, I, I, 4, 1e-2, 4, "bilinear_aa")
+    assert ei.value.status == gf.GF_EINVAL

@@ -15,7 +15,7 @@ from gpu_helpers import TOL_F16, TOL_F32, max_abs, oracle_q, oracle_rows
 
 pytestmark = pytest.mark.gpu
 
-MODE_NAMES = {0: "nearest", 1: "bilinear", 2: "box"}
+MODE_NAMES = {0: "nearest", 1: "bilinear", 2: "box", 3: "bilinear_aa"}
 
 
 @pytest.fixture(scope="module")
@@ -67,6 +67,12 @@ CASES = [
     (1, 1, 1, 3, 4, 0, 1e-2, 4, 1),         # r' = 0, H < s, a single 4-pixel column
     (2, 1, 2, 130, 1028, 64, 1e-3, 8, 2),   # s = 8, r' = 8, box subsample, batch, ragged last band
     (1, 1, 3, 1000, 2052, 20, 1e-2, 4, 0),  # r' = 5, five bands, ragged
+    # antialiased bilinear subsample (triangle filter of half-width s)
+    (1, 1, 3, 300, 704, 16, 1e-3, 4, 3),
+    (1, 1, 1, 61, 43, 6, 1e-3, 3, 3),       # odd s, ragged
+    (2, 3, 3, 96, 128, 8, 1e-2, 4, 3),      # batch, depthwise guide
+    (1, 1, 2, 203, 408, 16, 1e-3, 8, 3),    # s = 8, ragged last band
+    (1, 1, 1, 7, 5, 4, 1e-2, 2, 3),         # tiny: every tap window clipped
 ]
 
 
@@ -140,6 +146,18 @@ def test_config1_12mp_s1_row_bands(gf, scene12mp):
     H = I.shape[-2]
     for Y0, Y1 in ((0, 40), (1480, 1530), (H - 40, H)):
         ref = oracle_rows(I, p, Y0, Y1, 16, 1e-3, 1, 1)
+        err = max_abs(q[..., Y0:Y1, :], ref)
+        assert err <= TOL_F32, "rows %d-%d err %.3g" % (Y0, Y1, err)
+
+
+def test_config1_12mp_antialiased_row_bands(gf, scene12mp):
+    """12 MP, s = 4, antialiased bilinear subsample: bands of rows at the top, middle and bottom against
+    the oracle on cropped rows (the crop margin covers the wider subsample taps)."""
+    I, p = scene12mp
+    q = _run(gf, I, p, 16, 1e-3, 4, 3)
+    H = I.shape[-2]
+    for Y0, Y1 in ((0, 40), (1480, 1530), (H - 40, H)):
+        ref = oracle_rows(I, p, Y0, Y1, 16, 1e-3, 4, 3)
         err = max_abs(q[..., Y0:Y1, :], ref)
         assert err <= TOL_F32, "rows %d-%d err %.3g" % (Y0, Y1, err)
 

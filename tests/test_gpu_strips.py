@@ -49,6 +49,8 @@ CASES = [  # (H, W, C, CI, r, eps, s, mode, dtype, strips, extra)
     (600, 800, 3, 1, 12, 1e-2, 4, "bilinear", torch.uint8, 3, {}),
     (480, 640, 3, 3, 16, 1e-2, 4, "bilinear", torch.float32, 2, {"detail_gain": 5.0}),
     (512, 512, 3, 3, 0, 1e-2, 4, "box", torch.float32, 3, {"r_low": 2, "p_lowres": True}),
+    (700, 900, 3, 1, 16, 1e-3, 4, "bilinear_aa", torch.float32, 3, {}),
+    (701, 640, 1, 1, 24, 1e-3, 8, "bilinear_aa", torch.float16, 2, {}),
 ]
 
 
@@ -81,7 +83,8 @@ def test_strips_equal_whole_image(gf, case):
     # the rows around every strip edge against the oracle (on the values actually stored)
     Ih = I.cpu().numpy().astype(np.float64) / (255.0 if dtype == torch.uint8 else 1.0)
     ph = p.cpu().numpy().astype(np.float64) / (255.0 if dtype == torch.uint8 else 1.0)
-    modes = {"nearest": oracle.SUB_NEAREST, "bilinear": oracle.SUB_BILINEAR, "box": oracle.SUB_BOX}
+    modes = {"nearest": oracle.SUB_NEAREST, "bilinear": oracle.SUB_BILINEAR, "box": oracle.SUB_BOX,
+             "bilinear_aa": oracle.SUB_BILINEAR_AA}
     if extra.get("p_lowres"):
         ref = oracle.fast_guided_filter(Ih, ph, r, eps, s, modes[mode], r_low=extra["r_low"], p_lowres=True)
     elif H * W <= 1_000_000:

@@ -21,6 +21,9 @@ CASES = [  # (H, W, s, r, mode, row ranges)
     (99, 20, 3, 9, oracle.SUB_BILINEAR, [(0, 33), (33, 66), (66, 99)]),
     (256, 16, 8, 24, oracle.SUB_BILINEAR, [(0, 100), (100, 180), (180, 256), (127, 129)]),
     (45, 30, 4, 60, oracle.SUB_BILINEAR, [(10, 20)]),  # r' = 15 windows span the whole image
+    (120, 28, 4, 8, oracle.SUB_BILINEAR_AA, [(0, 4), (37, 61), (60, 120), (119, 120)]),
+    (99, 20, 3, 9, oracle.SUB_BILINEAR_AA, [(0, 33), (33, 66), (66, 99)]),
+    (256, 16, 8, 24, oracle.SUB_BILINEAR_AA, [(100, 180), (127, 129)]),
 ]
 
 
@@ -32,7 +35,7 @@ def test_band_reproduces_whole_image_rows(H, W, s, r, mode, ranges):
     rl = oracle.lowres_radius(r, s)
     whole = oracle.fast_guided_filter(I, p, r, 1e-2, s, mode)
     for rb, re in ranges:
-        row0, rows = binding.row_band(H, W, s, r, rb, re)
+        row0, rows = binding.row_band(H, W, s, r, rb, re, mode=mode)
         assert 0 <= row0 <= rb and re <= row0 + rows <= H
         assert row0 % s == 0 and ((row0 + rows) % s == 0 or row0 + rows == H)  # whole s-row blocks
         band = oracle.fast_guided_filter(I[..., row0:row0 + rows, :], p[..., row0:row0 + rows, :], r, 1e-2, s, mode,
