@@ -154,6 +154,97 @@ __global__ void __launch_bounds__(SUB_NT) k_subsample_aa(SubParams P)
     }
 }
 
+// Aligned FP32 fast path of the box and antialiased subsamples for s = 2, 4, 8 with H and W multiples of s.
+// Thread = one low-res column i, SUB_JB low-res rows.  Each source row is read once per thread as vectors:
+// the s-column chunk of block i (box), or the three chunks i-1, i, i+1 (antialiased: taps S i - S/2 + k,
+// k = 0 .. 2S-1, weight 2S - |2k + 1 - 2S|; chunks outside the image are skipped and their weights left out
+// of the normalisation -- S^2/4 on each side).  Neighbouring threads share chunks through L1.
+template <int S>
+__device__ __forceinline__ void ld_chunk(const float *p, float (&v)[S])
+{
+    if constexpr (S == 2) {
+        const float2 t = __ldcs(reinterpret_cast<const float2 *>(p));
+        v[0] = t.x; v[1] = t.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < S / 4; ++q) {
+            const float4 t = __ldcs(reinterpret_cast<const float4 *>(p) + q);
+            v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+        }
+    }
+}
+
+template <int MODE, int S>
+__global__ void __launch_bounds__(SUB_NT) k_subsample_wide(SubParams P)
+{
+    const int i = blockIdx.x * SUB_NT + threadIdx.x;
+    const int j0 = blockIdx.y * SUB_JB;
+    if (i >= P.w) return;
+    int z = blockIdx.z;
+    const SubJob &J = (z < P.job[0].planes) ? P.job[0] : P.job[1];
+    if (z >= P.job[0].planes) z -= P.job[0].planes;
+    const float *src = (const float *)J.src + (size_t)z * J.sps;
+    float *dst = J.dst + (size_t)z * J.dps + i;
+    const int H = J.H, W = J.W;
+    if (J.s == 1) {  // a low-res p given by the caller: copied
+        for (int u = 0; u < SUB_JB && j0 + u < P.h; ++u) dst[(size_t)(j0 + u) * P.w] = src[(size_t)(j0 + u) * W + i];
+        return;
+    }
+    float acc[SUB_JB];
+#pragma unroll
+    for (int u = 0; u < SUB_JB; ++u) acc[u] = 0.0f;
+    if constexpr (MODE == GF_SUB_BOX) {
+#pragma unroll
+        for (int u = 0; u < SUB_JB; ++u) {
+            if (j0 + u >= P.h) break;
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+                float v[S];
+                ld_chunk<S>(src + (size_t)(S * (j0 + u) + k) * W + S * i, v);
+#pragma unroll
+                for (int x = 0; x < S; ++x) acc[u] += v[x];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < SUB_JB; ++u)
+            if (j0 + u < P.h) dst[(size_t)(j0 + u) * P.w] = acc[u] * (1.0f / (float)(S * S));
+    } else {  // antialiased bilinear
+        const bool has_l = i > 0, has_r = S * (i + 1) < W;
+        const int jl = min(j0 + SUB_JB, P.h) - 1;
+        const int ya = max(0, S * j0 - S / 2), yb = min(H - 1, S * jl + 3 * S / 2 - 1);
+        for (int y = ya; y <= yb; ++y) {
+            const float *row = src + (size_t)y * W + S * i;
+            float l[S], m[S], r[S];
+            ld_chunk<S>(row, m);
+#pragma unroll
+            for (int x = 0; x < S; ++x) { l[x] = 0.0f; r[x] = 0.0f; }
+            if (has_l) ld_chunk<S>(row - S, l);
+            if (has_r) ld_chunk<S>(row + S, r);
+            // taps k = 0 .. 2S-1 are columns S i - S/2 + k: the last S/2 of chunk l, all of m, the first S/2 of r
+            float hs = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 2 * S; ++k) {
+                const int c = k - S / 2;  // column offset from S i
+                const float v = (c < 0) ? l[S + c] : (c < S ? m[c] : r[c - S]);
+                hs = fmaf((float)(2 * S - abs(2 * k + 1 - 2 * S)), v, hs);
+            }
+#pragma unroll
+            for (int u = 0; u < SUB_JB; ++u) {
+                const int t = y - (S * (j0 + u) - S / 2);  // tap index of row y for low-res row j0 + u
+                if (t >= 0 && t < 2 * S) acc[u] = fmaf((float)(2 * S - abs(2 * t + 1 - 2 * S)), hs, acc[u]);
+            }
+        }
+        const float nx = (float)(2 * S * S - (has_l ? 0 : S * S / 4) - (has_r ? 0 : S * S / 4));
+#pragma unroll
+        for (int u = 0; u < SUB_JB; ++u) {
+            const int j = j0 + u;
+            if (j >= P.h) break;
+            const float ny = (float)(2 * S * S - (j > 0 ? 0 : S * S / 4) - (S * (j + 1) < H ? 0 : S * S / 4));
+            dst[(size_t)j * P.w] = acc[u] / (nx * ny);
+        }
+    }
+}
+
 // Aligned FP32 fast path of k_subsample for s = 2, 4, 8 with H and W multiples of s (so no sample is
 // clamped): the two (bilinear) or one (nearest) source columns of a low-res pixel lie in one 8- or 16-byte
 // chunk (two for s = 8), read with one vector load per source row.
@@ -1183,6 +1274,15 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 // FP32 input at s = 2, 4, 8 (bilinear or nearest, full-res p) whose rows are 16-byte aligned and whose size
 // is a multiple of s: every subsample reads one or two whole vectors per source row and nothing is clamped.
+// The box and antialiased modes' fast path: FP32, s = 2, 4, 8, H and W multiples of s, aligned planes.
+// (The whole-plane stride is H * W of the whole image, a multiple of 4 floats, so every plane is aligned.)
+bool aligned_fp32_wide_subsample(const FwdPlan &P)
+{
+    return (P.dt_in == F32) && (P.mode == GF_SUB_BOX || P.mode == GF_SUB_BILINEAR_AA) &&
+           (P.s == 2 || P.s == 4 || P.s == 8) && (P.H % P.s == 0) && (P.W % P.s == 0) && (P.W % 4 == 0) &&
+           aligned16(P.I) && (P.p_lowres || aligned16(P.p));  // a low-res p is only copied
+}
+
 bool aligned_fp32_subsample(const FwdPlan &P)
 {
     return (P.dt_in == F32) && !P.p_lowres && (P.mode == GF_SUB_NEAREST || P.mode == GF_SUB_BILINEAR) &&
@@ -1233,6 +1333,17 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
                 if (P.s == 2) GF_SV(GF_SUB_NEAREST, 2); else if (P.s == 4) GF_SV(GF_SUB_NEAREST, 4); else GF_SV(GF_SUB_NEAREST, 8);
             }
 #undef GF_SV
+        } else if (aligned_fp32_wide_subsample(P)) {
+            dim3 grid((P.w + SUB_NT - 1) / SUB_NT, (P.h + SUB_JB - 1) / SUB_JB, nz);
+#define GF_SW(m, ss) k_subsample_wide<m, ss><<<grid, SUB_NT, 0, st>>>(sp)
+            if (P.mode == GF_SUB_BOX) {
+                if (P.s == 2) GF_SW(GF_SUB_BOX, 2); else if (P.s == 4) GF_SW(GF_SUB_BOX, 4); else GF_SW(GF_SUB_BOX, 8);
+            } else {
+                if (P.s == 2) GF_SW(GF_SUB_BILINEAR_AA, 2);
+                else if (P.s == 4) GF_SW(GF_SUB_BILINEAR_AA, 4);
+                else GF_SW(GF_SUB_BILINEAR_AA, 8);
+            }
+#undef GF_SW
         } else {
             dim3 grid((P.w + SUB_NT - 1) / SUB_NT, (P.h + SUB_JB - 1) / SUB_JB, nz);
             if (P.dt_in == F32) launch_sub_t<float>(sp, grid, st);

@@ -73,6 +73,12 @@ CASES = [
     (2, 3, 3, 96, 128, 8, 1e-2, 4, 3),      # batch, depthwise guide
     (1, 1, 2, 203, 408, 16, 1e-3, 8, 3),    # s = 8, ragged last band
     (1, 1, 1, 7, 5, 4, 1e-2, 2, 3),         # tiny: every tap window clipped
+    # vectorised FP32 box / antialiased subsample (H, W multiples of s)
+    (1, 1, 2, 128, 256, 8, 1e-2, 2, 2),
+    (2, 1, 3, 160, 320, 16, 1e-3, 8, 2),
+    (1, 1, 1, 64, 64, 4, 1e-2, 2, 3),
+    (1, 1, 2, 256, 512, 32, 1e-3, 8, 3),
+    (1, 3, 3, 8, 8, 4, 1e-2, 4, 3),         # one low-res column and two rows: both borders in each
 ]
 
 
