@@ -34,6 +34,11 @@
  *   R8 channels: the guide has CI = 1 channel shared by all C channels of p, or CI = C channels with
  *      channel c guiding channel c; each channel of p is filtered independently.
  *   R9 eps is added to var(I) as given (no rescaling); R10 q is not clamped.
+ *   R12 colour guide (the guided filter's colour form, which the paper cites but does not restate): with a
+ *      3-channel guide the model in each window is q = a^T I + b with a 3-vector a, a = (Sigma + eps U)^-1
+ *      cov_Ip and b = mean_p - a^T mean_I, Sigma being the 3 x 3 covariance of the guide in the window and
+ *      cov_Ip the covariance of each guide channel with p; Algorithm 2's subsample and upsample steps wrap it
+ *      unchanged, and q = mean_a^T I + mean_b on the full-resolution guide.
  *   R11 antialiased bilinear subsample (a fourth mode; the paper names only "bilinear", and this is the
  *      form a shrinking resize takes when it low-passes first): a triangle filter of half-width s centred
  *      on the low-res pixel centre, so source pixel x has weight max(0, 1 - |x + 1/2 - (i + 1/2) s| / s)
@@ -559,4 +564,101 @@ int gfo_detail_enhance(const double *I, const double *q, int N, int CI, int C, i
             for (size_t i = 0; i < HW; ++i) oc[i] = qc[i] + k * (Ic[i] - qc[i]);
         }
     return 0;
+}
+
+/* x = M^-1 v for a 3 x 3 matrix M by Cramer's rule.  Returns -1 if M is singular. */
+static int solve3(const double M[3][3], const double v[3], double x[3])
+{
+    double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                 M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    if (det == 0.0) return -1;
+    for (int k = 0; k < 3; ++k) {
+        double A[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) A[i][j] = (j == k) ? v[i] : M[i][j];
+        x[k] = (A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0])) / det;
+    }
+    return 0;
+}
+
+/*
+ * Colour-guided fast guided filter (R12) for a batch.
+ *   I: N x 3 x H x W colour guide;  p: N x C x H x W, or N x C x h x w when p_lowres != 0;  q: N x C x H x W.
+ *   Optional: a_out N x C x 3 x h x w (the 3-vector a of every window), b_out N x C x h x w.
+ * Returns 0, -1 on invalid arguments, -2 if some Sigma + eps U is singular.
+ */
+int gfo_color_guided_filter(const double *I, const double *p, int N, int C, int H, int W, int r_low, double eps,
+                            int s, int mode, int p_lowres, double *q, double *a_out, double *b_out)
+{
+    if (N < 1 || C < 1 || H < 1 || W < 1 || s < 1 || r_low < 0 || !(eps >= 0.0)) return -1;
+    if (mode < GFO_SUB_NEAREST || mode > GFO_SUB_BILINEAR_AA) return -1;
+    int h, w;
+    gfo_lowres_shape(H, W, s, &h, &w);
+    size_t n = (size_t)h * w, NF = (size_t)H * W;
+    static const int PK[6] = {0, 0, 0, 1, 1, 2}, PL[6] = {0, 1, 2, 1, 2, 2}; /* guide products rr rg rb gg gb bb */
+    double *buf = malloc(sizeof(double) * (n * 27 + NF * 4));
+    double *Il = buf, *mean_I = Il + 3 * n, *corr_I = mean_I + 3 * n, *pl = corr_I + 6 * n, *mean_p = pl + n;
+    double *corr_Ip = mean_p + n, *a = corr_Ip + 3 * n, *b = a + 3 * n, *mean_a = b + n, *mean_b = mean_a + 3 * n;
+    double *tmp = mean_b + n, *up = buf + n * 27;
+    int rc = 0;
+    for (int bn = 0; bn < N && rc == 0; ++bn) {
+        const double *Ig = I + (size_t)bn * 3 * NF;
+        /* step 1 for the guide: I' = f_subsample(I, s), channel by channel */
+        for (int k = 0; k < 3; ++k) gfo_subsample(Ig + k * NF, H, W, s, mode, Il + k * n);
+        /* step 2 for the guide: box means of I'_k and of every product I'_k I'_l */
+        for (int k = 0; k < 3; ++k) gfo_box_mean(Il + k * n, h, w, r_low, mean_I + k * n);
+        for (int m = 0; m < 6; ++m) {
+            for (size_t t = 0; t < n; ++t) tmp[t] = Il[PK[m] * n + t] * Il[PL[m] * n + t];
+            gfo_box_mean(tmp, h, w, r_low, corr_I + m * n);
+        }
+        for (int c = 0; c < C && rc == 0; ++c) {
+            /* steps 1-2 for p: p' and the box means of p' and of I'_k p' */
+            if (p_lowres)
+                memcpy(pl, p + ((size_t)bn * C + c) * n, sizeof(double) * n);
+            else
+                gfo_subsample(p + ((size_t)bn * C + c) * NF, H, W, s, mode, pl);
+            gfo_box_mean(pl, h, w, r_low, mean_p);
+            for (int k = 0; k < 3; ++k) {
+                for (size_t t = 0; t < n; ++t) tmp[t] = Il[k * n + t] * pl[t];
+                gfo_box_mean(tmp, h, w, r_low, corr_Ip + k * n);
+            }
+            /* steps 3-4: Sigma + eps U, cov_Ip, a = (Sigma + eps U)^-1 cov_Ip, b = mean_p - a^T mean_I */
+            for (size_t t = 0; t < n; ++t) {
+                double M[3][3], v[3], x[3];
+                for (int m = 0; m < 6; ++m) {
+                    double e = corr_I[m * n + t] - mean_I[PK[m] * n + t] * mean_I[PL[m] * n + t];
+                    M[PK[m]][PL[m]] = e;
+                    M[PL[m]][PK[m]] = e;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    M[k][k] += eps;
+                    v[k] = corr_Ip[k * n + t] - mean_I[k * n + t] * mean_p[t];
+                }
+                if (solve3(M, v, x) != 0) { rc = -2; break; }
+                double bb = mean_p[t];
+                for (int k = 0; k < 3; ++k) {
+                    a[k * n + t] = x[k];
+                    bb -= x[k] * mean_I[k * n + t];
+                }
+                b[t] = bb;
+            }
+            if (rc) break;
+            /* step 5: box means of a (each component) and b */
+            for (int k = 0; k < 3; ++k) gfo_box_mean(a + k * n, h, w, r_low, mean_a + k * n);
+            gfo_box_mean(b, h, w, r_low, mean_b);
+            /* steps 6-7: upsample, q = mean_a^T I + mean_b on the full-resolution guide */
+            double *qc = q + ((size_t)bn * C + c) * NF;
+            gfo_upsample(mean_b, h, w, s, H, W, up);
+            memcpy(qc, up, sizeof(double) * NF);
+            for (int k = 0; k < 3; ++k) {
+                gfo_upsample(mean_a + k * n, h, w, s, H, W, up);
+                for (size_t t = 0; t < NF; ++t) qc[t] += up[t] * Ig[k * NF + t];
+            }
+            if (a_out) memcpy(a_out + ((size_t)bn * C + c) * 3 * n, a, sizeof(double) * 3 * n);
+            if (b_out) memcpy(b_out + ((size_t)bn * C + c) * n, b, sizeof(double) * n);
+        }
+    }
+    free(buf);
+    return rc;
 }

@@ -51,6 +51,8 @@ def _load():
             lib.gfo_guided_filter.restype = i
             lib.gfo_fast_guided_filter_backward.argtypes = [D, D, D, i, i, i, i, i, i, d, i, i, i, i, D, D, D]
             lib.gfo_fast_guided_filter_backward.restype = i
+            lib.gfo_color_guided_filter.argtypes = [D, D, i, i, i, i, i, d, i, i, i, D, D, D]
+            lib.gfo_color_guided_filter.restype = i
             lib.gfo_detail_enhance.argtypes = [D, D, i, i, i, i, i, d, D]
             lib.gfo_detail_enhance.restype = i
             _lib = lib
@@ -162,6 +164,31 @@ def fast_guided_filter(I, p, r, eps, s, mode=SUB_BILINEAR, r_low=None, p_lowres=
         if inter:
             inter = {k: v[0] for k, v in inter.items()}
     return (q, inter) if intermediates else q
+
+
+def color_guided_filter(I, p, r, eps, s, mode=SUB_BILINEAR, r_low=None, p_lowres=False, intermediates=False):
+    """Colour-guided fast guided filter (R12) in FP64.  I: (3, H, W) or (N, 3, H, W); p: (C, H, W) or
+    (N, C, H, W) (at h x w when ``p_lowres``).  Returns q shaped like p at full resolution, plus
+    {"a": N x C x 3 x h x w, "b": N x C x h x w} when ``intermediates``."""
+    I4, _ = _as_nchw(I)
+    p4, prank = _as_nchw(p)
+    N, CI, H, W = I4.shape
+    C = p4.shape[1]
+    if CI != 3 or p4.shape[0] != N:
+        raise ValueError("the colour guide has 3 channels and the batch sizes must match")
+    h, w = lowres_shape(H, W, s)
+    rl = lowres_radius(r, s) if r_low is None else int(r_low)
+    q = np.empty((N, C, H, W), np.float64)
+    a = np.empty((N, C, 3, h, w), np.float64) if intermediates else None
+    b = np.empty((N, C, h, w), np.float64) if intermediates else None
+    rc = _load().gfo_color_guided_filter(_ptr(I4), _ptr(p4), N, C, H, W, rl, float(eps), int(s), int(mode),
+                                         int(bool(p_lowres)), _ptr(q), _ptr(a) if intermediates else None,
+                                         _ptr(b) if intermediates else None)
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments" if rc == -1 else "singular Sigma + eps U")
+    if prank == 3:
+        q = q[0]
+    return (q, {"a": a, "b": b}) if intermediates else q
 
 
 def detail_enhance(I, q, k):

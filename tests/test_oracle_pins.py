@@ -332,6 +332,80 @@ def test_depthwise_guide_channels():
 
 
 # ---------------------------------------------------------------------------------------------------------
+# Colour guide (R12): the guided filter's colour form inside Algorithm 2
+# ---------------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("s,mode", [(1, 1), (2, 0), (4, 1), (4, 2), (3, 3)])
+def test_color_guide_of_replicated_gray_equals_gray_guide_with_eps_over_3(s, mode):
+    # I_r = I_g = I_b = G makes Sigma = var 11^T and cov_Ip = cov 1, so (Sigma + eps U)^-1 cov_Ip =
+    # cov / (3 var + eps) 1 and a^T I = cov / (var + eps / 3) G: the gray filter with eps / 3
+    rng = _rng(20 + s)
+    G = rng.uniform(0, 1, (2, 1, 6 * s, 5 * s))
+    p = rng.uniform(0, 1, (2, 3, 6 * s, 5 * s))
+    q_col = oracle.color_guided_filter(np.repeat(G, 3, axis=1), p, 0, 3e-2, s, mode, r_low=2)
+    q_gray = oracle.fast_guided_filter(G, p, 0, 1e-2, s, mode, r_low=2)
+    np.testing.assert_allclose(q_col, q_gray, rtol=0, atol=1e-12)
+
+
+def _ridge_coefficients_color(I, p, r, eps):
+    """For every clipped window, minimise sum_i (a^T I_i + b - p_i)^2 + n eps |a|^2 (n = window size) with a
+    least-squares solver."""
+    _, h, w = I.shape
+    a = np.empty((3, h, w))
+    b = np.empty((h, w))
+    for j in range(h):
+        for i in range(w):
+            sl = (slice(None), slice(max(0, j - r), j + r + 1), slice(max(0, i - r), i + r + 1))
+            Iw = I[sl].reshape(3, -1).T
+            pw = p[sl[1:]].ravel()
+            n = pw.size
+            A = np.concatenate([np.concatenate([Iw, np.ones((n, 1))], 1),
+                                np.concatenate([np.sqrt(n * eps) * np.eye(3), np.zeros((3, 1))], 1)])
+            sol = np.linalg.lstsq(A, np.concatenate([pw, np.zeros(3)]), rcond=None)[0]
+            a[:, j, i], b[j, i] = sol[:3], sol[3]
+    return a, b
+
+
+@pytest.mark.parametrize("seed,r,eps", [(0, 1, 0.01), (1, 2, 1e-3), (2, 4, 0.1)])
+def test_color_coefficients_solve_ridge_regression(seed, r, eps):
+    rng = _rng(30 + seed)
+    I = rng.uniform(0, 1, (3, 9, 11))
+    p = rng.uniform(0, 1, (9, 11))
+    _, inter = oracle.color_guided_filter(I, p[None], r, eps, 1, oracle.SUB_BILINEAR, intermediates=True)
+    a_ref, b_ref = _ridge_coefficients_color(I, p, r, eps)
+    np.testing.assert_allclose(inter["a"][0, 0], a_ref, rtol=1e-8, atol=1e-9)
+    np.testing.assert_allclose(inter["b"][0, 0], b_ref, rtol=1e-8, atol=1e-9)
+
+
+@pytest.mark.parametrize("s,mode", [(1, 1), (2, 1), (4, 0), (4, 2), (4, 3), (8, 1)])
+def test_color_guide_matches_torch_restatement(s, mode):
+    rng = _rng(40 + s + mode)
+    N, C, H, W = 2, 2, 5 * s, 7 * s
+    I = rng.uniform(0, 1, (N, 3, H, W))
+    p = rng.uniform(0, 1, (N, C, H, W))
+    q = oracle.color_guided_filter(I, p, 0, 1e-2, s, mode, r_low=2)
+    ref = tr.color_guided_filter(torch.from_numpy(I), torch.from_numpy(p), 2, 1e-2, s, mode).numpy()
+    np.testing.assert_allclose(q, ref, rtol=1e-10, atol=1e-11)
+
+
+def test_color_guide_closed_forms_and_invariances():
+    rng = _rng(50)
+    I = rng.uniform(0, 1, (1, 3, 24, 32))
+    f = lambda I_, p_, e=1e-2: oracle.color_guided_filter(I_, p_, 8, e, 4, oracle.SUB_BILINEAR)
+    # constant p gives back the constant exactly in exact arithmetic (a = 0, b = c)
+    np.testing.assert_allclose(f(I, np.full((1, 1, 24, 32), 0.625)), 0.625, rtol=0, atol=1e-13)
+    # p = alpha^T I + beta with eps = 0: a = alpha, b = beta everywhere, so q = p
+    alpha, beta = np.array([0.5, -0.25, 0.75]), 0.125
+    p_lin = (alpha[None, :, None, None] * I).sum(1, keepdims=True) + beta
+    np.testing.assert_allclose(oracle.color_guided_filter(I, p_lin, 4, 0.0, 1, oracle.SUB_BILINEAR), p_lin,
+                               rtol=0, atol=1e-9)
+    # linear in p; a shift of every guide channel changes nothing
+    p1, p2 = rng.uniform(0, 1, (2, 1, 2, 24, 32))
+    np.testing.assert_allclose(f(I, 2.0 * p1 - 3.0 * p2), 2.0 * f(I, p1) - 3.0 * f(I, p2), atol=1e-12)
+    np.testing.assert_allclose(f(I + np.array([0.1, -0.2, 0.3])[None, :, None, None], p1), f(I, p1), atol=1e-12)
+
+
+# ---------------------------------------------------------------------------------------------------------
 # Detail enhancement (the application of Fig. 2: base layer q plus k times the detail layer I - q)
 # ---------------------------------------------------------------------------------------------------------
 

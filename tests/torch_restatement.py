@@ -69,3 +69,23 @@ def fast_guided_filter(I, p, r_low, eps, s, mode, p_lowres=False):
     mean_a = upsample(box_mean(a, r_low), s, H, W)
     mean_b = upsample(box_mean(b, r_low), s, H, W)
     return mean_a * Ig + mean_b
+
+
+def color_guided_filter(I, p, r_low, eps, s, mode, p_lowres=False):
+    """Colour-guided form: I (N, 3, H, W), p (N, C, H, W) or (N, C, h, w).  The 3 x 3 systems are solved
+    with ``torch.linalg.solve``.  Returns q: (N, C, H, W)."""
+    N, _, H, W = I.shape
+    Il = subsample(I, s, mode)
+    pl = p if p_lowres else subsample(p, s, mode)
+    h, w = Il.shape[-2:]
+    mean_I = box_mean(Il, r_low)                                             # (N, 3, h, w)
+    sigma = box_mean(Il[:, :, None] * Il[:, None], r_low) - mean_I[:, :, None] * mean_I[:, None]
+    mean_p = box_mean(pl, r_low)                                             # (N, C, h, w)
+    cov = box_mean(Il[:, None] * pl[:, :, None], r_low) - mean_I[:, None] * mean_p[:, :, None]
+    M = sigma.permute(0, 3, 4, 1, 2)[:, None] + eps * torch.eye(3, dtype=I.dtype)  # (N, 1, h, w, 3, 3)
+    a = torch.linalg.solve(M.expand(N, pl.shape[1], h, w, 3, 3), cov.permute(0, 1, 3, 4, 2))
+    a = a.permute(0, 1, 4, 2, 3)                                             # (N, C, 3, h, w)
+    b = mean_p - (a * mean_I[:, None]).sum(2)
+    mean_a = upsample(box_mean(a, r_low), s, H, W)
+    mean_b = upsample(box_mean(b, r_low), s, H, W)
+    return (mean_a * I[:, None]).sum(2) + mean_b
