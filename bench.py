@@ -387,7 +387,8 @@ def run_applications(dev, stream, ctx, world, steps, warmup, use_graph):
     flash / no-flash denoising (r = 8, eps = 0.02^2) and guided feathering (r = 60, eps = 0.001^2) with the
     parameters of the paper's figures, s = 4 bilinear, on 12 MP synthetic stand-ins: a 3-channel colour
     scene as its own (depthwise) guide, the clean scene guiding a noisy copy, and a gray scene guiding a
-    blocky binary mask.  One filter call per step; output MP/s."""
+    blocky binary mask; feathering and smoothing also with the colour scene as a colour guide (3 x 3
+    covariance).  One filter call per step; output MP/s."""
     import paper_1505_00996_gb300 as gf
     import synth
     Hh, Ww = H, W
@@ -396,16 +397,20 @@ def run_applications(dev, stream, ctx, world, steps, warmup, use_graph):
              ).clamp_(0.0, 1.0)
     gray = torch.from_numpy(synth.make_scene(Hh, Ww, seed=9)).to(dev)[None]
     mask = torch.from_numpy(synth.feather_mask(Hh, Ww, seed=10)).to(dev)[None]
-    apps = {"smoothing": (col, col, 4, 0.2 ** 2, 0.0), "detail_x5": (col, col, 16, 0.1 ** 2, 5.0),
-            "flash_no_flash": (col, noisy, 8, 0.02 ** 2, 0.0), "feathering": (gray, mask, 60, 0.001 ** 2, 0.0)}
+    apps = {"smoothing": (col, col, 4, 0.2 ** 2, 0.0, False), "detail_x5": (col, col, 16, 0.1 ** 2, 5.0, False),
+            "flash_no_flash": (col, noisy, 8, 0.02 ** 2, 0.0, False),
+            "feathering": (gray, mask, 60, 0.001 ** 2, 0.0, False),
+            "feathering_color_guide": (col, mask, 60, 0.001 ** 2, 0.0, True),
+            "smoothing_color_guide": (col, col, 4, 0.2 ** 2, 0.0, True)}
     res = {}
-    for name, (Ia, pa, r, eps, gain) in apps.items():
+    for name, (Ia, pa, r, eps, gain, colg) in apps.items():
         qa = torch.empty_like(pa)
-        call = (lambda Ia=Ia, pa=pa, qa=qa, r=r, eps=eps, gain=gain:
-                gf.fast_guided_filter(Ia, pa, r, eps, 4, "bilinear", out=qa, stream=stream, ctx=ctx, detail_gain=gain))
+        call = (lambda Ia=Ia, pa=pa, qa=qa, r=r, eps=eps, gain=gain, colg=colg:
+                gf.fast_guided_filter(Ia, pa, r, eps, 4, "bilinear", out=qa, stream=stream, ctx=ctx, detail_gain=gain,
+                                      color_guide=colg))
         ms_a = time_steps([(stream, call)], steps, warmup, world, 10, use_graph)
-        res[name] = {"C": int(pa.shape[0]), "guide_channels": int(Ia.shape[0]), "r": r, "eps": eps,
-                     "detail_gain": gain, "ms_per_step": round(ms_a, 5),
+        res[name] = {"C": int(pa.shape[0]), "guide_channels": int(Ia.shape[0]), "color_guide": colg, "r": r,
+                     "eps": eps, "detail_gain": gain, "ms_per_step": round(ms_a, 5),
                      "mp_per_s": round(world * Hh * Ww / 1e6 / (ms_a / 1e3), 1)}
     return res
 

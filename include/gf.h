@@ -98,6 +98,11 @@ typedef struct gf_ctx gf_ctx;
  *                   split across GPUs: each filters its own rows from the (replicated) input, and no data
  *                   is exchanged.  Not combined with a_out, b_out, mean_a_out, mean_b_out or stats_out;
  *                   forward only.
+ *   color_guide     nonzero: I has guide_channels = 3 channels used jointly as a colour guide for every
+ *                   channel of p (the guided filter's colour form, which the paper cites): per window
+ *                   a = (Sigma + eps U)^-1 cov_Ip with Sigma the 3 x 3 covariance of I', b = mean_p - a^T
+ *                   mean_I, and q = mean_a^T I + mean_b.  FP32 or FP16 storage; forward only; no low-res
+ *                   intermediate outputs; detail_gain needs C = 3 (channel c's detail is I_c - q_c).
  */
 typedef struct gf_opts {
     int batch;
@@ -117,6 +122,7 @@ typedef struct gf_opts {
     float detail_gain;
     int row_begin;
     int row_end;
+    int color_guide;
 } gf_opts;
 
 /* Default options: batch 1, gray guide, derived r', full-res p, FP32 in and out, nothing optional. */
@@ -142,7 +148,8 @@ gf_status gf_row_band(int H, int W, int s, int r, int r_low, gf_subsample_mode m
 
 /* Number of kernels one gf_filter call with these arguments launches (host-only; -1 for invalid
  * arguments): 4 when s > 1 (subsample, statistics + coefficients, box means of a and b, upsample + output),
- * 3 when s = 1 (no subsample). */
+ * 3 when s = 1 (no subsample); 6 with a colour guide (subsample, products, box means, coefficients, box
+ * means, upsample + output). */
 int gf_filter_kernel_count(int H, int W, int C, int s, gf_subsample_mode mode, const gf_opts *opts);
 
 /* Bytes of device scratch one gf_filter call with these arguments needs (host-only). */

@@ -49,6 +49,7 @@ class GFOpts(ctypes.Structure):
         ("detail_gain", ctypes.c_float),
         ("row_begin", ctypes.c_int),
         ("row_end", ctypes.c_int),
+        ("color_guide", ctypes.c_int),
     ]
 
 
@@ -244,7 +245,8 @@ def _stream_handle(stream):
 
 def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowres=False, out_dtype=None,
                        out=None, a_out=None, b_out=None, mean_a_out=None, mean_b_out=None, stats_out=None,
-                       workspace=None, kernel_events=None, stream=None, ctx=None, detail_gain=0.0, rows=None):
+                       workspace=None, kernel_events=None, stream=None, ctx=None, detail_gain=0.0, rows=None,
+                       color_guide=False):
     """Fast guided filter (Algorithm 2; Algorithm 1 at s = 1) on CUDA tensors, via ``gf_filter``.
 
     I: (H, W), (CI, H, W) or (N, CI, H, W); p: the same rank with C channels (at low resolution when
@@ -253,6 +255,7 @@ def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowr
     ``detail_gain`` k != 0 returns q + k (I - q) instead (detail enhancement when p is I).
     ``rows=(row_begin, row_end)`` computes only those output rows of q (needs ``out``, the whole q, whose
     other rows are left as they are): one strip of an image split across devices or streams.
+    ``color_guide=True``: I has 3 channels used jointly as a colour guide for every channel of p.
     """
     if not (I.is_cuda and p.is_cuda):
         raise ValueError("I and p must be CUDA tensors")
@@ -288,6 +291,7 @@ def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowr
     o.dtype_in = _DTYPES[I.dtype]
     o.dtype_out = _DTYPES[out_dtype]
     o.detail_gain = float(detail_gain)
+    o.color_guide = int(bool(color_guide))
     if rows is not None:
         if not given:
             raise ValueError("rows needs out= (the whole q; rows outside the range are not written)")

@@ -98,7 +98,16 @@ gf_status resolve(int H, int W, int C, int r, float eps, int s, int mode, const 
     if (mode < GF_SUB_NEAREST || mode > GF_SUB_BILINEAR_AA) return fail(GF_EINVAL, "unknown subsample mode");
     if (o->batch < 1) return fail(GF_EINVAL, "batch must be >= 1");
     const int CI = o->guide_channels == 0 ? 1 : o->guide_channels;
-    if (CI != 1 && CI != C) return fail(GF_EINVAL, "guide_channels must be 1 or C");
+    R.color = o->color_guide != 0;
+    if (R.color) {
+        if (CI != 3) return fail(GF_EINVAL, "a colour guide has guide_channels = 3");
+        if (o->dtype_in == GF_U8) return fail(GF_EINVAL, "a colour guide takes FP32 or FP16 input");
+        if (o->a_out || o->b_out || o->mean_a_out || o->mean_b_out || o->stats_out)
+            return fail(GF_EINVAL, "a colour guide does not produce the low-res intermediates");
+        if (o->detail_gain != 0.0f && C != 3) return fail(GF_EINVAL, "detail_gain with a colour guide needs C = 3");
+    } else if (CI != 1 && CI != C) {
+        return fail(GF_EINVAL, "guide_channels must be 1 or C");
+    }
     if (o->dtype_in < GF_F32 || o->dtype_in > GF_U8) return fail(GF_EINVAL, "unknown dtype_in");
     if (o->dtype_out != GF_F32 && o->dtype_out != GF_F16) return fail(GF_EINVAL, "dtype_out must be GF_F32 or GF_F16");
     if ((long long)H * W > (1LL << 31) - 1) return fail(GF_EINVAL, "H * W must be < 2^31");
@@ -176,9 +185,11 @@ FwdPlan make_plan(const Resolved &R, const Layout &L, const void *I, const void 
     P.Yw0 = R.Yw0;
     P.Yw1 = R.Yw1;
     P.lps = R.lps;
-    const bool sub = R.s > 1 || R.p_lowres;
+    const bool sub = R.s > 1 || R.p_lowres || R.color;
     P.Il = sub ? (float *)(ws + L.off_Il) : nullptr;
     P.pl = sub ? (float *)(ws + L.off_pl) : nullptr;
+    P.color = R.color;
+    for (int k = 0; k < 8; ++k) P.col[k] = R.color ? (float *)(ws + L.off_col[k]) : nullptr;
     P.a = (opts && opts->a_out) ? opts->a_out : (float *)(ws + L.off_a);
     P.b = (opts && opts->b_out) ? opts->b_out : (float *)(ws + L.off_b);
     P.ma = (opts && opts->mean_a_out) ? opts->mean_a_out : (float *)(ws + L.off_ma);
@@ -198,13 +209,16 @@ Layout layout_of(const Resolved &R, const gf_opts *o)
     Layout L;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t at = off; off += (bytes + 255) & ~size_t(255); return at; };
-    const bool sub = R.s > 1 || R.p_lowres;
+    const bool sub = R.s > 1 || R.p_lowres || R.color;
     L.off_Il = take(sub ? (size_t)R.N * R.CI * pb : 0);
     L.off_pl = take(sub ? nc : 0);
-    L.off_a = take((o && o->a_out) ? 0 : nc);
-    L.off_b = take((o && o->b_out) ? 0 : nc);
-    L.off_ma = take((o && o->mean_a_out) ? 0 : nc);
-    L.off_mb = take((o && o->mean_b_out) ? 0 : nc);
+    const bool gray = !R.color;
+    L.off_a = take((o && o->a_out) || !gray ? 0 : nc);
+    L.off_b = take((o && o->b_out) || !gray ? 0 : nc);
+    L.off_ma = take((o && o->mean_a_out) || !gray ? 0 : nc);
+    L.off_mb = take((o && o->mean_b_out) || !gray ? 0 : nc);
+    for (int k = 0; k < 8; ++k)  // colour guide: 4 arrays of 5 + 2C planes per image, then 4 of 2C
+        L.off_col[k] = take(R.color ? (size_t)R.N * (k < 4 ? 5 + 2 * R.C : 2 * R.C) * pb : 0);
     L.total = off;
     return L;
 }
@@ -242,6 +256,7 @@ gf_status check_backward(const Resolved &R)
     if (R.detail != 0.0f) return fail(GF_EINVAL, "detail_gain is forward only");
     if (R.mode == GF_SUB_BILINEAR_AA && R.s > 1) return fail(GF_EINVAL, "antialiased subsampling is forward only");
     if (R.Yw1 - R.Yw0 != R.H) return fail(GF_EINVAL, "a row range is forward only");
+    if (R.color) return fail(GF_EINVAL, "the colour guide is forward only");
     return GF_OK;
 }
 

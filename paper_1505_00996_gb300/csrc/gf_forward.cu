@@ -1292,9 +1292,48 @@ bool aligned_fp32_subsample(const FwdPlan &P)
 
 }  // namespace
 
-int forward_kernel_count(const Resolved &R) { return 3 + (R.s > 1 ? 1 : 0); }
+int forward_kernel_count(const Resolved &R) { return R.color ? 6 : 3 + (R.s > 1 ? 1 : 0); }
 
 namespace {
+
+// The colour-guide form after the subsample: products, their box means, the 3 x 3 solves, the box means of
+// the coefficients, and the output (kernels in gf_color.cu).
+cudaError_t launch_color_chain(const FwdPlan &P0, float *pl, StageTimer &tm, cudaStream_t st)
+{
+    FwdPlan P = P0;
+    P.pl = pl;  // I' itself when the call is self-guided
+    cudaError_t err;
+    const int K = 5 + 2 * P.C;
+    auto box_pairs = [&](float *X, float *Y, float *oX, float *oY, int per_image) {
+        BoxParams bp{};
+        bp.X = X; bp.Y = Y;
+        bp.xps = bp.yps = bp.ops = P.lps;
+        bp.CX = bp.C = per_image;
+        bp.out0 = oX; bp.out1 = oY;
+        bp.h = P.h; bp.w = P.w; bp.r = P.r_low;
+        return launch_box_t<float, KIND_MEAN2>(bp, P.N * per_image, st);
+    };
+    tm.before();
+    err = launch_color_products(P, st);
+    tm.after();
+    if (err != cudaSuccess) return err;
+    tm.before();
+    err = box_pairs(P.col[0], P.col[1], P.col[2], P.col[3], K);
+    tm.after();
+    if (err != cudaSuccess) return err;
+    tm.before();
+    err = launch_color_coef(P, st);
+    tm.after();
+    if (err != cudaSuccess) return err;
+    tm.before();
+    err = box_pairs(P.col[4], P.col[5], P.col[6], P.col[7], 2 * P.C);
+    tm.after();
+    if (err != cudaSuccess || P.skip_output) return err;
+    tm.before();
+    err = launch_color_output(P, st);
+    tm.after();
+    return err;
+}
 
 }  // namespace
 
@@ -1310,7 +1349,7 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
     // A self-guided call (p is I, one guide channel per channel) subsamples once and uses I' as p'; the
     // backward keeps its own p' plane, so its forward recomputation subsamples both.
     const bool self_guided = (P.I == P.p) && (P.CI == P.C) && !P.p_lowres && !P.need_lowres;
-    if (P.s > 1) {
+    if (P.s > 1 || P.color) {  // the colour stages read low-res planes only, so s = 1 copies
         SubParams sp;
         sp.h = P.h; sp.w = P.w; sp.mode = P.mode;
         // uint8 path: carry the subsampled values as exact integers J = k * (value in 1/255 units)
@@ -1356,6 +1395,8 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         Ysrc = self_guided ? P.Il : P.pl;
         src_dt = F32;
     }
+
+    if (P.color) return launch_color_chain(P, self_guided ? P.Il : P.pl, tm, st);
 
     // ---- Algorithm 2, box statistics + var/cov + coefficients a, b (Eq. 2-3)
     {

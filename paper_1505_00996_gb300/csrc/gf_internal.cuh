@@ -42,6 +42,11 @@ struct FwdPlan {
     float int_scale;     // 255 * k: J = int_scale * I' (uint8 path)
     cudaEvent_t *events; // 2*GF_MAX_STAGES or NULL
     float detail = 0.0f; // detail gain of the output epilogue (0: plain q)
+    // colour guide (CI = 3 used jointly): the scratch planes of gf_color.cu -- products A, B; their means;
+    // the coefficient planes (a_r, a_b), (a_g, b); their means.  K = 5 + 2C planes per image in each of the
+    // first four, 2C in each of the last four.
+    bool color = false;
+    float *col[8] = {};
     size_t fps = 0;      // plane stride (elements) of the full-res I, p and q (H * W of the whole image)
     size_t lpin = 0;     // plane stride of a low-res p given by the caller (h * w of the whole image)
     int Yw0 = 0, Yw1 = 0;  // output rows written, [Yw0, Yw1) of the H rows the plan covers
@@ -82,6 +87,7 @@ struct Resolved {
     bool p_lowres, dense_lowres, int_stats;
     float eps, int_scale;
     float detail;  // detail gain (gf_opts.detail_gain)
+    bool color;    // colour guide (gf_opts.color_guide)
     size_t lps;  // low-res plane stride in floats
     // Row band (gf_opts.row_begin / row_end): H and h above are those of the band of complete s-row blocks
     // that is filtered; it starts at full-res row row0 of the whole image, and the output rows written are
@@ -96,6 +102,7 @@ gf_status resolve(int H, int W, int C, int r, float eps, int s, int mode, const 
 // Byte offsets of a forward call's low-res planes in its scratch.
 struct Layout {
     size_t off_Il, off_pl, off_a, off_b, off_ma, off_mb, total;
+    size_t off_col[8];  // colour-guide planes (FwdPlan::col)
 };
 Layout layout_of(const Resolved &R, const gf_opts *o);
 
@@ -112,6 +119,11 @@ cudaError_t opt_in_smem(F *func, size_t smem) { return opt_in_smem(reinterpret_c
 
 // Kernels one forward call launches for these arguments (host-side, assuming 16-byte aligned buffers).
 int forward_kernel_count(const Resolved &R);
+
+// Colour-guide stages (gf_color.cu).
+cudaError_t launch_color_products(const FwdPlan &P, cudaStream_t st);
+cudaError_t launch_color_coef(const FwdPlan &P, cudaStream_t st);
+cudaError_t launch_color_output(const FwdPlan &P, cudaStream_t st);
 
 // Launch the forward chain on `stream`.  Returns cudaSuccess or the first launch error.
 cudaError_t launch_forward(const FwdPlan &P, cudaStream_t stream);
