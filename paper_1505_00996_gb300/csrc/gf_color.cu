@@ -135,57 +135,168 @@ __device__ __forceinline__ void st4g(T *p, bool vec, int valid, const float v[4]
         }
 }
 
-// Thread = 4 adjacent pixels of one row band and one channel; CTA = COL_NT threads along a row.
-template <typename TI, typename TQ>
-__global__ void __launch_bounds__(COL_NT) k_color_output(const TI *__restrict__ I, TQ *__restrict__ q,
-                                                         const float *__restrict__ MX, const float *__restrict__ MY,
-                                                         int C, int H, int W, int h, int w, int s, size_t fps,
-                                                         size_t lps, int R, int Yw0, int Yw1, float detail,
-                                                         bool vec_io)
+// CTA = one channel of one 512-pixel-wide band of CO_R rows; the channel is the fastest-varying block index,
+// so the channel CTAs of a band run side by side and read the guide through L2 once.  The low-res taps of
+// the four means (mean of a_r, a_g, a_b, b) under the band are staged in shared memory; each thread owns 4
+// adjacent pixels, keeps the horizontally interpolated upper and lower tap rows of the four maps in
+// registers (recomputed only when the tap rows change, every s rows), and reads the three guide planes with
+// 128-bit streaming loads.
+constexpr int CO_NT = 128, CO_BAND = 4 * CO_NT, CO_NST = 4;
+
+// 4 pixels from the thread's ring slot, as floats.
+template <typename T>
+__device__ __forceinline__ void ld4_ring(const unsigned char *p, float v[4])
 {
-    const int X0 = (blockIdx.x * COL_NT + threadIdx.x) * 4;
+    if constexpr (sizeof(T) == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+        const uint2 t = *reinterpret_cast<const uint2 *>(p);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+}
+
+template <typename TI, typename TQ>
+__global__ void __launch_bounds__(CO_NT) k_color_output(const TI *__restrict__ I, TQ *__restrict__ q,
+                                                        const float *__restrict__ MX, const float *__restrict__ MY,
+                                                        int C, int H, int W, int h, int w, int s, size_t fps,
+                                                        size_t lps, int R, int LCmax, int Yw0, int Yw1, float detail,
+                                                        bool vec_io)
+{
+    extern __shared__ float tap[];  // [4 maps][LR][LCmax]
+    const int c = blockIdx.x % C, band = blockIdx.x / C, n = blockIdx.z;
+    const int Xb = band * CO_BAND;
+    const int Yb = max((int)blockIdx.y * R, Yw0), Ye = min(min((int)blockIdx.y * R + R, H), Yw1);
+    if (Yb >= Ye) return;
+    int ly0, ly1, lx0, lx1, t0;
+    float ft;
+    up_taps(Yb, s, h, ly0, t0, ft);
+    up_taps(Ye - 1, s, h, t0, ly1, ft);
+    up_taps(Xb, s, w, lx0, t0, ft);
+    up_taps(min(Xb + CO_BAND, W) - 1, s, w, t0, lx1, ft);
+    const int LR = ly1 - ly0 + 1, LC = lx1 - lx0 + 1, tile = LR * LCmax;
+    const float *mx = MX + ((size_t)n * 2 * C + 2 * c) * lps, *my = MY + ((size_t)n * 2 * C + 2 * c) * lps;
+    for (int mr = 0; mr < 4 * LR; ++mr) {  // maps in order: mean of a_r (mx), a_g (my), a_b (mx + lps), b (my + lps)
+        const int m = mr / LR, row = mr - m * LR;
+        const float *src = ((m & 1) ? my : mx) + (m >> 1) * lps + (size_t)(ly0 + row) * w + lx0;
+        float *dst = tap + m * tile + row * LCmax;
+        for (int col = threadIdx.x; col < LC; col += CO_NT) cp_async4(dst + col, src + col);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    const int X0 = Xb + threadIdx.x * 4;
     if (X0 >= W) return;
     const int valid = min(4, W - X0);
-    const int c = blockIdx.z % C, n = blockIdx.z / C;
-    const int Yb = max((int)blockIdx.y * R, Yw0), Ye = min(min((int)blockIdx.y * R + R, H), Yw1);
     const bool vec = vec_io && (valid == 4);
-    const float *mx = MX + ((size_t)n * 2 * C + 2 * c) * lps, *my = MY + ((size_t)n * 2 * C + 2 * c) * lps;
-    const float *maps[4] = {mx, my, mx + lps, my + lps};  // mean of a_r, a_g, a_b, b
     int xa[4], xb[4];
     float fx[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) up_taps(min(X0 + k, W - 1), s, w, xa[k], xb[k], fx[k]);
+    for (int k = 0; k < 4; ++k) {
+        up_taps(min(X0 + k, W - 1), s, w, xa[k], xb[k], fx[k]);
+        xa[k] -= lx0;
+        xb[k] -= lx0;
+    }
+    // horizontally interpolated upper tap row (lo) and lower minus upper (d), per map and pixel
+    float lo[4][4], d[4][4];
+    auto hrow = [&](int yy, float (&o)[4][4]) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const float *rp = tap + m * tile + (yy - ly0) * LCmax;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o[m][k] = fmaf(fx[k], rp[xb[k]] - rp[xa[k]], rp[xa[k]]);
+        }
+    };
     const TI *Ig = I + (size_t)n * 3 * fps + X0;
     TQ *qc = q + ((size_t)n * C + c) * fps + X0;
-    for (int Y = Yb; Y < Ye; ++Y) {
-        int ya, yb;
-        float fy;
-        up_taps(Y, s, h, ya, yb, fy);
-        float m[4][4];  // [map][pixel]
+    // The three guide planes' 4 pixels of the next CO_NST - 1 rows are in flight at any time: each thread
+    // copies them into its own slots of a shared ring (cp.async, 16 or 8 bytes) and reads back only what it
+    // copied itself, so the only synchronisation is the thread's own group wait.  A thread whose 4 pixels
+    // are not one aligned vector (a ragged last group, unaligned planes) loads them directly instead.
+    constexpr int VB = 4 * (int)sizeof(TI);
+    unsigned char *ring = reinterpret_cast<unsigned char *>(tap + 4 * tile);  // [CO_NST][3][CO_NT][VB]
+    auto slot = [&](int stage, int k) { return ring + ((size_t)(stage * 3 + k) * CO_NT + threadIdx.x) * VB; };
+    auto issue = [&](int u) {
+        const int Y = Yb + u;
+        if (vec && Y < Ye) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float *r0 = maps[k] + (size_t)ya * w, *r1 = maps[k] + (size_t)yb * w;
-#pragma unroll
-            for (int x = 0; x < 4; ++x) {
-                const float t0 = fmaf(fx[x], r0[xb[x]] - r0[xa[x]], r0[xa[x]]);
-                const float t1 = fmaf(fx[x], r1[xb[x]] - r1[xa[x]], r1[xa[x]]);
-                m[k][x] = fmaf(fy, t1 - t0, t0);
+            for (int k = 0; k < 3; ++k) {
+                const TI *src = Ig + k * fps + (size_t)Y * W;
+                if constexpr (VB == 16) cp_async16(slot(u % CO_NST, k), src);
+                else ld_async_small<TI>(slot(u % CO_NST, k), src);
             }
         }
-        float ir[4], ig[4], ib[4], out[4];
+        cp_async_commit();  // one group per row, empty when nothing was copied, so the count stays uniform
+    };
+#pragma unroll
+    for (int u = 0; u < CO_NST - 1; ++u) issue(u);
+    float gv[3][4];
+    // vertical taps walked row by row: numerator 2Y + 1 - s over 2s, quotient qt and remainder rem (gf.h, R7)
+    const int den = 2 * s;
+    const float inv_den = 1.0f / (float)den;
+    int num = 2 * Yb + 1 - s, qt = 0, rem = 0;
+    if (num > 0) { qt = num / den; rem = num - qt * den; }
+    int cur_a = -1, cur_b = -1;
+    for (int Y = Yb; Y < Ye; ++Y) {
+        const int u = Y - Yb;
+        issue(u + CO_NST - 1);
+        cp_async_wait_group<CO_NST - 1>();  // this thread's copies of row u have landed
+        if (vec) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) ld4_ring<TI>(slot(u % CO_NST, k), gv[k]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) ld4g<TI>(Ig + k * fps + (size_t)Y * W, false, valid, gv[k]);
+        }
+        int ya, yb;
+        float fy;
+        if (num <= 0) { ya = yb = 0; fy = 0.0f; }
+        else if (qt >= h - 1) { ya = yb = h - 1; fy = 0.0f; }
+        else { ya = qt; yb = qt + 1; fy = (float)rem * inv_den; }
+        if (ya != cur_a || yb != cur_b) {
+            if (ya == cur_b) {  // the old lower row becomes the upper one
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) lo[m][k] += d[m][k];
+            } else {
+                hrow(ya, lo);
+            }
+            hrow(yb, d);
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) d[m][k] -= lo[m][k];
+            cur_a = ya;
+            cur_b = yb;
+        }
+        num += 2;
+        if (num > 0) {
+            if (num <= 2) { qt = num / den; rem = num - qt * den; }
+            else if ((rem += 2) >= den) { rem -= den; ++qt; }
+        }
+        const float *ir = gv[0], *ig = gv[1], *ib = gv[2];
+        float out[4];
         const size_t row = (size_t)Y * W;
-        ld4g<TI>(Ig + row, vec, valid, ir);
-        ld4g<TI>(Ig + fps + row, vec, valid, ig);
-        ld4g<TI>(Ig + 2 * fps + row, vec, valid, ib);
 #pragma unroll
-        for (int x = 0; x < 4; ++x) out[x] = fmaf(m[0][x], ir[x], fmaf(m[1][x], ig[x], fmaf(m[2][x], ib[x], m[3][x])));
+        for (int x = 0; x < 4; ++x) {
+            float m[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) m[k] = fmaf(fy, d[k][x], lo[k][x]);
+            out[x] = fmaf(m[0], ir[x], fmaf(m[1], ig[x], fmaf(m[2], ib[x], m[3])));
+        }
         if (detail != 0.0f) {  // C == 3: channel c's own guide channel is its detail source
-            const float *iv = (c == 0) ? ir : (c == 1 ? ig : ib);
 #pragma unroll
-            for (int x = 0; x < 4; ++x) out[x] = fmaf(detail, iv[x] - out[x], out[x]);
+            for (int x = 0; x < 4; ++x) {
+                const float iv = (c == 0) ? ir[x] : (c == 1 ? ig[x] : ib[x]);
+                out[x] = fmaf(detail, iv - out[x], out[x]);
+            }
         }
         st4g<TQ>(qc + row, vec, valid, out);
     }
+    cp_async_wait_all();
 }
 
 int blocks_for(size_t items) { return (int)std::min<size_t>((items + COL_NT - 1) / COL_NT, 152 * 8); }
@@ -209,13 +320,23 @@ cudaError_t launch_color_coef(const FwdPlan &P, cudaStream_t st)
 
 cudaError_t launch_color_output(const FwdPlan &P, cudaStream_t st)
 {
-    const int R = 16;
-    dim3 grid((P.W + 4 * COL_NT - 1) / (4 * COL_NT), (P.H + R - 1) / R, P.N * P.C);
-    // 128-bit loads and stores need every row of every plane on a 16-byte boundary (FP32 only)
-    const bool vec_io = (P.W % 4 == 0) && (P.fps % 4 == 0) && ((uintptr_t)P.I % 16 == 0) && ((uintptr_t)P.q % 16 == 0);
-#define GF_CO(TI, TQ)                                                                                          \
-    k_color_output<TI, TQ><<<grid, COL_NT, 0, st>>>((const TI *)P.I, (TQ *)P.q, P.col[6], P.col[7], P.C, P.H, P.W, \
-                                                    P.h, P.w, P.s, P.fps, P.lps, R, P.Yw0, P.Yw1, P.detail, vec_io)
+    const int R = 8 * P.s;
+    // tap rows / columns under R rows / CO_BAND columns: at most ceil((n - 1)/s) + 2 <= ceil(n/s) + 2
+    const int LR = (R + P.s - 1) / P.s + 2, LCmax = (CO_BAND + P.s - 1) / P.s + 2;
+    const size_t smem = (size_t)4 * LR * LCmax * sizeof(float) + (size_t)CO_NST * 3 * CO_NT * 4 * dtype_size(P.dt_in);
+    const int bands = (P.W + CO_BAND - 1) / CO_BAND;
+    dim3 grid(bands * P.C, (P.H + R - 1) / R, P.N);
+    // ring copies and 128-bit stores need every row of every plane on a vector boundary
+    const size_t vb = 4 * dtype_size(P.dt_in);
+    const bool vec_io = (P.W % 4 == 0) && (P.fps % 4 == 0) && ((uintptr_t)P.I % vb == 0) && ((uintptr_t)P.q % 16 == 0);
+    cudaError_t e;
+#define GF_CO(TI, TQ)                                                                                            \
+    do {                                                                                                         \
+        if ((e = opt_in_smem(k_color_output<TI, TQ>, smem)) != cudaSuccess) return e;                          \
+        k_color_output<TI, TQ><<<grid, CO_NT, smem, st>>>((const TI *)P.I, (TQ *)P.q, P.col[6], P.col[7], P.C, P.H, \
+                                                          P.W, P.h, P.w, P.s, P.fps, P.lps, R, LCmax, P.Yw0,     \
+                                                          P.Yw1, P.detail, vec_io);                              \
+    } while (0)
     if (P.dt_in == F32) {
         if (P.dt_out == F32) GF_CO(float, float); else GF_CO(float, __half);
     } else {

@@ -803,17 +803,6 @@ __device__ __forceinline__ void ld4_shared<uint8_t>(const void *p, float v[4])
 #pragma unroll
     for (int k = 0; k < 4; ++k) v[k] = (float)((t >> (8 * k)) & 0xffu) / 255.0f;
 }
-// 8-byte (FP16) and 4-byte (uint8) forms of the ring copy.
-template <typename T>
-__device__ __forceinline__ void ld_async_small(void *smem_dst, const T *gmem_src)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
-    if (sizeof(T) == 2)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem_src) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem_src) : "memory");
-}
-
 template <typename T>
 __device__ __forceinline__ void st4(T *p, bool vec, int valid, const float v[4]);
 template <>
