@@ -39,6 +39,8 @@
  *      cov_Ip and b = mean_p - a^T mean_I, Sigma being the 3 x 3 covariance of the guide in the window and
  *      cov_Ip the covariance of each guide channel with p; Algorithm 2's subsample and upsample steps wrap it
  *      unchanged, and q = mean_a^T I + mean_b on the full-resolution guide.
+ *   R13 a non-integer ratio s (a rational sn / sd > 1, e.g. 5/2): the same coordinate maps R2, R3, R5-R7, R11
+ *      with that s, evaluated exactly as ratios of integers; the box subsample needs an integer s.
  *   R11 antialiased bilinear subsample (a fourth mode; the paper names only "bilinear", and this is the
  *      form a shrinking resize takes when it low-passes first): a triangle filter of half-width s centred
  *      on the low-res pixel centre, so source pixel x has weight max(0, 1 - |x + 1/2 - (i + 1/2) s| / s)
@@ -59,21 +61,27 @@ static int imax(int a, int b) { return a > b ? a : b; }
 static int iclamp(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 static double dclamp(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+/* The ratio s is a rational sn / sd (sd = 1 for the integer ratios of Algorithm 2; R13 reads a non-integer
+ * ratio the same way), so every coordinate below is a ratio of integers and every floor, clamp and weight
+ * is decided exactly. */
+
 /* R6: r' from r and s (Algorithm 2 sets r' = r/s). */
-int gfo_lowres_radius(int r, int s)
+int gfo_lowres_radius_q(int r, int sn, int sd)
 {
-    if (s == 1) return r;
-    int rl = (2 * r + s) / (2 * s); /* floor(r/s + 1/2) */
+    if (sn == sd) return r;
+    int rl = (int)((2LL * r * sd + sn) / (2LL * sn)); /* floor(r/s + 1/2) */
     if (r >= 1 && rl < 1) rl = 1;
     return rl;
 }
+int gfo_lowres_radius(int r, int s) { return gfo_lowres_radius_q(r, s, 1); }
 
-/* R5 */
-void gfo_lowres_shape(int H, int W, int s, int *h, int *w)
+/* R5: h = ceil(H / s), w = ceil(W / s). */
+void gfo_lowres_shape_q(int H, int W, int sn, int sd, int *h, int *w)
 {
-    *h = (H + s - 1) / s;
-    *w = (W + s - 1) / s;
+    *h = (int)(((long long)H * sd + sn - 1) / sn);
+    *w = (int)(((long long)W * sd + sn - 1) / sn);
 }
+void gfo_lowres_shape(int H, int W, int s, int *h, int *w) { gfo_lowres_shape_q(H, W, s, 1, h, w); }
 
 /* One bilinear tap pair along an axis (R3/R7): position t on an axis of length n, clamped. */
 static void axis_taps(double t, int n, int *i0, int *i1, double *f)
@@ -85,50 +93,67 @@ static void axis_taps(double t, int n, int *i0, int *i1, double *f)
     *f = t - (double)a;
 }
 
-/* R11: triangle weight of source pixel x for low-res pixel i at ratio s. */
-static double aa_weight(int x, int i, int s)
+/* A bilinear tap pair at the position num / den (a ratio of integers) on an axis of length n, clamped. */
+static void axis_taps_q(long long num, long long den, int n, int *i0, int *i1, double *f)
 {
-    double d = fabs((x + 0.5) - (i + 0.5) * s) / s;
-    return d < 1.0 ? 1.0 - d : 0.0;
+    if (num <= 0) { *i0 = *i1 = 0; *f = 0.0; return; }
+    long long q = num / den;
+    if (q >= n - 1) { *i0 = *i1 = n - 1; *f = 0.0; return; }
+    *i0 = (int)q;
+    *i1 = (int)q + 1;
+    *f = (double)(num - q * den) / (double)den;
 }
 
-/* f_subsample(x, s), Algorithm 2 first step; modes R2/R3/R4/R11.  y is ceil(H/s) x ceil(W/s). */
-void gfo_subsample(const double *x, int H, int W, int s, int mode, double *y)
+/* R11: triangle weight of source pixel x for low-res pixel i at ratio s = sn / sd:
+ * max(0, 1 - |x + 1/2 - (i + 1/2) s| / s) = max(0, 2 sn - |(2x + 1) sd - (2i + 1) sn|) / (2 sn). */
+static double aa_weight(int x, int i, int sn, int sd)
+{
+    long long d = (2LL * x + 1) * sd - (2LL * i + 1) * sn;
+    long long num = 2LL * sn - (d < 0 ? -d : d);
+    return num > 0 ? (double)num / (2.0 * sn) : 0.0;
+}
+
+/* f_subsample(x, s), Algorithm 2 first step; modes R2/R3/R4/R11 at ratio s = sn / sd (box mode: integer s
+ * only).  y is ceil(H/s) x ceil(W/s). */
+void gfo_subsample_q(const double *x, int H, int W, int sn, int sd, int mode, double *y)
 {
     int h, w;
-    gfo_lowres_shape(H, W, s, &h, &w);
+    gfo_lowres_shape_q(H, W, sn, sd, &h, &w);
     for (int j = 0; j < h; ++j) {
         for (int i = 0; i < w; ++i) {
             double v = 0.0;
-            if (mode == GFO_SUB_NEAREST) {
-                int sy = iclamp((int)floor((j + 0.5) * s), 0, H - 1);
-                int sx = iclamp((int)floor((i + 0.5) * s), 0, W - 1);
+            if (mode == GFO_SUB_NEAREST) { /* floor((j + 1/2) s) */
+                int sy = iclamp((int)(((2LL * j + 1) * sn) / (2LL * sd)), 0, H - 1);
+                int sx = iclamp((int)(((2LL * i + 1) * sn) / (2LL * sd)), 0, W - 1);
                 v = x[(size_t)sy * W + sx];
-            } else if (mode == GFO_SUB_BILINEAR) {
+            } else if (mode == GFO_SUB_BILINEAR) { /* (j + 1/2) s - 1/2 = ((2j + 1) sn - sd) / (2 sd) */
                 int y0, y1, x0, x1;
                 double fy, fx;
-                axis_taps((j + 0.5) * s - 0.5, H, &y0, &y1, &fy);
-                axis_taps((i + 0.5) * s - 0.5, W, &x0, &x1, &fx);
+                axis_taps_q((2LL * j + 1) * sn - sd, 2LL * sd, H, &y0, &y1, &fy);
+                axis_taps_q((2LL * i + 1) * sn - sd, 2LL * sd, W, &x0, &x1, &fx);
                 double top = (1.0 - fx) * x[(size_t)y0 * W + x0] + fx * x[(size_t)y0 * W + x1];
                 double bot = (1.0 - fx) * x[(size_t)y1 * W + x0] + fx * x[(size_t)y1 * W + x1];
                 v = (1.0 - fy) * top + fy * bot;
             } else if (mode == GFO_SUB_BILINEAR_AA) {
                 /* every source pixel within s of the centre, weighted, over the sum of the weights used */
                 double acc = 0.0, wsum = 0.0;
-                for (int yy = imax(0, j * s - s); yy <= imin(H - 1, j * s + 2 * s); ++yy) {
-                    double wy = aa_weight(yy, j, s);
+                int ya = (int)(((long long)j * sn) / sd) - (sn + sd - 1) / sd - 1;
+                int xa = (int)(((long long)i * sn) / sd) - (sn + sd - 1) / sd - 1;
+                int span = 3 * ((sn + sd - 1) / sd) + 3; /* covers (i + 1/2) s +- s */
+                for (int yy = imax(0, ya); yy <= imin(H - 1, ya + span); ++yy) {
+                    double wy = aa_weight(yy, j, sn, sd);
                     if (wy == 0.0) continue;
-                    for (int xx = imax(0, i * s - s); xx <= imin(W - 1, i * s + 2 * s); ++xx) {
-                        double wx = aa_weight(xx, i, s);
+                    for (int xx = imax(0, xa); xx <= imin(W - 1, xa + span); ++xx) {
+                        double wx = aa_weight(xx, i, sn, sd);
                         if (wx == 0.0) continue;
                         acc += wy * wx * x[(size_t)yy * W + xx];
                         wsum += wy * wx;
                     }
                 }
                 v = acc / wsum;
-            } else { /* GFO_SUB_BOX */
-                int ya = j * s, yb = imin((j + 1) * s, H);
-                int xa = i * s, xb = imin((i + 1) * s, W);
+            } else { /* GFO_SUB_BOX (integer s = sn, sd = 1) */
+                int ya = j * sn, yb = imin((j + 1) * sn, H);
+                int xa = i * sn, xb = imin((i + 1) * sn, W);
                 double acc = 0.0;
                 for (int yy = ya; yy < yb; ++yy)
                     for (int xx = xa; xx < xb; ++xx) acc += x[(size_t)yy * W + xx];
@@ -138,6 +163,7 @@ void gfo_subsample(const double *x, int H, int W, int s, int mode, double *y)
         }
     }
 }
+void gfo_subsample(const double *x, int H, int W, int s, int mode, double *y) { gfo_subsample_q(x, H, W, s, 1, mode, y); }
 
 /* Sum of x over the clipped window of radius r around every pixel (no normalisation).  Separable:
  * the sum over a rectangle is the sum over its rows of the sums over its columns. */
@@ -204,22 +230,27 @@ static void box_mean_mode(const double *x, int h, int w, int r, int brute, doubl
         gfo_box_mean(x, h, w, r, y);
 }
 
-/* f_upsample(x, s) to H x W, bilinear (R7); Algorithm 2 upsampling step. */
-void gfo_upsample(const double *x, int h, int w, int s, int H, int W, double *y)
+/* f_upsample(x, s) to H x W, bilinear (R7); Algorithm 2 upsampling step.  Full-res X samples
+ * (X + 1/2) / s - 1/2 = ((2X + 1) sd - sn) / (2 sn). */
+void gfo_upsample_q(const double *x, int h, int w, int sn, int sd, int H, int W, double *y)
 {
     for (int Y = 0; Y < H; ++Y) {
         int y0, y1;
         double fy;
-        axis_taps((Y + 0.5) / (double)s - 0.5, h, &y0, &y1, &fy);
+        axis_taps_q((2LL * Y + 1) * sd - sn, 2LL * sn, h, &y0, &y1, &fy);
         for (int X = 0; X < W; ++X) {
             int x0, x1;
             double fx;
-            axis_taps((X + 0.5) / (double)s - 0.5, w, &x0, &x1, &fx);
+            axis_taps_q((2LL * X + 1) * sd - sn, 2LL * sn, w, &x0, &x1, &fx);
             double top = (1.0 - fx) * x[(size_t)y0 * w + x0] + fx * x[(size_t)y0 * w + x1];
             double bot = (1.0 - fx) * x[(size_t)y1 * w + x0] + fx * x[(size_t)y1 * w + x1];
             y[(size_t)Y * W + X] = (1.0 - fy) * top + fy * bot;
         }
     }
+}
+void gfo_upsample(const double *x, int h, int w, int s, int H, int W, double *y)
+{
+    gfo_upsample_q(x, h, w, s, 1, H, W, y);
 }
 
 /*
@@ -232,15 +263,17 @@ void gfo_upsample(const double *x, int h, int w, int s, int H, int W, double *y)
  *   stats_out         -- N x C x 4 x h x w: mean_I, corr_I, mean_p, corr_Ip (Algorithm 2 box step).
  * Returns 0, or -1 on invalid arguments.
  */
-int gfo_fast_guided_filter(const double *I, const double *p, int N, int CI, int C, int H, int W, int r_low,
-                           double eps, int s, int mode, int p_lowres, int brute, double *q, double *a_out,
-                           double *b_out, double *ma_out, double *mb_out, double *stats_out)
+int gfo_fast_guided_filter_q(const double *I, const double *p, int N, int CI, int C, int H, int W, int r_low,
+                             double eps, int sn, int sd, int mode, int p_lowres, int brute, double *q, double *a_out,
+                             double *b_out, double *ma_out, double *mb_out, double *stats_out)
 {
-    if (N < 1 || C < 1 || H < 1 || W < 1 || s < 1 || r_low < 0 || !(eps >= 0.0)) return -1;
+    if (N < 1 || C < 1 || H < 1 || W < 1 || sd < 1 || sn < sd || r_low < 0 || !(eps >= 0.0)) return -1;
     if (mode < GFO_SUB_NEAREST || mode > GFO_SUB_BILINEAR_AA) return -1;
+    if (mode == GFO_SUB_BOX && sn % sd != 0) return -1; /* box blocks need an integer ratio */
     if (CI != 1 && CI != C) return -1;
+    if (sn % sd == 0) { sn /= sd; sd = 1; }
     int h, w;
-    gfo_lowres_shape(H, W, s, &h, &w);
+    gfo_lowres_shape_q(H, W, sn, sd, &h, &w);
     size_t n = (size_t)h * w, NF = (size_t)H * W;
     double *Il = malloc(sizeof(double) * n), *pl = malloc(sizeof(double) * n);
     double *II = malloc(sizeof(double) * n), *Ip = malloc(sizeof(double) * n);
@@ -254,11 +287,11 @@ int gfo_fast_guided_filter(const double *I, const double *p, int N, int CI, int 
         for (int c = 0; c < C; ++c) {
             const double *Ig = I + ((size_t)bn * CI + (CI == 1 ? 0 : c)) * NF;
             /* step 1: I' = f_subsample(I, s), p' = f_subsample(p, s), r' = r/s */
-            gfo_subsample(Ig, H, W, s, mode, Il);
+            gfo_subsample_q(Ig, H, W, sn, sd, mode, Il);
             if (p_lowres)
                 memcpy(pl, p + ((size_t)bn * C + c) * n, sizeof(double) * n);
             else
-                gfo_subsample(p + ((size_t)bn * C + c) * NF, H, W, s, mode, pl);
+                gfo_subsample_q(p + ((size_t)bn * C + c) * NF, H, W, sn, sd, mode, pl);
             /* step 2: box means of I', p', I'.*I', I'.*p' */
             for (size_t k = 0; k < n; ++k) {
                 II[k] = Il[k] * Il[k];
@@ -279,8 +312,8 @@ int gfo_fast_guided_filter(const double *I, const double *p, int N, int CI, int 
             box_mean_mode(a, h, w, r_low, brute, mean_a);
             box_mean_mode(b, h, w, r_low, brute, mean_b);
             /* step 6: bilinear upsample to the original size */
-            gfo_upsample(mean_a, h, w, s, H, W, up_a);
-            gfo_upsample(mean_b, h, w, s, H, W, up_b);
+            gfo_upsample_q(mean_a, h, w, sn, sd, H, W, up_a);
+            gfo_upsample_q(mean_b, h, w, sn, sd, H, W, up_b);
             /* step 7: q = mean_a .* I + mean_b on the full-resolution guide (Eq. 4) */
             double *qc = q + ((size_t)bn * C + c) * NF;
             for (size_t k = 0; k < NF; ++k) qc[k] = up_a[k] * Ig[k] + up_b[k];
@@ -302,6 +335,15 @@ int gfo_fast_guided_filter(const double *I, const double *p, int N, int CI, int 
     free(Il); free(pl); free(II); free(Ip); free(mean_I); free(mean_p); free(corr_I); free(corr_Ip);
     free(a); free(b); free(mean_a); free(mean_b); free(up_a); free(up_b);
     return 0;
+}
+
+int gfo_fast_guided_filter(const double *I, const double *p, int N, int CI, int C, int H, int W, int r_low,
+                           double eps, int s, int mode, int p_lowres, int brute, double *q, double *a_out,
+                           double *b_out, double *ma_out, double *mb_out, double *stats_out)
+{
+    if (s < 1) return -1;
+    return gfo_fast_guided_filter_q(I, p, N, CI, C, H, W, r_low, eps, s, 1, mode, p_lowres, brute, q, a_out, b_out,
+                                    ma_out, mb_out, stats_out);
 }
 
 /* ---- Algorithm 1 (guided filter), coded separately ------------------------------------------------ */

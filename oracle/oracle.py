@@ -7,6 +7,7 @@ import ctypes
 import os
 import subprocess
 import threading
+from fractions import Fraction
 
 import numpy as np
 
@@ -41,6 +42,13 @@ def _load():
             lib.gfo_lowres_radius.argtypes = [i, i]
             lib.gfo_lowres_radius.restype = i
             lib.gfo_lowres_shape.argtypes = [i, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+            lib.gfo_lowres_radius_q.argtypes = [i, i, i]
+            lib.gfo_lowres_radius_q.restype = i
+            lib.gfo_lowres_shape_q.argtypes = [i, i, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+            lib.gfo_subsample_q.argtypes = [D, i, i, i, i, i, D]
+            lib.gfo_upsample_q.argtypes = [D, i, i, i, i, i, i, D]
+            lib.gfo_fast_guided_filter_q.argtypes = [D, D, i, i, i, i, i, i, d, i, i, i, i, i, D, D, D, D, D, D]
+            lib.gfo_fast_guided_filter_q.restype = i
             lib.gfo_subsample.argtypes = [D, i, i, i, i, D]
             for name in ("gfo_box_sum", "gfo_box_mean", "gfo_box_mean_bruteforce"):
                 getattr(lib, name).argtypes = [D, i, i, i, D]
@@ -69,14 +77,25 @@ def _ptr(x):
     return x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def ratio(s):
+    """The subsampling ratio as (sn, sd) with s = sn / sd: an int, a fractions.Fraction, or a float that is
+    an exact binary fraction (e.g. 2.5)."""
+    f = Fraction(s)
+    if f < 1:
+        raise ValueError("the ratio s must be >= 1")
+    return f.numerator, f.denominator
+
+
 def lowres_radius(r, s):
     """r' = r/s rounded half up, at least 1 when r >= 1; s = 1 gives r."""
-    return int(_load().gfo_lowres_radius(int(r), int(s)))
+    sn, sd = ratio(s)
+    return int(_load().gfo_lowres_radius_q(int(r), sn, sd))
 
 
 def lowres_shape(H, W, s):
+    sn, sd = ratio(s)
     h, w = ctypes.c_int(), ctypes.c_int()
-    _load().gfo_lowres_shape(int(H), int(W), int(s), ctypes.byref(h), ctypes.byref(w))
+    _load().gfo_lowres_shape_q(int(H), int(W), sn, sd, ctypes.byref(h), ctypes.byref(w))
     return h.value, w.value
 
 
@@ -85,7 +104,10 @@ def subsample(x, s, mode):
     H, W = x.shape
     h, w = lowres_shape(H, W, s)
     y = np.empty((h, w), np.float64)
-    _load().gfo_subsample(_ptr(x), H, W, int(s), int(mode), _ptr(y))
+    sn, sd = ratio(s)
+    if mode == SUB_BOX and sd != 1:
+        raise ValueError("box subsampling needs an integer ratio")
+    _load().gfo_subsample_q(_ptr(x), H, W, sn, sd, int(mode), _ptr(y))
     return y
 
 
@@ -113,7 +135,8 @@ def upsample(x, s, H, W):
     x = _c64(x)
     h, w = x.shape
     y = np.empty((H, W), np.float64)
-    _load().gfo_upsample(_ptr(x), h, w, int(s), int(H), int(W), _ptr(y))
+    sn, sd = ratio(s)
+    _load().gfo_upsample_q(_ptr(x), h, w, sn, sd, int(H), int(W), _ptr(y))
     return y
 
 
@@ -150,7 +173,8 @@ def fast_guided_filter(I, p, r, eps, s, mode=SUB_BILINEAR, r_low=None, p_lowres=
         inter = {k: np.empty((N, C, h, w), np.float64) for k in ("a", "b", "mean_a", "mean_b")}
         inter["stats"] = np.empty((N, C, 4, h, w), np.float64)
     g = (lambda k: _ptr(inter[k])) if inter else (lambda k: None)
-    rc = _load().gfo_fast_guided_filter(_ptr(I4), _ptr(p4), N, CI, C, H, W, rl, float(eps), int(s), int(mode),
+    sn, sd = ratio(s)
+    rc = _load().gfo_fast_guided_filter_q(_ptr(I4), _ptr(p4), N, CI, C, H, W, rl, float(eps), sn, sd, int(mode),
                                         int(bool(p_lowres)), int(bool(brute)), _ptr(q), g("a"), g("b"),
                                         g("mean_a"), g("mean_b"), g("stats"))
     if rc != 0:

@@ -118,6 +118,67 @@ def test_subsample_ragged_conventions():
     assert bil[2, 0] == pytest.approx(x[9, 1:3].mean())
 
 
+# ---------------------------------------------------------------------------------------------------------
+# Non-integer ratios (R13): s = sn / sd with the same coordinate maps, decided exactly
+# ---------------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", [oracle.SUB_NEAREST, oracle.SUB_BILINEAR, oracle.SUB_BILINEAR_AA])
+@pytest.mark.parametrize("s", [Fraction(5, 2), Fraction(3, 2), Fraction(7, 4)])
+def test_rational_subsample_matches_torch_scale_factor(mode, s):
+    # torch maps output pixel j to (j + 1/2) / scale_factor - 1/2 when the scale factor is given and not
+    # recomputed; with a binary fraction s that coordinate is exact, and the output has floor(H / s) rows
+    # (ceil here), so the common part is compared
+    H, W = 23, 17
+    x = _rng(int(s * 4) + mode).standard_normal((H, W))
+    torch_mode = {oracle.SUB_NEAREST: "nearest-exact", oracle.SUB_BILINEAR: "bilinear",
+                  oracle.SUB_BILINEAR_AA: "bilinear"}[mode]
+    kw = {} if mode == oracle.SUB_NEAREST else {"align_corners": False, "antialias": mode == oracle.SUB_BILINEAR_AA}
+    ref = torch.nn.functional.interpolate(torch.from_numpy(x)[None, None], scale_factor=float(1 / s), mode=torch_mode,
+                                          recompute_scale_factor=False, **kw)[0, 0].numpy()
+    y = oracle.subsample(x, s, mode)
+    assert y.shape == (-(-H * s.denominator // s.numerator), -(-W * s.denominator // s.numerator))
+    hh, ww = ref.shape
+    if mode == oracle.SUB_BILINEAR_AA:  # torch renormalises the clipped taps too; compare the interior
+        np.testing.assert_allclose(y[1:hh - 1, 1:ww - 1], ref[1:hh - 1, 1:ww - 1], rtol=1e-13, atol=1e-13)
+    else:
+        np.testing.assert_allclose(y[:hh, :ww], ref, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("s", [Fraction(5, 2), Fraction(3, 2), Fraction(9, 4)])
+def test_rational_upsample_matches_torch_scale_factor(s):
+    h, w = 7, 6
+    x = _rng(int(s * 8)).standard_normal((h, w))
+    H, W = int(h * s) - 1, int(w * s)
+    ref = torch.nn.functional.interpolate(torch.from_numpy(x)[None, None], scale_factor=float(s), mode="bilinear",
+                                          align_corners=False, recompute_scale_factor=False)[0, 0].numpy()
+    np.testing.assert_allclose(oracle.upsample(x, s, H, W), ref[:H, :W], rtol=1e-13, atol=1e-13)
+
+
+def test_rational_ratio_hand_values():
+    s = Fraction(4, 3)  # not a binary fraction: positions decided exactly
+    x = np.arange(7 * 5, dtype=np.float64).reshape(7, 5)
+    near = oracle.subsample(x, s, oracle.SUB_NEAREST)  # rows floor((2j + 1) 2 / 3) = 0, 2, 3, 4, 6, (7 -> 6)
+    assert near.shape == (6, 4)
+    np.testing.assert_array_equal(near[:, 0], x[[0, 2, 3, 4, 6, 6], 0])
+    bil = oracle.subsample(x, s, oracle.SUB_BILINEAR)  # rows ((2j + 1) 4 - 3) / 6 = 1/6, 3/2, 17/6, ...
+    assert bil[0, 0] == pytest.approx(x[0, 0] + (x[1, 0] - x[0, 0]) / 6 + (x[0, 1] - x[0, 0]) / 6, abs=1e-12)
+    assert bil[2, 0] == pytest.approx((1 - 5 / 6) * x[2, 0] + 5 / 6 * x[3, 0] + (x[2, 1] - x[2, 0]) / 6, abs=1e-12)
+    up = oracle.upsample(np.arange(4.0)[None, :].repeat(2, 0), s, 2, 5)  # columns ((2X + 1) 3 - 4) / 8
+    np.testing.assert_allclose(up[0], [0.0, 5 / 8, 11 / 8, 17 / 8, 23 / 8], atol=1e-15)
+    assert oracle.lowres_radius(16, Fraction(5, 2)) == 6 and oracle.lowres_radius(5, s) == 4
+    assert oracle.lowres_shape(10, 7, Fraction(5, 2)) == (4, 3)
+    with pytest.raises(ValueError):
+        oracle.subsample(x, s, oracle.SUB_BOX)
+
+
+def test_integer_ratio_given_as_fraction_is_the_integer_ratio():
+    rng = _rng(61)
+    I = rng.uniform(0, 1, (1, 1, 24, 20))
+    p = rng.uniform(0, 1, (1, 2, 24, 20))
+    np.testing.assert_array_equal(oracle.fast_guided_filter(I, p, 8, 1e-2, Fraction(8, 2), oracle.SUB_BILINEAR),
+                                  oracle.fast_guided_filter(I, p, 8, 1e-2, 4, oracle.SUB_BILINEAR))
+
+
 def test_antialiased_subsample_hand_weights():
     # R11 at s = 4 along y on an image constant along x: interior rows take the taps 4j-2 .. 4j+5 with
     # weights (1, 3, 5, 7, 7, 5, 3, 1) / 32; the top row loses taps -2, -1 and renormalises the rest,
@@ -229,10 +290,12 @@ def test_s1_equals_separately_coded_guided_filter(seed, H, W, r, eps):
 
 
 @pytest.mark.parametrize("s,mode,CI", [(2, 0, 1), (4, 1, 1), (4, 2, 3), (8, 1, 3), (3, 0, 3), (1, 1, 1), (4, 3, 1),
-                                       (3, 3, 3)])
+                                       (3, 3, 3), (Fraction(5, 2), 1, 1), (Fraction(3, 2), 0, 3),
+                                       (Fraction(5, 2), 3, 1)])
 def test_fgf_matches_torch_restatement(s, mode, CI):
-    rng = _rng(s * 10 + mode)
-    N, C, H, W = 2, 3, 6 * s, 5 * s
+    # sizes are multiples of sn, so the low-res grid is H sd / sn and torch's size-based scale equals s
+    rng = _rng(int(s * 10) + mode)
+    N, C, H, W = 2, 3, 6 * Fraction(s).numerator, 5 * Fraction(s).numerator
     I = rng.uniform(0, 1, (N, CI, H, W))
     p = rng.uniform(0, 1, (N, C, H, W))
     r_low = 2
