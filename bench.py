@@ -21,6 +21,7 @@ import statistics
 import subprocess
 import sys
 import time
+from fractions import Fraction
 
 import numpy as np
 import torch
@@ -353,6 +354,13 @@ def run_native(args, world, rank, local):
             ms_m = time_steps([(stream, call)], max(20, args.steps // 10), args.warmup, world, 10, use_graph)
             modes[mname] = {"ms_per_step": round(ms_m, 5), "mp_per_s": round(world * mp / (ms_m / 1e3), 1)}
         out["subsample_modes"] = modes
+        # ---- a non-integer ratio (generic kernels): s = 5/2 and 10/3 on the same workload
+        ratios = {}
+        for sr in (Fraction(5, 2), Fraction(10, 3)):
+            call = (lambda sr=sr: gf.fast_guided_filter(I, p, R, EPS, sr, MODE, out=q, stream=stream, ctx=ctx))
+            ms_r = time_steps([(stream, call)], max(20, args.steps // 10), args.warmup, world, 10, use_graph)
+            ratios[str(sr)] = {"ms_per_step": round(ms_r, 5), "mp_per_s": round(world * mp / (ms_r / 1e3), 1)}
+        out["non_integer_ratio"] = ratios
 
         # ---- trainable layer: batch 16 x 3 x 1024^2 guide, low-res p 16 x 3 x 256^2, s = 4 box, r' = 2, eps = 1e-2
         Ib = torch.rand((16, 3, 1024, 1024), device=dev)

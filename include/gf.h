@@ -98,6 +98,11 @@ typedef struct gf_ctx gf_ctx;
  *                   split across GPUs: each filters its own rows from the (replicated) input, and no data
  *                   is exchanged.  Not combined with a_out, b_out, mean_a_out, mean_b_out or stats_out;
  *                   forward only.
+ *   s_num, s_den    0, 0: the call's integer ratio s.  Otherwise the ratio is s_num / s_den >= 1 (for
+ *                   example 5 / 2), replacing s: the same coordinate maps with that s, decided exactly in
+ *                   integer arithmetic; h = ceil(H s_den / s_num).  A non-integer ratio takes nearest,
+ *                   bilinear or antialiased subsampling, FP32 or FP16 storage, a gray or depthwise guide,
+ *                   no row range; forward only.
  *   color_guide     nonzero: I has guide_channels = 3 channels used jointly as a colour guide for every
  *                   channel of p (the guided filter's colour form, which the paper cites): per window
  *                   a = (Sigma + eps U)^-1 cov_Ip with Sigma the 3 x 3 covariance of I', b = mean_p - a^T
@@ -123,6 +128,8 @@ typedef struct gf_opts {
     int row_begin;
     int row_end;
     int color_guide;
+    int s_num;
+    int s_den;
 } gf_opts;
 
 /* Default options: batch 1, gray guide, derived r', full-res p, FP32 in and out, nothing optional. */

@@ -4,8 +4,10 @@ This module only marshals arguments; every step of the filter runs in the librar
 library cannot be loaded the calls raise -- there is no CPU fallback.
 """
 import ctypes
+import math
 import os
 import threading
+from fractions import Fraction
 
 import torch
 
@@ -50,6 +52,8 @@ class GFOpts(ctypes.Structure):
         ("row_begin", ctypes.c_int),
         ("row_end", ctypes.c_int),
         ("color_guide", ctypes.c_int),
+        ("s_num", ctypes.c_int),
+        ("s_den", ctypes.c_int),
     ]
 
 
@@ -156,19 +160,36 @@ def opts_init():
     return o
 
 
+def _integer_ratio(s):
+    f = Fraction(s)
+    if f.denominator != 1:
+        raise ValueError("this call takes an integer ratio s")
+    return int(f)
+
+
 def lowres_geometry(H, W, s, r, r_low=-1):
     h, w, rp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    check(load_library().gf_lowres_geometry(int(H), int(W), int(s), int(r), int(r_low), ctypes.byref(h),
+    check(load_library().gf_lowres_geometry(int(H), int(W), _integer_ratio(s), int(r), int(r_low), ctypes.byref(h),
                                             ctypes.byref(w), ctypes.byref(rp)))
     return h.value, w.value, rp.value
+
+
+def _ratio(o, s):
+    """The integer s to pass with options `o`: an integer ratio as it is; a non-integer one (a Fraction, or
+    a float that is an exact binary fraction such as 2.5) goes into o.s_num / o.s_den."""
+    f = Fraction(s)
+    if f.denominator == 1:
+        return int(f)
+    o.s_num, o.s_den = f.numerator, f.denominator
+    return math.ceil(f)
 
 
 def row_band(H, W, s, r, row_begin, row_end, r_low=-1, mode="bilinear"):
     """(row0, rows): the full-res input rows a call restricted to output rows [row_begin, row_end) reads."""
     a, b = ctypes.c_int(), ctypes.c_int()
     m = MODES[mode] if isinstance(mode, str) else int(mode)
-    check(load_library().gf_row_band(int(H), int(W), int(s), int(r), int(r_low), m, int(row_begin), int(row_end),
-                                     ctypes.byref(a), ctypes.byref(b)))
+    check(load_library().gf_row_band(int(H), int(W), _integer_ratio(s), int(r), int(r_low), m, int(row_begin),
+                                     int(row_end), ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
 
 
@@ -287,6 +308,7 @@ def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowr
     o.batch = N
     o.guide_channels = CI
     o.r_low = -1 if r_low is None else int(r_low)
+    s = _ratio(o, s)
     o.p_lowres = int(bool(p_lowres))
     o.dtype_in = _DTYPES[I.dtype]
     o.dtype_out = _DTYPES[out_dtype]
@@ -347,6 +369,7 @@ def fast_guided_filter_host(I, p, r, eps, s=4, mode="bilinear", *, out=None, out
     o.batch = N
     o.guide_channels = CI
     o.r_low = -1 if r_low is None else int(r_low)
+    s = _ratio(o, s)
     o.dtype_in = _DTYPES[I.dtype]
     o.dtype_out = _DTYPES[out_dtype]
     ctx = ctx or default_context(device)
@@ -383,6 +406,7 @@ def fast_guided_filter_backward(I, p, dq, r, eps, s=4, mode="bilinear", *, r_low
     o.batch = N
     o.guide_channels = CI
     o.r_low = -1 if r_low is None else int(r_low)
+    s = _ratio(o, s)
     o.p_lowres = int(bool(p_lowres))
     ctx = ctx or default_context(I.device.index)
     m = MODES[mode] if isinstance(mode, str) else int(mode)

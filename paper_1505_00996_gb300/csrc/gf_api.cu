@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -60,12 +61,19 @@ gf_status grow(void **buf, size_t *have, size_t need, const char *what)
     return GF_OK;
 }
 
-int lowres_radius(int r, int s)
+int lowres_radius_q(int r, int sn, int sd)
 {
-    if (s == 1) return r;
-    int rl = (2 * r + s) / (2 * s);  // r/s rounded half up
+    if (sn == sd) return r;
+    int rl = (int)((2LL * r * sd + sn) / (2LL * sn));  // r/s rounded half up
     if (r >= 1 && rl < 1) rl = 1;
     return rl;
+}
+int lowres_radius(int r, int s) { return lowres_radius_q(r, s, 1); }
+
+int gcd_int(int a, int b)
+{
+    while (b) { const int t = a % b; a = b; b = t; }
+    return a;
 }
 
 struct DeviceGuard {
@@ -111,10 +119,31 @@ gf_status resolve(int H, int W, int C, int r, float eps, int s, int mode, const 
     if (o->dtype_in < GF_F32 || o->dtype_in > GF_U8) return fail(GF_EINVAL, "unknown dtype_in");
     if (o->dtype_out != GF_F32 && o->dtype_out != GF_F16) return fail(GF_EINVAL, "dtype_out must be GF_F32 or GF_F16");
     if ((long long)H * W > (1LL << 31) - 1) return fail(GF_EINVAL, "H * W must be < 2^31");
-    R.N = o->batch; R.C = C; R.CI = CI; R.H = H; R.W = W; R.s = s; R.mode = mode;
-    R.h = (H + s - 1) / s;
-    R.w = (W + s - 1) / s;
-    R.r_low = o->r_low >= 0 ? o->r_low : lowres_radius(r, s);
+    // the ratio: the integer s, or s_num / s_den in lowest terms (R13)
+    int sn = s, sd = 1;
+    if (o->s_num != 0 || o->s_den != 0) {
+        if (o->s_num < 1 || o->s_den < 1 || o->s_num < o->s_den)
+            return fail(GF_EINVAL, "s_num / s_den must be a ratio >= 1");
+        const int g = gcd_int(o->s_num, o->s_den);
+        sn = o->s_num / g;
+        sd = o->s_den / g;
+    }
+    if (sd != 1) {
+        if (mode == GF_SUB_BOX) return fail(GF_EINVAL, "box subsampling needs an integer ratio");
+        if (o->dtype_in == GF_U8) return fail(GF_EINVAL, "uint8 input needs an integer ratio");
+        if (R.color) return fail(GF_EINVAL, "the colour guide needs an integer ratio");
+        if (o->row_begin != 0 || o->row_end != 0) return fail(GF_EINVAL, "a row range needs an integer ratio");
+        // the kernels form (2X + 1) sd - sn and (2j + 3) sn in 32-bit integers
+        if ((2LL * std::max(H, W) + 1) * sd + sn > INT32_MAX || (2LL * std::max(H, W) + 3) * sn > INT32_MAX)
+            return fail(GF_EINVAL, "s_num, s_den too large for the image size");
+    }
+    R.N = o->batch; R.C = C; R.CI = CI; R.H = H; R.W = W; R.mode = mode;
+    R.sn = sn;
+    R.sd = sd;
+    R.s = (sn + sd - 1) / sd;  // = s for an integer ratio; sizes launches otherwise
+    R.h = (int)(((long long)H * sd + sn - 1) / sn);
+    R.w = (int)(((long long)W * sd + sn - 1) / sn);
+    R.r_low = o->r_low >= 0 ? o->r_low : lowres_radius_q(r, sn, sd);
     if (R.r_low > gfk::MAX_LOWRES_RADIUS) return fail(GF_EINVAL, "low-res radius r' > 128 is not supported");
     R.eps = eps;
     if (!isfinite(o->detail_gain)) return fail(GF_EINVAL, "detail_gain must be finite");
@@ -175,6 +204,7 @@ FwdPlan make_plan(const Resolved &R, const Layout &L, const void *I, const void 
     FwdPlan P;
     P.N = R.N; P.C = R.C; P.CI = R.CI; P.H = R.H; P.W = R.W; P.h = R.h; P.w = R.w; P.s = R.s;
     P.r_low = R.r_low; P.mode = R.mode; P.eps = R.eps; P.dt_in = R.dt_in; P.dt_out = R.dt_out;
+    P.sn = R.sn; P.sd = R.sd;
     P.p_lowres = R.p_lowres;
     const size_t row_off = (size_t)R.row0 * R.W;  // first element of the filtered band in each plane
     P.I = (const char *)I + row_off * dtype_size(R.dt_in);
@@ -257,6 +287,7 @@ gf_status check_backward(const Resolved &R)
     if (R.mode == GF_SUB_BILINEAR_AA && R.s > 1) return fail(GF_EINVAL, "antialiased subsampling is forward only");
     if (R.Yw1 - R.Yw0 != R.H) return fail(GF_EINVAL, "a row range is forward only");
     if (R.color) return fail(GF_EINVAL, "the colour guide is forward only");
+    if (R.sd != 1) return fail(GF_EINVAL, "a non-integer ratio is forward only");
     return GF_OK;
 }
 

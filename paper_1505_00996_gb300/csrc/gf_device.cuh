@@ -50,16 +50,20 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Upsampling taps along one axis: full-res index X samples position (X + 1/2)/s - 1/2 = (2X + 1 - s)/(2s),
-// clamped to [0, n-1].  Integer arithmetic keeps the taps exact.
-__device__ __forceinline__ void up_taps(int X, int s, int n, int &i0, int &i1, float &f)
+// Upsampling taps along one axis at ratio s = sn / sd: full-res index X samples position
+// (X + 1/2)/s - 1/2 = ((2X + 1) sd - sn)/(2 sn), clamped to [0, n-1].  Integer arithmetic keeps the taps exact.
+__device__ __forceinline__ void up_taps_q(int X, int sn, int sd, int n, int &i0, int &i1, float &f)
 {
-    const int num = 2 * X + 1 - s, den = 2 * s;
+    const int num = (2 * X + 1) * sd - sn, den = 2 * sn;
     if (num <= 0) { i0 = 0; i1 = 0; f = 0.0f; return; }
     const int qt = num / den, rem = num - qt * den;
     if (qt >= n - 1) { i0 = n - 1; i1 = n - 1; f = 0.0f; return; }
     i0 = qt; i1 = qt + 1; f = (float)rem / (float)den;
 }
+__device__ __forceinline__ void up_taps(int X, int s, int n, int &i0, int &i1, float &f) { up_taps_q(X, s, 1, n, i0, i1, f); }
+
+// floor(a / b) for b > 0 and any sign of a.
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 // Subsampling taps along one axis for low-res index j (Algorithm 2 first step, gf.h conventions): the
 // full-res positions t0, t1 that the sample reads and the weight f of t1 (nearest: t0 = t1, f = 0).  Box mode

@@ -44,6 +44,7 @@ struct SubJob {
     float *dst;
     int planes, H, W, s;
     size_t sps, dps;  // source / destination plane strides (elements)
+    int sn, sd;       // the ratio as sn / sd (s = sn, sd = 1 for an integer ratio)
 };
 struct SubParams {
     SubJob job[2];
@@ -51,20 +52,28 @@ struct SubParams {
     float scale;  // result multiplier: k on the uint8 path (exact integers J = k * value), else 1
 };
 
+// The source taps of a bilinear sample at ratio sn / sd: position ((2j + 1) sn - sd) / (2 sd), clamped.
+__device__ __forceinline__ void sub_bilinear_taps(int j, int sn, int sd, int n, int &t0, float &f)
+{
+    const int num = (2 * j + 1) * sn - sd, den = 2 * sd;
+    t0 = num / den;  // num >= 0 since sn >= sd
+    f = (float)(num - t0 * den) / (float)den;
+    if (t0 >= n - 1) { t0 = n - 1; f = 0.0f; }
+}
+
 template <typename T, int MODE>
-__device__ __forceinline__ float subsample_one(const T *src, int H, int W, int s, int j, int i)
+__device__ __forceinline__ float subsample_one(const T *src, int H, int W, int s, int sn, int sd, int j, int i)
 {
     if (MODE == GF_SUB_NEAREST || s == 1) {
-        const int sy = min(((2 * j + 1) * s) >> 1, H - 1);  // floor((j + 1/2) s)
-        const int sx = min(((2 * i + 1) * s) >> 1, W - 1);
+        const int sy = min(((2 * j + 1) * sn) / (2 * sd), H - 1);  // floor((j + 1/2) s)
+        const int sx = min(((2 * i + 1) * sn) / (2 * sd), W - 1);
         return ldv(src + (size_t)sy * W + sx);
     } else if (MODE == GF_SUB_BILINEAR) {
-        // source coordinate (j + 1/2) s - 1/2 = ((2j+1)s - 1) / 2, clamped to [0, H-1]
-        const int ny = (2 * j + 1) * s - 1, nx = (2 * i + 1) * s - 1;
-        int y0 = ny >> 1, x0 = nx >> 1;
-        float fy = (ny & 1) ? 0.5f : 0.0f, fx = (nx & 1) ? 0.5f : 0.0f;
-        if (y0 >= H - 1) { y0 = H - 1; fy = 0.0f; }
-        if (x0 >= W - 1) { x0 = W - 1; fx = 0.0f; }
+        // source coordinate (j + 1/2) s - 1/2, clamped to [0, H-1]
+        int y0, x0;
+        float fy, fx;
+        sub_bilinear_taps(j, sn, sd, H, y0, fy);
+        sub_bilinear_taps(i, sn, sd, W, x0, fx);
         const int y1 = min(y0 + 1, H - 1), x1 = min(x0 + 1, W - 1);
         const T *r0 = src + (size_t)y0 * W, *r1 = src + (size_t)y1 * W;
         const float top = (1.0f - fx) * ldv(r0 + x0) + fx * ldv(r0 + x1);
@@ -93,7 +102,7 @@ __global__ void __launch_bounds__(SUB_NT) k_subsample(SubParams P)
 #pragma unroll
     for (int u = 0; u < SUB_JB; ++u) {
         const int j = min(j0 + u, P.h - 1);
-        v[u] = subsample_one<T, MODE>(src, J.H, J.W, J.s, j, i);
+        v[u] = subsample_one<T, MODE>(src, J.H, J.W, J.s, J.sn, J.sd, j, i);
     }
     float *dst = J.dst + (size_t)z * J.dps + i;
 #pragma unroll
@@ -117,28 +126,31 @@ __global__ void __launch_bounds__(SUB_NT) k_subsample_aa(SubParams P)
     if (z >= P.job[0].planes) z -= P.job[0].planes;
     const T *src = (const T *)J.src + (size_t)z * J.sps;
     float *dst = J.dst + (size_t)z * J.dps + i;
-    const int s = J.s, H = J.H, W = J.W;
-    if (s == 1) {  // a low-res p given by the caller: copied
+    const int H = J.H, W = J.W, sn = J.sn, sd = J.sd;
+    if (J.s == 1) {  // a low-res p given by the caller: copied
         for (int u = 0; u < SUB_JB && j0 + u < P.h; ++u) dst[(size_t)(j0 + u) * P.w] = ldv(src + (size_t)(j0 + u) * W + i);
         return;
     }
-    // taps of column i: n(x) > 0 for x in [xa, xb], clipped to the image
-    const int cx = (2 * i + 1) * s;
-    const int xa = max(0, ((cx - 2 * s - 1) >> 1) + 1), xb = min(W - 1, ((cx + 2 * s) >> 1) - 1);
+    // Weight numerator of source index t for low-res index k: 2 sn - |(2t + 1) sd - (2k + 1) sn| (over 2 sn);
+    // positive for t in [lo(k), hi(k)]: (2t + 1) sd strictly within 2 sn of (2k + 1) sn.
+    auto wnum = [&](int t, int k) { return 2 * sn - abs((2 * t + 1) * sd - (2 * k + 1) * sn); };
+    auto lo_of = [&](int k) { return floor_div((2 * k + 1) * sn - 2 * sn - sd, 2 * sd) + 1; };
+    auto hi_of = [&](int k) { return -floor_div(-((2 * k + 1) * sn + 2 * sn - sd), 2 * sd) - 1; };
+    const int xa = max(0, lo_of(i)), xb = min(W - 1, hi_of(i));
     int nx = 0;
-    for (int x = xa; x <= xb; ++x) nx += 2 * s - abs(2 * x + 1 - cx);
+    for (int x = xa; x <= xb; ++x) nx += wnum(x, i);
     const int jl = min(j0 + SUB_JB, P.h) - 1;  // last low-res row of the block
-    const int ya = max(0, ((2 * j0 - 1) * s - 1 >> 1) + 1), yb = min(H - 1, ((2 * jl + 3) * s >> 1) - 1);
+    const int ya = max(0, lo_of(j0)), yb = min(H - 1, hi_of(jl));
     float acc[SUB_JB];
 #pragma unroll
     for (int u = 0; u < SUB_JB; ++u) acc[u] = 0.0f;
     for (int y = ya; y <= yb; ++y) {
         const T *row = src + (size_t)y * W;
         float hs = 0.0f;
-        for (int x = xa; x <= xb; ++x) hs = fmaf((float)(2 * s - abs(2 * x + 1 - cx)), ldv(row + x), hs);
+        for (int x = xa; x <= xb; ++x) hs = fmaf((float)wnum(x, i), ldv(row + x), hs);
 #pragma unroll
         for (int u = 0; u < SUB_JB; ++u) {
-            const int ny = 2 * s - abs(2 * y + 1 - (2 * (j0 + u) + 1) * s);
+            const int ny = wnum(y, j0 + u);
             if (ny > 0) acc[u] = fmaf((float)ny, hs, acc[u]);
         }
     }
@@ -146,10 +158,9 @@ __global__ void __launch_bounds__(SUB_NT) k_subsample_aa(SubParams P)
     for (int u = 0; u < SUB_JB; ++u) {
         const int j = j0 + u;
         if (j >= P.h) break;
-        const int cy = (2 * j + 1) * s;
-        const int ja = max(0, ((cy - 2 * s - 1) >> 1) + 1), jb = min(H - 1, ((cy + 2 * s) >> 1) - 1);
+        const int ja = max(0, lo_of(j)), jb = min(H - 1, hi_of(j));
         int ny = 0;
-        for (int y = ja; y <= jb; ++y) ny += 2 * s - abs(2 * y + 1 - cy);
+        for (int y = ja; y <= jb; ++y) ny += wnum(y, j);
         dst[(size_t)j * P.w] = acc[u] / ((float)nx * (float)ny) * P.scale;
     }
 }
@@ -726,6 +737,7 @@ struct UpParams {
     size_t lps;                       // low-res plane stride
     int LRmax, LCmax;                 // staged low-res tile bounds (rows, columns)
     float detail;                     // detail gain k: output q + k (I - q) (0: q itself)
+    int sn, sd;                       // the ratio as sn / sd (generic kernel; s = sn, sd = 1 if integer)
     size_t fps;                       // plane stride of the full-res I and q (elements)
     int Yw0, Yw1;                     // rows written: [Yw0, Yw1) of the H rows
 };
@@ -846,10 +858,10 @@ __global__ void __launch_bounds__(UP_NT) k_upsample_output(UpParams P)
     // low-res rows / columns this CTA samples
     int ly0, ly1, lx0, lx1, t0, t1;
     float ft;
-    up_taps(Yb, P.s, P.h, ly0, t0, ft);
-    up_taps(Ye - 1, P.s, P.h, t0, ly1, ft);
-    up_taps(Xb, P.s, P.w, lx0, t1, ft);
-    up_taps(min(Xb + UP_BAND, P.W) - 1, P.s, P.w, t1, lx1, ft);
+    up_taps_q(Yb, P.sn, P.sd, P.h, ly0, t0, ft);
+    up_taps_q(Ye - 1, P.sn, P.sd, P.h, t0, ly1, ft);
+    up_taps_q(Xb, P.sn, P.sd, P.w, lx0, t1, ft);
+    up_taps_q(min(Xb + UP_BAND, P.W) - 1, P.sn, P.sd, P.w, t1, lx1, ft);
     const int LR = ly1 - ly0 + 1, LC = lx1 - lx0 + 1;
     const int tile = P.LRmax * P.LCmax;
     for (int mr = 0; mr < CC * 2 * LR; ++mr) {  // (map, row) pairs; mc = cc * 2 + map
@@ -880,7 +892,7 @@ __global__ void __launch_bounds__(UP_NT) k_upsample_output(UpParams P)
     float fx[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        up_taps(min(X0 + k, P.W - 1), P.s, P.w, xa[k], xb[k], fx[k]);
+        up_taps_q(min(X0 + k, P.W - 1), P.sn, P.sd, P.w, xa[k], xb[k], fx[k]);
         xa[k] -= lx0;
         xb[k] -= lx0;
     }
@@ -916,7 +928,7 @@ __global__ void __launch_bounds__(UP_NT) k_upsample_output(UpParams P)
             if (Y >= Ye) break;
             int ya, yb;
             float fy;
-            up_taps(Y, P.s, P.h, ya, yb, fy);
+            up_taps_q(Y, P.sn, P.sd, P.h, ya, yb, fy);
             if (ya != cur0) {
                 if (ya == cur1) {
 #pragma unroll
@@ -1238,7 +1250,7 @@ void launch_up_t(UpParams up, int N, int CC, bool vec, cudaStream_t st)
 #undef GF_S1
         return;
     }
-    if (vec && (up.s == 4 || up.s == 8)) {
+    if (vec && up.sd == 1 && (up.s == 4 || up.s == 8)) {
         up.R = 8 * up.s;  // 8 low-res rows per CTA
         up.LRmax = up.R / up.s + 2;
         up.LCmax = UP_BAND / up.s + 2;
@@ -1249,11 +1261,15 @@ void launch_up_t(UpParams up, int N, int CC, bool vec, cudaStream_t st)
         else k_upsample_output_s4x<TI, TQ, 8><<<grid, UP_NT, smem, st>>>(up);
         return;
     }
-    up.LRmax = (up.R + up.s - 1) / up.s + 2;
-    up.LCmax = (UP_BAND + up.s - 1) / up.s + 2;
+    up.LRmax = (up.R * up.sd + up.sn - 1) / up.sn + 2;  // ceil(R / s) + 2 tap rows under R full-res rows
+    up.LCmax = (UP_BAND * up.sd + up.sn - 1) / up.sn + 2;
     dim3 grid(bands, (up.H + up.R - 1) / up.R, N * up.CG);
     const size_t smem = (size_t)CC * 2 * up.LRmax * up.LCmax * sizeof(float);
-#define GF_UP(cc, v) k_upsample_output<TI, TQ, cc, v><<<grid, UP_NT, smem, st>>>(up)
+#define GF_UP(cc, v)                                                                 \
+    do {                                                                             \
+        if (opt_in_smem(k_upsample_output<TI, TQ, cc, v>, smem) == cudaSuccess)      \
+            k_upsample_output<TI, TQ, cc, v><<<grid, UP_NT, smem, st>>>(up);         \
+    } while (0)
     if (CC == 3) { if (vec) GF_UP(3, true); else GF_UP(3, false); }
     else { if (vec) GF_UP(1, true); else GF_UP(1, false); }
 #undef GF_UP
@@ -1267,7 +1283,7 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 // (The whole-plane stride is H * W of the whole image, a multiple of 4 floats, so every plane is aligned.)
 bool aligned_fp32_wide_subsample(const FwdPlan &P)
 {
-    return (P.dt_in == F32) && (P.mode == GF_SUB_BOX || P.mode == GF_SUB_BILINEAR_AA) &&
+    return (P.dt_in == F32) && (P.mode == GF_SUB_BOX || P.mode == GF_SUB_BILINEAR_AA) && P.sd == 1 &&
            (P.s == 2 || P.s == 4 || P.s == 8) && (P.H % P.s == 0) && (P.W % P.s == 0) && (P.W % 4 == 0) &&
            aligned16(P.I) && (P.p_lowres || aligned16(P.p));  // a low-res p is only copied
 }
@@ -1275,7 +1291,7 @@ bool aligned_fp32_wide_subsample(const FwdPlan &P)
 bool aligned_fp32_subsample(const FwdPlan &P)
 {
     return (P.dt_in == F32) && !P.p_lowres && (P.mode == GF_SUB_NEAREST || P.mode == GF_SUB_BILINEAR) &&
-           (P.s == 2 || P.s == 4 || P.s == 8) &&
+           P.sd == 1 && (P.s == 2 || P.s == 4 || P.s == 8) &&
            (P.H % P.s == 0) && (P.W % P.s == 0) && (P.W % 4 == 0) && aligned16(P.I) && aligned16(P.p);
 }
 
@@ -1343,11 +1359,11 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         sp.h = P.h; sp.w = P.w; sp.mode = P.mode;
         // uint8 path: carry the subsampled values as exact integers J = k * (value in 1/255 units)
         sp.scale = P.int_stats ? P.int_scale / 255.0f : 1.0f;
-        sp.job[0] = SubJob{P.I, P.Il, P.N * P.CI, P.H, P.W, P.s, P.fps, P.lps};
+        sp.job[0] = SubJob{P.I, P.Il, P.N * P.CI, P.H, P.W, P.s, P.fps, P.lps, P.sn, P.sd};
         if (!P.p_lowres)
-            sp.job[1] = SubJob{P.p, P.pl, planesNC, P.H, P.W, P.s, P.fps, P.lps};
+            sp.job[1] = SubJob{P.p, P.pl, planesNC, P.H, P.W, P.s, P.fps, P.lps, P.sn, P.sd};
         else  // a low-res p is only copied into the FP32 workspace
-            sp.job[1] = SubJob{P.p, P.pl, planesNC, P.h, P.w, 1, P.lpin, P.lps};
+            sp.job[1] = SubJob{P.p, P.pl, planesNC, P.h, P.w, 1, P.lpin, P.lps, 1, 1};
         const int nz = P.N * P.CI + (self_guided ? 0 : planesNC);
         const bool vec_ok = aligned_fp32_subsample(P);
         tm.before();
@@ -1432,6 +1448,8 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         UpParams up{};
         up.I = P.I; up.ma = P.ma; up.mb = P.mb; up.q = P.q;
         up.detail = P.detail;
+        up.sn = P.sn;
+        up.sd = P.sd;
         up.fps = P.fps;
         up.Yw0 = P.Yw0;
         up.Yw1 = P.Yw1;

@@ -26,6 +26,7 @@ inline size_t plane_stride_f32(size_t elems) { return (elems + 63) & ~size_t(63)
 // Everything one forward call needs, resolved on the host.
 struct FwdPlan {
     int N, C, CI, H, W, h, w, s, r_low, mode;
+    int sn = 1, sd = 1;  // the ratio as sn / sd; s = sn when sd = 1, else ceil(sn / sd) (sizes launches only)
     float eps;
     int dt_in, dt_out;
     bool p_lowres;
@@ -84,6 +85,7 @@ gf_status server_pause(Server *s, int paused);
 // A forward call's arguments, checked and resolved on the host (gf_api.cu).
 struct Resolved {
     int N, C, CI, H, W, h, w, s, r_low, mode, dt_in, dt_out;
+    int sn, sd;  // the ratio s = sn / sd (sd = 1 for an integer ratio; then s = sn)
     bool p_lowres, dense_lowres, int_stats;
     float eps, int_scale;
     float detail;  // detail gain (gf_opts.detail_gain)

@@ -35,7 +35,8 @@ class Server:
         req = binding.GFRequest()
         self.lib.gf_opts_init(ctypes.byref(req.opts))
         req.I, req.p, req.q = I4.data_ptr(), p4.data_ptr(), q.data_ptr()
-        req.H, req.W, req.C, req.r, req.eps, req.s = H, W, C, int(r), float(eps), int(s)
+        req.H, req.W, req.C, req.r, req.eps = H, W, C, int(r), float(eps)
+        req.s = binding._ratio(req.opts, s)  # a non-integer ratio travels in the options
         req.mode = binding.MODES[mode] if isinstance(mode, str) else int(mode)
         req.opts.batch = N
         req.opts.guide_channels = CI

@@ -5,6 +5,8 @@ the same seeded inputs: tiny, ragged and multi-tile shapes, every subsample mode
 depthwise guides, the 512 x 512 and 12 MP workloads, and the intermediates (a, b, their means, the window
 statistics).  Tolerance: max-abs 1e-4 on [0, 1] data for FP32 (2e-3 for FP16 storage).
 """
+from fractions import Fraction
+
 import numpy as np
 import pytest
 import torch
@@ -306,3 +308,45 @@ def test_precision_variants_at_12mp(gf, scene12mp):
     assert report["f32"][0] <= TOL_F32
     assert report["f16"][0] <= TOL_F16
     assert report["u8"][0] <= TOL_F32
+
+
+RATIONAL_CASES = [  # (N, CI, C, H, W, r, eps, s, mode, dtype)
+    (1, 1, 3, 300, 704, 16, 1e-3, Fraction(5, 2), 1, torch.float32),
+    (1, 1, 1, 61, 43, 6, 1e-3, Fraction(3, 2), 0, torch.float32),
+    (1, 1, 2, 203, 408, 16, 1e-3, Fraction(7, 4), 3, torch.float32),
+    (2, 3, 3, 97, 130, 8, 1e-2, Fraction(4, 3), 1, torch.float32),   # not a binary fraction; depthwise, batch
+    (1, 1, 3, 480, 640, 12, 1e-2, Fraction(9, 4), 1, torch.float16),
+    (1, 1, 1, 5, 3, 4, 1e-2, Fraction(5, 2), 1, torch.float32),       # tiny, every tap clamped
+    (1, 1, 3, 1000, 1500, 20, 1e-3, Fraction(10, 3), 1, torch.float32),
+]
+
+
+@pytest.mark.parametrize("case", RATIONAL_CASES, ids=lambda c: "%dx%d_s%s_m%d_%s" % (c[3], c[4], str(c[7]).replace("/", "o"),
+                                                                                       c[8], str(c[9]).split(".")[-1]))
+def test_non_integer_ratio_parity(gf, case):
+    N, CI, C, H, W, r, eps, s, mode, dtype = case
+    I = _rand((N, CI, H, W), 11 + H)
+    p = _rand((N, C, H, W), 12 + W)
+    if dtype == torch.float16:
+        I, p = I.astype(np.float16), p.astype(np.float16)
+    q = gf.fast_guided_filter(torch.from_numpy(I).cuda(), torch.from_numpy(p).cuda(), r, eps, s, MODE_NAMES[mode])
+    torch.cuda.synchronize()
+    ref = oracle_q(I.astype(np.float64), p.astype(np.float64), r, eps, s, mode)
+    err = max_abs(q.float().cpu().numpy(), ref)
+    assert err <= (TOL_F16 if dtype == torch.float16 else TOL_F32), "max-abs error %.3g" % err
+
+
+def test_non_integer_ratio_argument_checks(gf):
+    I = torch.rand(1, 1, 64, 64, device="cuda")
+    for mode in ("box",):
+        with pytest.raises(gf.GFError):
+            gf.fast_guided_filter(I, I, 8, 1e-2, Fraction(5, 2), mode)
+    with pytest.raises(gf.GFError):
+        gf.fast_guided_filter((I * 255).to(torch.uint8), (I * 255).to(torch.uint8), 8, 1e-2, Fraction(5, 2))
+    with pytest.raises(gf.GFError):
+        gf.fast_guided_filter_backward(I, I, I, 8, 1e-2, Fraction(5, 2))
+    # an integer written as a fraction is the integer ratio
+    a = gf.fast_guided_filter(I, I, 8, 1e-2, Fraction(8, 2))
+    b = gf.fast_guided_filter(I, I, 8, 1e-2, 4)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
