@@ -36,7 +36,8 @@ namespace gfk {
 // ------------------------------------------------------------------------------------------------------
 // k_subsample
 // ------------------------------------------------------------------------------------------------------
-constexpr int SUB_NT = 128;  // threads per CTA (one low-res column each)
+constexpr int SUB_NT = 128;      // threads per CTA (one low-res column each)
+constexpr int SUB_NT_VEC = 256;  // the same for the aligned FP32 nearest/bilinear kernel (measured best)
 constexpr int SUB_JB = 4;    // low-res rows per thread
 
 struct SubJob {
@@ -256,37 +257,72 @@ __global__ void __launch_bounds__(SUB_NT) k_subsample_wide(SubParams P)
     }
 }
 
-// Aligned FP32 fast path of k_subsample for s = 2, 4, 8 with H and W multiples of s (so no sample is
-// clamped): the two (bilinear) or one (nearest) source columns of a low-res pixel lie in one 8- or 16-byte
-// chunk (two for s = 8), read with one vector load per source row.
-template <int MODE, int S>
-__global__ void __launch_bounds__(SUB_NT) k_subsample_vec(SubParams P)
+// The two source columns a bilinear sample at ratio S reads (S/2 - 1 and S/2 of the block; the sample
+// twice for nearest, column S/2), from one aligned vector load of the block's first S (S <= 4) or 8 (S = 8:
+// columns 3 and 4) values.  FP32, FP16 (converted) or uint8 (raw byte values, as ldv gives them).
+template <typename T, int S, int MODE>
+__device__ __forceinline__ float2 ld_block_pair(const T *rp)
 {
-    constexpr int JB = (S == 8) ? 4 : 8;
-    const int i = blockIdx.x * SUB_NT + threadIdx.x;
+    float v0, v1;  // columns S/2 - 1 and S/2
+    if constexpr (sizeof(T) == 4) {
+        if constexpr (S == 2) {
+            const float2 t = __ldcs(reinterpret_cast<const float2 *>(rp));
+            v0 = t.x; v1 = t.y;
+        } else if constexpr (S == 4) {
+            const float4 t = __ldcs(reinterpret_cast<const float4 *>(rp));
+            v0 = t.y; v1 = t.z;
+        } else {
+            const float4 b = __ldcs(reinterpret_cast<const float4 *>(rp + 4));
+            v1 = b.x;
+            v0 = (MODE == GF_SUB_BILINEAR) ? __ldcs(reinterpret_cast<const float4 *>(rp)).w : b.x;
+        }
+    } else if constexpr (sizeof(T) == 2) {
+        if constexpr (S == 2) {
+            const unsigned t = __ldcs(reinterpret_cast<const unsigned *>(rp));
+            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&t));
+            v0 = f.x; v1 = f.y;
+        } else if constexpr (S == 4) {
+            const uint2 t = __ldcs(reinterpret_cast<const uint2 *>(rp));
+            const float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
+            const float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));
+            v0 = lo.y; v1 = hi.x;
+        } else {
+            const uint4 t = __ldcs(reinterpret_cast<const uint4 *>(rp));
+            const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));  // columns 2, 3
+            const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&t.z));  // columns 4, 5
+            v0 = a.y; v1 = b.x;
+        }
+    } else {
+        if constexpr (S == 2) {
+            const unsigned short t = __ldcs(reinterpret_cast<const unsigned short *>(rp));
+            v0 = (float)(t & 0xffu); v1 = (float)(t >> 8);
+        } else if constexpr (S == 4) {
+            const unsigned t = __ldcs(reinterpret_cast<const unsigned *>(rp));
+            v0 = (float)((t >> 8) & 0xffu); v1 = (float)((t >> 16) & 0xffu);
+        } else {
+            const uint2 t = __ldcs(reinterpret_cast<const uint2 *>(rp));
+            v0 = (float)(t.x >> 24); v1 = (float)(t.y & 0xffu);
+        }
+    }
+    return MODE == GF_SUB_BILINEAR ? make_float2(v0, v1) : make_float2(v1, v1);
+}
+
+// Aligned fast path of k_subsample (nearest / bilinear) for s = 2, 4, 8 with H and W multiples of s (so no
+// sample is clamped): the one or two source columns of a low-res pixel are read with one vector load per
+// source row (two for FP32 at s = 8).
+template <typename T, int MODE, int S>
+__global__ void __launch_bounds__(SUB_NT_VEC) k_subsample_vec(SubParams P)
+{
+    constexpr int JB = (S == 8) ? 1 : 2;  // low-res rows per thread: short threads, many of them (measured best)
+    const int i = blockIdx.x * SUB_NT_VEC + threadIdx.x;
     const int j0 = blockIdx.y * JB;
     if (i >= P.w) return;
     int z = blockIdx.z;
     const SubJob &J = (z < P.job[0].planes) ? P.job[0] : P.job[1];
     if (z >= P.job[0].planes) z -= P.job[0].planes;
-    const float *src = (const float *)J.src + (size_t)z * J.sps;
+    const T *src = (const T *)J.src + (size_t)z * J.sps;
     const int W = J.W;
-    // source row pair (bilinear) or row (nearest) of low-res row j, and the two source columns' chunk
-    auto row_val = [&](int y) -> float2 {  // returns the two columns around the sample (bilinear) / the sample twice
-        const float *rp = src + (size_t)y * W + (size_t)i * S;
-        if (S == 2) {
-            const float2 t = __ldcs(reinterpret_cast<const float2 *>(rp));
-            return MODE == GF_SUB_BILINEAR ? t : make_float2(t.y, t.y);
-        } else if (S == 4) {
-            const float4 t = __ldcs(reinterpret_cast<const float4 *>(rp));
-            return MODE == GF_SUB_BILINEAR ? make_float2(t.y, t.z) : make_float2(t.z, t.z);
-        } else {
-            const float4 b = __ldcs(reinterpret_cast<const float4 *>(rp + 4));
-            if (MODE == GF_SUB_NEAREST) return make_float2(b.x, b.x);
-            const float4 a = __ldcs(reinterpret_cast<const float4 *>(rp));
-            return make_float2(a.w, b.x);
-        }
-    };
+    auto row_val = [&](int y) { return ld_block_pair<T, S, MODE>(src + (size_t)y * W + (size_t)i * S); };
     float2 top[JB], bot[JB];
 #pragma unroll
     for (int u = 0; u < JB; ++u) {
@@ -1288,11 +1324,13 @@ bool aligned_fp32_wide_subsample(const FwdPlan &P)
            aligned16(P.I) && (P.p_lowres || aligned16(P.p));  // a low-res p is only copied
 }
 
-bool aligned_fp32_subsample(const FwdPlan &P)
+bool aligned_vec_subsample(const FwdPlan &P)
 {
-    return (P.dt_in == F32) && !P.p_lowres && (P.mode == GF_SUB_NEAREST || P.mode == GF_SUB_BILINEAR) &&
-           P.sd == 1 && (P.s == 2 || P.s == 4 || P.s == 8) &&
-           (P.H % P.s == 0) && (P.W % P.s == 0) && (P.W % 4 == 0) && aligned16(P.I) && aligned16(P.p);
+    // every row of every plane starts on a 16-byte boundary: 16-byte aligned planes, W a multiple of 16 bytes
+    const size_t rowb = (size_t)P.W * dtype_size(P.dt_in);
+    return !P.p_lowres && (P.mode == GF_SUB_NEAREST || P.mode == GF_SUB_BILINEAR) && P.sd == 1 &&
+           (P.s == 2 || P.s == 4 || P.s == 8) && (P.H % P.s == 0) && (P.W % P.s == 0) && (rowb % 16 == 0) &&
+           ((P.fps * dtype_size(P.dt_in)) % 16 == 0) && aligned16(P.I) && aligned16(P.p);
 }
 
 }  // namespace
@@ -1365,12 +1403,17 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         else  // a low-res p is only copied into the FP32 workspace
             sp.job[1] = SubJob{P.p, P.pl, planesNC, P.h, P.w, 1, P.lpin, P.lps, 1, 1};
         const int nz = P.N * P.CI + (self_guided ? 0 : planesNC);
-        const bool vec_ok = aligned_fp32_subsample(P);
+        const bool vec_ok = aligned_vec_subsample(P);
         tm.before();
         if (vec_ok) {
-            const int jb = (P.s == 8) ? 4 : 8;
-            dim3 grid((P.w + SUB_NT - 1) / SUB_NT, (P.h + jb - 1) / jb, nz);
-#define GF_SV(m, ss) k_subsample_vec<m, ss><<<grid, SUB_NT, 0, st>>>(sp)
+            const int jb = (P.s == 8) ? 1 : 2;
+            dim3 grid((P.w + SUB_NT_VEC - 1) / SUB_NT_VEC, (P.h + jb - 1) / jb, nz);
+#define GF_SV(m, ss)                                                                       \
+    do {                                                                                   \
+        if (P.dt_in == F32) k_subsample_vec<float, m, ss><<<grid, SUB_NT_VEC, 0, st>>>(sp);    \
+        else if (P.dt_in == F16) k_subsample_vec<__half, m, ss><<<grid, SUB_NT_VEC, 0, st>>>(sp); \
+        else k_subsample_vec<uint8_t, m, ss><<<grid, SUB_NT_VEC, 0, st>>>(sp);                \
+    } while (0)
             if (P.mode == GF_SUB_BILINEAR) {
                 if (P.s == 2) GF_SV(GF_SUB_BILINEAR, 2); else if (P.s == 4) GF_SV(GF_SUB_BILINEAR, 4); else GF_SV(GF_SUB_BILINEAR, 8);
             } else {

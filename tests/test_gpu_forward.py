@@ -350,3 +350,33 @@ def test_non_integer_ratio_argument_checks(gf):
     b = gf.fast_guided_filter(I, I, 8, 1e-2, 4)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("s,mode", [(2, "bilinear"), (4, "bilinear"), (8, "bilinear"), (4, "nearest")])
+@pytest.mark.parametrize("dtype", [torch.float16, torch.uint8])
+def test_vector_subsample_matches_generic_path(gf, s, mode, dtype):
+    """FP16 / uint8 storage: 16-byte aligned planes take the vector subsample, the same data one element off
+    the alignment takes the generic one; the results agree (uint8: the same exact integer window sums)."""
+    H, W, C = 256, 512, 3
+    I = torch.from_numpy(synth.make_scene(H, W, seed=31)).cuda()[None, None]
+    p = torch.from_numpy(synth.rgb_noisy_input(synth.make_scene(H, W, seed=31), seed=32)).cuda()[None]
+    if dtype == torch.uint8:
+        I, p = (I * 255).round().to(dtype), (p * 255).round().to(dtype)
+    else:
+        I, p = I.to(dtype), p.to(dtype)
+
+    def shifted(t):  # the same values at an address one element past a 16-byte boundary
+        buf = torch.empty(t.numel() + 16, dtype=t.dtype, device="cuda")
+        v = buf[1:1 + t.numel()].view(t.shape)
+        v.copy_(t)
+        return v
+
+    st_a = torch.empty((1, C, 4, -(-H // s), -(-W // s)), dtype=torch.int32 if dtype == torch.uint8 else torch.float32,
+                       device="cuda")
+    st_b = torch.empty_like(st_a)
+    qa = gf.fast_guided_filter(I, p, 4 * s, 1e-2, s, mode, stats_out=st_a)
+    qb = gf.fast_guided_filter(shifted(I), shifted(p), 4 * s, 1e-2, s, mode, stats_out=st_b)
+    torch.cuda.synchronize()
+    assert torch.equal(st_a, st_b)  # the subsampled values, hence every window sum, are identical
+    # the two output kernels round in a different order; FP16 q may differ by one unit in the last place
+    assert float((qa.float() - qb.float()).abs().max()) <= (1e-3 if dtype == torch.float16 else 1e-6)
