@@ -380,6 +380,7 @@ def run_native(args, world, rank, local):
         del Ib, pb, gq, qb
         out["applications"] = run_applications(dev, stream, ctx, world, max(20, args.steps // 10), args.warmup,
                                                use_graph)
+        out["small_images"] = run_small_images(dev, stream, ctx, world)
         if rank == 0:
             out["cpu_baseline"] = cpu_baseline(I_np, p_np)
         out["serving"] = run_serving(local)
@@ -420,6 +421,44 @@ def run_applications(dev, stream, ctx, world, steps, warmup, use_graph):
         res[name] = {"C": int(pa.shape[0]), "guide_channels": int(Ia.shape[0]), "color_guide": colg, "r": r,
                      "eps": eps, "detail_gain": gain, "ms_per_step": round(ms_a, 5),
                      "mp_per_s": round(world * Hh * Ww / 1e6 / (ms_a / 1e3), 1)}
+    return res
+
+
+# --------------------------------------------------------------------------------------------------------
+# small images: the four-kernel chain against the single fused kernel
+# --------------------------------------------------------------------------------------------------------
+
+def run_small_images(dev, stream, ctx, world, calls=200):
+    """Per-call GPU time of the chain (fused=-1) and of the single kernel (fused=1) on small gray-guided
+    images (s = 4 bilinear, eps = 1e-2): replayed from a CUDA graph, and launched call by call (queued behind
+    a spin kernel so the host is not on the clock; the time between two events around the batch)."""
+    import paper_1505_00996_gb300 as gf
+    import synth
+    res = {}
+    for (Hh, Ww, Cc, r) in ((256, 256, 1, 4), (512, 512, 1, 8), (480, 640, 3, 3), (1024, 1024, 1, 8),
+                            (720, 1280, 3, 8)):
+        Ig = torch.from_numpy(synth.make_scene(Hh, Ww, seed=12)).to(dev)
+        pc = Ig[None].repeat(Cc, 1, 1).contiguous()
+        qc = torch.empty_like(pc)
+        row = {}
+        for name, fz in (("chain", -1), ("fused", 1)):
+            fn = (lambda fz=fz: gf.fast_guided_filter(Ig, pc, r, 1e-2, 4, "bilinear", out=qc, stream=stream, ctx=ctx,
+                                                       fused=fz))
+            ms_g = time_steps([(stream, fn)], calls, 5, world, 20, True)
+            for _ in range(5):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                torch.cuda._sleep(int(0.03 * 2.0e9))
+                e0.record(stream)
+                for _ in range(calls):
+                    fn()
+                e1.record(stream)
+            torch.cuda.synchronize()
+            row[name] = {"graph_us": round(ms_g * 1e3, 2), "eager_us": round(e0.elapsed_time(e1) / calls * 1e3, 2)}
+        row["auto"] = "fused" if gf.load_library().gf_filter_kernel_count(Hh, Ww, Cc, 4, 1, None) == 1 else "chain"
+        res["%dx%d_C%d_r%d" % (Hh, Ww, Cc, r)] = row
     return res
 
 

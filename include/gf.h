@@ -39,6 +39,7 @@ extern "C" {
 
 #define GF_ABI_VERSION 2
 #define GF_MAX_STAGES 8 /* kernel stages one gf_filter call can launch (for gf_opts.kernel_events) */
+#define GF_FUSED_AUTO_PIXELS (1 << 20) /* gf_opts.fused = 0 runs the single kernel up to N*C*H*W pixels */
 
 typedef enum gf_status {
     GF_OK = 0,
@@ -103,6 +104,12 @@ typedef struct gf_ctx gf_ctx;
  *                   integer arithmetic; h = ceil(H s_den / s_num).  A non-integer ratio takes nearest,
  *                   bilinear or antialiased subsampling, FP32 or FP16 storage, a gray or depthwise guide,
  *                   no row range; forward only.
+ *   fused           0: run the whole filter as one kernel (each CTA recomputes its halo) for a subsampled
+ *                   call (s > 1) on a small image (N*C*H*W <= GF_FUSED_AUTO_PIXELS), where the four-kernel
+ *                   chain is dominated by per-kernel fixed costs; 1: always (GF_EINVAL where unsupported);
+ *                   -1: never.  The single
+ *                   kernel takes FP32 or FP16 storage, a gray or depthwise guide, any subsample mode and
+ *                   ratio, r' up to what fits its tiles in shared memory, and no low-res intermediate outputs.
  *   color_guide     nonzero: I has guide_channels = 3 channels used jointly as a colour guide for every
  *                   channel of p (the guided filter's colour form, which the paper cites): per window
  *                   a = (Sigma + eps U)^-1 cov_Ip with Sigma the 3 x 3 covariance of I', b = mean_p - a^T
@@ -130,6 +137,7 @@ typedef struct gf_opts {
     int color_guide;
     int s_num;
     int s_den;
+    int fused;
 } gf_opts;
 
 /* Default options: batch 1, gray guide, derived r', full-res p, FP32 in and out, nothing optional. */
@@ -154,9 +162,9 @@ gf_status gf_row_band(int H, int W, int s, int r, int r_low, gf_subsample_mode m
                       int *row0, int *rows);
 
 /* Number of kernels one gf_filter call with these arguments launches (host-only; -1 for invalid
- * arguments): 4 when s > 1 (subsample, statistics + coefficients, box means of a and b, upsample + output),
- * 3 when s = 1 (no subsample); 6 with a colour guide (subsample, products, box means, coefficients, box
- * means, upsample + output). */
+ * arguments): 1 when the single fused kernel runs (gf_opts.fused); else 4 when s > 1 (subsample,
+ * statistics + coefficients, box means of a and b, upsample + output), 3 when s = 1 (no subsample); 6 with
+ * a colour guide (subsample, products, box means, coefficients, box means, upsample + output). */
 int gf_filter_kernel_count(int H, int W, int C, int s, gf_subsample_mode mode, const gf_opts *opts);
 
 /* Bytes of device scratch one gf_filter call with these arguments needs (host-only). */

@@ -54,6 +54,7 @@ class GFOpts(ctypes.Structure):
         ("color_guide", ctypes.c_int),
         ("s_num", ctypes.c_int),
         ("s_den", ctypes.c_int),
+        ("fused", ctypes.c_int),
     ]
 
 
@@ -267,7 +268,7 @@ def _stream_handle(stream):
 def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowres=False, out_dtype=None,
                        out=None, a_out=None, b_out=None, mean_a_out=None, mean_b_out=None, stats_out=None,
                        workspace=None, kernel_events=None, stream=None, ctx=None, detail_gain=0.0, rows=None,
-                       color_guide=False):
+                       color_guide=False, fused=0):
     """Fast guided filter (Algorithm 2; Algorithm 1 at s = 1) on CUDA tensors, via ``gf_filter``.
 
     I: (H, W), (CI, H, W) or (N, CI, H, W); p: the same rank with C channels (at low resolution when
@@ -277,6 +278,7 @@ def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowr
     ``rows=(row_begin, row_end)`` computes only those output rows of q (needs ``out``, the whole q, whose
     other rows are left as they are): one strip of an image split across devices or streams.
     ``color_guide=True``: I has 3 channels used jointly as a colour guide for every channel of p.
+    ``fused``: 0 runs the whole filter as one kernel for small images, 1 always, -1 never.
     """
     if not (I.is_cuda and p.is_cuda):
         raise ValueError("I and p must be CUDA tensors")
@@ -314,6 +316,7 @@ def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowr
     o.dtype_out = _DTYPES[out_dtype]
     o.detail_gain = float(detail_gain)
     o.color_guide = int(bool(color_guide))
+    o.fused = int(fused)
     if rows is not None:
         if not given:
             raise ValueError("rows needs out= (the whole q; rows outside the range are not written)")

@@ -191,6 +191,18 @@ gf_status resolve(int H, int W, int C, int r, float eps, int s, int mode, const 
         R.Yw1 = o->row_end - R.row0;
     }
     if (R.h > 65535) return fail(GF_EINVAL, "low-res height ceil(H/s) must be <= 65535");
+    // the single fused kernel: forced, automatic for small images, or off
+    {
+        const bool inter = o->a_out || o->b_out || o->mean_a_out || o->mean_b_out || o->stats_out;
+        const bool ok = gfk::fused_supported(R, inter);
+        if (o->fused > 0 && !ok)
+            return fail(GF_EINVAL, "the fused kernel does not take these arguments (colour guide, uint8, "
+                                   "intermediate outputs or too large a radius)");
+        // automatic: subsampled calls up to GF_FUSED_AUTO_PIXELS pixel-channels, where the single kernel was
+        // measured faster than the chain launched call by call (at s = 1 its direct window sums lose)
+        R.fused = ok && (o->fused > 0 || (o->fused == 0 && R.s > 1 &&
+                                          (long long)R.N * C * H * W <= GF_FUSED_AUTO_PIXELS));
+    }
     const long long planes = (long long)R.N * (R.CI + C);
     if (planes > 65535) return fail(GF_EINVAL, "batch * (guide channels + C) must be <= 65535");
     R.dense_lowres = (o->a_out || o->b_out || o->mean_a_out || o->mean_b_out);
@@ -229,6 +241,7 @@ FwdPlan make_plan(const Resolved &R, const Layout &L, const void *I, const void 
     P.int_scale = R.int_scale;
     P.events = (opts && opts->kernel_events) ? (cudaEvent_t *)opts->kernel_events : nullptr;
     P.detail = R.detail;
+    P.fused = R.fused;
     return P;
 }
 

@@ -105,4 +105,65 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b)
     return r;
 }
 
+// The source taps of a bilinear sample at ratio sn / sd: position ((2j + 1) sn - sd) / (2 sd), clamped.
+__device__ __forceinline__ void sub_bilinear_taps(int j, int sn, int sd, int n, int &t0, float &f)
+{
+    const int num = (2 * j + 1) * sn - sd, den = 2 * sd;
+    t0 = num / den;  // num >= 0 since sn >= sd
+    f = (float)(num - t0 * den) / (float)den;
+    if (t0 >= n - 1) { t0 = n - 1; f = 0.0f; }
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ float subsample_one(const T *src, int H, int W, int s, int sn, int sd, int j, int i)
+{
+    if (MODE == GF_SUB_NEAREST || s == 1) {
+        const int sy = min(((2 * j + 1) * sn) / (2 * sd), H - 1);  // floor((j + 1/2) s)
+        const int sx = min(((2 * i + 1) * sn) / (2 * sd), W - 1);
+        return ldv(src + (size_t)sy * W + sx);
+    } else if (MODE == GF_SUB_BILINEAR) {
+        // source coordinate (j + 1/2) s - 1/2, clamped to [0, H-1]
+        int y0, x0;
+        float fy, fx;
+        sub_bilinear_taps(j, sn, sd, H, y0, fy);
+        sub_bilinear_taps(i, sn, sd, W, x0, fx);
+        const int y1 = min(y0 + 1, H - 1), x1 = min(x0 + 1, W - 1);
+        const T *r0 = src + (size_t)y0 * W, *r1 = src + (size_t)y1 * W;
+        const float top = (1.0f - fx) * ldv(r0 + x0) + fx * ldv(r0 + x1);
+        const float bot = (1.0f - fx) * ldv(r1 + x0) + fx * ldv(r1 + x1);
+        return (1.0f - fy) * top + fy * bot;
+    } else {  // box: mean of the s x s block clipped to the image
+        const int ya = j * s, yb = min(ya + s, H), xa = i * s, xb = min(xa + s, W);
+        float acc = 0.0f;
+        for (int yy = ya; yy < yb; ++yy)
+            for (int xx = xa; xx < xb; ++xx) acc += ldv(src + (size_t)yy * W + xx);
+        return acc / (float)((yb - ya) * (xb - xa));
+    }
+}
+
+
+// Antialiased bilinear sample (triangle filter of half-width s = sn / sd, renormalised over the taps inside
+// the image) of low-res pixel (j, i), computed directly: for one-off samples (the fused kernel); the
+// subsample kernels walk rows instead.
+template <typename T>
+__device__ __forceinline__ float subsample_aa_one(const T *src, int H, int W, int sn, int sd, int j, int i)
+{
+    auto wnum = [&](int t, int k) { return 2 * sn - abs((2 * t + 1) * sd - (2 * k + 1) * sn); };
+    auto lo_of = [&](int k) { return max(0, floor_div((2 * k + 1) * sn - 2 * sn - sd, 2 * sd) + 1); };
+    auto hi_of = [&](int k, int n) { return min(n - 1, -floor_div(-((2 * k + 1) * sn + 2 * sn - sd), 2 * sd) - 1); };
+    const int ya = lo_of(j), yb = hi_of(j, H), xa = lo_of(i), xb = hi_of(i, W);
+    float acc = 0.0f;
+    int ny = 0, nx = 0;
+    for (int x = xa; x <= xb; ++x) nx += wnum(x, i);
+    for (int y = ya; y <= yb; ++y) {
+        const int wy = wnum(y, j);
+        ny += wy;
+        const T *row = src + (size_t)y * W;
+        float hs = 0.0f;
+        for (int x = xa; x <= xb; ++x) hs = fmaf((float)wnum(x, i), ldv(row + x), hs);
+        acc = fmaf((float)wy, hs, acc);
+    }
+    return acc / ((float)nx * (float)ny);
+}
+
 }  // namespace gfk

@@ -53,42 +53,6 @@ struct SubParams {
     float scale;  // result multiplier: k on the uint8 path (exact integers J = k * value), else 1
 };
 
-// The source taps of a bilinear sample at ratio sn / sd: position ((2j + 1) sn - sd) / (2 sd), clamped.
-__device__ __forceinline__ void sub_bilinear_taps(int j, int sn, int sd, int n, int &t0, float &f)
-{
-    const int num = (2 * j + 1) * sn - sd, den = 2 * sd;
-    t0 = num / den;  // num >= 0 since sn >= sd
-    f = (float)(num - t0 * den) / (float)den;
-    if (t0 >= n - 1) { t0 = n - 1; f = 0.0f; }
-}
-
-template <typename T, int MODE>
-__device__ __forceinline__ float subsample_one(const T *src, int H, int W, int s, int sn, int sd, int j, int i)
-{
-    if (MODE == GF_SUB_NEAREST || s == 1) {
-        const int sy = min(((2 * j + 1) * sn) / (2 * sd), H - 1);  // floor((j + 1/2) s)
-        const int sx = min(((2 * i + 1) * sn) / (2 * sd), W - 1);
-        return ldv(src + (size_t)sy * W + sx);
-    } else if (MODE == GF_SUB_BILINEAR) {
-        // source coordinate (j + 1/2) s - 1/2, clamped to [0, H-1]
-        int y0, x0;
-        float fy, fx;
-        sub_bilinear_taps(j, sn, sd, H, y0, fy);
-        sub_bilinear_taps(i, sn, sd, W, x0, fx);
-        const int y1 = min(y0 + 1, H - 1), x1 = min(x0 + 1, W - 1);
-        const T *r0 = src + (size_t)y0 * W, *r1 = src + (size_t)y1 * W;
-        const float top = (1.0f - fx) * ldv(r0 + x0) + fx * ldv(r0 + x1);
-        const float bot = (1.0f - fx) * ldv(r1 + x0) + fx * ldv(r1 + x1);
-        return (1.0f - fy) * top + fy * bot;
-    } else {  // box: mean of the s x s block clipped to the image
-        const int ya = j * s, yb = min(ya + s, H), xa = i * s, xb = min(xa + s, W);
-        float acc = 0.0f;
-        for (int yy = ya; yy < yb; ++yy)
-            for (int xx = xa; xx < xb; ++xx) acc += ldv(src + (size_t)yy * W + xx);
-        return acc / (float)((yb - ya) * (xb - xa));
-    }
-}
-
 template <typename T, int MODE>
 __global__ void __launch_bounds__(SUB_NT) k_subsample(SubParams P)
 {
@@ -1335,7 +1299,7 @@ bool aligned_vec_subsample(const FwdPlan &P)
 
 }  // namespace
 
-int forward_kernel_count(const Resolved &R) { return R.color ? 6 : 3 + (R.s > 1 ? 1 : 0); }
+int forward_kernel_count(const Resolved &R) { return R.fused ? 1 : (R.color ? 6 : 3 + (R.s > 1 ? 1 : 0)); }
 
 namespace {
 
@@ -1384,6 +1348,12 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
 {
     StageTimer tm{P.events, st};
     cudaError_t err;
+    if (P.fused && !P.skip_output && !P.need_lowres) {  // the whole filter in one kernel
+        tm.before();
+        err = launch_fused(P, st);
+        tm.after();
+        return err;
+    }
     const int planesNC = P.N * P.C;
 
     // ---- Algorithm 2, first step: subsample I and p (skipped at s = 1)

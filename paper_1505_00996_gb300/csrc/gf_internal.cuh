@@ -48,6 +48,7 @@ struct FwdPlan {
     // first four, 2C in each of the last four.
     bool color = false;
     float *col[8] = {};
+    bool fused = false;  // the whole filter in one kernel (gf_fused.cu)
     size_t fps = 0;      // plane stride (elements) of the full-res I, p and q (H * W of the whole image)
     size_t lpin = 0;     // plane stride of a low-res p given by the caller (h * w of the whole image)
     int Yw0 = 0, Yw1 = 0;  // output rows written, [Yw0, Yw1) of the H rows the plan covers
@@ -90,6 +91,7 @@ struct Resolved {
     float eps, int_scale;
     float detail;  // detail gain (gf_opts.detail_gain)
     bool color;    // colour guide (gf_opts.color_guide)
+    bool fused;    // one fused kernel (gf_opts.fused, resolved)
     size_t lps;  // low-res plane stride in floats
     // Row band (gf_opts.row_begin / row_end): H and h above are those of the band of complete s-row blocks
     // that is filtered; it starts at full-res row row0 of the whole image, and the output rows written are
@@ -121,6 +123,10 @@ cudaError_t opt_in_smem(F *func, size_t smem) { return opt_in_smem(reinterpret_c
 
 // Kernels one forward call launches for these arguments (host-side, assuming 16-byte aligned buffers).
 int forward_kernel_count(const Resolved &R);
+
+// The single-kernel form (gf_fused.cu): whether it can run these arguments, and its launch.
+bool fused_supported(const Resolved &R, bool intermediates);
+cudaError_t launch_fused(const FwdPlan &P, cudaStream_t st);
 
 // Colour-guide stages (gf_color.cu).
 cudaError_t launch_color_products(const FwdPlan &P, cudaStream_t st);

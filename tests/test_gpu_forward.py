@@ -84,12 +84,15 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("fused", [-1, 0], ids=["chain", "auto"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "N%dCI%dC%d_%dx%d_r%d_s%d_m%d" % (c[0], c[1], c[2], c[3], c[4], c[5], c[7], c[8]))
-def test_fp32_parity(gf, case):
+def test_fp32_parity(gf, case, fused):
+    """Every case through the four-kernel chain, and with the automatic choice (the single fused kernel for
+    images up to GF_FUSED_AUTO_PIXELS where it takes the arguments)."""
     N, CI, C, H, W, r, eps, s, mode = case
     I = _rand((N, CI, H, W), 1 + H + W)
     p = _rand((N, C, H, W), 2 + H * W)
-    q = _run(gf, I, p, r, eps, s, mode)
+    q = _run(gf, I, p, r, eps, s, mode, fused=fused)
     ref = oracle_q(I, p, r, eps, s, mode)
     assert q.shape == ref.shape
     err = max_abs(q, ref)
@@ -277,9 +280,12 @@ def test_empty_input_returns_empty(gf):
 def test_kernel_events_recorded(gf):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * gf.GF_MAX_STAGES)]
     I = _rand((1, 1, 256, 256), 15)
-    _run(gf, I, I, 8, 1e-2, 4, 1, kernel_events=ev)
+    _run(gf, I, I, 8, 1e-2, 4, 1, kernel_events=ev, fused=-1)
     for k in range(4):  # subsample, statistics + coefficients, box means of a and b, upsample + output
         assert ev[2 * k].elapsed_time(ev[2 * k + 1]) >= 0.0
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(2 * gf.GF_MAX_STAGES)]
+    _run(gf, I, I, 8, 1e-2, 4, 1, kernel_events=ev1, fused=1)  # one kernel
+    assert ev1[0].elapsed_time(ev1[1]) >= 0.0
 
 
 def test_precision_variants_at_12mp(gf, scene12mp):
@@ -323,13 +329,15 @@ RATIONAL_CASES = [  # (N, CI, C, H, W, r, eps, s, mode, dtype)
 
 @pytest.mark.parametrize("case", RATIONAL_CASES, ids=lambda c: "%dx%d_s%s_m%d_%s" % (c[3], c[4], str(c[7]).replace("/", "o"),
                                                                                        c[8], str(c[9]).split(".")[-1]))
-def test_non_integer_ratio_parity(gf, case):
+@pytest.mark.parametrize("fused", [-1, 0], ids=["chain", "auto"])
+def test_non_integer_ratio_parity(gf, case, fused):
     N, CI, C, H, W, r, eps, s, mode, dtype = case
     I = _rand((N, CI, H, W), 11 + H)
     p = _rand((N, C, H, W), 12 + W)
     if dtype == torch.float16:
         I, p = I.astype(np.float16), p.astype(np.float16)
-    q = gf.fast_guided_filter(torch.from_numpy(I).cuda(), torch.from_numpy(p).cuda(), r, eps, s, MODE_NAMES[mode])
+    q = gf.fast_guided_filter(torch.from_numpy(I).cuda(), torch.from_numpy(p).cuda(), r, eps, s, MODE_NAMES[mode],
+                              fused=fused)
     torch.cuda.synchronize()
     ref = oracle_q(I.astype(np.float64), p.astype(np.float64), r, eps, s, mode)
     err = max_abs(q.float().cpu().numpy(), ref)
