@@ -742,16 +742,6 @@ struct UpParams {
     int Yw0, Yw1;                     // rows written: [Yw0, Yw1) of the H rows
 };
 
-// Detail-enhancement epilogue (the application of the paper's Fig. 2): q + k (I - q), the guide's detail
-// I - q scaled by k on top of the filtered image.  k = 0 leaves q as it is.
-__device__ __forceinline__ void detail_epilogue(float k, const float iv[4], float out[4])
-{
-    if (k != 0.0f) {
-#pragma unroll
-        for (int x = 0; x < 4; ++x) out[x] = fmaf(k, iv[x] - out[x], out[x]);
-    }
-}
-
 template <typename T>
 __device__ __forceinline__ void ld4(const T *p, bool vec, int valid, float v[4]);
 template <>
@@ -788,59 +778,6 @@ __device__ __forceinline__ void ld4<uint8_t>(const uint8_t *p, bool vec, int val
     } else {
 #pragma unroll
         for (int k = 0; k < 4; ++k) v[k] = (k < valid) ? (float)p[k] / 255.0f : 0.0f;
-    }
-}
-
-// 4 pixels of I from the thread's shared ring slot, as floats.
-template <typename T>
-__device__ __forceinline__ void ld4_shared(const void *p, float v[4]);
-template <>
-__device__ __forceinline__ void ld4_shared<float>(const void *p, float v[4])
-{
-    const float4 t = *reinterpret_cast<const float4 *>(p);
-    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-}
-template <>
-__device__ __forceinline__ void ld4_shared<__half>(const void *p, float v[4])
-{
-    const uint2 t = *reinterpret_cast<const uint2 *>(p);
-    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
-    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-}
-template <>
-__device__ __forceinline__ void ld4_shared<uint8_t>(const void *p, float v[4])
-{
-    const uint32_t t = *reinterpret_cast<const uint32_t *>(p);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = (float)((t >> (8 * k)) & 0xffu) / 255.0f;
-}
-template <typename T>
-__device__ __forceinline__ void st4(T *p, bool vec, int valid, const float v[4]);
-template <>
-__device__ __forceinline__ void st4<float>(float *p, bool vec, int valid, const float v[4])
-{
-    if (vec) {
-        __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
-    } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (k < valid) __stcs(p + k, v[k]);
-    }
-}
-template <>
-__device__ __forceinline__ void st4<__half>(__half *p, bool vec, int valid, const float v[4])
-{
-    if (vec) {
-        const __half2 lo = __floats2half2_rn(v[0], v[1]), hi = __floats2half2_rn(v[2], v[3]);
-        uint2 t;
-        t.x = *reinterpret_cast<const uint32_t *>(&lo);
-        t.y = *reinterpret_cast<const uint32_t *>(&hi);
-        __stcs(reinterpret_cast<uint2 *>(p), t);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (k < valid) p[k] = __float2half_rn(v[k]);
     }
 }
 
