@@ -161,6 +161,11 @@ gf_status gf_lowres_geometry(int H, int W, int s, int r, int r_low, int *h, int 
 gf_status gf_row_band(int H, int W, int s, int r, int r_low, gf_subsample_mode mode, int row_begin, int row_end,
                       int *row0, int *rows);
 
+/* Fault bits the library's kernels recorded on `device` since the last clear (host call; synchronous
+ * copy from the device).  Bit 0: a bounded wait of a pipelined kernel gave up (the kernel stopped early;
+ * its output is incomplete).  clear != 0 resets them.  GF_ECUDA if the copy fails. */
+gf_status gf_kernel_faults(int device, unsigned *flags, int clear);
+
 /* Number of kernels one gf_filter call with these arguments launches (host-only; -1 for invalid
  * arguments): 1 when the single fused kernel runs (gf_opts.fused); else 4 when s > 1 (subsample,
  * statistics + coefficients, box means of a and b, upsample + output), 3 when s = 1 (no subsample); 6 with

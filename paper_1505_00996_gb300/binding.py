@@ -113,6 +113,8 @@ def load_library(build_if_missing=True):
         lib.gf_lowres_geometry.restype = i
         lib.gf_workspace_size.argtypes = [i, i, i, i, P(GFOpts), P(sz)]
         lib.gf_workspace_size.restype = i
+        lib.gf_kernel_faults.argtypes = [i, P(ctypes.c_uint), i]
+        lib.gf_kernel_faults.restype = i
         lib.gf_row_band.argtypes = [i, i, i, i, i, i, i, i, P(i), P(i)]
         lib.gf_row_band.restype = i
         lib.gf_filter_kernel_count.argtypes = [i, i, i, i, i, P(GFOpts)]
@@ -159,6 +161,15 @@ def opts_init():
     o = GFOpts()
     load_library().gf_opts_init(ctypes.byref(o))
     return o
+
+
+def kernel_faults(device=None, clear=True):
+    """Fault bits the kernels recorded on `device` (bit 0: a bounded wait gave up); cleared by default."""
+    if device is None:
+        device = torch.cuda.current_device()
+    v = ctypes.c_uint()
+    check(load_library().gf_kernel_faults(int(device), ctypes.byref(v), int(bool(clear))))
+    return v.value
 
 
 def _integer_ratio(s):

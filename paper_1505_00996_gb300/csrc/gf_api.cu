@@ -546,6 +546,15 @@ gf_status gf_serve_stats_get(gf_ctx *ctx, gf_serve_stats *out)
     return gfk::server_stats(ctx->server, out);
 }
 
+gf_status gf_kernel_faults(int device, unsigned *flags, int clear)
+{
+    if (!flags) return fail(GF_EINVAL, "flags is NULL");
+    DeviceGuard guard(device);
+    cudaError_t e = gfk::read_kernel_faults(flags, clear != 0);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the kernel fault bits");
+    return GF_OK;
+}
+
 gf_status gf_row_band(int H, int W, int s, int r, int r_low, gf_subsample_mode mode, int row_begin, int row_end,
                       int *row0, int *rows)
 {

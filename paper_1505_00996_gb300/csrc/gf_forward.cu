@@ -1188,6 +1188,13 @@ void launch_up_t(UpParams up, int N, int CC, bool vec, cudaStream_t st)
         return;
     }
     if (vec && up.sd == 1 && (up.s == 4 || up.s == 8)) {
+        // the guide streamed by TMA when the tensor map can describe it; else the per-thread cp.async ring
+        constexpr int DT_IN = sizeof(TI) == 4 ? F32 : (sizeof(TI) == 2 ? F16 : U8);
+        constexpr int DT_OUT = sizeof(TQ) == 4 ? F32 : F16;
+        if (output_tma_ok(up.I, DT_IN, up.W, up.fps) &&
+            launch_output_tma(up.I, up.ma, up.mb, up.q, N, up.C, up.CI, up.H, up.W, up.h, up.w, up.s, up.lps, up.fps,
+                              up.Yw0, up.Yw1, up.detail, DT_IN, DT_OUT, st) == cudaSuccess)
+            return;
         up.R = 8 * up.s;  // 8 low-res rows per CTA
         up.LRmax = up.R / up.s + 2;
         up.LCmax = UP_BAND / up.s + 2;

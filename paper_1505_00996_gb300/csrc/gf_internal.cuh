@@ -124,6 +124,14 @@ cudaError_t opt_in_smem(F *func, size_t smem) { return opt_in_smem(reinterpret_c
 // Kernels one forward call launches for these arguments (host-side, assuming 16-byte aligned buffers).
 int forward_kernel_count(const Resolved &R);
 
+// The TMA-fed s = 4, 8 output kernel (gf_tma.cu): whether it takes these buffers, its launch, and the
+// bounded-wait fault bits its kernels record.
+bool output_tma_ok(const void *I, int dt_in, int W, size_t fps);
+cudaError_t launch_output_tma(const void *I, const float *ma, const float *mb, void *q, int N, int C, int CI, int H,
+                              int W, int h, int w, int s, size_t lps, size_t fps, int Yw0, int Yw1, float detail,
+                              int dt_in, int dt_out, cudaStream_t st);
+cudaError_t read_kernel_faults(unsigned *flags, bool clear);
+
 // The single-kernel form (gf_fused.cu): whether it can run these arguments, and its launch.
 bool fused_supported(const Resolved &R, bool intermediates);
 cudaError_t launch_fused(const FwdPlan &P, cudaStream_t st);

@@ -1,0 +1,293 @@
+// gf_tma.cu -- the s = 4, 8 upsample-and-output kernel with the guide streamed by the Tensor Memory
+// Accelerator (Algorithm 2, last two steps: bilinear upsampling of mean_a, mean_b and q = mean_a I + mean_b).
+//
+// Same work split and arithmetic as k_upsample_output_s4x (one channel of one 512-pixel band per CTA, rows
+// walked in the s-row runs that share a pair of low-res tap rows, 4 pixels per consumer thread), but the
+// rows of I reach shared memory as 2-D TMA tiles instead of per-thread copies:
+//   warp 4 (producer)  one lane issues, for each quad of 4 rows, two cp.async.bulk.tensor loads of a
+//                      256-column x 4-row box into a ring stage, arming the stage's "full" mbarrier with
+//                      the bytes to expect; before reusing a stage it waits on the stage's "empty" barrier;
+//   warps 0-3          wait on "full", read their 4 pixels of the 4 rows, write q (128-bit streaming
+//                      stores), and release the stage with one arrival per warp on "empty".
+// Out-of-image rows and columns of a box read as zeros and are never used.  Every wait is bounded: after
+// WAIT_LIMIT failed polls a thread records a timeout in g_wait_faults (read by gf_kernel_faults) and leaves
+// its loop; the producer then drains the loads it issued (bounded again) before the CTA exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdlib>
+
+#include "gf_device.cuh"
+#include "gf_internal.cuh"
+
+namespace gfk {
+
+__device__ unsigned g_wait_faults;  // bit 0: a bounded mbarrier wait of the TMA output kernel gave up
+
+namespace {
+
+constexpr int TO_CONS = 128;            // consumer threads (4 warps), 4 pixels each
+constexpr int TO_NT = TO_CONS + 32;     // plus one producer warp
+constexpr int TO_BAND = 4 * TO_CONS;    // 512 columns per CTA
+constexpr int TO_BOX_X = 256;           // TMA box: 256 columns x 4 rows (a box dimension is at most 256)
+constexpr int TO_NST = 4;               // ring stages (quads of rows in flight)
+constexpr unsigned WAIT_LIMIT = 1u << 20;
+
+struct TmaOutParams {
+    const float *ma, *mb;
+    void *q;
+    int C, CI, H, W, h, w, R, LRmax, LCmax, Yw0, Yw1;
+    size_t lps, fps;
+    float detail;
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false (and the fault bit set) when it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
+{
+    for (unsigned it = 0; it < WAIT_LIMIT; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicOr(&g_wait_faults, 1u);
+    return false;
+}
+
+template <typename TI, typename TQ, int S>
+__global__ void __launch_bounds__(TO_NT, 4) k_output_tma(const __grid_constant__ CUtensorMap tmI, TmaOutParams P)
+{
+    extern __shared__ __align__(128) unsigned char sm[];
+    constexpr int ES = (int)sizeof(TI);
+    constexpr int BOX_BYTES = TO_BOX_X * 4 * ES;  // one 256 x 4 box
+    constexpr int STAGE = 2 * BOX_BYTES;          // 512 columns x 4 rows
+    const int nb = P.R / S, jb = blockIdx.y * nb;
+    const int c = blockIdx.x % P.C, band = blockIdx.x / P.C, n = blockIdx.z;
+    const int Xb = band * TO_BAND;
+    const int Yb = max(jb * S, P.Yw0), Ye = min(min(jb * S + P.R, P.H), P.Yw1);
+    if (Yb >= Ye) return;  // uniform over the CTA
+    const int ly0 = jb - 1, lx0 = Xb / S - 1;
+    const int LR = P.LRmax, LC = P.LCmax, tile = LR * LC;
+    float *tap = reinterpret_cast<float *>(sm + TO_NST * STAGE);  // [2][LR][LC]
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(tap + 2 * tile);  // full[NST], empty[NST]
+    const unsigned full0 = smem_addr(bars), empty0 = smem_addr(bars + TO_NST);
+    constexpr int QPR = S / 4;
+    // quads (4-row groups of the runs) this CTA uses: those starting above Ye
+    const int nquads_all = (nb + 1) * QPR;
+    int nquads = 0;
+    while (nquads < nquads_all && S * (jb - 1 + nquads / QPR) + S / 2 + 4 * (nquads % QPR) < Ye) ++nquads;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TO_NST; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(full0 + 8 * s), "r"(1) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(empty0 + 8 * s), "r"(TO_CONS / 32) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+
+    if (threadIdx.x >= TO_CONS) {  // ---- producer warp
+        if (threadIdx.x == TO_CONS) {
+            const int plane = n * P.CI + (P.CI == 1 ? 0 : c);
+            int issued = 0;
+            for (int u = 0; u < nquads; ++u) {
+                const int st = u % TO_NST;
+                if (u >= TO_NST && !mbar_wait(empty0 + 8 * st, ((u / TO_NST) - 1) & 1)) break;
+                const unsigned fb = full0 + 8 * st;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(STAGE) : "memory");
+                const int y = S * (jb - 1 + u / QPR) + S / 2 + 4 * (u % QPR);  // may be < 0: zero fill
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const unsigned dst = smem_addr(sm + st * STAGE + k * BOX_BYTES);
+                    asm volatile(
+                        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                        " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(dst),
+                        "l"(reinterpret_cast<unsigned long long>(&tmI)), "r"(Xb + k * TO_BOX_X), "r"(y), "r"(plane),
+                        "r"(fb)
+                        : "memory");
+                }
+                ++issued;
+            }
+            // drain: every load issued has landed before the CTA may exit (the consumers waited on all of
+            // them unless a wait gave up)
+            for (int u = max(0, issued - TO_NST); u < issued; ++u) mbar_wait(full0 + 8 * (u % TO_NST), (u / TO_NST) & 1);
+        }
+        return;
+    }
+
+    // ---- consumers: the tap tile (cp.async with clamped coordinates), then the rows
+    {
+        const int c0 = threadIdx.x, c1 = threadIdx.x + TO_CONS;
+        const int g0 = min(max(lx0 + c0, 0), P.w - 1), g1 = min(max(lx0 + c1, 0), P.w - 1);
+        const float *pa = P.ma + (size_t)(n * P.C + c) * P.lps, *pb = P.mb + (size_t)(n * P.C + c) * P.lps;
+        for (int row = 0; row < LR; ++row) {
+            const size_t go = (size_t)min(max(ly0 + row, 0), P.h - 1) * P.w;
+            float *da = tap + row * LC, *db = da + tile;
+            if (c0 < LC) { cp_async4(da + c0, pa + go + g0); cp_async4(db + c0, pb + go + g0); }
+            if (c1 < LC) { cp_async4(da + c1, pa + go + g1); cp_async4(db + c1, pb + go + g1); }
+        }
+        cp_async_wait_all();
+        asm volatile("bar.sync 1, %0;\n" ::"r"(TO_CONS) : "memory");  // consumers only
+    }
+    const int X0 = Xb + threadIdx.x * 4;
+    const bool active = X0 < P.W;  // threads past the image still take part in the barriers
+    const int ti = X0 / S - lx0;
+    const int g = (S == 8) ? ((X0 >> 2) & 1) : 0;
+    auto hrow = [&](int tr, float (&o)[2][4]) {
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const float *row = tap + m * tile + tr * LC;
+            if (S == 4) {
+                const float a = row[ti - 1], b = row[ti], cc = row[ti + 1];
+                o[m][0] = fmaf(0.625f, b - a, a);
+                o[m][1] = fmaf(0.875f, b - a, a);
+                o[m][2] = fmaf(0.125f, cc - b, b);
+                o[m][3] = fmaf(0.375f, cc - b, b);
+            } else {
+                const int lo = g ? ti : ti - 1;
+                const float a = row[lo], b = row[lo + 1];
+                const float f0 = g ? 0.0625f : 0.5625f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) o[m][k] = fmaf(f0 + 0.125f * k, b - a, a);
+            }
+        }
+    };
+    TQ *Qp = (TQ *)P.q + (size_t)(n * P.C + c) * P.fps + X0;
+    // the thread's 4 pixels inside a stage: box threadIdx / 64, column 4 (threadIdx % 64)
+    const int box = threadIdx.x / (TO_BOX_X / 4), bcol = 4 * (threadIdx.x % (TO_BOX_X / 4));
+    float lo[2][4], d[2][4];
+    if (active) hrow(0, lo);
+    const int lane = threadIdx.x & 31;
+    for (int u = 0; u < nquads; ++u) {
+        const int st = u % TO_NST;
+        if (!mbar_wait(full0 + 8 * st, (u / TO_NST) & 1)) break;
+        const int t = u / QPR, sub = u % QPR;
+        const int Yq = S * (jb - 1 + t) + S / 2 + 4 * sub;
+        if (active) {
+            if (sub == 0) {
+                if (t > 0) {
+#pragma unroll
+                    for (int m = 0; m < 2; ++m)
+#pragma unroll
+                        for (int x = 0; x < 4; ++x) lo[m][x] += d[m][x];
+                }
+                hrow(t + 1, d);
+#pragma unroll
+                for (int m = 0; m < 2; ++m)
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) d[m][x] -= lo[m][x];
+            }
+            const float fy0 = (S == 4) ? 0.125f : (sub ? 0.5625f : 0.0625f);
+            const unsigned char *sbase = sm + st * STAGE + box * BOX_BYTES + bcol * ES;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int Y = Yq + k;
+                if (Y < Yb || Y >= Ye) continue;
+                float iv[4];
+                ld4_shared<TI>(sbase + k * TO_BOX_X * ES, iv);
+                const float fy = fy0 + (float)k / (float)S;
+                float out[4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const float A = fmaf(fy, d[0][x], lo[0][x]);  // upsampled mean_a
+                    const float B = fmaf(fy, d[1][x], lo[1][x]);  // upsampled mean_b
+                    out[x] = fmaf(A, iv[x], B);                   // Eq. (4)
+                }
+                detail_epilogue(P.detail, iv, out);
+                st4<TQ>(Qp + (size_t)Y * P.W, true, 4, out);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(empty0 + 8 * st) : "memory");
+    }
+}
+
+using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
+
+EncodeFn encode_fn()
+{
+    static EncodeFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<EncodeFn>(p);
+    }();
+    return fn;
+}
+
+}  // namespace
+
+bool output_tma_ok(const void *I, int dt_in, int W, size_t fps)
+{
+    const size_t es = dtype_size(dt_in);
+    return encode_fn() != nullptr && ((uintptr_t)I % 16 == 0) && ((size_t)W * es) % 16 == 0 && (fps * es) % 16 == 0 &&
+           getenv("GF_NO_TMA") == nullptr;
+}
+
+cudaError_t launch_output_tma(const void *I, const float *ma, const float *mb, void *q, int N, int C, int CI, int H,
+                              int W, int h, int w, int s, size_t lps, size_t fps, int Yw0, int Yw1, float detail,
+                              int dt_in, int dt_out, cudaStream_t st)
+{
+    const size_t es = dtype_size(dt_in);
+    CUtensorMap map;
+    const CUtensorMapDataType dtype = dt_in == F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                      : (dt_in == F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N * CI};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * es, (cuuint64_t)fps * es};
+    const cuuint32_t box[3] = {(cuuint32_t)TO_BOX_X, 4, 1}, estr[3] = {1, 1, 1};
+    if (encode_fn()(&map, dtype, 3, const_cast<void *>(I), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    TmaOutParams P;
+    P.ma = ma; P.mb = mb; P.q = q;
+    P.C = C; P.CI = CI; P.H = H; P.W = W; P.h = h; P.w = w;
+    P.R = 8 * s;
+    P.LRmax = P.R / s + 2;
+    P.LCmax = ((TO_BAND / s + 2) + 1) & ~1;
+    P.Yw0 = Yw0; P.Yw1 = Yw1;
+    P.lps = lps; P.fps = fps;
+    P.detail = detail;
+    const int bands = (W + TO_BAND - 1) / TO_BAND;
+    dim3 grid(bands * C, (H + P.R - 1) / P.R, N);
+    const size_t smem = (size_t)TO_NST * 2 * TO_BOX_X * 4 * es + (size_t)2 * P.LRmax * P.LCmax * sizeof(float) +
+                        2 * TO_NST * sizeof(unsigned long long);
+    cudaError_t e;
+#define GF_TO(TI, TQ, SS)                                                                  \
+    do {                                                                                   \
+        if ((e = opt_in_smem(k_output_tma<TI, TQ, SS>, smem)) != cudaSuccess) return e;    \
+        k_output_tma<TI, TQ, SS><<<grid, TO_NT, smem, st>>>(map, P);                       \
+    } while (0)
+#define GF_TO_S(TI, TQ) do { if (s == 4) GF_TO(TI, TQ, 4); else GF_TO(TI, TQ, 8); } while (0)
+    if (dt_in == F32) {
+        if (dt_out == F32) GF_TO_S(float, float); else GF_TO_S(float, __half);
+    } else if (dt_in == F16) {
+        if (dt_out == F32) GF_TO_S(__half, float); else GF_TO_S(__half, __half);
+    } else {
+        if (dt_out == F32) GF_TO_S(uint8_t, float); else GF_TO_S(uint8_t, __half);
+    }
+#undef GF_TO_S
+#undef GF_TO
+    return cudaGetLastError();
+}
+
+cudaError_t read_kernel_faults(unsigned *flags, bool clear)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(flags, g_wait_faults, sizeof(unsigned));
+    if (e == cudaSuccess && clear) {
+        const unsigned zero = 0;
+        e = cudaMemcpyToSymbol(g_wait_faults, &zero, sizeof(unsigned));
+    }
+    return e;
+}
+
+}  // namespace gfk
