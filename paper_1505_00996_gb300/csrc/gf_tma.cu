@@ -30,7 +30,7 @@ constexpr int TO_CONS = 128;            // consumer threads (4 warps), 4 pixels 
 constexpr int TO_NT = TO_CONS + 32;     // plus one producer warp
 constexpr int TO_BAND = 4 * TO_CONS;    // 512 columns per CTA
 constexpr int TO_BOX_X = 256;           // TMA box: 256 columns x 4 rows (a box dimension is at most 256)
-constexpr int TO_NST = 4;               // ring stages (quads of rows in flight)
+constexpr int TO_NST = 6;               // ring stages (quads of rows in flight; 6 measured best with two images in flight)
 constexpr unsigned WAIT_LIMIT = 1u << 20;
 
 struct TmaOutParams {
