@@ -127,6 +127,8 @@ def load_library(build_if_missing=True):
         lib.gf_filter.restype = i
         lib.gf_filter_host.argtypes = [vp, vp, vp, vp, i, i, i, i, f, i, i, P(GFOpts), vp]
         lib.gf_filter_host.restype = i
+        lib.gf_host_strips.argtypes = [i, i, i, i, i, P(GFOpts), P(i)]
+        lib.gf_host_strips.restype = i
         lib.gf_filter_noalloc.argtypes = [vp, vp, vp, i, i, i, i, f, i, i, P(GFOpts), vp]
         lib.gf_filter_noalloc.restype = i
         lib.gf_backward_workspace_size.argtypes = [i, i, i, i, P(GFOpts), P(sz)]
@@ -203,6 +205,23 @@ def row_band(H, W, s, r, row_begin, row_end, r_low=-1, mode="bilinear"):
     check(load_library().gf_row_band(int(H), int(W), _integer_ratio(s), int(r), int(r_low), m, int(row_begin),
                                      int(row_end), ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def host_strips(H, W, C, s, mode="bilinear", *, batch=1, guide_channels=1, dtype=torch.float32, out_dtype=None):
+    """Row boundaries [0, ..., H] of the strips ``gf_filter_host`` pipelines such a call in, or None when it
+    copies in, filters and copies out in one piece."""
+    o = opts_init()
+    o.batch = int(batch)
+    o.guide_channels = int(guide_channels)
+    s = _ratio(o, s)
+    o.dtype_in = _DTYPES[dtype]
+    o.dtype_out = _DTYPES[out_dtype or (torch.float16 if dtype == torch.float16 else torch.float32)]
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    ys = (ctypes.c_int * 9)()
+    k = load_library().gf_host_strips(int(H), int(W), int(C), int(s), m, ctypes.byref(o), ys)
+    if k < 0:
+        check(GF_EINVAL)
+    return list(ys[:k + 1]) if k >= 2 else None
 
 
 def row_strips(H, parts, align=1):

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "gf_internal.cuh"
 
@@ -24,6 +25,10 @@ struct gf_ctx {
     size_t arena_bytes = 0;
     void *stage = nullptr;  // device copies of host buffers (gf_filter_host)
     size_t stage_bytes = 0;
+    // gf_filter_host's strip pipeline: one call at a time per context, two copy streams of its own
+    std::mutex host_mu;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    std::vector<cudaEvent_t> host_ev;
     gfk::Server *server = nullptr;  // serving loop, created with the context, started on first submit
 };
 
@@ -314,6 +319,127 @@ using gfk::BwdLayout;
 using gfk::bwd_layout_of;
 using gfk::check_backward;
 
+namespace {
+
+// Host-buffer pipeline (gf_filter_host on large images): the output rows are cut into strips; the input rows
+// each strip's band needs are copied in on one stream, the strip is filtered on the caller's stream as a
+// row-range call (the same rows as the whole-image call up to FP32 rounding order), and its output rows are
+// copied out on a third stream, so uploads, filtering and downloads of different strips overlap.
+constexpr int HOST_MAX_STRIPS = 8;
+constexpr size_t HOST_PIPE_MIN_BYTES = size_t(8) << 20;  // below this the copies are too short to overlap
+
+// Strip boundaries Y[0] = 0 < ... < Y[K] = H (multiples of 8 s), K >= 2; or K < 2 when the call keeps the
+// single copy-in / filter / copy-out sequence (small, low-res p, colour guide, non-integer ratio, single
+// fused kernel, low-res outputs, its own row range or kernel events).
+int host_strips(const Resolved &R, const gf_opts *o, size_t host_bytes, std::vector<int> &Y)
+{
+    Y.clear();
+    if (host_bytes < HOST_PIPE_MIN_BYTES) return 0;
+    if (R.sd != 1 || R.color || R.p_lowres || R.fused || R.dense_lowres) return 0;
+    if (o && (o->row_begin || o->row_end || o->stats_out || o->kernel_events)) return 0;
+    const int align = 8 * R.s;
+    const int K = std::min(HOST_MAX_STRIPS, R.H / (64 * R.s));
+    if (K < 2) return 0;
+    const int rows = (R.H + K - 1) / K;
+    const int step = (rows + align - 1) / align * align;
+    for (int y = 0; y < R.H; y += step) Y.push_back(y);
+    Y.push_back(R.H);
+    return (int)Y.size() - 1;
+}
+
+gf_status host_pipeline(gf_ctx *ctx, const Resolved &R, const std::vector<int> &Y, const void *I_host,
+                        const void *p_host, void *q_host, char *dI, char *dp, char *dq, int r, float eps, int s,
+                        gf_subsample_mode mode, const gf_opts *opts, cudaStream_t stream)
+{
+    const int K = (int)Y.size() - 1;
+    const int H = R.H, W = R.W, C = R.C;
+    gf_opts so;
+    if (opts) so = *opts; else gf_opts_init(&so);
+    // the input rows each strip reads (its band), and the scratch the largest band needs
+    std::vector<int> band_end(K);
+    size_t ws_need = 0;
+    for (int k = 0; k < K; ++k) {
+        so.row_begin = Y[k];
+        so.row_end = Y[k + 1];
+        Resolved Rk;
+        gf_status st = resolve(H, W, C, r, eps, s, (int)mode, &so, Rk);
+        if (st != GF_OK) return st;
+        band_end[k] = std::max(Rk.row0 + Rk.H, k > 0 ? band_end[k - 1] : 0);
+        ws_need = std::max(ws_need, layout_of(Rk, &so).total);
+    }
+    cudaError_t e;
+    {
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        if (!so.workspace) {
+            gf_status st = grow(&ctx->arena, &ctx->arena_bytes, ws_need, "the scratch arena");
+            if (st != GF_OK) return st;
+        }
+        if (!ctx->copy_in) {
+            if ((e = cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking)) != cudaSuccess)
+                return cuda_fail(e, "creating the host-call copy streams");
+        }
+        while (ctx->host_ev.size() < size_t(2 * HOST_MAX_STRIPS + 2)) {
+            cudaEvent_t ev;
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(e, "creating the host-call events");
+            ctx->host_ev.push_back(ev);
+        }
+    }
+    cudaEvent_t *ev = ctx->host_ev.data();  // [0] start, [1 + k] strip k's input, [1 + K + k] strip k's output
+    const size_t ein = gfk::dtype_size(R.dt_in), eout = gfk::dtype_size(R.dt_out);
+    const size_t plane = (size_t)H * W;
+    const int in_planes = R.N * R.CI, p_planes = R.N * C;
+    gf_status result = GF_OK;
+    auto check = [&](cudaError_t err, const char *what) {
+        if (err != cudaSuccess && result == GF_OK) result = cuda_fail(err, what);
+        return result == GF_OK;
+    };
+    // the copies start after the work already queued on the caller's stream
+    bool ok = check(cudaEventRecord(ev[0], stream), "cudaEventRecord") &&
+              check(cudaStreamWaitEvent(ctx->copy_in, ev[0], 0), "cudaStreamWaitEvent") &&
+              check(cudaStreamWaitEvent(ctx->copy_out, ev[0], 0), "cudaStreamWaitEvent");
+    int copied = 0;  // input rows [0, copied) of every plane are queued
+    for (int k = 0; ok && k < K; ++k) {
+        if (band_end[k] > copied) {
+            const size_t off = (size_t)copied * W, n = (size_t)(band_end[k] - copied) * W;
+            for (int pl = 0; ok && pl < in_planes; ++pl)
+                ok = check(cudaMemcpyAsync(dI + (pl * plane + off) * ein, (const char *)I_host + (pl * plane + off) * ein,
+                                           n * ein, cudaMemcpyHostToDevice, ctx->copy_in), "cudaMemcpyAsync of I rows");
+            for (int pl = 0; ok && pl < p_planes; ++pl)
+                ok = check(cudaMemcpyAsync(dp + (pl * plane + off) * ein, (const char *)p_host + (pl * plane + off) * ein,
+                                           n * ein, cudaMemcpyHostToDevice, ctx->copy_in), "cudaMemcpyAsync of p rows");
+            copied = band_end[k];
+        }
+        ok = ok && check(cudaEventRecord(ev[1 + k], ctx->copy_in), "cudaEventRecord") &&
+             check(cudaStreamWaitEvent(stream, ev[1 + k], 0), "cudaStreamWaitEvent");
+        if (!ok) break;
+        so.row_begin = Y[k];
+        so.row_end = Y[k + 1];
+        gf_status st = gf_filter(ctx, dI, dp, dq, H, W, C, r, eps, s, mode, &so, stream);
+        if (st != GF_OK) {
+            result = st;
+            break;
+        }
+        ok = check(cudaEventRecord(ev[1 + K + k], stream), "cudaEventRecord") &&
+             check(cudaStreamWaitEvent(ctx->copy_out, ev[1 + K + k], 0), "cudaStreamWaitEvent");
+        const size_t off = (size_t)Y[k] * W, n = (size_t)(Y[k + 1] - Y[k]) * W;
+        for (int pl = 0; ok && pl < p_planes; ++pl)
+            ok = check(cudaMemcpyAsync((char *)q_host + (pl * plane + off) * eout, dq + (pl * plane + off) * eout,
+                                       n * eout, cudaMemcpyDeviceToHost, ctx->copy_out), "cudaMemcpyAsync of q rows");
+    }
+    // drain all three streams (also after an error, so that no copy into the staging buffers is left in flight)
+    cudaError_t e1 = cudaStreamSynchronize(ctx->copy_in);
+    cudaError_t e2 = cudaStreamSynchronize(ctx->copy_out);
+    cudaError_t e3 = cudaStreamSynchronize(stream);
+    check(e1, "cudaStreamSynchronize of the copy-in stream");
+    check(e2, "cudaStreamSynchronize of the copy-out stream");
+    check(e3, "cudaStreamSynchronize");
+    return result;
+}
+
+}  // namespace
+
 extern "C" {
 
 void gf_opts_init(gf_opts *o)
@@ -376,6 +502,9 @@ gf_status gf_destroy(gf_ctx *ctx)
         cudaDeviceSynchronize();
         if (ctx->arena) cudaFree(ctx->arena);
         if (ctx->stage) cudaFree(ctx->stage);
+        if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
+        if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
+        for (cudaEvent_t ev : ctx->host_ev) cudaEventDestroy(ev);
     }
     delete ctx;
     return GF_OK;
@@ -426,6 +555,7 @@ gf_status gf_filter_host(gf_ctx *ctx, const void *I_host, const void *p_host, vo
     const size_t bq = (size_t)R.N * R.C * plane * gfk::dtype_size(R.dt_out);
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     DeviceGuard guard(ctx->device);
+    std::lock_guard<std::mutex> host_lock(ctx->host_mu);  // the staging buffers serve one host call at a time
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     char *base;
     {
@@ -434,7 +564,10 @@ gf_status gf_filter_host(gf_ctx *ctx, const void *I_host, const void *p_host, vo
         if (st != GF_OK) return st;
         base = (char *)ctx->stage;
     }
-    void *dI = base, *dp = base + al(bI), *dq = base + al(bI) + al(bp);
+    char *dI = base, *dp = base + al(bI), *dq = base + al(bI) + al(bp);
+    std::vector<int> Y;
+    if (host_strips(R, opts, bI + bp + bq, Y) >= 2)
+        return host_pipeline(ctx, R, Y, I_host, p_host, q_host, dI, dp, dq, r, eps, s, mode, opts, stream);
     cudaError_t e;
     if ((e = cudaMemcpyAsync(dI, I_host, bI, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpyAsync of I");
@@ -446,6 +579,21 @@ gf_status gf_filter_host(gf_ctx *ctx, const void *I_host, const void *p_host, vo
         return cuda_fail(e, "cudaMemcpyAsync of q");
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return GF_OK;
+}
+
+int gf_host_strips(int H, int W, int C, int s, gf_subsample_mode mode, const gf_opts *opts, int *row_starts)
+{
+    Resolved R;
+    if (resolve(H, W, C, 0, 0.0f, s, (int)mode, opts, R) != GF_OK) return -1;
+    const size_t plane = (size_t)R.H * R.W;
+    const size_t bytes = (size_t)R.N * (R.CI + R.C) * plane * gfk::dtype_size(R.dt_in) +
+                         (size_t)R.N * R.C * plane * gfk::dtype_size(R.dt_out);
+    std::vector<int> Y;
+    const int K = host_strips(R, opts, bytes, Y);
+    if (K < 2) return 1;
+    if (row_starts)
+        for (int k = 0; k <= K; ++k) row_starts[k] = Y[k];
+    return K;
 }
 
 gf_status gf_backward_workspace_size(int H, int W, int C, int s, const gf_opts *opts, size_t *bytes)

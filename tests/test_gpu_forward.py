@@ -241,6 +241,47 @@ def test_host_buffers_match_device_call(gf):
     np.testing.assert_array_equal(q_host, q_dev)
 
 
+@pytest.mark.parametrize("N,CI,C,H,W,s,mode,dtype,pinned", [
+    (1, 1, 3, 1100, 900, 4, 1, torch.float32, False),   # ragged last strip, pageable host memory
+    (1, 1, 3, 1100, 904, 4, 1, torch.float32, True),    # pinned: the copies overlap
+    (2, 3, 3, 600, 700, 4, 2, torch.float16, True),     # batch, depthwise guide, FP16 storage, box
+    (1, 1, 3, 1200, 1000, 8, 0, torch.uint8, True),     # uint8, s = 8 nearest
+])
+def test_host_pipeline_matches_device_call(gf, N, CI, C, H, W, s, mode, dtype, pinned):
+    """Large host calls run as a strip pipeline (uploads, row-range filters and downloads overlapping on
+    three streams); every strip equals the same rows of the one-piece device call up to FP32 rounding order
+    and the FP64 oracle within the path's tolerance."""
+    ys = gf.host_strips(H, W, C, s, MODE_NAMES[mode], batch=N, guide_channels=CI, dtype=dtype)
+    assert ys is not None and len(ys) >= 3
+    I = _rand((N, CI, H, W), 21)
+    p = _rand((N, C, H, W), 22)
+    if dtype == torch.uint8:
+        Iq, pq = (np.round(I * 255.0).astype(np.uint8), np.round(p * 255.0).astype(np.uint8))
+        I_t, p_t = torch.from_numpy(Iq), torch.from_numpy(pq)
+        I_ref, p_ref = Iq / 255.0, pq / 255.0
+        tol = TOL_F32
+    elif dtype == torch.float16:
+        I_t, p_t = torch.from_numpy(I).half(), torch.from_numpy(p).half()
+        I_ref, p_ref = I_t.double().numpy(), p_t.double().numpy()
+        tol = TOL_F16
+    else:
+        I_t, p_t = torch.from_numpy(I), torch.from_numpy(p)
+        I_ref, p_ref = I.astype(np.float64), p.astype(np.float64)
+        tol = TOL_F32
+    if pinned:
+        I_t, p_t = I_t.pin_memory(), p_t.pin_memory()
+    ctx = gf.Context(0)
+    q_host = gf.fast_guided_filter_host(I_t, p_t, 16, 1e-3, s, MODE_NAMES[mode], ctx=ctx)
+    q_host2 = gf.fast_guided_filter_host(I_t, p_t, 16, 1e-3, s, MODE_NAMES[mode], ctx=ctx)  # reused streams
+    q_dev = gf.fast_guided_filter(I_t.cuda(), p_t.cuda(), 16, 1e-3, s, MODE_NAMES[mode], ctx=ctx)
+    torch.cuda.synchronize()
+    q_host, q_host2, q_dev = q_host.float().numpy(), q_host2.float().numpy(), q_dev.float().cpu().numpy()
+    np.testing.assert_array_equal(q_host, q_host2)
+    assert max_abs(q_host, q_dev) <= (2e-3 if dtype == torch.float16 else 2e-5)
+    ref = oracle_q(I_ref, p_ref, 16, 1e-3, s, mode)
+    assert max_abs(q_host, ref) <= tol
+
+
 def test_caller_workspace(gf):
     import ctypes
     I = _rand((1, 1, 70, 90), 13)
