@@ -206,16 +206,18 @@ gf_status gf_filter(gf_ctx *ctx, const void *I, const void *p, void *q, int H, i
  * filtered as a row-range call (gf_opts.row_begin / row_end) as soon as the input rows of its band are on
  * the device, and its output rows are copied back while later strips are uploaded and filtered (two copy
  * streams owned by the context).  Each strip equals the same rows of the whole-image call up to FP32
- * rounding order.
+ * rounding order.  With nearest or bilinear subsampling at s >= 3 only the rows of p that the subsample
+ * reads are uploaded (rows s j + (s - 1) / 2 and the next of every s-row block, and a partial last block
+ * whole): half of p at s = 4, a quarter at s = 8.
  */
 gf_status gf_filter_host(gf_ctx *ctx, const void *I_host, const void *p_host, void *q_host, int H, int W, int C,
                          int r, float eps, int s, gf_subsample_mode mode, const gf_opts *opts, void *cuda_stream);
 
 /* The strips gf_filter_host pipelines a call with these arguments in (host-only): returns K >= 2 and, if
  * row_starts is not NULL, writes its K + 1 boundaries 0 = Y_0 < Y_1 < ... < Y_K = H (multiples of 8 s;
- * up to 8 strips, at least 64 s rows each); returns 1 when the call is not pipelined (under 8 MiB of host
- * data, a low-res p, a colour guide, a non-integer ratio, the single fused kernel, low-res outputs, its
- * own row range or kernel events), -1 for invalid arguments.  row_starts holds at least 9 ints. */
+ * up to 16 strips, at least 32 s rows each); returns 1 when the call is not pipelined (under 8 MiB of
+ * host data, a low-res p, a colour guide, a non-integer ratio, the single fused kernel, low-res outputs,
+ * its own row range or kernel events), -1 for invalid arguments.  row_starts holds at least 17 ints. */
 int gf_host_strips(int H, int W, int C, int s, gf_subsample_mode mode, const gf_opts *opts, int *row_starts);
 
 /*

@@ -325,7 +325,7 @@ namespace {
 // each strip's band needs are copied in on one stream, the strip is filtered on the caller's stream as a
 // row-range call (the same rows as the whole-image call up to FP32 rounding order), and its output rows are
 // copied out on a third stream, so uploads, filtering and downloads of different strips overlap.
-constexpr int HOST_MAX_STRIPS = 8;
+constexpr int HOST_MAX_STRIPS = 16;
 constexpr size_t HOST_PIPE_MIN_BYTES = size_t(8) << 20;  // below this the copies are too short to overlap
 
 // Strip boundaries Y[0] = 0 < ... < Y[K] = H (multiples of 8 s), K >= 2; or K < 2 when the call keeps the
@@ -338,7 +338,7 @@ int host_strips(const Resolved &R, const gf_opts *o, size_t host_bytes, std::vec
     if (R.sd != 1 || R.color || R.p_lowres || R.fused || R.dense_lowres) return 0;
     if (o && (o->row_begin || o->row_end || o->stats_out || o->kernel_events)) return 0;
     const int align = 8 * R.s;
-    const int K = std::min(HOST_MAX_STRIPS, R.H / (64 * R.s));
+    const int K = std::min(HOST_MAX_STRIPS, R.H / (32 * R.s));
     if (K < 2) return 0;
     const int rows = (R.H + K - 1) / K;
     const int step = (rows + align - 1) / align * align;
@@ -390,6 +390,11 @@ gf_status host_pipeline(gf_ctx *ctx, const Resolved &R, const std::vector<int> &
     const size_t ein = gfk::dtype_size(R.dt_in), eout = gfk::dtype_size(R.dt_out);
     const size_t plane = (size_t)H * W;
     const int in_planes = R.N * R.CI, p_planes = R.N * C;
+    // Nearest and bilinear subsampling read p only through the subsample, which takes rows s j + o and
+    // s j + o + 1 (o = floor((s - 1) / 2)) of block j, clamped to the last row: only those rows of p are
+    // uploaded (half of p at s = 4, a quarter at s = 8).  The other rows of the staging copy are never read.
+    const bool sampled_p = (R.mode == GF_SUB_NEAREST || R.mode == GF_SUB_BILINEAR) && s >= 3;
+    const int o = (s - 1) / 2;
     gf_status result = GF_OK;
     auto check = [&](cudaError_t err, const char *what) {
         if (err != cudaSuccess && result == GF_OK) result = cuda_fail(err, what);
@@ -406,9 +411,29 @@ gf_status host_pipeline(gf_ctx *ctx, const Resolved &R, const std::vector<int> &
             for (int pl = 0; ok && pl < in_planes; ++pl)
                 ok = check(cudaMemcpyAsync(dI + (pl * plane + off) * ein, (const char *)I_host + (pl * plane + off) * ein,
                                            n * ein, cudaMemcpyHostToDevice, ctx->copy_in), "cudaMemcpyAsync of I rows");
-            for (int pl = 0; ok && pl < p_planes; ++pl)
-                ok = check(cudaMemcpyAsync(dp + (pl * plane + off) * ein, (const char *)p_host + (pl * plane + off) * ein,
-                                           n * ein, cudaMemcpyHostToDevice, ctx->copy_in), "cudaMemcpyAsync of p rows");
+            if (!sampled_p) {
+                for (int pl = 0; ok && pl < p_planes; ++pl)
+                    ok = check(cudaMemcpyAsync(dp + (pl * plane + off) * ein, (const char *)p_host + (pl * plane + off) * ein,
+                                               n * ein, cudaMemcpyHostToDevice, ctx->copy_in), "cudaMemcpyAsync of p rows");
+            } else {
+                // rows s j + o and s j + o + 1 of each whole s-row block (copied starts on a block), and every
+                // row of a partial last block (its samples may be clamped to row H - 1)
+                const int whole = (band_end[k] == H ? H / s : band_end[k] / s) - copied / s;
+                const size_t bpitch = (size_t)s * W * ein;
+                for (int pl = 0; ok && whole > 0 && pl < p_planes; ++pl) {
+                    const size_t at = (pl * plane + (size_t)(copied + o) * W) * ein;
+                    ok = check(cudaMemcpy2DAsync(dp + at, bpitch, (const char *)p_host + at, bpitch, 2 * (size_t)W * ein,
+                                                 whole, cudaMemcpyHostToDevice, ctx->copy_in), "cudaMemcpy2DAsync of p rows");
+                }
+                const int tail0 = std::max(copied, H / s * s);
+                if (band_end[k] == H && tail0 < H) {
+                    const size_t t_off = (size_t)tail0 * W, t_n = (size_t)(H - tail0) * W;
+                    for (int pl = 0; ok && pl < p_planes; ++pl)
+                        ok = check(cudaMemcpyAsync(dp + (pl * plane + t_off) * ein,
+                                                   (const char *)p_host + (pl * plane + t_off) * ein, t_n * ein,
+                                                   cudaMemcpyHostToDevice, ctx->copy_in), "cudaMemcpyAsync of p rows");
+                }
+            }
             copied = band_end[k];
         }
         ok = ok && check(cudaEventRecord(ev[1 + k], ctx->copy_in), "cudaEventRecord") &&

@@ -246,11 +246,14 @@ def test_host_buffers_match_device_call(gf):
     (1, 1, 3, 1100, 904, 4, 1, torch.float32, True),    # pinned: the copies overlap
     (2, 3, 3, 600, 700, 4, 2, torch.float16, True),     # batch, depthwise guide, FP16 storage, box
     (1, 1, 3, 1200, 1000, 8, 0, torch.uint8, True),     # uint8, s = 8 nearest
+    (1, 1, 3, 1102, 900, 3, 1, torch.float32, True),    # odd s: rows 1, 2 of each block; partial last block
+    (1, 1, 1, 2050, 1200, 8, 0, torch.float32, True),   # nearest s = 8, partial last block (rows clamped)
 ])
 def test_host_pipeline_matches_device_call(gf, N, CI, C, H, W, s, mode, dtype, pinned):
     """Large host calls run as a strip pipeline (uploads, row-range filters and downloads overlapping on
-    three streams); every strip equals the same rows of the one-piece device call up to FP32 rounding order
-    and the FP64 oracle within the path's tolerance."""
+    three streams, only the sampled rows of p uploaded for nearest / bilinear at s >= 3); every strip equals
+    the same rows of the one-piece device call up to FP32 rounding order and the FP64 oracle within the
+    path's tolerance."""
     ys = gf.host_strips(H, W, C, s, MODE_NAMES[mode], batch=N, guide_channels=CI, dtype=dtype)
     assert ys is not None and len(ys) >= 3
     I = _rand((N, CI, H, W), 21)
