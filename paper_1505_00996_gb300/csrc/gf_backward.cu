@@ -19,10 +19,14 @@
 // the transposed bilinear / subsample maps, evaluated as gathers (no atomics).
 //
 //   k_bwd_upsample_T   dMA, dMB: per low-res tile, a horizontal gather of g.*I and g into a shared table of
-//                      full-res rows x low-res columns, then a vertical gather.
+//                      full-res rows x low-res columns, then a vertical gather; k_bwd_upsample_T_v is its
+//                      block-vector form for s = 4, 8 (float4 loads, constant tap weights inside the image).
 //   k_bwd_box_T        B^T of 2 maps with the chain epilogue (4 maps out, per-CTA partial sums of deps), or
-//                      B^T of 4 maps with the final combination into dI', dp'.  Same tiling as k_box_tile.
-//   k_bwd_full         full-res: dI = sum_c g_c U(mean_a_c) + D^T(dI'), dp = D^T(dp').
+//                      B^T of 4 maps with the final combination into dI', dp'.  Same tiling as k_box_tile;
+//                      the epilogue runs in the write-out phase, a thread per pixel, so the forward planes it
+//                      reads (statistics, a, I', p') are read coalesced.
+//   k_bwd_full         full-res: dI = sum_c g_c U(mean_a_c) + D^T(dI'), dp = D^T(dp'); k_bwd_full_v is its
+//                      4-pixel vector form for s = 4, 8 (H, W multiples of s), where D^T is block-local.
 //   k_reduce_eps       deterministic sum of the per-CTA deps partials (FP64 accumulation).
 #include <algorithm>
 
@@ -122,6 +126,114 @@ __global__ void __launch_bounds__(UT_NT) k_bwd_upsample_T(UpTParams P)
     }
 }
 
+// Vector form of k_bwd_upsample_T for s = 4, 8 with W a multiple of s and 16-byte aligned planes.  The
+// horizontal gather runs per s-pixel block (float4 loads of g and I): under the bilinear upsample, pixel
+// t of block i (t < s/2) feeds low-res columns i - 1 and i, and pixel t >= s/2 feeds i and i + 1, with
+// weights that are compile-time constants away from the image's first and last block (there the clamped
+// taps are formed by up_taps).  Each block leaves its contributions to its left neighbour, itself and its
+// right neighbour in a shared table; column i of the tile then adds its own, its left block's right and its
+// right block's left contribution.  The vertical gather is k_bwd_upsample_T's.
+template <int S>
+__global__ void __launch_bounds__(UT_NT) k_bwd_upsample_T_v(UpTParams P)
+{
+    static_assert(S % 4 == 0, "blocks of whole float4 groups");
+    extern __shared__ float sm[];
+    constexpr int NB = UT_TI + 2;            // blocks i0 - 1 .. i0 + UT_TI
+    constexpr int ncand = 3 * S;
+    const int TJ = P.TJ;
+    const int i0 = blockIdx.x * UT_TI, j0 = blockIdx.y * TJ;
+    const int plane = blockIdx.z, n = plane / P.C, c = plane - n * P.C;
+    const size_t HW = (size_t)P.H * P.W;
+    const float *g = P.g + (size_t)plane * HW;
+    const float *I = P.I + (size_t)(n * P.CI + (P.CI == 1 ? 0 : c)) * HW;
+    const int Y0 = max(0, S * (j0 - 1)), Y1 = min(P.H, S * (j0 + TJ + 1));
+    const int NR = Y1 - Y0;
+    float *Hs = sm;                          // [6][NR][NB]: g.*I to (left, own, right), then g to the same
+    float *Tga = Hs + (size_t)6 * NR * NB;   // [NR][UT_TI] horizontal gathers of g .* I
+    float *Tg = Tga + (size_t)NR * UT_TI;    // [NR][UT_TI] horizontal gathers of g
+    float *wy = Tg + (size_t)NR * UT_TI;     // [TJ][ncand] weights of Y = s(j-1) + t onto row j
+    for (int k = threadIdx.x; k < TJ * ncand; k += UT_NT) {
+        const int jl = k / ncand, t = k - jl * ncand;
+        const int j = j0 + jl, Y = S * (j - 1) + t;
+        wy[k] = (j < P.h && Y >= 0 && Y < P.H) ? up_weight(Y, j, S, P.h) : 0.0f;
+    }
+    const size_t hs = (size_t)NR * NB;
+    for (int k = threadIdx.x; k < NR * NB; k += UT_NT) {
+        const int yl = k / NB, bl = k - yl * NB;
+        const int i = i0 - 1 + bl;
+        float ga[3] = {0.0f, 0.0f, 0.0f}, gg[3] = {0.0f, 0.0f, 0.0f};  // to columns i - 1, i, i + 1
+        if (i >= 0 && i < P.w) {
+            const size_t ro = (size_t)(Y0 + yl) * P.W + (size_t)i * S;
+            const bool inner = i >= 1 && i <= P.w - 2;
+#pragma unroll
+            for (int v = 0; v < S / 4; ++v) {
+                const float4 g4 = __ldg(reinterpret_cast<const float4 *>(g + ro + 4 * v));
+                const float4 I4 = __ldg(reinterpret_cast<const float4 *>(I + ro + 4 * v));
+                const float gv[4] = {g4.x, g4.y, g4.z, g4.w}, Iv[4] = {I4.x, I4.y, I4.z, I4.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int t = 4 * v + u;
+                    const float a = gv[u] * Iv[u];
+                    if (inner) {
+                        // source position (X + 1/2)/s - 1/2 = i + (2t + 1 - s)/(2s): taps i - 1, i or i, i + 1
+                        const bool lo = 2 * t + 1 < S;
+                        const float f = (float)(2 * t + 1 - S + (lo ? 2 * S : 0)) / (float)(2 * S);
+                        const int k0 = lo ? 0 : 1;
+                        ga[k0] = fmaf(1.0f - f, a, ga[k0]);
+                        ga[k0 + 1] = fmaf(f, a, ga[k0 + 1]);
+                        gg[k0] = fmaf(1.0f - f, gv[u], gg[k0]);
+                        gg[k0 + 1] = fmaf(f, gv[u], gg[k0 + 1]);
+                    } else {
+                        int xa, xb;
+                        float f;
+                        up_taps(i * S + t, S, P.w, xa, xb, f);
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            const float wgt = (xa == i - 1 + d ? 1.0f - f : 0.0f) + (xb == i - 1 + d ? f : 0.0f);
+                            ga[d] = fmaf(wgt, a, ga[d]);
+                            gg[d] = fmaf(wgt, gv[u], gg[d]);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            Hs[d * hs + k] = ga[d];
+            Hs[(3 + d) * hs + k] = gg[d];
+        }
+    }
+    __syncthreads();
+    // column il of the tile (block bl = il + 1): own + left block's right + right block's left
+    for (int k = threadIdx.x; k < NR * UT_TI; k += UT_NT) {
+        const int yl = k / UT_TI, il = k - yl * UT_TI;
+        const size_t b = (size_t)yl * NB + il;
+        Tga[k] = Hs[1 * hs + b + 1] + Hs[2 * hs + b] + Hs[0 * hs + b + 2];
+        Tg[k] = Hs[4 * hs + b + 1] + Hs[5 * hs + b] + Hs[3 * hs + b + 2];
+    }
+    __syncthreads();
+    // vertical gather: dM[j][i] = sum_y wy(y -> j) T[y][i]
+    for (int k = threadIdx.x; k < TJ * UT_TI; k += UT_NT) {
+        const int jl = k / UT_TI, il = k - jl * UT_TI;
+        const int j = j0 + jl, i = i0 + il;
+        if (j >= P.h || i >= P.w) continue;
+        float sa = 0.0f, sb = 0.0f;
+        const int yb = S * (j - 1);
+#pragma unroll 4
+        for (int t = 0; t < ncand; ++t) {
+            const float wgt = wy[jl * ncand + t];
+            if (wgt != 0.0f) {
+                const int yl = yb + t - Y0;
+                sa = fmaf(wgt, Tga[yl * UT_TI + il], sa);
+                sb = fmaf(wgt, Tg[yl * UT_TI + il], sb);
+            }
+        }
+        const size_t o = (size_t)plane * P.lps + (size_t)j * P.w + i;
+        P.dma[o] = sa;
+        P.dmb[o] = sb;
+    }
+}
+
 // ------------------------------------------------------------------------------------------------------
 // k_bwd_box_T
 // ------------------------------------------------------------------------------------------------------
@@ -161,7 +273,7 @@ __global__ void __launch_bounds__(BB_NT) k_bwd_box_T(BoxTParams P)
     const int h = P.h, w = P.w, r = P.r;
     const int span = BB_TW + 2 * r;
     float *Vt = smf;                                 // [NIN][span][BB_VP]
-    float *Ot = smf + (size_t)NIN * span * BB_VP;     // [NOUT][BB_TH][BB_OP]
+    float *Ot = smf;                                 // [NIN][BB_TH][BB_OP] window sums, over Vt after phase 2
     const int x0 = blockIdx.x * BB_TW, y0 = blockIdx.y * BB_TH;
     const int plane = blockIdx.z;
     const size_t pbase = (size_t)plane * P.lps;
@@ -210,86 +322,102 @@ __global__ void __launch_bounds__(BB_NT) k_bwd_box_T(BoxTParams P)
     }
     __syncthreads();
 
-    // ---- phase 2: horizontal sums and the epilogue
+    // ---- phase 2: horizontal sums, one row segment per thread; the sums wait in registers until every thread
+    // has read the column sums, then go to a staging tile over them
+    static_assert(BB_TH * (BB_TW / BB_RH) <= BB_NT, "one phase-2 item per thread");
+    float O[NIN][BB_RH];
+    {
+        const int yr = tid % BB_TH, seg = tid / BB_TH;
+        const int y = y0 + yr, xa = seg * BB_RH;
+        const bool item = tid < BB_TH * (BB_TW / BB_RH) && y < h && x0 + xa < w;
+        if (item) {
+            float S[NIN], Sc[NIN];
+#pragma unroll
+            for (int q = 0; q < NIN; ++q) { S[q] = 0.0f; Sc[q] = 0.0f; }
+            auto vacc = [&](int col, float sign) {
+#pragma unroll
+                for (int q = 0; q < NIN; ++q) {
+                    const float v = sign * Vt[((size_t)q * span + col) * BB_VP + yr];
+                    if (COMP) {
+                        const float t = S[q] + v;
+                        Sc[q] += (fabsf(S[q]) >= fabsf(v)) ? ((S[q] - t) + v) : ((v - t) + S[q]);
+                        S[q] = t;
+                    } else {
+                        S[q] += v;
+                    }
+                }
+            };
+            for (int k = 0; k <= 2 * r; ++k) vacc(xa + k, 1.0f);
+#pragma unroll
+            for (int i = 0; i < BB_RH; ++i) {
+                if (x0 + xa + i >= w) break;
+                if (i > 0) {
+                    vacc(xa + i + 2 * r, 1.0f);
+                    vacc(xa + i - 1, -1.0f);
+                }
+#pragma unroll
+                for (int q = 0; q < NIN; ++q) O[q][i] = S[q] + Sc[q];
+            }
+        }
+        __syncthreads();  // every column sum has been read
+        if (item) {
+#pragma unroll
+            for (int i = 0; i < BB_RH; ++i) {
+                if (x0 + xa + i >= w) break;
+#pragma unroll
+                for (int q = 0; q < NIN; ++q) Ot[(q * BB_TH + yr) * BB_OP + xa + i] = O[q][i];
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 3: the epilogue, thread per output pixel (coalesced reads of the forward planes and writes)
     float eps_acc = 0.0f;
     const int n = plane / P.C, c = plane - n * P.C;
-    for (int item = tid; item < BB_TH * (BB_TW / BB_RH); item += BB_NT) {
-        const int yr = item % BB_TH, seg = item / BB_TH;
-        const int y = y0 + yr, xa = seg * BB_RH;
-        if (y >= h || x0 + xa >= w) continue;
-        float S[NIN], Sc[NIN];
+    for (int idx = tid; idx < BB_TH * BB_TW; idx += BB_NT) {
+        const int yr = idx / BB_TW, xt = idx - yr * BB_TW;
+        const int y = y0 + yr, x = x0 + xt;
+        if (y >= h || x >= w) continue;
+        const size_t pix = (size_t)y * w + x;
+        float t[NIN];
 #pragma unroll
-        for (int q = 0; q < NIN; ++q) { S[q] = 0.0f; Sc[q] = 0.0f; }
-        auto vacc = [&](int col, float sign) {
-#pragma unroll
-            for (int q = 0; q < NIN; ++q) {
-                const float v = sign * Vt[((size_t)q * span + col) * BB_VP + yr];
-                if (COMP) {
-                    const float t = S[q] + v;
-                    Sc[q] += (fabsf(S[q]) >= fabsf(v)) ? ((S[q] - t) + v) : ((v - t) + S[q]);
-                    S[q] = t;
-                } else {
-                    S[q] += v;
-                }
-            }
-        };
-        for (int k = 0; k <= 2 * r; ++k) vacc(xa + k, 1.0f);
-#pragma unroll
-        for (int i = 0; i < BB_RH; ++i) {
-            const int xt = xa + i, x = x0 + xt;
-            if (x >= w) break;
-            if (i > 0) {
-                vacc(xt + 2 * r, 1.0f);
-                vacc(xt - 1, -1.0f);
-            }
-            const size_t pix = (size_t)y * w + x;
-            float o[NOUT];
-            if (EPI == EPI_CHAIN) {
-                const float da0 = S[0] + Sc[0], db = S[1] + Sc[1];  // B^T(dMA), B^T(dMB)
-                const size_t ps = (size_t)h * w;
-                const float *st = P.stats + (size_t)plane * 4 * ps + pix;
-                const float mI = st[0], cI = st[ps], mp = st[2 * ps];
-                const float a = P.a[pbase + pix];
-                const float var = fmaxf(cI - mI * mI, 0.0f);
-                const float inv = 1.0f / (var + P.eps);
-                const float da = da0 - mI * db;          // through b = mean_p - a mean_I
-                const float dcov = da * inv;              // through a = cov / (var + eps)
-                const float dvar = -da * a * inv;
-                eps_acc += dvar;
-                o[0] = -a * db - 2.0f * mI * dvar - mp * dcov;  // d mean_I
-                o[1] = dvar;                                    // d corr_I
-                o[2] = dcov;                                    // d corr_Ip
-                o[3] = db - mI * dcov;                          // d mean_p
-            } else {
-                const float tmI = S[0] + Sc[0], tcII = S[1] + Sc[1], tcIp = S[2] + Sc[2], tmp = S[3] + Sc[3];
-                const float Iv = P.Il[(size_t)(n * P.CI + (P.CI == 1 ? 0 : c)) * P.xps + pix];
-                const float pv = P.pl[(size_t)plane * P.yps + pix];
-                o[0] = tmI + 2.0f * Iv * tcII + pv * tcIp;  // dI'
-                o[1] = tmp + Iv * tcIp;                     // dp'
-            }
-#pragma unroll
-            for (int q = 0; q < NOUT; ++q) Ot[(q * BB_TH + yr) * BB_OP + xt] = o[q];
+        for (int q = 0; q < NIN; ++q) t[q] = Ot[(q * BB_TH + yr) * BB_OP + xt];
+        float o[NOUT];
+        if (EPI == EPI_CHAIN) {
+            const float da0 = t[0], db = t[1];  // B^T(dMA), B^T(dMB)
+            const size_t ps = (size_t)h * w;
+            const float *st = P.stats + (size_t)plane * 4 * ps + pix;
+            const float mI = st[0], cI = st[ps], mp = st[2 * ps];
+            const float a = P.a[pbase + pix];
+            const float var = fmaxf(cI - mI * mI, 0.0f);
+            const float inv = 1.0f / (var + P.eps);
+            const float da = da0 - mI * db;          // through b = mean_p - a mean_I
+            const float dcov = da * inv;              // through a = cov / (var + eps)
+            const float dvar = -da * a * inv;
+            eps_acc += dvar;
+            o[0] = -a * db - 2.0f * mI * dvar - mp * dcov;  // d mean_I
+            o[1] = dvar;                                    // d corr_I
+            o[2] = dcov;                                    // d corr_Ip
+            o[3] = db - mI * dcov;                          // d mean_p
+        } else {
+            const float tmI = t[0], tcII = t[1], tcIp = t[2], tmp = t[3];
+            const float Iv = P.Il[(size_t)(n * P.CI + (P.CI == 1 ? 0 : c)) * P.xps + pix];
+            const float pv = P.pl[(size_t)plane * P.yps + pix];
+            o[0] = tmI + 2.0f * Iv * tcII + pv * tcIp;  // dI'
+            o[1] = tmp + Iv * tcIp;                     // dp'
         }
+#pragma unroll
+        for (int q = 0; q < NOUT; ++q) P.out[q][pbase + pix] = o[q];
     }
     if (EPI == EPI_CHAIN) {
         // deterministic CTA reduction of the deps contributions
         for (int off = 16; off > 0; off >>= 1) eps_acc += __shfl_xor_sync(0xffffffffu, eps_acc, off);
         if ((tid & 31) == 0) red[tid >> 5] = eps_acc;
-    }
-    __syncthreads();
-    if (EPI == EPI_CHAIN && tid == 0) {
-        float t = 0.0f;
-        for (int k = 0; k < BB_NT / 32; ++k) t += red[k];
-        P.eps_partial[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
-    }
-
-    // ---- phase 3: coalesced write-out
-    for (int idx = tid; idx < BB_TH * BB_TW; idx += BB_NT) {
-        const int yr = idx / BB_TW, xt = idx - yr * BB_TW;
-        const int y = y0 + yr, x = x0 + xt;
-        if (y < h && x < w) {
-#pragma unroll
-            for (int q = 0; q < NOUT; ++q) P.out[q][pbase + (size_t)y * w + x] = Ot[(q * BB_TH + yr) * BB_OP + xt];
+        __syncthreads();
+        if (tid == 0) {
+            float tt = 0.0f;
+            for (int k = 0; k < BB_NT / 32; ++k) tt += red[k];
+            P.eps_partial[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = tt;
         }
     }
 }
@@ -375,6 +503,62 @@ __global__ void __launch_bounds__(BF_NT) k_bwd_full(FullParams P)
     if (P.CI == 1) P.dI[(size_t)n * HW + pix] = dI_shared;
 }
 
+// Vector form of k_bwd_full for s = 4, 8 with H and W multiples of s and 16-byte aligned planes.  Then every
+// transposed-subsample weight of a full-res pixel comes from its own s x s block -- the block's mean (box),
+// its centre pixel (nearest) or its central 2 x 2 (bilinear at even s) -- with weight wsub(Y mod s) *
+// wsub(X mod s).  A thread owns 4 adjacent pixels of one row, all in one block: it reads g as float4, takes
+// the block's dI', dp' once, and writes dI (and dp) as float4.
+template <int S, int MODE>
+__global__ void __launch_bounds__(BF_NT) k_bwd_full_v(FullParams P)
+{
+    static_assert(S % 4 == 0, "4 adjacent pixels in one block");
+    const int X0 = 4 * (blockIdx.x * BF_NT + threadIdx.x), Y = blockIdx.y, n = blockIdx.z;
+    if (X0 >= P.W) return;
+    const size_t HW = (size_t)P.H * P.W, pix = (size_t)Y * P.W + X0;
+    int ya, yb, xa[4], xb[4];
+    float fy, fx[4];
+    up_taps(Y, S, P.h, ya, yb, fy);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) up_taps(X0 + k, S, P.w, xa[k], xb[k], fx[k]);
+    auto wsub = [](int t) -> float {
+        if (MODE == GF_SUB_BOX) return 1.0f / (float)S;
+        if (MODE == GF_SUB_NEAREST) return t == S / 2 ? 1.0f : 0.0f;
+        return (t == S / 2 - 1 || t == S / 2) ? 0.5f : 0.0f;  // bilinear, even s
+    };
+    const float wy = wsub(Y % S);
+    float wx[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) wx[k] = wsub((X0 + k) % S);
+    const size_t blk = (size_t)(Y / S) * P.w + X0 / S;  // the block's low-res pixel
+    float4 shared = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int c = 0; c < P.C; ++c) {
+        const size_t lp = (size_t)(n * P.C + c) * P.lps;
+        const float *ra = P.ma + lp + (size_t)ya * P.w, *rb = P.ma + lp + (size_t)yb * P.w;
+        float A[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {  // U(mean_a), as k_bwd_full forms it
+            const float A0 = fmaf(fx[k], __ldg(ra + xb[k]) - __ldg(ra + xa[k]), __ldg(ra + xa[k]));
+            const float A1 = fmaf(fx[k], __ldg(rb + xb[k]) - __ldg(rb + xa[k]), __ldg(rb + xa[k]));
+            A[k] = fmaf(fy, A1 - A0, A0);
+        }
+        const float4 gv = __ldg(reinterpret_cast<const float4 *>(P.g + (size_t)(n * P.C + c) * HW + pix));
+        const float tI = wy != 0.0f ? wy * __ldg(P.dIl + lp + blk) : 0.0f;  // D^T(dI') before the x weight
+        const float4 dIc = make_float4(fmaf(gv.x, A[0], tI * wx[0]), fmaf(gv.y, A[1], tI * wx[1]),
+                                       fmaf(gv.z, A[2], tI * wx[2]), fmaf(gv.w, A[3], tI * wx[3]));
+        if (P.CI == 1) {
+            shared.x += dIc.x; shared.y += dIc.y; shared.z += dIc.z; shared.w += dIc.w;
+        } else {
+            *reinterpret_cast<float4 *>(P.dI + (size_t)(n * P.CI + c) * HW + pix) = dIc;
+        }
+        if (P.dp) {
+            const float tp = wy != 0.0f ? wy * __ldg(P.dpl + lp + blk) : 0.0f;  // D^T(dp')
+            *reinterpret_cast<float4 *>(P.dp + (size_t)(n * P.C + c) * HW + pix) =
+                make_float4(tp * wx[0], tp * wx[1], tp * wx[2], tp * wx[3]);
+        }
+    }
+    if (P.CI == 1) *reinterpret_cast<float4 *>(P.dI + (size_t)n * HW + pix) = shared;
+}
+
 // ------------------------------------------------------------------------------------------------------
 // k_reduce_eps
 // ------------------------------------------------------------------------------------------------------
@@ -400,8 +584,8 @@ namespace {
 template <int NIN, int EPI>
 cudaError_t launch_box_T(const BoxTParams &bp, int planes, cudaStream_t st)
 {
-    const size_t smem = ((size_t)NIN * (BB_TW + 2 * bp.r) * BB_VP + (size_t)((EPI == EPI_CHAIN) ? 4 : 2) * BB_TH * BB_OP) *
-                        sizeof(float);
+    // the staging tile of the window sums lies over the column sums: the larger of the two
+    const size_t smem = std::max((size_t)NIN * (BB_TW + 2 * bp.r) * BB_VP, (size_t)NIN * BB_TH * BB_OP) * sizeof(float);
     dim3 grid((bp.w + BB_TW - 1) / BB_TW, (bp.h + BB_TH - 1) / BB_TH, planes);
     if (bp.r > 16) {
         cudaError_t e = opt_in_smem(k_bwd_box_T<NIN, EPI, true>, smem);
@@ -431,7 +615,27 @@ cudaError_t launch_backward(const BwdPlan &B, cudaStream_t st)
     if ((err = launch_forward(F, st)) != cudaSuccess) return err;
 
     // ---- dMA = U^T(g .* I), dMB = U^T(g)
-    {
+    const bool up_vec = (F.s == 4 || F.s == 8) && F.W % F.s == 0 &&
+                        ((reinterpret_cast<uintptr_t>(B.dq) | reinterpret_cast<uintptr_t>(F.I)) & 15u) == 0;
+    if (up_vec) {
+        UpTParams up;
+        up.g = B.dq; up.I = (const float *)F.I; up.dma = B.dma; up.dmb = B.dmb;
+        up.C = F.C; up.CI = F.CI; up.H = F.H; up.W = F.W; up.h = F.h; up.w = F.w; up.s = F.s;
+        up.TJ = F.s == 4 ? 8 : 4;
+        up.lps = F.lps;
+        const int NRmax = F.s * (up.TJ + 2);
+        const size_t smem = ((size_t)6 * NRmax * (UT_TI + 2) + (size_t)2 * NRmax * UT_TI + (size_t)up.TJ * 3 * F.s) *
+                            sizeof(float);
+        dim3 grid((F.w + UT_TI - 1) / UT_TI, (F.h + up.TJ - 1) / up.TJ, planes);
+        if (F.s == 4) {
+            if ((err = opt_in_smem(k_bwd_upsample_T_v<4>, smem)) != cudaSuccess) return err;
+            k_bwd_upsample_T_v<4><<<grid, UT_NT, smem, st>>>(up);
+        } else {
+            if ((err = opt_in_smem(k_bwd_upsample_T_v<8>, smem)) != cudaSuccess) return err;
+            k_bwd_upsample_T_v<8><<<grid, UT_NT, smem, st>>>(up);
+        }
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    } else {
         UpTParams up;
         up.g = B.dq; up.I = (const float *)F.I; up.dma = B.dma; up.dmb = B.dmb;
         up.C = F.C; up.CI = F.CI; up.H = F.H; up.W = F.W; up.h = F.h; up.w = F.w; up.s = F.s;
@@ -476,8 +680,26 @@ cudaError_t launch_backward(const BwdPlan &B, cudaStream_t st)
         fp.dp = F.p_lowres ? nullptr : B.dp;
         fp.C = F.C; fp.CI = F.CI; fp.H = F.H; fp.W = F.W; fp.h = F.h; fp.w = F.w; fp.s = F.s; fp.mode = F.mode;
         fp.lps = F.lps;
-        dim3 grid((F.W + BF_NT - 1) / BF_NT, F.H, F.N);
-        k_bwd_full<<<grid, BF_NT, 0, st>>>(fp);
+        auto al16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+        const bool vec = (F.s == 4 || F.s == 8) && F.H % F.s == 0 && F.W % F.s == 0 && F.mode != GF_SUB_BILINEAR_AA &&
+                         al16(fp.g) && al16(fp.dI) && (!fp.dp || al16(fp.dp));
+        if (vec) {
+            dim3 grid((F.W / 4 + BF_NT - 1) / BF_NT, F.H, F.N);
+#define GF_BFV(ss, m) k_bwd_full_v<ss, m><<<grid, BF_NT, 0, st>>>(fp)
+            if (F.s == 4) {
+                if (F.mode == GF_SUB_BOX) GF_BFV(4, GF_SUB_BOX);
+                else if (F.mode == GF_SUB_NEAREST) GF_BFV(4, GF_SUB_NEAREST);
+                else GF_BFV(4, GF_SUB_BILINEAR);
+            } else {
+                if (F.mode == GF_SUB_BOX) GF_BFV(8, GF_SUB_BOX);
+                else if (F.mode == GF_SUB_NEAREST) GF_BFV(8, GF_SUB_NEAREST);
+                else GF_BFV(8, GF_SUB_BILINEAR);
+            }
+#undef GF_BFV
+        } else {
+            dim3 grid((F.W + BF_NT - 1) / BF_NT, F.H, F.N);
+            k_bwd_full<<<grid, BF_NT, 0, st>>>(fp);
+        }
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         if (F.p_lowres) {  // p was given at low resolution: dp = dp' (dense copy out of the strided workspace)
             if ((err = cudaMemcpy2DAsync(B.dp, (size_t)F.h * F.w * sizeof(float), B.dpl, F.lps * sizeof(float),

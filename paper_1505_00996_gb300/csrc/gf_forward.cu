@@ -564,6 +564,7 @@ __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile_x2(BoxParams P)
     const int span = BT_TW + 2 * r;
     float2 *Vt = reinterpret_cast<float2 *>(smf);           // [NP][span][BT_VP]
     float *Ot = smf + (size_t)2 * NP * span * BT_VP;         // [2][BT_TH][BT_OP]
+    float *St = Ot + 2 * BT_TH * BT_OP;                      // [4][BT_TH][BT_OP] window statistics (P.stats only)
     const int x0 = blockIdx.x * BT_TW, y0 = blockIdx.y * BT_TH;
     const int plane = blockIdx.z;
     const int n = plane / P.C, c = plane - n * P.C;
@@ -691,14 +692,13 @@ __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile_x2(BoxParams P)
                 const float cov = eIp - mI * mp;                   // cov_Ip
                 o0 = __fdividef(cov, var + P.eps);                 // a, Eq. (2)
                 o1 = (mp + shift.y) - o0 * (mI + shift.x);         // b, Eq. (3)
-                if (P.stats) {
-                    const size_t ps = (size_t)h * w;
-                    float *st = (float *)P.stats + (size_t)plane * 4 * ps + (size_t)y * w + x;
+                if (P.stats) {  // staged, written as coalesced rows in phase 3
                     const float cx = shift.x, cy = shift.y;
-                    st[0] = mI + cx;
-                    st[ps] = eII + cx * (2.0f * mI + cx);
-                    st[2 * ps] = mp + cy;
-                    st[3 * ps] = eIp + cx * mp + cy * mI + cx * cy;
+                    const int so = yr * BT_OP + xt;
+                    St[so] = mI + cx;
+                    St[BT_TH * BT_OP + so] = eII + cx * (2.0f * mI + cx);
+                    St[2 * BT_TH * BT_OP + so] = mp + cy;
+                    St[3 * BT_TH * BT_OP + so] = eIp + cx * mp + cy * mI + cx * cy;
                 }
             } else {
                 o0 = S[0].x * inv + shift.x;
@@ -718,6 +718,12 @@ __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile_x2(BoxParams P)
         if (y < h && x < w) {
             P.out0[obase + (size_t)y * w + x] = Ot[yr * BT_OP + xt];
             P.out1[obase + (size_t)y * w + x] = Ot[BT_TH * BT_OP + yr * BT_OP + xt];
+            if (KIND == KIND_STATS_F && P.stats) {
+                const size_t ps = (size_t)h * w;
+                float *st = (float *)P.stats + (size_t)plane * 4 * ps + (size_t)y * w + x;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) st[q * ps] = St[q * BT_TH * BT_OP + yr * BT_OP + xt];
+            }
         }
     }
 }
@@ -1144,7 +1150,9 @@ template <typename T, int KIND, int RV, int RH, int RC = 0>
 cudaError_t launch_box_x2(const BoxParams &bp, int planes, cudaStream_t st)
 {
     const int nq = (KIND == KIND_MEAN2) ? 2 : 4;
-    const size_t smem = box_tile_smem(nq, bp.r);
+    // plus the staging tile of the four window statistics when they are an output
+    const size_t smem = box_tile_smem(nq, bp.r) +
+                        ((KIND == KIND_STATS_F && bp.stats) ? (size_t)4 * BT_TH * BT_OP * sizeof(float) : 0);
     cudaError_t e = opt_in_smem(k_box_tile_x2<T, KIND, RV, RH, RC>, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((bp.w + BT_TW - 1) / BT_TW, (bp.h + BT_TH - 1) / BT_TH, planes);

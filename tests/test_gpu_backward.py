@@ -48,6 +48,11 @@ BWD_CASES = [
     (1, 3, 3, 96, 136, 2, 1e-2, 8, 1, False),
     (1, 1, 3, 97, 130, 3, 1e-2, 4, 2, False),
     (1, 1, 1, 1, 9, 1, 1e-2, 2, 1, False),
+    # vector forms of the full-res kernels (s = 4, 8; H, W multiples of s)
+    (1, 1, 2, 64, 96, 2, 1e-2, 4, 0, False),   # nearest
+    (2, 1, 3, 48, 64, 1, 1e-2, 8, 2, False),   # box, gray guide, full-res p
+    (1, 1, 2, 16, 24, 1, 1e-2, 8, 1, False),   # w = 3: both edge blocks and one inside
+    (1, 1, 1, 16, 8, 1, 1e-2, 8, 0, False),    # w = 1: one block at both edges (h = 2: var > 0)
 ]
 
 
