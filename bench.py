@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", choices=["headline", "training"], default="headline",
+                    help="training: only the trainable-layer forward + backward (batch 16 x 3 x 1024^2)")
     ap.add_argument("--no-graph", action="store_true", help="launch every step eagerly instead of graph replay")
     ap.add_argument("--no-extras", action="store_true", help="skip the s sweep, e2e, cpu baseline")
     ap.add_argument("--streams", type=int, default=2,
@@ -362,22 +364,7 @@ def run_native(args, world, rank, local):
             ratios[str(sr)] = {"ms_per_step": round(ms_r, 5), "mp_per_s": round(world * mp / (ms_r / 1e3), 1)}
         out["non_integer_ratio"] = ratios
 
-        # ---- trainable layer: batch 16 x 3 x 1024^2 guide, low-res p 16 x 3 x 256^2, s = 4 box, r' = 2, eps = 1e-2
-        Ib = torch.rand((16, 3, 1024, 1024), device=dev)
-        pb = torch.rand((16, 3, 256, 256), device=dev)
-        gq = torch.rand_like(Ib) * 2.0 - 1.0
-        qb = torch.empty_like(Ib)
-        fwd = lambda: gf.fast_guided_filter(Ib, pb, 0, 1e-2, 4, "box", r_low=2, p_lowres=True, out=qb, stream=stream,
-                                            ctx=ctx)
-        bwd = lambda: gf.fast_guided_filter_backward(Ib, pb, gq, 0, 1e-2, 4, "box", r_low=2, p_lowres=True,
-                                                     stream=stream, ctx=ctx)
-        k_tr = max(5, args.steps // 200)
-        ms_f = time_steps([(stream, fwd)], k_tr, 3, world, 1, False)
-        ms_b = time_steps([(stream, bwd)], k_tr, 3, world, 1, False)
-        out["training"] = {"workload": "trainable layer, batch 16 x 3 x 1024^2, s=4 box, r'=2, eps=1e-2, low-res p",
-                           "forward_ms": round(ms_f, 4), "backward_ms": round(ms_b, 4),
-                           "mp_per_s_fwd_bwd": round(world * 16 * 1.048576 / ((ms_f + ms_b) / 1e3), 1), "steps": k_tr}
-        del Ib, pb, gq, qb
+        out["training"] = run_training(dev, stream, ctx, world, max(5, args.steps // 200), 3)
         out["applications"] = run_applications(dev, stream, ctx, world, max(20, args.steps // 10), args.warmup,
                                                use_graph)
         out["small_images"] = run_small_images(dev, stream, ctx, world)
@@ -385,6 +372,45 @@ def run_native(args, world, rank, local):
             out["cpu_baseline"] = cpu_baseline(I_np, p_np)
         out["serving"] = run_serving(local)
     return out
+
+
+TRAIN_WORKLOAD = "trainable layer, batch 16 x 3 x 1024^2, s=4 box, r'=2, eps=1e-2, low-res p"
+
+
+def run_training(dev, stream, ctx, world, steps, warmup):
+    """Trainable-layer workload: batch 16 x 3 x 1024^2 guide (depthwise), low-res p 16 x 3 x 256^2, s = 4 box,
+    r' = 2, eps = 1e-2; forward and hand-written backward (dI, dp, d eps) timed apart."""
+    import paper_1505_00996_gb300 as gf
+    g = torch.Generator(device=dev).manual_seed(3)
+    Ib = torch.rand((16, 3, 1024, 1024), device=dev, generator=g)
+    pb = torch.rand((16, 3, 256, 256), device=dev, generator=g)
+    gq = torch.rand(Ib.shape, device=dev, generator=g) * 2.0 - 1.0
+    qb = torch.empty_like(Ib)
+    fwd = lambda: gf.fast_guided_filter(Ib, pb, 0, 1e-2, 4, "box", r_low=2, p_lowres=True, out=qb, stream=stream,
+                                        ctx=ctx)
+    bwd = lambda: gf.fast_guided_filter_backward(Ib, pb, gq, 0, 1e-2, 4, "box", r_low=2, p_lowres=True,
+                                                 stream=stream, ctx=ctx)
+    ms_f = time_steps([(stream, fwd)], steps, warmup, world, 1, False)
+    ms_b = time_steps([(stream, bwd)], steps, warmup, world, 1, False)
+    return {"workload": TRAIN_WORKLOAD, "forward_ms": round(ms_f, 4), "backward_ms": round(ms_b, 4),
+            "mp_per_s_fwd_bwd": round(world * 16 * 1.048576 / ((ms_f + ms_b) / 1e3), 1), "steps": steps}
+
+
+def run_training_only(args, world, local):
+    """--workload training: the trainable-layer forward + backward alone (one JSON line)."""
+    import paper_1505_00996_gb300 as gf
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream, ctx = torch.cuda.Stream(device=dev), gf.Context(local)
+    tr = run_training(dev, stream, ctx, world, args.steps, max(3, args.warmup))
+    mp = world * 16 * 1.048576
+    ms = tr["forward_ms"] + tr["backward_ms"]
+    return {"metric": "trainable layer forward + backward MP/s", "value": tr["mp_per_s_fwd_bwd"], "unit": "MP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": TRAIN_WORKLOAD, "global_batch": 16 * world,
+                       "l2": "inputs larger than L2 (201 MB per guide tensor); no flush"},
+            "training": tr, "mp_per_step": mp}
 
 
 # --------------------------------------------------------------------------------------------------------
@@ -588,6 +614,8 @@ def main():
     world, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
         out = run_reference(args, world, rank)
+    elif args.workload == "training":
+        out = run_training_only(args, world, local)
     else:
         out = run_native(args, world, rank, local)
     if rank == 0 and out is not None:

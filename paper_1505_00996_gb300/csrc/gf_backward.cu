@@ -515,11 +515,22 @@ __global__ void __launch_bounds__(BF_NT) k_bwd_full_v(FullParams P)
     const int X0 = 4 * (blockIdx.x * BF_NT + threadIdx.x), Y = blockIdx.y, n = blockIdx.z;
     if (X0 >= P.W) return;
     const size_t HW = (size_t)P.H * P.W, pix = (size_t)Y * P.W + X0;
-    int ya, yb, xa[4], xb[4];
-    float fy, fx[4];
+    int ya, yb;
+    float fy;
     up_taps(Y, S, P.h, ya, yb, fy);
+    // The 4 pixels' bilinear taps: pixel t of block i (t < s/2) lies between low-res columns i - 1 and i,
+    // pixel t >= s/2 between i and i + 1, at weight fx of the right one; at the image's first and last block
+    // the clamped column indices give the clamped taps (a lerp between equal values returns that value).
+    const int ib = X0 / S, t0 = X0 - ib * S;
+    const int cl = max(ib - 1, 0), cr = min(ib + 1, P.w - 1);
+    bool lo[4];
+    float fx[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) up_taps(X0 + k, S, P.w, xa[k], xb[k], fx[k]);
+    for (int k = 0; k < 4; ++k) {
+        const int t = t0 + k;
+        lo[k] = 2 * t + 1 < S;
+        fx[k] = (float)(2 * t + 1 - S + (lo[k] ? 2 * S : 0)) * (1.0f / (float)(2 * S));
+    }
     auto wsub = [](int t) -> float {
         if (MODE == GF_SUB_BOX) return 1.0f / (float)S;
         if (MODE == GF_SUB_NEAREST) return t == S / 2 ? 1.0f : 0.0f;
@@ -534,12 +545,15 @@ __global__ void __launch_bounds__(BF_NT) k_bwd_full_v(FullParams P)
     for (int c = 0; c < P.C; ++c) {
         const size_t lp = (size_t)(n * P.C + c) * P.lps;
         const float *ra = P.ma + lp + (size_t)ya * P.w, *rb = P.ma + lp + (size_t)yb * P.w;
+        // U(mean_a): the three columns lerped vertically first, then each pixel between its two columns
+        const float vl = fmaf(fy, __ldg(rb + cl) - __ldg(ra + cl), __ldg(ra + cl));
+        const float vc = fmaf(fy, __ldg(rb + ib) - __ldg(ra + ib), __ldg(ra + ib));
+        const float vr = fmaf(fy, __ldg(rb + cr) - __ldg(ra + cr), __ldg(ra + cr));
         float A[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {  // U(mean_a), as k_bwd_full forms it
-            const float A0 = fmaf(fx[k], __ldg(ra + xb[k]) - __ldg(ra + xa[k]), __ldg(ra + xa[k]));
-            const float A1 = fmaf(fx[k], __ldg(rb + xb[k]) - __ldg(rb + xa[k]), __ldg(rb + xa[k]));
-            A[k] = fmaf(fy, A1 - A0, A0);
+        for (int k = 0; k < 4; ++k) {
+            const float a0 = lo[k] ? vl : vc, a1 = lo[k] ? vc : vr;
+            A[k] = fmaf(fx[k], a1 - a0, a0);
         }
         const float4 gv = __ldg(reinterpret_cast<const float4 *>(P.g + (size_t)(n * P.C + c) * HW + pix));
         const float tI = wy != 0.0f ? wy * __ldg(P.dIl + lp + blk) : 0.0f;  // D^T(dI') before the x weight
