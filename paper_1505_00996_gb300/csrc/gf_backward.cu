@@ -20,7 +20,9 @@
 //
 //   k_bwd_upsample_T   dMA, dMB: per low-res tile, a horizontal gather of g.*I and g into a shared table of
 //                      full-res rows x low-res columns, then a vertical gather; k_bwd_upsample_T_v is its
-//                      block-vector form for s = 4, 8 (float4 loads, constant tap weights inside the image).
+//                      vector form for s = 4, 8 (each low-res column gathers its 2s pixels with vector
+//                      loads and compile-time weights; the image's edge columns and rows take the general
+//                      candidate loop).
 //   k_bwd_box_T        B^T of 2 maps with the chain epilogue (4 maps out, per-CTA partial sums of deps), or
 //                      B^T of 4 maps with the final combination into dI', dp'.  Same tiling as k_box_tile;
 //                      the epilogue runs in the write-out phase, a thread per pixel, so the forward planes it
@@ -126,20 +128,51 @@ __global__ void __launch_bounds__(UT_NT) k_bwd_upsample_T(UpTParams P)
     }
 }
 
-// Vector form of k_bwd_upsample_T for s = 4, 8 with W a multiple of s and 16-byte aligned planes.  The
-// horizontal gather runs per s-pixel block (float4 loads of g and I): under the bilinear upsample, pixel
-// t of block i (t < s/2) feeds low-res columns i - 1 and i, and pixel t >= s/2 feeds i and i + 1, with
-// weights that are compile-time constants away from the image's first and last block (there the clamped
-// taps are formed by up_taps).  Each block leaves its contributions to its left neighbour, itself and its
-// right neighbour in a shared table; column i of the tile then adds its own, its left block's right and its
-// right block's left contribution.  The vertical gather is k_bwd_upsample_T's.
+// Vector form of k_bwd_upsample_T for s = 4, 8 with H and W multiples of s and 16-byte aligned planes.
+// Under the bilinear upsample, pixel t of block i lies between low-res columns i - 1 and i at weight f_t of
+// column i when t < s/2 (f_t = (2t + 1 + s)/(2s)), and between i and i + 1 at weight f_t = (2t + 1 - s)/(2s)
+// of column i + 1 when t >= s/2.  So low-res column i gathers the second half of block i - 1 (weights f_t),
+// all of block i (f_t, then 1 - f_t) and the first half of block i + 1 (1 - f_t): 2s pixels with weights
+// known at compile time.  A thread forms that sum for one (full-res row, low-res column) from vector loads
+// of the three blocks (neighbouring threads share them through L1); low-res rows gather full-res rows with
+// the same pattern.  The image's first and last low-res column and row, whose taps are clamped, take the
+// general candidate loop of k_bwd_upsample_T.
+template <int S>
+__host__ __device__ constexpr float up_f(int t)
+{
+    return (float)(2 * t + 1 - S + (2 * t + 1 < S ? 2 * S : 0)) / (float)(2 * S);
+}
+// weight with which pixel t of block i + b (b = -1, 0, 1) reaches low-res index i (interior)
+template <int S>
+__host__ __device__ constexpr float up_wT(int b, int t)
+{
+    return b < 0 ? (2 * t + 1 > S ? up_f<S>(t) : 0.0f)
+                 : b == 0 ? (2 * t + 1 < S ? up_f<S>(t) : 1.0f - up_f<S>(t))
+                          : (2 * t + 1 < S ? 1.0f - up_f<S>(t) : 0.0f);
+}
+
+template <int N>
+__device__ __forceinline__ void ld_vec(const float *p, float (&v)[N])
+{
+    static_assert(N == 2 || N % 4 == 0, "float2 or float4 pieces");
+    if constexpr (N == 2) {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        v[0] = t.x; v[1] = t.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < N / 4; ++q) {
+            const float4 t = __ldg(reinterpret_cast<const float4 *>(p + 4 * q));
+            v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+        }
+    }
+}
+
 template <int S>
 __global__ void __launch_bounds__(UT_NT) k_bwd_upsample_T_v(UpTParams P)
 {
-    static_assert(S % 4 == 0, "blocks of whole float4 groups");
+    static_assert(S % 4 == 0, "half blocks of whole float2 / float4 pieces");
     extern __shared__ float sm[];
-    constexpr int NB = UT_TI + 2;            // blocks i0 - 1 .. i0 + UT_TI
-    constexpr int ncand = 3 * S;
+    constexpr int ncand = 3 * S, HS = S / 2;
     const int TJ = P.TJ;
     const int i0 = blockIdx.x * UT_TI, j0 = blockIdx.y * TJ;
     const int plane = blockIdx.z, n = plane / P.C, c = plane - n * P.C;
@@ -148,68 +181,60 @@ __global__ void __launch_bounds__(UT_NT) k_bwd_upsample_T_v(UpTParams P)
     const float *I = P.I + (size_t)(n * P.CI + (P.CI == 1 ? 0 : c)) * HW;
     const int Y0 = max(0, S * (j0 - 1)), Y1 = min(P.H, S * (j0 + TJ + 1));
     const int NR = Y1 - Y0;
-    float *Hs = sm;                          // [6][NR][NB]: g.*I to (left, own, right), then g to the same
-    float *Tga = Hs + (size_t)6 * NR * NB;   // [NR][UT_TI] horizontal gathers of g .* I
+    float *Tga = sm;                         // [NR][UT_TI] horizontal gathers of g .* I
     float *Tg = Tga + (size_t)NR * UT_TI;    // [NR][UT_TI] horizontal gathers of g
-    float *wy = Tg + (size_t)NR * UT_TI;     // [TJ][ncand] weights of Y = s(j-1) + t onto row j
+    float *wy = Tg + (size_t)NR * UT_TI;     // [TJ][ncand] weights of Y = s(j-1) + t onto row j (edge rows)
     for (int k = threadIdx.x; k < TJ * ncand; k += UT_NT) {
         const int jl = k / ncand, t = k - jl * ncand;
         const int j = j0 + jl, Y = S * (j - 1) + t;
         wy[k] = (j < P.h && Y >= 0 && Y < P.H) ? up_weight(Y, j, S, P.h) : 0.0f;
     }
-    const size_t hs = (size_t)NR * NB;
-    for (int k = threadIdx.x; k < NR * NB; k += UT_NT) {
-        const int yl = k / NB, bl = k - yl * NB;
-        const int i = i0 - 1 + bl;
-        float ga[3] = {0.0f, 0.0f, 0.0f}, gg[3] = {0.0f, 0.0f, 0.0f};  // to columns i - 1, i, i + 1
-        if (i >= 0 && i < P.w) {
-            const size_t ro = (size_t)(Y0 + yl) * P.W + (size_t)i * S;
-            const bool inner = i >= 1 && i <= P.w - 2;
+    // horizontal gather: T[y][i] = sum_X wx(X -> i) v(y, X)
+    for (int k = threadIdx.x; k < NR * UT_TI; k += UT_NT) {
+        const int yl = k / UT_TI, il = k - yl * UT_TI;
+        const int i = i0 + il;
+        float sa = 0.0f, sg = 0.0f;
+        if (i < P.w) {
+            const float *gr = g + (size_t)(Y0 + yl) * P.W, *Ir = I + (size_t)(Y0 + yl) * P.W;
+            if (i >= 1 && i <= P.w - 2) {
+                float gl[HS], Il[HS], gc[S], Ic[S], gn[HS], In[HS];
+                ld_vec<HS>(gr + (size_t)S * i - HS, gl);
+                ld_vec<HS>(Ir + (size_t)S * i - HS, Il);
+                ld_vec<S>(gr + (size_t)S * i, gc);
+                ld_vec<S>(Ir + (size_t)S * i, Ic);
+                ld_vec<HS>(gr + (size_t)S * (i + 1), gn);
+                ld_vec<HS>(Ir + (size_t)S * (i + 1), In);
 #pragma unroll
-            for (int v = 0; v < S / 4; ++v) {
-                const float4 g4 = __ldg(reinterpret_cast<const float4 *>(g + ro + 4 * v));
-                const float4 I4 = __ldg(reinterpret_cast<const float4 *>(I + ro + 4 * v));
-                const float gv[4] = {g4.x, g4.y, g4.z, g4.w}, Iv[4] = {I4.x, I4.y, I4.z, I4.w};
+                for (int t = 0; t < HS; ++t) {
+                    sa = fmaf(up_wT<S>(-1, HS + t), gl[t] * Il[t], sa);
+                    sg = fmaf(up_wT<S>(-1, HS + t), gl[t], sg);
+                }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int t = 4 * v + u;
-                    const float a = gv[u] * Iv[u];
-                    if (inner) {
-                        // source position (X + 1/2)/s - 1/2 = i + (2t + 1 - s)/(2s): taps i - 1, i or i, i + 1
-                        const bool lo = 2 * t + 1 < S;
-                        const float f = (float)(2 * t + 1 - S + (lo ? 2 * S : 0)) / (float)(2 * S);
-                        const int k0 = lo ? 0 : 1;
-                        ga[k0] = fmaf(1.0f - f, a, ga[k0]);
-                        ga[k0 + 1] = fmaf(f, a, ga[k0 + 1]);
-                        gg[k0] = fmaf(1.0f - f, gv[u], gg[k0]);
-                        gg[k0 + 1] = fmaf(f, gv[u], gg[k0 + 1]);
-                    } else {
-                        int xa, xb;
-                        float f;
-                        up_taps(i * S + t, S, P.w, xa, xb, f);
+                for (int t = 0; t < S; ++t) {
+                    sa = fmaf(up_wT<S>(0, t), gc[t] * Ic[t], sa);
+                    sg = fmaf(up_wT<S>(0, t), gc[t], sg);
+                }
 #pragma unroll
-                        for (int d = 0; d < 3; ++d) {
-                            const float wgt = (xa == i - 1 + d ? 1.0f - f : 0.0f) + (xb == i - 1 + d ? f : 0.0f);
-                            ga[d] = fmaf(wgt, a, ga[d]);
-                            gg[d] = fmaf(wgt, gv[u], gg[d]);
-                        }
+                for (int t = 0; t < HS; ++t) {
+                    sa = fmaf(up_wT<S>(1, t), gn[t] * In[t], sa);
+                    sg = fmaf(up_wT<S>(1, t), gn[t], sg);
+                }
+            } else {
+                const int xb = S * (i - 1);
+                for (int t = 0; t < ncand; ++t) {
+                    const int X = xb + t;
+                    if (X < 0 || X >= P.W) continue;
+                    const float wgt = up_weight(X, i, S, P.w);
+                    if (wgt != 0.0f) {
+                        const float gv = __ldg(gr + X);
+                        sg = fmaf(wgt, gv, sg);
+                        sa = fmaf(wgt, gv * __ldg(Ir + X), sa);
                     }
                 }
             }
         }
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            Hs[d * hs + k] = ga[d];
-            Hs[(3 + d) * hs + k] = gg[d];
-        }
-    }
-    __syncthreads();
-    // column il of the tile (block bl = il + 1): own + left block's right + right block's left
-    for (int k = threadIdx.x; k < NR * UT_TI; k += UT_NT) {
-        const int yl = k / UT_TI, il = k - yl * UT_TI;
-        const size_t b = (size_t)yl * NB + il;
-        Tga[k] = Hs[1 * hs + b + 1] + Hs[2 * hs + b] + Hs[0 * hs + b + 2];
-        Tg[k] = Hs[4 * hs + b + 1] + Hs[5 * hs + b] + Hs[3 * hs + b + 2];
+        Tga[k] = sa;
+        Tg[k] = sg;
     }
     __syncthreads();
     // vertical gather: dM[j][i] = sum_y wy(y -> j) T[y][i]
@@ -218,14 +243,25 @@ __global__ void __launch_bounds__(UT_NT) k_bwd_upsample_T_v(UpTParams P)
         const int j = j0 + jl, i = i0 + il;
         if (j >= P.h || i >= P.w) continue;
         float sa = 0.0f, sb = 0.0f;
-        const int yb = S * (j - 1);
-#pragma unroll 4
-        for (int t = 0; t < ncand; ++t) {
-            const float wgt = wy[jl * ncand + t];
-            if (wgt != 0.0f) {
-                const int yl = yb + t - Y0;
+        if (j >= 1 && j <= P.h - 2) {
+            const int yl0 = S * (j - 1) + HS - Y0;  // first row: the second half of block j - 1
+#pragma unroll
+            for (int t = 0; t < 2 * S; ++t) {
+                // rows S(j-1) + HS + t: block j - 1 (t < HS), block j (HS <= t < S + HS), block j + 1
+                const float wgt = t < HS ? up_wT<S>(-1, HS + t) : (t < S + HS ? up_wT<S>(0, t - HS) : up_wT<S>(1, t - S - HS));
+                const int yl = yl0 + t;
                 sa = fmaf(wgt, Tga[yl * UT_TI + il], sa);
                 sb = fmaf(wgt, Tg[yl * UT_TI + il], sb);
+            }
+        } else {
+            const int yb = S * (j - 1);
+            for (int t = 0; t < ncand; ++t) {
+                const float wgt = wy[jl * ncand + t];
+                if (wgt != 0.0f) {
+                    const int yl = yb + t - Y0;
+                    sa = fmaf(wgt, Tga[yl * UT_TI + il], sa);
+                    sb = fmaf(wgt, Tg[yl * UT_TI + il], sb);
+                }
             }
         }
         const size_t o = (size_t)plane * P.lps + (size_t)j * P.w + i;
@@ -629,17 +665,16 @@ cudaError_t launch_backward(const BwdPlan &B, cudaStream_t st)
     if ((err = launch_forward(F, st)) != cudaSuccess) return err;
 
     // ---- dMA = U^T(g .* I), dMB = U^T(g)
-    const bool up_vec = (F.s == 4 || F.s == 8) && F.W % F.s == 0 &&
+    const bool up_vec = (F.s == 4 || F.s == 8) && F.W % F.s == 0 && F.H % F.s == 0 &&
                         ((reinterpret_cast<uintptr_t>(B.dq) | reinterpret_cast<uintptr_t>(F.I)) & 15u) == 0;
     if (up_vec) {
         UpTParams up;
         up.g = B.dq; up.I = (const float *)F.I; up.dma = B.dma; up.dmb = B.dmb;
         up.C = F.C; up.CI = F.CI; up.H = F.H; up.W = F.W; up.h = F.h; up.w = F.w; up.s = F.s;
-        up.TJ = F.s == 4 ? 8 : 4;
+        up.TJ = 8;
         up.lps = F.lps;
         const int NRmax = F.s * (up.TJ + 2);
-        const size_t smem = ((size_t)6 * NRmax * (UT_TI + 2) + (size_t)2 * NRmax * UT_TI + (size_t)up.TJ * 3 * F.s) *
-                            sizeof(float);
+        const size_t smem = ((size_t)2 * NRmax * UT_TI + (size_t)up.TJ * 3 * F.s) * sizeof(float);
         dim3 grid((F.w + UT_TI - 1) / UT_TI, (F.h + up.TJ - 1) / up.TJ, planes);
         if (F.s == 4) {
             if ((err = opt_in_smem(k_bwd_upsample_T_v<4>, smem)) != cudaSuccess) return err;
