@@ -44,8 +44,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=["headline", "training"], default="headline",
-                    help="training: only the trainable-layer forward + backward (batch 16 x 3 x 1024^2)")
+    ap.add_argument("--workload", choices=["headline", "training", "applications"], default="headline",
+                    help="training: only the trainable-layer forward + backward (batch 16 x 3 x 1024^2); "
+                         "applications: only the paper's four applications at 12 MP (gray, depthwise and colour "
+                         "guides)")
     ap.add_argument("--no-graph", action="store_true", help="launch every step eagerly instead of graph replay")
     ap.add_argument("--no-extras", action="store_true", help="skip the s sweep, e2e, cpu baseline")
     ap.add_argument("--streams", type=int, default=2,
@@ -450,6 +452,24 @@ def run_applications(dev, stream, ctx, world, steps, warmup, use_graph):
     return res
 
 
+def run_applications_only(args, world, local):
+    """--workload applications: the applications of the paper's figures alone (one JSON line; value = the
+    colour-guided smoothing's MP/s, the slowest of them)."""
+    import paper_1505_00996_gb300 as gf
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream, ctx = torch.cuda.Stream(device=dev), gf.Context(local)
+    res = run_applications(dev, stream, ctx, world, args.steps, max(3, args.warmup), not args.no_graph)
+    v = res["smoothing_color_guide"]
+    return {"metric": "colour-guided smoothing output MP/s (12 MP, s = 4, r = 4)", "value": v["mp_per_s"],
+            "unit": "MP/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": v["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "applications of the paper's figures, 12 MP 4000x3000, s=4 bilinear",
+                       "l2": "inputs larger than L2; no flush", "cuda_graph": not args.no_graph},
+            "applications": res}
+
+
 # --------------------------------------------------------------------------------------------------------
 # small images: the four-kernel chain against the single fused kernel
 # --------------------------------------------------------------------------------------------------------
@@ -616,6 +636,8 @@ def main():
         out = run_reference(args, world, rank)
     elif args.workload == "training":
         out = run_training_only(args, world, local)
+    elif args.workload == "applications":
+        out = run_applications_only(args, world, local)
     else:
         out = run_native(args, world, rank, local)
     if rank == 0 and out is not None:
