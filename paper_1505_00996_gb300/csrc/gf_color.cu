@@ -18,7 +18,8 @@
 //                     (a_g, b) of every channel.
 //   box means         of the 4C coefficient planes.
 //   k_color_output    per full-res pixel and channel: the four means interpolated bilinearly (gf.h
-//                     conventions) and q = mean_a^T I + mean_b, plus the optional detail epilogue.
+//                     conventions) and q = mean_a^T I + mean_b, plus the optional detail epilogue;
+//                     k_color_output_s4x is its run form for s = 4, 8 on aligned rows (compile-time weights).
 #include <algorithm>
 
 #include "gf_device.cuh"
@@ -299,6 +300,131 @@ __global__ void __launch_bounds__(CO_NT) k_color_output(const TI *__restrict__ I
     cp_async_wait_all();
 }
 
+// Run form of k_color_output for s = 4, 8 on aligned rows (the guide read as whole vectors).  Run j covers
+// full-res rows s j + s/2 .. s j + s/2 + s - 1, which all sample low-res rows j and j + 1 with vertical weight
+// (2k + 1)/(2s) on row j + 1 for row k of the run; across a row the thread's 4 pixels sample fixed low-res
+// columns with fixed weights (s = 4: 5/8, 7/8 of column i for pixels 0, 1; 1/8, 3/8 of column i + 1 for
+// pixels 2, 3).  So the four means are interpolated horizontally once per run per tap row, and each output
+// value costs one FMA per mean and three for q.  The tap tile is filled with clamped indices, so the image's
+// edges give the clamped taps (an interpolation between equal values returns that value).  The CTA covers
+// 8 runs of one channel of a 512-pixel band; the guide's three planes reach each thread through its own
+// cp.async ring slots as in k_color_output.
+template <typename TI, typename TQ, int S>
+__global__ void __launch_bounds__(CO_NT) k_color_output_s4x(const TI *__restrict__ I, TQ *__restrict__ q,
+                                                            const float *__restrict__ MX, const float *__restrict__ MY,
+                                                            int C, int H, int W, int h, int w, size_t fps, size_t lps,
+                                                            int LR, int LC, int Yw0, int Yw1, float detail)
+{
+    static_assert(S % 4 == 0, "whole 4-row groups per run");
+    extern __shared__ float tap[];  // [4 maps][LR][LC]: means at low-res rows jb - 1 .. jb + NB, clamped
+    constexpr int NB = 8;           // runs (low-res rows) per CTA
+    const int c = blockIdx.x % C, band = blockIdx.x / C, n = blockIdx.z;
+    const int jb = blockIdx.y * NB;
+    const int Xb = band * CO_BAND;
+    const int Yb = max(jb * S, Yw0), Ye = min(min(jb * S + NB * S, H), Yw1);  // rows written by this CTA
+    if (Yb >= Ye) return;
+    const int ly0 = jb - 1, lx0 = Xb / S - 1;
+    const int tile = LR * LC;
+    const float *mx = MX + ((size_t)n * 2 * C + 2 * c) * lps, *my = MY + ((size_t)n * 2 * C + 2 * c) * lps;
+    for (int k = threadIdx.x; k < 4 * tile; k += CO_NT) {  // maps: mean of a_r (mx), a_g (my), a_b, b
+        const int m = k / tile, rem = k - m * tile, row = rem / LC, col = rem - row * LC;
+        const int gy = min(max(ly0 + row, 0), h - 1), gx = min(max(lx0 + col, 0), w - 1);
+        cp_async4(tap + k, ((m & 1) ? my : mx) + (m >> 1) * lps + (size_t)gy * w + gx);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    const int X0 = Xb + threadIdx.x * 4;
+    if (X0 >= W) return;
+    const int ti = X0 / S - lx0;  // tile column of the low-res column that holds pixel X0 (>= 1)
+    const int g = (S == 8) ? ((X0 >> 2) & 1) : 0;
+    // horizontally interpolated tap row `tr` of the four means for the thread's 4 pixels
+    auto hrow = [&](int tr, float (&o)[4][4]) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const float *row = tap + m * tile + tr * LC;
+            if (S == 4) {
+                const float a = row[ti - 1], b = row[ti], cc = row[ti + 1];
+                o[m][0] = fmaf(0.625f, b - a, a);
+                o[m][1] = fmaf(0.875f, b - a, a);
+                o[m][2] = fmaf(0.125f, cc - b, b);
+                o[m][3] = fmaf(0.375f, cc - b, b);
+            } else {
+                const int lo = g ? ti : ti - 1;
+                const float a = row[lo], b = row[lo + 1];
+                const float f0 = g ? 0.0625f : 0.5625f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) o[m][k] = fmaf(f0 + 0.125f * k, b - a, a);
+            }
+        }
+    };
+    const TI *Ig = I + (size_t)n * 3 * fps + X0;
+    TQ *qc = q + ((size_t)n * C + c) * fps + X0;
+    constexpr int VB = 4 * (int)sizeof(TI);
+    unsigned char *ring = reinterpret_cast<unsigned char *>(tap + 4 * tile);  // [CO_NST][3][CO_NT][VB]
+    auto slot = [&](int stage, int k) { return ring + ((size_t)(stage * 3 + k) * CO_NT + threadIdx.x) * VB; };
+    const int Ys = S * (jb - 1) + S / 2;  // first row of the first run
+    constexpr int NROWS = (NB + 1) * S;   // rows of the NB + 1 runs
+    auto issue = [&](int u) {  // row Ys + u of the walk
+        const int Y = Ys + u;
+        if (u < NROWS && Y >= Yb && Y < Ye) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const TI *src = Ig + k * fps + (size_t)Y * W;
+                if constexpr (VB == 16) cp_async16(slot(u % CO_NST, k), src);
+                else ld_async_small<TI>(slot(u % CO_NST, k), src);
+            }
+        }
+        cp_async_commit();  // one group per row, empty when nothing was copied, so the count stays uniform
+    };
+#pragma unroll
+    for (int u = 0; u < CO_NST - 1; ++u) issue(u);
+    float lo[4][4], d[4][4];
+    hrow(0, lo);  // low-res row jb - 1
+    for (int t = 0; t <= NB; ++t) {
+        // run t samples tile rows t, t + 1: the previous run's lower row becomes the upper one
+        if (t > 0) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int x = 0; x < 4; ++x) lo[m][x] += d[m][x];
+        }
+        hrow(t + 1, d);
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+#pragma unroll
+            for (int x = 0; x < 4; ++x) d[m][x] -= lo[m][x];
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            const int u = t * S + k, Y = Ys + u;
+            issue(u + CO_NST - 1);
+            cp_async_wait_group<CO_NST - 1>();  // this thread's copies of row u have landed
+            if (Y < Yb || Y >= Ye) continue;
+            float gv[3][4];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) ld4_ring<TI>(slot(k % CO_NST, p), gv[p]);  // u % CO_NST == k % CO_NST
+            const float fy = (float)(2 * k + 1) * (1.0f / (float)(2 * S));
+            float out[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                float mm[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) mm[m] = fmaf(fy, d[m][x], lo[m][x]);
+                out[x] = fmaf(mm[0], gv[0][x], fmaf(mm[1], gv[1][x], fmaf(mm[2], gv[2][x], mm[3])));
+            }
+            if (detail != 0.0f) {  // C == 3: channel c's own guide channel is its detail source
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const float iv = (c == 0) ? gv[0][x] : (c == 1 ? gv[1][x] : gv[2][x]);
+                    out[x] = fmaf(detail, iv - out[x], out[x]);
+                }
+            }
+            st4g<TQ>(qc + (size_t)Y * W, true, 4, out);
+        }
+    }
+    cp_async_wait_all();
+}
+
 int blocks_for(size_t items) { return (int)std::min<size_t>((items + COL_NT - 1) / COL_NT, 152 * 8); }
 
 }  // namespace
@@ -330,6 +456,28 @@ cudaError_t launch_color_output(const FwdPlan &P, cudaStream_t st)
     const size_t vb = 4 * dtype_size(P.dt_in);
     const bool vec_io = (P.W % 4 == 0) && (P.fps % 4 == 0) && ((uintptr_t)P.I % vb == 0) && ((uintptr_t)P.q % 16 == 0);
     cudaError_t e;
+    if (vec_io && (P.s == 4 || P.s == 8)) {  // the run form
+        constexpr int NB = 8;
+        const int LRr = NB + 2, LCr = CO_BAND / P.s + 2;
+        const size_t smem_r = (size_t)4 * LRr * LCr * sizeof(float) + (size_t)CO_NST * 3 * CO_NT * 4 * dtype_size(P.dt_in);
+        dim3 grid_r(bands * P.C, (P.h + NB - 1) / NB, P.N);
+#define GF_COR(TI, TQ, SS)                                                                                        \
+    do {                                                                                                          \
+        if ((e = opt_in_smem(k_color_output_s4x<TI, TQ, SS>, smem_r)) != cudaSuccess) return e;                  \
+        k_color_output_s4x<TI, TQ, SS><<<grid_r, CO_NT, smem_r, st>>>((const TI *)P.I, (TQ *)P.q, P.col[6], P.col[7], \
+                                                                     P.C, P.H, P.W, P.h, P.w, P.fps, P.lps, LRr, LCr,  \
+                                                                     P.Yw0, P.Yw1, P.detail);                        \
+    } while (0)
+#define GF_COS(TI, TQ) do { if (P.s == 4) GF_COR(TI, TQ, 4); else GF_COR(TI, TQ, 8); } while (0)
+        if (P.dt_in == F32) {
+            if (P.dt_out == F32) GF_COS(float, float); else GF_COS(float, __half);
+        } else {
+            if (P.dt_out == F32) GF_COS(__half, float); else GF_COS(__half, __half);
+        }
+#undef GF_COS
+#undef GF_COR
+        return cudaGetLastError();
+    }
 #define GF_CO(TI, TQ)                                                                                            \
     do {                                                                                                         \
         if ((e = opt_in_smem(k_color_output<TI, TQ>, smem)) != cudaSuccess) return e;                          \
