@@ -334,8 +334,13 @@ def run_native(args, world, rank, local):
         for _ in range(k_e2e):
             gf.fast_guided_filter_host(I_h, p_h, R, EPS, S, MODE, out=q_h, stream=stream, ctx=ctx)
         dt = max_over_ranks((time.perf_counter() - t0) / k_e2e, world)
+        # the library uploads only the rows of p that a nearest / bilinear subsample at s >= 3 reads: 2 of every
+        # s rows (gf.h, gf_filter_host)
+        p_moved = p_h.numel() * 4 * (2 / S if MODE in ("nearest", "bilinear") and S >= 3 else 1)
         out["e2e"] = {"value": round(world * mp / dt, 1), "unit": "MP/s",
                       "h2d_bytes_per_step": (I_h.numel() + p_h.numel()) * 4, "d2h_bytes_per_step": q_h.numel() * 4,
+                      "h2d_bytes_transferred_per_step": int(I_h.numel() * 4 + p_moved),
+                      "strips": len(gf.host_strips(H, W, C, S, MODE) or [0, H]) - 1,
                       "steps": k_e2e, "api": "gf_filter_host"}
         # ---- storage precision: the same 12 MP s = 4 workload stored as FP16, and as uint8
         prec = {"f32": {"ms_per_step": round(ms_serial, 5), "mp_per_s": round(world * mp / (ms_serial / 1e3), 1)}}

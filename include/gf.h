@@ -215,9 +215,9 @@ gf_status gf_filter_host(gf_ctx *ctx, const void *I_host, const void *p_host, vo
 
 /* The strips gf_filter_host pipelines a call with these arguments in (host-only): returns K >= 2 and, if
  * row_starts is not NULL, writes its K + 1 boundaries 0 = Y_0 < Y_1 < ... < Y_K = H (multiples of 8 s;
- * up to 16 strips, at least 32 s rows each); returns 1 when the call is not pipelined (under 8 MiB of
+ * up to 8 strips, at least 64 s rows each); returns 1 when the call is not pipelined (under 8 MiB of
  * host data, a low-res p, a colour guide, a non-integer ratio, the single fused kernel, low-res outputs,
- * its own row range or kernel events), -1 for invalid arguments.  row_starts holds at least 17 ints. */
+ * its own row range or kernel events), -1 for invalid arguments.  row_starts holds at least 9 ints. */
 int gf_host_strips(int H, int W, int C, int s, gf_subsample_mode mode, const gf_opts *opts, int *row_starts);
 
 /*

@@ -217,7 +217,7 @@ def host_strips(H, W, C, s, mode="bilinear", *, batch=1, guide_channels=1, dtype
     o.dtype_in = _DTYPES[dtype]
     o.dtype_out = _DTYPES[out_dtype or (torch.float16 if dtype == torch.float16 else torch.float32)]
     m = MODES[mode] if isinstance(mode, str) else int(mode)
-    ys = (ctypes.c_int * 17)()
+    ys = (ctypes.c_int * 9)()  # gf_host_strips writes at most 9 boundaries
     k = load_library().gf_host_strips(int(H), int(W), int(C), int(s), m, ctypes.byref(o), ys)
     if k < 0:
         check(GF_EINVAL)

@@ -118,20 +118,20 @@ def test_kernel_count(lib):
 
 def test_host_strips(lib):
     """The strips gf_filter_host pipelines a large host call in: contiguous, cover every row, inner
-    boundaries on multiples of 8 s, at most 16; small or unsupported forms are not pipelined."""
+    boundaries on multiples of 8 s, at most 8; small or unsupported forms are not pipelined."""
     import torch
     from fractions import Fraction
 
     from paper_1505_00996_gb300 import binding
     ys = binding.host_strips(3000, 4000, 3, 4)
-    assert ys[0] == 0 and ys[-1] == 3000 and 2 <= len(ys) - 1 <= 16
+    assert ys[0] == 0 and ys[-1] == 3000 and 2 <= len(ys) - 1 <= 8
     assert all(a < b for a, b in zip(ys, ys[1:]))
     assert all(y % 32 == 0 for y in ys[:-1])
-    assert all(b - a >= 32 * 4 or b == 3000 for a, b in zip(ys, ys[1:]))
+    assert all(b - a >= 64 * 4 or b == 3000 for a, b in zip(ys, ys[1:]))
     ys8 = binding.host_strips(3000, 4000, 3, 8, batch=2, guide_channels=3, dtype=torch.float16)
     assert ys8[0] == 0 and ys8[-1] == 3000 and all(y % 64 == 0 for y in ys8[:-1])
     assert binding.host_strips(512, 512, 1, 4) is None          # 3 MB of host data: one piece
     assert binding.host_strips(3000, 4000, 3, Fraction(5, 2)) is None
-    assert binding.host_strips(200, 40000, 3, 4) is None        # fewer than 2 x 32 s rows
+    assert binding.host_strips(500, 40000, 3, 4) is None        # fewer than 2 x 64 s rows
     with pytest.raises(binding.GFError):
         binding.host_strips(0, 4000, 3, 4)
