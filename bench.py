@@ -44,10 +44,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=["headline", "training", "applications"], default="headline",
+    ap.add_argument("--workload", choices=["headline", "training", "applications", "precision"], default="headline",
                     help="training: only the trainable-layer forward + backward (batch 16 x 3 x 1024^2); "
                          "applications: only the paper's four applications at 12 MP (gray, depthwise and colour "
-                         "guides)")
+                         "guides); precision: only the 12 MP workload stored as FP32, FP16 and uint8")
     ap.add_argument("--no-graph", action="store_true", help="launch every step eagerly instead of graph replay")
     ap.add_argument("--no-extras", action="store_true", help="skip the s sweep, e2e, cpu baseline")
     ap.add_argument("--streams", type=int, default=2,
@@ -342,20 +342,9 @@ def run_native(args, world, rank, local):
                       "h2d_bytes_transferred_per_step": int(I_h.numel() * 4 + p_moved),
                       "strips": len(gf.host_strips(H, W, C, S, MODE) or [0, H]) - 1,
                       "steps": k_e2e, "api": "gf_filter_host"}
-        # ---- storage precision: the same 12 MP s = 4 workload stored as FP16, and as uint8
-        prec = {"f32": {"ms_per_step": round(ms_serial, 5), "mp_per_s": round(world * mp / (ms_serial / 1e3), 1)}}
-        for name, dt in (("f16", torch.float16), ("u8", torch.uint8)):
-            if dt == torch.uint8:
-                Iv = (lanes[0]["I"] * 255.0).round().clamp(0, 255).to(torch.uint8)
-                pv = (lanes[0]["p"] * 255.0).round().clamp(0, 255).to(torch.uint8)
-            else:
-                Iv, pv = lanes[0]["I"].to(dt), lanes[0]["p"].to(dt)
-            qv = torch.empty((1, C, H, W), dtype=torch.float16 if dt == torch.float16 else torch.float32, device=dev)
-            call = (lambda Iv=Iv, pv=pv, qv=qv: gf.fast_guided_filter(Iv, pv, R, EPS, S, MODE, out=qv, stream=stream,
-                                                                       ctx=ctx))
-            ms_v = time_steps([(stream, call)], max(20, args.steps // 10), args.warmup, world, 10, use_graph)
-            prec[name] = {"ms_per_step": round(ms_v, 5), "mp_per_s": round(world * mp / (ms_v / 1e3), 1)}
-        out["precision"] = prec
+        # ---- storage precision: the same 12 MP s = 4 workload stored as FP32, FP16 and uint8 (one stream)
+        out["precision"] = run_precision(dev, stream, ctx, world, lanes[0]["I"], lanes[0]["p"],
+                                         max(20, args.steps // 10), args.warmup, use_graph)
         # ---- subsample modes on the same workload (bilinear is the headline)
         modes = {}
         for mname in ("nearest", "box", "bilinear_aa"):
@@ -455,6 +444,44 @@ def run_applications(dev, stream, ctx, world, steps, warmup, use_graph):
                      "eps": eps, "detail_gain": gain, "ms_per_step": round(ms_a, 5),
                      "mp_per_s": round(world * Hh * Ww / 1e6 / (ms_a / 1e3), 1)}
     return res
+
+
+def run_precision(dev, stream, ctx, world, I, p, steps, warmup, use_graph):
+    """The 12 MP workload with I and p stored as FP32, FP16 (q FP16) and uint8 (round(255 x), q FP32), one
+    stream each."""
+    import paper_1505_00996_gb300 as gf
+    mp = H * W / 1e6
+    res = {}
+    for name, dt in (("f32", torch.float32), ("f16", torch.float16), ("u8", torch.uint8)):
+        if dt == torch.uint8:
+            Iv = (I * 255.0).round().clamp(0, 255).to(torch.uint8)
+            pv = (p * 255.0).round().clamp(0, 255).to(torch.uint8)
+        else:
+            Iv, pv = I.to(dt), p.to(dt)
+        qv = torch.empty((1, C, H, W), dtype=torch.float16 if dt == torch.float16 else torch.float32, device=dev)
+        call = (lambda Iv=Iv, pv=pv, qv=qv: gf.fast_guided_filter(Iv, pv, R, EPS, S, MODE, out=qv, stream=stream,
+                                                                   ctx=ctx))
+        ms_v = time_steps([(stream, call)], steps, warmup, world, 10, use_graph)
+        res[name] = {"ms_per_step": round(ms_v, 5), "mp_per_s": round(world * mp / (ms_v / 1e3), 1)}
+    return res
+
+
+def run_precision_only(args, world, local):
+    """--workload precision: the 12 MP workload in the three storage precisions alone (one JSON line; value =
+    the uint8 storage's MP/s)."""
+    import paper_1505_00996_gb300 as gf
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream, ctx = torch.cuda.Stream(device=dev), gf.Context(local)
+    I_np, p_np = make_inputs(0)
+    I, p = torch.from_numpy(I_np).to(dev), torch.from_numpy(p_np).to(dev)
+    res = run_precision(dev, stream, ctx, world, I, p, args.steps, max(3, args.warmup), not args.no_graph)
+    return {"metric": "output MP/s at 12MP r=16 s=4, uint8 storage", "value": res["u8"]["mp_per_s"], "unit": "MP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": res["u8"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD + ", stored as FP32, FP16 and uint8", "cuda_graph": not args.no_graph,
+                       "l2": "inputs larger than L2; no flush"},
+            "precision": res}
 
 
 def run_applications_only(args, world, local):
@@ -643,6 +670,8 @@ def main():
         out = run_training_only(args, world, local)
     elif args.workload == "applications":
         out = run_applications_only(args, world, local)
+    elif args.workload == "precision":
+        out = run_precision_only(args, world, local)
     else:
         out = run_native(args, world, rank, local)
     if rank == 0 and out is not None:

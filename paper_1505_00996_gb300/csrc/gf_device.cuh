@@ -176,6 +176,10 @@ __device__ __forceinline__ void detail_epilogue(float k, const float iv[4], floa
     }
 }
 
+// A uint8 sample as a value on [0, 1]: b / 255, formed as the exact float of b times the rounded reciprocal
+// of 255 -- within one unit in the last place of the quotient, without a division per pixel.
+__device__ __forceinline__ float u8_unit(uint32_t b) { return (float)b * (1.0f / 255.0f); }
+
 // 4 pixels of I from the thread's shared ring slot, as floats.
 template <typename T>
 __device__ __forceinline__ void ld4_shared(const void *p, float v[4]);
@@ -198,7 +202,7 @@ __device__ __forceinline__ void ld4_shared<uint8_t>(const void *p, float v[4])
 {
     const uint32_t t = *reinterpret_cast<const uint32_t *>(p);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = (float)((t >> (8 * k)) & 0xffu) / 255.0f;
+    for (int k = 0; k < 4; ++k) v[k] = u8_unit((t >> (8 * k)) & 0xffu);
 }
 template <typename T>
 __device__ __forceinline__ void st4(T *p, bool vec, int valid, const float v[4]);

@@ -780,10 +780,10 @@ __device__ __forceinline__ void ld4<uint8_t>(const uint8_t *p, bool vec, int val
     if (vec) {
         const uint32_t t = __ldcs(reinterpret_cast<const unsigned int *>(p));
 #pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = (float)((t >> (8 * k)) & 0xffu) / 255.0f;
+        for (int k = 0; k < 4; ++k) v[k] = u8_unit((t >> (8 * k)) & 0xffu);
     } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = (k < valid) ? (float)p[k] / 255.0f : 0.0f;
+        for (int k = 0; k < 4; ++k) v[k] = (k < valid) ? u8_unit(p[k]) : 0.0f;
     }
 }
 
