@@ -556,6 +556,11 @@ template <typename T, int KIND, int BT_RV, int BT_RH, int RC = 0>
 __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile_x2(BoxParams P)
 {
     constexpr int NP = (KIND == KIND_MEAN2) ? 1 : 2;  // float2 pairs
+    // uint8 input (KIND 1): the samples are integers J, P <= 1020 and J^2, J P <= 1020^2 < 2^24, so the
+    // unshifted FP32 column sums of at most 2 r' + 2 <= 10 rows are exact; they are staged as uint32 and the
+    // horizontal sums and the variance and covariance numerators are exact integers (r' <= 4 only).
+    constexpr bool INT = (KIND == KIND_STATS_INT);
+    static_assert(!INT || (RC > 0 && RC <= 4), "the integer form needs a compile-time r' <= 4");
     extern __shared__ float smf[];
     const int BT_NT = blockDim.x;
     const int tid = threadIdx.x;
@@ -570,7 +575,9 @@ __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile_x2(BoxParams P)
     const int n = plane / P.C, c = plane - n * P.C;
     const T *Xp = (const T *)P.X + (size_t)(n * P.CX + (P.CX == 1 ? 0 : c)) * P.xps;
     const T *Yp = (const T *)P.Y + (size_t)plane * P.yps;
-    const float2 shift = make_float2(ldv(Xp + (size_t)y0 * w + x0), ldv(Yp + (size_t)y0 * w + x0));
+    const float2 shift = INT ? make_float2(0.0f, 0.0f)
+                             : make_float2(ldv(Xp + (size_t)y0 * w + x0), ldv(Yp + (size_t)y0 * w + x0));
+    uint2 *Vu = reinterpret_cast<uint2 *>(smf);  // INT: the same tile as uint32 pairs
 
     // ---- phase 1: vertical window sums
     constexpr int NSEG_V = BT_TH / BT_RV;
@@ -612,13 +619,21 @@ __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile_x2(BoxParams P)
                         acc(i - 1, true);
                     }
 #pragma unroll
-                    for (int k = 0; k < NP; ++k) Vt[((size_t)k * span + xc) * BT_VP + vrow + i] = S[k];
+                    for (int k = 0; k < NP; ++k) {
+                        const size_t vi = ((size_t)k * span + xc) * BT_VP + vrow + i;
+                        if (INT) Vu[vi] = make_uint2(__float2uint_rn(S[k].x), __float2uint_rn(S[k].y));
+                        else Vt[vi] = S[k];
+                    }
                 }
             } else {
 #pragma unroll
                 for (int i = 0; i < BT_RV; ++i)
 #pragma unroll
-                    for (int k = 0; k < NP; ++k) Vt[((size_t)k * span + xc) * BT_VP + vrow + i] = S[k];
+                    for (int k = 0; k < NP; ++k) {
+                        const size_t vi = ((size_t)k * span + xc) * BT_VP + vrow + i;
+                        if (INT) Vu[vi] = make_uint2(0u, 0u);
+                        else Vt[vi] = S[k];
+                    }
             }
             continue;
         }
@@ -664,13 +679,22 @@ __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile_x2(BoxParams P)
         if (y >= h || x0 + xa >= w) continue;
         const int ny = min(h - 1, y + r) - max(0, y - r) + 1;
         const float2 *col = Vt + yr;  // column k of pair plane q at col[q * kstride + k * BT_VP]
+        const uint2 *ucol = Vu + yr;
         float2 S[NP];
+        uint2 U[NP];
 #pragma unroll
-        for (int k = 0; k < NP; ++k) S[k] = make_float2(0.0f, 0.0f);
+        for (int k = 0; k < NP; ++k) { S[k] = make_float2(0.0f, 0.0f); U[k] = make_uint2(0u, 0u); }
 #pragma unroll
         for (int k = 0; k <= 2 * r; ++k) {
 #pragma unroll
-            for (int q = 0; q < NP; ++q) S[q] = add2(S[q], col[q * kstride + (size_t)(xa + k) * BT_VP]);
+            for (int q = 0; q < NP; ++q) {
+                if (INT) {
+                    const uint2 t = ucol[q * kstride + (size_t)(xa + k) * BT_VP];
+                    U[q].x += t.x; U[q].y += t.y;
+                } else {
+                    S[q] = add2(S[q], col[q * kstride + (size_t)(xa + k) * BT_VP]);
+                }
+            }
         }
 #pragma unroll
         for (int i = 0; i < BT_RH; ++i) {
@@ -678,14 +702,37 @@ __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile_x2(BoxParams P)
             if (x >= w) break;
             if (i > 0) {
 #pragma unroll
-                for (int q = 0; q < NP; ++q)
-                    S[q] = sub2(add2(S[q], col[q * kstride + (size_t)(xt + 2 * r) * BT_VP]),
-                                col[q * kstride + (size_t)(xt - 1) * BT_VP]);
+                for (int q = 0; q < NP; ++q) {
+                    if (INT) {
+                        const uint2 a = ucol[q * kstride + (size_t)(xt + 2 * r) * BT_VP];
+                        const uint2 b = ucol[q * kstride + (size_t)(xt - 1) * BT_VP];
+                        U[q].x = U[q].x + a.x - b.x;
+                        U[q].y = U[q].y + a.y - b.y;
+                    } else {
+                        S[q] = sub2(add2(S[q], col[q * kstride + (size_t)(xt + 2 * r) * BT_VP]),
+                                    col[q * kstride + (size_t)(xt - 1) * BT_VP]);
+                    }
+                }
             }
             const int nx = min(w - 1, x + r) - max(0, x - r) + 1;
             const float inv = __fdividef(1.0f, (float)(nx * ny));
             float o0, o1;
-            if (KIND == KIND_STATS_F) {
+            if (INT) {
+                // exact integer numerators of var and cov (n^2 (255 k)^2 times them), as k_box_tile forms them
+                const long long nn = nx * ny;
+                const long long vnum = nn * (long long)U[1].x - (long long)U[0].x * (long long)U[0].x;
+                const long long cnum = nn * (long long)U[1].y - (long long)U[0].x * (long long)U[0].y;
+                const float den = (float)vnum + P.eps * ((float)nn * (float)nn) * (P.int_scale * P.int_scale);
+                o0 = __fdividef((float)cnum, den);                                                   // a, Eq. (2)
+                o1 = __fdividef((float)U[0].y - o0 * (float)U[0].x, (float)(nx * ny) * P.int_scale);  // b, Eq. (3)
+                if (P.stats) {  // the integer window sums, staged as bit patterns
+                    const int so = yr * BT_OP + xt;
+                    St[so] = __uint_as_float(U[0].x);
+                    St[BT_TH * BT_OP + so] = __uint_as_float(U[1].x);
+                    St[2 * BT_TH * BT_OP + so] = __uint_as_float(U[0].y);
+                    St[3 * BT_TH * BT_OP + so] = __uint_as_float(U[1].y);
+                }
+            } else if (KIND == KIND_STATS_F) {
                 const float mI = S[0].x * inv, mp = S[0].y * inv;    // shifted means
                 const float eII = S[1].x * inv, eIp = S[1].y * inv;
                 const float var = fmaxf(eII - mI * mI, 0.0f);      // var_I
@@ -718,11 +765,11 @@ __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile_x2(BoxParams P)
         if (y < h && x < w) {
             P.out0[obase + (size_t)y * w + x] = Ot[yr * BT_OP + xt];
             P.out1[obase + (size_t)y * w + x] = Ot[BT_TH * BT_OP + yr * BT_OP + xt];
-            if (KIND == KIND_STATS_F && P.stats) {
+            if (KIND != KIND_MEAN2 && P.stats) {  // FP32 statistics, or the uint32 window sums (KIND 1)
                 const size_t ps = (size_t)h * w;
-                float *st = (float *)P.stats + (size_t)plane * 4 * ps + (size_t)y * w + x;
+                uint32_t *st = (uint32_t *)P.stats + (size_t)plane * 4 * ps + (size_t)y * w + x;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) st[q * ps] = St[q * BT_TH * BT_OP + yr * BT_OP + xt];
+                for (int q = 0; q < 4; ++q) st[q * ps] = __float_as_uint(St[q * BT_TH * BT_OP + yr * BT_OP + xt]);
             }
         }
     }
@@ -1152,7 +1199,7 @@ cudaError_t launch_box_x2(const BoxParams &bp, int planes, cudaStream_t st)
     const int nq = (KIND == KIND_MEAN2) ? 2 : 4;
     // plus the staging tile of the four window statistics when they are an output
     const size_t smem = box_tile_smem(nq, bp.r) +
-                        ((KIND == KIND_STATS_F && bp.stats) ? (size_t)4 * BT_TH * BT_OP * sizeof(float) : 0);
+                        ((KIND != KIND_MEAN2 && bp.stats) ? (size_t)4 * BT_TH * BT_OP * sizeof(float) : 0);
     cudaError_t e = opt_in_smem(k_box_tile_x2<T, KIND, RV, RH, RC>, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((bp.w + BT_TW - 1) / BT_TW, (bp.h + BT_TH - 1) / BT_TH, planes);
@@ -1165,6 +1212,15 @@ cudaError_t launch_box_x2(const BoxParams &bp, int planes, cudaStream_t st)
 template <typename T, int KIND>
 cudaError_t launch_box_t(const BoxParams &bp, int planes, cudaStream_t st)
 {
+    if constexpr (KIND == KIND_STATS_INT && std::is_same<T, float>::value) {
+        switch (bp.r) {  // exact FP32 column sums staged as integers (k_box_tile_x2), r' <= 4
+        case 1: return launch_box_x2<T, KIND, 8, 8, 1>(bp, planes, st);
+        case 2: return launch_box_x2<T, KIND, 8, 8, 2>(bp, planes, st);
+        case 3: return launch_box_x2<T, KIND, 8, 8, 3>(bp, planes, st);
+        case 4: return launch_box_x2<T, KIND, 8, 8, 4>(bp, planes, st);
+        default: break;
+        }
+    }
     if constexpr (KIND != KIND_STATS_INT) {
         switch (bp.r) {  // common small radii with the radius known at compile time
         case 1: return launch_box_x2<T, KIND, 8, 8, 1>(bp, planes, st);
