@@ -299,14 +299,15 @@ struct BoxTParams {
 
 __device__ __forceinline__ int win_count(int k, int r, int n) { return min(n - 1, k + r) - max(0, k - r) + 1; }
 
-template <int NIN, int EPI, bool COMP>
+template <int NIN, int EPI, bool COMP, int RC = 0>
 __global__ void __launch_bounds__(BB_NT) k_bwd_box_T(BoxTParams P)
 {
+    static_assert(RC == 0 || !COMP, "a compile-time radius is for the small, uncompensated windows");
     constexpr int NOUT = (EPI == EPI_CHAIN) ? 4 : 2;
     extern __shared__ float smf[];
     __shared__ float red[BB_NT / 32];
     const int tid = threadIdx.x;
-    const int h = P.h, w = P.w, r = P.r;
+    const int h = P.h, w = P.w, r = RC > 0 ? RC : P.r;
     const int span = BB_TW + 2 * r;
     float *Vt = smf;                                 // [NIN][span][BB_VP]
     float *Ot = smf;                                 // [NIN][BB_TH][BB_OP] window sums, over Vt after phase 2
@@ -321,6 +322,43 @@ __global__ void __launch_bounds__(BB_NT) k_bwd_box_T(BoxTParams P)
         float S[NIN], Sc[NIN];
 #pragma unroll
         for (int q = 0; q < NIN; ++q) { S[q] = 0.0f; Sc[q] = 0.0f; }
+        if constexpr (RC > 0) {
+            // radius known at compile time: the RV + 2 RC scaled rows of the segment's window span are requested
+            // at once into registers (rows outside the image count as zero), then slid over
+            if (gx >= 0 && gx < w && ya < h) {
+                constexpr int NR = BB_RV + 2 * RC;
+                const float inx = __fdividef(1.0f, (float)win_count(gx, RC, w));
+                float v[NR][NIN];
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    const int yy = ya - RC + k;
+                    const bool ok = yy >= 0 && yy < h;
+                    const float sc = ok ? inx * __fdividef(1.0f, (float)win_count(yy, RC, h)) : 0.0f;
+                    const size_t o = pbase + (size_t)(ok ? yy : 0) * w + gx;
+#pragma unroll
+                    for (int q = 0; q < NIN; ++q) v[k][q] = ok ? sc * __ldg(P.in[q] + o) : 0.0f;
+                }
+#pragma unroll
+                for (int k = 0; k <= 2 * RC; ++k)
+#pragma unroll
+                    for (int q = 0; q < NIN; ++q) S[q] += v[k][q];
+#pragma unroll
+                for (int i = 0; i < BB_RV; ++i) {
+                    if (i > 0) {
+#pragma unroll
+                        for (int q = 0; q < NIN; ++q) S[q] = (S[q] + v[i + 2 * RC][q]) - v[i - 1][q];
+                    }
+#pragma unroll
+                    for (int q = 0; q < NIN; ++q) Vt[((size_t)q * span + xc) * BB_VP + vrow + i] = S[q];
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < BB_RV; ++i)
+#pragma unroll
+                    for (int q = 0; q < NIN; ++q) Vt[((size_t)q * span + xc) * BB_VP + vrow + i] = 0.0f;
+            }
+            continue;
+        }
         if (gx >= 0 && gx < w && ya < h) {
             const float inx = __fdividef(1.0f, (float)win_count(gx, r, w));
             auto add_row = [&](int yy, float sign) {
@@ -637,6 +675,22 @@ cudaError_t launch_box_T(const BoxTParams &bp, int planes, cudaStream_t st)
     // the staging tile of the window sums lies over the column sums: the larger of the two
     const size_t smem = std::max((size_t)NIN * (BB_TW + 2 * bp.r) * BB_VP, (size_t)NIN * BB_TH * BB_OP) * sizeof(float);
     dim3 grid((bp.w + BB_TW - 1) / BB_TW, (bp.h + BB_TH - 1) / BB_TH, planes);
+    if (bp.r >= 1 && bp.r <= 4) {  // compile-time radius: every row of a column segment requested at once
+        cudaError_t e = cudaSuccess;
+#define GF_BT(RR)                                                                             \
+    do {                                                                                      \
+        if ((e = opt_in_smem(k_bwd_box_T<NIN, EPI, false, RR>, smem)) != cudaSuccess) return e; \
+        k_bwd_box_T<NIN, EPI, false, RR><<<grid, BB_NT, smem, st>>>(bp);                        \
+    } while (0)
+        switch (bp.r) {
+        case 1: GF_BT(1); break;
+        case 2: GF_BT(2); break;
+        case 3: GF_BT(3); break;
+        default: GF_BT(4); break;
+        }
+#undef GF_BT
+        return cudaGetLastError();
+    }
     if (bp.r > 16) {
         cudaError_t e = opt_in_smem(k_bwd_box_T<NIN, EPI, true>, smem);
         if (e != cudaSuccess) return e;
@@ -671,7 +725,7 @@ cudaError_t launch_backward(const BwdPlan &B, cudaStream_t st)
         UpTParams up;
         up.g = B.dq; up.I = (const float *)F.I; up.dma = B.dma; up.dmb = B.dmb;
         up.C = F.C; up.CI = F.CI; up.H = F.H; up.W = F.W; up.h = F.h; up.w = F.w; up.s = F.s;
-        up.TJ = 8;
+        up.TJ = 16;
         up.lps = F.lps;
         const int NRmax = F.s * (up.TJ + 2);
         const size_t smem = ((size_t)2 * NRmax * UT_TI + (size_t)up.TJ * 3 * F.s) * sizeof(float);
