@@ -189,52 +189,73 @@ __global__ void __launch_bounds__(UT_NT) k_bwd_upsample_T_v(UpTParams P)
         const int j = j0 + jl, Y = S * (j - 1) + t;
         wy[k] = (j < P.h && Y >= 0 && Y < P.H) ? up_weight(Y, j, S, P.h) : 0.0f;
     }
-    // horizontal gather: T[y][i] = sum_X wx(X -> i) v(y, X)
-    for (int k = threadIdx.x; k < NR * UT_TI; k += UT_NT) {
-        const int yl = k / UT_TI, il = k - yl * UT_TI;
-        const int i = i0 + il;
-        float sa = 0.0f, sg = 0.0f;
-        if (i < P.w) {
-            const float *gr = g + (size_t)(Y0 + yl) * P.W, *Ir = I + (size_t)(Y0 + yl) * P.W;
-            if (i >= 1 && i <= P.w - 2) {
-                float gl[HS], Il[HS], gc[S], Ic[S], gn[HS], In[HS];
-                ld_vec<HS>(gr + (size_t)S * i - HS, gl);
-                ld_vec<HS>(Ir + (size_t)S * i - HS, Il);
-                ld_vec<S>(gr + (size_t)S * i, gc);
-                ld_vec<S>(Ir + (size_t)S * i, Ic);
-                ld_vec<HS>(gr + (size_t)S * (i + 1), gn);
-                ld_vec<HS>(Ir + (size_t)S * (i + 1), In);
-#pragma unroll
-                for (int t = 0; t < HS; ++t) {
-                    sa = fmaf(up_wT<S>(-1, HS + t), gl[t] * Il[t], sa);
-                    sg = fmaf(up_wT<S>(-1, HS + t), gl[t], sg);
-                }
-#pragma unroll
-                for (int t = 0; t < S; ++t) {
-                    sa = fmaf(up_wT<S>(0, t), gc[t] * Ic[t], sa);
-                    sg = fmaf(up_wT<S>(0, t), gc[t], sg);
-                }
-#pragma unroll
-                for (int t = 0; t < HS; ++t) {
-                    sa = fmaf(up_wT<S>(1, t), gn[t] * In[t], sa);
-                    sg = fmaf(up_wT<S>(1, t), gn[t], sg);
-                }
-            } else {
-                const int xb = S * (i - 1);
-                for (int t = 0; t < ncand; ++t) {
-                    const int X = xb + t;
-                    if (X < 0 || X >= P.W) continue;
-                    const float wgt = up_weight(X, i, S, P.w);
-                    if (wgt != 0.0f) {
-                        const float gv = __ldg(gr + X);
-                        sg = fmaf(wgt, gv, sg);
-                        sa = fmaf(wgt, gv * __ldg(Ir + X), sa);
-                    }
-                }
+    // horizontal gather: T[y][i] = sum_X wx(X -> i) v(y, X), two adjacent columns i, i + 1 per thread: inside
+    // the image they share the loads of blocks i and i + 1
+    auto edge_col = [&](const float *gr, const float *Ir, int i, float &sa, float &sg) {
+        const int xb = S * (i - 1);
+        for (int t = 0; t < ncand; ++t) {
+            const int X = xb + t;
+            if (X < 0 || X >= P.W) continue;
+            const float wgt = up_weight(X, i, S, P.w);
+            if (wgt != 0.0f) {
+                const float gv = __ldg(gr + X);
+                sg = fmaf(wgt, gv, sg);
+                sa = fmaf(wgt, gv * __ldg(Ir + X), sa);
             }
         }
-        Tga[k] = sa;
-        Tg[k] = sg;
+    };
+    for (int k = threadIdx.x; k < NR * (UT_TI / 2); k += UT_NT) {
+        const int yl = k / (UT_TI / 2), il = 2 * (k - yl * (UT_TI / 2));
+        const int i = i0 + il;
+        float sa0 = 0.0f, sg0 = 0.0f, sa1 = 0.0f, sg1 = 0.0f;
+        const float *gr = g + (size_t)(Y0 + yl) * P.W, *Ir = I + (size_t)(Y0 + yl) * P.W;
+        if (i >= 1 && i + 1 <= P.w - 2) {
+            float gl[HS], Il[HS], g0[S], I0[S], g1[S], I1[S], gn[HS], In[HS];
+            ld_vec<HS>(gr + (size_t)S * i - HS, gl);
+            ld_vec<HS>(Ir + (size_t)S * i - HS, Il);
+            ld_vec<S>(gr + (size_t)S * i, g0);
+            ld_vec<S>(Ir + (size_t)S * i, I0);
+            ld_vec<S>(gr + (size_t)S * (i + 1), g1);
+            ld_vec<S>(Ir + (size_t)S * (i + 1), I1);
+            ld_vec<HS>(gr + (size_t)S * (i + 2), gn);
+            ld_vec<HS>(Ir + (size_t)S * (i + 2), In);
+#pragma unroll
+            for (int t = 0; t < HS; ++t) {  // block i - 1 (second half) -> column i
+                sa0 = fmaf(up_wT<S>(-1, HS + t), gl[t] * Il[t], sa0);
+                sg0 = fmaf(up_wT<S>(-1, HS + t), gl[t], sg0);
+            }
+#pragma unroll
+            for (int t = 0; t < S; ++t) {  // block i -> column i (all) and column i + 1 (second half)
+                const float a = g0[t] * I0[t];
+                sa0 = fmaf(up_wT<S>(0, t), a, sa0);
+                sg0 = fmaf(up_wT<S>(0, t), g0[t], sg0);
+                if (t >= HS) {
+                    sa1 = fmaf(up_wT<S>(-1, t), a, sa1);
+                    sg1 = fmaf(up_wT<S>(-1, t), g0[t], sg1);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < S; ++t) {  // block i + 1 -> column i (first half) and column i + 1 (all)
+                const float a = g1[t] * I1[t];
+                if (t < HS) {
+                    sa0 = fmaf(up_wT<S>(1, t), a, sa0);
+                    sg0 = fmaf(up_wT<S>(1, t), g1[t], sg0);
+                }
+                sa1 = fmaf(up_wT<S>(0, t), a, sa1);
+                sg1 = fmaf(up_wT<S>(0, t), g1[t], sg1);
+            }
+#pragma unroll
+            for (int t = 0; t < HS; ++t) {  // block i + 2 (first half) -> column i + 1
+                sa1 = fmaf(up_wT<S>(1, t), gn[t] * In[t], sa1);
+                sg1 = fmaf(up_wT<S>(1, t), gn[t], sg1);
+            }
+        } else {
+            if (i < P.w) edge_col(gr, Ir, i, sa0, sg0);
+            if (i + 1 < P.w) edge_col(gr, Ir, i + 1, sa1, sg1);
+        }
+        const int o = yl * UT_TI + il;
+        *reinterpret_cast<float2 *>(Tga + o) = make_float2(sa0, sa1);
+        *reinterpret_cast<float2 *>(Tg + o) = make_float2(sg0, sg1);
     }
     __syncthreads();
     // vertical gather: dM[j][i] = sum_y wy(y -> j) T[y][i]
