@@ -316,6 +316,16 @@ gf_status gf_serve_stats_get(gf_ctx *ctx, gf_serve_stats *out);
 gf_status gf_filter_noalloc(const void *I, const void *p, void *q, int H, int W, int C, int r, float eps, int s,
                             gf_subsample_mode mode, const gf_opts *opts, void *cuda_stream);
 
+/*
+ * Environment variables read by the library (none is needed in normal use):
+ *   GF_NO_TMA       set: the s = 4, 8 output step uses its per-thread cp.async form instead of the
+ *                   TMA-fed kernel (same results; for comparing the two and for drivers without
+ *                   cuTensorMapEncodeTiled).  Read at every call.
+ *   GF_FAULT        "launch:K": the serving loop's launch attempt number K (counting from 0) launches
+ *                   nothing and fails its request with GF_ECUDA (host-side fault injection for tests of
+ *                   the error path; no GPU fault is made).  Read when the context is created.
+ */
+
 #ifdef __cplusplus
 }
 #endif
