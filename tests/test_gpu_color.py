@@ -53,6 +53,7 @@ CASES = [  # (N, C, H, W, r, eps, s, mode, p_lowres)
     (1, 1, 203, 408, 16, 1e-3, 8, "bilinear_aa", False),
     (2, 3, 96, 128, 0, 1e-2, 4, "box", True),
     (1, 4, 257, 1030, 24, 1e-4, 8, "bilinear", False),
+    (1, 3, 136, 264, 16, 1e-3, 8, "bilinear", False),    # s = 8 run form of the output, C = 3
     (1, 1, 7, 5, 4, 1e-2, 2, "bilinear", False),
 ]
 
