@@ -376,17 +376,22 @@ TRAIN_WORKLOAD = "trainable layer, batch 16 x 3 x 1024^2, s=4 box, r'=2, eps=1e-
 
 def run_training(dev, stream, ctx, world, steps, warmup):
     """Trainable-layer workload: batch 16 x 3 x 1024^2 guide (depthwise), low-res p 16 x 3 x 256^2, s = 4 box,
-    r' = 2, eps = 1e-2; forward and hand-written backward (dI, dp, d eps) timed apart."""
+    r' = 2, eps = 1e-2; forward (keeping its low-res planes for the backward) and hand-written backward
+    (dI, dp, d eps) timed apart."""
     import paper_1505_00996_gb300 as gf
     g = torch.Generator(device=dev).manual_seed(3)
     Ib = torch.rand((16, 3, 1024, 1024), device=dev, generator=g)
     pb = torch.rand((16, 3, 256, 256), device=dev, generator=g)
     gq = torch.rand(Ib.shape, device=dev, generator=g) * 2.0 - 1.0
     qb = torch.empty_like(Ib)
+    # the forward keeps its low-res planes in the backward's workspace (as the autograd layer does), so the
+    # backward does not recompute them
+    ws = torch.empty(gf.backward_workspace_size(1024, 1024, 3, 4, batch=16, guide_channels=3, r_low=2, p_lowres=True),
+                     dtype=torch.uint8, device=dev)
     fwd = lambda: gf.fast_guided_filter(Ib, pb, 0, 1e-2, 4, "box", r_low=2, p_lowres=True, out=qb, stream=stream,
-                                        ctx=ctx)
+                                        ctx=ctx, workspace=ws, saved_forward=True)
     bwd = lambda: gf.fast_guided_filter_backward(Ib, pb, gq, 0, 1e-2, 4, "box", r_low=2, p_lowres=True,
-                                                 stream=stream, ctx=ctx)
+                                                 stream=stream, ctx=ctx, workspace=ws, saved_forward=True)
     ms_f = time_steps([(stream, fwd)], steps, warmup, world, 1, False)
     ms_b = time_steps([(stream, bwd)], steps, warmup, world, 1, False)
     return {"workload": TRAIN_WORKLOAD, "forward_ms": round(ms_f, 4), "backward_ms": round(ms_b, 4),

@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define GF_ABI_VERSION 2
+#define GF_ABI_VERSION 3
 #define GF_MAX_STAGES 8 /* kernel stages one gf_filter call can launch (for gf_opts.kernel_events) */
 #define GF_FUSED_AUTO_PIXELS (1 << 20) /* gf_opts.fused = 0 runs the single kernel up to N*C*H*W pixels */
 
@@ -110,6 +110,14 @@ typedef struct gf_ctx gf_ctx;
  *                   -1: never.  The single
  *                   kernel takes FP32 or FP16 storage, a gray or depthwise guide, any subsample mode and
  *                   ratio, r' up to what fits its tiles in shared memory, and no low-res intermediate outputs.
+ *   saved_forward   nonzero, with a workspace of at least gf_backward_workspace_size() bytes: gf_filter
+ *                   also keeps the forward's low-res planes (I', p', the window statistics, a, the box
+ *                   means) in that workspace, laid out as gf_filter_backward reads them, and
+ *                   gf_filter_backward given the same workspace and flag skips recomputing them.  The
+ *                   backward call must use the same arguments and inputs as the forward that saved them,
+ *                   with no other call on that workspace in between (not checked).  Takes what the
+ *                   backward takes (FP32, nearest / bilinear / box, integer ratio, no row range, detail
+ *                   gain or colour guide) and no low-res intermediate outputs; GF_EINVAL otherwise.
  *   color_guide     nonzero: I has guide_channels = 3 channels used jointly as a colour guide for every
  *                   channel of p (the guided filter's colour form, which the paper cites): per window
  *                   a = (Sigma + eps U)^-1 cov_Ip with Sigma the 3 x 3 covariance of I', b = mean_p - a^T
@@ -138,6 +146,7 @@ typedef struct gf_opts {
     int s_num;
     int s_den;
     int fused;
+    int saved_forward;
 } gf_opts;
 
 /* Default options: batch 1, gray guide, derived r', full-res p, FP32 in and out, nothing optional. */
@@ -227,7 +236,8 @@ int gf_host_strips(int H, int W, int C, int s, gf_subsample_mode mode, const gf_
  *   resolution, or N x C x h x w when opts->p_lowres), and, if d_eps is not NULL, the device scalar
  *   dL/d eps (summed over every channel, pixel and batch element).  All FP32 (opts->dtype_in and dtype_out
  *   must be GF_F32); the other arguments are those of the forward call.  The forward statistics are
- *   recomputed.  Scratch: the context arena, or opts->workspace of gf_backward_workspace_size() bytes.
+ *   recomputed, unless opts->saved_forward names a workspace a gf_filter call filled (see gf_opts).
+ *   Scratch: the context arena, or opts->workspace of gf_backward_workspace_size() bytes.
  *   Asynchronous on cuda_stream; deterministic (no atomics).
  */
 gf_status gf_backward_workspace_size(int H, int W, int C, int s, const gf_opts *opts, size_t *bytes);

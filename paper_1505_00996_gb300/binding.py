@@ -32,6 +32,9 @@ class GFError(RuntimeError):
         self.status = status
 
 
+ABI_VERSION = 3  # GF_ABI_VERSION of include/gf.h that GFOpts mirrors
+
+
 class GFOpts(ctypes.Structure):
     _fields_ = [
         ("batch", ctypes.c_int),
@@ -55,6 +58,7 @@ class GFOpts(ctypes.Structure):
         ("s_num", ctypes.c_int),
         ("s_den", ctypes.c_int),
         ("fused", ctypes.c_int),
+        ("saved_forward", ctypes.c_int),
     ]
 
 
@@ -108,6 +112,9 @@ def load_library(build_if_missing=True):
         lib.gf_opts_init.argtypes = [P(GFOpts)]
         lib.gf_opts_init.restype = None
         lib.gf_abi_version.restype = i
+        if lib.gf_abi_version() != ABI_VERSION:
+            raise RuntimeError("libgf.so has ABI version %d, this binding needs %d: rebuild it"
+                               % (lib.gf_abi_version(), ABI_VERSION))
         lib.gf_last_error.restype = ctypes.c_char_p
         lib.gf_lowres_geometry.argtypes = [i, i, i, i, i, P(i), P(i), P(i)]
         lib.gf_lowres_geometry.restype = i
@@ -298,7 +305,7 @@ def _stream_handle(stream):
 def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowres=False, out_dtype=None,
                        out=None, a_out=None, b_out=None, mean_a_out=None, mean_b_out=None, stats_out=None,
                        workspace=None, kernel_events=None, stream=None, ctx=None, detail_gain=0.0, rows=None,
-                       color_guide=False, fused=0):
+                       color_guide=False, fused=0, saved_forward=False):
     """Fast guided filter (Algorithm 2; Algorithm 1 at s = 1) on CUDA tensors, via ``gf_filter``.
 
     I: (H, W), (CI, H, W) or (N, CI, H, W); p: the same rank with C channels (at low resolution when
@@ -309,6 +316,8 @@ def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowr
     other rows are left as they are): one strip of an image split across devices or streams.
     ``color_guide=True``: I has 3 channels used jointly as a colour guide for every channel of p.
     ``fused``: 0 runs the whole filter as one kernel for small images, 1 always, -1 never.
+    ``saved_forward=True`` with ``workspace`` (``backward_workspace_size`` bytes) keeps the low-res planes
+    there for a ``fast_guided_filter_backward`` call with the same arguments, workspace and flag.
     """
     if not (I.is_cuda and p.is_cuda):
         raise ValueError("I and p must be CUDA tensors")
@@ -347,6 +356,7 @@ def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowr
     o.detail_gain = float(detail_gain)
     o.color_guide = int(bool(color_guide))
     o.fused = int(fused)
+    o.saved_forward = int(bool(saved_forward))
     if rows is not None:
         if not given:
             raise ValueError("rows needs out= (the whole q; rows outside the range are not written)")
@@ -415,12 +425,27 @@ def fast_guided_filter_host(I, p, r, eps, s=4, mode="bilinear", *, out=None, out
     return out.reshape(p.shape[:-2] + (H, W)) if prank < 4 else out
 
 
+def backward_workspace_size(H, W, C, s=4, *, batch=1, guide_channels=1, r_low=None, p_lowres=False):
+    """Bytes of scratch a backward call (and a forward call that saves for it) needs."""
+    o = opts_init()
+    o.batch, o.guide_channels = int(batch), int(guide_channels)
+    o.r_low = -1 if r_low is None else int(r_low)
+    o.p_lowres = int(bool(p_lowres))
+    s = _ratio(o, s)
+    n = ctypes.c_size_t()
+    check(load_library().gf_backward_workspace_size(int(H), int(W), int(C), int(s), ctypes.byref(o), ctypes.byref(n)))
+    return n.value
+
+
 def fast_guided_filter_backward(I, p, dq, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowres=False,
-                                need_eps=True, stream=None, ctx=None):
+                                need_eps=True, stream=None, ctx=None, workspace=None, saved_forward=False):
     """Backward pass of ``fast_guided_filter`` via ``gf_filter_backward`` (FP32 CUDA tensors).
 
     dq has the shape of q.  Returns (dI, dp, deps): dI shaped like I, dp shaped like p, deps a 0-dim
-    device tensor (or None when ``need_eps`` is False)."""
+    device tensor (or None when ``need_eps`` is False).  ``workspace``: optional scratch of
+    ``backward_workspace_size`` bytes; with ``saved_forward=True`` it holds the low-res planes a
+    ``fast_guided_filter(..., saved_forward=True)`` call with the same arguments left there, and they are
+    not recomputed."""
     if not (I.is_cuda and p.is_cuda and dq.is_cuda):
         raise ValueError("I, p and dq must be CUDA tensors")
     if I.dtype != torch.float32 or p.dtype != torch.float32 or dq.dtype != torch.float32:
@@ -441,6 +466,10 @@ def fast_guided_filter_backward(I, p, dq, r, eps, s=4, mode="bilinear", *, r_low
     o.r_low = -1 if r_low is None else int(r_low)
     s = _ratio(o, s)
     o.p_lowres = int(bool(p_lowres))
+    o.saved_forward = int(bool(saved_forward))
+    if workspace is not None:
+        o.workspace = workspace.data_ptr()
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
     ctx = ctx or default_context(I.device.index)
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     with torch.cuda.device(I.device):

@@ -336,7 +336,7 @@ int host_strips(const Resolved &R, const gf_opts *o, size_t host_bytes, std::vec
     Y.clear();
     if (host_bytes < HOST_PIPE_MIN_BYTES) return 0;
     if (R.sd != 1 || R.color || R.p_lowres || R.fused || R.dense_lowres) return 0;
-    if (o && (o->row_begin || o->row_end || o->stats_out || o->kernel_events)) return 0;
+    if (o && (o->row_begin || o->row_end || o->stats_out || o->kernel_events || o->saved_forward)) return 0;
     const int align = 8 * R.s;
     const int K = std::min(HOST_MAX_STRIPS, R.H / (64 * R.s));
     if (K < 2) return 0;
@@ -543,6 +543,26 @@ gf_status gf_filter(gf_ctx *ctx, const void *I, const void *p, void *q, int H, i
     Resolved R;
     gf_status st = resolve(H, W, C, r, eps, s, (int)mode, opts, R);
     if (st != GF_OK) return st;
+    if (opts && opts->saved_forward) {
+        // the forward of a later gf_filter_backward: its low-res planes stay in the backward's workspace layout
+        if ((st = check_backward(R)) != GF_OK) return st;
+        if (opts->a_out || opts->b_out || opts->mean_a_out || opts->mean_b_out || opts->stats_out)
+            return fail(GF_EINVAL, "saved_forward does not produce low-res intermediate outputs");
+        if (!opts->workspace) return fail(GF_EINVAL, "saved_forward needs opts->workspace (gf_backward_workspace_size bytes)");
+        R.lps = gfk::plane_stride_f32((size_t)R.h * R.w);
+        const BwdLayout BL = bwd_layout_of(R);
+        if (opts->workspace_bytes < BL.total)
+            return fail(GF_EINVAL, "saved_forward: workspace_bytes is smaller than gf_backward_workspace_size()");
+        DeviceGuard guard(ctx->device);
+        char *ws = (char *)opts->workspace;
+        gfk::FwdPlan P = gfk::make_plan(R, BL.fwd, I, p, q, ws, nullptr);
+        P.stats = ws + BL.off_stats;
+        P.need_lowres = true;
+        P.events = opts->kernel_events ? (cudaEvent_t *)opts->kernel_events : nullptr;
+        cudaError_t e = gfk::launch_forward(P, (cudaStream_t)cuda_stream);
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch in gf_filter");
+        return GF_OK;
+    }
     const Layout L = layout_of(R, opts);
 
     DeviceGuard guard(ctx->device);
@@ -648,6 +668,8 @@ gf_status gf_filter_backward(gf_ctx *ctx, const void *I, const void *p, const vo
     DeviceGuard guard(ctx->device);
     std::unique_lock<std::mutex> lock(ctx->mu, std::defer_lock);
     char *ws = nullptr;
+    const bool saved = opts && opts->saved_forward;
+    if (saved && !opts->workspace) return fail(GF_EINVAL, "saved_forward needs the workspace the forward filled");
     if (opts && opts->workspace) {
         if (opts->workspace_bytes < L.total)
             return fail(GF_EINVAL, "workspace_bytes is smaller than gf_backward_workspace_size()");
@@ -660,6 +682,7 @@ gf_status gf_filter_backward(gf_ctx *ctx, const void *I, const void *p, const vo
     }
 
     gfk::BwdPlan B;
+    B.fwd_saved = saved;
     B.fwd = gfk::make_plan(R, L.fwd, I, p, nullptr, ws, nullptr);
     gfk::FwdPlan &P = B.fwd;
     P.stats = ws + L.off_stats;

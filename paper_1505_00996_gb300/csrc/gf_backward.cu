@@ -736,8 +736,8 @@ cudaError_t launch_backward(const BwdPlan &B, cudaStream_t st)
     cudaError_t err;
     const FwdPlan &F = B.fwd;
     const int planes = F.N * F.C;
-    // ---- forward recomputation: low-res planes, statistics, a, mean_a
-    if ((err = launch_forward(F, st)) != cudaSuccess) return err;
+    // ---- forward recomputation: low-res planes, statistics, a, mean_a (unless a gf_filter call saved them)
+    if (!B.fwd_saved && (err = launch_forward(F, st)) != cudaSuccess) return err;
 
     // ---- dMA = U^T(g .* I), dMB = U^T(g)
     const bool up_vec = (F.s == 4 || F.s == 8) && F.W % F.s == 0 && F.H % F.s == 0 &&

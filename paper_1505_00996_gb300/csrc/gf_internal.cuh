@@ -60,6 +60,7 @@ struct FwdPlan {
 // write the window statistics (fwd.stats), a, mean_a and the low-res I', p' into the workspace.
 struct BwdPlan {
     FwdPlan fwd;
+    bool fwd_saved = false;  // the workspace already holds fwd's low-res planes (gf_opts.saved_forward)
     const float *dq;      // dL/dq, N x C x H x W
     float *dI, *dp;       // outputs: N x CI x H x W; like p (full or low resolution)
     float *d_eps;         // device scalar or NULL

@@ -61,8 +61,8 @@ extern "C" gf_status gf_filter_noalloc(const void *I, const void *p, void *q, in
         gf_set_error("I, p and q must be device pointers");
         return GF_EINVAL;
     }
-    if (opts && opts->workspace) {
-        gf_set_error("gf_filter_noalloc uses its static scratch; opts->workspace must be NULL");
+    if (opts && (opts->workspace || opts->saved_forward)) {
+        gf_set_error("gf_filter_noalloc uses its static scratch; opts->workspace and saved_forward must be unset");
         return GF_EINVAL;
     }
     gfk::Resolved R;

@@ -47,7 +47,8 @@ def test_opts_defaults(lib):
     o = binding.opts_init()
     assert (o.batch, o.guide_channels, o.r_low, o.p_lowres, o.dtype_in, o.dtype_out) == (1, 1, -1, 0, 0, 0)
     assert not o.workspace and not o.kernel_events
-    assert lib.gf_abi_version() == 2
+    assert lib.gf_abi_version() == 3
+    assert o.saved_forward == 0
 
 
 @pytest.mark.parametrize("H,W,s,r", [(3000, 4000, 4, 16), (3000, 4000, 8, 16), (3000, 4000, 1, 16), (10, 13, 4, 6),

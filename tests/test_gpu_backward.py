@@ -176,3 +176,36 @@ def test_antialiased_subsample_is_forward_only(gf):
     with pytest.raises(gf.GFError) as ei:
         gf.fast_guided_filter_backward(I, I, I, 4, 1e-2, 4, "bilinear_aa")
     assert ei.value.status == gf.GF_EINVAL
+
+
+@pytest.mark.parametrize("case", [
+    (1, 1, 3, 120, 200, 4, 1e-3, 4, 1, False),   # gray guide, bilinear
+    (2, 3, 3, 64, 64, 2, 1e-2, 4, 2, True),      # depthwise guide, box, low-res p
+    (1, 1, 2, 61, 43, 1, 5e-2, 3, 0, False),     # odd s, nearest, ragged
+], ids=lambda c: "N%dCI%dC%d_%dx%d_s%d_m%d" % (c[0], c[1], c[2], c[3], c[4], c[7], c[8]))
+def test_saved_forward_equals_recomputation(gf, case):
+    """gf_opts.saved_forward: the forward keeps its low-res planes in the backward's workspace and the backward
+    skips recomputing them.  q and every gradient equal those of the plain forward and the recomputing
+    backward bit for bit (the same kernels compute the same planes)."""
+    N, CI, C, H, W, rl, eps, s, mode, p_lowres = case
+    rng = np.random.default_rng(7 * H + W)
+    h, w = oracle.lowres_shape(H, W, s)
+    I = torch.from_numpy(rng.uniform(0, 1, (N, CI, H, W)).astype(np.float32)).cuda()
+    p = torch.from_numpy(rng.uniform(0, 1, (N, C, h, w) if p_lowres else (N, C, H, W)).astype(np.float32)).cuda()
+    g = torch.from_numpy(rng.uniform(-1, 1, (N, C, H, W)).astype(np.float32)).cuda()
+    kw = dict(r_low=rl, p_lowres=p_lowres)
+    q_plain = gf.fast_guided_filter(I, p, 0, eps, s, MODE_NAMES[mode], fused=-1, **kw)
+    ws = torch.empty(gf.backward_workspace_size(H, W, C, s, batch=N, guide_channels=CI, **kw), dtype=torch.uint8,
+                     device="cuda")
+    q_saved = gf.fast_guided_filter(I, p, 0, eps, s, MODE_NAMES[mode], workspace=ws, saved_forward=True, **kw)
+    ref = gf.fast_guided_filter_backward(I, p, g, 0, eps, s, MODE_NAMES[mode], **kw)
+    got = gf.fast_guided_filter_backward(I, p, g, 0, eps, s, MODE_NAMES[mode], workspace=ws, saved_forward=True, **kw)
+    got2 = gf.fast_guided_filter_backward(I, p, g, 0, eps, s, MODE_NAMES[mode], workspace=ws, saved_forward=True, **kw)
+    torch.cuda.synchronize()
+    assert torch.equal(q_saved, q_plain)
+    for a, b, c in zip(got, ref, got2):
+        assert torch.equal(a, b)
+        assert torch.equal(c, b)  # the backward leaves the saved planes as they were
+    with pytest.raises(gf.GFError) as ei:  # the saving forward needs the workspace
+        gf.fast_guided_filter(I, p, 0, eps, s, MODE_NAMES[mode], saved_forward=True, **kw)
+    assert ei.value.status == gf.GF_EINVAL
