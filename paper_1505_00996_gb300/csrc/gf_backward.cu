@@ -19,10 +19,10 @@
 // the transposed bilinear / subsample maps, evaluated as gathers (no atomics).
 //
 //   k_bwd_upsample_T   dMA, dMB: per low-res tile, a horizontal gather of g.*I and g into a shared table of
-//                      full-res rows x low-res columns, then a vertical gather; k_bwd_upsample_T_v is its
-//                      vector form for s = 4, 8 (each low-res column gathers its 2s pixels with vector
-//                      loads and compile-time weights; the image's edge columns and rows take the general
-//                      candidate loop).
+//                      full-res rows x low-res columns, then a vertical gather.  k_bwd_upsample_T_w is the
+//                      form for s = 4, 8 (H, W multiples of s): each lane reads one s-pixel block of a row
+//                      with vector loads, the three columns it reaches are summed across lanes by warp
+//                      shuffles, and each warp walks down its rows keeping three low-res row sums in registers.
 //   k_bwd_box_T        B^T of 2 maps with the chain epilogue (4 maps out, per-CTA partial sums of deps), or
 //                      B^T of 4 maps with the final combination into dI', dp'.  Same tiling as k_box_tile;
 //                      the epilogue runs in the write-out phase, a thread per pixel, so the forward planes it
@@ -128,15 +128,9 @@ __global__ void __launch_bounds__(UT_NT) k_bwd_upsample_T(UpTParams P)
     }
 }
 
-// Vector form of k_bwd_upsample_T for s = 4, 8 with H and W multiples of s and 16-byte aligned planes.
-// Under the bilinear upsample, pixel t of block i lies between low-res columns i - 1 and i at weight f_t of
-// column i when t < s/2 (f_t = (2t + 1 + s)/(2s)), and between i and i + 1 at weight f_t = (2t + 1 - s)/(2s)
-// of column i + 1 when t >= s/2.  So low-res column i gathers the second half of block i - 1 (weights f_t),
-// all of block i (f_t, then 1 - f_t) and the first half of block i + 1 (1 - f_t): 2s pixels with weights
-// known at compile time.  A thread forms that sum for one (full-res row, low-res column) from vector loads
-// of the three blocks (neighbouring threads share them through L1); low-res rows gather full-res rows with
-// the same pattern.  The image's first and last low-res column and row, whose taps are clamped, take the
-// general candidate loop of k_bwd_upsample_T.
+// Interior weights of the bilinear upsample for an even integer s: pixel t of block i lies between low-res
+// columns i - 1 and i at weight f_t of column i when t < s/2 (f_t = (2t + 1 + s)/(2s)), and between i and i + 1
+// at weight f_t = (2t + 1 - s)/(2s) of column i + 1 when t >= s/2.
 template <int S>
 __host__ __device__ constexpr float up_f(int t)
 {
@@ -167,127 +161,91 @@ __device__ __forceinline__ void ld_vec(const float *p, float (&v)[N])
     }
 }
 
+// Walking form of U^T for s = 4, 8 (H and W multiples of s, 16-byte aligned planes).  Under the bilinear
+// upsample, pixel t of block i reaches low-res column i - 1 with weight up_wT(1, t) (first half only), column i
+// with up_wT(0, t) and column i + 1 with up_wT(-1, t) (second half only); rows likewise.  Lane l of a warp reads
+// block i = i0 - 1 + l of a full-res row with vector loads and forms its three partial sums L, M, R; column i
+// then totals M_i + R_{i-1} + L_{i+1}, the neighbours' parts arriving by warp shuffles.  Lanes 0 and 31 only
+// supply those parts for the tile's outer columns, so a warp produces UW_TI = 30 columns.  The warp walks down
+// its TJ low-res rows keeping the row sums of rows j - 1, j, j + 1 in registers (no shared memory, no block
+// barrier): after block row j is read, row j - 1 is complete and is stored.  At the image's first and last
+// column (row) the upsample's taps are clamped, so the half block that would reach column -1 (or w) reaches
+// the edge column with weight 1 instead: the part is folded into M there.
+constexpr int UW_WARPS = 4;   // warps per CTA, each on its own TJ low-res rows
+constexpr int UW_TI = 30;     // low-res columns per warp (lanes 1 .. 30)
+
 template <int S>
-__global__ void __launch_bounds__(UT_NT) k_bwd_upsample_T_v(UpTParams P)
+__global__ void __launch_bounds__(32 * UW_WARPS) k_bwd_upsample_T_w(UpTParams P)
 {
-    static_assert(S % 4 == 0, "half blocks of whole float2 / float4 pieces");
-    extern __shared__ float sm[];
-    constexpr int ncand = 3 * S, HS = S / 2;
-    const int TJ = P.TJ;
-    const int i0 = blockIdx.x * UT_TI, j0 = blockIdx.y * TJ;
+    static_assert(S % 4 == 0, "whole float4 pieces per block");
+    constexpr int HS = S / 2;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ja = (blockIdx.y * UW_WARPS + warp) * P.TJ;
+    if (ja >= P.h) return;  // the whole warp: nothing below waits on the other warps
+    const int je = min(P.h, ja + P.TJ);
+    const int i = blockIdx.x * UW_TI - 1 + lane;  // the block this lane reads
     const int plane = blockIdx.z, n = plane / P.C, c = plane - n * P.C;
     const size_t HW = (size_t)P.H * P.W;
-    const float *g = P.g + (size_t)plane * HW;
-    const float *I = P.I + (size_t)(n * P.CI + (P.CI == 1 ? 0 : c)) * HW;
-    const int Y0 = max(0, S * (j0 - 1)), Y1 = min(P.H, S * (j0 + TJ + 1));
-    const int NR = Y1 - Y0;
-    float *Tga = sm;                         // [NR][UT_TI] horizontal gathers of g .* I
-    float *Tg = Tga + (size_t)NR * UT_TI;    // [NR][UT_TI] horizontal gathers of g
-    float *wy = Tg + (size_t)NR * UT_TI;     // [TJ][ncand] weights of Y = s(j-1) + t onto row j (edge rows)
-    for (int k = threadIdx.x; k < TJ * ncand; k += UT_NT) {
-        const int jl = k / ncand, t = k - jl * ncand;
-        const int j = j0 + jl, Y = S * (j - 1) + t;
-        wy[k] = (j < P.h && Y >= 0 && Y < P.H) ? up_weight(Y, j, S, P.h) : 0.0f;
-    }
-    // horizontal gather: T[y][i] = sum_X wx(X -> i) v(y, X), two adjacent columns i, i + 1 per thread: inside
-    // the image they share the loads of blocks i and i + 1
-    auto edge_col = [&](const float *gr, const float *Ir, int i, float &sa, float &sg) {
-        const int xb = S * (i - 1);
-        for (int t = 0; t < ncand; ++t) {
-            const int X = xb + t;
-            if (X < 0 || X >= P.W) continue;
-            const float wgt = up_weight(X, i, S, P.w);
-            if (wgt != 0.0f) {
-                const float gv = __ldg(gr + X);
-                sg = fmaf(wgt, gv, sg);
-                sa = fmaf(wgt, gv * __ldg(Ir + X), sa);
-            }
-        }
-    };
-    for (int k = threadIdx.x; k < NR * (UT_TI / 2); k += UT_NT) {
-        const int yl = k / (UT_TI / 2), il = 2 * (k - yl * (UT_TI / 2));
-        const int i = i0 + il;
-        float sa0 = 0.0f, sg0 = 0.0f, sa1 = 0.0f, sg1 = 0.0f;
-        const float *gr = g + (size_t)(Y0 + yl) * P.W, *Ir = I + (size_t)(Y0 + yl) * P.W;
-        if (i >= 1 && i + 1 <= P.w - 2) {
-            float gl[HS], Il[HS], g0[S], I0[S], g1[S], I1[S], gn[HS], In[HS];
-            ld_vec<HS>(gr + (size_t)S * i - HS, gl);
-            ld_vec<HS>(Ir + (size_t)S * i - HS, Il);
-            ld_vec<S>(gr + (size_t)S * i, g0);
-            ld_vec<S>(Ir + (size_t)S * i, I0);
-            ld_vec<S>(gr + (size_t)S * (i + 1), g1);
-            ld_vec<S>(Ir + (size_t)S * (i + 1), I1);
-            ld_vec<HS>(gr + (size_t)S * (i + 2), gn);
-            ld_vec<HS>(Ir + (size_t)S * (i + 2), In);
+    const float *g = P.g + (size_t)plane * HW + (size_t)S * max(i, 0);
+    const float *I = P.I + (size_t)(n * P.CI + (P.CI == 1 ? 0 : c)) * HW + (size_t)S * max(i, 0);
+    const bool col_ok = i >= 0 && i < P.w;
+    const bool first = i == 0, last = i == P.w - 1;
+    const bool store = lane >= 1 && lane <= UW_TI && col_ok;
+    float pa = 0.0f, pg = 0.0f, ca = 0.0f, cg = 0.0f;  // sums of low-res rows jb - 1 and jb
+    for (int jb = ja - 1; jb <= je; ++jb) {
+        float na = 0.0f, ng = 0.0f;                    // sums of low-res row jb + 1
+        const bool blk = jb >= 0 && jb < P.h;
 #pragma unroll
-            for (int t = 0; t < HS; ++t) {  // block i - 1 (second half) -> column i
-                sa0 = fmaf(up_wT<S>(-1, HS + t), gl[t] * Il[t], sa0);
-                sg0 = fmaf(up_wT<S>(-1, HS + t), gl[t], sg0);
-            }
+        for (int t = 0; t < S; ++t) {
+            // block row ja - 1 gives only its second half, block row je only its first half (warp-uniform)
+            if (!blk || (jb < ja && t < HS) || (jb == je && t >= HS)) continue;
+            float gv[S], Iv[S];
+            if (col_ok) {
+                const size_t ro = (size_t)(S * jb + t) * P.W;
+                ld_vec<S>(g + ro, gv);
+                ld_vec<S>(I + ro, Iv);
+            } else {
 #pragma unroll
-            for (int t = 0; t < S; ++t) {  // block i -> column i (all) and column i + 1 (second half)
-                const float a = g0[t] * I0[t];
-                sa0 = fmaf(up_wT<S>(0, t), a, sa0);
-                sg0 = fmaf(up_wT<S>(0, t), g0[t], sg0);
-                if (t >= HS) {
-                    sa1 = fmaf(up_wT<S>(-1, t), a, sa1);
-                    sg1 = fmaf(up_wT<S>(-1, t), g0[t], sg1);
+                for (int u = 0; u < S; ++u) gv[u] = Iv[u] = 0.0f;
+            }
+            float La = 0.0f, Lg = 0.0f, Ma = 0.0f, Mg = 0.0f, Ra = 0.0f, Rg = 0.0f;
+#pragma unroll
+            for (int u = 0; u < S; ++u) {
+                const float a = gv[u] * Iv[u];
+                if (u < HS) {
+                    La = fmaf(up_wT<S>(1, u), a, La);
+                    Lg = fmaf(up_wT<S>(1, u), gv[u], Lg);
+                } else {
+                    Ra = fmaf(up_wT<S>(-1, u), a, Ra);
+                    Rg = fmaf(up_wT<S>(-1, u), gv[u], Rg);
                 }
+                Ma = fmaf(up_wT<S>(0, u), a, Ma);
+                Mg = fmaf(up_wT<S>(0, u), gv[u], Mg);
             }
-#pragma unroll
-            for (int t = 0; t < S; ++t) {  // block i + 1 -> column i (first half) and column i + 1 (all)
-                const float a = g1[t] * I1[t];
-                if (t < HS) {
-                    sa0 = fmaf(up_wT<S>(1, t), a, sa0);
-                    sg0 = fmaf(up_wT<S>(1, t), g1[t], sg0);
-                }
-                sa1 = fmaf(up_wT<S>(0, t), a, sa1);
-                sg1 = fmaf(up_wT<S>(0, t), g1[t], sg1);
+            if (first) { Ma += La; Mg += Lg; }
+            if (last) { Ma += Ra; Mg += Rg; }
+            const float Ta = Ma + __shfl_up_sync(FULL, Ra, 1) + __shfl_down_sync(FULL, La, 1);
+            const float Tg = Mg + __shfl_up_sync(FULL, Rg, 1) + __shfl_down_sync(FULL, Lg, 1);
+            if (t < HS) {
+                pa = fmaf(up_wT<S>(1, t), Ta, pa);
+                pg = fmaf(up_wT<S>(1, t), Tg, pg);
+            } else {
+                na = fmaf(up_wT<S>(-1, t), Ta, na);
+                ng = fmaf(up_wT<S>(-1, t), Tg, ng);
             }
-#pragma unroll
-            for (int t = 0; t < HS; ++t) {  // block i + 2 (first half) -> column i + 1
-                sa1 = fmaf(up_wT<S>(1, t), gn[t] * In[t], sa1);
-                sg1 = fmaf(up_wT<S>(1, t), gn[t], sg1);
-            }
-        } else {
-            if (i < P.w) edge_col(gr, Ir, i, sa0, sg0);
-            if (i + 1 < P.w) edge_col(gr, Ir, i + 1, sa1, sg1);
+            ca = fmaf(up_wT<S>(0, t), Ta, ca);
+            cg = fmaf(up_wT<S>(0, t), Tg, cg);
         }
-        const int o = yl * UT_TI + il;
-        *reinterpret_cast<float2 *>(Tga + o) = make_float2(sa0, sa1);
-        *reinterpret_cast<float2 *>(Tg + o) = make_float2(sg0, sg1);
-    }
-    __syncthreads();
-    // vertical gather: dM[j][i] = sum_y wy(y -> j) T[y][i]
-    for (int k = threadIdx.x; k < TJ * UT_TI; k += UT_NT) {
-        const int jl = k / UT_TI, il = k - jl * UT_TI;
-        const int j = j0 + jl, i = i0 + il;
-        if (j >= P.h || i >= P.w) continue;
-        float sa = 0.0f, sb = 0.0f;
-        if (j >= 1 && j <= P.h - 2) {
-            const int yl0 = S * (j - 1) + HS - Y0;  // first row: the second half of block j - 1
-#pragma unroll
-            for (int t = 0; t < 2 * S; ++t) {
-                // rows S(j-1) + HS + t: block j - 1 (t < HS), block j (HS <= t < S + HS), block j + 1
-                const float wgt = t < HS ? up_wT<S>(-1, HS + t) : (t < S + HS ? up_wT<S>(0, t - HS) : up_wT<S>(1, t - S - HS));
-                const int yl = yl0 + t;
-                sa = fmaf(wgt, Tga[yl * UT_TI + il], sa);
-                sb = fmaf(wgt, Tg[yl * UT_TI + il], sb);
-            }
-        } else {
-            const int yb = S * (j - 1);
-            for (int t = 0; t < ncand; ++t) {
-                const float wgt = wy[jl * ncand + t];
-                if (wgt != 0.0f) {
-                    const int yl = yb + t - Y0;
-                    sa = fmaf(wgt, Tga[yl * UT_TI + il], sa);
-                    sb = fmaf(wgt, Tg[yl * UT_TI + il], sb);
-                }
-            }
+        if (jb == 0) { ca += pa; cg += pg; }
+        if (jb == P.h - 1) { ca += na; cg += ng; }
+        if (jb - 1 >= ja && store) {  // low-res row jb - 1 has all its rows now
+            const size_t o = (size_t)plane * P.lps + (size_t)(jb - 1) * P.w + i;
+            P.dma[o] = pa;
+            P.dmb[o] = pg;
         }
-        const size_t o = (size_t)plane * P.lps + (size_t)j * P.w + i;
-        P.dma[o] = sa;
-        P.dmb[o] = sb;
+        pa = ca; pg = cg;
+        ca = na; cg = ng;
     }
 }
 
@@ -748,16 +706,12 @@ cudaError_t launch_backward(const BwdPlan &B, cudaStream_t st)
         up.C = F.C; up.CI = F.CI; up.H = F.H; up.W = F.W; up.h = F.h; up.w = F.w; up.s = F.s;
         up.TJ = 16;
         up.lps = F.lps;
-        const int NRmax = F.s * (up.TJ + 2);
-        const size_t smem = ((size_t)2 * NRmax * UT_TI + (size_t)up.TJ * 3 * F.s) * sizeof(float);
-        dim3 grid((F.w + UT_TI - 1) / UT_TI, (F.h + up.TJ - 1) / up.TJ, planes);
-        if (F.s == 4) {
-            if ((err = opt_in_smem(k_bwd_upsample_T_v<4>, smem)) != cudaSuccess) return err;
-            k_bwd_upsample_T_v<4><<<grid, UT_NT, smem, st>>>(up);
-        } else {
-            if ((err = opt_in_smem(k_bwd_upsample_T_v<8>, smem)) != cudaSuccess) return err;
-            k_bwd_upsample_T_v<8><<<grid, UT_NT, smem, st>>>(up);
-        }
+        const int rows_per_cta = UW_WARPS * up.TJ;
+        dim3 grid((F.w + UW_TI - 1) / UW_TI, (F.h + rows_per_cta - 1) / rows_per_cta, planes);
+        if (F.s == 4)
+            k_bwd_upsample_T_w<4><<<grid, 32 * UW_WARPS, 0, st>>>(up);
+        else
+            k_bwd_upsample_T_w<8><<<grid, 32 * UW_WARPS, 0, st>>>(up);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     } else {
         UpTParams up;

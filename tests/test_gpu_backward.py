@@ -53,6 +53,8 @@ BWD_CASES = [
     (2, 1, 3, 48, 64, 1, 1e-2, 8, 2, False),   # box, gray guide, full-res p
     (1, 1, 2, 16, 24, 1, 1e-2, 8, 1, False),   # w = 3: both edge blocks and one inside
     (1, 1, 1, 16, 8, 1, 1e-2, 8, 0, False),    # w = 1: one block at both edges (h = 2: var > 0)
+    (1, 1, 2, 280, 260, 2, 1e-2, 4, 1, False), # h = 70, w = 65: several column tiles and row chunks of U^T
+    (1, 1, 1, 528, 496, 1, 1e-2, 8, 0, False), # s = 8: h = 66, w = 62
 ]
 
 
