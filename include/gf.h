@@ -334,6 +334,10 @@ gf_status gf_filter_noalloc(const void *I, const void *p, void *q, int H, int W,
  *   GF_FAULT        "launch:K": the serving loop's launch attempt number K (counting from 0) launches
  *                   nothing and fails its request with GF_ECUDA (host-side fault injection for tests of
  *                   the error path; no GPU fault is made).  Read when the context is created.
+ *
+ * Timeline profilers: gf_filter, gf_filter_host, gf_filter_backward, gf_filter_noalloc and each serving
+ * launch push an NVTX range named after the call ("gf_filter", ..., "gf_serve launch") for its host-side
+ * duration; without a profiler attached the ranges cost nothing.
  */
 
 #ifdef __cplusplus

@@ -538,6 +538,7 @@ gf_status gf_destroy(gf_ctx *ctx)
 gf_status gf_filter(gf_ctx *ctx, const void *I, const void *p, void *q, int H, int W, int C, int r, float eps, int s,
                     gf_subsample_mode mode, const gf_opts *opts, void *cuda_stream)
 {
+    gfk::NvtxRange range("gf_filter");
     if (!ctx) return fail(GF_EINVAL, "ctx is NULL");
     if (!I || !p || !q) return fail(GF_EINVAL, "I, p and q must be device pointers");
     Resolved R;
@@ -588,6 +589,7 @@ gf_status gf_filter(gf_ctx *ctx, const void *I, const void *p, void *q, int H, i
 gf_status gf_filter_host(gf_ctx *ctx, const void *I_host, const void *p_host, void *q_host, int H, int W, int C,
                          int r, float eps, int s, gf_subsample_mode mode, const gf_opts *opts, void *cuda_stream)
 {
+    gfk::NvtxRange range("gf_filter_host");
     if (!ctx) return fail(GF_EINVAL, "ctx is NULL");
     if (!I_host || !p_host || !q_host) return fail(GF_EINVAL, "I, p and q must be host pointers");
     Resolved R;
@@ -656,6 +658,7 @@ gf_status gf_filter_backward(gf_ctx *ctx, const void *I, const void *p, const vo
                              int H, int W, int C, int r, float eps, int s, gf_subsample_mode mode, const gf_opts *opts,
                              void *cuda_stream)
 {
+    gfk::NvtxRange range("gf_filter_backward");
     if (!ctx) return fail(GF_EINVAL, "ctx is NULL");
     if (!I || !p || !dq || !dI || !dp) return fail(GF_EINVAL, "I, p, dq, dI and dp must be device pointers");
     Resolved R;

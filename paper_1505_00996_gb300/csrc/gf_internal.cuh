@@ -10,7 +10,33 @@
 
 #include "../../include/gf.h"
 
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define GF_HAVE_NVTX 1
+#endif
+
 namespace gfk {
+
+// A named NVTX range around one entry-point call or serving launch, for timeline profilers; without a
+// profiler attached the push and pop return at once.
+struct NvtxRange {
+    explicit NvtxRange(const char *name)
+    {
+#ifdef GF_HAVE_NVTX
+        nvtxRangePushA(name);
+#else
+        (void)name;
+#endif
+    }
+    ~NvtxRange()
+    {
+#ifdef GF_HAVE_NVTX
+        nvtxRangePop();
+#endif
+    }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Element type of an input plane.
 enum DType { F32 = GF_F32, F16 = GF_F16, U8 = GF_U8 };

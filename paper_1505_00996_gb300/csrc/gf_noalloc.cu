@@ -57,6 +57,7 @@ gf_status scratch_for_current_device(void **out)
 extern "C" gf_status gf_filter_noalloc(const void *I, const void *p, void *q, int H, int W, int C, int r, float eps,
                                        int s, gf_subsample_mode mode, const gf_opts *opts, void *cuda_stream)
 {
+    gfk::NvtxRange range("gf_filter_noalloc");
     if (!I || !p || !q) {
         gf_set_error("I, p and q must be device pointers");
         return GF_EINVAL;

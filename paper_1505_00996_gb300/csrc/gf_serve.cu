@@ -145,6 +145,7 @@ void CUDART_CB on_done(void *arg)
 // *launched_some tells whether any kernel was enqueued before a failure.
 gf_status launch_request(Server *s, Request &r, bool *launched_some)
 {
+    NvtxRange range("gf_serve launch");
     *launched_some = false;
     if (s->fault_launch >= 0 && s->launches++ == s->fault_launch) {  // injected: nothing is launched
         gf_set_error("injected launch failure (GF_FAULT)");
