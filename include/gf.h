@@ -199,6 +199,8 @@ gf_status gf_destroy(gf_ctx *ctx);
  *   r >= 0 full-res radius; eps >= 0 regulariser added to var(I) (data on the [0,1] scale for the
  *   paper's eps values); s >= 1 subsampling ratio; mode: subsample mode.
  *   opts may be NULL (defaults).  cuda_stream: the stream the kernels run on.
+ *   Size limits (GF_EINVAL otherwise): H * W < 2^31, ceil(H/s) <= 65535, batch * (CI + C) <= 65535,
+ *   r' <= 128; uint8 input also needs (2r'+1)^2 (255k)^2 < 2^32 (k = 4 for bilinear at even s, else 1).
  * Without a caller workspace the call uses the context arena; growing it is synchronous, and two
  * calls that share a context arena must not run concurrently on different streams.
  * Returns GF_OK once the kernels are enqueued.
@@ -238,6 +240,7 @@ int gf_host_strips(int H, int W, int C, int s, gf_subsample_mode mode, const gf_
  *   must be GF_F32); the other arguments are those of the forward call.  The forward statistics are
  *   recomputed, unless opts->saved_forward names a workspace a gf_filter call filled (see gf_opts).
  *   Scratch: the context arena, or opts->workspace of gf_backward_workspace_size() bytes.
+ *   Size limits: those of gf_filter, and H <= 65535, batch <= 65535 (GF_EINVAL otherwise).
  *   Asynchronous on cuda_stream; deterministic (no atomics).
  */
 gf_status gf_backward_workspace_size(int H, int W, int C, int s, const gf_opts *opts, size_t *bytes);

@@ -136,3 +136,27 @@ def test_host_strips(lib):
     assert binding.host_strips(500, 40000, 3, 4) is None        # fewer than 2 x 64 s rows
     with pytest.raises(binding.GFError):
         binding.host_strips(0, 4000, 3, 4)
+
+
+def test_size_limits(lib):
+    """The documented size limits of gf_filter, each checked on both sides of its bound (host-only)."""
+    from paper_1505_00996_gb300 import binding
+    n = ctypes.c_size_t()
+
+    def ws(H, W, C, s, **fields):
+        o = binding.opts_init()
+        for k, v in fields.items():
+            setattr(o, k, v)
+        return lib.gf_workspace_size(H, W, C, s, ctypes.byref(o), ctypes.byref(n))
+
+    assert ws(46340, 46340, 1, 4) == binding.GF_OK           # H * W = 2147395600 < 2^31
+    assert ws(46341, 46341, 1, 4) == binding.GF_EINVAL       # H * W = 2147488281 >= 2^31
+    assert b"2^31" in lib.gf_last_error()
+    assert ws(65535, 2, 1, 1) == binding.GF_OK               # ceil(H / s) = 65535
+    assert ws(65536, 2, 1, 1) == binding.GF_EINVAL
+    assert ws(262140, 2, 1, 4) == binding.GF_OK              # ceil(262140 / 4) = 65535
+    assert ws(262141, 2, 1, 4) == binding.GF_EINVAL
+    assert ws(8, 8, 3, 4, batch=16383) == binding.GF_OK      # batch * (1 + 3) = 65532 planes
+    assert ws(8, 8, 3, 4, batch=16384) == binding.GF_EINVAL  # 65536 planes
+    assert ws(64, 64, 1, 4, r_low=128) == binding.GF_OK
+    assert ws(64, 64, 1, 4, r_low=129) == binding.GF_EINVAL
