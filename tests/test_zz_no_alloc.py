@@ -10,7 +10,6 @@ last so that a run stopping at the first failure has already run every other tes
 """
 import ctypes
 
-import numpy as np
 import pytest
 import torch
 
