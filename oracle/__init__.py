@@ -7,5 +7,5 @@ the two share no code.  See ``gf_oracle.c`` for the readings of the paper's open
 from .oracle import (  # noqa: F401
     SUB_NEAREST, SUB_BILINEAR, SUB_BOX, SUB_BILINEAR_AA, build, lowres_radius, lowres_shape, subsample, box_sum, box_mean,
     box_mean_bruteforce, upsample, fast_guided_filter, guided_filter, fast_guided_filter_backward,
-    detail_enhance, color_guided_filter, ratio,
+    detail_enhance, color_guided_filter, ratio, compile_library, use_library,
 )

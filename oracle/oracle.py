@@ -3,6 +3,7 @@
 TEST INFRASTRUCTURE: imported only by the tests, the smoke check and the benchmark's CPU-baseline leg.
 Every function takes and returns float64 numpy arrays; the C side does all of the arithmetic.
 """
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -21,50 +22,76 @@ _lock = threading.Lock()
 _lib = None
 
 
+def compile_library(src, out):
+    """gcc ``src`` (a copy of ``gf_oracle.c``) into the shared library ``out`` with the oracle's flags (no FMA
+    contraction, so that x86 and Arm hosts round the same way)."""
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", out, src, "-lm"])
+
+
 def build(force=False):
     """Compile ``gf_oracle.c`` with gcc into ``oracle/_build/libgforacle.so`` (no FMA contraction, so that
     x86 and Arm hosts round the same way).  Returns the library path."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        compile_library(_SRC, tmp)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def _bind(lib):
+    """Declare the argument types of the C entry points on a loaded build of ``gf_oracle.c``."""
+    D = ctypes.POINTER(ctypes.c_double)
+    i, d = ctypes.c_int, ctypes.c_double
+    lib.gfo_lowres_radius.argtypes = [i, i]
+    lib.gfo_lowres_radius.restype = i
+    lib.gfo_lowres_shape.argtypes = [i, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.gfo_lowres_radius_q.argtypes = [i, i, i]
+    lib.gfo_lowres_radius_q.restype = i
+    lib.gfo_lowres_shape_q.argtypes = [i, i, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.gfo_subsample_q.argtypes = [D, i, i, i, i, i, D]
+    lib.gfo_upsample_q.argtypes = [D, i, i, i, i, i, i, D]
+    lib.gfo_fast_guided_filter_q.argtypes = [D, D, i, i, i, i, i, i, d, i, i, i, i, i, D, D, D, D, D, D]
+    lib.gfo_fast_guided_filter_q.restype = i
+    lib.gfo_subsample.argtypes = [D, i, i, i, i, D]
+    for name in ("gfo_box_sum", "gfo_box_mean", "gfo_box_mean_bruteforce"):
+        getattr(lib, name).argtypes = [D, i, i, i, D]
+    lib.gfo_upsample.argtypes = [D, i, i, i, i, i, D]
+    lib.gfo_fast_guided_filter.argtypes = [D, D, i, i, i, i, i, i, d, i, i, i, i, D, D, D, D, D, D]
+    lib.gfo_fast_guided_filter.restype = i
+    lib.gfo_guided_filter.argtypes = [D, D, i, i, i, d, D]
+    lib.gfo_guided_filter.restype = i
+    lib.gfo_fast_guided_filter_backward.argtypes = [D, D, D, i, i, i, i, i, i, d, i, i, i, i, D, D, D]
+    lib.gfo_fast_guided_filter_backward.restype = i
+    lib.gfo_color_guided_filter.argtypes = [D, D, i, i, i, i, i, d, i, i, i, D, D, D]
+    lib.gfo_color_guided_filter.restype = i
+    lib.gfo_detail_enhance.argtypes = [D, D, i, i, i, i, i, d, D]
+    lib.gfo_detail_enhance.restype = i
+    return lib
 
 
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            D = ctypes.POINTER(ctypes.c_double)
-            i, d = ctypes.c_int, ctypes.c_double
-            lib.gfo_lowres_radius.argtypes = [i, i]
-            lib.gfo_lowres_radius.restype = i
-            lib.gfo_lowres_shape.argtypes = [i, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
-            lib.gfo_lowres_radius_q.argtypes = [i, i, i]
-            lib.gfo_lowres_radius_q.restype = i
-            lib.gfo_lowres_shape_q.argtypes = [i, i, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
-            lib.gfo_subsample_q.argtypes = [D, i, i, i, i, i, D]
-            lib.gfo_upsample_q.argtypes = [D, i, i, i, i, i, i, D]
-            lib.gfo_fast_guided_filter_q.argtypes = [D, D, i, i, i, i, i, i, d, i, i, i, i, i, D, D, D, D, D, D]
-            lib.gfo_fast_guided_filter_q.restype = i
-            lib.gfo_subsample.argtypes = [D, i, i, i, i, D]
-            for name in ("gfo_box_sum", "gfo_box_mean", "gfo_box_mean_bruteforce"):
-                getattr(lib, name).argtypes = [D, i, i, i, D]
-            lib.gfo_upsample.argtypes = [D, i, i, i, i, i, D]
-            lib.gfo_fast_guided_filter.argtypes = [D, D, i, i, i, i, i, i, d, i, i, i, i, D, D, D, D, D, D]
-            lib.gfo_fast_guided_filter.restype = i
-            lib.gfo_guided_filter.argtypes = [D, D, i, i, i, d, D]
-            lib.gfo_guided_filter.restype = i
-            lib.gfo_fast_guided_filter_backward.argtypes = [D, D, D, i, i, i, i, i, i, d, i, i, i, i, D, D, D]
-            lib.gfo_fast_guided_filter_backward.restype = i
-            lib.gfo_color_guided_filter.argtypes = [D, D, i, i, i, i, i, d, i, i, i, D, D, D]
-            lib.gfo_color_guided_filter.restype = i
-            lib.gfo_detail_enhance.argtypes = [D, D, i, i, i, i, i, d, D]
-            lib.gfo_detail_enhance.restype = i
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(build()))
     return _lib
+
+
+@contextlib.contextmanager
+def use_library(path):
+    """Run every oracle function from another build of ``gf_oracle.c`` (the shared library at ``path``)
+    while the block runs; the mutation tests use it to run the pins on copies with a planted mistake."""
+    global _lib
+    _load()
+    variant = _bind(ctypes.CDLL(path))
+    with _lock:
+        saved, _lib = _lib, variant
+    try:
+        yield
+    finally:
+        with _lock:
+            _lib = saved
 
 
 def _c64(x):

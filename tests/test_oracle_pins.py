@@ -503,8 +503,10 @@ def _loss(I, p, Wt, r_low, eps, s, mode, p_lowres):
 
 
 @pytest.mark.parametrize("s,mode,CI,p_lowres", [(1, 1, 1, False), (2, 1, 1, False), (2, 0, 3, False),
-                                                (3, 2, 2, False), (2, 2, 2, True)])
+                                                (3, 2, 2, False), (2, 2, 2, True), (3, 1, 1, False)])
 def test_backward_central_differences(s, mode, CI, p_lowres):
+    # (odd s with bilinear subsampling puts every sample on a pixel, weights 1 and 0; even s gives 1/2 and
+    # 1/2, where a swapped weight of the transposed subsample would go unseen)
     rng = _rng(20 + s + mode)
     N, C, H, W, r_low, eps, hstep = 1, 2, 7, 6, 1, 0.05, 1e-3
     CI = 1 if CI == 1 else C
