@@ -48,6 +48,7 @@ BWD_CASES = [
     (1, 3, 3, 96, 136, 2, 1e-2, 8, 1, False),
     (1, 1, 3, 97, 130, 3, 1e-2, 4, 2, False),
     (1, 1, 1, 1, 9, 1, 1e-2, 2, 1, False),
+    (1, 1, 2, 45, 57, 2, 1e-2, 3, 1, False),   # odd s, bilinear: every sample on a pixel (weights 1, 0)
     # vector forms of the full-res kernels (s = 4, 8; H, W multiples of s)
     (1, 1, 2, 64, 96, 2, 1e-2, 4, 0, False),   # nearest
     (2, 1, 3, 48, 64, 1, 1e-2, 8, 2, False),   # box, gray guide, full-res p
