@@ -45,7 +45,7 @@ PINS = [
      _each(pins.test_fgf_matches_torch_restatement, [(2, 0, 1), (4, 1, 1), (4, 2, 3), (4, 3, 1)])),
     ("backward vs central differences",
      _each(pins.test_backward_central_differences,
-           [(2, 1, 1, False), (3, 1, 1, False), (3, 2, 2, False), (2, 0, 3, False)])),
+           [(2, 1, 1, False), (3, 1, 1, False), (3, 2, 2, False), (2, 0, 3, False), (2, 2, 2, True)])),
     ("backward vs float64 autograd", _each(pins.test_backward_matches_torch_autograd, [(4, 1, 1), (2, 0, 3)])),
     ("colour: replicated gray guide equals gray guide with eps / 3",
      _each(pins.test_color_guide_of_replicated_gray_equals_gray_guide_with_eps_over_3, [(2, 0), (4, 1)])),
@@ -124,6 +124,30 @@ MUTATIONS = [
     ("colour guide: covariance matrix filled on one side only (R12)",
      "M[PL[m]][PK[m]] = e;",
      "M[PL[m]][PK[m]] = 0.5 * e;"),
+    ("depthwise guide: every channel guided by guide channel 0 (R8)",
+     "const double *Ig = I + ((size_t)bn * CI + (CI == 1 ? 0 : c)) * NF;\n            /* step 1",
+     "const double *Ig = I + ((size_t)bn * CI + 0) * NF;\n            /* step 1"),
+    ("adjoint: depthwise guide channel 0 for every channel",
+     "const double *Ig = I + ((size_t)bn * CI + (CI == 1 ? 0 : c)) * NF;\n            const double *g = gq",
+     "const double *Ig = I + ((size_t)bn * CI + 0) * NF;\n            const double *g = gq"),
+    ("adjoint: wrong sign of d eps",
+     "eps_acc += dvar;",
+     "eps_acc -= dvar;"),
+    ("adjoint: transposed upsample off by half a row",
+     "axis_taps((Yi + 0.5) / (double)s - 0.5, h, &y0, &y1, &fy);",
+     "axis_taps((Yi + 0.5) / (double)s, h, &y0, &y1, &fy);"),
+    ("adjoint: transposed nearest subsample without the half-pixel offset",
+     "int sy = iclamp((int)floor((j + 0.5) * s), 0, H - 1);",
+     "int sy = iclamp((int)floor(j * (double)s), 0, H - 1);"),
+    ("adjoint: gradient of a low-res p dropped",
+     "memcpy(dpc, dpl, sizeof(double) * n);",
+     "memset(dpc, 0, sizeof(double) * n);"),
+    ("Algorithm 1: summed-area window one column short",
+     "int ia = imax(0, i - r), ib = imin(w - 1, i + r) + 1;",
+     "int ia = imax(0, i - r), ib = imin(w - 1, i + r) + (r > 0 ? 0 : 1);"),
+    ("colour guide: guide products squared instead of crossed (R12)",
+     "for (size_t t = 0; t < n; ++t) tmp[t] = Il[PK[m] * n + t] * Il[PL[m] * n + t];",
+     "for (size_t t = 0; t < n; ++t) tmp[t] = Il[PK[m] * n + t] * Il[PK[m] * n + t];"),
     ("detail epilogue with the detail layer reversed (Fig. 2)",
      "oc[i] = qc[i] + k * (Ic[i] - qc[i]);",
      "oc[i] = qc[i] + k * (qc[i] - Ic[i]);"),
