@@ -13,6 +13,7 @@ oracle's own build is not touched: the copies go to ``oracle/_build/mutants`` an
 import json
 import os
 import zlib
+from fractions import Fraction
 
 import pytest
 
@@ -51,6 +52,11 @@ PINS = [
      _each(pins.test_color_guide_of_replicated_gray_equals_gray_guide_with_eps_over_3, [(2, 0), (4, 1)])),
     ("colour vs the float64 torch restatement", _each(pins.test_color_guide_matches_torch_restatement, [(4, 1)])),
     ("detail epilogue special gains", pins.test_detail_enhance_special_gains),
+    ("non-integer ratios vs torch interpolate",
+     lambda: ([pins.test_rational_subsample_matches_torch_scale_factor(m, s)
+               for m in (0, 1, 3) for s in (Fraction(5, 2), Fraction(7, 4))] +
+              [pins.test_rational_upsample_matches_torch_scale_factor(s) for s in (Fraction(5, 2), Fraction(9, 4))])),
+    ("non-integer ratio hand values", pins.test_rational_ratio_hand_values),
 ]
 
 # (name, text of gf_oracle.c, the same text with the mistake planted)
@@ -148,6 +154,15 @@ MUTATIONS = [
     ("colour guide: guide products squared instead of crossed (R12)",
      "for (size_t t = 0; t < n; ++t) tmp[t] = Il[PK[m] * n + t] * Il[PL[m] * n + t];",
      "for (size_t t = 0; t < n; ++t) tmp[t] = Il[PK[m] * n + t] * Il[PK[m] * n + t];"),
+    ("non-integer ratio: bilinear subsample offset ignoring the denominator (R13)",
+     "axis_taps_q((2LL * i + 1) * sn - sd, 2LL * sd, W, &x0, &x1, &fx);",
+     "axis_taps_q((2LL * i + 1) * sn - 1, 2LL * sd, W, &x0, &x1, &fx);"),
+    ("non-integer ratio: upsample scale with the denominator dropped (R13)",
+     "axis_taps_q((2LL * Y + 1) * sd - sn, 2LL * sn, h, &y0, &y1, &fy);",
+     "axis_taps_q((2LL * Y + 1) - sn / sd, 2LL * (sn / sd), h, &y0, &y1, &fy);"),
+    ("non-integer ratio: low-res width from the integer part of s (R13)",
+     "*w = (int)(((long long)W * sd + sn - 1) / sn);",
+     "*w = (int)(((long long)W + sn / sd - 1) / (sn / sd));"),
     ("detail epilogue with the detail layer reversed (Fig. 2)",
      "oc[i] = qc[i] + k * (Ic[i] - qc[i]);",
      "oc[i] = qc[i] + k * (qc[i] - Ic[i]);"),
