@@ -4,7 +4,8 @@ A call restricted to output rows [row_begin, row_end) filters only the band of i
 gf_row_band reports, as if it were a whole image.  The claim checked here: the oracle run on that band
 alone gives the same output rows as the oracle run on the whole image (to FP64 rounding), for every
 subsample mode, ratio, radius and position of the strip -- so the band keeps every window that
-reaches the strip and none of the band's own cut edges leak into it.
+reaches the strip and none of the band's own cut edges leak into it.  Also checked: the rows of p that
+the host-buffer call uploads for nearest and bilinear subsampling are all the subsample reads.
 """
 import numpy as np
 import pytest
@@ -87,3 +88,27 @@ def test_row_strips_partition():
         assert all(a[1] == b[0] for a, b in zip(strips, strips[1:]))
         assert all(lo <= hi for lo, hi in strips)
         assert all(lo % align == 0 for lo, _ in strips)
+
+
+@pytest.mark.parametrize("mode", [oracle.SUB_NEAREST, oracle.SUB_BILINEAR])
+@pytest.mark.parametrize("s", [3, 4, 5, 8])
+@pytest.mark.parametrize("H", [40, 43])
+def test_host_upload_rows_are_the_rows_the_subsample_reads(mode, s, H):
+    """gf_filter_host uploads, for nearest and bilinear subsampling at s >= 3, only rows s j + o and
+    s j + o + 1 (o = floor((s - 1) / 2)) of each whole s-row block of p, and every row of a partial last
+    block.  With every other row of p set to NaN, the oracle's subsample (R2, R3) must be unchanged: those
+    rows are never read, not even with weight 0."""
+    W = 11
+    p = np.random.default_rng(H * 10 + s).uniform(0, 1, (H, W))
+    o = (s - 1) // 2
+    uploaded = np.zeros(H, bool)
+    for j in range(H // s):
+        uploaded[s * j + o] = uploaded[s * j + o + 1] = True
+    uploaded[(H // s) * s:] = True
+    p_holes = p.copy()
+    p_holes[~uploaded] = np.nan
+    ref = oracle.subsample(p, s, mode)
+    got = oracle.subsample(p_holes, s, mode)
+    assert not np.isnan(got).any()
+    np.testing.assert_array_equal(got, ref)
+    assert uploaded.sum() < H  # the rule does leave rows out
