@@ -112,3 +112,21 @@ def test_host_upload_rows_are_the_rows_the_subsample_reads(mode, s, H):
     assert not np.isnan(got).any()
     np.testing.assert_array_equal(got, ref)
     assert uploaded.sum() < H  # the rule does leave rows out
+
+
+@pytest.mark.parametrize("H,W,s,r,mode", [(3000, 4000, 4, 16, "bilinear"), (3001, 4000, 4, 16, "nearest"),
+                                          (2999, 3000, 8, 60, "bilinear"), (4000, 3000, 3, 9, "box"),
+                                          (2500, 3400, 5, 20, "bilinear_aa")])
+def test_host_strip_bands_are_whole_blocks(H, W, s, r, mode):
+    """The host pipeline uploads each strip's band after the previous strips' bands and starts its sampled
+    rows of p on a block boundary, so every strip's band must start on a multiple of s and end on one (or
+    at H), and the bands must reach every input row a strip reads, in order."""
+    ys = binding.host_strips(H, W, 3, s, mode)
+    assert ys is not None
+    end = 0
+    for a, b in zip(ys, ys[1:]):
+        row0, rows = binding.row_band(H, W, s, r, a, b, mode=mode)
+        assert row0 % s == 0 and ((row0 + rows) % s == 0 or row0 + rows == H)
+        assert row0 <= a and b <= row0 + rows  # the band holds the strip's own rows
+        end = max(end, row0 + rows)
+    assert end == H
