@@ -48,9 +48,12 @@ PINS = [
      _each(pins.test_backward_central_differences,
            [(2, 1, 1, False), (3, 1, 1, False), (3, 2, 2, False), (2, 0, 3, False), (2, 2, 2, True)])),
     ("backward vs float64 autograd", _each(pins.test_backward_matches_torch_autograd, [(4, 1, 1), (2, 0, 3)])),
+    ("backward of a low-res p batch vs float64 autograd", pins.test_backward_lowres_p_batch_matches_torch_autograd),
     ("colour: replicated gray guide equals gray guide with eps / 3",
      _each(pins.test_color_guide_of_replicated_gray_equals_gray_guide_with_eps_over_3, [(2, 0), (4, 1)])),
     ("colour vs the float64 torch restatement", _each(pins.test_color_guide_matches_torch_restatement, [(4, 1)])),
+    ("low-res p vs the float64 torch restatement",
+     lambda: [pins.test_fgf_lowres_p_matches_torch_restatement(), pins.test_color_guide_lowres_p_matches_torch_restatement()]),
     ("detail epilogue special gains", pins.test_detail_enhance_special_gains),
     ("non-integer ratios vs torch interpolate",
      lambda: ([pins.test_rational_subsample_matches_torch_scale_factor(m, s)
@@ -163,6 +166,19 @@ MUTATIONS = [
     ("non-integer ratio: low-res width from the integer part of s (R13)",
      "*w = (int)(((long long)W * sd + sn - 1) / sn);",
      "*w = (int)(((long long)W + sn / sd - 1) / (sn / sd));"),
+    ("low-res p of image 0 for every image of a batch (Alg. 2)",
+     "memcpy(pl, p + ((size_t)bn * C + c) * n, sizeof(double) * n);\n            else\n                gfo_subsample_q(",
+     "memcpy(pl, p + ((size_t)c) * n, sizeof(double) * n);\n            else\n                gfo_subsample_q("),
+    ("adjoint: low-res p of image 0 for every image of a batch",
+     "memcpy(pl, p + ((size_t)bn * C + c) * n, sizeof(double) * n);\n            else\n                "
+     "gfo_subsample(p + ((size_t)bn * C + c) * NF, H, W, s, mode, pl);\n            box_mean_mode",
+     "memcpy(pl, p + ((size_t)c) * n, sizeof(double) * n);\n            else\n                "
+     "gfo_subsample(p + ((size_t)bn * C + c) * NF, H, W, s, mode, pl);\n            box_mean_mode"),
+    ("colour guide: low-res p of image 0 for every image of a batch (R12)",
+     "memcpy(pl, p + ((size_t)bn * C + c) * n, sizeof(double) * n);\n            else\n                "
+     "gfo_subsample(p + ((size_t)bn * C + c) * NF, H, W, s, mode, pl);\n            gfo_box_mean(pl",
+     "memcpy(pl, p + ((size_t)c) * n, sizeof(double) * n);\n            else\n                "
+     "gfo_subsample(p + ((size_t)bn * C + c) * NF, H, W, s, mode, pl);\n            gfo_box_mean(pl"),
     ("detail epilogue with the detail layer reversed (Fig. 2)",
      "oc[i] = qc[i] + k * (Ic[i] - qc[i]);",
      "oc[i] = qc[i] + k * (qc[i] - Ic[i]);"),

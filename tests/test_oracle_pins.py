@@ -451,6 +451,16 @@ def test_color_guide_matches_torch_restatement(s, mode):
     np.testing.assert_allclose(q, ref, rtol=1e-10, atol=1e-11)
 
 
+def test_color_guide_lowres_p_matches_torch_restatement():
+    rng = _rng(47)
+    s, N, C, H, W = 4, 2, 3, 28, 20
+    I = rng.uniform(0, 1, (N, 3, H, W))
+    p = rng.uniform(0, 1, (N, C, H // s, W // s))
+    q = oracle.color_guided_filter(I, p, 0, 1e-2, s, oracle.SUB_BOX, r_low=2, p_lowres=True)
+    ref = tr.color_guided_filter(torch.from_numpy(I), torch.from_numpy(p), 2, 1e-2, s, 2, p_lowres=True).numpy()
+    np.testing.assert_allclose(q, ref, rtol=1e-10, atol=1e-11)
+
+
 def test_color_guide_closed_forms_and_invariances():
     rng = _rng(50)
     I = rng.uniform(0, 1, (1, 3, 24, 32))
@@ -548,6 +558,23 @@ def test_backward_matches_torch_autograd(s, mode, CI):
     tp = torch.tensor(p, requires_grad=True)
     te = torch.tensor(eps, dtype=torch.float64, requires_grad=True)
     (tr.fast_guided_filter(tI, tp, r_low, te, s, mode) * torch.from_numpy(Wt)).sum().backward()
+    np.testing.assert_allclose(dI, tI.grad.numpy(), rtol=1e-10, atol=1e-11)
+    np.testing.assert_allclose(dp, tp.grad.numpy(), rtol=1e-10, atol=1e-11)
+    assert deps == pytest.approx(te.grad.item(), rel=1e-10, abs=1e-11)
+
+
+def test_backward_lowres_p_batch_matches_torch_autograd():
+    """The trainable-layer form: a batch of low-res p (box subsample of the guide, s = 4)."""
+    rng = _rng(35)
+    s, N, C, H, W, r_low, eps = 4, 2, 3, 16, 12, 2, 1e-2
+    I = rng.uniform(0, 1, (N, C, H, W))
+    p = rng.uniform(0, 1, (N, C, H // s, W // s))
+    Wt = rng.uniform(-1, 1, (N, C, H, W))
+    dI, dp, deps = oracle.fast_guided_filter_backward(I, p, Wt, 0, eps, s, oracle.SUB_BOX, r_low=r_low, p_lowres=True)
+    tI = torch.tensor(I, requires_grad=True)
+    tp = torch.tensor(p, requires_grad=True)
+    te = torch.tensor(eps, dtype=torch.float64, requires_grad=True)
+    (tr.fast_guided_filter(tI, tp, r_low, te, s, 2, p_lowres=True) * torch.from_numpy(Wt)).sum().backward()
     np.testing.assert_allclose(dI, tI.grad.numpy(), rtol=1e-10, atol=1e-11)
     np.testing.assert_allclose(dp, tp.grad.numpy(), rtol=1e-10, atol=1e-11)
     assert deps == pytest.approx(te.grad.item(), rel=1e-10, abs=1e-11)
