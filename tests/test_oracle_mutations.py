@@ -179,6 +179,24 @@ MUTATIONS = [
      "gfo_subsample(p + ((size_t)bn * C + c) * NF, H, W, s, mode, pl);\n            gfo_box_mean(pl",
      "memcpy(pl, p + ((size_t)c) * n, sizeof(double) * n);\n            else\n                "
      "gfo_subsample(p + ((size_t)bn * C + c) * NF, H, W, s, mode, pl);\n            gfo_box_mean(pl"),
+    ("box sum one column short (R1)",
+     "for (int ii = imax(0, i - r); ii <= imin(w - 1, i + r); ++ii) acc += x[(size_t)j * w + ii];",
+     "for (int ii = imax(0, i - r); ii < imin(w - 1, i + r); ++ii) acc += x[(size_t)j * w + ii];"),
+    ("antialiased subsample without renormalising the weights (R11)",
+     "v = acc / wsum;",
+     "v = acc;"),
+    ("adjoint: direct term g U(mean_a) of dI dropped",
+     "for (size_t k = 0; k < NF; ++k) dIg[k] += g[k] * up_a[k];",
+     "for (size_t k = 0; k < NF; ++k) dIg[k] += 0.0 * g[k] * up_a[k];"),
+    ("adjoint: p' term of dI' dropped",
+     "dIl[k] += 2.0 * Il[k] * tI[k] + pl[k] * tp[k];",
+     "dIl[k] += 2.0 * Il[k] * tI[k];"),
+    ("colour guide: wrong sign in the 3 x 3 determinant (R12)",
+     "- M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0])",
+     "+ M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0])"),
+    ("detail epilogue: guide channel 0 for every channel (Fig. 2)",
+     "const double *Ic = I + ((size_t)n * CI + (CI == 1 ? 0 : c)) * HW;",
+     "const double *Ic = I + ((size_t)n * CI + 0) * HW;"),
     ("detail epilogue with the detail layer reversed (Fig. 2)",
      "oc[i] = qc[i] + k * (Ic[i] - qc[i]);",
      "oc[i] = qc[i] + k * (qc[i] - Ic[i]);"),
