@@ -34,6 +34,9 @@ def _each(fn, cases):
 PINS = [
     ("hand examples (Eq. 2-4)", lambda: [pins.test_hand_examples(ex) for ex in EXAMPLES]),
     ("box mean vs avg_pool2d", _each(pins.test_box_mean_matches_avg_pool, [((7, 11), 2), ((5, 5), 7), ((1, 13), 3)])),
+    ("separable box mean vs brute-force windows", _each(pins.test_box_mean_matches_bruteforce, [(0,), (1,)])),
+    ("brute-force and separable back ends agree",
+     lambda: [pins.test_brute_and_separable_box_backends_agree(), pins.test_backward_brute_and_separable_agree()]),
     ("subsample vs torch interpolate / avg_pool2d",
      _each(pins.test_subsample_matches_torch_divisible, [(m, s) for m in range(4) for s in (2, 3, 4)])),
     ("ragged box subsample vs avg_pool2d", _each(pins.test_box_subsample_ragged_matches_avg_pool, [(10, 13, 4), (7, 9, 3)])),
@@ -197,6 +200,24 @@ MUTATIONS = [
     ("detail epilogue: guide channel 0 for every channel (Fig. 2)",
      "const double *Ic = I + ((size_t)n * CI + (CI == 1 ? 0 : c)) * HW;",
      "const double *Ic = I + ((size_t)n * CI + 0) * HW;"),
+    ("window count unclipped along the rows (R1)",
+     "int nx = imin(w - 1, i + r) - imax(0, i - r) + 1;",
+     "int nx = 2 * r + 1;"),
+    ("brute-force box mean divided by the full window (R1)",
+     "y[(size_t)j * w + i] = acc / (double)n;",
+     "y[(size_t)j * w + i] = acc / (double)((2 * r + 1) * (2 * r + 1));"),
+    ("r' not raised to 1 for small r (R6)",
+     "if (r >= 1 && rl < 1) rl = 1;",
+     "if (r >= 1 && rl < 0) rl = 1;"),
+    ("adjoint: eps left out of the derivative of a",
+     "double inv = 1.0 / (var[k] + eps);",
+     "double inv = 1.0 / (var[k] + 0.5 * eps);"),
+    ("adjoint: brute-force transposed box mean without the window counts",
+     "double v = y[(size_t)j * w + i] / window_count(j, i, h, w, r);",
+     "double v = y[(size_t)j * w + i];"),
+    ("colour guide: box means of a skipped (R12)",
+     "for (int k = 0; k < 3; ++k) gfo_box_mean(a + k * n, h, w, r_low, mean_a + k * n);",
+     "for (int k = 0; k < 3; ++k) memcpy(mean_a + k * n, a + k * n, sizeof(double) * n);"),
     ("detail epilogue with the detail layer reversed (Fig. 2)",
      "oc[i] = qc[i] + k * (Ic[i] - qc[i]);",
      "oc[i] = qc[i] + k * (qc[i] - Ic[i]);"),
