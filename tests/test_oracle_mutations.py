@@ -218,6 +218,21 @@ MUTATIONS = [
     ("colour guide: box means of a skipped (R12)",
      "for (int k = 0; k < 3; ++k) gfo_box_mean(a + k * n, h, w, r_low, mean_a + k * n);",
      "for (int k = 0; k < 3; ++k) memcpy(mean_a + k * n, a + k * n, sizeof(double) * n);"),
+    ("antialiased subsample over too narrow a span of source pixels (R11)",
+     "int span = 3 * ((sn + sd - 1) / sd) + 3;",
+     "int span = (sn + sd - 1) / sd;"),
+    ("Algorithm 1: wrong sign of b",
+     "b[k] = mp[k] - a[k] * mI[k];",
+     "b[k] = mp[k] + a[k] * mI[k];"),
+    ("adjoint: d a missing the path through b",
+     "double da_k = da[k] - mean_I[k] * db[k];",
+     "double da_k = da[k];"),
+    ("adjoint: d mean_p missing the path through cov",
+     "dmp_k += -mean_I[k] * dcov;",
+     "dmp_k += 0.0 * dcov;"),
+    ("adjoint: transposed box subsample dividing ragged blocks by s^2",
+     "double v = g / (double)((yb - ya) * (xb - xa));",
+     "double v = g / (double)(s * s);"),
     ("detail epilogue with the detail layer reversed (Fig. 2)",
      "oc[i] = qc[i] + k * (Ic[i] - qc[i]);",
      "oc[i] = qc[i] + k * (qc[i] - Ic[i]);"),
