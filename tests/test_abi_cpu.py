@@ -160,3 +160,53 @@ def test_size_limits(lib):
     assert ws(8, 8, 3, 4, batch=16384) == binding.GF_EINVAL  # 65536 planes
     assert ws(64, 64, 1, 4, r_low=128) == binding.GF_OK
     assert ws(64, 64, 1, 4, r_low=129) == binding.GF_EINVAL
+
+
+# Each documented argument rule of gf_opts (include/gf.h), broken once: (H, W, C, s, mode, opts fields, part of
+# the message).  gf_filter_kernel_count resolves the arguments exactly as gf_filter does, host-only.
+ARGUMENT_RULES = [
+    (64, 64, 1, 4, "bilinear", {"batch": 0}, b"batch"),
+    (64, 64, 1, 4, "bilinear", {"dtype_in": 7}, b"dtype_in"),
+    (64, 64, 1, 4, "bilinear", {"dtype_out": 2}, b"dtype_out"),
+    (64, 64, 3, 4, "bilinear", {"color_guide": 1, "guide_channels": 1}, b"guide_channels = 3"),
+    (64, 64, 3, 4, "bilinear", {"color_guide": 1, "guide_channels": 3, "dtype_in": 2}, b"colour guide"),
+    (64, 64, 1, 4, "bilinear", {"color_guide": 1, "guide_channels": 3, "detail_gain": 2.0}, b"C = 3"),
+    (64, 64, 1, 4, "bilinear", {"detail_gain": float("inf")}, b"detail_gain"),
+    (64, 64, 1, 4, "bilinear", {"s_num": 2, "s_den": 5}, b"ratio"),
+    (64, 64, 1, 4, "box", {"s_num": 5, "s_den": 2}, b"box"),
+    (64, 64, 1, 4, "bilinear", {"s_num": 5, "s_den": 2, "dtype_in": 2}, b"uint8"),
+    (64, 64, 1, 4, "bilinear", {"s_num": 5, "s_den": 2, "row_begin": 0, "row_end": 8}, b"row range"),
+    (64, 64, 1, 4, "box", {"dtype_in": 2}, b"uint8"),
+    (64, 64, 1, 4, "bilinear_aa", {"dtype_in": 2}, b"uint8"),
+    (64, 64, 1, 4, "bilinear", {"dtype_in": 2, "p_lowres": 1}, b"uint8"),
+    (64, 64, 1, 4, "bilinear", {"row_begin": 10, "row_end": 10}, b"row range"),
+    (64, 64, 1, 4, "bilinear", {"row_begin": 0, "row_end": 65}, b"row range"),
+    (64, 64, 1, 4, "bilinear", {"r_low": 129}, b"r' > 128"),
+]
+
+
+@pytest.mark.parametrize("H,W,C,s,mode,fields,msg", ARGUMENT_RULES,
+                         ids=["-".join("%s=%s" % kv for kv in r[5].items()) + "-" + r[4] for r in ARGUMENT_RULES])
+def test_documented_argument_rules(lib, H, W, C, s, mode, fields, msg):
+    from paper_1505_00996_gb300 import binding
+    o = binding.opts_init()
+    for k, v in fields.items():
+        setattr(o, k, v)
+    assert lib.gf_filter_kernel_count(H, W, C, s, binding.MODES[mode], ctypes.byref(o)) == -1
+    assert msg in lib.gf_last_error(), lib.gf_last_error()
+    # the same arguments without the broken rule resolve
+    assert lib.gf_filter_kernel_count(H, W, C, s, binding.MODES[mode], ctypes.byref(binding.opts_init())) > 0
+
+
+def test_intermediate_outputs_exclude_row_ranges_and_colour(lib):
+    from paper_1505_00996_gb300 import binding
+    buf = (ctypes.c_float * 16)()
+    o = binding.opts_init()
+    o.a_out = ctypes.addressof(buf)  # host memory: only the host-side argument check runs
+    o.row_begin, o.row_end = 0, 8
+    assert lib.gf_filter_kernel_count(64, 64, 1, 4, binding.GF_SUB_BILINEAR, ctypes.byref(o)) == -1
+    assert b"row range" in lib.gf_last_error()
+    o.row_begin = o.row_end = 0
+    o.color_guide, o.guide_channels = 1, 3
+    assert lib.gf_filter_kernel_count(64, 64, 3, 4, binding.GF_SUB_BILINEAR, ctypes.byref(o)) == -1
+    assert b"intermediates" in lib.gf_last_error()
