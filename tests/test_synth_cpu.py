@@ -1,6 +1,8 @@
-"""The seeded input generators (``synth``) against the recipes the design record states for the paper's
-workloads (CPU).  They hold none of the method's arithmetic; these checks make sure that the inputs every
-parity test and benchmark uses have the stated shapes, value ranges, structure and determinism."""
+"""The seeded input generators (``synth``) against the recipes their docstrings give for the stand-ins of the
+paper's workloads (CPU): gradient scenes with flat rectangles and N(0, 0.05^2) noise on [0, 1], noisy
+per-channel inputs, blocky feathering masks, uint8 / FP16 storage, the trainable-layer batch and the
+serving request stream.  They hold none of the method's arithmetic; these checks make sure that the
+inputs every parity test and benchmark uses have those shapes, value ranges, structure and determinism."""
 import numpy as np
 import pytest
 
