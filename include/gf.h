@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define GF_ABI_VERSION 3
+#define GF_ABI_VERSION 4
 #define GF_MAX_STAGES 8 /* kernel stages one gf_filter call can launch (for gf_opts.kernel_events) */
 #define GF_FUSED_AUTO_PIXELS (1 << 20) /* gf_opts.fused = 0 runs the single kernel up to N*C*H*W pixels */
 
@@ -50,7 +50,9 @@ typedef enum gf_status {
     GF_ETIMEOUT = -4,   /* gf_poll: not finished within the timeout */
     GF_EBUSY = -5,      /* the serving queue is full */
     GF_ECANCELED = -6,  /* the request was cancelled */
-    GF_ENOTFOUND = -7   /* unknown ticket */
+    GF_ENOTFOUND = -7,  /* unknown ticket */
+    GF_EWAIT = -8       /* a bounded wait inside a kernel gave up (its data never arrived): the output of
+                           the call or request is incomplete */
 } gf_status;
 
 typedef enum gf_subsample_mode {
@@ -123,6 +125,10 @@ typedef struct gf_ctx gf_ctx;
  *                   a = (Sigma + eps U)^-1 cov_Ip with Sigma the 3 x 3 covariance of I', b = mean_p - a^T
  *                   mean_I, and q = mean_a^T I + mean_b.  FP32 or FP16 storage; forward only; no low-res
  *                   intermediate outputs; detail_gain needs C = 3 (channel c's detail is I_c - q_c).
+ *   test_wait_fault nonzero (tests of the timeout path only): the TMA-fed output kernel leaves the first
+ *                   stage of its ring unfilled and every bounded wait of the call gives up after 256 polls,
+ *                   so the consumers' first wait runs out; the kernel records GF_EWAIT in the call's fault
+ *                   word and returns with q incomplete.  No GPU fault is made.
  */
 typedef struct gf_opts {
     int batch;
@@ -147,6 +153,7 @@ typedef struct gf_opts {
     int s_den;
     int fused;
     int saved_forward;
+    int test_wait_fault;
 } gf_opts;
 
 /* Default options: batch 1, gray guide, derived r', full-res p, FP32 in and out, nothing optional. */

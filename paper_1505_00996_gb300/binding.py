@@ -13,8 +13,8 @@ import torch
 
 from . import _build
 
-GF_OK, GF_PENDING, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_ETIMEOUT, GF_EBUSY, GF_ECANCELED, GF_ENOTFOUND = \
-    0, 1, -1, -2, -3, -4, -5, -6, -7
+GF_OK, GF_PENDING, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_ETIMEOUT, GF_EBUSY, GF_ECANCELED, GF_ENOTFOUND, GF_EWAIT = \
+    0, 1, -1, -2, -3, -4, -5, -6, -7, -8
 GF_SUB_NEAREST, GF_SUB_BILINEAR, GF_SUB_BOX, GF_SUB_BILINEAR_AA = 0, 1, 2, 3
 GF_F32, GF_F16, GF_U8 = 0, 1, 2
 GF_MAX_STAGES = 8
@@ -23,7 +23,7 @@ MODES = {"nearest": GF_SUB_NEAREST, "bilinear": GF_SUB_BILINEAR, "box": GF_SUB_B
          "bilinear_aa": GF_SUB_BILINEAR_AA}
 _DTYPES = {torch.float32: GF_F32, torch.float16: GF_F16, torch.uint8: GF_U8}
 _STATUS_NAMES = {0: "GF_OK", 1: "GF_PENDING", -1: "GF_EINVAL", -2: "GF_ENOMEM", -3: "GF_ECUDA",
-                 -4: "GF_ETIMEOUT", -5: "GF_EBUSY", -6: "GF_ECANCELED", -7: "GF_ENOTFOUND"}
+                 -4: "GF_ETIMEOUT", -5: "GF_EBUSY", -6: "GF_ECANCELED", -7: "GF_ENOTFOUND", -8: "GF_EWAIT"}
 
 
 class GFError(RuntimeError):
@@ -32,7 +32,7 @@ class GFError(RuntimeError):
         self.status = status
 
 
-ABI_VERSION = 3  # GF_ABI_VERSION of include/gf.h that GFOpts mirrors
+ABI_VERSION = 4  # GF_ABI_VERSION of include/gf.h that GFOpts mirrors
 
 
 class GFOpts(ctypes.Structure):
@@ -59,6 +59,7 @@ class GFOpts(ctypes.Structure):
         ("s_den", ctypes.c_int),
         ("fused", ctypes.c_int),
         ("saved_forward", ctypes.c_int),
+        ("test_wait_fault", ctypes.c_int),
     ]
 
 

@@ -155,6 +155,7 @@ gf_status resolve(int H, int W, int C, int r, float eps, int s, int mode, const 
     R.detail = o->detail_gain;
     R.dt_in = o->dtype_in;
     R.dt_out = o->dtype_out;
+    R.saved_forward = o->saved_forward != 0;
     R.p_lowres = o->p_lowres != 0;
     R.int_stats = (o->dtype_in == GF_U8);
     R.int_scale = 255.0f;
@@ -247,7 +248,21 @@ FwdPlan make_plan(const Resolved &R, const Layout &L, const void *I, const void 
     P.events = (opts && opts->kernel_events) ? (cudaEvent_t *)opts->kernel_events : nullptr;
     P.detail = R.detail;
     P.fused = R.fused;
+    P.lowres_out = R.dense_lowres;
+    P.fault = call_fault_sink(ws, L, opts);
     return P;
+}
+
+FaultSink call_fault_sink(char *ws, const Layout &L, const gf_opts *opts)
+{
+    FaultSink f;
+    f.call = (unsigned *)(ws + L.off_fault);
+    f.sticky = sticky_fault_word();
+    if (opts && opts->test_wait_fault) {
+        f.limit = 256;
+        f.inject = 1;
+    }
+    return f;
 }
 
 Layout layout_of(const Resolved &R, const gf_opts *o)
@@ -267,6 +282,7 @@ Layout layout_of(const Resolved &R, const gf_opts *o)
     L.off_mb = take((o && o->mean_b_out) || !gray ? 0 : nc);
     for (int k = 0; k < 8; ++k)  // colour guide: 4 arrays of 5 + 2C planes per image, then 4 of 2C
         L.off_col[k] = take(R.color ? (size_t)R.N * (k < 4 ? 5 + 2 * R.C : 2 * R.C) * pb : 0);
+    L.off_fault = take(sizeof(unsigned));  // the call's fault word
     L.total = off;
     return L;
 }

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "../../include/gf.h"
+#include "gf_internal.cuh"
 
 namespace gfk {
 
@@ -49,6 +50,60 @@ __device__ __forceinline__ void ld_async_small(void *smem_dst, const T *gmem_src
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// ------------------------------------------------------------------------------------------------------
+// mbarrier and TMA (cp.async.bulk.tensor) helpers.  Every wait is bounded: after FaultSink::limit failed
+// polls the waiting thread ORs `bit` into the call's fault word (and the device's sticky word) and gives
+// up, so a kernel whose data never arrives returns instead of hanging.
+// ------------------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ void report_fault(const FaultSink &f, unsigned bit)
+{
+    if (f.call) atomicOr(f.call, bit);
+    if (f.sticky) atomicOr(f.sticky, bit);
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false (and the fault reported) when it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, const FaultSink &f, unsigned bit)
+{
+    for (unsigned it = 0; it < f.limit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    report_fault(f, bit);
+    return false;
+}
+// One 3-D tiled TMA load (box at element coordinates x, y, z; x * element size a multiple of 16 bytes)
+// into shared memory, completing on `bar` with its byte count.
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int x, int y, int z, unsigned bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
 
 // Upsampling taps along one axis at ratio s = sn / sd: full-res index X samples position
 // (X + 1/2)/s - 1/2 = ((2X + 1) sd - sn)/(2 sn), clamped to [0, n-1].  Integer arithmetic keeps the taps exact.

@@ -51,11 +51,20 @@ struct SubParams {
     SubJob job[2];
     int h, w, mode;
     float scale;  // result multiplier: k on the uint8 path (exact integers J = k * value), else 1
+    unsigned *clear_word;  // the call's fault word, zeroed by the first thread (the chain's first kernel)
 };
+
+// The first thread of the chain's first kernel zeroes the call's fault word; the kernels after it, which
+// may report into it, start only once this kernel has finished.
+__device__ __forceinline__ void clear_call_fault(unsigned *word)
+{
+    if (word && (blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x) == 0) *word = 0u;
+}
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(SUB_NT) k_subsample(SubParams P)
 {
+    clear_call_fault(P.clear_word);
     const int i = blockIdx.x * SUB_NT + threadIdx.x;
     const int j0 = blockIdx.y * SUB_JB;
     if (i >= P.w) return;
@@ -83,6 +92,7 @@ __global__ void __launch_bounds__(SUB_NT) k_subsample(SubParams P)
 template <typename T>
 __global__ void __launch_bounds__(SUB_NT) k_subsample_aa(SubParams P)
 {
+    clear_call_fault(P.clear_word);
     const int i = blockIdx.x * SUB_NT + threadIdx.x;
     const int j0 = blockIdx.y * SUB_JB;
     if (i >= P.w) return;
@@ -153,6 +163,7 @@ __device__ __forceinline__ void ld_chunk(const float *p, float (&v)[S])
 template <int MODE, int S>
 __global__ void __launch_bounds__(SUB_NT) k_subsample_wide(SubParams P)
 {
+    clear_call_fault(P.clear_word);
     const int i = blockIdx.x * SUB_NT + threadIdx.x;
     const int j0 = blockIdx.y * SUB_JB;
     if (i >= P.w) return;
@@ -277,6 +288,7 @@ __device__ __forceinline__ float2 ld_block_pair(const T *rp)
 template <typename T, int MODE, int S>
 __global__ void __launch_bounds__(SUB_NT_VEC) k_subsample_vec(SubParams P)
 {
+    clear_call_fault(P.clear_word);
     constexpr int JB = (S == 8) ? 1 : 2;  // low-res rows per thread: short threads, many of them (measured best)
     const int i = blockIdx.x * SUB_NT_VEC + threadIdx.x;
     const int j0 = blockIdx.y * JB;
@@ -793,6 +805,7 @@ struct UpParams {
     int sn, sd;                       // the ratio as sn / sd (generic kernel; s = sn, sd = 1 if integer)
     size_t fps;                       // plane stride of the full-res I and q (elements)
     int Yw0, Yw1;                     // rows written: [Yw0, Yw1) of the H rows
+    FaultSink fault;                  // the TMA-fed form's bounded waits
 };
 
 template <typename T>
@@ -1257,7 +1270,7 @@ void launch_up_t(UpParams up, int N, int CC, bool vec, cudaStream_t st)
         constexpr int DT_OUT = sizeof(TQ) == 4 ? F32 : F16;
         if (output_tma_ok(up.I, DT_IN, up.W, up.fps) &&
             launch_output_tma(up.I, up.ma, up.mb, up.q, N, up.C, up.CI, up.H, up.W, up.h, up.w, up.s, up.lps, up.fps,
-                              up.Yw0, up.Yw1, up.detail, DT_IN, DT_OUT, st) == cudaSuccess)
+                              up.Yw0, up.Yw1, up.detail, DT_IN, DT_OUT, up.fault, st) == cudaSuccess)
             return;
         up.R = 8 * up.s;  // 8 low-res rows per CTA
         up.LRmax = up.R / up.s + 2;
@@ -1307,7 +1320,27 @@ bool aligned_vec_subsample(const FwdPlan &P)
 
 }  // namespace
 
-int forward_kernel_count(const Resolved &R) { return R.fused ? 1 : (R.color ? 6 : 3 + (R.s > 1 ? 1 : 0)); }
+// Where the TMA-fed box kernels (gf_box.cu) are taken when they accept the planes: at full resolution (s = 1) and
+// at r' > 8.  Measured on one GB300: at s = 1 (12 MP, r = 16) the whole call takes 0.47 ms against 0.90 ms with the
+// per-thread-load kernels, and the feathering figure's r' = 15 (12 MP, s = 4) 38 us against 47 us; at r' <= 8 on
+// low-res planes, which stay in L2, the per-thread-load kernels overlap better with the other stream's HBM-bound
+// kernels (12 MP, s = 4, two images in flight: 177 k against 169 k MP/s) and serve small requests faster.
+static bool box_tma_pays(int s, int r_low) { return s == 1 || r_low > 8; }
+
+bool s1_means_output_form(const Resolved &R)
+{
+    return R.s == 1 && R.sd == 1 && !R.color && !R.fused && !R.dense_lowres && !R.p_lowres && !R.saved_forward &&
+           R.dt_in == F32 &&
+           (R.dt_out == F32 || R.dt_out == F16) && R.W % 4 == 0 && R.r_low <= 16;
+}
+
+int forward_kernel_count(const Resolved &R)
+{
+    if (R.fused) return 1;
+    if (R.color) return 6;
+    if (R.s > 1) return 4;
+    return s1_means_output_form(R) ? 2 : 3;
+}
 
 namespace {
 
@@ -1320,6 +1353,15 @@ cudaError_t launch_color_chain(const FwdPlan &P0, float *pl, StageTimer &tm, cud
     cudaError_t err;
     const int K = 5 + 2 * P.C;
     auto box_pairs = [&](float *X, float *Y, float *oX, float *oY, int per_image) {
+        BoxTmaJob J{};
+        J.kind = BOX_JOB_MEANS;
+        J.X = X; J.Y = Y;
+        J.xps = J.yps = J.ops = P.lps;
+        J.N = P.N; J.C = J.CX = per_image;
+        J.h = P.h; J.w = P.w; J.r = P.r_low;
+        J.out0 = oX; J.out1 = oY;
+        J.fault = P.fault;
+        if (box_tma_pays(P.s, P.r_low) && box_tma_supported(J)) return launch_box_tma(J, st);
         BoxParams bp{};
         bp.X = X; bp.Y = Y;
         bp.xps = bp.yps = bp.ops = P.lps;
@@ -1356,7 +1398,13 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
 {
     StageTimer tm{P.events, st};
     cudaError_t err;
-    if (P.fused && !P.skip_output && !P.need_lowres) {  // the whole filter in one kernel
+    // The call's fault word starts at zero (kernels whose bounded waits give up OR their bit into it): the
+    // first kernel of the chain zeroes it (the single fused kernel, or the subsample), else a memset does.
+    const bool fused_call = P.fused && !P.skip_output && !P.need_lowres;
+    if (P.fault.call && !fused_call && !(P.s > 1 || P.color) &&
+        (err = cudaMemsetAsync(P.fault.call, 0, sizeof(unsigned), st)) != cudaSuccess)
+        return err;
+    if (fused_call) {  // the whole filter in one kernel
         tm.before();
         err = launch_fused(P, st);
         tm.after();
@@ -1375,6 +1423,7 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         sp.h = P.h; sp.w = P.w; sp.mode = P.mode;
         // uint8 path: carry the subsampled values as exact integers J = k * (value in 1/255 units)
         sp.scale = P.int_stats ? P.int_scale / 255.0f : 1.0f;
+        sp.clear_word = P.fault.call;
         sp.job[0] = SubJob{P.I, P.Il, P.N * P.CI, P.H, P.W, P.s, P.fps, P.lps, P.sn, P.sd};
         if (!P.p_lowres)
             sp.job[1] = SubJob{P.p, P.pl, planesNC, P.H, P.W, P.s, P.fps, P.lps, P.sn, P.sd};
@@ -1436,8 +1485,20 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         bp.stats = P.stats;
         bp.h = P.h; bp.w = P.w; bp.r = P.r_low; bp.eps = P.eps;
         bp.int_scale = P.int_scale;
+        BoxTmaJob J{};
+        J.kind = BOX_JOB_STATS;
+        J.X = (const float *)Xsrc; J.Y = (const float *)Ysrc;
+        J.xps = bp.xps; J.yps = bp.yps;
+        J.N = P.N; J.C = P.C; J.CX = P.CI;
+        J.h = P.h; J.w = P.w; J.r = P.r_low; J.eps = P.eps;
+        J.out0 = P.a; J.out1 = P.b; J.ops = P.lps;
+        J.fault = P.fault;
+        const bool tma = !P.int_stats && !P.stats && src_dt == F32 && box_tma_pays(P.s, P.r_low) &&
+                         box_tma_supported(J);
         tm.before();
-        if (P.int_stats) {
+        if (tma) {
+            err = launch_box_tma(J, st);
+        } else if (P.int_stats) {
             if (src_dt == F32) err = launch_box_t<float, KIND_STATS_INT>(bp, planesNC, st);
             else err = launch_box_t<uint8_t, KIND_STATS_INT>(bp, planesNC, st);
         } else {
@@ -1448,16 +1509,48 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         if (err != cudaSuccess) return err;
     }
 
+    // ---- s = 1: the upsample is the identity, so the box means of a and b and the output are one kernel
+    if (P.s == 1 && !P.skip_output && !P.need_lowres && !P.lowres_out && !P.color && P.dt_in == F32 &&
+        (P.dt_out == F32 || P.dt_out == F16)) {
+        BoxTmaJob J{};
+        J.kind = BOX_JOB_MEANS_OUTPUT;
+        J.X = P.a; J.Y = P.b;
+        J.xps = J.yps = P.lps;
+        J.N = P.N; J.C = J.CX = P.C;
+        J.h = P.h; J.w = P.w; J.r = P.r_low;
+        J.I = (const float *)P.I; J.q = P.q; J.fps = P.fps; J.CI = P.CI;
+        J.Yw0 = P.Yw0; J.Yw1 = P.Yw1; J.dt_out = P.dt_out; J.detail = P.detail;
+        J.fault = P.fault;
+        if (box_tma_supported(J)) {
+            tm.before();
+            err = launch_box_tma(J, st);
+            tm.after();
+            return err;
+        }
+    }
+
     // ---- Algorithm 2, box means of a and b
     {
-        BoxParams bp{};
-        bp.X = P.a; bp.Y = P.b;
-        bp.xps = P.lps; bp.yps = P.lps;
-        bp.CX = P.C; bp.C = P.C;
-        bp.out0 = P.ma; bp.out1 = P.mb; bp.ops = P.lps;
-        bp.h = P.h; bp.w = P.w; bp.r = P.r_low;
+        BoxTmaJob J{};
+        J.kind = BOX_JOB_MEANS;
+        J.X = P.a; J.Y = P.b;
+        J.xps = J.yps = J.ops = P.lps;
+        J.N = P.N; J.C = J.CX = P.C;
+        J.h = P.h; J.w = P.w; J.r = P.r_low;
+        J.out0 = P.ma; J.out1 = P.mb;
+        J.fault = P.fault;
         tm.before();
-        err = launch_box_t<float, KIND_MEAN2>(bp, planesNC, st);
+        if (box_tma_pays(P.s, P.r_low) && box_tma_supported(J)) {
+            err = launch_box_tma(J, st);
+        } else {
+            BoxParams bp{};
+            bp.X = P.a; bp.Y = P.b;
+            bp.xps = P.lps; bp.yps = P.lps;
+            bp.CX = P.C; bp.C = P.C;
+            bp.out0 = P.ma; bp.out1 = P.mb; bp.ops = P.lps;
+            bp.h = P.h; bp.w = P.w; bp.r = P.r_low;
+            err = launch_box_t<float, KIND_MEAN2>(bp, planesNC, st);
+        }
         tm.after();
         if (err != cudaSuccess) return err;
     }
@@ -1467,6 +1560,7 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
     // ---- Algorithm 2, bilinear upsample of mean_a, mean_b fused with q = mean_a .* I + mean_b
     {
         UpParams up{};
+        up.fault = P.fault;
         up.I = P.I; up.ma = P.ma; up.mb = P.mb; up.q = P.q;
         up.detail = P.detail;
         up.sn = P.sn;

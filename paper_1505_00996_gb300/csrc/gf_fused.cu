@@ -35,6 +35,7 @@ struct FusedParams {
     bool p_lowres;
     int TH, TW;        // full-res tile
     int Yw0, Yw1;      // rows written
+    unsigned *clear_word;  // the call's fault word: zeroed by the first thread (this is the call's only kernel)
 };
 
 template <typename TI, typename TQ, int MODE>
@@ -42,6 +43,7 @@ __global__ void __launch_bounds__(FU_NT) k_fgf_fused(FusedParams P)
 {
     extern __shared__ float sm[];
     const int tid = threadIdx.x;
+    if (P.clear_word && (blockIdx.x | blockIdx.y | blockIdx.z | tid) == 0) *P.clear_word = 0u;
     const int n = blockIdx.z / P.C, c = blockIdx.z - n * P.C;
     const int X0 = blockIdx.x * P.TW, X1 = min(X0 + P.TW, P.W);  // columns [X0, X1)
     const int Ya = max((int)blockIdx.y * P.TH, P.Yw0), Yb = min(min((int)blockIdx.y * P.TH + P.TH, P.H), P.Yw1);
@@ -236,6 +238,7 @@ cudaError_t launch_fused(const FwdPlan &P, cudaStream_t st)
     F.fps = P.fps; F.lpin = P.lpin; F.p_lowres = P.p_lowres;
     F.TH = S.TH; F.TW = S.TW;
     F.Yw0 = P.Yw0; F.Yw1 = P.Yw1;
+    F.clear_word = P.fault.call;
     dim3 grid((P.W + S.TW - 1) / S.TW, (P.H + S.TH - 1) / S.TH, P.N * P.C);
     cudaError_t e;
 #define GF_FU(TI, TQ, M)                                                                     \

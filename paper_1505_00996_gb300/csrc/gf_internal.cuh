@@ -2,6 +2,7 @@
 // Nothing here is part of the public ABI (include/gf.h is).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -36,6 +37,21 @@ struct NvtxRange {
     }
     NvtxRange(const NvtxRange &) = delete;
     NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+// Fault bits of the kernels with bounded waits (FaultSink).
+enum : unsigned { FAULT_OUTPUT_TMA = 1u, FAULT_BOX_TMA = 2u };
+
+// Where a kernel with bounded waits reports a wait that gave up: the fault word of its call (in the call's
+// scratch, cleared when the call starts) and the device's sticky word (gf_kernel_faults).  Either may be
+// NULL.  `limit` is the number of polls before a wait gives up.  `inject` (tests of the timeout path only,
+// gf_opts.test_wait_fault) makes the TMA output kernel's producer leave its first stage unfilled, so that
+// its consumers' first wait runs out.
+struct FaultSink {
+    unsigned *call = nullptr;
+    unsigned *sticky = nullptr;
+    unsigned limit = 1u << 20;
+    unsigned inject = 0;
 };
 
 // Element type of an input plane.
@@ -78,6 +94,8 @@ struct FwdPlan {
     size_t fps = 0;      // plane stride (elements) of the full-res I, p and q (H * W of the whole image)
     size_t lpin = 0;     // plane stride of a low-res p given by the caller (h * w of the whole image)
     int Yw0 = 0, Yw1 = 0;  // output rows written, [Yw0, Yw1) of the H rows the plan covers
+    bool lowres_out = false;   // a, b, mean_a or mean_b are caller outputs (no fusion may skip them)
+    FaultSink fault;           // where kernels with bounded waits report a wait that gave up
     bool skip_output = false;  // stop after the low-res stages (the backward's forward recomputation)
     bool need_lowres = false;  // keep I', p' in the workspace (no fused subsample); the backward reads them
 };
@@ -119,6 +137,7 @@ struct Resolved {
     float detail;  // detail gain (gf_opts.detail_gain)
     bool color;    // colour guide (gf_opts.color_guide)
     bool fused;    // one fused kernel (gf_opts.fused, resolved)
+    bool saved_forward;  // gf_opts.saved_forward: the low-res planes stay in the backward's workspace
     size_t lps;  // low-res plane stride in floats
     // Row band (gf_opts.row_begin / row_end): H and h above are those of the band of complete s-row blocks
     // that is filtered; it starts at full-res row row0 of the whole image, and the output rows written are
@@ -132,7 +151,7 @@ gf_status resolve(int H, int W, int C, int r, float eps, int s, int mode, const 
 
 // Byte offsets of a forward call's low-res planes in its scratch.
 struct Layout {
-    size_t off_Il, off_pl, off_a, off_b, off_ma, off_mb, total;
+    size_t off_Il, off_pl, off_a, off_b, off_ma, off_mb, off_fault, total;
     size_t off_col[8];  // colour-guide planes (FwdPlan::col)
 };
 Layout layout_of(const Resolved &R, const gf_opts *o);
@@ -150,14 +169,51 @@ cudaError_t opt_in_smem(F *func, size_t smem) { return opt_in_smem(reinterpret_c
 
 // Kernels one forward call launches for these arguments (host-side, assuming 16-byte aligned buffers).
 int forward_kernel_count(const Resolved &R);
+// Whether an s = 1 call takes the box means of a and b fused with the output (the identity upsample lets
+// each output pixel use its own means): FP32 input, FP32 or FP16 output, rows a multiple of 4 pixels, a
+// radius the TMA box kernels take, no low-res outputs.  Alignment and TMA availability are checked at launch.
+bool s1_means_output_form(const Resolved &R);
+// Fault word of a forward call: ws + off_fault, plus the device's sticky word; the test hook of
+// gf_opts.test_wait_fault.
+FaultSink call_fault_sink(char *ws, const Layout &L, const gf_opts *opts);
 
 // The TMA-fed s = 4, 8 output kernel (gf_tma.cu): whether it takes these buffers, its launch, and the
 // bounded-wait fault bits its kernels record.
 bool output_tma_ok(const void *I, int dt_in, int W, size_t fps);
 cudaError_t launch_output_tma(const void *I, const float *ma, const float *mb, void *q, int N, int C, int CI, int H,
                               int W, int h, int w, int s, size_t lps, size_t fps, int Yw0, int Yw1, float detail,
-                              int dt_in, int dt_out, cudaStream_t st);
+                              int dt_in, int dt_out, const FaultSink &fault, cudaStream_t st);
 cudaError_t read_kernel_faults(unsigned *flags, bool clear);
+// Device address of the current device's sticky fault word (NULL if it cannot be had).
+unsigned *sticky_fault_word();
+// A 3-D tiled tensor map over `planes` planes of h rows of w elements of type dt (F32, F16, U8), row pitch
+// w elements, plane pitch plane_stride elements, box box_w x box_h x 1, zeros outside; false when the
+// encoder is unavailable or rejects the arguments (the caller then takes a path without TMA).
+bool encode_tmap_3d(CUtensorMap *map, int dt, const void *base, int w, int h, int planes, size_t plane_stride,
+                    int box_w, int box_h);
+
+// The TMA-fed box kernels (gf_box.cu): Algorithm 2's box statistics + coefficients, the box means of a and b,
+// and (s = 1) the box means fused with the output.  FP32 planes whose rows are 16-byte aligned, r' <= 16.
+enum { BOX_JOB_STATS = 0, BOX_JOB_MEANS = 2, BOX_JOB_MEANS_OUTPUT = 3 };
+struct BoxTmaJob {
+    int kind;
+    const float *X, *Y;  // STATS: guide planes (N * CX) and input planes (N * C); MEANS*: a and b (N * C each)
+    size_t xps, yps;     // plane strides (elements)
+    int N, C, CX, h, w, r;
+    float eps;
+    float *out0, *out1;  // STATS: a, b; MEANS: mean_a, mean_b
+    size_t ops;
+    // MEANS_OUTPUT: the full-res guide I (CI planes per image, FP32, plane stride fps), the output q (dt_out),
+    // the rows [Yw0, Yw1) written, the detail gain
+    const float *I;
+    void *q;
+    size_t fps;
+    int CI, Yw0, Yw1, dt_out;
+    float detail;
+    FaultSink fault;
+};
+bool box_tma_supported(const BoxTmaJob &J);
+cudaError_t launch_box_tma(const BoxTmaJob &J, cudaStream_t st);
 
 // The single-kernel form (gf_fused.cu): whether it can run these arguments, and its launch.
 bool fused_supported(const Resolved &R, bool intermediates);

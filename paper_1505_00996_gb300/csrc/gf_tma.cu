@@ -10,19 +10,23 @@
 //   warps 0-3          wait on "full", read their 4 pixels of the 4 rows, write q (128-bit streaming
 //                      stores), and release the stage with one arrival per warp on "empty".
 // Out-of-image rows and columns of a box read as zeros and are never used.  Every wait is bounded: after
-// WAIT_LIMIT failed polls a thread records a timeout in g_wait_faults (read by gf_kernel_faults) and leaves
-// its loop; the producer then drains the loads it issued (bounded again) before the CTA exits.
+// FaultSink::limit failed polls a thread reports FAULT_OUTPUT_TMA (the call's fault word and the device's
+// sticky word, gf_kernel_faults) and leaves its loop; the producer then drains the loads it issued
+// (bounded again) before the CTA exits.  If that drain gives up too, a load may still be landing in the
+// CTA's shared memory when it exits; the call's fault word says so and the call's output is not valid.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include <cstdlib>
+#include <map>
+#include <mutex>
 
 #include "gf_device.cuh"
 #include "gf_internal.cuh"
 
 namespace gfk {
 
-__device__ unsigned g_wait_faults;  // bit 0: a bounded mbarrier wait of the TMA output kernel gave up
+__device__ unsigned g_wait_faults;  // sticky OR of the FAULT_* bits of every call on this device
 
 namespace {
 
@@ -31,7 +35,6 @@ constexpr int TO_NT = TO_CONS + 32;     // plus one producer warp
 constexpr int TO_BAND = 4 * TO_CONS;    // 512 columns per CTA
 constexpr int TO_BOX_X = 256;           // TMA box: 256 columns x 4 rows (a box dimension is at most 256)
 constexpr int TO_NST = 6;               // ring stages (quads of rows in flight; 6 measured best with two images in flight)
-constexpr unsigned WAIT_LIMIT = 1u << 20;
 
 struct TmaOutParams {
     const float *ma, *mb;
@@ -39,27 +42,9 @@ struct TmaOutParams {
     int C, CI, H, W, h, w, R, LRmax, LCmax, Yw0, Yw1;
     size_t lps, fps;
     float detail;
+    FaultSink fault;
+    int skip_first;  // test hook (gf_opts.test_wait_fault): the producer never issues its first stage
 };
-
-__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase with the given parity; false (and the fault bit set) when it gave up.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
-{
-    for (unsigned it = 0; it < WAIT_LIMIT; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    atomicOr(&g_wait_faults, 1u);
-    return false;
-}
 
 template <typename TI, typename TQ, int S>
 __global__ void __launch_bounds__(TO_NT, 4) k_output_tma(const __grid_constant__ CUtensorMap tmI, TmaOutParams P)
@@ -77,7 +62,7 @@ __global__ void __launch_bounds__(TO_NT, 4) k_output_tma(const __grid_constant__
     const int LR = P.LRmax, LC = P.LCmax, tile = LR * LC;
     float *tap = reinterpret_cast<float *>(sm + TO_NST * STAGE);  // [2][LR][LC]
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(tap + 2 * tile);  // full[NST], empty[NST]
-    const unsigned full0 = smem_addr(bars), empty0 = smem_addr(bars + TO_NST);
+    const unsigned full0 = smem_u32(bars), empty0 = smem_u32(bars + TO_NST);
     constexpr int QPR = S / 4;
     // quads (4-row groups of the runs) this CTA uses: those starting above Ye
     const int nquads_all = (nb + 1) * QPR;
@@ -86,10 +71,10 @@ __global__ void __launch_bounds__(TO_NT, 4) k_output_tma(const __grid_constant__
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TO_NST; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(full0 + 8 * s), "r"(1) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(empty0 + 8 * s), "r"(TO_CONS / 32) : "memory");
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, TO_CONS / 32);
         }
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        mbar_fence_init();
     }
     __syncthreads();
 
@@ -97,27 +82,25 @@ __global__ void __launch_bounds__(TO_NT, 4) k_output_tma(const __grid_constant__
         if (threadIdx.x == TO_CONS) {
             const int plane = n * P.CI + (P.CI == 1 ? 0 : c);
             int issued = 0;
-            for (int u = 0; u < nquads; ++u) {
+            int first = 0;
+            if (P.skip_first) {  // test hook: stage 0 is never filled, so the consumers' first wait runs out
+                first = 1;
+            }
+            for (int u = first; u < nquads; ++u) {
                 const int st = u % TO_NST;
-                if (u >= TO_NST && !mbar_wait(empty0 + 8 * st, ((u / TO_NST) - 1) & 1)) break;
+                if (u >= TO_NST && !mbar_wait(empty0 + 8 * st, ((u / TO_NST) - 1) & 1, P.fault, FAULT_OUTPUT_TMA))
+                    break;
                 const unsigned fb = full0 + 8 * st;
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(STAGE) : "memory");
+                mbar_expect_tx(fb, STAGE);
                 const int y = S * (jb - 1 + u / QPR) + S / 2 + 4 * (u % QPR);  // may be < 0: zero fill
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const unsigned dst = smem_addr(sm + st * STAGE + k * BOX_BYTES);
-                    asm volatile(
-                        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-                        " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(dst),
-                        "l"(reinterpret_cast<unsigned long long>(&tmI)), "r"(Xb + k * TO_BOX_X), "r"(y), "r"(plane),
-                        "r"(fb)
-                        : "memory");
-                }
-                ++issued;
+                for (int k = 0; k < 2; ++k) tma_load_3d(sm + st * STAGE + k * BOX_BYTES, &tmI, Xb + k * TO_BOX_X, y, plane, fb);
+                issued = u + 1;
             }
             // drain: every load issued has landed before the CTA may exit (the consumers waited on all of
             // them unless a wait gave up)
-            for (int u = max(0, issued - TO_NST); u < issued; ++u) mbar_wait(full0 + 8 * (u % TO_NST), (u / TO_NST) & 1);
+            for (int u = max(first, issued - TO_NST); u < issued; ++u)
+                mbar_wait(full0 + 8 * (u % TO_NST), (u / TO_NST) & 1, P.fault, FAULT_OUTPUT_TMA);
         }
         return;
     }
@@ -167,7 +150,7 @@ __global__ void __launch_bounds__(TO_NT, 4) k_output_tma(const __grid_constant__
     const int lane = threadIdx.x & 31;
     for (int u = 0; u < nquads; ++u) {
         const int st = u % TO_NST;
-        if (!mbar_wait(full0 + 8 * st, (u / TO_NST) & 1)) break;
+        if (!mbar_wait(full0 + 8 * st, (u / TO_NST) & 1, P.fault, FAULT_OUTPUT_TMA)) break;
         const int t = u / QPR, sub = u % QPR;
         const int Yq = S * (jb - 1 + t) + S / 2 + 4 * sub;
         if (active) {
@@ -205,26 +188,71 @@ __global__ void __launch_bounds__(TO_NT, 4) k_output_tma(const __grid_constant__
             }
         }
         __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(empty0 + 8 * st) : "memory");
+        if (lane == 0) mbar_arrive(empty0 + 8 * st);
     }
 }
 
 using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
+using CtxGetCurrentFn = PFN_cuCtxGetCurrent_v4000;
+
+template <typename F>
+F driver_fn(const char *name, int version)
+{
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, version, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+        p = nullptr;
+    return reinterpret_cast<F>(p);
+}
 
 EncodeFn encode_fn()
 {
-    static EncodeFn fn = [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            p = nullptr;
-        return reinterpret_cast<EncodeFn>(p);
-    }();
+    static EncodeFn fn = driver_fn<EncodeFn>("cuTensorMapEncodeTiled", 12000);
     return fn;
 }
 
 }  // namespace
+
+bool encode_tmap_3d(CUtensorMap *map, int dt, const void *base, int w, int h, int planes, size_t plane_stride,
+                    int box_w, int box_h)
+{
+    EncodeFn enc = encode_fn();
+    if (!enc) return false;
+    const size_t es = dtype_size(dt);
+    const CUtensorMapDataType dtype = dt == F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                      : (dt == F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
+    const cuuint64_t dims[3] = {(cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)w * es, (cuuint64_t)plane_stride * es};
+    const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1}, estr[3] = {1, 1, 1};
+    return enc(map, dtype, 3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The sticky word's device address, looked up once per CUDA context (a context made after cudaDeviceReset
+// gets its own lookup, so no stale address is used).
+unsigned *sticky_fault_word()
+{
+    static CtxGetCurrentFn get_ctx = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent", 4000);
+    static std::mutex mu;
+    static std::map<void *, unsigned *> cache;
+    CUcontext ctx = nullptr;
+    if (!get_ctx || get_ctx(&ctx) != CUDA_SUCCESS || !ctx) {
+        cudaFree(0);  // make the device's primary context current
+        if (!get_ctx || get_ctx(&ctx) != CUDA_SUCCESS || !ctx) return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find((void *)ctx);
+    if (it != cache.end()) return it->second;
+    void *addr = nullptr;
+    if (cudaGetSymbolAddress(&addr, g_wait_faults) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cache[(void *)ctx] = (unsigned *)addr;
+    return (unsigned *)addr;
+}
 
 bool output_tma_ok(const void *I, int dt_in, int W, size_t fps)
 {
@@ -235,19 +263,11 @@ bool output_tma_ok(const void *I, int dt_in, int W, size_t fps)
 
 cudaError_t launch_output_tma(const void *I, const float *ma, const float *mb, void *q, int N, int C, int CI, int H,
                               int W, int h, int w, int s, size_t lps, size_t fps, int Yw0, int Yw1, float detail,
-                              int dt_in, int dt_out, cudaStream_t st)
+                              int dt_in, int dt_out, const FaultSink &fault, cudaStream_t st)
 {
     const size_t es = dtype_size(dt_in);
     CUtensorMap map;
-    const CUtensorMapDataType dtype = dt_in == F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                      : (dt_in == F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
-    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N * CI};
-    const cuuint64_t strides[2] = {(cuuint64_t)W * es, (cuuint64_t)fps * es};
-    const cuuint32_t box[3] = {(cuuint32_t)TO_BOX_X, 4, 1}, estr[3] = {1, 1, 1};
-    if (encode_fn()(&map, dtype, 3, const_cast<void *>(I), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
+    if (!encode_tmap_3d(&map, dt_in, I, W, H, N * CI, fps, TO_BOX_X, 4)) return cudaErrorInvalidValue;
     TmaOutParams P;
     P.ma = ma; P.mb = mb; P.q = q;
     P.C = C; P.CI = CI; P.H = H; P.W = W; P.h = h; P.w = w;
@@ -257,6 +277,8 @@ cudaError_t launch_output_tma(const void *I, const float *ma, const float *mb, v
     P.Yw0 = Yw0; P.Yw1 = Yw1;
     P.lps = lps; P.fps = fps;
     P.detail = detail;
+    P.fault = fault;
+    P.skip_first = fault.inject ? 1 : 0;
     const int bands = (W + TO_BAND - 1) / TO_BAND;
     dim3 grid(bands * C, (H + P.R - 1) / P.R, N);
     const size_t smem = (size_t)TO_NST * 2 * TO_BOX_X * 4 * es + (size_t)2 * P.LRmax * P.LCmax * sizeof(float) +

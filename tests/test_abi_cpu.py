@@ -47,8 +47,8 @@ def test_opts_defaults(lib):
     o = binding.opts_init()
     assert (o.batch, o.guide_channels, o.r_low, o.p_lowres, o.dtype_in, o.dtype_out) == (1, 1, -1, 0, 0, 0)
     assert not o.workspace and not o.kernel_events
-    assert lib.gf_abi_version() == 3
-    assert o.saved_forward == 0
+    assert lib.gf_abi_version() == 4
+    assert o.saved_forward == 0 and o.test_wait_fault == 0
 
 
 @pytest.mark.parametrize("H,W,s,r", [(3000, 4000, 4, 16), (3000, 4000, 8, 16), (3000, 4000, 1, 16), (10, 13, 4, 6),
@@ -113,7 +113,10 @@ def test_kernel_count(lib):
     o = binding.opts_init()
     count = lambda H, W, s, mode: lib.gf_filter_kernel_count(H, W, 3, s, mode, ctypes.byref(o))
     assert count(3000, 4000, 4, binding.GF_SUB_BILINEAR) == 4
-    assert count(3000, 4000, 1, binding.GF_SUB_BILINEAR) == 3   # s = 1: no subsample stage
+    # s = 1: no subsample stage, and the identity upsample lets the box means of a, b and the output share
+    # one kernel (rows a multiple of 4 pixels); otherwise statistics, box means and output apart
+    assert count(3000, 4000, 1, binding.GF_SUB_BILINEAR) == 2
+    assert count(3000, 4001, 1, binding.GF_SUB_BILINEAR) == 3
     assert count(0, 4000, 4, binding.GF_SUB_BILINEAR) == -1
 
 

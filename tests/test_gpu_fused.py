@@ -92,7 +92,7 @@ def test_automatic_choice_and_checks(gf):
     assert count(1024, 1024, 1) == 1                  # N C H W = 2^20: still one
     assert count(1024, 1024, 3) == 4                  # above the threshold: the chain
     s1 = lib.gf_filter_kernel_count(256, 256, 1, 1, gf.GF_SUB_BILINEAR, ctypes.byref(o))
-    assert s1 == 3                                    # s = 1: the chain unless forced
+    assert s1 == 2                                    # s = 1: the chain (statistics, box means + output)
     o.fused = -1
     assert count(512, 512, 3) == 4
     o.fused = 1
