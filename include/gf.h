@@ -177,9 +177,12 @@ gf_status gf_lowres_geometry(int H, int W, int s, int r, int r_low, int *h, int 
 gf_status gf_row_band(int H, int W, int s, int r, int r_low, gf_subsample_mode mode, int row_begin, int row_end,
                       int *row0, int *rows);
 
-/* Fault bits the library's kernels recorded on `device` since the last clear (host call; synchronous
- * copy from the device).  Bit 0: a bounded wait of a pipelined kernel gave up (the kernel stopped early;
- * its output is incomplete).  clear != 0 resets them.  GF_ECUDA if the copy fails. */
+/* Fault bits the library's kernels recorded on `device` since the last clear, over all calls (host call;
+ * synchronous copy from the device).  Bit 0: a bounded wait of the TMA-fed output kernel gave up; bit 1:
+ * one of the TMA-fed box kernels (the kernel stopped early; the output of that call is incomplete).
+ * clear != 0 resets them.  GF_ECUDA if the copy fails.  Besides these device-wide bits, every call keeps
+ * a fault word of its own in its scratch, zeroed when the call starts: gf_filter_host and the serving loop
+ * read it after the call and report GF_EWAIT when it is set. */
 gf_status gf_kernel_faults(int device, unsigned *flags, int clear);
 
 /* Number of kernels one gf_filter call with these arguments launches (host-only; -1 for invalid
@@ -227,6 +230,7 @@ gf_status gf_filter(gf_ctx *ctx, const void *I, const void *p, void *q, int H, i
  * rounding order.  With nearest or bilinear subsampling at s >= 3 only the rows of p that the subsample
  * reads are uploaded (rows s j + (s - 1) / 2 and the next of every s-row block, and a partial last block
  * whole): half of p at s = 4, a quarter at s = 8.
+ * Returns GF_EWAIT (q incomplete) when a kernel of the call gave up a bounded wait.
  */
 gf_status gf_filter_host(gf_ctx *ctx, const void *I_host, const void *p_host, void *q_host, int H, int W, int C,
                          int r, float eps, int s, gf_subsample_mode mode, const gf_opts *opts, void *cuda_stream);
@@ -264,7 +268,10 @@ gf_status gf_filter_backward(gf_ctx *ctx, const void *I, const void *p, const vo
  * streams, so requests that arrive while others are on the GPU overlap with them.  gf_poll returns the
  * outcome.  The per-pixel arithmetic is that of gf_filter, so a request's q is the same whether it ran alone
  * or among others.  I, p and q stay caller-owned and must remain valid until gf_poll reports a terminal
- * status (GF_OK, GF_ECANCELED or an error).  Times are seconds on gf_clock().
+ * status (GF_OK, GF_ECANCELED or an error).  Times are seconds on gf_clock().  A request whose inputs are
+ * still being written by work on another stream names an event recorded after that work (ready_event); its
+ * kernels then wait for the event on the GPU.  A request whose kernel gave up a bounded wait (its data
+ * never arrived) is reported GF_EWAIT, not GF_OK.
  */
 typedef struct gf_request {
     const void *I, *p;  /* device inputs, as for gf_filter */
@@ -273,8 +280,12 @@ typedef struct gf_request {
     float eps;
     int s;
     gf_subsample_mode mode;
-    gf_opts opts;       /* batch, guide_channels, r_low, p_lowres, dtype_in/out; other fields are ignored */
+    gf_opts opts;       /* batch, guide_channels, r_low, p_lowres, dtype_in/out, fused, test_wait_fault;
+                           other fields are ignored */
     void *user;         /* caller's tag, returned in gf_result */
+    void *ready_event;  /* optional cudaEvent_t (as void*): the request's kernels wait for the work recorded in
+                           it when gf_submit is called (record it after the work that writes I and p; the
+                           event may be re-recorded or destroyed once gf_submit returns).  NULL: none */
 } gf_request;
 
 typedef struct gf_result {
@@ -288,6 +299,8 @@ typedef struct gf_result {
 typedef struct gf_serve_stats {
     int queued, running, slots;
     size_t budget_bytes, scratch_in_use;
+    long long launches;      /* requests launched so far */
+    double launch_seconds;   /* host time the scheduler spent enqueuing them (kernels and bookkeeping) */
 } gf_serve_stats;
 
 /* Monotonic clock of the serving timestamps, in seconds. */
@@ -327,11 +340,12 @@ gf_status gf_serve_stats_get(gf_ctx *ctx, gf_serve_stats *out);
  * fixed array of 64 MiB compiled into the library, which every GPU that loads the library holds until the
  * process exits; a call whose scratch (gf_workspace_size) exceeds 64 MiB returns GF_EINVAL with a message
  * (a 12 MP, 3-channel FP32 call at s = 4 needs about 48 MB; s = 1 at that size does not fit).  Runs on the
- * current CUDA device.  The first call on each device looks up that device's address of the array; make
- * that first call before any stream capture.  Every call shares the one array, which keeps the last
- * call's contents (the filter writes each scratch plane before reading it, so nothing needs clearing):
- * calls whose kernels overlap on the GPU -- on different streams, or from different threads -- race on
- * it and must be serialised by the caller.  No cudaMalloc, cudaFree or other allocating call is made.
+ * current CUDA device.  The first call in each CUDA context looks up that context's address of the array
+ * (a context made after cudaDeviceReset gets its own lookup); make that first call before any stream
+ * capture.  Every call shares the one array, which keeps the last call's contents (the filter writes each
+ * scratch plane before reading it, and zeroes the call's fault word itself): calls whose kernels overlap
+ * on the GPU -- on different streams, or from different threads -- race on it and must be serialised by
+ * the caller.  No cudaMalloc, cudaFree or other allocating call is made.
  */
 gf_status gf_filter_noalloc(const void *I, const void *p, void *q, int H, int W, int C, int r, float eps, int s,
                             gf_subsample_mode mode, const gf_opts *opts, void *cuda_stream);

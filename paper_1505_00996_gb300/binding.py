@@ -68,7 +68,7 @@ class GFRequest(ctypes.Structure):
         ("I", ctypes.c_void_p), ("p", ctypes.c_void_p), ("q", ctypes.c_void_p),
         ("H", ctypes.c_int), ("W", ctypes.c_int), ("C", ctypes.c_int), ("r", ctypes.c_int),
         ("eps", ctypes.c_float), ("s", ctypes.c_int), ("mode", ctypes.c_int),
-        ("opts", GFOpts), ("user", ctypes.c_void_p),
+        ("opts", GFOpts), ("user", ctypes.c_void_p), ("ready_event", ctypes.c_void_p),
     ]
 
 
@@ -84,6 +84,7 @@ class GFServeStats(ctypes.Structure):
     _fields_ = [
         ("queued", ctypes.c_int), ("running", ctypes.c_int), ("slots", ctypes.c_int),
         ("budget_bytes", ctypes.c_size_t), ("scratch_in_use", ctypes.c_size_t),
+        ("launches", ctypes.c_longlong), ("launch_seconds", ctypes.c_double),
     ]
 
 
@@ -174,7 +175,8 @@ def opts_init():
 
 
 def kernel_faults(device=None, clear=True):
-    """Fault bits the kernels recorded on `device` (bit 0: a bounded wait gave up); cleared by default."""
+    """Fault bits the kernels recorded on `device` since the last clear (bit 0: a bounded wait of the TMA output
+    kernel gave up, bit 1: of a TMA box kernel); cleared by default."""
     if device is None:
         device = torch.cuda.current_device()
     v = ctypes.c_uint()
@@ -306,7 +308,7 @@ def _stream_handle(stream):
 def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowres=False, out_dtype=None,
                        out=None, a_out=None, b_out=None, mean_a_out=None, mean_b_out=None, stats_out=None,
                        workspace=None, kernel_events=None, stream=None, ctx=None, detail_gain=0.0, rows=None,
-                       color_guide=False, fused=0, saved_forward=False):
+                       color_guide=False, fused=0, saved_forward=False, test_wait_fault=False):
     """Fast guided filter (Algorithm 2; Algorithm 1 at s = 1) on CUDA tensors, via ``gf_filter``.
 
     I: (H, W), (CI, H, W) or (N, CI, H, W); p: the same rank with C channels (at low resolution when
@@ -319,6 +321,7 @@ def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowr
     ``fused``: 0 runs the whole filter as one kernel for small images, 1 always, -1 never.
     ``saved_forward=True`` with ``workspace`` (``backward_workspace_size`` bytes) keeps the low-res planes
     there for a ``fast_guided_filter_backward`` call with the same arguments, workspace and flag.
+    ``test_wait_fault=True`` is the test hook of gf_opts.test_wait_fault (a bounded wait is made to run out).
     """
     if not (I.is_cuda and p.is_cuda):
         raise ValueError("I and p must be CUDA tensors")
@@ -358,6 +361,7 @@ def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowr
     o.color_guide = int(bool(color_guide))
     o.fused = int(fused)
     o.saved_forward = int(bool(saved_forward))
+    o.test_wait_fault = int(bool(test_wait_fault))
     if rows is not None:
         if not given:
             raise ValueError("rows needs out= (the whole q; rows outside the range are not written)")
@@ -396,9 +400,10 @@ def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowr
 
 
 def fast_guided_filter_host(I, p, r, eps, s=4, mode="bilinear", *, out=None, out_dtype=None, r_low=None,
-                            stream=None, ctx=None, device=None):
+                            stream=None, ctx=None, device=None, fused=0, test_wait_fault=False):
     """Same filter on HOST (CPU) tensors through ``gf_filter_host``: the library copies the inputs to the
-    device, filters and copies q back before returning."""
+    device, filters and copies q back before returning.  A kernel that gave up a bounded wait makes it raise
+    GFError with status GF_EWAIT."""
     if I.is_cuda or p.is_cuda:
         raise ValueError("gf_filter_host takes host tensors")
     I4, _ = _nchw(I, "I")
@@ -416,6 +421,8 @@ def fast_guided_filter_host(I, p, r, eps, s=4, mode="bilinear", *, out=None, out
     s = _ratio(o, s)
     o.dtype_in = _DTYPES[I.dtype]
     o.dtype_out = _DTYPES[out_dtype]
+    o.fused = int(fused)
+    o.test_wait_fault = int(bool(test_wait_fault))
     ctx = ctx or default_context(device)
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     I4 = I4.contiguous()

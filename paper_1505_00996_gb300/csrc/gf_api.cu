@@ -2,6 +2,7 @@
 // the context and its scratch arena, and the host-buffer wrapper.  All arithmetic runs in the kernels of
 // gf_forward.cu.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -258,10 +259,7 @@ FaultSink call_fault_sink(char *ws, const Layout &L, const gf_opts *opts)
     FaultSink f;
     f.call = (unsigned *)(ws + L.off_fault);
     f.sticky = sticky_fault_word();
-    if (opts && opts->test_wait_fault) {
-        f.limit = 256;
-        f.inject = 1;
-    }
+    if (opts && opts->test_wait_fault) f.inject = 1;
     return f;
 }
 
@@ -272,6 +270,8 @@ Layout layout_of(const Resolved &R, const gf_opts *o)
     Layout L;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t at = off; off += (bytes + 255) & ~size_t(255); return at; };
+    // the call's fault word first, at the same place in every layout (the strips of one host call share it)
+    L.off_fault = take(sizeof(unsigned));
     const bool sub = R.s > 1 || R.p_lowres || R.color;
     L.off_Il = take(sub ? (size_t)R.N * R.CI * pb : 0);
     L.off_pl = take(sub ? nc : 0);
@@ -282,7 +282,6 @@ Layout layout_of(const Resolved &R, const gf_opts *o)
     L.off_mb = take((o && o->mean_b_out) || !gray ? 0 : nc);
     for (int k = 0; k < 8; ++k)  // colour guide: 4 arrays of 5 + 2C planes per image, then 4 of 2C
         L.off_col[k] = take(R.color ? (size_t)R.N * (k < 4 ? 5 + 2 * R.C : 2 * R.C) * pb : 0);
-    L.off_fault = take(sizeof(unsigned));  // the call's fault word
     L.total = off;
     return L;
 }
@@ -336,6 +335,78 @@ using gfk::bwd_layout_of;
 using gfk::check_backward;
 
 namespace {
+
+// gf_filter on device buffers.  clear_fault = false leaves the call's fault word as it was, so that the strips
+// of one gf_filter_host call accumulate into one word.
+gf_status filter_device(gf_ctx *ctx, const void *I, const void *p, void *q, int H, int W, int C, int r, float eps,
+                        int s, gf_subsample_mode mode, const gf_opts *opts, void *cuda_stream, bool clear_fault)
+{
+    if (!ctx) return fail(GF_EINVAL, "ctx is NULL");
+    if (!I || !p || !q) return fail(GF_EINVAL, "I, p and q must be device pointers");
+    Resolved R;
+    gf_status st = resolve(H, W, C, r, eps, s, (int)mode, opts, R);
+    if (st != GF_OK) return st;
+    if (opts && opts->saved_forward) {
+        // the forward of a later gf_filter_backward: its low-res planes stay in the backward's workspace layout
+        if ((st = check_backward(R)) != GF_OK) return st;
+        if (opts->a_out || opts->b_out || opts->mean_a_out || opts->mean_b_out || opts->stats_out)
+            return fail(GF_EINVAL, "saved_forward does not produce low-res intermediate outputs");
+        if (!opts->workspace) return fail(GF_EINVAL, "saved_forward needs opts->workspace (gf_backward_workspace_size bytes)");
+        R.lps = gfk::plane_stride_f32((size_t)R.h * R.w);
+        const BwdLayout BL = bwd_layout_of(R);
+        if (opts->workspace_bytes < BL.total)
+            return fail(GF_EINVAL, "saved_forward: workspace_bytes is smaller than gf_backward_workspace_size()");
+        DeviceGuard guard(ctx->device);
+        char *ws = (char *)opts->workspace;
+        gfk::FwdPlan P = gfk::make_plan(R, BL.fwd, I, p, q, ws, nullptr);
+        P.stats = ws + BL.off_stats;
+        P.need_lowres = true;
+        P.events = opts->kernel_events ? (cudaEvent_t *)opts->kernel_events : nullptr;
+        P.clear_fault = clear_fault;
+        cudaError_t e = gfk::launch_forward(P, (cudaStream_t)cuda_stream);
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch in gf_filter");
+        return GF_OK;
+    }
+    const Layout L = layout_of(R, opts);
+
+    DeviceGuard guard(ctx->device);
+    std::unique_lock<std::mutex> lock(ctx->mu, std::defer_lock);
+    char *ws = nullptr;
+    if (opts && opts->workspace) {
+        if (opts->workspace_bytes < L.total)
+            return fail(GF_EINVAL, "workspace_bytes is smaller than gf_workspace_size()");
+        ws = (char *)opts->workspace;
+    } else {
+        lock.lock();
+        st = grow(&ctx->arena, &ctx->arena_bytes, L.total, "the scratch arena");
+        if (st != GF_OK) return st;
+        ws = (char *)ctx->arena;
+    }
+
+    gfk::FwdPlan P = gfk::make_plan(R, L, I, p, q, ws, opts);
+    P.clear_fault = clear_fault;
+    cudaError_t e = gfk::launch_forward(P, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch in gf_filter");
+    return GF_OK;
+}
+
+// After a synchronous host call: the fault word of its scratch (offset 0 of the context arena or of the
+// caller's workspace) is read back; a bounded wait inside a kernel that gave up makes the call GF_EWAIT.
+gf_status check_call_faults(gf_ctx *ctx, const gf_opts *opts)
+{
+    const void *ws = (opts && opts->workspace) ? opts->workspace : ctx->arena;
+    if (!ws) return GF_OK;
+    unsigned word = 0;
+    cudaError_t e = cudaMemcpy(&word, ws, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the call's fault word");
+    if (word != 0) {
+        char bits[16];
+        snprintf(bits, sizeof(bits), "0x%x", word);
+        return fail(GF_EWAIT, std::string("a kernel gave up a bounded wait (fault bits ") + bits +
+                                  "): the output is incomplete");
+    }
+    return GF_OK;
+}
 
 // Host-buffer pipeline (gf_filter_host on large images): the output rows are cut into strips; the input rows
 // each strip's band needs are copied in on one stream, the strip is filtered on the caller's stream as a
@@ -457,7 +528,7 @@ gf_status host_pipeline(gf_ctx *ctx, const Resolved &R, const std::vector<int> &
         if (!ok) break;
         so.row_begin = Y[k];
         so.row_end = Y[k + 1];
-        gf_status st = gf_filter(ctx, dI, dp, dq, H, W, C, r, eps, s, mode, &so, stream);
+        gf_status st = filter_device(ctx, dI, dp, dq, H, W, C, r, eps, s, mode, &so, stream, k == 0);
         if (st != GF_OK) {
             result = st;
             break;
@@ -476,6 +547,7 @@ gf_status host_pipeline(gf_ctx *ctx, const Resolved &R, const std::vector<int> &
     check(e1, "cudaStreamSynchronize of the copy-in stream");
     check(e2, "cudaStreamSynchronize of the copy-out stream");
     check(e3, "cudaStreamSynchronize");
+    if (result == GF_OK) result = check_call_faults(ctx, opts);
     return result;
 }
 
@@ -555,51 +627,7 @@ gf_status gf_filter(gf_ctx *ctx, const void *I, const void *p, void *q, int H, i
                     gf_subsample_mode mode, const gf_opts *opts, void *cuda_stream)
 {
     gfk::NvtxRange range("gf_filter");
-    if (!ctx) return fail(GF_EINVAL, "ctx is NULL");
-    if (!I || !p || !q) return fail(GF_EINVAL, "I, p and q must be device pointers");
-    Resolved R;
-    gf_status st = resolve(H, W, C, r, eps, s, (int)mode, opts, R);
-    if (st != GF_OK) return st;
-    if (opts && opts->saved_forward) {
-        // the forward of a later gf_filter_backward: its low-res planes stay in the backward's workspace layout
-        if ((st = check_backward(R)) != GF_OK) return st;
-        if (opts->a_out || opts->b_out || opts->mean_a_out || opts->mean_b_out || opts->stats_out)
-            return fail(GF_EINVAL, "saved_forward does not produce low-res intermediate outputs");
-        if (!opts->workspace) return fail(GF_EINVAL, "saved_forward needs opts->workspace (gf_backward_workspace_size bytes)");
-        R.lps = gfk::plane_stride_f32((size_t)R.h * R.w);
-        const BwdLayout BL = bwd_layout_of(R);
-        if (opts->workspace_bytes < BL.total)
-            return fail(GF_EINVAL, "saved_forward: workspace_bytes is smaller than gf_backward_workspace_size()");
-        DeviceGuard guard(ctx->device);
-        char *ws = (char *)opts->workspace;
-        gfk::FwdPlan P = gfk::make_plan(R, BL.fwd, I, p, q, ws, nullptr);
-        P.stats = ws + BL.off_stats;
-        P.need_lowres = true;
-        P.events = opts->kernel_events ? (cudaEvent_t *)opts->kernel_events : nullptr;
-        cudaError_t e = gfk::launch_forward(P, (cudaStream_t)cuda_stream);
-        if (e != cudaSuccess) return cuda_fail(e, "kernel launch in gf_filter");
-        return GF_OK;
-    }
-    const Layout L = layout_of(R, opts);
-
-    DeviceGuard guard(ctx->device);
-    std::unique_lock<std::mutex> lock(ctx->mu, std::defer_lock);
-    char *ws = nullptr;
-    if (opts && opts->workspace) {
-        if (opts->workspace_bytes < L.total)
-            return fail(GF_EINVAL, "workspace_bytes is smaller than gf_workspace_size()");
-        ws = (char *)opts->workspace;
-    } else {
-        lock.lock();
-        st = grow(&ctx->arena, &ctx->arena_bytes, L.total, "the scratch arena");
-        if (st != GF_OK) return st;
-        ws = (char *)ctx->arena;
-    }
-
-    const gfk::FwdPlan P = gfk::make_plan(R, L, I, p, q, ws, opts);
-    cudaError_t e = gfk::launch_forward(P, (cudaStream_t)cuda_stream);
-    if (e != cudaSuccess) return cuda_fail(e, "kernel launch in gf_filter");
-    return GF_OK;
+    return filter_device(ctx, I, p, q, H, W, C, r, eps, s, mode, opts, cuda_stream, true);
 }
 
 gf_status gf_filter_host(gf_ctx *ctx, const void *I_host, const void *p_host, void *q_host, int H, int W, int C,
@@ -641,7 +669,7 @@ gf_status gf_filter_host(gf_ctx *ctx, const void *I_host, const void *p_host, vo
     if ((e = cudaMemcpyAsync(q_host, dq, bq, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpyAsync of q");
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-    return GF_OK;
+    return check_call_faults(ctx, opts);
 }
 
 int gf_host_strips(int H, int W, int C, int s, gf_subsample_mode mode, const gf_opts *opts, int *row_starts)

@@ -1401,8 +1401,9 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
     // The call's fault word starts at zero (kernels whose bounded waits give up OR their bit into it): the
     // first kernel of the chain zeroes it (the single fused kernel, or the subsample), else a memset does.
     const bool fused_call = P.fused && !P.skip_output && !P.need_lowres;
-    if (P.fault.call && !fused_call && !(P.s > 1 || P.color) &&
-        (err = cudaMemsetAsync(P.fault.call, 0, sizeof(unsigned), st)) != cudaSuccess)
+    unsigned *clear_word = P.clear_fault ? P.fault.call : nullptr;
+    if (clear_word && !fused_call && !(P.s > 1 || P.color) &&
+        (err = cudaMemsetAsync(clear_word, 0, sizeof(unsigned), st)) != cudaSuccess)
         return err;
     if (fused_call) {  // the whole filter in one kernel
         tm.before();
@@ -1423,7 +1424,7 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         sp.h = P.h; sp.w = P.w; sp.mode = P.mode;
         // uint8 path: carry the subsampled values as exact integers J = k * (value in 1/255 units)
         sp.scale = P.int_stats ? P.int_scale / 255.0f : 1.0f;
-        sp.clear_word = P.fault.call;
+        sp.clear_word = clear_word;
         sp.job[0] = SubJob{P.I, P.Il, P.N * P.CI, P.H, P.W, P.s, P.fps, P.lps, P.sn, P.sd};
         if (!P.p_lowres)
             sp.job[1] = SubJob{P.p, P.pl, planesNC, P.H, P.W, P.s, P.fps, P.lps, P.sn, P.sd};

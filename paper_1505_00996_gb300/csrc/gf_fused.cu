@@ -238,7 +238,7 @@ cudaError_t launch_fused(const FwdPlan &P, cudaStream_t st)
     F.fps = P.fps; F.lpin = P.lpin; F.p_lowres = P.p_lowres;
     F.TH = S.TH; F.TW = S.TW;
     F.Yw0 = P.Yw0; F.Yw1 = P.Yw1;
-    F.clear_word = P.fault.call;
+    F.clear_word = P.clear_fault ? P.fault.call : nullptr;
     dim3 grid((P.W + S.TW - 1) / S.TW, (P.H + S.TH - 1) / S.TH, P.N * P.C);
     cudaError_t e;
 #define GF_FU(TI, TQ, M)                                                                     \

@@ -45,12 +45,16 @@ enum : unsigned { FAULT_OUTPUT_TMA = 1u, FAULT_BOX_TMA = 2u };
 // Where a kernel with bounded waits reports a wait that gave up: the fault word of its call (in the call's
 // scratch, cleared when the call starts) and the device's sticky word (gf_kernel_faults).  Either may be
 // NULL.  `limit` is the number of polls before a wait gives up.  `inject` (tests of the timeout path only,
-// gf_opts.test_wait_fault) makes the TMA output kernel's producer leave its first stage unfilled, so that
-// its consumers' first wait runs out.
+// gf_opts.test_wait_fault) makes the TMA output kernel's producer leave its first stage unfilled and gives
+// that kernel's waits for data and for free stages INJECT_LIMIT polls, so that its consumers' first wait runs
+// out; waits for copies already issued (the producer's drain, the box kernels' tile loads) keep `limit`, so
+// no CTA leaves while a copy into its shared memory may still be landing.
+constexpr unsigned WAIT_LIMIT = 1u << 20;
+constexpr unsigned INJECT_LIMIT = 256;
 struct FaultSink {
     unsigned *call = nullptr;
     unsigned *sticky = nullptr;
-    unsigned limit = 1u << 20;
+    unsigned limit = WAIT_LIMIT;
     unsigned inject = 0;
 };
 
@@ -96,6 +100,7 @@ struct FwdPlan {
     int Yw0 = 0, Yw1 = 0;  // output rows written, [Yw0, Yw1) of the H rows the plan covers
     bool lowres_out = false;   // a, b, mean_a or mean_b are caller outputs (no fusion may skip them)
     FaultSink fault;           // where kernels with bounded waits report a wait that gave up
+    bool clear_fault = true;   // the call zeroes its fault word first (false: keep accumulating into it)
     bool skip_output = false;  // stop after the low-res stages (the backward's forward recomputation)
     bool need_lowres = false;  // keep I', p' in the workspace (no fused subsample); the backward reads them
 };

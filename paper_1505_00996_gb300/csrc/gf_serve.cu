@@ -10,9 +10,13 @@
 // admits more work.  The per-pixel arithmetic does not depend on what else is running, so a request's
 // result is the same alone and in a mix.
 //
-// Failure handling is host-side: a failed launch marks its request GF_ECUDA and the loop carries on; the
-// environment variable GF_FAULT=launch:<k> makes the k-th admitted launch report failure without launching
-// anything (used by the tests); waits in gf_poll are bounded by the caller's timeout.
+// Failure handling: a failed launch marks its request GF_ECUDA and the loop carries on; the environment
+// variable GF_FAULT=launch:<k> makes the k-th admitted launch report failure without launching anything
+// (used by the tests); waits in gf_poll are bounded by the caller's timeout.  After a request's kernels its
+// slot stream copies the request's fault word (the bounded waits inside the kernels) to pinned host memory
+// ahead of the completion callback, and the scheduler reports a request whose word is set as GF_EWAIT.
+// A request's ready_event is waited for on the slot stream before its kernels, so inputs that another
+// stream is still writing are complete when they are read.
 #include <stdlib.h>
 #include <string.h>
 
@@ -105,6 +109,7 @@ struct Request {
     std::atomic<double> t_done{0.0};
     std::atomic<int> finished{0};  // set by the stream callback
     struct Server *srv = nullptr;
+    cudaEvent_t ready = nullptr;   // the caller's inputs are complete at this event (owned copy; may be NULL)
 };
 
 }  // namespace
@@ -127,17 +132,24 @@ struct Server {
     std::thread thread;
     long long launches = 0, fault_launch = -1;
     bool paused = false;  // admission held (requests stay queued)
+    unsigned *fault_host = nullptr;  // pinned, one word per slot: the fault word of the request on that slot
+    cudaStream_t ready_stream = nullptr;  // where a request's ready event is captured at submission
+    long long launched = 0;          // requests enqueued, and the host time spent enqueuing them
+    double launch_seconds = 0.0;
 };
 
 namespace {
 
+// Stream callback after a request's kernels (and its fault-word copy).  It takes the server's lock before
+// publishing completion, so the scheduler cannot retire the request -- after which gf_poll may free it --
+// while the callback still uses it.  No CUDA call is made here.
 void CUDART_CB on_done(void *arg)
 {
     Request *r = static_cast<Request *>(arg);
-    r->t_done.store(now_seconds());
-    r->finished.store(1, std::memory_order_release);
     Server *s = r->srv;
     std::lock_guard<std::mutex> lock(s->mu);
+    r->t_done.store(now_seconds());
+    r->finished.store(1, std::memory_order_release);
     s->cv_sched.notify_all();
 }
 
@@ -151,12 +163,28 @@ gf_status launch_request(Server *s, Request &r, bool *launched_some)
         gf_set_error("injected launch failure (GF_FAULT)");
         return GF_ECUDA;
     }
+    const double t0 = now_seconds();
     char *ws = (char *)s->arena + r.off;
-    const FwdPlan P = make_plan(r.R, r.L, r.req.I, r.req.p, r.req.q, ws, nullptr);
+    const FwdPlan P = make_plan(r.R, r.L, r.req.I, r.req.p, r.req.q, ws, &r.req.opts);
     cudaStream_t st = s->streams[r.slot];
+    cudaError_t e = cudaSuccess;
+    if (r.ready) {
+        e = cudaStreamWaitEvent(st, r.ready, 0);  // the inputs are complete
+        cudaEventDestroy(r.ready);                 // released once the wait has been resolved
+        r.ready = nullptr;
+    }
+    if (e != cudaSuccess) {
+        gf_set_error(std::string("serving launch: waiting for the request's ready event: ") + cudaGetErrorString(e));
+        return GF_ECUDA;
+    }
     *launched_some = true;
-    cudaError_t e = launch_forward(P, st);
+    s->fault_host[r.slot] = 0;
+    e = launch_forward(P, st);
+    if (e == cudaSuccess && P.fault.call)
+        e = cudaMemcpyAsync(&s->fault_host[r.slot], P.fault.call, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaLaunchHostFunc(st, on_done, &r);
+    ++s->launched;
+    s->launch_seconds += now_seconds() - t0;
     if (e != cudaSuccess) {
         gf_set_error(std::string("serving launch: ") + cudaGetErrorString(e));
         return GF_ECUDA;
@@ -176,6 +204,10 @@ void scheduler(Server *s)
             auto &r = *s->reqs[t];
             if (r.finished.load(std::memory_order_acquire)) {
                 r.state = DONE;
+                if (s->fault_host[k] != 0) {  // a kernel of the request gave up a bounded wait: q is incomplete
+                    r.state = FAILED;
+                    r.status = GF_EWAIT;
+                }
                 s->alloc.release(r.off, r.L.total);
                 s->slot_owner[k] = 0;
                 s->cv_done.notify_all();
@@ -244,10 +276,22 @@ gf_status server_start(Server *s)
         gf_set_error(std::string("serving arena of ") + std::to_string(s->budget) + " bytes: " + cudaGetErrorString(e));
         return GF_ENOMEM;
     }
+    e = cudaHostAlloc((void **)&s->fault_host, sizeof(unsigned) * s->nslots, cudaHostAllocPortable);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(s->arena);
+        s->arena = nullptr;
+        s->fault_host = nullptr;
+        cudaSetDevice(prev);
+        gf_set_error(std::string("serving fault words (pinned host memory): ") + cudaGetErrorString(e));
+        return GF_ENOMEM;
+    }
+    for (int k = 0; k < s->nslots; ++k) s->fault_host[k] = 0;
     s->alloc.reset(s->budget);
     s->streams.resize(s->nslots);
     s->slot_owner.assign(s->nslots, 0);
     for (int k = 0; k < s->nslots; ++k) cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking);
+    cudaStreamCreateWithFlags(&s->ready_stream, cudaStreamNonBlocking);
     cudaSetDevice(prev);
     s->thread = std::thread(scheduler, s);
     s->started = true;
@@ -287,9 +331,13 @@ void server_destroy(Server *s)
             cudaStreamSynchronize(st);
             cudaStreamDestroy(st);
         }
+        if (s->ready_stream) cudaStreamDestroy(s->ready_stream);
         if (s->arena) cudaFree(s->arena);
+        if (s->fault_host) cudaFreeHost(s->fault_host);
         cudaSetDevice(prev);
     }
+    for (auto &kv : s->reqs)
+        if (kv.second->ready) cudaEventDestroy(kv.second->ready);
     delete s;
 }
 
@@ -340,6 +388,18 @@ gf_status server_submit(Server *s, const gf_request *req, uint64_t *ticket)
         return GF_EBUSY;
     }
     if ((st = server_start(s)) != GF_OK) return st;
+    if (req->ready_event) {
+        // capture the caller's event as it stands now: an event of our own completes with it
+        cudaError_t e = cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s->ready_stream, (cudaEvent_t)req->ready_event, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(r->ready, s->ready_stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (r->ready) cudaEventDestroy(r->ready);
+            gf_set_error(std::string("request ready_event: ") + cudaGetErrorString(e));
+            return GF_ECUDA;
+        }
+    }
     r->ticket = s->next_ticket++;
     r->t_submit = now_seconds();
     s->reqs[r->ticket] = r;
@@ -376,8 +436,15 @@ gf_status server_poll(Server *s, uint64_t ticket, int64_t timeout_us, gf_result 
         out->scratch_bytes = r->L.total;
     }
     const gf_status st = r->state == CANCELED ? GF_ECANCELED : r->status;
+    if (r->ready) {  // never launched (cancelled)
+        cudaEventDestroy(r->ready);
+        r->ready = nullptr;
+    }
     s->reqs.erase(it);  // a terminal result is delivered once
-    if (st != GF_OK) gf_set_error(st == GF_ECANCELED ? "request was cancelled" : "request failed");
+    if (st != GF_OK)
+        gf_set_error(st == GF_ECANCELED ? "request was cancelled"
+                     : st == GF_EWAIT   ? "request failed: a kernel gave up a bounded wait (q is incomplete)"
+                                        : "request failed");
     return st;
 }
 
@@ -418,6 +485,8 @@ gf_status server_stats(Server *s, gf_serve_stats *out)
     out->budget_bytes = s->budget;
     out->scratch_in_use = s->alloc.in_use();
     out->slots = s->nslots;
+    out->launches = s->launched;
+    out->launch_seconds = s->launch_seconds;
     return GF_OK;
 }
 

@@ -78,6 +78,9 @@ __global__ void __launch_bounds__(TO_NT, 4) k_output_tma(const __grid_constant__
     }
     __syncthreads();
 
+    // waits for data and for free stages (shortened by the test hook); the drain keeps the full limit
+    FaultSink fw = P.fault;
+    if (P.skip_first) fw.limit = INJECT_LIMIT;
     if (threadIdx.x >= TO_CONS) {  // ---- producer warp
         if (threadIdx.x == TO_CONS) {
             const int plane = n * P.CI + (P.CI == 1 ? 0 : c);
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(TO_NT, 4) k_output_tma(const __grid_constant__
             }
             for (int u = first; u < nquads; ++u) {
                 const int st = u % TO_NST;
-                if (u >= TO_NST && !mbar_wait(empty0 + 8 * st, ((u / TO_NST) - 1) & 1, P.fault, FAULT_OUTPUT_TMA))
+                if (u >= TO_NST && !mbar_wait(empty0 + 8 * st, ((u / TO_NST) - 1) & 1, fw, FAULT_OUTPUT_TMA))
                     break;
                 const unsigned fb = full0 + 8 * st;
                 mbar_expect_tx(fb, STAGE);
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(TO_NT, 4) k_output_tma(const __grid_constant__
     const int lane = threadIdx.x & 31;
     for (int u = 0; u < nquads; ++u) {
         const int st = u % TO_NST;
-        if (!mbar_wait(full0 + 8 * st, (u / TO_NST) & 1, P.fault, FAULT_OUTPUT_TMA)) break;
+        if (!mbar_wait(full0 + 8 * st, (u / TO_NST) & 1, fw, FAULT_OUTPUT_TMA)) break;
         const int t = u / QPR, sub = u % QPR;
         const int Yq = S * (jb - 1 + t) + S / 2 + 4 * sub;
         if (active) {
@@ -238,9 +241,14 @@ unsigned *sticky_fault_word()
     static std::mutex mu;
     static std::map<void *, unsigned *> cache;
     CUcontext ctx = nullptr;
-    if (!get_ctx || get_ctx(&ctx) != CUDA_SUCCESS || !ctx) {
-        cudaFree(0);  // make the device's primary context current
-        if (!get_ctx || get_ctx(&ctx) != CUDA_SUCCESS || !ctx) return nullptr;
+    if (!get_ctx) return nullptr;
+    if (get_ctx(&ctx) != CUDA_SUCCESS || !ctx) {
+        void *probe = nullptr;  // the runtime makes the device's primary context current for this lookup
+        if (cudaGetSymbolAddress(&probe, g_wait_faults) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        if (get_ctx(&ctx) != CUDA_SUCCESS || !ctx) return nullptr;
     }
     std::lock_guard<std::mutex> lock(mu);
     auto it = cache.find((void *)ctx);

@@ -2,7 +2,9 @@
 
 ``Server`` owns a context whose scheduler thread admits queued filter requests as stream slots and HBM
 budget free up; their kernels overlap on the GPU.  It keeps every submitted tensor alive until the request's
-outcome has been collected, since the library reads I and p and writes q asynchronously.
+outcome has been collected, since the library reads I and p and writes q asynchronously.  Each submission
+records an event on the stream that produced I and p (the current stream unless given), and the request's
+kernels wait for it, so inputs still being written when submit is called are complete when they are read.
 """
 import ctypes
 
@@ -23,9 +25,12 @@ class Server:
     def clock(self):
         return self.lib.gf_clock()
 
-    def submit(self, I, p, q, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowres=False):
+    def submit(self, I, p, q, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowres=False, fused=0, stream=None,
+               test_wait_fault=False):
         """Queue q = FGF(I, p).  I: (H, W) or (CI, H, W) or (N, CI, H, W) CUDA tensor; p likewise with C
-        channels; q preallocated with the output shape and dtype.  Returns the ticket."""
+        channels; q preallocated with the output shape and dtype.  ``stream``: the stream whose queued work
+        writes I and p (default: the current stream).  ``test_wait_fault``: the timeout-path test hook of
+        gf_opts.test_wait_fault.  Returns the ticket."""
         I4, _ = binding._nchw(I, "I")
         p4, _ = binding._nchw(p, "p")
         N, CI, H, W = I4.shape
@@ -44,6 +49,11 @@ class Server:
         req.opts.p_lowres = int(bool(p_lowres))
         req.opts.dtype_in = _DTYPES[I.dtype]
         req.opts.dtype_out = _DTYPES[q.dtype]
+        req.opts.fused = int(fused)
+        req.opts.test_wait_fault = int(bool(test_wait_fault))
+        ready = torch.cuda.Event()
+        ready.record(stream if stream is not None else torch.cuda.current_stream(I.device))
+        req.ready_event = ready.cuda_event  # captured by gf_submit; the event may go once it returns
         ticket = ctypes.c_uint64()
         binding.check(self.lib.gf_submit(self.ctx.handle, ctypes.byref(req), ctypes.byref(ticket)))
         self._alive[ticket.value] = (I, p, q)
@@ -81,7 +91,7 @@ class Server:
         st = binding.GFServeStats()
         binding.check(self.lib.gf_serve_stats_get(self.ctx.handle, ctypes.byref(st)))
         return {"queued": st.queued, "running": st.running, "slots": st.slots, "budget_bytes": st.budget_bytes,
-                "scratch_in_use": st.scratch_in_use}
+                "scratch_in_use": st.scratch_in_use, "launches": st.launches, "launch_seconds": st.launch_seconds}
 
     def close(self):
         self.ctx.close()

@@ -167,3 +167,45 @@ def test_context_with_queued_work_shuts_down(gf):
     t0 = time.perf_counter()
     srv.close()
     assert time.perf_counter() - t0 < 5.0
+
+
+def test_inputs_written_on_another_stream_are_waited_for(gf):
+    """Inputs still being written when the request is submitted (a long kernel ahead of their copy on the
+    producing stream, no synchronize): the request's kernels wait for the event submit records there."""
+    H, W, C = 600, 800, 3
+    src_I, src_p = _make(H, W, C, torch.float32, 12)
+    ref = gf.fast_guided_filter(src_I, src_p, 8, 1e-2, 4, "bilinear")
+    torch.cuda.synchronize()
+    srv = gf.Server(slots=2)
+    producer = torch.cuda.Stream()
+    I = torch.zeros_like(src_I)
+    p = torch.zeros_like(src_p)
+    q = torch.full((1, C, H, W), float("nan"), device="cuda")
+    with torch.cuda.stream(producer):
+        torch.cuda._sleep(int(0.05 * 2.0e9))  # about 50 ms of GPU time before the inputs are written
+        I.copy_(src_I)
+        p.copy_(src_p)
+        t = srv.submit(I, p, q, 8, 1e-2, 4, "bilinear")  # records its ready event on the producing stream
+    res = srv.poll(t)
+    srv.close()
+    assert res["status"] == gf.GF_OK
+    assert torch.equal(q, ref.view_as(q))
+
+
+def test_request_whose_wait_runs_out_fails_alone(gf):
+    """A request made to give up a bounded wait (gf_opts.test_wait_fault) is reported GF_EWAIT; the requests
+    around it complete normally, and a request after it on the same slot is green."""
+    I, p = _make(512, 1024, 3, torch.float32, 13)
+    ref = gf.fast_guided_filter(I, p, 16, 1e-3, 4, "bilinear", fused=-1)
+    torch.cuda.synchronize()
+    gf.kernel_faults(clear=True)
+    srv = gf.Server(slots=1)
+    qs = [torch.full((1, 3, 512, 1024), -1.0, device="cuda") for _ in range(4)]
+    tickets = [srv.submit(I, p, q, 16, 1e-3, 4, "bilinear", fused=-1, test_wait_fault=(k == 1))
+               for k, q in enumerate(qs)]
+    statuses = [srv.poll(t)["status"] for t in tickets]
+    srv.close()
+    assert statuses == [gf.GF_OK, gf.GF_EWAIT, gf.GF_OK, gf.GF_OK]
+    for k in (0, 2, 3):
+        assert torch.equal(qs[k], ref.view_as(qs[k]))
+    assert gf.kernel_faults(clear=True) & 1
