@@ -557,7 +557,8 @@ def run_serving(local, n_requests=512, slots=4):
     """Seeded Poisson stream of mixed requests (0.3-24 MP, aspect 4:3 / 16:9 / 1:1, 1 or 3 channels,
     r = round(0.004 max(H, W)), eps in {1e-4, 1e-2}, s in {4, 8}, FP16 storage) through gf_submit/gf_poll:
     one-at-a-time launches (gf_filter, each waited for) give the capacity; the loop is then fed all requests
-    at once (saturated) and as Poisson arrivals at 0.5, 0.8 and 1.0 x that capacity.  Request k reads its
+    at once (queued with admission paused, then released: saturated) and as Poisson arrivals at 0.5, 0.8 and
+    1.0 x that capacity, with direct launches and again through per-bucket CUDA graphs.  Request k reads its
     inputs from buffer k mod SERVE_POOL of a pool of distinct images, so requests in flight together never
     share input lines through L2.  The host time the scheduler spends launching a request is reported against
     the p50 latency of the requests under 2 MP."""
@@ -597,48 +598,63 @@ def run_serving(local, n_requests=512, slots=4):
     one_total = sum(service)
     capacity = n_requests / one_total  # requests per second
 
-    srv = gf.Server(device=local, hbm_budget_bytes=8 << 30, slots=slots)
+    def run_mode(graphs):
+        srv = gf.Server(device=local, hbm_budget_bytes=8 << 30, slots=slots, graphs=graphs)
 
-    def run_stream(arrivals):
-        tickets = []
-        st0 = srv.stats()
-        t_start = srv.clock()
-        for a, rq, (I, p, q) in zip(arrivals, reqs, views):
-            while srv.clock() - t_start < a:
-                pass
-            tickets.append(srv.submit(I, p, q, rq["r"], rq["eps"], rq["s"], "bilinear"))
-        res = [srv.poll(t) for t in tickets]
-        assert all(r["status"] == gf.GF_OK for r in res)
-        st1 = srv.stats()
-        lat = np.array([r["t_done"] - r["t_submit"] for r in res]) * 1e3
-        span = max(r["t_done"] for r in res) - t_start
-        launch_us = 1e6 * (st1["launch_seconds"] - st0["launch_seconds"]) / max(1, st1["launches"] - st0["launches"])
-        out = {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-               "mp_per_s": round(total_mp / span, 1), "launch_us_per_request": round(launch_us, 2)}
-        if len(arrivals) == n_requests:
-            p50_small = float(np.percentile(lat[small], 50))
-            out["p50_ms_under_2mp"] = round(p50_small, 3)
-            out["launch_share_of_p50_under_2mp"] = round(launch_us / 1e3 / p50_small, 3)
-        return out
+        def run_stream(arrivals, held=False):
+            """Submit at the given arrival times; held: queue everything with admission paused, then release
+            it (the saturated form: latency counts from the release)."""
+            tickets = []
+            st0 = srv.stats()
+            if held:
+                srv.pause(True)
+            t_start = srv.clock()
+            for a, rq, (I, p, q) in zip(arrivals, reqs, views):
+                while srv.clock() - t_start < a:
+                    pass
+                tickets.append(srv.submit(I, p, q, rq["r"], rq["eps"], rq["s"], "bilinear"))
+            if held:
+                t_start = srv.clock()
+                srv.pause(False)
+            res = [srv.poll(t) for t in tickets]
+            assert all(r["status"] == gf.GF_OK for r in res)
+            st1 = srv.stats()
+            lat = np.array([r["t_done"] - max(r["t_submit"], t_start) for r in res]) * 1e3
+            span = max(r["t_done"] for r in res) - t_start
+            n = max(1, st1["launches"] - st0["launches"])
+            launch_us = 1e6 * (st1["launch_seconds"] - st0["launch_seconds"]) / n
+            out = {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                   "mp_per_s": round(total_mp / span, 1), "launch_us_per_request": round(launch_us, 2),
+                   "graph_launch_share": round((st1["graph_launches"] - st0["graph_launches"]) / n, 3)}
+            if len(arrivals) == n_requests and not held:
+                p50_small = float(np.percentile(lat[small], 50))
+                out["p50_ms_under_2mp"] = round(p50_small, 3)
+                out["launch_share_of_p50_under_2mp"] = round(launch_us / 1e3 / p50_small, 3)
+            return out
 
-    run_stream([0.0] * 16)  # warm the loop
-    saturated = run_stream([0.0] * n_requests)
-    gaps = np.array([rq["arrival_s"] for rq in reqs])
-    loads = []
-    for frac in (0.5, 0.8, 1.0):
-        lam = frac * capacity
-        r = run_stream(list(gaps / lam))
-        r["load"] = frac
-        r["arrival_rate_per_s"] = round(lam, 1)
-        loads.append(r)
-    srv.close()
+        run_stream([0.0] * 64)  # warm the loop (and the graphs of the common buckets)
+        saturated = run_stream([0.0] * n_requests, held=True)
+        gaps = np.array([rq["arrival_s"] for rq in reqs])
+        loads = []
+        for frac in (0.5, 0.8, 1.0):
+            lam = frac * capacity
+            r = run_stream(list(gaps / lam))
+            r["load"] = frac
+            r["arrival_rate_per_s"] = round(lam, 1)
+            loads.append(r)
+        srv.close()
+        return saturated, loads
+
+    saturated, loads = run_mode(False)
+    saturated_graphs, loads_graphs = run_mode(True)
     svc_ms = np.array(service) * 1e3
     return {"requests": n_requests, "slots": slots, "storage": "f16", "total_mp": round(total_mp, 1),
             "inputs": "request k reads buffer k mod %d of a pool of distinct images (1.5 GB), no input shared "
                       "through L2 by requests in flight together" % SERVE_POOL, "requests_under_2mp": int(small.sum()),
             "one_at_a_time": {"mp_per_s": round(total_mp / one_total, 1), "p50_ms": round(float(np.percentile(svc_ms, 50)), 3),
                               "p99_ms": round(float(np.percentile(svc_ms, 99)), 3), "capacity_req_per_s": round(capacity, 1)},
-            "saturated": saturated, "poisson": loads}
+            "saturated": saturated, "poisson": loads,
+            "per_bucket_graphs": {"saturated": saturated_graphs, "poisson": loads_graphs}}
 
 
 # --------------------------------------------------------------------------------------------------------

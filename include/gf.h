@@ -299,8 +299,9 @@ typedef struct gf_result {
 typedef struct gf_serve_stats {
     int queued, running, slots;
     size_t budget_bytes, scratch_in_use;
-    long long launches;      /* requests launched so far */
-    double launch_seconds;   /* host time the scheduler spent enqueuing them (kernels and bookkeeping) */
+    long long launches;        /* requests launched so far */
+    long long graph_launches;  /* of which through their bucket's CUDA graph (gf_serve_graphs) */
+    double launch_seconds;     /* host time the scheduler spent enqueuing them (kernels and bookkeeping) */
 } gf_serve_stats;
 
 /* Monotonic clock of the serving timestamps, in seconds. */
@@ -309,6 +310,14 @@ double gf_clock(void);
 /* Stream slots (concurrent requests, default 4, at most 64) and queue limit (default 4096) of the serving
  * loop.  Only before the first gf_submit on the context (GF_EBUSY afterwards). */
 gf_status gf_serve_config(gf_ctx *ctx, int slots, size_t queue_limit);
+
+/* Per-bucket CUDA graphs for the serving launches: enable = 1 replays the launch sequence of a request
+ * through an executable graph shared by the requests of its bucket on its slot (the same kernels: storage
+ * types, channels, ratio, subsample mode, r', single-kernel or chain form, alignment classes), captured and
+ * updated to the request's sizes and buffers; 0 (the default) launches every request's work directly, which
+ * costs less host time per request on a GB300 host (18 us against 28-34 us for capture, update and graph
+ * launch).  Only before the first gf_submit on the context (GF_EBUSY afterwards). */
+gf_status gf_serve_graphs(gf_ctx *ctx, int enable);
 
 /* Queue a request.  GF_EINVAL for bad arguments, GF_ENOMEM if its scratch can never fit the budget,
  * GF_EBUSY if the queue is full; otherwise GF_OK and *ticket. */

@@ -777,6 +777,12 @@ gf_status gf_cancel(gf_ctx *ctx, uint64_t ticket)
     return gfk::server_cancel(ctx->server, ticket);
 }
 
+gf_status gf_serve_graphs(gf_ctx *ctx, int enable)
+{
+    if (!ctx) return fail(GF_EINVAL, "ctx is NULL");
+    return gfk::server_graphs(ctx->server, enable);
+}
+
 gf_status gf_serve_pause(gf_ctx *ctx, int paused)
 {
     if (!ctx) return fail(GF_EINVAL, "ctx is NULL");

@@ -132,6 +132,7 @@ gf_status server_poll(Server *s, uint64_t ticket, int64_t timeout_us, gf_result 
 gf_status server_cancel(Server *s, uint64_t ticket);
 gf_status server_stats(Server *s, gf_serve_stats *out);
 gf_status server_pause(Server *s, int paused);
+gf_status server_graphs(Server *s, int enable);
 
 // A forward call's arguments, checked and resolved on the host (gf_api.cu).
 struct Resolved {

@@ -17,6 +17,18 @@
 // ahead of the completion callback, and the scheduler reports a request whose word is set as GF_EWAIT.
 // A request's ready_event is waited for on the slot stream before its kernels, so inputs that another
 // stream is still writing are complete when they are read.
+//
+// Per-bucket CUDA graphs (off unless gf_serve_graphs turns them on): requests whose launch sequence has the
+// same kernels -- the same bucket: storage types, channels, ratio, subsample mode, r', the single-kernel or
+// chain form, the alignment classes that pick the vector and TMA kernels -- on the same slot share one
+// executable graph.  The first request of a bucket on a slot is launched directly; later ones are captured
+// on the slot stream, folded into the bucket's executable with cudaGraphExecUpdate (new grid sizes, pointers
+// and arguments) and launched with one cudaGraphLaunch.  An executable is only updated once its previous
+// launch has finished (its last node is the completion callback that frees the slot).  Measured on a GB300
+// host (Grace) with the 512-request FP16 mix: capture, update and graph launch cost 28-34 us of host time per
+// request against 18 us for launching the same work directly, at the same throughput, so direct launches are
+// the default.
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -134,7 +146,11 @@ struct Server {
     bool paused = false;  // admission held (requests stay queued)
     unsigned *fault_host = nullptr;  // pinned, one word per slot: the fault word of the request on that slot
     cudaStream_t ready_stream = nullptr;  // where a request's ready event is captured at submission
-    long long launched = 0;          // requests enqueued, and the host time spent enqueuing them
+    bool use_graphs = false;
+    std::map<std::string, cudaGraphExec_t> graphs;  // bucket + slot -> executable graph
+    std::map<std::string, int> seen;                // buckets launched once directly on a slot
+    long long launched = 0;          // requests enqueued, how many through a graph, the host time spent
+    long long graph_launched = 0;
     double launch_seconds = 0.0;
 };
 
@@ -153,17 +169,33 @@ void CUDART_CB on_done(void *arg)
     s->cv_sched.notify_all();
 }
 
-// Enqueue the request's kernels on its slot (called with the lock held).  Returns the launch status;
-// *launched_some tells whether any kernel was enqueued before a failure.
-gf_status launch_request(Server *s, Request &r, bool *launched_some)
+// The bucket of a request on a slot: everything that decides which kernels its launch sequence has.
+std::string bucket_of(const Request &r, int slot)
+{
+    const Resolved &R = r.R;
+    auto a16 = [](const void *p) { return (int)((reinterpret_cast<uintptr_t>(p) & 15u) == 0); };
+    char key[256];
+    snprintf(key, sizeof(key), "%d|%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d|%d %d %d %d %d|%d %d %d", slot, R.N, R.C,
+             R.CI, R.s, R.sn, R.sd, R.mode, R.dt_in, R.dt_out, R.r_low, (int)R.fused, (int)R.color, (int)R.p_lowres,
+             (int)(R.detail != 0.0f), (int)(r.req.opts.test_wait_fault != 0), R.W % 16, R.W % R.s, R.H % R.s,
+             R.w % 4, (int)(r.req.I == r.req.p), a16(r.req.I), a16(r.req.p), a16(r.req.q));
+    return key;
+}
+
+// Enqueue the request's work on its slot.  Called WITHOUT the server lock: the completion callback of an
+// earlier request takes that lock, and no CUDA call may wait on a callback that waits on us.  Touches only the
+// request, its slot's fault word and the scheduler's own graph tables.  Returns the launch status;
+// *launched_some tells whether any work was enqueued before a failure, *via_graph whether it went through the
+// bucket's graph.
+gf_status launch_request(Server *s, Request &r, bool *launched_some, bool *via_graph)
 {
     NvtxRange range("gf_serve launch");
     *launched_some = false;
+    *via_graph = false;
     if (s->fault_launch >= 0 && s->launches++ == s->fault_launch) {  // injected: nothing is launched
         gf_set_error("injected launch failure (GF_FAULT)");
         return GF_ECUDA;
     }
-    const double t0 = now_seconds();
     char *ws = (char *)s->arena + r.off;
     const FwdPlan P = make_plan(r.R, r.L, r.req.I, r.req.p, r.req.q, ws, &r.req.opts);
     cudaStream_t st = s->streams[r.slot];
@@ -179,12 +211,49 @@ gf_status launch_request(Server *s, Request &r, bool *launched_some)
     }
     *launched_some = true;
     s->fault_host[r.slot] = 0;
-    e = launch_forward(P, st);
-    if (e == cudaSuccess && P.fault.call)
-        e = cudaMemcpyAsync(&s->fault_host[r.slot], P.fault.call, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaLaunchHostFunc(st, on_done, &r);
-    ++s->launched;
-    s->launch_seconds += now_seconds() - t0;
+    // the request's work: its kernels, the copy of its fault word, the completion callback
+    auto enqueue = [&]() {
+        cudaError_t err = launch_forward(P, st);
+        if (err == cudaSuccess && P.fault.call)
+            err = cudaMemcpyAsync(&s->fault_host[r.slot], P.fault.call, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaLaunchHostFunc(st, on_done, &r);
+        return err;
+    };
+    bool done = false;
+    if (s->use_graphs) {
+        const std::string key = bucket_of(r, r.slot);
+        if (s->seen[key]++ > 0) {  // not the bucket's first request on this slot: through its graph
+            cudaGraph_t g = nullptr;
+            cudaError_t ec = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (ec == cudaSuccess) {
+                ec = enqueue();
+                cudaError_t ee = cudaStreamEndCapture(st, &g);
+                if (ec == cudaSuccess) ec = ee;
+            }
+            if (ec == cudaSuccess && g) {
+                cudaGraphExec_t &exec = s->graphs[key];
+                if (exec) {
+                    cudaGraphExecUpdateResultInfo info;
+                    if (cudaGraphExecUpdate(exec, g, &info) != cudaSuccess) {  // not the same kernels after all
+                        cudaGetLastError();
+                        cudaGraphExecDestroy(exec);
+                        exec = nullptr;
+                    }
+                }
+                if (!exec) ec = cudaGraphInstantiate(&exec, g, 0);
+                if (ec == cudaSuccess) {
+                    ec = cudaGraphLaunch(exec, st);
+                    done = (ec == cudaSuccess);
+                    *via_graph = done;
+                } else {
+                    exec = nullptr;
+                }
+            }
+            if (g) cudaGraphDestroy(g);
+            if (!done) cudaGetLastError();  // nothing of the request was enqueued: launch it directly
+        }
+    }
+    if (!done) e = enqueue();
     if (e != cudaSuccess) {
         gf_set_error(std::string("serving launch: ") + cudaGetErrorString(e));
         return GF_ECUDA;
@@ -196,6 +265,7 @@ void scheduler(Server *s)
 {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lock(s->mu);
+    std::vector<std::shared_ptr<Request>> admitted;
     while (true) {
         // retire finished requests: free their slot and scratch
         for (int k = 0; k < s->nslots; ++k) {
@@ -214,6 +284,7 @@ void scheduler(Server *s)
             }
         }
         // admit from the head of the queue while a slot is free and the scratch fits
+        admitted.clear();
         while (!s->paused && !s->queue.empty()) {
             const uint64_t t = s->queue.front();
             auto it = s->reqs.find(t);
@@ -234,26 +305,44 @@ void scheduler(Server *s)
             r.t_admit = now_seconds();
             r.state = RUNNING;
             s->slot_owner[slot] = t;
-            bool launched_some = false;
-            const gf_status st = launch_request(s, r, &launched_some);
-            if (st != GF_OK) {
-                if (launched_some) {
-                    // Kernels of the request may still be running: wait for them before the scratch is reused.
-                    // Never with the lock held: an earlier request's completion callback on this stream may be
-                    // waiting for it.
-                    auto keep = it->second;
-                    lock.unlock();
-                    cudaStreamSynchronize(s->streams[slot]);
+            admitted.push_back(it->second);
+        }
+        // launch them with the lock released (their state is RUNNING: nothing else touches them meanwhile)
+        if (!admitted.empty()) {
+            struct Outcome {
+                gf_status st;
+                bool via_graph;
+            };
+            std::vector<Outcome> outcome(admitted.size());
+            lock.unlock();
+            double launch_s = 0.0;
+            for (size_t k = 0; k < admitted.size(); ++k) {
+                Request &r = *admitted[k];
+                bool launched_some = false;
+                const double t0 = now_seconds();
+                outcome[k].st = launch_request(s, r, &launched_some, &outcome[k].via_graph);
+                launch_s += now_seconds() - t0;
+                if (outcome[k].st != GF_OK && launched_some) {
+                    // work of the request may still be running: wait for it before the scratch is reused
+                    cudaStreamSynchronize(s->streams[r.slot]);
                     cudaGetLastError();
-                    lock.lock();
                 }
+            }
+            lock.lock();
+            s->launched += (long long)admitted.size();
+            s->launch_seconds += launch_s;
+            for (size_t k = 0; k < admitted.size(); ++k) {
+                Request &r = *admitted[k];
+                s->graph_launched += outcome[k].via_graph ? 1 : 0;
+                if (outcome[k].st == GF_OK) continue;
                 r.state = FAILED;
-                r.status = st;
+                r.status = outcome[k].st;
                 r.t_done.store(now_seconds());
                 s->alloc.release(r.off, r.L.total);
-                s->slot_owner[slot] = 0;
+                s->slot_owner[r.slot] = 0;
                 s->cv_done.notify_all();
             }
+            continue;  // requests may have finished meanwhile: retire and admit again before waiting
         }
         bool running = false;
         for (int k = 0; k < s->nslots; ++k) running |= (s->slot_owner[k] != 0);
@@ -332,6 +421,8 @@ void server_destroy(Server *s)
             cudaStreamDestroy(st);
         }
         if (s->ready_stream) cudaStreamDestroy(s->ready_stream);
+        for (auto &kv : s->graphs)
+            if (kv.second) cudaGraphExecDestroy(kv.second);
         if (s->arena) cudaFree(s->arena);
         if (s->fault_host) cudaFreeHost(s->fault_host);
         cudaSetDevice(prev);
@@ -465,6 +556,17 @@ gf_status server_cancel(Server *s, uint64_t ticket)
     return GF_OK;
 }
 
+gf_status server_graphs(Server *s, int enable)
+{
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->started) {
+        gf_set_error("gf_serve_graphs must be called before the first gf_submit");
+        return GF_EBUSY;
+    }
+    s->use_graphs = enable != 0;
+    return GF_OK;
+}
+
 gf_status server_pause(Server *s, int paused)
 {
     std::lock_guard<std::mutex> lock(s->mu);
@@ -486,6 +588,7 @@ gf_status server_stats(Server *s, gf_serve_stats *out)
     out->scratch_in_use = s->alloc.in_use();
     out->slots = s->nslots;
     out->launches = s->launched;
+    out->graph_launches = s->graph_launched;
     out->launch_seconds = s->launch_seconds;
     return GF_OK;
 }

@@ -16,10 +16,12 @@ _DTYPES = {torch.float32: binding.GF_F32, torch.float16: binding.GF_F16, torch.u
 
 
 class Server:
-    def __init__(self, device=None, hbm_budget_bytes=0, slots=4, queue_limit=0):
+    def __init__(self, device=None, hbm_budget_bytes=0, slots=4, queue_limit=0, graphs=False):
+        """``graphs``: replay each request's launches through its bucket's CUDA graph (gf_serve_graphs)."""
         self.ctx = binding.Context(device, hbm_budget_bytes)
         self.lib = binding.load_library()
         binding.check(self.lib.gf_serve_config(self.ctx.handle, int(slots), int(queue_limit)))
+        binding.check(self.lib.gf_serve_graphs(self.ctx.handle, int(bool(graphs))))
         self._alive = {}
 
     def clock(self):
@@ -91,7 +93,8 @@ class Server:
         st = binding.GFServeStats()
         binding.check(self.lib.gf_serve_stats_get(self.ctx.handle, ctypes.byref(st)))
         return {"queued": st.queued, "running": st.running, "slots": st.slots, "budget_bytes": st.budget_bytes,
-                "scratch_in_use": st.scratch_in_use, "launches": st.launches, "launch_seconds": st.launch_seconds}
+                "scratch_in_use": st.scratch_in_use, "launches": st.launches, "graph_launches": st.graph_launches,
+                "launch_seconds": st.launch_seconds}
 
     def close(self):
         self.ctx.close()

@@ -51,20 +51,27 @@ MIX = [  # (H, W, C, r, eps, s, mode, dtype)
 ]
 
 
-def test_mixed_requests_equal_their_solo_results(gf):
+@pytest.mark.parametrize("graphs", [True, False], ids=["graphs", "direct"])
+def test_mixed_requests_equal_their_solo_results(gf, graphs):
+    """Every request of the mix equals its solo gf_filter result bit for bit, with the per-bucket graphs (the
+    mix runs twice, so the second pass replays updated graphs) and with direct launches."""
     inputs = [_make(H, W, C, dt, 100 + k) for k, (H, W, C, r, e, s, m, dt) in enumerate(MIX)]
     refs = []
     for (I, p), (H, W, C, r, e, s, m, dt) in zip(inputs, MIX):
         refs.append(gf.fast_guided_filter(I, p, r, e, s, m))
     torch.cuda.synchronize()
-    srv = gf.Server(slots=4)
+    srv = gf.Server(slots=4, graphs=graphs)
     outs, tickets = [], []
-    for (I, p), (H, W, C, r, e, s, m, dt), ref in zip(inputs, MIX, refs):
-        q = torch.full_like(ref, float("nan"))
-        outs.append(q)
-        tickets.append(srv.submit(I, p, q, r, e, s, m))
+    for rep in range(2):
+        for (I, p), (H, W, C, r, e, s, m, dt), ref in zip(inputs, MIX, refs):
+            q = torch.full_like(ref, float("nan"))
+            outs.append(q)
+            tickets.append(srv.submit(I, p, q, r, e, s, m))
+    refs = refs + refs
     results = [srv.poll(t) for t in tickets]
+    stats = srv.stats()
     srv.close()
+    assert (stats["graph_launches"] > 0) == graphs and stats["launches"] == len(tickets)
     assert all(res["status"] == gf.GF_OK for res in results)
     for q, ref in zip(outs, refs):
         assert torch.equal(q, ref)
