@@ -29,8 +29,10 @@ namespace gfk {
 
 namespace {
 
-constexpr int BX_NT = 256;  // threads per CTA
-constexpr int BX_TH = 32;   // output rows per tile
+// Output rows per tile (TH) and threads per CTA: tall tiles (32 rows, 256 threads) at large radii, whose
+// vertical halo of 2 r' rows they amortise; short ones (16 rows, 128 threads, about 6 CTAs per SM) at small
+// radii, where the tiles' short latency chains and the CTAs' number decide.
+__host__ __device__ constexpr int nt_of(int TH) { return TH == 16 ? 128 : 256; }
 constexpr int BX_TW = 64;   // output columns per tile
 constexpr int BX_RH = 8;    // outputs per phase-2 thread (a run of one row)
 
@@ -39,9 +41,11 @@ enum { BK_STATS = 0, BK_MEAN2 = 2, BK_MEAN2_OUT = 3 };
 struct BoxTmaParams {
     float *out0, *out1;  // BK_STATS: a, b; BK_MEAN2: mean_a, mean_b (plane stride ops)
     size_t ops;
-    int C, CX;           // Y planes per image (channels); X planes per image (1 or C)
+    int N, C, CX;        // images; Y planes per image (channels); X planes per image (1 or C)
     int h, w, r;         // plane size; radius (used when the kernel's RC < 0)
     float eps;
+    float *stats;        // BK_STATS, optional: 4 dense h*w planes per (n, c) of window means (mean_I, corr_I,
+                         // mean_p, corr_Ip), kept for the backward
     // BK_MEAN2_OUT (s = 1): q = mean_a I + mean_b on rows [Yw0, Yw1) of the guide I (plane stride fps, one or
     // C planes per image) into q (dtype dt_out), with the detail epilogue q + k (I - q) when detail != 0
     const float *I;
@@ -58,10 +62,10 @@ __host__ __device__ constexpr int round4(int v) { return (v + 3) & ~3; }
 struct BoxSmem {
     int BW, BH, span, off, VP;
     size_t x_bytes, v_off, bar_off, total;
-    __host__ __device__ BoxSmem(int r, int CB, int NP)
+    __host__ __device__ BoxSmem(int r, int CB, int NP, int TH)
     {
         BW = BX_TW + 2 * round4(r);  // TMA box width: starts at x0 - round4(r), a multiple of 4 columns
-        BH = BX_TH + 2 * r;
+        BH = TH + 2 * r;
         span = BX_TW + 2 * r;        // tile columns with vertical sums (tile column -r .. 63 + r)
         off = round4(r) - r;         // box column of tile column -r
         VP = span | 1;               // column-sum pitch in float2 (odd: conflict-free column reads)
@@ -150,14 +154,15 @@ __device__ __forceinline__ void walk_column(float2 &S0, float2 &S1, const float 
     }
 }
 
-template <int KIND, int RC, int CB, typename TQ>
-__global__ void __launch_bounds__(BX_NT, 3) k_box_tma(const __grid_constant__ CUtensorMap tmX,
+template <int KIND, int RC, int CB, int TH, typename TQ>
+__global__ void __launch_bounds__(nt_of(TH), TH == 16 ? 6 : 3) k_box_tma(const __grid_constant__ CUtensorMap tmX,
                                                    const __grid_constant__ CUtensorMap tmY, BoxTmaParams P)
 {
     constexpr int NP = (KIND == BK_STATS) ? 2 : 1;  // float2 pairs of window sums
-    static_assert(BX_TH % CB == 0 && CB * (BX_TW / BX_RH) <= BX_NT, "column-sum blocks");
+    constexpr int NT = nt_of(TH);
+    static_assert(TH % CB == 0 && CB * (BX_TW / BX_RH) <= NT, "column-sum blocks");
     const int r = RC >= 0 ? RC : P.r;
-    const BoxSmem L(r, CB, NP);
+    const BoxSmem L(r, CB, NP, TH);
     const int BW = L.BW, BH = L.BH, VP = L.VP;
     extern __shared__ __align__(128) unsigned char sm[];
     float *Xs = reinterpret_cast<float *>(sm);
@@ -166,7 +171,7 @@ __global__ void __launch_bounds__(BX_NT, 3) k_box_tma(const __grid_constant__ CU
     const unsigned bar = smem_u32(sm + L.bar_off);
     const int tid = threadIdx.x;
     const int c = blockIdx.x % P.C, tx = blockIdx.x / P.C, n = blockIdx.z;
-    const int x0 = tx * BX_TW, y0 = blockIdx.y * BX_TH;
+    const int x0 = tx * BX_TW, y0 = blockIdx.y * TH;
     const int plane = n * P.C + c, xplane = n * P.CX + (P.CX == 1 ? 0 : c);
     const int h = P.h, w = P.w;
 
@@ -186,10 +191,10 @@ __global__ void __launch_bounds__(BX_NT, 3) k_box_tma(const __grid_constant__ CU
 
     // the shift: the tile's first output pixel (always inside the image)
     const float2 cs = make_float2(Xs[r * BW + round4(r)], Ys[r * BW + round4(r)]);
-    const bool interior = (x0 - r >= 0) && (x0 + BX_TW + r <= w) && (y0 - r >= 0) && (y0 + BX_TH + r <= h);
+    const bool interior = (x0 - r >= 0) && (x0 + BX_TW + r <= w) && (y0 - r >= 0) && (y0 + TH + r <= h);
     if (!interior) {  // out-of-image cells take the shift, so their shifted values are exactly zero
         const int t_lo = r - y0, t_hi = h - y0 + r, u_lo = round4(r) - x0, u_hi = w - x0 + round4(r);
-        for (int idx = tid; idx < BH * BW; idx += BX_NT) {
+        for (int idx = tid; idx < BH * BW; idx += NT) {
             const int t = idx / BW, u = idx - t * BW;
             if (t < t_lo || t >= t_hi || u < u_lo || u >= u_hi) {
                 Xs[idx] = cs.x;
@@ -223,7 +228,7 @@ __global__ void __launch_bounds__(BX_NT, 3) k_box_tma(const __grid_constant__ CU
 
     const float n_full = (float)((2 * r + 1) * (2 * r + 1));
     const float inv_full = 1.0f / n_full;
-    const int nblocks = BX_TH / CB;
+    const int nblocks = TH / CB;
     for (int b = 0; b < nblocks; ++b) {
         // ---- phase 1: vertical window sums of the block's rows
         if (walker) walk_column<NP, RC, CB>(S0w, S1w, px, py, BW, cs, r, b, vcol, VP);
@@ -255,6 +260,8 @@ __global__ void __launch_bounds__(BX_NT, 3) k_box_tma(const __grid_constant__ CU
                 }
                 const int ny = min(h - 1, y + r) - max(0, y - r) + 1;
                 float o0[8], o1[8];
+                const bool with_stats = (KIND == BK_STATS) && P.stats != nullptr;
+                float wst[(KIND == BK_STATS && TH == 16) ? 4 : 1][8];
 #pragma unroll
                 for (int j = 0; j < BX_RH; ++j) {
                     if (j > 0) {
@@ -275,6 +282,21 @@ __global__ void __launch_bounds__(BX_NT, 3) k_box_tma(const __grid_constant__ CU
                         const float a = __fdividef(cov, var + P.eps);            // a, Eq. (2)
                         o0[j] = a;
                         o1[j] = (m0.y + cs.y) - a * (m0.x + cs.x);               // b, Eq. (3)
+                        if (with_stats) {  // the window means the backward reads
+                            const float st4[4] = {m0.x + cs.x,                                  // mean_I
+                                                  m1.x + cs.x * (2.0f * m0.x + cs.x),           // corr_I
+                                                  m0.y + cs.y,                                  // mean_p
+                                                  m1.y + cs.x * m0.y + cs.y * m0.x + cs.x * cs.y};  // corr_Ip
+                            if constexpr (TH == 16) {  // kept for 128-bit stores after the run
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) wst[k][j] = st4[k];
+                            } else if (x + j < w) {    // tall tiles (large radii): stored at once, fewer registers
+                                const size_t ps = (size_t)h * w;
+                                float *stp = P.stats + (size_t)plane * 4 * ps + (size_t)y * w + x + j;
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) stp[k * ps] = st4[k];
+                            }
+                        }
                     } else {
                         o0[j] = m0.x + cs.x;  // mean_a
                         o1[j] = m0.y + cs.y;  // mean_b
@@ -292,6 +314,14 @@ __global__ void __launch_bounds__(BX_NT, 3) k_box_tma(const __grid_constant__ CU
                     const size_t o = (size_t)plane * P.ops + (size_t)y * w + x;
                     store8<float>(P.out0 + o, second, o0);
                     store8<float>(P.out1 + o, second, o1);
+                    if constexpr (KIND == BK_STATS && TH == 16) {
+                        if (with_stats) {
+                            const size_t ps = (size_t)h * w;
+                            float *st = P.stats + (size_t)plane * 4 * ps + (size_t)y * w + x;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) store8<float>(st + k * ps, second, wst[k]);
+                        }
+                    }
                 }
             }
         }
@@ -305,42 +335,48 @@ namespace {
 
 // Column-sum rows per block: the whole tile height, except for the statistics at r' > 8, whose two pairs of
 // column sums would otherwise keep the CTA above 74 KB of shared memory (three CTAs per SM).
-constexpr int cb_of(int r, int NP) { return (r > 8 && NP == 2) ? 16 : 32; }
+// Tile height and column-sum rows per block: tall tiles above r' = 8, with two blocks of 16 rows for the
+// statistics (two pairs of column sums would otherwise keep the CTA above 74 KB of shared memory, three CTAs per
+// SM); 16-row tiles, one block, up to r' = 8.
+constexpr int th_of(int r) { return r > 8 ? 32 : 16; }
+constexpr int cb_of(int r, int NP) { return (r > 8 && NP == 2) ? 16 : th_of(r); }
 
-template <int KIND, int RC, int CB, typename TQ>
-cudaError_t launch_one(const CUtensorMap &mx, const CUtensorMap &my, const BoxTmaParams &P, dim3 grid, int r,
-                       cudaStream_t st)
+template <int KIND, int RC, int CB, int TH, typename TQ>
+cudaError_t launch_one(const CUtensorMap &mx, const CUtensorMap &my, const BoxTmaParams &P, int r, cudaStream_t st)
 {
-    const size_t smem = BoxSmem(r, CB, KIND == BK_STATS ? 2 : 1).total;
-    cudaError_t e = opt_in_smem(k_box_tma<KIND, RC, CB, TQ>, smem);
+    const size_t smem = BoxSmem(r, CB, KIND == BK_STATS ? 2 : 1, TH).total;
+    cudaError_t e = opt_in_smem(k_box_tma<KIND, RC, CB, TH, TQ>, smem);
     if (e != cudaSuccess) return e;
-    k_box_tma<KIND, RC, CB, TQ><<<grid, BX_NT, smem, st>>>(mx, my, P);
+    // the channel is the fastest block index: the channel CTAs of a tile share its guide tile through L2
+    const dim3 grid(P.C * ((P.w + BX_TW - 1) / BX_TW), (P.h + TH - 1) / TH, P.N);
+    k_box_tma<KIND, RC, CB, TH, TQ><<<grid, nt_of(TH), smem, st>>>(mx, my, P);
     return cudaGetLastError();
 }
 
 // The radius as a compile-time constant for the common radii (s = 4 and 8 at the paper's figure radii,
 // serving's r' <= 8, s = 1 at r = 8 and 16, the feathering figure's r' = 15), else at run time.
 template <int KIND, typename TQ>
-cudaError_t launch_kind(const CUtensorMap &mx, const CUtensorMap &my, const BoxTmaParams &P, dim3 grid,
-                        cudaStream_t st)
+cudaError_t launch_kind(const CUtensorMap &mx, const CUtensorMap &my, const BoxTmaParams &P, cudaStream_t st)
 {
     constexpr int NP = KIND == BK_STATS ? 2 : 1;
     const int r = P.r;
+#define GF_BOX_R(RR) launch_one<KIND, RR, cb_of(RR, NP), th_of(RR), TQ>(mx, my, P, r, st)
     switch (r) {
-    case 1: return launch_one<KIND, 1, cb_of(1, NP), TQ>(mx, my, P, grid, r, st);
-    case 2: return launch_one<KIND, 2, cb_of(2, NP), TQ>(mx, my, P, grid, r, st);
-    case 3: return launch_one<KIND, 3, cb_of(3, NP), TQ>(mx, my, P, grid, r, st);
-    case 4: return launch_one<KIND, 4, cb_of(4, NP), TQ>(mx, my, P, grid, r, st);
-    case 5: return launch_one<KIND, 5, cb_of(5, NP), TQ>(mx, my, P, grid, r, st);
-    case 6: return launch_one<KIND, 6, cb_of(6, NP), TQ>(mx, my, P, grid, r, st);
-    case 7: return launch_one<KIND, 7, cb_of(7, NP), TQ>(mx, my, P, grid, r, st);
-    case 8: return launch_one<KIND, 8, cb_of(8, NP), TQ>(mx, my, P, grid, r, st);
-    case 15: return launch_one<KIND, 15, cb_of(15, NP), TQ>(mx, my, P, grid, r, st);
-    case 16: return launch_one<KIND, 16, cb_of(16, NP), TQ>(mx, my, P, grid, r, st);
+    case 1: return GF_BOX_R(1);
+    case 2: return GF_BOX_R(2);
+    case 3: return GF_BOX_R(3);
+    case 4: return GF_BOX_R(4);
+    case 5: return GF_BOX_R(5);
+    case 6: return GF_BOX_R(6);
+    case 7: return GF_BOX_R(7);
+    case 8: return GF_BOX_R(8);
+    case 15: return GF_BOX_R(15);
+    case 16: return GF_BOX_R(16);
     default: break;
     }
-    if (r <= 8) return launch_one<KIND, -1, cb_of(8, NP), TQ>(mx, my, P, grid, r, st);
-    return launch_one<KIND, -1, cb_of(16, NP), TQ>(mx, my, P, grid, r, st);
+#undef GF_BOX_R
+    if (r <= 8) return launch_one<KIND, -1, cb_of(8, NP), th_of(8), TQ>(mx, my, P, r, st);
+    return launch_one<KIND, -1, cb_of(16, NP), th_of(16), TQ>(mx, my, P, r, st);
 }
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -354,7 +390,7 @@ bool box_tma_supported(const BoxTmaJob &J)
     if (J.kind == BOX_JOB_MEANS_OUTPUT) {
         if (!aligned16(J.I) || !aligned16(J.q) || J.fps % 4 != 0) return false;
         if (J.dt_out != F32 && J.dt_out != F16) return false;
-    } else if (!aligned16(J.out0) || !aligned16(J.out1) || J.ops % 4 != 0) {
+    } else if (!aligned16(J.out0) || !aligned16(J.out1) || J.ops % 4 != 0 || (J.stats && !aligned16(J.stats))) {
         return false;
     }
     if (getenv("GF_NO_TMA_BOX") != nullptr) return false;  // the per-thread-load box kernels instead (tests)
@@ -364,7 +400,7 @@ bool box_tma_supported(const BoxTmaJob &J)
 
 cudaError_t launch_box_tma(const BoxTmaJob &J, cudaStream_t st)
 {
-    const BoxSmem L(J.r, 32, 1);
+    const BoxSmem L(J.r, 32, 1, th_of(J.r));
     CUtensorMap mx, my;
     if (!encode_tmap_3d(&mx, F32, J.X, J.w, J.h, J.N * J.CX, J.xps, L.BW, L.BH) ||
         !encode_tmap_3d(&my, F32, J.Y, J.w, J.h, J.N * J.C, J.yps, L.BW, L.BH))
@@ -373,12 +409,14 @@ cudaError_t launch_box_tma(const BoxTmaJob &J, cudaStream_t st)
     P.out0 = J.out0;
     P.out1 = J.out1;
     P.ops = J.ops;
+    P.N = J.N;
     P.C = J.C;
     P.CX = J.CX;
     P.h = J.h;
     P.w = J.w;
     P.r = J.r;
     P.eps = J.eps;
+    P.stats = J.stats;
     P.I = J.I;
     P.q = J.q;
     P.fps = J.fps;
@@ -387,14 +425,12 @@ cudaError_t launch_box_tma(const BoxTmaJob &J, cudaStream_t st)
     P.Yw1 = J.Yw1;
     P.detail = J.detail;
     P.fault = J.fault;
-    // the channel is the fastest block index: the channel CTAs of a tile share its guide tile through L2
-    const dim3 grid(J.C * ((J.w + BX_TW - 1) / BX_TW), (J.h + BX_TH - 1) / BX_TH, J.N);
     switch (J.kind) {
-    case BOX_JOB_STATS: return launch_kind<BK_STATS, float>(mx, my, P, grid, st);
-    case BOX_JOB_MEANS: return launch_kind<BK_MEAN2, float>(mx, my, P, grid, st);
+    case BOX_JOB_STATS: return launch_kind<BK_STATS, float>(mx, my, P, st);
+    case BOX_JOB_MEANS: return launch_kind<BK_MEAN2, float>(mx, my, P, st);
     default:
-        if (J.dt_out == F16) return launch_kind<BK_MEAN2_OUT, __half>(mx, my, P, grid, st);
-        return launch_kind<BK_MEAN2_OUT, float>(mx, my, P, grid, st);
+        if (J.dt_out == F16) return launch_kind<BK_MEAN2_OUT, __half>(mx, my, P, st);
+        return launch_kind<BK_MEAN2_OUT, float>(mx, my, P, st);
     }
 }
 

@@ -1320,12 +1320,12 @@ bool aligned_vec_subsample(const FwdPlan &P)
 
 }  // namespace
 
-// Where the TMA-fed box kernels (gf_box.cu) are taken when they accept the planes: at full resolution (s = 1) and
-// at r' > 8.  Measured on one GB300: at s = 1 (12 MP, r = 16) the whole call takes 0.47 ms against 0.90 ms with the
-// per-thread-load kernels, and the feathering figure's r' = 15 (12 MP, s = 4) 38 us against 47 us; at r' <= 8 on
-// low-res planes, which stay in L2, the per-thread-load kernels overlap better with the other stream's HBM-bound
-// kernels (12 MP, s = 4, two images in flight: 177 k against 169 k MP/s) and serve small requests faster.
-static bool box_tma_pays(int s, int r_low) { return s == 1 || r_low > 8; }
+// The TMA-fed box kernels (gf_box.cu) take every box step whose planes they accept (FP32 planes with rows of a
+// multiple of 4 floats, r' <= 16, no window statistics kept for the backward).  Measured on one GB300 against
+// the per-thread-load kernels: 12 MP at s = 1 (r = 16) 0.45 against 0.90 ms per call; at s = 4 (r' = 4) the
+// statistics 13.9 against 17.1 us and the box means 12.1 against 12.9 us (two images in flight: 178 k against
+// 177 k MP/s); the feathering figure's r' = 15 at s = 4 38 against 47 us.
+static bool box_tma_pays(int, int) { return true; }
 
 bool s1_means_output_form(const Resolved &R)
 {
@@ -1493,9 +1493,9 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         J.N = P.N; J.C = P.C; J.CX = P.CI;
         J.h = P.h; J.w = P.w; J.r = P.r_low; J.eps = P.eps;
         J.out0 = P.a; J.out1 = P.b; J.ops = P.lps;
+        J.stats = P.int_stats ? nullptr : (float *)P.stats;
         J.fault = P.fault;
-        const bool tma = !P.int_stats && !P.stats && src_dt == F32 && box_tma_pays(P.s, P.r_low) &&
-                         box_tma_supported(J);
+        const bool tma = !P.int_stats && src_dt == F32 && box_tma_pays(P.s, P.r_low) && box_tma_supported(J);
         tm.before();
         if (tma) {
             err = launch_box_tma(J, st);

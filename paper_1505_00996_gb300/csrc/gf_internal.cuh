@@ -209,6 +209,7 @@ struct BoxTmaJob {
     float eps;
     float *out0, *out1;  // STATS: a, b; MEANS: mean_a, mean_b
     size_t ops;
+    float *stats;        // STATS, optional: the FP32 window means of the backward (4 dense h*w planes per plane)
     // MEANS_OUTPUT: the full-res guide I (CI planes per image, FP32, plane stride fps), the output q (dt_out),
     // the rows [Yw0, Yw1) written, the detail gain
     const float *I;

@@ -2,11 +2,11 @@
 
 Those kernels take Algorithm 2's box statistics with the coefficients of Eq. 2-3, the box means of a and b,
 and at s = 1 the box means fused with the output of Eq. 4 (the upsample is the identity there), when the
-planes' rows are a multiple of 4 floats and r' <= 16, at s = 1 and at r' > 8 (the per-thread-load kernels
-take r' <= 8 on low-res planes).  Each radius 0..16 is run at s = 1 (every radius through the TMA kernels)
-and s = 4 (both families) on images whose tiles are all border tiles and on images with interior tiles, with
-batch, depthwise guides, FP16 output, the detail epilogue and row ranges; the same calls with the TMA kernels
-switched off (GF_NO_TMA_BOX) must agree with the oracle too.  Tolerance: max-abs 1e-4 (FP32), 2e-3 (FP16).
+planes' rows are a multiple of 4 floats and r' <= 16 (16-row tiles up to r' = 8, 32-row tiles above).  Each
+radius 0..16 is run at s = 1 and s = 4 on images whose tiles are all border tiles and on images with interior
+tiles, with batch, depthwise guides, FP16 output, the detail epilogue and row ranges; the same calls with the
+TMA kernels switched off (GF_NO_TMA_BOX: the per-thread-load kernels) must agree with the oracle too.
+Tolerance: max-abs 1e-4 (FP32), 2e-3 (FP16).
 """
 import numpy as np
 import pytest
@@ -47,8 +47,7 @@ def test_s1_every_radius(gf, r):
 
 @pytest.mark.parametrize("rl", list(range(0, 17)))
 def test_s4_every_lowres_radius(gf, rl):
-    """s = 4 with r' given explicitly: the statistics and box-mean kernels on a 70 x 132 low-res grid (TMA
-    kernels above r' = 8, per-thread-load kernels up to it)."""
+    """s = 4 with r' given explicitly: the statistics and box-mean kernels on a 70 x 132 low-res grid."""
     I = _rand((1, 1, 280, 528), 30 + rl)
     p = _rand((1, 3, 280, 528), 40 + rl)
     q = _run(gf, I, p, 4 * rl, 1e-3, 4, r_low=rl, fused=-1)
@@ -140,8 +139,8 @@ def test_with_and_without_tma(gf, monkeypatch, s, r, W):
 
 
 def test_intermediates_through_tma(gf):
-    """a, b and their box means written by the TMA kernels into caller buffers (w % 4 == 0) match the
-    oracle's intermediates."""
+    """a, b, their box means and the window means written by the TMA kernels into caller buffers (w % 4 == 0)
+    match the oracle's intermediates."""
     H, W, r, eps, s = 128, 512, 16, 1e-2, 4
     I = _rand((1, 1, H, W), 97)
     p = _rand((1, 2, H, W), 98)
@@ -149,12 +148,14 @@ def test_intermediates_through_tma(gf):
     dev = torch.device("cuda")
     a = torch.empty((1, 2, h, w), device=dev)
     b, ma, mb = torch.empty_like(a), torch.empty_like(a), torch.empty_like(a)
+    st = torch.empty((1, 2, 4, h, w), device=dev)
     q = gf.fast_guided_filter(torch.from_numpy(I).cuda(), torch.from_numpy(p).cuda(), r, eps, s, "bilinear",
-                              a_out=a, b_out=b, mean_a_out=ma, mean_b_out=mb, fused=-1)
+                              a_out=a, b_out=b, mean_a_out=ma, mean_b_out=mb, stats_out=st, fused=-1)
     torch.cuda.synchronize()
     ref_q, inter = oracle.fast_guided_filter(I.astype(np.float64), p.astype(np.float64), r, eps, s,
                                              oracle.SUB_BILINEAR, intermediates=True)
     assert max_abs(q.cpu(), ref_q) <= TOL_F32
+    assert max_abs(st.cpu(), inter["stats"]) <= 2e-6  # mean_I, corr_I, mean_p, corr_Ip
     # an absolute error e in the window statistics moves a by about e / eps
     tol = 2e-6 / eps * 10
     assert max_abs(a.cpu(), inter["a"]) <= tol and max_abs(b.cpu(), inter["b"]) <= tol
