@@ -277,8 +277,10 @@ __global__ void __launch_bounds__(nt_of(TH), TH == 16 ? 6 : 3) k_box_tma(const _
                     const float2 m0 = mul2(S0, make_float2(inv, inv));
                     if (KIND == BK_STATS) {
                         const float2 m1 = mul2(S1, make_float2(inv, inv));
-                        const float var = fmaxf(fmaf(-m0.x, m0.x, m1.x), 0.0f);  // var_I
-                        const float cov = fmaf(-m0.x, m0.y, m1.y);               // cov_Ip
+                        // var_I and cov_Ip; a one-sample window (r' = 0) has both exactly 0 (Eq. 2 then gives a = 0),
+                        // where the shifted sums would leave the rounding of the square, amplified by 1 / eps
+                        const float var = r ? fmaxf(fmaf(-m0.x, m0.x, m1.x), 0.0f) : 0.0f;
+                        const float cov = r ? fmaf(-m0.x, m0.y, m1.y) : 0.0f;
                         const float a = __fdividef(cov, var + P.eps);            // a, Eq. (2)
                         o0[j] = a;
                         o1[j] = (m0.y + cs.y) - a * (m0.x + cs.x);               // b, Eq. (3)

@@ -512,8 +512,9 @@ __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile(BoxParams P)
                 const float inv = __fdividef(1.0f, (float)cnt);
                 const float mI = (S[0] + Sc[0]) * inv, mp = (S[2] + Sc[2]) * inv;  // shifted means
                 const float eII = (S[1] + Sc[1]) * inv, eIp = (S[3] + Sc[3]) * inv;
-                const float var = fmaxf(eII - mI * mI, 0.0f);  // var_I
-                const float cov = eIp - mI * mp;               // cov_Ip
+                // var_I, cov_Ip: exactly 0 for a one-sample window (r' = 0), where Eq. 2 gives a = 0
+                const float var = r ? fmaxf(eII - mI * mI, 0.0f) : 0.0f;
+                const float cov = r ? eIp - mI * mp : 0.0f;
                 o0 = __fdividef(cov, var + P.eps);             // a, Eq. (2)
                 o1 = (mp + cy) - o0 * (mI + cx);               // b, Eq. (3)
                 if (P.stats) {
@@ -747,8 +748,9 @@ __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile_x2(BoxParams P)
             } else if (KIND == KIND_STATS_F) {
                 const float mI = S[0].x * inv, mp = S[0].y * inv;    // shifted means
                 const float eII = S[1].x * inv, eIp = S[1].y * inv;
-                const float var = fmaxf(eII - mI * mI, 0.0f);      // var_I
-                const float cov = eIp - mI * mp;                   // cov_Ip
+                // var_I, cov_Ip: exactly 0 for a one-sample window (r' = 0), where Eq. 2 gives a = 0
+                const float var = r ? fmaxf(eII - mI * mI, 0.0f) : 0.0f;
+                const float cov = r ? eIp - mI * mp : 0.0f;
                 o0 = __fdividef(cov, var + P.eps);                 // a, Eq. (2)
                 o1 = (mp + shift.y) - o0 * (mI + shift.x);         // b, Eq. (3)
                 if (P.stats) {  // staged, written as coalesced rows in phase 3

@@ -120,7 +120,8 @@ __global__ void __launch_bounds__(FU_NT) k_fgf_fused(FusedParams P)
         }
         const float inv = 1.0f / (float)((min(h - 1, ja + r) - max(0, ja - r) + 1) * (kb - ka + 1));
         const float mI = s0 * inv, mp = s1 * inv, eII = s2 * inv, eIp = s3 * inv;  // shifted means
-        const float var = fmaxf(eII - mI * mI, 0.0f), cov = eIp - mI * mp;
+        // var_I, cov_Ip: exactly 0 for a one-sample window (r' = 0), where Eq. 2 gives a = 0
+        const float var = r ? fmaxf(eII - mI * mI, 0.0f) : 0.0f, cov = r ? eIp - mI * mp : 0.0f;
         const float a = cov / (var + P.eps);  // Eq. (2)
         AB[idx] = a;
         AB[Ah * Aw + idx] = (mp + sp) - a * (mI + sI);  // Eq. (3)

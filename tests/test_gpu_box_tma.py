@@ -160,3 +160,18 @@ def test_intermediates_through_tma(gf):
     tol = 2e-6 / eps * 10
     assert max_abs(a.cpu(), inter["a"]) <= tol and max_abs(b.cpu(), inter["b"]) <= tol
     assert max_abs(ma.cpu(), inter["mean_a"]) <= tol and max_abs(mb.cpu(), inter["mean_b"]) <= tol
+
+
+@pytest.mark.parametrize("fused", [-1, 1], ids=["chain", "single_kernel"])
+@pytest.mark.parametrize("W", [528, 530], ids=["tma", "per_thread_loads"])
+@pytest.mark.parametrize("mode", ["nearest", "bilinear"])
+def test_one_sample_window_is_exact(gf, mode, W, fused):
+    """r' = 0 (one-sample windows): var_I = cov_Ip = 0 exactly, so Eq. 2 gives a = 0 and q is the upsampled
+    box mean of p' whatever eps; with a tiny eps any rounding left in var or cov would be amplified by 1 / eps.
+    Every statistics kernel (TMA tiles, per-thread loads, the single fused kernel)."""
+    m = {"nearest": oracle.SUB_NEAREST, "bilinear": oracle.SUB_BILINEAR}[mode]
+    I = _rand((1, 1, 280, W), 500)
+    p = _rand((1, 3, 280, W), 501)
+    q = _run(gf, I, p, 0, 1e-6, 4, mode, r_low=0, fused=fused)
+    ref = oracle.fast_guided_filter(I.astype(np.float64), p.astype(np.float64), 0, 1e-6, 4, m, r_low=0)
+    assert max_abs(q, ref) <= TOL_F32
