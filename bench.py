@@ -97,12 +97,13 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback (6.8 TB/s, no MEASURED_PEAKS.json)"
 
 
-def profiled_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if one exists for this workload."""
-    path = os.path.join(ROOT, "profiles", "%s_12mp_s4.md" % kernel)
+def profiled_traffic(key):
+    """DRAM bytes for `key` ("dram_bytes_per_launch <kernel>" or "step_dram_bytes") from the committed ncu
+    capture of one 12 MP s = 4 call with write-backs counted (profiles/traffic_12mp_s4_step.md), if present."""
+    path = os.path.join(ROOT, "profiles", "traffic_12mp_s4_step.md")
     try:
         for line in open(path):
-            if line.startswith("dram_bytes_per_launch:"):
+            if line.startswith(key + ":"):
                 return int(float(line.split(":", 1)[1].strip()))
     except OSError:
         pass
@@ -290,8 +291,12 @@ def run_native(args, world, rank, local):
     peak, peak_src = measured_hbm_peak()
     achieved = alg_bytes / (stage_ms["k_upsample_output"] / 1e3) / 1e9
     roofline = {"kernel": "k_upsample_output", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": profiled_traffic("k_upsample_output"),
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": profiled_traffic("dram_bytes_per_launch k_upsample_output"),
                 "algorithmic_bytes": alg_bytes, "peak_source": peak_src,
+                "step_traffic": profiled_traffic("step_dram_bytes"), "step_algorithmic_bytes": 372000000,
+                "traffic_source": "ncu dram__bytes_read/write.sum, --cache-control none, one steady call "
+                                  "(profiles/traffic_12mp_s4_step.md)",
                 "stage_us": {k: round(v * 1e3, 2) for k, v in stage_ms.items()}}
 
     out = {"metric": METRIC, "value": round(value, 1), "unit": "MP/s", "n_gpus": world, "steps": args.steps,
