@@ -100,6 +100,8 @@ def load_library(build_if_missing=True):
     """Load libgf.so (building it first if it is missing and ``build_if_missing``).  Raises if it cannot
     be loaded: callers never fall back to another implementation."""
     global _lib
+    if _lib is not None:  # loaded: no lock on the per-call path
+        return _lib
     with _lib_lock:
         if _lib is not None:
             return _lib
@@ -170,10 +172,16 @@ def check(status):
     return status
 
 
+_DEFAULT_OPTS = None  # gf_opts_init's result, copied for every call
+
+
 def opts_init():
-    o = GFOpts()
-    load_library().gf_opts_init(ctypes.byref(o))
-    return o
+    global _DEFAULT_OPTS
+    if _DEFAULT_OPTS is None:
+        o = GFOpts()
+        load_library().gf_opts_init(ctypes.byref(o))
+        _DEFAULT_OPTS = bytes(o)
+    return GFOpts.from_buffer_copy(_DEFAULT_OPTS)
 
 
 def kernel_faults(device=None, clear=True):
@@ -203,6 +211,8 @@ def lowres_geometry(H, W, s, r, r_low=-1):
 def _ratio(o, s):
     """The integer s to pass with options `o`: an integer ratio as it is; a non-integer one (a Fraction, or
     a float that is an exact binary fraction such as 2.5) goes into o.s_num / o.s_den."""
+    if type(s) is int:
+        return s
     f = Fraction(s)
     if f.denominator == 1:
         return int(f)
@@ -387,11 +397,13 @@ def fast_guided_filter(I, p, r, eps, s=4, mode="bilinear", *, r_low=None, p_lowr
                 e.record(st)
         ev_arr = (ctypes.c_void_p * (2 * GF_MAX_STAGES))(*[e.cuda_event for e in kernel_events])
         o.kernel_events = ctypes.cast(ev_arr, ctypes.c_void_p)
-    ctx = ctx or default_context(I.device.index)
+    dev = I.device.index
+    ctx = ctx or default_context(dev)
     m = MODES[mode] if isinstance(mode, str) else int(mode)
-    with torch.cuda.device(I.device):
-        check(load_library().gf_filter(ctx.handle, _ptr(I4), _ptr(p4), _ptr(out), H, W, C, int(r), float(eps),
-                                       int(s), m, ctypes.byref(o), _stream_handle(stream)))
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)  # the current stream of I's device; the library sets the device
+    check(load_library().gf_filter(ctx.handle, _ptr(I4), _ptr(p4), _ptr(out), H, W, C, int(r), float(eps),
+                                   int(s), m, ctypes.byref(o), ctypes.c_void_p(stream.cuda_stream)))
     if given:
         return result
     if prank == 2:
