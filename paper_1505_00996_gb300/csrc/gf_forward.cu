@@ -1328,6 +1328,9 @@ bool aligned_vec_subsample(const FwdPlan &P)
 // statistics 13.9 against 17.1 us and the box means 12.1 against 12.9 us (two images in flight: 178 k against
 // 177 k MP/s); the feathering figure's r' = 15 at s = 4 38 against 47 us.
 static bool box_tma_pays(int, int) { return true; }
+// The column-strip kernels (gf_strip.cu) take the box steps at large radii, where the tiles' 2r halo rows and
+// columns cost more than their outputs.
+static bool strip_pays(int r) { return r > 8; }
 
 bool s1_means_output_form(const Resolved &R)
 {
@@ -1363,6 +1366,7 @@ cudaError_t launch_color_chain(const FwdPlan &P0, float *pl, StageTimer &tm, cud
         J.h = P.h; J.w = P.w; J.r = P.r_low;
         J.out0 = oX; J.out1 = oY;
         J.fault = P.fault;
+        if (strip_pays(P.r_low) && strip_box_supported(J)) return launch_strip_box(J, st);
         if (box_tma_pays(P.s, P.r_low) && box_tma_supported(J)) return launch_box_tma(J, st);
         BoxParams bp{};
         bp.X = X; bp.Y = Y;
@@ -1497,9 +1501,13 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         J.out0 = P.a; J.out1 = P.b; J.ops = P.lps;
         J.stats = P.int_stats ? nullptr : (float *)P.stats;
         J.fault = P.fault;
-        const bool tma = !P.int_stats && src_dt == F32 && box_tma_pays(P.s, P.r_low) && box_tma_supported(J);
+        const bool fp32 = !P.int_stats && src_dt == F32;
+        const bool strip = fp32 && strip_pays(P.r_low) && strip_box_supported(J);
+        const bool tma = !strip && fp32 && box_tma_pays(P.s, P.r_low) && box_tma_supported(J);
         tm.before();
-        if (tma) {
+        if (strip) {
+            err = launch_strip_box(J, st);
+        } else if (tma) {
             err = launch_box_tma(J, st);
         } else if (P.int_stats) {
             if (src_dt == F32) err = launch_box_t<float, KIND_STATS_INT>(bp, planesNC, st);
@@ -1524,9 +1532,10 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         J.I = (const float *)P.I; J.q = P.q; J.fps = P.fps; J.CI = P.CI;
         J.Yw0 = P.Yw0; J.Yw1 = P.Yw1; J.dt_out = P.dt_out; J.detail = P.detail;
         J.fault = P.fault;
-        if (box_tma_supported(J)) {
+        const bool strip = strip_pays(P.r_low) && strip_box_supported(J);
+        if (strip || box_tma_supported(J)) {
             tm.before();
-            err = launch_box_tma(J, st);
+            err = strip ? launch_strip_box(J, st) : launch_box_tma(J, st);
             tm.after();
             return err;
         }
@@ -1543,7 +1552,9 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         J.out0 = P.ma; J.out1 = P.mb;
         J.fault = P.fault;
         tm.before();
-        if (box_tma_pays(P.s, P.r_low) && box_tma_supported(J)) {
+        if (strip_pays(P.r_low) && strip_box_supported(J)) {
+            err = launch_strip_box(J, st);
+        } else if (box_tma_pays(P.s, P.r_low) && box_tma_supported(J)) {
             err = launch_box_tma(J, st);
         } else {
             BoxParams bp{};

@@ -221,6 +221,10 @@ struct BoxTmaJob {
 };
 bool box_tma_supported(const BoxTmaJob &J);
 cudaError_t launch_box_tma(const BoxTmaJob &J, cudaStream_t st);
+// The column-strip box kernels (gf_strip.cu) for radii 1..16: whether they take the job (FP32 planes, rows a
+// multiple of 4 outputs, 16-byte aligned outputs, no window statistics kept), and their launch.
+bool strip_box_supported(const BoxTmaJob &J);
+cudaError_t launch_strip_box(const BoxTmaJob &J, cudaStream_t st);
 
 // The single-kernel form (gf_fused.cu): whether it can run these arguments, and its launch.
 bool fused_supported(const Resolved &R, bool intermediates);

@@ -1,0 +1,547 @@
+// gf_strip.cu -- column-strip kernels for the box steps at large radii (He and Sun, "Fast Guided Filter", 2015):
+//
+//   SK_STATS     Algorithm 2 (Algorithm 1 at s = 1), box statistics mean_I, mean_p, corr_I, corr_Ip at radius r,
+//                fused with var_I, cov_Ip and the coefficients a (Eq. 2) and b (Eq. 3);
+//   SK_MEAN2     box means of a and b;
+//   SK_MEAN2_OUT box means of a and b fused with q = mean_a I + mean_b (Eq. 4), at s = 1 only, where the
+//                upsample is the identity.
+//
+// f_mean is the box mean over the window clipped to the image, divided by the window's in-image count.
+//
+// One CTA owns a strip of 128 output columns over a segment of rows, of one plane or, when one guide plane
+// serves three channels, of all three (the guide's sums are then formed once per pixel).  Phase 1: one thread
+// per strip column (the 128 columns and the r halo on each side: 160 threads at r = 16) carries the vertical
+// window sums down the segment, adding the row that enters the window and subtracting the row that leaves it,
+// both read straight from global memory (the leaving row was read 2r + 1 rows earlier, so it comes from L2),
+// and writes the sums of a block of 10 rows to shared memory.  Phase 2: every thread takes a run of 8 outputs of
+// one row of the block, slides the horizontal window along the column sums, applies the epilogue and stores
+// with 128-bit stores.  A window is opened once per segment, not per tile, and both phases keep all threads
+// busy, which the tile form (gf_box.cu) cannot at large radii: its 2r halo rows and columns cost more there
+// than the outputs themselves.
+//
+// Statistics are taken of values shifted by one sample of the segment (its first output pixel), so
+// E[I^2] - E[I]^2 is formed from terms near the local level; pairs of quantities travel as packed FP32x2.
+#include <atomic>
+
+#include "gf_device.cuh"
+#include "gf_internal.cuh"
+
+namespace gfk {
+
+namespace {
+
+constexpr int SP_TW = 128;                      // output columns per strip
+constexpr int SP_NT = 160;                      // threads: walkers (128 + 2r <= 160), then the runs
+constexpr int SP_RUN = 8;                       // outputs per phase-2 run
+constexpr int SP_CB = SP_NT / (SP_TW / SP_RUN); // rows per block: 10
+constexpr int SP_RMAX = (SP_NT - SP_TW) / 2;    // 16
+// Longest segment: the running sums carry the rounding of every row added and subtracted, so a window is
+// reopened (with a new shift) at least every 160 rows.
+constexpr int SP_SEG_MAX = 16 * SP_CB;
+
+enum { SK_STATS = 0, SK_MEAN2 = 2, SK_MEAN2_OUT = 3 };
+
+struct StripParams {
+    const float *X, *Y;  // SK_STATS: guide planes (CX per image) and input planes (C per image); else a and b
+    size_t xps, yps;     // plane strides (elements); rows are w elements apart
+    int C, CX;           // channels per image; guide planes per image (1 or C)
+    int groups;          // CTAs across the channels of one image (C / NY)
+    int h, w, r;         // plane size; radius (used when the kernel's RC < 0)
+    int ylo, yhi, seg;   // output rows [ylo, yhi), seg rows per CTA (a multiple of SP_CB)
+    float eps;
+    float *out0, *out1;  // SK_STATS: a, b; SK_MEAN2: mean_a, mean_b (plane stride ops)
+    size_t ops;
+    int stream_out;      // the outputs are stored with the streaming (evict-first) policy
+    // SK_MEAN2_OUT: q = mean_a I + mean_b into q (dtype TQ, plane stride fps), the guide I with CI planes per
+    // image (plane stride fps); the detail epilogue q + k (I - q) when detail != 0
+    const float *I;
+    void *q;
+    size_t fps;
+    int CI;
+    float detail;
+};
+
+// Pairs of window sums carried per column: statistics of NY channels sharing one guide carry (dX, dY_c) and
+// (dX^2, dX dY_c) -- 2 pairs for one channel, 4 for three; box means carry (a, b).
+__host__ __device__ constexpr int nq_of(int KIND, int NY) { return KIND == SK_STATS ? (NY == 1 ? 2 : 4) : 1; }
+// Column sums of the block are double-buffered (one barrier per block) where they are small enough to leave
+// room for four CTAs per SM.
+__host__ __device__ constexpr bool db_of(int NQ) { return NQ <= 2; }
+
+// Shared-memory index of column c.  float4 elements (NQ >= 2): the low three bits XOR-swizzled by c / 8, so the
+// 8 runs read by a quarter-warp fall on distinct banks; float2 elements (NQ == 1): one pad per 8 columns.
+__host__ __device__ constexpr int vp_of(int NQ) { return NQ == 1 ? SP_NT + SP_NT / 8 + 1 : SP_NT; }
+__device__ __forceinline__ int vidx4(int c) { return c ^ ((c >> 3) & 7); }
+__device__ __forceinline__ int vidx2(int c) { return c + (c >> 3); }
+
+// Bytes of shared memory of one CTA.
+__host__ __device__ constexpr size_t strip_smem(int NQ)
+{
+    return (size_t)(db_of(NQ) ? 2 : 1) * SP_CB * vp_of(NQ) * (NQ == 1 ? 8 : 16) * (NQ == 1 ? 1 : NQ / 2);
+}
+
+// One strip column's sources: the planes it reads (statistics: the guide, then NY inputs; box means: a, b),
+// offset to the column, and for the statistics the shift subtracted from each.
+template <int KIND, int NY>
+struct Column {
+    static constexpr int NS = (KIND == SK_STATS) ? 1 + NY : 2;
+    static constexpr int NQ = nq_of(KIND, NY);
+    const float *p[NS];
+    float c[NS];
+    int w;
+    __device__ __forceinline__ void load(int t, float v[NS]) const
+    {
+#pragma unroll
+        for (int k = 0; k < NS; ++k) v[k] = __ldg(p[k] + t * w);
+    }
+    // the pairs one row contributes to the window sums
+    __device__ __forceinline__ void pairs(const float v[NS], float2 q[NQ]) const
+    {
+        if constexpr (KIND != SK_STATS) {
+            q[0] = make_float2(v[0], v[1]);
+        } else if constexpr (NY == 1) {
+            const float2 d = sub2(make_float2(v[0], v[1]), make_float2(c[0], c[1]));
+            q[0] = d;
+            q[1] = mul2(make_float2(d.x, d.x), d);  // (dX^2, dX dY)
+        } else {
+            const float2 d0 = sub2(make_float2(v[0], v[1]), make_float2(c[0], c[1]));
+            const float2 d1 = sub2(make_float2(v[2], v[3]), make_float2(c[2], c[3]));
+            const float2 xx = make_float2(d0.x, d0.x);
+            q[0] = d0;            // (dX, dY_0)
+            q[1] = d1;            // (dY_1, dY_2)
+            q[2] = mul2(xx, d0);  // (dX^2, dX dY_0)
+            q[3] = mul2(xx, d1);  // (dX dY_1, dX dY_2)
+        }
+    }
+    __device__ __forceinline__ void add_row(int t, float2 S[NQ]) const
+    {
+        float v[NS];
+        float2 q[NQ];
+        load(t, v);
+        pairs(v, q);
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) S[k] = add2(S[k], q[k]);
+    }
+};
+
+// Column sums of one row of a block into shared memory (walker column j).
+template <int NQ>
+__device__ __forceinline__ void put_sums(unsigned char *buf, int k, int j, const float2 S[NQ])
+{
+    constexpr int VP = vp_of(NQ);
+    if constexpr (NQ == 1) {
+        reinterpret_cast<float2 *>(buf)[k * VP + vidx2(j)] = S[0];
+    } else {
+        float4 *VA = reinterpret_cast<float4 *>(buf);
+        VA[k * VP + vidx4(j)] = make_float4(S[0].x, S[0].y, S[1].x, S[1].y);
+        if constexpr (NQ == 4) VA[(SP_CB + k) * VP + vidx4(j)] = make_float4(S[2].x, S[2].y, S[3].x, S[3].y);
+    }
+}
+// Column sums at shared-memory index `idx` (vidx2 / vidx4 of the column) of row k of a block.
+template <int NQ>
+__device__ __forceinline__ void get_sums(const unsigned char *buf, int k, int idx, float2 S[NQ])
+{
+    constexpr int VP = vp_of(NQ);
+    if constexpr (NQ == 1) {
+        S[0] = reinterpret_cast<const float2 *>(buf)[k * VP + idx];
+    } else {
+        const float4 *VA = reinterpret_cast<const float4 *>(buf);
+        const float4 a = VA[k * VP + idx];
+        S[0] = make_float2(a.x, a.y);
+        S[1] = make_float2(a.z, a.w);
+        if constexpr (NQ == 4) {
+            const float4 b = VA[(SP_CB + k) * VP + idx];
+            S[2] = make_float2(b.x, b.y);
+            S[3] = make_float2(b.z, b.w);
+        }
+    }
+}
+
+// Phase 1 of one block for one walker column: the vertical window sums of rows yb .. yb + SP_CB - 1.  S holds
+// the sums of rows [yb - r, yb + r - 1] (clipped to the image) on entry and is carried on to the next block.
+template <int KIND, int NY, int RC>
+__device__ __forceinline__ void walk_block(const Column<KIND, NY> &col, float2 (&S)[nq_of(KIND, NY)], int yb,
+                                           int r, int h, unsigned char *buf, int j)
+{
+    constexpr int NQ = nq_of(KIND, NY);
+    constexpr int NS = Column<KIND, NY>::NS;
+    if (yb - r >= 0 && yb + SP_CB - 1 + r < h) {  // every row entering and leaving is in the image
+#pragma unroll
+        for (int k = 0; k < SP_CB; ++k) {
+            float ve[NS], vl[NS];
+            col.load(yb + k + r, ve);
+            col.load(yb + k - r, vl);
+            float2 qe[NQ], ql[NQ];
+            col.pairs(ve, qe);
+            col.pairs(vl, ql);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) S[q] = add2(S[q], qe[q]);
+            put_sums<NQ>(buf, k, j, S);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) S[q] = sub2(S[q], ql[q]);
+        }
+    } else {
+#pragma unroll 2
+        for (int k = 0; k < SP_CB; ++k) {
+            const int y = yb + k;
+            if (y + r < h) col.add_row(y + r, S);
+            put_sums<NQ>(buf, k, j, S);
+            if (y - r >= 0 && y - r < h) {
+                float v[NS];
+                float2 q[NQ];
+                col.load(y - r, v);
+                col.pairs(v, q);
+#pragma unroll
+                for (int i = 0; i < NQ; ++i) S[i] = sub2(S[i], q[i]);
+            }
+        }
+    }
+}
+
+template <typename TQ>
+__device__ __forceinline__ void store4q(TQ *p, const float v[4]);
+template <>
+__device__ __forceinline__ void store4q<float>(float *p, const float v[4])
+{
+    __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+}
+template <>
+__device__ __forceinline__ void store4q<__half>(__half *p, const float v[4])
+{
+    const __half2 lo = __floats2half2_rn(v[0], v[1]), hi = __floats2half2_rn(v[2], v[3]);
+    *reinterpret_cast<uint2 *>(p) =
+        make_uint2(*reinterpret_cast<const unsigned *>(&lo), *reinterpret_cast<const unsigned *>(&hi));
+}
+
+__host__ __device__ constexpr size_t buf_bytes(int NQ)
+{
+    return (size_t)SP_CB * vp_of(NQ) * (NQ == 1 ? 8 : 16) * (NQ == 1 ? 1 : NQ / 2);
+}
+
+// CTAs per SM the registers are sized for: the box means' column sums take 29 KB, room for six CTAs; the
+// statistics' take 51 KB, room for four.
+__host__ __device__ constexpr int minb_of(int NQ) { return NQ == 1 ? 6 : 4; }
+
+template <int KIND, int NY, int RC, typename TQ>
+__global__ void __launch_bounds__(SP_NT, minb_of(nq_of(KIND, NY))) k_box_strip(StripParams P)
+{
+    constexpr int NQ = nq_of(KIND, NY);
+    constexpr int NS = Column<KIND, NY>::NS;
+    constexpr int NBUF = db_of(NQ) ? 2 : 1;
+    const int r = RC >= 0 ? RC : P.r;
+    const int h = P.h, w = P.w, tid = threadIdx.x;
+    const int grp = blockIdx.x % P.groups, sx = blockIdx.x / P.groups, n = blockIdx.z;
+    const int x0 = sx * SP_TW;
+    const int y0 = P.ylo + blockIdx.y * P.seg, yend = min(y0 + P.seg, P.yhi);
+    extern __shared__ __align__(16) unsigned char sm[];
+
+    // ---- this CTA's planes; for the statistics, the shift: every plane's value at the first output pixel
+    const float *base[NS];
+    if constexpr (KIND == SK_STATS) {
+        base[0] = P.X + (size_t)(n * P.CX + (P.CX == 1 ? 0 : grp * NY)) * P.xps;
+#pragma unroll
+        for (int k = 0; k < NY; ++k) base[1 + k] = P.Y + (size_t)(n * P.C + grp * NY + k) * P.yps;
+    } else {
+        base[0] = P.X + (size_t)(n * P.C + grp) * P.xps;
+        base[1] = P.Y + (size_t)(n * P.C + grp) * P.yps;
+    }
+    Column<KIND, NY> col;
+    col.w = w;
+    const int xc = x0 - r + tid;  // this thread's walker column
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        col.p[k] = base[k] + xc;
+        col.c[k] = (KIND == SK_STATS) ? __ldg(base[k] + (size_t)y0 * w + x0) : 0.0f;
+    }
+    const bool walker = tid < SP_TW + 2 * r;
+    const bool colok = walker && xc >= 0 && xc < w;
+
+    // ---- the window of the segment's first row, less its last row: rows [y0 - r, y0 + r - 1]
+    float2 S[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) S[q] = make_float2(0.0f, 0.0f);
+    if (colok) {
+        if (RC >= 0 && y0 - r >= 0 && y0 + r <= h) {
+#pragma unroll
+            for (int i = 0; i < 2 * (RC > 0 ? RC : 0); ++i) col.add_row(y0 - r + i, S);
+        } else {
+            for (int t = max(y0 - r, 0); t < min(y0 + r, h); ++t) col.add_row(t, S);
+        }
+    }
+
+    // ---- phase-2 task: run g (outputs x0 + 8g .. + 7) of row k of each block
+    const int pk = tid >> 4, pg = tid & 15;
+    const int ox = x0 + pg * SP_RUN;
+    const bool second = ox + 4 < w;
+    const float inv_full = 1.0f / (float)((2 * r + 1) * (2 * r + 1));
+    const bool x_interior = (ox - r >= 0) && (ox + SP_RUN - 1 + r < w);
+
+    const int nblocks = (yend - y0 + SP_CB - 1) / SP_CB;
+    for (int b = 0; b < nblocks; ++b) {
+        const int yb = y0 + b * SP_CB;
+        unsigned char *buf = sm + (NBUF == 2 ? (size_t)(b & 1) * buf_bytes(NQ) : 0);
+        // ---- phase 1: vertical window sums of the block's rows
+        if (colok) {
+            walk_block<KIND, NY, RC>(col, S, yb, r, h, buf, tid);
+        } else if (walker) {  // a column outside the image contributes nothing
+            const float2 Z[NQ] = {};
+#pragma unroll 1
+            for (int k = 0; k < SP_CB; ++k) put_sums<NQ>(buf, k, tid, Z);
+        }
+        __syncthreads();
+
+        // ---- phase 2: horizontal window sums along a run of 8 outputs, epilogue, 128-bit stores
+        const int y = yb + pk;
+        if (y < yend && ox < w) {
+            float iv[8];
+            if constexpr (KIND == SK_MEAN2_OUT) {  // the guide under the run, requested before the sums
+                const float *Ip = P.I + (size_t)(n * P.CI + (P.CI == 1 ? 0 : grp)) * P.fps + (size_t)y * w + ox;
+                const float4 u = __ldcs(reinterpret_cast<const float4 *>(Ip));
+                const float4 v = second ? __ldcs(reinterpret_cast<const float4 *>(Ip) + 1)
+                                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                iv[0] = u.x; iv[1] = u.y; iv[2] = u.z; iv[3] = u.w;
+                iv[4] = v.x; iv[5] = v.y; iv[6] = v.z; iv[7] = v.w;
+            }
+            // The run's first window covers walker columns c0 .. c0 + 2r.  With the swizzled layout a whole block of
+            // 8 columns occupies 8 consecutive slots in some order, which a sum does not see: full blocks are read
+            // slot by slot, lane g taking slot (e + g) mod 8 at step e so that the 8 lanes of a quarter-warp fall on
+            // distinct banks, and only the columns of a partial block go through the swizzle.
+            const int c0 = pg * SP_RUN;
+            int rot[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) rot[e] = c0 + ((e + pg) & 7);
+            auto idx_of = [&](int c) { return NQ == 1 ? vidx2(c) : vidx4(c); };
+            float2 T[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) T[q] = make_float2(0.0f, 0.0f);
+            auto acc = [&](int idx) {
+                float2 u[NQ];
+                get_sums<NQ>(buf, pk, idx, u);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) T[q] = add2(T[q], u[q]);
+            };
+            if constexpr (RC >= 0) {
+                constexpr int full = (NQ == 1) ? 0 : (2 * RC + 1) / 8;
+#pragma unroll
+                for (int i = 0; i < 8 * full; ++i) acc(rot[i & 7] + (i & ~7));
+#pragma unroll
+                for (int i = 8 * full; i <= 2 * RC; ++i) acc(idx_of(c0 + i));
+            } else {
+                const int full = (NQ == 1) ? 0 : (2 * r + 1) / 8;
+                for (int b8 = 0; b8 < 8 * full; b8 += 8) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) acc(rot[e] + b8);
+                }
+#pragma unroll 4
+                for (int i = 8 * full; i <= 2 * r; ++i) acc(idx_of(c0 + i));
+            }
+            const bool interior = x_interior && (y - r >= 0) && (y + r < h);
+            const int ny = min(h - 1, y + r) - max(0, y - r) + 1;
+            constexpr int NO = (KIND == SK_STATS) ? 2 * NY : (KIND == SK_MEAN2 ? 2 : 1);
+            float o[NO][4];
+#pragma unroll
+            for (int j = 0; j < SP_RUN; ++j) {
+                if (j > 0) {
+                    float2 ua[NQ], ub[NQ];
+                    get_sums<NQ>(buf, pk, idx_of(c0 + j + 2 * r), ua);
+                    get_sums<NQ>(buf, pk, idx_of(c0 + j - 1), ub);
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) T[q] = add2(T[q], sub2(ua[q], ub[q]));
+                }
+                float inv = inv_full;
+                if (!interior) {
+                    const int xx = ox + j;
+                    const int nx = min(w - 1, xx + r) - max(0, xx - r) + 1;
+                    inv = __fdividef(1.0f, (float)(nx * ny));
+                }
+                const float2 iv2 = make_float2(inv, inv);
+                const int jj = j & 3;
+                if constexpr (KIND == SK_STATS) {
+                    const float2 m0 = mul2(T[0], iv2);
+                    if constexpr (NY == 1) {
+                        const float2 m1 = mul2(T[1], iv2);
+                        // var_I, cov_Ip; exactly 0 for a one-sample window (r = 0), as in the tile kernels
+                        const float var = r ? fmaxf(fmaf(-m0.x, m0.x, m1.x), 0.0f) : 0.0f;
+                        const float cov = r ? fmaf(-m0.x, m0.y, m1.y) : 0.0f;
+                        const float a = __fdividef(cov, var + P.eps);            // a, Eq. (2)
+                        o[0][jj] = a;
+                        o[1][jj] = (m0.y + col.c[1]) - a * (m0.x + col.c[0]);    // b, Eq. (3)
+                    } else {
+                        const float2 m1 = mul2(T[1], iv2), m2 = mul2(T[2], iv2), m3 = mul2(T[3], iv2);
+                        const float var = r ? fmaxf(fmaf(-m0.x, m0.x, m2.x), 0.0f) : 0.0f;
+                        const float rv = __fdividef(1.0f, var + P.eps);
+                        const float mx = m0.x + col.c[0];
+                        const float my[3] = {m0.y, m1.x, m1.y}, mxy[3] = {m2.y, m3.x, m3.y};
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            const float cov = r ? fmaf(-m0.x, my[k], mxy[k]) : 0.0f;
+                            const float a = cov * rv;                             // a, Eq. (2)
+                            o[2 * k][jj] = a;
+                            o[2 * k + 1][jj] = (my[k] + col.c[1 + k]) - a * mx;   // b, Eq. (3)
+                        }
+                    }
+                } else if constexpr (KIND == SK_MEAN2) {
+                    o[0][jj] = T[0].x * inv;  // mean_a
+                    o[1][jj] = T[0].y * inv;  // mean_b
+                } else {
+                    float qv = fmaf(T[0].x * inv, iv[j], T[0].y * inv);  // Eq. (4)
+                    if (P.detail != 0.0f) qv = fmaf(P.detail, iv[j] - qv, qv);
+                    o[0][jj] = qv;
+                }
+                if (jj == 3 && (j == 3 || second)) {  // a float4 of every output plane
+                    const int xs = ox + j - 3;
+                    if constexpr (KIND == SK_MEAN2_OUT) {
+                        store4q<TQ>((TQ *)P.q + (size_t)(n * P.C + grp) * P.fps + (size_t)y * w + xs, o[0]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < NO / 2; ++k) {
+                            const size_t off = (size_t)(n * P.C + grp * (NO / 2) + k) * P.ops + (size_t)y * w + xs;
+                            const float4 va = make_float4(o[2 * k][0], o[2 * k][1], o[2 * k][2], o[2 * k][3]);
+                            const float4 vb = make_float4(o[2 * k + 1][0], o[2 * k + 1][1], o[2 * k + 1][2], o[2 * k + 1][3]);
+                            if (P.stream_out) {  // planes larger than L2: streamed past the rows kept there
+                                __stcs(reinterpret_cast<float4 *>(P.out0 + off), va);
+                                __stcs(reinterpret_cast<float4 *>(P.out1 + off), vb);
+                            } else {             // small planes stay in L2 for the next kernel
+                                *reinterpret_cast<float4 *>(P.out0 + off) = va;
+                                *reinterpret_cast<float4 *>(P.out1 + off) = vb;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (NBUF == 1 && b + 1 < nblocks) __syncthreads();  // the column sums are rewritten by the next block
+    }
+}
+
+// SMs of the current device (cached per device ordinal).
+int sm_count()
+{
+    static std::atomic<int> cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+    const int slot = dev < 64 ? dev : 63;
+    int n = cached[slot].load(std::memory_order_relaxed);
+    if (n == 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+        if (dev < 64) cached[slot].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
+// Rows per CTA (at most SP_SEG_MAX): the segment length that minimises (waves of CTAs) x (rows a CTA walks, its 2r opening rows
+// included) for `tasks` CTAs per segment row and `resident` CTAs on the GPU at once.
+int segment_rows(int rows, int r, long long tasks, long long resident)
+{
+    const int max_seg = min(((rows + SP_CB - 1) / SP_CB) * SP_CB, SP_SEG_MAX);
+    int best = max_seg;
+    long long best_cost = -1;
+    for (int seg = SP_CB; seg <= max_seg; seg += SP_CB) {
+        const long long nseg = (rows + seg - 1) / seg;
+        const long long waves = (tasks * nseg + resident - 1) / resident;
+        const long long cost = waves * (seg + 2 * r);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = seg;
+        }
+    }
+    return best;
+}
+
+template <int KIND, int NY, int RC, typename TQ>
+cudaError_t launch_strip(StripParams P, int N, cudaStream_t st)
+{
+    auto kern = k_box_strip<KIND, NY, RC, TQ>;
+    constexpr size_t smem = strip_smem(nq_of(KIND, NY));
+    cudaError_t e = opt_in_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    static std::atomic<int> per_sm_cached{0};  // CTAs per SM of this instantiation
+    int per_sm = per_sm_cached.load(std::memory_order_relaxed);
+    if (per_sm == 0) {
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SP_NT, smem)) != cudaSuccess) return e;
+        per_sm = per_sm > 0 ? per_sm : 1;
+        per_sm_cached.store(per_sm, std::memory_order_relaxed);
+    }
+    const int strips = (P.w + SP_TW - 1) / SP_TW;
+    const long long tasks = (long long)strips * P.groups * N;
+    P.seg = segment_rows(P.yhi - P.ylo, P.r, tasks, (long long)per_sm * sm_count());
+    const dim3 grid((unsigned)(strips * P.groups), (unsigned)((P.yhi - P.ylo + P.seg - 1) / P.seg), (unsigned)N);
+    kern<<<grid, SP_NT, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+// The radius as a compile-time constant at r = 16 (s = 1 at the paper's 12 MP figure radius) and 15 (the
+// feathering figure's r' at s = 4), else at run time.
+template <int KIND, int NY, typename TQ>
+cudaError_t launch_radius(const StripParams &P, int N, cudaStream_t st)
+{
+    if (P.r == 16) return launch_strip<KIND, NY, 16, TQ>(P, N, st);
+    if (P.r == 15) return launch_strip<KIND, NY, 15, TQ>(P, N, st);
+    return launch_strip<KIND, NY, -1, TQ>(P, N, st);
+}
+
+bool aligned16s(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+bool strip_box_supported(const BoxTmaJob &J)
+{
+    if (J.r < 1 || J.r > SP_RMAX || J.w % 4 != 0 || J.stats != nullptr) return false;
+    if ((long long)J.h * J.w >= (1LL << 31) || J.h > 65535 * SP_CB || J.N > 65535 || J.N < 1) return false;
+    if ((long long)((J.w + SP_TW - 1) / SP_TW) * J.C >= (1LL << 31)) return false;
+    if (J.kind == BOX_JOB_MEANS_OUTPUT) {
+        if (!aligned16s(J.I) || !aligned16s(J.q) || J.fps % 4 != 0) return false;
+        if (J.dt_out != F32 && J.dt_out != F16) return false;
+        if (J.Yw0 < 0 || J.Yw1 > J.h || J.Yw0 >= J.Yw1) return false;
+    } else if (!aligned16s(J.out0) || !aligned16s(J.out1) || J.ops % 4 != 0) {
+        return false;
+    }
+    return getenv("GF_NO_STRIP_BOX") == nullptr;  // the tile kernels instead (tests)
+}
+
+cudaError_t launch_strip_box(const BoxTmaJob &J, cudaStream_t st)
+{
+    StripParams P{};
+    P.X = J.X;
+    P.Y = J.Y;
+    P.xps = J.xps;
+    P.yps = J.yps;
+    P.C = J.C;
+    P.CX = J.CX;
+    P.h = J.h;
+    P.w = J.w;
+    P.r = J.r;
+    P.ylo = 0;
+    P.yhi = J.h;
+    P.eps = J.eps;
+    P.out0 = J.out0;
+    P.out1 = J.out1;
+    P.ops = J.ops;
+    // outputs larger than half of L2 do not stay there for the next kernel anyway
+    P.stream_out = (double)J.N * J.C * J.h * J.w * 2 * sizeof(float) > 64e6;
+    P.I = J.I;
+    P.q = J.q;
+    P.fps = J.fps;
+    P.CI = J.CI;
+    P.detail = J.detail;
+    switch (J.kind) {
+    case BOX_JOB_STATS:
+        if (J.CX == 1 && J.C % 3 == 0) {  // one guide plane for three channels: its sums formed once
+            P.groups = J.C / 3;
+            return launch_radius<SK_STATS, 3, float>(P, J.N, st);
+        }
+        P.groups = J.C;
+        return launch_radius<SK_STATS, 1, float>(P, J.N, st);
+    case BOX_JOB_MEANS:
+        P.groups = J.C;
+        return launch_radius<SK_MEAN2, 1, float>(P, J.N, st);
+    default:
+        P.groups = J.C;
+        P.ylo = J.Yw0;
+        P.yhi = J.Yw1;
+        if (J.dt_out == F16) return launch_radius<SK_MEAN2_OUT, 1, __half>(P, J.N, st);
+        return launch_radius<SK_MEAN2_OUT, 1, float>(P, J.N, st);
+    }
+}
+
+}  // namespace gfk
