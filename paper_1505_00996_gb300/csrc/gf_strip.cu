@@ -22,6 +22,7 @@
 // Statistics are taken of values shifted by one sample of the segment (its first output pixel), so
 // E[I^2] - E[I]^2 is formed from terms near the local level; pairs of quantities travel as packed FP32x2.
 #include <atomic>
+#include <type_traits>
 
 #include "gf_device.cuh"
 #include "gf_internal.cuh"
@@ -69,10 +70,12 @@ __host__ __device__ constexpr int nq_of(int KIND, int NY) { return KIND == SK_ST
 __host__ __device__ constexpr bool db_of(int NQ) { return NQ <= 2; }
 
 // Shared-memory index of column c.  float4 elements (NQ >= 2): the low three bits XOR-swizzled by c / 8, so the
-// 8 runs read by a quarter-warp fall on distinct banks; float2 elements (NQ == 1): one pad per 8 columns.
-__host__ __device__ constexpr int vp_of(int NQ) { return NQ == 1 ? SP_NT + SP_NT / 8 + 1 : SP_NT; }
+// 8 runs read by a quarter-warp fall on distinct banks.  float2 elements (NQ == 1): two pads per 8 columns, so
+// each even / odd pair of columns is one aligned 16-byte word and the runs of a quarter-warp (10 float2 apart)
+// again fall on distinct banks.
+__host__ __device__ constexpr int vp_of(int NQ) { return NQ == 1 ? SP_NT + 2 * (SP_NT / 8) : SP_NT; }
 __device__ __forceinline__ int vidx4(int c) { return c ^ ((c >> 3) & 7); }
-__device__ __forceinline__ int vidx2(int c) { return c + (c >> 3); }
+__device__ __forceinline__ int vidx2(int c) { return c + 2 * (c >> 3); }
 
 // Bytes of shared memory of one CTA.
 __host__ __device__ constexpr size_t strip_smem(int NQ)
@@ -137,64 +140,67 @@ __device__ __forceinline__ void put_sums(unsigned char *buf, int k, int j, const
         if constexpr (NQ == 4) VA[(SP_CB + k) * VP + vidx4(j)] = make_float4(S[2].x, S[2].y, S[3].x, S[3].y);
     }
 }
-// Column sums at shared-memory index `idx` (vidx2 / vidx4 of the column) of row k of a block.
-template <int NQ>
-__device__ __forceinline__ void get_sums(const unsigned char *buf, int k, int idx, float2 S[NQ])
-{
-    constexpr int VP = vp_of(NQ);
-    if constexpr (NQ == 1) {
-        S[0] = reinterpret_cast<const float2 *>(buf)[k * VP + idx];
-    } else {
-        const float4 *VA = reinterpret_cast<const float4 *>(buf);
-        const float4 a = VA[k * VP + idx];
-        S[0] = make_float2(a.x, a.y);
-        S[1] = make_float2(a.z, a.w);
-        if constexpr (NQ == 4) {
-            const float4 b = VA[(SP_CB + k) * VP + idx];
-            S[2] = make_float2(b.x, b.y);
-            S[3] = make_float2(b.z, b.w);
+// The rows one walker column reads for a block of output rows yb .. yb + SP_CB - 1: row yb + k + r enters the
+// window of output row yb + k and row yb + k - r leaves it after.  They are requested one block ahead (fetch
+// right after the previous block's column sums are written), so the loads are in flight during phase 2.  A row
+// outside the image reads as the shift value, whose shifted pair is exactly zero.  The three-channel statistics
+// (four planes) have no registers to spare for that and read their rows when they use them.
+template <int KIND, int NY>
+struct RowBatch {
+    static constexpr int NS = Column<KIND, NY>::NS;
+    static constexpr bool PRE_L = (NS <= 2);  // the leaving rows too
+    float e[SP_CB][NS], l[PRE_L ? SP_CB : 1][NS];
+    __device__ __forceinline__ static float ld_row(const Column<KIND, NY> &col, int t, int h, int k)
+    {
+        return (t >= 0 && t < h) ? __ldg(col.p[k] + t * col.w) : col.c[k];
+    }
+    template <bool CHECK>
+    __device__ __forceinline__ void fetch_rows(const Column<KIND, NY> &col, int yb, int r, int h)
+    {
+#pragma unroll
+        for (int k = 0; k < SP_CB; ++k) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                e[k][q] = CHECK ? ld_row(col, yb + k + r, h, q) : __ldg(col.p[q] + (yb + k + r) * col.w);
+                if constexpr (PRE_L)
+                    l[k][q] = CHECK ? ld_row(col, yb + k - r, h, q) : __ldg(col.p[q] + (yb + k - r) * col.w);
+            }
         }
     }
-}
+    __device__ __forceinline__ void fetch(const Column<KIND, NY> &col, int yb, int r, int h)
+    {
+        if (yb - r >= 0 && yb + SP_CB - 1 + r < h) fetch_rows<false>(col, yb, r, h);
+        else fetch_rows<true>(col, yb, r, h);
+    }
+};
 
-// Phase 1 of one block for one walker column: the vertical window sums of rows yb .. yb + SP_CB - 1.  S holds
-// the sums of rows [yb - r, yb + r - 1] (clipped to the image) on entry and is carried on to the next block.
-template <int KIND, int NY, int RC>
-__device__ __forceinline__ void walk_block(const Column<KIND, NY> &col, float2 (&S)[nq_of(KIND, NY)], int yb,
-                                           int r, int h, unsigned char *buf, int j)
+// Phase 1 of one block for one walker column: the vertical window sums of rows yb .. yb + SP_CB - 1 from the
+// batch fetched for them.  S holds the sums of rows [yb - r, yb + r - 1] (clipped to the image) on entry and is
+// carried on to the next block.
+template <int KIND, int NY>
+__device__ __forceinline__ void walk_block(const Column<KIND, NY> &col, const RowBatch<KIND, NY> &B,
+                                           float2 (&S)[nq_of(KIND, NY)], int yb, int r, int h, unsigned char *buf,
+                                           int j)
 {
     constexpr int NQ = nq_of(KIND, NY);
     constexpr int NS = Column<KIND, NY>::NS;
-    if (yb - r >= 0 && yb + SP_CB - 1 + r < h) {  // every row entering and leaving is in the image
 #pragma unroll
-        for (int k = 0; k < SP_CB; ++k) {
-            float ve[NS], vl[NS];
-            col.load(yb + k + r, ve);
-            col.load(yb + k - r, vl);
-            float2 qe[NQ], ql[NQ];
-            col.pairs(ve, qe);
+    for (int k = 0; k < SP_CB; ++k) {
+        float2 qe[NQ], ql[NQ];
+        col.pairs(B.e[k], qe);
+        if constexpr (RowBatch<KIND, NY>::PRE_L) {
+            col.pairs(B.l[k], ql);
+        } else {
+            float vl[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) vl[q] = RowBatch<KIND, NY>::ld_row(col, yb + k - r, h, q);
             col.pairs(vl, ql);
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) S[q] = add2(S[q], qe[q]);
-            put_sums<NQ>(buf, k, j, S);
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) S[q] = sub2(S[q], ql[q]);
         }
-    } else {
-#pragma unroll 2
-        for (int k = 0; k < SP_CB; ++k) {
-            const int y = yb + k;
-            if (y + r < h) col.add_row(y + r, S);
-            put_sums<NQ>(buf, k, j, S);
-            if (y - r >= 0 && y - r < h) {
-                float v[NS];
-                float2 q[NQ];
-                col.load(y - r, v);
-                col.pairs(v, q);
 #pragma unroll
-                for (int i = 0; i < NQ; ++i) S[i] = sub2(S[i], q[i]);
-            }
-        }
+        for (int q = 0; q < NQ; ++q) S[q] = add2(S[q], qe[q]);
+        put_sums<NQ>(buf, k, j, S);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) S[q] = sub2(S[q], ql[q]);
     }
 }
 
@@ -218,9 +224,131 @@ __host__ __device__ constexpr size_t buf_bytes(int NQ)
     return (size_t)SP_CB * vp_of(NQ) * (NQ == 1 ? 8 : 16) * (NQ == 1 ? 1 : NQ / 2);
 }
 
-// CTAs per SM the registers are sized for: the box means' column sums take 29 KB, room for six CTAs; the
-// statistics' take 51 KB, room for four.
-__host__ __device__ constexpr int minb_of(int NQ) { return NQ == 1 ? 6 : 4; }
+// Phase-2 reads of one run: the column sums of walker columns c0 + i (c0 = 8 g) of row k of a block.
+//   float2 layout (NQ == 1): column c at c + c / 8, i.e. 9 g + i + i / 8 -- a constant offset from the run's base;
+//   float4 layout (NQ >= 2): column c at c ^ ((c / 8) mod 8).  The window's whole 8-column blocks are read slot
+//   by slot, lane g taking slot (e + g) mod 8 at step e (8 distinct banks across a quarter-warp, constant offsets
+//   from 8 per-thread bases); single columns take the swizzle: one XOR and one address per read.
+template <int NQ>
+struct RunReader {
+    const float4 *pair2;  // NQ == 1: the run's base (column pairs c0 + i, c0 + i + 1 for even i)
+    const float4 *row4;   // NQ >= 2: the block's row
+    int pg;
+    __device__ __forceinline__ RunReader(const unsigned char *buf, int k, int g) : pg(g)
+    {
+        constexpr int VP = vp_of(NQ);
+        pair2 = reinterpret_cast<const float4 *>(reinterpret_cast<const float2 *>(buf) + k * VP + 10 * g);
+        row4 = reinterpret_cast<const float4 *>(buf) + k * VP;
+    }
+    // NQ == 1: columns c0 + i and c0 + i + 1 (i even) as (a, b, a', b')
+    __device__ __forceinline__ float4 pair_at(int i) const { return pair2[(i + 2 * (i >> 3)) >> 1]; }
+    // NQ == 1: the window sums of the run's 8 outputs at once
+    template <int RC>
+    __device__ __forceinline__ void windows8(int r, float2 W[SP_RUN]) const
+    {
+        const int rr = RC >= 0 ? RC : r;
+        float2 a = make_float2(0.0f, 0.0f), b = make_float2(0.0f, 0.0f);
+        if constexpr (RC >= 0) {
+#pragma unroll
+            for (int i = 0; i < 2 * RC; i += 2) {
+                const float4 q = pair_at(i);
+                a = add2(a, make_float2(q.x, q.y));
+                b = add2(b, make_float2(q.z, q.w));
+            }
+        } else {
+#pragma unroll 4
+            for (int i = 0; i < 2 * r; i += 2) {
+                const float4 q = pair_at(i);
+                a = add2(a, make_float2(q.x, q.y));
+                b = add2(b, make_float2(q.z, q.w));
+            }
+        }
+        // column 2r closes the first window; columns 2r + 1 .. 2r + 7 enter, columns 0 .. 6 leave
+        const float4 e0 = pair_at(2 * rr), e1 = pair_at(2 * rr + 2), e2 = pair_at(2 * rr + 4), e3 = pair_at(2 * rr + 6);
+        const float4 l0 = pair_at(0), l1 = pair_at(2), l2 = pair_at(4), l3 = pair_at(6);
+        const float2 enter[8] = {make_float2(0.0f, 0.0f), make_float2(e0.z, e0.w), make_float2(e1.x, e1.y),
+                                 make_float2(e1.z, e1.w),  make_float2(e2.x, e2.y), make_float2(e2.z, e2.w),
+                                 make_float2(e3.x, e3.y),  make_float2(e3.z, e3.w)};
+        const float2 leave[8] = {make_float2(l0.x, l0.y), make_float2(l0.z, l0.w), make_float2(l1.x, l1.y),
+                                 make_float2(l1.z, l1.w), make_float2(l2.x, l2.y), make_float2(l2.z, l2.w),
+                                 make_float2(l3.x, l3.y), make_float2(l3.z, l3.w)};
+        W[0] = add2(add2(a, b), make_float2(e0.x, e0.y));
+#pragma unroll
+        for (int j = 1; j < SP_RUN; ++j) W[j] = add2(W[j - 1], sub2(enter[j], leave[j - 1]));
+    }
+    __device__ __forceinline__ void add_at(const float4 *p, float2 T[NQ]) const
+    {
+        const float4 a = p[0];
+        T[0] = add2(T[0], make_float2(a.x, a.y));
+        T[1] = add2(T[1], make_float2(a.z, a.w));
+        if constexpr (NQ == 4) {
+            const float4 b = p[SP_CB * vp_of(NQ)];
+            T[2] = add2(T[2], make_float2(b.x, b.y));
+            T[3] = add2(T[3], make_float2(b.z, b.w));
+        }
+    }
+    __device__ __forceinline__ void get_at(const float4 *p, float2 u[NQ]) const
+    {
+        const float4 a = p[0];
+        u[0] = make_float2(a.x, a.y);
+        u[1] = make_float2(a.z, a.w);
+        if constexpr (NQ == 4) {
+            const float4 b = p[SP_CB * vp_of(NQ)];
+            u[2] = make_float2(b.x, b.y);
+            u[3] = make_float2(b.z, b.w);
+        }
+    }
+    // column c0 + i through the swizzle
+    __device__ __forceinline__ const float4 *col4(int i) const
+    {
+        const int blk = pg + (i >> 3);
+        return row4 + 8 * blk + ((i & 7) ^ (blk & 7));
+    }
+    // T = sums of walker columns c0 .. c0 + 2r
+    template <int RC>
+    __device__ __forceinline__ void window(int r, float2 T[NQ]) const
+    {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) T[q] = make_float2(0.0f, 0.0f);
+        if constexpr (NQ == 1) {
+            // not used: windows8 gives the float2 layout's sums
+        } else {
+            const int n = 2 * (RC >= 0 ? RC : r) + 1, full = n >> 3;
+            const float4 *rot[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) rot[e] = row4 + 8 * pg + ((e + pg) & 7);
+            if constexpr (RC >= 0) {
+#pragma unroll
+                for (int i = 0; i < 8 * ((2 * RC + 1) >> 3); ++i) add_at(rot[i & 7] + (i & ~7), T);
+#pragma unroll
+                for (int i = 8 * ((2 * RC + 1) >> 3); i <= 2 * RC; ++i) add_at(col4(i), T);
+            } else {
+                for (int b8 = 0; b8 < 8 * full; b8 += 8) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) add_at(rot[e] + b8, T);
+                }
+                for (int i = 8 * full; i < n; ++i) add_at(col4(i), T);
+            }
+        }
+    }
+    // the window of output j from that of output j - 1: column c0 + j + 2r enters, c0 + j - 1 leaves
+    template <int RC>
+    __device__ __forceinline__ void slide(int j, int r, float2 T[NQ]) const
+    {
+        const int rr = RC >= 0 ? RC : r;
+        if constexpr (NQ >= 2) {
+            float2 ua[NQ], ub[NQ];
+            get_at(col4(j + 2 * rr), ua);
+            get_at(col4(j - 1), ub);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) T[q] = add2(T[q], sub2(ua[q], ub[q]));
+        }
+    }
+};
+
+// CTAs per SM the registers are sized for: four, three for the three-channel statistics, whose batch of entering
+// rows (four planes) needs the registers of a 3-CTA split.
+__host__ __device__ constexpr int minb_of(int NQ) { return NQ == 4 ? 3 : 4; }
 
 template <int KIND, int NY, int RC, typename TQ>
 __global__ void __launch_bounds__(SP_NT, minb_of(nq_of(KIND, NY))) k_box_strip(StripParams P)
@@ -277,12 +405,15 @@ __global__ void __launch_bounds__(SP_NT, minb_of(nq_of(KIND, NY))) k_box_strip(S
     const bool x_interior = (ox - r >= 0) && (ox + SP_RUN - 1 + r < w);
 
     const int nblocks = (yend - y0 + SP_CB - 1) / SP_CB;
+    RowBatch<KIND, NY> B;
+    if (colok) B.fetch(col, y0, r, h);
     for (int b = 0; b < nblocks; ++b) {
         const int yb = y0 + b * SP_CB;
         unsigned char *buf = sm + (NBUF == 2 ? (size_t)(b & 1) * buf_bytes(NQ) : 0);
-        // ---- phase 1: vertical window sums of the block's rows
+        // ---- phase 1: vertical window sums of the block's rows; then the next block's rows are requested
         if (colok) {
-            walk_block<KIND, NY, RC>(col, S, yb, r, h, buf, tid);
+            walk_block<KIND, NY>(col, B, S, yb, r, h, buf, tid);
+            if (b + 1 < nblocks) B.fetch(col, yb + SP_CB, r, h);
         } else if (walker) {  // a column outside the image contributes nothing
             const float2 Z[NQ] = {};
 #pragma unroll 1
@@ -302,113 +433,100 @@ __global__ void __launch_bounds__(SP_NT, minb_of(nq_of(KIND, NY))) k_box_strip(S
                 iv[0] = u.x; iv[1] = u.y; iv[2] = u.z; iv[3] = u.w;
                 iv[4] = v.x; iv[5] = v.y; iv[6] = v.z; iv[7] = v.w;
             }
-            // The run's first window covers walker columns c0 .. c0 + 2r.  With the swizzled layout a whole block of
-            // 8 columns occupies 8 consecutive slots in some order, which a sum does not see: full blocks are read
-            // slot by slot, lane g taking slot (e + g) mod 8 at step e so that the 8 lanes of a quarter-warp fall on
-            // distinct banks, and only the columns of a partial block go through the swizzle.
-            const int c0 = pg * SP_RUN;
-            int rot[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) rot[e] = c0 + ((e + pg) & 7);
-            auto idx_of = [&](int c) { return NQ == 1 ? vidx2(c) : vidx4(c); };
+            const RunReader<NQ> rd(buf, pk, pg);
             float2 T[NQ];
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) T[q] = make_float2(0.0f, 0.0f);
-            auto acc = [&](int idx) {
-                float2 u[NQ];
-                get_sums<NQ>(buf, pk, idx, u);
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) T[q] = add2(T[q], u[q]);
-            };
-            if constexpr (RC >= 0) {
-                constexpr int full = (NQ == 1) ? 0 : (2 * RC + 1) / 8;
-#pragma unroll
-                for (int i = 0; i < 8 * full; ++i) acc(rot[i & 7] + (i & ~7));
-#pragma unroll
-                for (int i = 8 * full; i <= 2 * RC; ++i) acc(idx_of(c0 + i));
-            } else {
-                const int full = (NQ == 1) ? 0 : (2 * r + 1) / 8;
-                for (int b8 = 0; b8 < 8 * full; b8 += 8) {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) acc(rot[e] + b8);
-                }
-#pragma unroll 4
-                for (int i = 8 * full; i <= 2 * r; ++i) acc(idx_of(c0 + i));
-            }
+            float2 W8[NQ == 1 ? SP_RUN : 1];
+            if constexpr (NQ == 1) rd.windows8<RC>(r, W8);
+            else rd.window<RC>(r, T);
             const bool interior = x_interior && (y - r >= 0) && (y + r < h);
             const int ny = min(h - 1, y + r) - max(0, y - r) + 1;
+            // output rows of this run
             constexpr int NO = (KIND == SK_STATS) ? 2 * NY : (KIND == SK_MEAN2 ? 2 : 1);
-            float o[NO][4];
+            float *dst0[NO / 2 > 0 ? NO / 2 : 1], *dst1[NO / 2 > 0 ? NO / 2 : 1];
+            TQ *dq = nullptr;
+            if constexpr (KIND == SK_MEAN2_OUT) {
+                dq = (TQ *)P.q + (size_t)(n * P.C + grp) * P.fps + (size_t)y * w + ox;
+            } else {
 #pragma unroll
-            for (int j = 0; j < SP_RUN; ++j) {
-                if (j > 0) {
-                    float2 ua[NQ], ub[NQ];
-                    get_sums<NQ>(buf, pk, idx_of(c0 + j + 2 * r), ua);
-                    get_sums<NQ>(buf, pk, idx_of(c0 + j - 1), ub);
-#pragma unroll
-                    for (int q = 0; q < NQ; ++q) T[q] = add2(T[q], sub2(ua[q], ub[q]));
+                for (int k = 0; k < NO / 2; ++k) {
+                    const size_t off = (size_t)(n * P.C + grp * (NO / 2) + k) * P.ops + (size_t)y * w + ox;
+                    dst0[k] = P.out0 + off;
+                    dst1[k] = P.out1 + off;
                 }
-                float inv = inv_full;
-                if (!interior) {
-                    const int xx = ox + j;
-                    const int nx = min(w - 1, xx + r) - max(0, xx - r) + 1;
-                    inv = __fdividef(1.0f, (float)(nx * ny));
-                }
-                const float2 iv2 = make_float2(inv, inv);
-                const int jj = j & 3;
-                if constexpr (KIND == SK_STATS) {
-                    const float2 m0 = mul2(T[0], iv2);
-                    if constexpr (NY == 1) {
-                        const float2 m1 = mul2(T[1], iv2);
-                        // var_I, cov_Ip; exactly 0 for a one-sample window (r = 0), as in the tile kernels
-                        const float var = r ? fmaxf(fmaf(-m0.x, m0.x, m1.x), 0.0f) : 0.0f;
-                        const float cov = r ? fmaf(-m0.x, m0.y, m1.y) : 0.0f;
-                        const float a = __fdividef(cov, var + P.eps);            // a, Eq. (2)
-                        o[0][jj] = a;
-                        o[1][jj] = (m0.y + col.c[1]) - a * (m0.x + col.c[0]);    // b, Eq. (3)
-                    } else {
-                        const float2 m1 = mul2(T[1], iv2), m2 = mul2(T[2], iv2), m3 = mul2(T[3], iv2);
-                        const float var = r ? fmaxf(fmaf(-m0.x, m0.x, m2.x), 0.0f) : 0.0f;
-                        const float rv = __fdividef(1.0f, var + P.eps);
-                        const float mx = m0.x + col.c[0];
-                        const float my[3] = {m0.y, m1.x, m1.y}, mxy[3] = {m2.y, m3.x, m3.y};
+            }
+            auto run = [&](auto border_tag) {
+                constexpr bool BORDER = decltype(border_tag)::value;
+                float o[NO][4];
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const float cov = r ? fmaf(-m0.x, my[k], mxy[k]) : 0.0f;
-                            const float a = cov * rv;                             // a, Eq. (2)
-                            o[2 * k][jj] = a;
-                            o[2 * k + 1][jj] = (my[k] + col.c[1 + k]) - a * mx;   // b, Eq. (3)
-                        }
+                for (int j = 0; j < SP_RUN; ++j) {
+                    if constexpr (NQ == 1) T[0] = W8[j];
+                    else if (j > 0) rd.slide<RC>(j, r, T);
+                    float inv = inv_full;
+                    if constexpr (BORDER) {
+                        const int xx = ox + j;
+                        const int nx = min(w - 1, xx + r) - max(0, xx - r) + 1;
+                        inv = __fdividef(1.0f, (float)(nx * ny));
                     }
-                } else if constexpr (KIND == SK_MEAN2) {
-                    o[0][jj] = T[0].x * inv;  // mean_a
-                    o[1][jj] = T[0].y * inv;  // mean_b
-                } else {
-                    float qv = fmaf(T[0].x * inv, iv[j], T[0].y * inv);  // Eq. (4)
-                    if (P.detail != 0.0f) qv = fmaf(P.detail, iv[j] - qv, qv);
-                    o[0][jj] = qv;
-                }
-                if (jj == 3 && (j == 3 || second)) {  // a float4 of every output plane
-                    const int xs = ox + j - 3;
-                    if constexpr (KIND == SK_MEAN2_OUT) {
-                        store4q<TQ>((TQ *)P.q + (size_t)(n * P.C + grp) * P.fps + (size_t)y * w + xs, o[0]);
-                    } else {
+                    const float2 iv2 = make_float2(inv, inv);
+                    const int jj = j & 3;
+                    if constexpr (KIND == SK_STATS) {
+                        const float2 m0 = mul2(T[0], iv2);
+                        if constexpr (NY == 1) {
+                            const float2 m1 = mul2(T[1], iv2);
+                            // var_I, cov_Ip; exactly 0 for a one-sample window (r = 0), as in the tile kernels
+                            const float var = r ? fmaxf(fmaf(-m0.x, m0.x, m1.x), 0.0f) : 0.0f;
+                            const float cov = r ? fmaf(-m0.x, m0.y, m1.y) : 0.0f;
+                            const float a = __fdividef(cov, var + P.eps);            // a, Eq. (2)
+                            o[0][jj] = a;
+                            o[1][jj] = (m0.y + col.c[1]) - a * (m0.x + col.c[0]);    // b, Eq. (3)
+                        } else {
+                            const float2 m1 = mul2(T[1], iv2), m2 = mul2(T[2], iv2), m3 = mul2(T[3], iv2);
+                            const float var = r ? fmaxf(fmaf(-m0.x, m0.x, m2.x), 0.0f) : 0.0f;
+                            const float rv = __fdividef(1.0f, var + P.eps);
+                            const float mx = m0.x + col.c[0];
+                            const float my[3] = {m0.y, m1.x, m1.y}, mxy[3] = {m2.y, m3.x, m3.y};
 #pragma unroll
-                        for (int k = 0; k < NO / 2; ++k) {
-                            const size_t off = (size_t)(n * P.C + grp * (NO / 2) + k) * P.ops + (size_t)y * w + xs;
-                            const float4 va = make_float4(o[2 * k][0], o[2 * k][1], o[2 * k][2], o[2 * k][3]);
-                            const float4 vb = make_float4(o[2 * k + 1][0], o[2 * k + 1][1], o[2 * k + 1][2], o[2 * k + 1][3]);
-                            if (P.stream_out) {  // planes larger than L2: streamed past the rows kept there
-                                __stcs(reinterpret_cast<float4 *>(P.out0 + off), va);
-                                __stcs(reinterpret_cast<float4 *>(P.out1 + off), vb);
-                            } else {             // small planes stay in L2 for the next kernel
-                                *reinterpret_cast<float4 *>(P.out0 + off) = va;
-                                *reinterpret_cast<float4 *>(P.out1 + off) = vb;
+                            for (int k = 0; k < 3; ++k) {
+                                const float cov = r ? fmaf(-m0.x, my[k], mxy[k]) : 0.0f;
+                                const float a = cov * rv;                             // a, Eq. (2)
+                                o[2 * k][jj] = a;
+                                o[2 * k + 1][jj] = (my[k] + col.c[1 + k]) - a * mx;   // b, Eq. (3)
+                            }
+                        }
+                    } else if constexpr (KIND == SK_MEAN2) {
+                        o[0][jj] = T[0].x * inv;  // mean_a
+                        o[1][jj] = T[0].y * inv;  // mean_b
+                    } else {
+                        o[0][jj] = fmaf(T[0].x * inv, iv[j], T[0].y * inv);  // Eq. (4)
+                    }
+                    if (jj == 3 && (j == 3 || second)) {  // a float4 of every output plane
+                        const int xs = j - 3;
+                        if constexpr (KIND == SK_MEAN2_OUT) {
+                            if (P.detail != 0.0f) {
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) o[0][e] = fmaf(P.detail, iv[xs + e] - o[0][e], o[0][e]);
+                            }
+                            store4q<TQ>(dq + xs, o[0]);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < NO / 2; ++k) {
+                                const float4 va = make_float4(o[2 * k][0], o[2 * k][1], o[2 * k][2], o[2 * k][3]);
+                                const float4 vb =
+                                    make_float4(o[2 * k + 1][0], o[2 * k + 1][1], o[2 * k + 1][2], o[2 * k + 1][3]);
+                                if (P.stream_out) {  // planes larger than L2: streamed
+                                    __stcs(reinterpret_cast<float4 *>(dst0[k] + xs), va);
+                                    __stcs(reinterpret_cast<float4 *>(dst1[k] + xs), vb);
+                                } else {             // small planes stay in L2 for the next kernel
+                                    *reinterpret_cast<float4 *>(dst0[k] + xs) = va;
+                                    *reinterpret_cast<float4 *>(dst1[k] + xs) = vb;
+                                }
                             }
                         }
                     }
                 }
-            }
+            };
+            if (interior) run(std::false_type{});
+            else run(std::true_type{});
         }
         if (NBUF == 1 && b + 1 < nblocks) __syncthreads();  // the column sums are rewritten by the next block
     }
@@ -477,6 +595,7 @@ cudaError_t launch_radius(const StripParams &P, int N, cudaStream_t st)
 {
     if (P.r == 16) return launch_strip<KIND, NY, 16, TQ>(P, N, st);
     if (P.r == 15) return launch_strip<KIND, NY, 15, TQ>(P, N, st);
+    if (P.r == 4) return launch_strip<KIND, NY, 4, TQ>(P, N, st);
     return launch_strip<KIND, NY, -1, TQ>(P, N, st);
 }
 
