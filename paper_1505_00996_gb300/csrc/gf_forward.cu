@@ -1329,12 +1329,15 @@ bool aligned_vec_subsample(const FwdPlan &P)
 // 177 k MP/s); the feathering figure's r' = 15 at s = 4 38 against 47 us.
 static bool box_tma_pays(int, int) { return true; }
 // The column-strip kernels (gf_strip.cu) take the box steps at large radii, where the tiles' 2r halo rows and
-// columns cost more than their outputs.
-// GF_STRIP_MIN_R (read once) lowers the threshold, so that tests can run every radius through these kernels.
-static bool strip_pays(int r)
+// columns cost more than their outputs, and on large planes, whose long segments amortise the window opening.
+// Measured on the 12 MP scene (3 channels, gray guide): s = 1 calls at r = 4 / 8 / 12 take 246 / 287 / 305 us
+// with strips against 291 / 335 / 482 us with tiles; s = 4 calls (0.75 MP low-res planes) at r' = 6, 8 take
+// 88.2 / 87.4 us against 83.5 / 84.5 us.  GF_STRIP_MIN_R (read per call) replaces the rule by r >= its value,
+// so that tests and measurements can send any radius through either form.
+static bool strip_pays(int r, int h, int w)
 {
-    static const int min_r = getenv("GF_STRIP_MIN_R") ? atoi(getenv("GF_STRIP_MIN_R")) : 9;
-    return r >= min_r;
+    const char *e = getenv("GF_STRIP_MIN_R");
+    return r >= (e ? atoi(e) : 9) || (!e && (long long)h * w >= (2LL << 20));
 }
 
 bool s1_means_output_form(const Resolved &R)
@@ -1371,7 +1374,7 @@ cudaError_t launch_color_chain(const FwdPlan &P0, float *pl, StageTimer &tm, cud
         J.h = P.h; J.w = P.w; J.r = P.r_low;
         J.out0 = oX; J.out1 = oY;
         J.fault = P.fault;
-        if (strip_pays(P.r_low) && strip_box_supported(J)) return launch_strip_box(J, st);
+        if (strip_pays(P.r_low, P.h, P.w) && strip_box_supported(J)) return launch_strip_box(J, st);
         if (box_tma_pays(P.s, P.r_low) && box_tma_supported(J)) return launch_box_tma(J, st);
         BoxParams bp{};
         bp.X = X; bp.Y = Y;
@@ -1507,7 +1510,7 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         J.stats = P.int_stats ? nullptr : (float *)P.stats;
         J.fault = P.fault;
         const bool fp32 = !P.int_stats && src_dt == F32;
-        const bool strip = fp32 && strip_pays(P.r_low) && strip_box_supported(J);
+        const bool strip = fp32 && strip_pays(P.r_low, P.h, P.w) && strip_box_supported(J);
         const bool tma = !strip && fp32 && box_tma_pays(P.s, P.r_low) && box_tma_supported(J);
         tm.before();
         if (strip) {
@@ -1537,7 +1540,7 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         J.I = (const float *)P.I; J.q = P.q; J.fps = P.fps; J.CI = P.CI;
         J.Yw0 = P.Yw0; J.Yw1 = P.Yw1; J.dt_out = P.dt_out; J.detail = P.detail;
         J.fault = P.fault;
-        const bool strip = strip_pays(P.r_low) && strip_box_supported(J);
+        const bool strip = strip_pays(P.r_low, P.h, P.w) && strip_box_supported(J);
         if (strip || box_tma_supported(J)) {
             tm.before();
             err = strip ? launch_strip_box(J, st) : launch_box_tma(J, st);
@@ -1557,7 +1560,7 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         J.out0 = P.ma; J.out1 = P.mb;
         J.fault = P.fault;
         tm.before();
-        if (strip_pays(P.r_low) && strip_box_supported(J)) {
+        if (strip_pays(P.r_low, P.h, P.w) && strip_box_supported(J)) {
             err = launch_strip_box(J, st);
         } else if (box_tma_pays(P.s, P.r_low) && box_tma_supported(J)) {
             err = launch_box_tma(J, st);

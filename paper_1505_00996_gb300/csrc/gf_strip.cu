@@ -78,9 +78,14 @@ __device__ __forceinline__ int vidx4(int c) { return c ^ ((c >> 3) & 7); }
 __device__ __forceinline__ int vidx2(int c) { return c + 2 * (c >> 3); }
 
 // Bytes of shared memory of one CTA.
+// The block sums shared by the runs of a row: [SP_CB rows][SP_NT / 8 blocks] of NQ float2 (as NQ / 2 float4
+// arrays when NQ >= 2).
+constexpr int SP_NBLK = SP_NT / 8;
+__host__ __device__ constexpr size_t bsum_bytes(int NQ) { return (size_t)SP_CB * SP_NBLK * 8 * NQ; }
 __host__ __device__ constexpr size_t strip_smem(int NQ)
 {
-    return (size_t)(db_of(NQ) ? 2 : 1) * SP_CB * vp_of(NQ) * (NQ == 1 ? 8 : 16) * (NQ == 1 ? 1 : NQ / 2);
+    return (size_t)(db_of(NQ) ? 2 : 1) * SP_CB * vp_of(NQ) * (NQ == 1 ? 8 : 16) * (NQ == 1 ? 1 : NQ / 2) +
+           bsum_bytes(NQ);
 }
 
 // One strip column's sources: the planes it reads (statistics: the guide, then NY inputs; box means: a, b),
@@ -242,39 +247,58 @@ struct RunReader {
     }
     // NQ == 1: columns c0 + i and c0 + i + 1 (i even) as (a, b, a', b')
     __device__ __forceinline__ float4 pair_at(int i) const { return pair2[(i + 2 * (i >> 3)) >> 1]; }
-    // NQ == 1: the window sums of the run's 8 outputs at once
+    // The windows of the run's outputs from the sums of whole 8-column blocks, which the 16 runs of a row (lanes
+    // of one half-warp) share through this row's block sums `bs`: a run sums its own block (whose columns leave
+    // its windows) and reads the other full blocks' sums, then only single columns of the block or two that its
+    // windows' right ends cross.  Output j's window is walker columns c0 + j .. c0 + j + 2r: n = 2r + 1 columns,
+    // for j = 0 nb full blocks and rem columns of block nb (relative to the run's own block).  Blocks 16 .. 19
+    // (the strip's right halo) are no run's own block: the run nb blocks to their left sums them.  Every lane of
+    // the warp calls these (they synchronise the warp), live run or not; `bs` is next written after the block
+    // barrier that follows the next phase 1.
+    //
+    // NQ == 1: all 8 window sums W at once; the own block's columns stay in registers, the entering columns
+    // n .. n + 6 are the 4 column pairs from n - 1.
     template <int RC>
-    __device__ __forceinline__ void windows8(int r, float2 W[SP_RUN]) const
+    __device__ __forceinline__ void windows8_shared(int r, float2 *bs, float2 W[SP_RUN]) const
     {
-        const int rr = RC >= 0 ? RC : r;
-        float2 a = make_float2(0.0f, 0.0f), b = make_float2(0.0f, 0.0f);
-        if constexpr (RC >= 0) {
+        const int n = 2 * (RC >= 0 ? RC : r) + 1, nb = n >> 3, rem = n & 7;
+        float2 own[8];
 #pragma unroll
-            for (int i = 0; i < 2 * RC; i += 2) {
-                const float4 q = pair_at(i);
-                a = add2(a, make_float2(q.x, q.y));
-                b = add2(b, make_float2(q.z, q.w));
-            }
-        } else {
-#pragma unroll 4
-            for (int i = 0; i < 2 * r; i += 2) {
-                const float4 q = pair_at(i);
-                a = add2(a, make_float2(q.x, q.y));
-                b = add2(b, make_float2(q.z, q.w));
-            }
+        for (int i = 0; i < 8; i += 2) {
+            const float4 q = pair_at(i);
+            own[i] = make_float2(q.x, q.y);
+            own[i + 1] = make_float2(q.z, q.w);
         }
-        // column 2r closes the first window; columns 2r + 1 .. 2r + 7 enter, columns 0 .. 6 leave
-        const float4 e0 = pair_at(2 * rr), e1 = pair_at(2 * rr + 2), e2 = pair_at(2 * rr + 4), e3 = pair_at(2 * rr + 6);
-        const float4 l0 = pair_at(0), l1 = pair_at(2), l2 = pair_at(4), l3 = pair_at(6);
-        const float2 enter[8] = {make_float2(0.0f, 0.0f), make_float2(e0.z, e0.w), make_float2(e1.x, e1.y),
-                                 make_float2(e1.z, e1.w),  make_float2(e2.x, e2.y), make_float2(e2.z, e2.w),
-                                 make_float2(e3.x, e3.y),  make_float2(e3.z, e3.w)};
-        const float2 leave[8] = {make_float2(l0.x, l0.y), make_float2(l0.z, l0.w), make_float2(l1.x, l1.y),
-                                 make_float2(l1.z, l1.w), make_float2(l2.x, l2.y), make_float2(l2.z, l2.w),
-                                 make_float2(l3.x, l3.y), make_float2(l3.z, l3.w)};
-        W[0] = add2(add2(a, b), make_float2(e0.x, e0.y));
+        const float2 b_own = add2(add2(add2(own[0], own[1]), add2(own[2], own[3])),
+                                  add2(add2(own[4], own[5]), add2(own[6], own[7])));
+        bs[pg] = b_own;
+        if (pg + nb >= SP_TW / 8 && pg + nb < SP_NBLK) {
+            float2 f = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int j = 1; j < SP_RUN; ++j) W[j] = add2(W[j - 1], sub2(enter[j], leave[j - 1]));
+            for (int i = 0; i < 8; i += 2) {
+                const float4 q = pair_at(8 * nb + i);
+                f = add2(f, add2(make_float2(q.x, q.y), make_float2(q.z, q.w)));
+            }
+            bs[pg + nb] = f;
+        }
+        __syncwarp();
+        float2 w0 = nb >= 1 ? b_own : make_float2(0.0f, 0.0f);
+        for (int d = 1; d < nb; ++d) w0 = add2(w0, bs[pg + d]);
+        for (int c = 0; c < rem; c += 2) {
+            const float4 q = pair_at(8 * nb + c);
+            w0 = add2(w0, make_float2(q.x, q.y));
+            if (c + 1 < rem) w0 = add2(w0, make_float2(q.z, q.w));
+        }
+        float4 ep[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) ep[t] = pair_at(n - 1 + 2 * t);
+        W[0] = w0;
+#pragma unroll
+        for (int j = 1; j < SP_RUN; ++j) {
+            const float4 q = ep[j >> 1];  // column n + j - 1 = (n - 1) + j
+            const float2 e = (j & 1) ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
+            W[j] = add2(W[j - 1], sub2(e, own[j - 1]));
+        }
     }
     __device__ __forceinline__ void add_at(const float4 *p, float2 T[NQ]) const
     {
@@ -304,32 +328,44 @@ struct RunReader {
         const int blk = pg + (i >> 3);
         return row4 + 8 * blk + ((i & 7) ^ (blk & 7));
     }
-    // T = sums of walker columns c0 .. c0 + 2r
+    // NQ >= 2: T = the first window's sums (the slides re-read single columns: the own block's columns would take
+    // 8 NQ registers).  bA / bB hold pairs 0-1 and 2-3 of this row's block sums.
     template <int RC>
-    __device__ __forceinline__ void window(int r, float2 T[NQ]) const
+    __device__ __forceinline__ void window_shared(int r, float4 *bA, float4 *bB, float2 T[NQ]) const
     {
+        const int n = 2 * (RC >= 0 ? RC : r) + 1, nb = n >> 3, rem = n & 7;
+        auto block_sum = [&](int blk, float2 B[NQ]) {  // slot (e + g) mod 8 at step e: distinct banks per quarter-warp
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) T[q] = make_float2(0.0f, 0.0f);
-        if constexpr (NQ == 1) {
-            // not used: windows8 gives the float2 layout's sums
-        } else {
-            const int n = 2 * (RC >= 0 ? RC : r) + 1, full = n >> 3;
-            const float4 *rot[8];
+            for (int q = 0; q < NQ; ++q) B[q] = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) rot[e] = row4 + 8 * pg + ((e + pg) & 7);
-            if constexpr (RC >= 0) {
+            for (int e = 0; e < 8; ++e) add_at(row4 + 8 * blk + ((e + pg) & 7), B);
+        };
+        auto put = [&](int m, const float2 B[NQ]) {
+            bA[m] = make_float4(B[0].x, B[0].y, B[1].x, B[1].y);
+            if constexpr (NQ == 4) bB[m] = make_float4(B[2].x, B[2].y, B[3].x, B[3].y);
+        };
+        float2 Bo[NQ];
+        block_sum(pg, Bo);
+        put(pg, Bo);
+        if (pg + nb >= SP_TW / 8 && pg + nb < SP_NBLK) {
+            float2 Bf[NQ];
+            block_sum(pg + nb, Bf);
+            put(pg + nb, Bf);
+        }
+        __syncwarp();
 #pragma unroll
-                for (int i = 0; i < 8 * ((2 * RC + 1) >> 3); ++i) add_at(rot[i & 7] + (i & ~7), T);
-#pragma unroll
-                for (int i = 8 * ((2 * RC + 1) >> 3); i <= 2 * RC; ++i) add_at(col4(i), T);
-            } else {
-                for (int b8 = 0; b8 < 8 * full; b8 += 8) {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) add_at(rot[e] + b8, T);
-                }
-                for (int i = 8 * full; i < n; ++i) add_at(col4(i), T);
+        for (int q = 0; q < NQ; ++q) T[q] = nb >= 1 ? Bo[q] : make_float2(0.0f, 0.0f);
+        for (int d = 1; d < nb; ++d) {
+            const float4 a = bA[pg + d];
+            T[0] = add2(T[0], make_float2(a.x, a.y));
+            T[1] = add2(T[1], make_float2(a.z, a.w));
+            if constexpr (NQ == 4) {
+                const float4 b = bB[pg + d];
+                T[2] = add2(T[2], make_float2(b.x, b.y));
+                T[3] = add2(T[3], make_float2(b.z, b.w));
             }
         }
+        for (int c = 0; c < rem; ++c) add_at(col4(8 * nb + c), T);
     }
     // the window of output j from that of output j - 1: column c0 + j + 2r enters, c0 + j - 1 leaves
     template <int RC>
@@ -346,12 +382,13 @@ struct RunReader {
     }
 };
 
-// CTAs per SM the registers are sized for: four, three for the three-channel statistics, whose batch of entering
-// rows (four planes) needs the registers of a 3-CTA split.
-__host__ __device__ constexpr int minb_of(int NQ) { return NQ == 4 ? 3 : 4; }
+// CTAs per SM the registers are sized for: four; three for the three-channel statistics, whose batch of entering
+// rows (four planes) needs the registers of a 3-CTA split, and for the box means + output, which also holds the
+// next block's guide row.
+__host__ __device__ constexpr int minb_of(int KIND, int NQ) { return (NQ == 4 || KIND == SK_MEAN2_OUT) ? 3 : 4; }
 
 template <int KIND, int NY, int RC, typename TQ>
-__global__ void __launch_bounds__(SP_NT, minb_of(nq_of(KIND, NY))) k_box_strip(StripParams P)
+__global__ void __launch_bounds__(SP_NT, minb_of(KIND, nq_of(KIND, NY))) k_box_strip(StripParams P)
 {
     constexpr int NQ = nq_of(KIND, NY);
     constexpr int NS = Column<KIND, NY>::NS;
@@ -405,6 +442,19 @@ __global__ void __launch_bounds__(SP_NT, minb_of(nq_of(KIND, NY))) k_box_strip(S
     const bool x_interior = (ox - r >= 0) && (ox + SP_RUN - 1 + r < w);
 
     const int nblocks = (yend - y0 + SP_CB - 1) / SP_CB;
+    // SK_MEAN2_OUT: the guide under this thread's run of output row y, requested a block ahead of its use
+    float ivn[8];
+    auto load_guide = [&](int yg, float (&dst)[8]) {
+        if (yg < yend && ox < w) {
+            const float *Ip = P.I + (size_t)(n * P.CI + (P.CI == 1 ? 0 : grp)) * P.fps + (size_t)yg * w + ox;
+            const float4 u = __ldcs(reinterpret_cast<const float4 *>(Ip));
+            const float4 v = second ? __ldcs(reinterpret_cast<const float4 *>(Ip) + 1)
+                                    : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            dst[0] = u.x; dst[1] = u.y; dst[2] = u.z; dst[3] = u.w;
+            dst[4] = v.x; dst[5] = v.y; dst[6] = v.z; dst[7] = v.w;
+        }
+    };
+    if constexpr (KIND == SK_MEAN2_OUT) load_guide(y0 + pk, ivn);
     RowBatch<KIND, NY> B;
     if (colok) B.fetch(col, y0, r, h);
     for (int b = 0; b < nblocks; ++b) {
@@ -423,21 +473,26 @@ __global__ void __launch_bounds__(SP_NT, minb_of(nq_of(KIND, NY))) k_box_strip(S
 
         // ---- phase 2: horizontal window sums along a run of 8 outputs, epilogue, 128-bit stores
         const int y = yb + pk;
-        if (y < yend && ox < w) {
-            float iv[8];
-            if constexpr (KIND == SK_MEAN2_OUT) {  // the guide under the run, requested before the sums
-                const float *Ip = P.I + (size_t)(n * P.CI + (P.CI == 1 ? 0 : grp)) * P.fps + (size_t)y * w + ox;
-                const float4 u = __ldcs(reinterpret_cast<const float4 *>(Ip));
-                const float4 v = second ? __ldcs(reinterpret_cast<const float4 *>(Ip) + 1)
-                                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                iv[0] = u.x; iv[1] = u.y; iv[2] = u.z; iv[3] = u.w;
-                iv[4] = v.x; iv[5] = v.y; iv[6] = v.z; iv[7] = v.w;
+        const bool live = (y < yend) && (ox < w);
+        float iv[8];
+        if constexpr (KIND == SK_MEAN2_OUT) {  // this block's guide row; the next block's is requested now
+#pragma unroll
+            for (int e = 0; e < 8; ++e) iv[e] = ivn[e];
+            if (b + 1 < nblocks) load_guide(y + SP_CB, ivn);
+        }
+        const RunReader<NQ> rd(buf, pk, pg);
+        float2 W8[NQ == 1 ? SP_RUN : 1];
+        float2 T[NQ];
+        {
+            unsigned char *bs = sm + NBUF * buf_bytes(NQ);
+            if constexpr (NQ == 1) {
+                rd.template windows8_shared<RC>(r, reinterpret_cast<float2 *>(bs) + pk * SP_NBLK, W8);
+            } else {
+                float4 *bA = reinterpret_cast<float4 *>(bs) + pk * SP_NBLK;
+                rd.template window_shared<RC>(r, bA, bA + SP_CB * SP_NBLK, T);
             }
-            const RunReader<NQ> rd(buf, pk, pg);
-            float2 T[NQ];
-            float2 W8[NQ == 1 ? SP_RUN : 1];
-            if constexpr (NQ == 1) rd.windows8<RC>(r, W8);
-            else rd.window<RC>(r, T);
+        }
+        if (live) {
             const bool interior = x_interior && (y - r >= 0) && (y + r < h);
             const int ny = min(h - 1, y + r) - max(0, y - r) + 1;
             // output rows of this run
@@ -460,7 +515,7 @@ __global__ void __launch_bounds__(SP_NT, minb_of(nq_of(KIND, NY))) k_box_strip(S
 #pragma unroll
                 for (int j = 0; j < SP_RUN; ++j) {
                     if constexpr (NQ == 1) T[0] = W8[j];
-                    else if (j > 0) rd.slide<RC>(j, r, T);
+                    else if (j > 0) rd.template slide<RC>(j, r, T);
                     float inv = inv_full;
                     if constexpr (BORDER) {
                         const int xx = ox + j;

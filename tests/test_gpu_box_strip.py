@@ -181,3 +181,20 @@ def test_color_guide_box_steps(gf, s, r):
     torch.cuda.synchronize()
     ref = oracle.color_guided_filter(I.astype(np.float64), p.astype(np.float64), r, 1e-3, s, oracle.SUB_BILINEAR)
     assert max_abs(q.cpu().numpy(), ref) <= TOL_F32
+
+
+@pytest.mark.parametrize("r", list(range(1, 9)))
+def test_small_radii_through_strips(gf, monkeypatch, r):
+    """Radii 1..8 through the strip kernels (GF_STRIP_MIN_R=1, read per call) at s = 1 and s = 4: the windows
+    narrower than a block of 8 columns and the run-time radius path."""
+    monkeypatch.setenv("GF_STRIP_MIN_R", "1")
+    I = _rand((1, 1, 173, 300), 600 + r)
+    p = _rand((1, 3, 173, 300), 610 + r)
+    q = _run(gf, I, p, r, 1e-3, 1)
+    assert max_abs(q, oracle_q(I, p, r, 1e-3, 1, oracle.SUB_BILINEAR)) <= TOL_F32
+    I4 = _rand((1, 2, 280, 520), 620 + r)
+    p4 = _rand((1, 2, 280, 520), 630 + r)
+    q4 = _run(gf, I4, p4, 4 * r, 1e-3, 4, r_low=r, fused=-1)
+    ref4 = oracle.fast_guided_filter(I4.astype(np.float64), p4.astype(np.float64), 4 * r, 1e-3, 4,
+                                     oracle.SUB_BILINEAR, r_low=r)
+    assert max_abs(q4, ref4) <= TOL_F32
