@@ -558,38 +558,32 @@ def run_small_images(dev, stream, ctx, world, calls=200):
 SERVE_POOL = 8  # input buffers the requests rotate through (8 x (24 MP I + 72 MP p) FP16 = 1.5 GB >> 129 MB L2)
 
 
-def run_serving(local, n_requests=512, slots=4):
-    """Seeded Poisson stream of mixed requests (0.3-24 MP, aspect 4:3 / 16:9 / 1:1, 1 or 3 channels,
-    r = round(0.004 max(H, W)), eps in {1e-4, 1e-2}, s in {4, 8}, FP16 storage) through gf_submit/gf_poll:
-    one-at-a-time launches (gf_filter, each waited for) give the capacity; the loop is then fed all requests
-    at once (queued with admission paused, then released: saturated) and as Poisson arrivals at 0.5, 0.8 and
-    1.0 x that capacity, with direct launches and again through per-bucket CUDA graphs.  Request k reads its
-    inputs from buffer k mod SERVE_POOL of a pool of distinct images, so requests in flight together never
-    share input lines through L2.  The host time the scheduler spends launching a request is reported against
-    the p50 latency of the requests under 2 MP."""
-    import paper_1505_00996_gb300 as gf
+def _serving_views(gf, dev, reqs, seed):
+    """Distinct FP16 inputs for a request stream: request k reads buffer k mod SERVE_POOL of a pool of copies of
+    one scene, each shifted by a different offset (so requests in flight together never share input lines
+    through L2), and writes its own output."""
     import synth
-    dev = torch.device("cuda", local)
-    reqs = synth.serving_stream(n_requests=n_requests, seed=2, rate_per_s=1.0)
     maxpix = max(rq["H"] * rq["W"] for rq in reqs)
     side = int(np.ceil(np.sqrt(maxpix)))
-    base = synth.make_scene(side, side, seed=2)
+    base = synth.make_scene(side, side, seed=seed)
     I0 = torch.from_numpy(base).to(torch.float16).to(dev).reshape(-1)[:maxpix]
-    p0 = torch.from_numpy(synth.rgb_noisy_input(base, seed=3)).to(torch.float16).to(dev).reshape(-1)[:3 * maxpix]
-    # distinct buffers with distinct content: the base image shifted by a different offset in each
+    p0 = torch.from_numpy(synth.rgb_noisy_input(base, seed=seed + 1)).to(torch.float16).to(dev).reshape(-1)[:3 * maxpix]
     pool = [(torch.roll(I0, 7919 * k), torch.roll(p0, 7919 * k)) for k in range(SERVE_POOL)]
     views = []
     for k, rq in enumerate(reqs):
         H, W, C = rq["H"], rq["W"], rq["C"]
         Ibuf, pbuf = pool[k % SERVE_POOL]
-        I = Ibuf[:H * W].view(H, W)
-        p = pbuf[:C * H * W].view(C, H, W)
-        q = torch.empty((C, H, W), dtype=torch.float16, device=dev)
-        views.append((I, p, q))
-    total_mp = sum(rq["H"] * rq["W"] for rq in reqs) / 1e6
-    small = np.array([rq["H"] * rq["W"] < 2e6 for rq in reqs])
+        views.append((Ibuf[:H * W].view(H, W), pbuf[:C * H * W].view(C, H, W),
+                      torch.empty((C, H, W), dtype=torch.float16, device=dev)))
+    return views
 
-    # one at a time: plain gf_filter launches, each waited for
+
+def _serve_stream(gf, local, reqs, views, slots, modes, small):
+    """One-at-a-time capacity, then for each (name, graphs, tile_queue) mode: the saturated form (all requests
+    queued with admission paused, then released) and Poisson arrivals at 0.5, 0.8 and 1.0 x capacity."""
+    n_requests = len(reqs)
+    dev = torch.device("cuda", local)
+    total_mp = sum(rq["H"] * rq["W"] for rq in reqs) / 1e6
     stream = torch.cuda.Stream(device=dev)
     for rq, (I, p, q) in list(zip(reqs, views))[:8]:
         gf.fast_guided_filter(I, p, rq["r"], rq["eps"], rq["s"], "bilinear", out=q, stream=stream)
@@ -602,13 +596,16 @@ def run_serving(local, n_requests=512, slots=4):
         service.append(time.perf_counter() - t0)
     one_total = sum(service)
     capacity = n_requests / one_total  # requests per second
+    svc_ms = np.array(service) * 1e3
+    out = {"one_at_a_time": {"mp_per_s": round(total_mp / one_total, 1),
+                             "p50_ms": round(float(np.percentile(svc_ms, 50)), 3),
+                             "p99_ms": round(float(np.percentile(svc_ms, 99)), 3),
+                             "capacity_req_per_s": round(capacity, 1)}}
 
-    def run_mode(graphs):
-        srv = gf.Server(device=local, hbm_budget_bytes=8 << 30, slots=slots, graphs=graphs)
+    def run_mode(graphs, tile_queue):
+        srv = gf.Server(device=local, hbm_budget_bytes=8 << 30, slots=slots, graphs=graphs, tile_queue=tile_queue)
 
         def run_stream(arrivals, held=False):
-            """Submit at the given arrival times; held: queue everything with admission paused, then release
-            it (the saturated form: latency counts from the release)."""
             tickets = []
             st0 = srv.stats()
             if held:
@@ -628,14 +625,15 @@ def run_serving(local, n_requests=512, slots=4):
             span = max(r["t_done"] for r in res) - t_start
             n = max(1, st1["launches"] - st0["launches"])
             launch_us = 1e6 * (st1["launch_seconds"] - st0["launch_seconds"]) / n
-            out = {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                   "mp_per_s": round(total_mp / span, 1), "launch_us_per_request": round(launch_us, 2),
-                   "graph_launch_share": round((st1["graph_launches"] - st0["graph_launches"]) / n, 3)}
-            if len(arrivals) == n_requests and not held:
+            o = {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                 "mp_per_s": round(total_mp / span, 1), "launch_us_per_request": round(launch_us, 2),
+                 "graph_launch_share": round((st1["graph_launches"] - st0["graph_launches"]) / n, 3),
+                 "tile_queue_share": round((st1["queue_requests"] - st0["queue_requests"]) / n, 3)}
+            if len(arrivals) == n_requests and small.any():
                 p50_small = float(np.percentile(lat[small], 50))
-                out["p50_ms_under_2mp"] = round(p50_small, 3)
-                out["launch_share_of_p50_under_2mp"] = round(launch_us / 1e3 / p50_small, 3)
-            return out
+                o["p50_ms_under_2mp"] = round(p50_small, 3)
+                o["launch_share_of_p50_under_2mp"] = round(launch_us / 1e3 / p50_small, 3)
+            return o
 
         run_stream([0.0] * 64)  # warm the loop (and the graphs of the common buckets)
         saturated = run_stream([0.0] * n_requests, held=True)
@@ -648,18 +646,48 @@ def run_serving(local, n_requests=512, slots=4):
             r["arrival_rate_per_s"] = round(lam, 1)
             loads.append(r)
         srv.close()
-        return saturated, loads
+        return {"saturated": saturated, "poisson": loads}
 
-    saturated, loads = run_mode(False)
-    saturated_graphs, loads_graphs = run_mode(True)
-    svc_ms = np.array(service) * 1e3
+    for name, graphs, tile_queue in modes:
+        out[name] = run_mode(graphs, tile_queue)
+    return out
+
+
+def run_serving(local, n_requests=512, slots=4):
+    """Seeded Poisson stream of mixed requests (0.3-24 MP, aspect 4:3 / 16:9 / 1:1, 1 or 3 channels,
+    r = round(0.004 max(H, W)), eps in {1e-4, 1e-2}, s in {4, 8}, FP16 storage) through gf_submit/gf_poll:
+    one-at-a-time launches (gf_filter, each waited for) give the capacity; the loop is then fed all requests
+    at once (queued with admission paused, then released: saturated) and as Poisson arrivals at 0.5, 0.8 and
+    1.0 x that capacity -- with direct launches and the tile queue (the default), with direct launches only,
+    and through per-bucket CUDA graphs.  Request k reads its inputs from buffer k mod SERVE_POOL of a pool of
+    distinct images, so requests in flight together never share input lines through L2.  The host time the
+    scheduler spends launching a request is reported against the p50 latency of the requests under 2 MP.
+    A second stream of small requests (0.05-0.33 MP, all of them single-kernel requests) shows the tile queue,
+    with and without it."""
+    import paper_1505_00996_gb300 as gf
+    import synth
+    dev = torch.device("cuda", local)
+    reqs = synth.serving_stream(n_requests=n_requests, seed=2, rate_per_s=1.0)
+    views = _serving_views(gf, dev, reqs, seed=2)
+    small = np.array([rq["H"] * rq["W"] < 2e6 for rq in reqs])
+    main = _serve_stream(gf, local, reqs, views, slots,
+                         [("default", False, True), ("direct", False, False), ("per_bucket_graphs", True, False)],
+                         small)
+    del views
+    sreqs = synth.serving_stream(n_requests=n_requests, seed=5, rate_per_s=1.0, mp_range=(0.05, 0.33))
+    sviews = _serving_views(gf, dev, sreqs, seed=5)
+    ssmall = np.ones(len(sreqs), dtype=bool)
+    small_stream = _serve_stream(gf, local, sreqs, sviews, slots,
+                                 [("tile_queue", False, True), ("direct", False, False)], ssmall)
+    total_mp = sum(rq["H"] * rq["W"] for rq in reqs) / 1e6
     return {"requests": n_requests, "slots": slots, "storage": "f16", "total_mp": round(total_mp, 1),
-            "inputs": "request k reads buffer k mod %d of a pool of distinct images (1.5 GB), no input shared "
+            "inputs": "request k reads buffer k mod %d of a pool of distinct images, no input shared "
                       "through L2 by requests in flight together" % SERVE_POOL, "requests_under_2mp": int(small.sum()),
-            "one_at_a_time": {"mp_per_s": round(total_mp / one_total, 1), "p50_ms": round(float(np.percentile(svc_ms, 50)), 3),
-                              "p99_ms": round(float(np.percentile(svc_ms, 99)), 3), "capacity_req_per_s": round(capacity, 1)},
-            "saturated": saturated, "poisson": loads,
-            "per_bucket_graphs": {"saturated": saturated_graphs, "poisson": loads_graphs}}
+            "one_at_a_time": main["one_at_a_time"], "saturated": main["default"]["saturated"],
+            "poisson": main["default"]["poisson"], "direct": main["direct"],
+            "per_bucket_graphs": main["per_bucket_graphs"],
+            "small_requests": dict(small_stream, requests=n_requests, mp_range=[0.05, 0.33],
+                                   total_mp=round(sum(rq["H"] * rq["W"] for rq in sreqs) / 1e6, 1))}
 
 
 # --------------------------------------------------------------------------------------------------------

@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define GF_ABI_VERSION 4
+#define GF_ABI_VERSION 5
 #define GF_MAX_STAGES 8 /* kernel stages one gf_filter call can launch (for gf_opts.kernel_events) */
 #define GF_FUSED_AUTO_PIXELS (1 << 20) /* gf_opts.fused = 0 runs the single kernel up to N*C*H*W pixels */
 
@@ -301,6 +301,8 @@ typedef struct gf_serve_stats {
     size_t budget_bytes, scratch_in_use;
     long long launches;        /* requests launched so far */
     long long graph_launches;  /* of which through their bucket's CUDA graph (gf_serve_graphs) */
+    long long queue_launches;  /* tile-queue launches (gf_serve_tile_queue) */
+    long long queue_requests;  /* requests those launches carried */
     double launch_seconds;     /* host time the scheduler spent enqueuing them (kernels and bookkeeping) */
 } gf_serve_stats;
 
@@ -318,6 +320,16 @@ gf_status gf_serve_config(gf_ctx *ctx, int slots, size_t queue_limit);
  * costs less host time per request on a GB300 host (18 us against 28-34 us for capture, update and graph
  * launch).  Only before the first gf_submit on the context (GF_EBUSY afterwards). */
 gf_status gf_serve_graphs(gf_ctx *ctx, int enable);
+
+/* The tile queue for the serving launches (one launch for requests of mixed sizes): enable = 1 (the
+ * default) admits, once every other slot is taken, the requests that gf_filter would run as its single kernel
+ * (small images, no colour guide) and that stand next to each other at the head of the queue with the same
+ * storage types and subsample mode together onto the last slot, up to 16, and runs them as ONE launch of that
+ * kernel's tile-queue form: a grid over
+ * their (request, tile) items with one descriptor per request.  Every request keeps its own scratch, fault
+ * word, completion and result, bit for bit its solo result.  0 launches every request on its own.  Only
+ * before the first gf_submit on the context (GF_EBUSY afterwards). */
+gf_status gf_serve_tile_queue(gf_ctx *ctx, int enable);
 
 /* Queue a request.  GF_EINVAL for bad arguments, GF_ENOMEM if its scratch can never fit the budget,
  * GF_EBUSY if the queue is full; otherwise GF_OK and *ticket. */

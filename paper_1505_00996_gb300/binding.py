@@ -32,7 +32,7 @@ class GFError(RuntimeError):
         self.status = status
 
 
-ABI_VERSION = 4  # GF_ABI_VERSION of include/gf.h that GFOpts mirrors
+ABI_VERSION = 5  # GF_ABI_VERSION of include/gf.h that GFOpts mirrors
 
 
 class GFOpts(ctypes.Structure):
@@ -84,7 +84,8 @@ class GFServeStats(ctypes.Structure):
     _fields_ = [
         ("queued", ctypes.c_int), ("running", ctypes.c_int), ("slots", ctypes.c_int),
         ("budget_bytes", ctypes.c_size_t), ("scratch_in_use", ctypes.c_size_t),
-        ("launches", ctypes.c_longlong), ("graph_launches", ctypes.c_longlong), ("launch_seconds", ctypes.c_double),
+        ("launches", ctypes.c_longlong), ("graph_launches", ctypes.c_longlong),
+        ("queue_launches", ctypes.c_longlong), ("queue_requests", ctypes.c_longlong), ("launch_seconds", ctypes.c_double),
     ]
 
 
@@ -153,6 +154,8 @@ def load_library(build_if_missing=True):
         lib.gf_serve_pause.restype = i
         lib.gf_serve_graphs.argtypes = [vp, i]
         lib.gf_serve_graphs.restype = i
+        lib.gf_serve_tile_queue.argtypes = [vp, i]
+        lib.gf_serve_tile_queue.restype = i
         lib.gf_submit.argtypes = [vp, P(GFRequest), P(ctypes.c_uint64)]
         lib.gf_submit.restype = i
         lib.gf_poll.argtypes = [vp, ctypes.c_uint64, ctypes.c_int64, P(GFResult)]

@@ -783,6 +783,12 @@ gf_status gf_serve_graphs(gf_ctx *ctx, int enable)
     return gfk::server_graphs(ctx->server, enable);
 }
 
+gf_status gf_serve_tile_queue(gf_ctx *ctx, int enable)
+{
+    if (!ctx) return fail(GF_EINVAL, "ctx is NULL");
+    return gfk::server_queue(ctx->server, enable);
+}
+
 gf_status gf_serve_pause(gf_ctx *ctx, int paused)
 {
     if (!ctx) return fail(GF_EINVAL, "ctx is NULL");

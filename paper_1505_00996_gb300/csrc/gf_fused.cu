@@ -38,15 +38,15 @@ struct FusedParams {
     unsigned *clear_word;  // the call's fault word: zeroed by the first thread (this is the call's only kernel)
 };
 
+// The whole filter for output tile (bx, by) of plane bz = n C + c (one CTA; sm: the CTA's shared memory).
 template <typename TI, typename TQ, int MODE>
-__global__ void __launch_bounds__(FU_NT) k_fgf_fused(FusedParams P)
+__device__ __forceinline__ void fused_tile(const FusedParams &P, int bx, int by, int bz, float *sm)
 {
-    extern __shared__ float sm[];
     const int tid = threadIdx.x;
-    if (P.clear_word && (blockIdx.x | blockIdx.y | blockIdx.z | tid) == 0) *P.clear_word = 0u;
-    const int n = blockIdx.z / P.C, c = blockIdx.z - n * P.C;
-    const int X0 = blockIdx.x * P.TW, X1 = min(X0 + P.TW, P.W);  // columns [X0, X1)
-    const int Ya = max((int)blockIdx.y * P.TH, P.Yw0), Yb = min(min((int)blockIdx.y * P.TH + P.TH, P.H), P.Yw1);
+    if (P.clear_word && (bx | by | bz | tid) == 0) *P.clear_word = 0u;
+    const int n = bz / P.C, c = bz - n * P.C;
+    const int X0 = bx * P.TW, X1 = min(X0 + P.TW, P.W);  // columns [X0, X1)
+    const int Ya = max(by * P.TH, P.Yw0), Yb = min(min(by * P.TH + P.TH, P.H), P.Yw1);
     if (Ya >= Yb) return;
     const int h = P.h, w = P.w, r = P.r;
     // regions in low-res coordinates, inclusive bounds
@@ -187,6 +187,35 @@ __global__ void __launch_bounds__(FU_NT) k_fgf_fused(FusedParams P)
     }
 }
 
+template <typename TI, typename TQ, int MODE>
+__global__ void __launch_bounds__(FU_NT) k_fgf_fused(FusedParams P)
+{
+    extern __shared__ float sm[];
+    fused_tile<TI, TQ, MODE>(P, blockIdx.x, blockIdx.y, blockIdx.z, sm);
+}
+
+// The tile-queue form: one launch for the tiles of up to FUSED_QUEUE_MAX requests of the same storage types
+// and subsample mode, each with its own descriptor (sizes, strides, r', s, eps, pointers, tile shape).  CTA t
+// takes tile t - start[k] of request k, the k with start[k] <= t < start[k + 1]; each tile is computed exactly
+// as the request's own launch computes it, so a request's output does not depend on what it was batched with.
+struct FusedQueue {
+    int n;
+    int start[FUSED_QUEUE_MAX + 1];
+    int gx[FUSED_QUEUE_MAX], gy[FUSED_QUEUE_MAX];  // the request's tile columns and rows
+    FusedParams p[FUSED_QUEUE_MAX];
+};
+
+template <typename TI, typename TQ, int MODE>
+__global__ void __launch_bounds__(FU_NT) k_fgf_fused_queue(const __grid_constant__ FusedQueue Q)
+{
+    extern __shared__ float sm[];
+    const int t = blockIdx.x;
+    int k = 0;
+    while (k + 1 < Q.n && t >= Q.start[k + 1]) ++k;
+    const int local = t - Q.start[k], gx = Q.gx[k], gy = Q.gy[k];
+    fused_tile<TI, TQ, MODE>(Q.p[k], local % gx, (local / gx) % gy, local / (gx * gy), sm);
+}
+
 // Upper bounds of the region sizes for a TH x TW tile (low-res rows / columns), and the shared memory.
 struct FusedShape {
     int TH, TW;
@@ -227,10 +256,11 @@ bool fused_supported(const Resolved &R, bool intermediates)
     return !R.color && !R.int_stats && !intermediates && fused_shape(R.sn, R.sd, R.r_low, R.H, R.W, 1, S);
 }
 
-cudaError_t launch_fused(const FwdPlan &P, cudaStream_t st)
+namespace {
+
+// The kernel's descriptor of a plan, with the plan's tile shape.
+FusedParams fused_params(const FwdPlan &P, const FusedShape &S)
 {
-    FusedShape S;
-    if (!fused_shape(P.sn, P.sd, P.r_low, P.H, P.W, (long long)P.N * P.C, S)) return cudaErrorInvalidValue;
     FusedParams F;
     F.I = P.I; F.p = P.p; F.q = P.q;
     F.C = P.C; F.CI = P.CI; F.H = P.H; F.W = P.W; F.h = P.h; F.w = P.w;
@@ -240,6 +270,64 @@ cudaError_t launch_fused(const FwdPlan &P, cudaStream_t st)
     F.TH = S.TH; F.TW = S.TW;
     F.Yw0 = P.Yw0; F.Yw1 = P.Yw1;
     F.clear_word = P.clear_fault ? P.fault.call : nullptr;
+    return F;
+}
+
+}  // namespace
+
+cudaError_t launch_fused_queue(const FwdPlan *plans, int n, cudaStream_t st)
+{
+    if (n < 1 || n > FUSED_QUEUE_MAX) return cudaErrorInvalidValue;
+    FusedQueue Q{};
+    Q.n = n;
+    size_t smem = 0;
+    long long total = 0;
+    for (int k = 0; k < n; ++k) {
+        const FwdPlan &P = plans[k];
+        if (P.dt_in != plans[0].dt_in || P.dt_out != plans[0].dt_out || P.mode != plans[0].mode)
+            return cudaErrorInvalidValue;
+        FusedShape S;
+        if (!fused_shape(P.sn, P.sd, P.r_low, P.H, P.W, (long long)P.N * P.C, S)) return cudaErrorInvalidValue;
+        Q.p[k] = fused_params(P, S);
+        Q.gx[k] = (P.W + S.TW - 1) / S.TW;
+        Q.gy[k] = (P.H + S.TH - 1) / S.TH;
+        Q.start[k] = (int)total;
+        total += (long long)Q.gx[k] * Q.gy[k] * P.N * P.C;
+        smem = std::max(smem, S.smem);
+    }
+    if (total < 1 || total >= (1LL << 31)) return cudaErrorInvalidValue;
+    Q.start[n] = (int)total;
+    const FwdPlan &P0 = plans[0];
+    cudaError_t e;
+#define GF_FQ(TI, TQ, M)                                                                     \
+    do {                                                                                     \
+        if ((e = opt_in_smem(k_fgf_fused_queue<TI, TQ, M>, smem)) != cudaSuccess) return e;  \
+        k_fgf_fused_queue<TI, TQ, M><<<(unsigned)total, FU_NT, smem, st>>>(Q);               \
+    } while (0)
+#define GF_FQ_MODE(TI, TQ)                                                                   \
+    do {                                                                                     \
+        switch (P0.mode) {                                                                   \
+        case GF_SUB_NEAREST: GF_FQ(TI, TQ, GF_SUB_NEAREST); break;                           \
+        case GF_SUB_BILINEAR: GF_FQ(TI, TQ, GF_SUB_BILINEAR); break;                         \
+        case GF_SUB_BOX: GF_FQ(TI, TQ, GF_SUB_BOX); break;                                   \
+        default: GF_FQ(TI, TQ, GF_SUB_BILINEAR_AA); break;                                   \
+        }                                                                                    \
+    } while (0)
+    if (P0.dt_in == F32) {
+        if (P0.dt_out == F32) GF_FQ_MODE(float, float); else GF_FQ_MODE(float, __half);
+    } else {
+        if (P0.dt_out == F32) GF_FQ_MODE(__half, float); else GF_FQ_MODE(__half, __half);
+    }
+#undef GF_FQ_MODE
+#undef GF_FQ
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused(const FwdPlan &P, cudaStream_t st)
+{
+    FusedShape S;
+    if (!fused_shape(P.sn, P.sd, P.r_low, P.H, P.W, (long long)P.N * P.C, S)) return cudaErrorInvalidValue;
+    const FusedParams F = fused_params(P, S);
     dim3 grid((P.W + S.TW - 1) / S.TW, (P.H + S.TH - 1) / S.TH, P.N * P.C);
     cudaError_t e;
 #define GF_FU(TI, TQ, M)                                                                     \

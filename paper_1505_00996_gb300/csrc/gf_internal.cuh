@@ -133,6 +133,7 @@ gf_status server_cancel(Server *s, uint64_t ticket);
 gf_status server_stats(Server *s, gf_serve_stats *out);
 gf_status server_pause(Server *s, int paused);
 gf_status server_graphs(Server *s, int enable);
+gf_status server_queue(Server *s, int enable);
 
 // A forward call's arguments, checked and resolved on the host (gf_api.cu).
 struct Resolved {
@@ -229,6 +230,10 @@ cudaError_t launch_strip_box(const BoxTmaJob &J, cudaStream_t st);
 // The single-kernel form (gf_fused.cu): whether it can run these arguments, and its launch.
 bool fused_supported(const Resolved &R, bool intermediates);
 cudaError_t launch_fused(const FwdPlan &P, cudaStream_t st);
+// The tile-queue form of the single kernel: one launch for the tiles of n <= FUSED_QUEUE_MAX fused plans with
+// the same input and output storage types and subsample mode (each plan's output exactly its own launch's).
+constexpr int FUSED_QUEUE_MAX = 16;
+cudaError_t launch_fused_queue(const FwdPlan *plans, int n, cudaStream_t st);
 
 // Colour-guide stages (gf_color.cu).
 cudaError_t launch_color_products(const FwdPlan &P, cudaStream_t st);

@@ -18,6 +18,13 @@
 // A request's ready_event is waited for on the slot stream before its kernels, so inputs that another
 // stream is still writing are complete when they are read.
 //
+// Tile queue (on unless gf_serve_tile_queue turns it off): when every slot is taken, requests small enough for
+// the single-kernel form (gf_filter's fused path) that stand next to each other at the head of the queue and
+// share storage types and subsample mode are admitted together onto the last free slot, up to 16 at a time,
+// and run as ONE launch of the single kernel's tile-queue form: a grid over the (request, tile) items with per-request descriptors.  Each
+// keeps its own scratch, fault word and completion callback, and each tile is computed exactly as the
+// request's own launch computes it, so batching changes no result.
+//
 // Per-bucket CUDA graphs (off unless gf_serve_graphs turns them on): requests whose launch sequence has the
 // same kernels -- the same bucket: storage types, channels, ratio, subsample mode, r', the single-kernel or
 // chain form, the alignment classes that pick the vector and TMA kernels -- on the same slot share one
@@ -122,6 +129,7 @@ struct Request {
     std::atomic<int> finished{0};  // set by the stream callback
     struct Server *srv = nullptr;
     cudaEvent_t ready = nullptr;   // the caller's inputs are complete at this event (owned copy; may be NULL)
+    int bindex = 0;                // position in its slot's batch (its fault word's index)
 };
 
 }  // namespace
@@ -134,7 +142,8 @@ struct Server {
     void *arena = nullptr;
     ArenaAllocator alloc;
     std::vector<cudaStream_t> streams;
-    std::vector<uint64_t> slot_owner;  // ticket running on each slot, 0 = free
+    std::vector<uint64_t> slot_owner;  // first ticket running on each slot, 0 = free
+    std::vector<std::vector<uint64_t>> slot_batch;  // every ticket running on each slot (tile-queue batches)
     std::mutex mu;
     std::condition_variable cv_sched, cv_done;
     std::deque<uint64_t> queue;
@@ -144,13 +153,15 @@ struct Server {
     std::thread thread;
     long long launches = 0, fault_launch = -1;
     bool paused = false;  // admission held (requests stay queued)
-    unsigned *fault_host = nullptr;  // pinned, one word per slot: the fault word of the request on that slot
+    unsigned *fault_host = nullptr;  // pinned, FUSED_QUEUE_MAX words per slot: the fault words of its requests
     cudaStream_t ready_stream = nullptr;  // where a request's ready event is captured at submission
     bool use_graphs = false;
+    bool use_queue = true;           // tile-queue batches of single-kernel requests
     std::map<std::string, cudaGraphExec_t> graphs;  // bucket + slot -> executable graph
     std::map<std::string, int> seen;                // buckets launched once directly on a slot
     long long launched = 0;          // requests enqueued, how many through a graph, the host time spent
     long long graph_launched = 0;
+    long long queue_launches = 0, queue_requests = 0;  // tile-queue launches and the requests they carried
     double launch_seconds = 0.0;
 };
 
@@ -210,12 +221,13 @@ gf_status launch_request(Server *s, Request &r, bool *launched_some, bool *via_g
         return GF_ECUDA;
     }
     *launched_some = true;
-    s->fault_host[r.slot] = 0;
+    unsigned *fault_word = &s->fault_host[(size_t)r.slot * FUSED_QUEUE_MAX + r.bindex];
+    *fault_word = 0;
     // the request's work: its kernels, the copy of its fault word, the completion callback
     auto enqueue = [&]() {
         cudaError_t err = launch_forward(P, st);
         if (err == cudaSuccess && P.fault.call)
-            err = cudaMemcpyAsync(&s->fault_host[r.slot], P.fault.call, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+            err = cudaMemcpyAsync(fault_word, P.fault.call, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
         if (err == cudaSuccess) err = cudaLaunchHostFunc(st, on_done, &r);
         return err;
     };
@@ -261,26 +273,94 @@ gf_status launch_request(Server *s, Request &r, bool *launched_some, bool *via_g
     return GF_OK;
 }
 
+// Whether a request can join a tile-queue batch, and the key a batch's requests share (the kernel's template).
+bool queueable(const Server *s, const Request &r)
+{
+    return s->use_queue && r.R.fused && !r.R.color && r.req.opts.test_wait_fault == 0;
+}
+long long queue_key(const Request &r) { return (long long)r.R.dt_in * 10000 + r.R.dt_out * 100 + r.R.mode; }
+
+// Enqueue a tile-queue batch (requests of one slot, in admission order) as one launch.  Like launch_request:
+// called without the server lock, touching only the batch's requests and their slot's fault words.  An
+// injected failure (GF_FAULT) fails its own request, which then stays out of the launch.  Fills st[k] for each
+// request; *launched_some tells whether any work was enqueued.
+void launch_batch(Server *s, Request *const *b, int n, gf_status *st, bool *launched_some)
+{
+    NvtxRange range("gf_serve launch batch");
+    *launched_some = false;
+    const int slot = b[0]->slot;
+    cudaStream_t stream = s->streams[slot];
+    FwdPlan plans[FUSED_QUEUE_MAX];
+    Request *in[FUSED_QUEUE_MAX];
+    int m = 0;
+    for (int k = 0; k < n; ++k) {
+        Request &r = *b[k];
+        st[k] = GF_OK;
+        if (s->fault_launch >= 0 && s->launches++ == s->fault_launch) {  // injected: this request is left out
+            st[k] = GF_ECUDA;
+            continue;
+        }
+        if (r.ready) {
+            const cudaError_t e = cudaStreamWaitEvent(stream, r.ready, 0);
+            cudaEventDestroy(r.ready);
+            r.ready = nullptr;
+            if (e != cudaSuccess) {
+                st[k] = GF_ECUDA;
+                continue;
+            }
+            *launched_some = true;
+        }
+        s->fault_host[(size_t)slot * FUSED_QUEUE_MAX + r.bindex] = 0;
+        plans[m] = make_plan(r.R, r.L, r.req.I, r.req.p, r.req.q, (char *)s->arena + r.off, &r.req.opts);
+        in[m++] = &r;
+    }
+    if (m == 0) return;
+    cudaError_t e = launch_fused_queue(plans, m, stream);
+    if (e == cudaSuccess) *launched_some = true;
+    for (int k = 0; k < m && e == cudaSuccess; ++k) {
+        Request &r = *in[k];
+        if (plans[k].fault.call)
+            e = cudaMemcpyAsync(&s->fault_host[(size_t)slot * FUSED_QUEUE_MAX + r.bindex], plans[k].fault.call,
+                                sizeof(unsigned), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaLaunchHostFunc(stream, on_done, &r);
+    }
+    if (e != cudaSuccess) {
+        gf_set_error(std::string("serving launch (tile queue): ") + cudaGetErrorString(e));
+        for (int k = 0; k < n; ++k)
+            if (st[k] == GF_OK && !b[k]->finished.load()) st[k] = GF_ECUDA;
+    }
+}
+
 void scheduler(Server *s)
 {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lock(s->mu);
     std::vector<std::shared_ptr<Request>> admitted;
     while (true) {
-        // retire finished requests: free their slot and scratch
+        // retire finished requests (their scratch is freed); a slot is free once all of its batch is retired
         for (int k = 0; k < s->nslots; ++k) {
-            const uint64_t t = s->slot_owner[k];
-            if (!t) continue;
-            auto &r = *s->reqs[t];
-            if (r.finished.load(std::memory_order_acquire)) {
+            if (!s->slot_owner[k]) continue;
+            bool all = true;
+            for (const uint64_t t : s->slot_batch[k]) {
+                auto it = s->reqs.find(t);  // a retired request may have been polled and erased already
+                if (it == s->reqs.end()) continue;
+                auto &r = *it->second;
+                if (r.state != RUNNING) continue;  // retired already (or failed at launch)
+                if (!r.finished.load(std::memory_order_acquire)) {
+                    all = false;
+                    continue;
+                }
                 r.state = DONE;
-                if (s->fault_host[k] != 0) {  // a kernel of the request gave up a bounded wait: q is incomplete
+                if (s->fault_host[(size_t)k * FUSED_QUEUE_MAX + r.bindex] != 0) {  // a bounded wait gave up
                     r.state = FAILED;
                     r.status = GF_EWAIT;
                 }
                 s->alloc.release(r.off, r.L.total);
-                s->slot_owner[k] = 0;
                 s->cv_done.notify_all();
+            }
+            if (all) {
+                s->slot_owner[k] = 0;
+                s->slot_batch[k].clear();
             }
         }
         // admit from the head of the queue while a slot is free and the scratch fits
@@ -302,10 +382,38 @@ void scheduler(Server *s)
             s->queue.pop_front();
             r.off = off;
             r.slot = slot;
+            r.bindex = 0;
             r.t_admit = now_seconds();
             r.state = RUNNING;
             s->slot_owner[slot] = t;
+            s->slot_batch[slot].assign(1, t);
             admitted.push_back(it->second);
+            // the tile queue: the requests right behind it that take the same single-kernel launch join its slot,
+            // when no other slot is free for them (under light load every request keeps a slot of its own)
+            if (!queueable(s, r)) continue;
+            bool other_free = false;
+            for (int k = 0; k < s->nslots; ++k) other_free |= (!s->slot_owner[k]);
+            if (other_free) continue;
+            while ((int)s->slot_batch[slot].size() < FUSED_QUEUE_MAX && !s->queue.empty()) {
+                const uint64_t t2 = s->queue.front();
+                auto it2 = s->reqs.find(t2);
+                if (it2 == s->reqs.end() || it2->second->state != QUEUED) {
+                    s->queue.pop_front();
+                    continue;
+                }
+                Request &r2 = *it2->second;
+                if (!queueable(s, r2) || queue_key(r2) != queue_key(r)) break;
+                size_t off2;
+                if (!s->alloc.alloc(r2.L.total, &off2)) break;
+                s->queue.pop_front();
+                r2.off = off2;
+                r2.slot = slot;
+                r2.bindex = (int)s->slot_batch[slot].size();
+                r2.t_admit = now_seconds();
+                r2.state = RUNNING;
+                s->slot_batch[slot].push_back(t2);
+                admitted.push_back(it2->second);
+            }
         }
         // launch them with the lock released (their state is RUNNING: nothing else touches them meanwhile)
         if (!admitted.empty()) {
@@ -316,20 +424,38 @@ void scheduler(Server *s)
             std::vector<Outcome> outcome(admitted.size());
             lock.unlock();
             double launch_s = 0.0;
-            for (size_t k = 0; k < admitted.size(); ++k) {
+            long long qlaunches = 0, qrequests = 0;
+            for (size_t k = 0; k < admitted.size();) {
                 Request &r = *admitted[k];
+                size_t e = k + 1;  // the slot's batch: the admitted requests with the same slot, in order
+                while (e < admitted.size() && admitted[e]->slot == r.slot) ++e;
                 bool launched_some = false;
                 const double t0 = now_seconds();
-                outcome[k].st = launch_request(s, r, &launched_some, &outcome[k].via_graph);
+                if (e - k == 1) {
+                    outcome[k].st = launch_request(s, r, &launched_some, &outcome[k].via_graph);
+                } else {
+                    Request *b[FUSED_QUEUE_MAX];
+                    gf_status st[FUSED_QUEUE_MAX];
+                    for (size_t j = k; j < e; ++j) b[j - k] = admitted[j].get();
+                    launch_batch(s, b, (int)(e - k), st, &launched_some);
+                    for (size_t j = k; j < e; ++j) outcome[j] = {st[j - k], false};
+                    ++qlaunches;
+                    qrequests += (long long)(e - k);
+                }
                 launch_s += now_seconds() - t0;
-                if (outcome[k].st != GF_OK && launched_some) {
-                    // work of the request may still be running: wait for it before the scratch is reused
+                bool failed = false;
+                for (size_t j = k; j < e; ++j) failed |= (outcome[j].st != GF_OK);
+                if (failed && launched_some) {
+                    // work of the slot may still be running: wait for it before failed requests' scratch is reused
                     cudaStreamSynchronize(s->streams[r.slot]);
                     cudaGetLastError();
                 }
+                k = e;
             }
             lock.lock();
             s->launched += (long long)admitted.size();
+            s->queue_launches += qlaunches;
+            s->queue_requests += qrequests;
             s->launch_seconds += launch_s;
             for (size_t k = 0; k < admitted.size(); ++k) {
                 Request &r = *admitted[k];
@@ -339,8 +465,21 @@ void scheduler(Server *s)
                 r.status = outcome[k].st;
                 r.t_done.store(now_seconds());
                 s->alloc.release(r.off, r.L.total);
-                s->slot_owner[r.slot] = 0;
                 s->cv_done.notify_all();
+            }
+            // a slot none of whose requests is running any more is free (the retire pass covers the rest)
+            for (size_t k = 0; k < admitted.size(); ++k) {
+                const int slot = admitted[k]->slot;
+                if (!s->slot_owner[slot]) continue;
+                bool any = false;
+                for (const uint64_t t : s->slot_batch[slot]) {
+                    auto it = s->reqs.find(t);
+                    any |= (it != s->reqs.end() && it->second->state == RUNNING);
+                }
+                if (!any) {
+                    s->slot_owner[slot] = 0;
+                    s->slot_batch[slot].clear();
+                }
             }
             continue;  // requests may have finished meanwhile: retire and admit again before waiting
         }
@@ -365,7 +504,7 @@ gf_status server_start(Server *s)
         gf_set_error(std::string("serving arena of ") + std::to_string(s->budget) + " bytes: " + cudaGetErrorString(e));
         return GF_ENOMEM;
     }
-    e = cudaHostAlloc((void **)&s->fault_host, sizeof(unsigned) * s->nslots, cudaHostAllocPortable);
+    e = cudaHostAlloc((void **)&s->fault_host, sizeof(unsigned) * s->nslots * FUSED_QUEUE_MAX, cudaHostAllocPortable);
     if (e != cudaSuccess) {
         cudaGetLastError();
         cudaFree(s->arena);
@@ -375,10 +514,11 @@ gf_status server_start(Server *s)
         gf_set_error(std::string("serving fault words (pinned host memory): ") + cudaGetErrorString(e));
         return GF_ENOMEM;
     }
-    for (int k = 0; k < s->nslots; ++k) s->fault_host[k] = 0;
+    for (int k = 0; k < s->nslots * FUSED_QUEUE_MAX; ++k) s->fault_host[k] = 0;
     s->alloc.reset(s->budget);
     s->streams.resize(s->nslots);
     s->slot_owner.assign(s->nslots, 0);
+    s->slot_batch.assign(s->nslots, {});
     for (int k = 0; k < s->nslots; ++k) cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking);
     cudaStreamCreateWithFlags(&s->ready_stream, cudaStreamNonBlocking);
     cudaSetDevice(prev);
@@ -468,17 +608,17 @@ gf_status server_submit(Server *s, const gf_request *req, uint64_t *ticket)
     if (st != GF_OK) return st;
     r->L = layout_of(r->R, &r->req.opts);
     r->srv = s;
-    std::lock_guard<std::mutex> lock(s->mu);
-    if (r->L.total > s->budget) {
-        gf_set_error("request scratch of " + std::to_string(r->L.total) + " bytes can never fit the serving budget of " +
-                     std::to_string(s->budget) + " bytes");
-        return GF_ENOMEM;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (r->L.total > s->budget) {
+            gf_set_error("request scratch of " + std::to_string(r->L.total) +
+                         " bytes can never fit the serving budget of " + std::to_string(s->budget) + " bytes");
+            return GF_ENOMEM;
+        }
+        if ((st = server_start(s)) != GF_OK) return st;  // the first request: nothing is running yet
     }
-    if (s->queue.size() >= s->queue_limit) {
-        gf_set_error("serving queue is full");
-        return GF_EBUSY;
-    }
-    if ((st = server_start(s)) != GF_OK) return st;
+    // The ready event is captured with the lock released: completion callbacks take the lock, and no CUDA
+    // call is made while holding what a callback may be waiting for.
     if (req->ready_event) {
         // capture the caller's event as it stands now: an event of our own completes with it
         cudaError_t e = cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming);
@@ -487,9 +627,18 @@ gf_status server_submit(Server *s, const gf_request *req, uint64_t *ticket)
         if (e != cudaSuccess) {
             cudaGetLastError();
             if (r->ready) cudaEventDestroy(r->ready);
+            r->ready = nullptr;
             gf_set_error(std::string("request ready_event: ") + cudaGetErrorString(e));
             return GF_ECUDA;
         }
+    }
+    std::unique_lock<std::mutex> lock(s->mu);
+    if (s->queue.size() >= s->queue_limit) {
+        lock.unlock();
+        if (r->ready) cudaEventDestroy(r->ready);
+        r->ready = nullptr;
+        gf_set_error("serving queue is full");
+        return GF_EBUSY;
     }
     r->ticket = s->next_ticket++;
     r->t_submit = now_seconds();
@@ -527,11 +676,11 @@ gf_status server_poll(Server *s, uint64_t ticket, int64_t timeout_us, gf_result 
         out->scratch_bytes = r->L.total;
     }
     const gf_status st = r->state == CANCELED ? GF_ECANCELED : r->status;
-    if (r->ready) {  // never launched (cancelled)
-        cudaEventDestroy(r->ready);
-        r->ready = nullptr;
-    }
+    cudaEvent_t unused_ready = r->ready;  // never launched (cancelled): destroyed below, outside the lock
+    r->ready = nullptr;
     s->reqs.erase(it);  // a terminal result is delivered once
+    lock.unlock();
+    if (unused_ready) cudaEventDestroy(unused_ready);
     if (st != GF_OK)
         gf_set_error(st == GF_ECANCELED ? "request was cancelled"
                      : st == GF_EWAIT   ? "request failed: a kernel gave up a bounded wait (q is incomplete)"
@@ -567,6 +716,17 @@ gf_status server_graphs(Server *s, int enable)
     return GF_OK;
 }
 
+gf_status server_queue(Server *s, int enable)
+{
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->started) {
+        gf_set_error("gf_serve_tile_queue must be called before the first gf_submit");
+        return GF_EBUSY;
+    }
+    s->use_queue = enable != 0;
+    return GF_OK;
+}
+
 gf_status server_pause(Server *s, int paused)
 {
     std::lock_guard<std::mutex> lock(s->mu);
@@ -589,6 +749,8 @@ gf_status server_stats(Server *s, gf_serve_stats *out)
     out->slots = s->nslots;
     out->launches = s->launched;
     out->graph_launches = s->graph_launched;
+    out->queue_launches = s->queue_launches;
+    out->queue_requests = s->queue_requests;
     out->launch_seconds = s->launch_seconds;
     return GF_OK;
 }

@@ -16,12 +16,14 @@ _DTYPES = {torch.float32: binding.GF_F32, torch.float16: binding.GF_F16, torch.u
 
 
 class Server:
-    def __init__(self, device=None, hbm_budget_bytes=0, slots=4, queue_limit=0, graphs=False):
-        """``graphs``: replay each request's launches through its bucket's CUDA graph (gf_serve_graphs)."""
+    def __init__(self, device=None, hbm_budget_bytes=0, slots=4, queue_limit=0, graphs=False, tile_queue=True):
+        """``graphs``: replay each request's launches through its bucket's CUDA graph (gf_serve_graphs).
+        ``tile_queue``: run neighbouring single-kernel requests as one tile-queue launch (gf_serve_tile_queue)."""
         self.ctx = binding.Context(device, hbm_budget_bytes)
         self.lib = binding.load_library()
         binding.check(self.lib.gf_serve_config(self.ctx.handle, int(slots), int(queue_limit)))
         binding.check(self.lib.gf_serve_graphs(self.ctx.handle, int(bool(graphs))))
+        binding.check(self.lib.gf_serve_tile_queue(self.ctx.handle, int(bool(tile_queue))))
         self._alive = {}
 
     def clock(self):
@@ -94,6 +96,7 @@ class Server:
         binding.check(self.lib.gf_serve_stats_get(self.ctx.handle, ctypes.byref(st)))
         return {"queued": st.queued, "running": st.running, "slots": st.slots, "budget_bytes": st.budget_bytes,
                 "scratch_in_use": st.scratch_in_use, "launches": st.launches, "graph_launches": st.graph_launches,
+                "queue_launches": st.queue_launches, "queue_requests": st.queue_requests,
                 "launch_seconds": st.launch_seconds}
 
     def close(self):

@@ -47,7 +47,7 @@ def test_opts_defaults(lib):
     o = binding.opts_init()
     assert (o.batch, o.guide_channels, o.r_low, o.p_lowres, o.dtype_in, o.dtype_out) == (1, 1, -1, 0, 0, 0)
     assert not o.workspace and not o.kernel_events
-    assert lib.gf_abi_version() == 4
+    assert lib.gf_abi_version() == 5
     assert o.saved_forward == 0 and o.test_wait_fault == 0
 
 

@@ -2,7 +2,7 @@
 
 Checks: a mixed batch of requests (sizes, radii, ratios, channel counts, FP16 and FP32 storage) gives, for
 every request, exactly the result of running it alone through gf_filter, while requests overlap on the
-device; admission never exceeds the HBM budget or the slot count; a request that can never fit is
+device, with direct launches, per-bucket graphs and tile-queue launches of several small requests; admission never exceeds the HBM budget or the slot count; a request that can never fit is
 refused; held requests report pending / time out and can be cancelled; an injected launch failure fails
 only its own request; and a context with queued work shuts down cleanly.
 """
@@ -51,16 +51,18 @@ MIX = [  # (H, W, C, r, eps, s, mode, dtype)
 ]
 
 
-@pytest.mark.parametrize("graphs", [True, False], ids=["graphs", "direct"])
-def test_mixed_requests_equal_their_solo_results(gf, graphs):
+@pytest.mark.parametrize("graphs,tile_queue", [(True, False), (False, False), (False, True)],
+                         ids=["graphs", "direct", "tile_queue"])
+def test_mixed_requests_equal_their_solo_results(gf, graphs, tile_queue):
     """Every request of the mix equals its solo gf_filter result bit for bit, with the per-bucket graphs (the
-    mix runs twice, so the second pass replays updated graphs) and with direct launches."""
+    mix runs twice, so the second pass replays updated graphs), with direct launches, and with the tile queue
+    (neighbouring single-kernel requests in one launch)."""
     inputs = [_make(H, W, C, dt, 100 + k) for k, (H, W, C, r, e, s, m, dt) in enumerate(MIX)]
     refs = []
     for (I, p), (H, W, C, r, e, s, m, dt) in zip(inputs, MIX):
         refs.append(gf.fast_guided_filter(I, p, r, e, s, m))
     torch.cuda.synchronize()
-    srv = gf.Server(slots=4, graphs=graphs)
+    srv = gf.Server(slots=4, graphs=graphs, tile_queue=tile_queue)
     outs, tickets = [], []
     for rep in range(2):
         for (I, p), (H, W, C, r, e, s, m, dt), ref in zip(inputs, MIX, refs):
@@ -72,6 +74,7 @@ def test_mixed_requests_equal_their_solo_results(gf, graphs):
     stats = srv.stats()
     srv.close()
     assert (stats["graph_launches"] > 0) == graphs and stats["launches"] == len(tickets)
+    assert tile_queue or stats["queue_launches"] == 0
     assert all(res["status"] == gf.GF_OK for res in results)
     for q, ref in zip(outs, refs):
         assert torch.equal(q, ref)
@@ -83,6 +86,43 @@ def test_mixed_requests_equal_their_solo_results(gf, graphs):
     ref64 = oracle.fast_guided_filter(I.float().cpu().numpy().astype(np.float64),
                                       p.float().cpu().numpy().astype(np.float64), r, e, s, oracle.SUB_BILINEAR)
     assert max_abs(outs[0].float().cpu(), ref64) <= TOL_F16
+
+
+SMALL = [  # single-kernel requests (s > 1, at most 2^20 pixel-channels): (H, W, C, r, eps, s, mode)
+    (480, 640, 3, 3, 1e-4, 4, "bilinear"),
+    (333, 517, 1, 2, 1e-2, 4, "bilinear"),
+    (611, 409, 3, 5, 1e-2, 8, "bilinear"),
+    (100, 3000, 1, 12, 1e-4, 8, "bilinear"),
+    (256, 256, 3, 4, 1e-3, 2, "bilinear"),
+    (97, 131, 1, 1, 1e-2, 4, "bilinear"),
+    (512, 512, 3, 8, 1e-2, 4, "bilinear"),
+    (300, 700, 2, 6, 1e-4, 4, "bilinear"),
+]
+
+
+@pytest.mark.parametrize("slots", [1, 3])
+def test_tile_queue_batches_equal_their_solo_results(gf, slots):
+    """Small FP16 requests of mixed sizes, radii, ratios and channel counts queued while admission is held,
+    then released: they run in tile-queue launches of several requests each, and every result equals its solo
+    gf_filter result bit for bit.  A FP32 request in the middle of the stream starts a batch of its own."""
+    reqs = SMALL * 3
+    inputs = [_make(H, W, C, torch.float32 if k == 9 else torch.float16, 300 + k)
+              for k, (H, W, C, r, e, s, m) in enumerate(reqs)]
+    refs = [gf.fast_guided_filter(I, p, r, e, s, m) for (I, p), (H, W, C, r, e, s, m) in zip(inputs, reqs)]
+    torch.cuda.synchronize()
+    srv = gf.Server(slots=slots)
+    srv.pause(True)
+    outs = [torch.full_like(ref, float("nan")) for ref in refs]
+    tickets = [srv.submit(I, p, q, r, e, s, m) for (I, p), q, (H, W, C, r, e, s, m) in zip(inputs, outs, reqs)]
+    srv.pause(False)
+    results = [srv.poll(t) for t in tickets]
+    stats = srv.stats()
+    srv.close()
+    assert all(res["status"] == gf.GF_OK for res in results)
+    assert stats["queue_launches"] >= 2 and stats["queue_requests"] >= len(reqs) - 3
+    assert stats["launches"] == len(reqs)
+    for q, ref in zip(outs, refs):
+        assert torch.equal(q, ref)
 
 
 def test_admission_respects_budget_and_slots(gf):
