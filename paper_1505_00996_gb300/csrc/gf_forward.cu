@@ -1329,15 +1329,18 @@ bool aligned_vec_subsample(const FwdPlan &P)
 // 177 k MP/s); the feathering figure's r' = 15 at s = 4 38 against 47 us.
 static bool box_tma_pays(int, int) { return true; }
 // The column-strip kernels (gf_strip.cu) take the box steps at large radii, where the tiles' 2r halo rows and
-// columns cost more than their outputs, and on large planes, whose long segments amortise the window opening.
-// Measured on the 12 MP scene (3 channels, gray guide): s = 1 calls at r = 4 / 8 / 12 take 246 / 287 / 305 us
-// with strips against 291 / 335 / 482 us with tiles; s = 4 calls (0.75 MP low-res planes) at r' = 6, 8 take
-// 88.2 / 87.4 us against 83.5 / 84.5 us.  GF_STRIP_MIN_R (read per call) replaces the rule by r >= its value,
-// so that tests and measurements can send any radius through either form.
-static bool strip_pays(int r, int h, int w)
+// columns cost more than their outputs; on large planes, whose long segments amortise the window opening; and
+// for three channels of one gray guide at r' = 4 (a compile-time radius of the strip kernels), where one strip
+// CTA forms the guide's sums once for the three.  Measured on the 12 MP scene: s = 1 calls at r = 4 / 8 / 12
+// take 246 / 287 / 305 us with strips against 291 / 335 / 482 us with tiles; at s = 4 (r' = 4, gray guide, 3
+// channels) two images in flight take 64.4-64.6 against 67.1 us per image; at s = 8 (r' = 2) 251 k against
+// 261 k MP/s, with a depthwise guide or r' = 1 the strips lost 1-4 %, and at the run-time radii r' = 5, 6 (s =
+// 10/3, 5/2, one image at a time) 1.5-3 %, so the tiles keep those.  GF_STRIP_MIN_R (read per call) replaces
+// the rule by r >= its value, so that tests and measurements can send any radius through either form.
+static bool strip_pays(int r, int h, int w, bool gray3)
 {
-    const char *e = getenv("GF_STRIP_MIN_R");
-    return r >= (e ? atoi(e) : 9) || (!e && (long long)h * w >= (2LL << 20));
+    if (const char *e = getenv("GF_STRIP_MIN_R")) return r >= atoi(e);
+    return r >= 9 || (long long)h * w >= (2LL << 20) || (gray3 && r == 4);
 }
 
 bool s1_means_output_form(const Resolved &R)
@@ -1374,7 +1377,7 @@ cudaError_t launch_color_chain(const FwdPlan &P0, float *pl, StageTimer &tm, cud
         J.h = P.h; J.w = P.w; J.r = P.r_low;
         J.out0 = oX; J.out1 = oY;
         J.fault = P.fault;
-        if (strip_pays(P.r_low, P.h, P.w) && strip_box_supported(J)) return launch_strip_box(J, st);
+        if (strip_pays(P.r_low, P.h, P.w, P.CI == 1 && P.C % 3 == 0) && strip_box_supported(J)) return launch_strip_box(J, st);
         if (box_tma_pays(P.s, P.r_low) && box_tma_supported(J)) return launch_box_tma(J, st);
         BoxParams bp{};
         bp.X = X; bp.Y = Y;
@@ -1510,7 +1513,7 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         J.stats = P.int_stats ? nullptr : (float *)P.stats;
         J.fault = P.fault;
         const bool fp32 = !P.int_stats && src_dt == F32;
-        const bool strip = fp32 && strip_pays(P.r_low, P.h, P.w) && strip_box_supported(J);
+        const bool strip = fp32 && strip_pays(P.r_low, P.h, P.w, P.CI == 1 && P.C % 3 == 0) && strip_box_supported(J);
         const bool tma = !strip && fp32 && box_tma_pays(P.s, P.r_low) && box_tma_supported(J);
         tm.before();
         if (strip) {
@@ -1540,7 +1543,7 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         J.I = (const float *)P.I; J.q = P.q; J.fps = P.fps; J.CI = P.CI;
         J.Yw0 = P.Yw0; J.Yw1 = P.Yw1; J.dt_out = P.dt_out; J.detail = P.detail;
         J.fault = P.fault;
-        const bool strip = strip_pays(P.r_low, P.h, P.w) && strip_box_supported(J);
+        const bool strip = strip_pays(P.r_low, P.h, P.w, P.CI == 1 && P.C % 3 == 0) && strip_box_supported(J);
         if (strip || box_tma_supported(J)) {
             tm.before();
             err = strip ? launch_strip_box(J, st) : launch_box_tma(J, st);
@@ -1560,7 +1563,7 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
         J.out0 = P.ma; J.out1 = P.mb;
         J.fault = P.fault;
         tm.before();
-        if (strip_pays(P.r_low, P.h, P.w) && strip_box_supported(J)) {
+        if (strip_pays(P.r_low, P.h, P.w, P.CI == 1 && P.C % 3 == 0) && strip_box_supported(J)) {
             err = launch_strip_box(J, st);
         } else if (box_tma_pays(P.s, P.r_low) && box_tma_supported(J)) {
             err = launch_box_tma(J, st);
