@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(nt_of(TH), TH == 16 ? 6 : 3) k_box_tma(const _
     const int x0 = tx * BX_TW, y0 = blockIdx.y * TH;
     const int plane = n * P.C + c, xplane = n * P.CX + (P.CX == 1 ? 0 : c);
     const int h = P.h, w = P.w;
+    pdl_wait();  // launched with programmatic serialization: the previous kernel's planes are complete here
 
     // ---- phase 0: the tile and its halo, X and Y, by TMA (zeros outside the image)
     if (tid == 0) {
@@ -329,6 +330,7 @@ __global__ void __launch_bounds__(nt_of(TH), TH == 16 ? 6 : 3) k_box_tma(const _
         }
         if (b + 1 < nblocks) __syncthreads();  // the column sums are rewritten by the next block
     }
+    pdl_trigger();  // this CTA's outputs are written: the next kernel may be scheduled
 }
 
 }  // namespace
@@ -351,7 +353,8 @@ cudaError_t launch_one(const CUtensorMap &mx, const CUtensorMap &my, const BoxTm
     if (e != cudaSuccess) return e;
     // the channel is the fastest block index: the channel CTAs of a tile share its guide tile through L2
     const dim3 grid(P.C * ((P.w + BX_TW - 1) / BX_TW), (P.h + TH - 1) / TH, P.N);
-    k_box_tma<KIND, RC, CB, TH, TQ><<<grid, nt_of(TH), smem, st>>>(mx, my, P);
+    if ((e = launch_pdl(k_box_tma<KIND, RC, CB, TH, TQ>, grid, dim3(nt_of(TH)), smem, st, mx, my, P)) != cudaSuccess)
+        return e;
     return cudaGetLastError();
 }
 

@@ -65,6 +65,14 @@ __device__ __forceinline__ void report_fault(const FaultSink &f, unsigned bit)
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+// Programmatic dependent launch.  A kernel launched with the programmatic stream serialization attribute
+// (launch_pdl) may be scheduled while the kernel before it in the stream is still finishing; pdl_wait returns
+// once that kernel has completed and its memory operations are visible, so such a kernel calls it before it
+// touches global memory (without the attribute it returns at once).  pdl_trigger lets the next kernel be
+// scheduled once every CTA of this one has called it or exited.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 __device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");

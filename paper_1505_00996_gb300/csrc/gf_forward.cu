@@ -288,6 +288,7 @@ __device__ __forceinline__ float2 ld_block_pair(const T *rp)
 template <typename T, int MODE, int S>
 __global__ void __launch_bounds__(SUB_NT_VEC) k_subsample_vec(SubParams P)
 {
+    pdl_wait();  // launched with programmatic serialization: the previous call's kernels are complete here
     clear_call_fault(P.clear_word);
     constexpr int JB = (S == 8) ? 1 : 2;  // low-res rows per thread: short threads, many of them (measured best)
     const int i = blockIdx.x * SUB_NT_VEC + threadIdx.x;
@@ -321,6 +322,7 @@ __global__ void __launch_bounds__(SUB_NT_VEC) k_subsample_vec(SubParams P)
             v = top[u].x;
         dst[(size_t)(j0 + u) * P.w] = v * P.scale;
     }
+    pdl_trigger();  // the next kernel may be scheduled once every CTA is here
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -1455,9 +1457,9 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
             dim3 grid((P.w + SUB_NT_VEC - 1) / SUB_NT_VEC, (P.h + jb - 1) / jb, nz);
 #define GF_SV(m, ss)                                                                       \
     do {                                                                                   \
-        if (P.dt_in == F32) k_subsample_vec<float, m, ss><<<grid, SUB_NT_VEC, 0, st>>>(sp);    \
-        else if (P.dt_in == F16) k_subsample_vec<__half, m, ss><<<grid, SUB_NT_VEC, 0, st>>>(sp); \
-        else k_subsample_vec<uint8_t, m, ss><<<grid, SUB_NT_VEC, 0, st>>>(sp);                \
+        if (P.dt_in == F32) launch_pdl(k_subsample_vec<float, m, ss>, grid, dim3(SUB_NT_VEC), 0, st, sp);    \
+        else if (P.dt_in == F16) launch_pdl(k_subsample_vec<__half, m, ss>, grid, dim3(SUB_NT_VEC), 0, st, sp); \
+        else launch_pdl(k_subsample_vec<uint8_t, m, ss>, grid, dim3(SUB_NT_VEC), 0, st, sp);                \
     } while (0)
             if (P.mode == GF_SUB_BILINEAR) {
                 if (P.s == 2) GF_SV(GF_SUB_BILINEAR, 2); else if (P.s == 4) GF_SV(GF_SUB_BILINEAR, 4); else GF_SV(GF_SUB_BILINEAR, 8);

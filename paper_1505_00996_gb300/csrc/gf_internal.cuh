@@ -2,6 +2,7 @@
 // Nothing here is part of the public ABI (include/gf.h is).
 #pragma once
 
+#include <utility>
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -171,6 +172,23 @@ FwdPlan make_plan(const Resolved &R, const Layout &L, const void *I, const void 
 // Opt kernel `func` in to `smem` bytes of dynamic shared memory on the current device when that is above the
 // 48 KB default.  Thread-safe; the attribute is set once per kernel, device and larger size.
 cudaError_t opt_in_smem(const void *func, size_t smem);
+// Launch with the programmatic stream serialization attribute: the kernel (which calls pdl_wait before any
+// global memory access) may be scheduled while the previous kernel in the stream finishes.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 template <typename F>
 cudaError_t opt_in_smem(F *func, size_t smem) { return opt_in_smem(reinterpret_cast<const void *>(func), smem); }
 

@@ -399,6 +399,7 @@ __global__ void __launch_bounds__(SP_NT, minb_of(KIND, nq_of(KIND, NY))) k_box_s
     const int x0 = sx * SP_TW;
     const int y0 = P.ylo + blockIdx.y * P.seg, yend = min(y0 + P.seg, P.yhi);
     extern __shared__ __align__(16) unsigned char sm[];
+    pdl_wait();  // launched with programmatic serialization: the previous kernel's planes are complete here
 
     // ---- this CTA's planes; for the statistics, the shift: every plane's value at the first output pixel
     const float *base[NS];
@@ -585,6 +586,7 @@ __global__ void __launch_bounds__(SP_NT, minb_of(KIND, nq_of(KIND, NY))) k_box_s
         }
         if (NBUF == 1 && b + 1 < nblocks) __syncthreads();  // the column sums are rewritten by the next block
     }
+    pdl_trigger();  // this CTA's outputs are written: the next kernel may be scheduled
 }
 
 // SMs of the current device (cached per device ordinal).
@@ -639,7 +641,7 @@ cudaError_t launch_strip(StripParams P, int N, cudaStream_t st)
     const long long tasks = (long long)strips * P.groups * N;
     P.seg = segment_rows(P.yhi - P.ylo, P.r, tasks, (long long)per_sm * sm_count());
     const dim3 grid((unsigned)(strips * P.groups), (unsigned)((P.yhi - P.ylo + P.seg - 1) / P.seg), (unsigned)N);
-    kern<<<grid, SP_NT, smem, st>>>(P);
+    if ((e = launch_pdl(kern, grid, dim3(SP_NT), smem, st, P)) != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

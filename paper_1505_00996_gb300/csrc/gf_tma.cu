@@ -50,6 +50,7 @@ template <typename TI, typename TQ, int S>
 __global__ void __launch_bounds__(TO_NT, 4) k_output_tma(const __grid_constant__ CUtensorMap tmI, TmaOutParams P)
 {
     extern __shared__ __align__(128) unsigned char sm[];
+    pdl_wait();  // launched with programmatic serialization: mean_a, mean_b are complete here
     constexpr int ES = (int)sizeof(TI);
     constexpr int BOX_BYTES = TO_BOX_X * 4 * ES;  // one 256 x 4 box
     constexpr int STAGE = 2 * BOX_BYTES;          // 512 columns x 4 rows
@@ -295,7 +296,8 @@ cudaError_t launch_output_tma(const void *I, const float *ma, const float *mb, v
 #define GF_TO(TI, TQ, SS)                                                                  \
     do {                                                                                   \
         if ((e = opt_in_smem(k_output_tma<TI, TQ, SS>, smem)) != cudaSuccess) return e;    \
-        k_output_tma<TI, TQ, SS><<<grid, TO_NT, smem, st>>>(map, P);                       \
+        if ((e = launch_pdl(k_output_tma<TI, TQ, SS>, grid, dim3(TO_NT), smem, st, map, P)) != cudaSuccess) \
+            return e;                                                                      \
     } while (0)
 #define GF_TO_S(TI, TQ) do { if (s == 4) GF_TO(TI, TQ, 4); else GF_TO(TI, TQ, 8); } while (0)
     if (dt_in == F32) {
