@@ -61,6 +61,7 @@ __device__ __forceinline__ float up_weight(int X, int i, int s, int n)
 
 __global__ void __launch_bounds__(UT_NT) k_bwd_upsample_T(UpTParams P)
 {
+    pdl_wait();  // launched with programmatic serialization: earlier kernels are complete here
     extern __shared__ float sm[];
     const int s = P.s, TJ = P.TJ;
     const int i0 = blockIdx.x * UT_TI, j0 = blockIdx.y * TJ;
@@ -126,6 +127,7 @@ __global__ void __launch_bounds__(UT_NT) k_bwd_upsample_T(UpTParams P)
         P.dma[o] = sa;
         P.dmb[o] = sb;
     }
+    pdl_trigger();
 }
 
 // Interior weights of the bilinear upsample for an even integer s: pixel t of block i lies between low-res
@@ -177,6 +179,7 @@ constexpr int UW_TI = 30;     // low-res columns per warp (lanes 1 .. 30)
 template <int S>
 __global__ void __launch_bounds__(32 * UW_WARPS) k_bwd_upsample_T_w(UpTParams P)
 {
+    pdl_wait();  // launched with programmatic serialization: earlier kernels are complete here
     static_assert(S % 4 == 0, "whole float4 pieces per block");
     constexpr int HS = S / 2;
     constexpr unsigned FULL = 0xffffffffu;
@@ -247,6 +250,7 @@ __global__ void __launch_bounds__(32 * UW_WARPS) k_bwd_upsample_T_w(UpTParams P)
         pa = ca; pg = cg;
         ca = na; cg = ng;
     }
+    pdl_trigger();
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -281,6 +285,7 @@ __device__ __forceinline__ int win_count(int k, int r, int n) { return min(n - 1
 template <int NIN, int EPI, bool COMP, int RC = 0>
 __global__ void __launch_bounds__(BB_NT) k_bwd_box_T(BoxTParams P)
 {
+    pdl_wait();  // launched with programmatic serialization: earlier kernels are complete here
     static_assert(RC == 0 || !COMP, "a compile-time radius is for the small, uncompensated windows");
     constexpr int NOUT = (EPI == EPI_CHAIN) ? 4 : 2;
     extern __shared__ float smf[];
@@ -473,6 +478,7 @@ __global__ void __launch_bounds__(BB_NT) k_bwd_box_T(BoxTParams P)
             P.eps_partial[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = tt;
         }
     }
+    pdl_trigger();
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -516,6 +522,7 @@ __device__ __forceinline__ void sub_adjoint(int Y, int s, int H, int h, int mode
 
 __global__ void __launch_bounds__(BF_NT) k_bwd_full(FullParams P)
 {
+    pdl_wait();  // launched with programmatic serialization: earlier kernels are complete here
     const int X = blockIdx.x * BF_NT + threadIdx.x, Y = blockIdx.y, n = blockIdx.z;
     if (X >= P.W) return;
     const size_t HW = (size_t)P.H * P.W, pix = (size_t)Y * P.W + X;
@@ -554,6 +561,7 @@ __global__ void __launch_bounds__(BF_NT) k_bwd_full(FullParams P)
         if (P.dp) P.dp[(size_t)(n * P.C + c) * HW + pix] = tp;        // D^T(dp')
     }
     if (P.CI == 1) P.dI[(size_t)n * HW + pix] = dI_shared;
+    pdl_trigger();
 }
 
 // Vector form of k_bwd_full for s = 4, 8 with H and W multiples of s and 16-byte aligned planes.  Then every
@@ -564,6 +572,7 @@ __global__ void __launch_bounds__(BF_NT) k_bwd_full(FullParams P)
 template <int S, int MODE>
 __global__ void __launch_bounds__(BF_NT) k_bwd_full_v(FullParams P)
 {
+    pdl_wait();  // launched with programmatic serialization: earlier kernels are complete here
     static_assert(S % 4 == 0, "4 adjacent pixels in one block");
     const int X0 = 4 * (blockIdx.x * BF_NT + threadIdx.x), Y = blockIdx.y, n = blockIdx.z;
     if (X0 >= P.W) return;
@@ -624,6 +633,7 @@ __global__ void __launch_bounds__(BF_NT) k_bwd_full_v(FullParams P)
         }
     }
     if (P.CI == 1) *reinterpret_cast<float4 *>(P.dI + (size_t)n * HW + pix) = shared;
+    pdl_trigger();
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -631,6 +641,7 @@ __global__ void __launch_bounds__(BF_NT) k_bwd_full_v(FullParams P)
 // ------------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_reduce_eps(const float *partial, int n, float *out)
 {
+    pdl_wait();  // launched with programmatic serialization: earlier kernels are complete here
     __shared__ double red[256];
     double t = 0.0;
     for (int k = threadIdx.x; k < n; k += 256) t += (double)partial[k];
@@ -641,6 +652,7 @@ __global__ void __launch_bounds__(256) k_reduce_eps(const float *partial, int n,
         __syncthreads();
     }
     if (threadIdx.x == 0) *out = (float)red[0];
+    pdl_trigger();
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -659,7 +671,7 @@ cudaError_t launch_box_T(const BoxTParams &bp, int planes, cudaStream_t st)
 #define GF_BT(RR)                                                                             \
     do {                                                                                      \
         if ((e = opt_in_smem(k_bwd_box_T<NIN, EPI, false, RR>, smem)) != cudaSuccess) return e; \
-        k_bwd_box_T<NIN, EPI, false, RR><<<grid, BB_NT, smem, st>>>(bp);                        \
+        launch_pdl(k_bwd_box_T<NIN, EPI, false, RR>, grid, dim3(BB_NT), smem, st, bp);                        \
     } while (0)
         switch (bp.r) {
         case 1: GF_BT(1); break;
@@ -673,11 +685,11 @@ cudaError_t launch_box_T(const BoxTParams &bp, int planes, cudaStream_t st)
     if (bp.r > 16) {
         cudaError_t e = opt_in_smem(k_bwd_box_T<NIN, EPI, true>, smem);
         if (e != cudaSuccess) return e;
-        k_bwd_box_T<NIN, EPI, true><<<grid, BB_NT, smem, st>>>(bp);
+        launch_pdl(k_bwd_box_T<NIN, EPI, true>, grid, dim3(BB_NT), smem, st, bp);
     } else {
         cudaError_t e = opt_in_smem(k_bwd_box_T<NIN, EPI, false>, smem);
         if (e != cudaSuccess) return e;
-        k_bwd_box_T<NIN, EPI, false><<<grid, BB_NT, smem, st>>>(bp);
+        launch_pdl(k_bwd_box_T<NIN, EPI, false>, grid, dim3(BB_NT), smem, st, bp);
     }
     return cudaGetLastError();
 }
@@ -709,9 +721,9 @@ cudaError_t launch_backward(const BwdPlan &B, cudaStream_t st)
         const int rows_per_cta = UW_WARPS * up.TJ;
         dim3 grid((F.w + UW_TI - 1) / UW_TI, (F.h + rows_per_cta - 1) / rows_per_cta, planes);
         if (F.s == 4)
-            k_bwd_upsample_T_w<4><<<grid, 32 * UW_WARPS, 0, st>>>(up);
+            launch_pdl(k_bwd_upsample_T_w<4>, grid, dim3(32 * UW_WARPS), 0, st, up);
         else
-            k_bwd_upsample_T_w<8><<<grid, 32 * UW_WARPS, 0, st>>>(up);
+            launch_pdl(k_bwd_upsample_T_w<8>, grid, dim3(32 * UW_WARPS), 0, st, up);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     } else {
         UpTParams up;
@@ -723,7 +735,7 @@ cudaError_t launch_backward(const BwdPlan &B, cudaStream_t st)
         const size_t smem = ((size_t)2 * NRmax * UT_TI + (size_t)UT_TI * 3 * F.s + (size_t)up.TJ * 3 * F.s) * sizeof(float);
         if ((err = opt_in_smem(k_bwd_upsample_T, smem)) != cudaSuccess) return err;
         dim3 grid((F.w + UT_TI - 1) / UT_TI, (F.h + up.TJ - 1) / up.TJ, planes);
-        k_bwd_upsample_T<<<grid, UT_NT, smem, st>>>(up);
+        launch_pdl(k_bwd_upsample_T, grid, dim3(UT_NT), smem, st, up);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
 
@@ -763,7 +775,7 @@ cudaError_t launch_backward(const BwdPlan &B, cudaStream_t st)
                          al16(fp.g) && al16(fp.dI) && (!fp.dp || al16(fp.dp));
         if (vec) {
             dim3 grid((F.W / 4 + BF_NT - 1) / BF_NT, F.H, F.N);
-#define GF_BFV(ss, m) k_bwd_full_v<ss, m><<<grid, BF_NT, 0, st>>>(fp)
+#define GF_BFV(ss, m) launch_pdl(k_bwd_full_v<ss, m>, grid, dim3(BF_NT), 0, st, fp)
             if (F.s == 4) {
                 if (F.mode == GF_SUB_BOX) GF_BFV(4, GF_SUB_BOX);
                 else if (F.mode == GF_SUB_NEAREST) GF_BFV(4, GF_SUB_NEAREST);
@@ -776,7 +788,7 @@ cudaError_t launch_backward(const BwdPlan &B, cudaStream_t st)
 #undef GF_BFV
         } else {
             dim3 grid((F.W + BF_NT - 1) / BF_NT, F.H, F.N);
-            k_bwd_full<<<grid, BF_NT, 0, st>>>(fp);
+            launch_pdl(k_bwd_full, grid, dim3(BF_NT), 0, st, fp);
         }
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         if (F.p_lowres) {  // p was given at low resolution: dp = dp' (dense copy out of the strided workspace)
@@ -789,7 +801,7 @@ cudaError_t launch_backward(const BwdPlan &B, cudaStream_t st)
     // ---- deps
     if (B.d_eps) {
         const int np = (int)bwd_eps_partials(F.N, F.C, F.h, F.w);
-        k_reduce_eps<<<1, 256, 0, st>>>(B.eps_partial, np, B.d_eps);
+        launch_pdl(k_reduce_eps, 1, dim3(256), 0, st, B.eps_partial, np, B.d_eps);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     return cudaSuccess;

@@ -64,6 +64,7 @@ __device__ __forceinline__ void clear_call_fault(unsigned *word)
 template <typename T, int MODE>
 __global__ void __launch_bounds__(SUB_NT) k_subsample(SubParams P)
 {
+    pdl_wait();  // launched with programmatic serialization: earlier kernels are complete here
     clear_call_fault(P.clear_word);
     const int i = blockIdx.x * SUB_NT + threadIdx.x;
     const int j0 = blockIdx.y * SUB_JB;
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(SUB_NT) k_subsample(SubParams P)
 #pragma unroll
     for (int u = 0; u < SUB_JB; ++u)
         if (j0 + u < P.h) dst[(size_t)(j0 + u) * P.w] = v[u] * P.scale;
+    pdl_trigger();
 }
 
 // Antialiased bilinear subsample: along each axis, source pixel x weighs n(x) = 2s - |2x + 1 - (2i + 1)s|
@@ -92,6 +94,7 @@ __global__ void __launch_bounds__(SUB_NT) k_subsample(SubParams P)
 template <typename T>
 __global__ void __launch_bounds__(SUB_NT) k_subsample_aa(SubParams P)
 {
+    pdl_wait();  // launched with programmatic serialization: earlier kernels are complete here
     clear_call_fault(P.clear_word);
     const int i = blockIdx.x * SUB_NT + threadIdx.x;
     const int j0 = blockIdx.y * SUB_JB;
@@ -138,6 +141,7 @@ __global__ void __launch_bounds__(SUB_NT) k_subsample_aa(SubParams P)
         for (int y = ja; y <= jb; ++y) ny += wnum(y, j);
         dst[(size_t)j * P.w] = acc[u] / ((float)nx * (float)ny) * P.scale;
     }
+    pdl_trigger();
 }
 
 // Aligned FP32 fast path of the box and antialiased subsamples for s = 2, 4, 8 with H and W multiples of s.
@@ -163,6 +167,7 @@ __device__ __forceinline__ void ld_chunk(const float *p, float (&v)[S])
 template <int MODE, int S>
 __global__ void __launch_bounds__(SUB_NT) k_subsample_wide(SubParams P)
 {
+    pdl_wait();  // launched with programmatic serialization: earlier kernels are complete here
     clear_call_fault(P.clear_word);
     const int i = blockIdx.x * SUB_NT + threadIdx.x;
     const int j0 = blockIdx.y * SUB_JB;
@@ -230,6 +235,7 @@ __global__ void __launch_bounds__(SUB_NT) k_subsample_wide(SubParams P)
             dst[(size_t)j * P.w] = acc[u] / (nx * ny);
         }
     }
+    pdl_trigger();
 }
 
 // The two source columns a bilinear sample at ratio S reads (S/2 - 1 and S/2 of the block; the sample
@@ -392,6 +398,7 @@ struct Quant {
 template <typename T, int KIND, bool COMP, int BT_RV, int BT_RH>
 __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile(BoxParams P)
 {
+    pdl_wait();  // launched with programmatic serialization: earlier kernels are complete here
     const int BT_NT = blockDim.x;
     using Q = Quant<KIND>;
     constexpr int NQ = Q::NQ;
@@ -561,6 +568,7 @@ __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile(BoxParams P)
             P.out1[obase + (size_t)y * w + x] = Ot[BT_TH * BT_OP + yr * BT_OP + xt];
         }
     }
+    pdl_trigger();
 }
 
 // Packed form of k_box_tile for the FP32 kinds (KIND 0 and 2) at r' <= 16: the window sums travel as float2
@@ -570,6 +578,7 @@ __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile(BoxParams P)
 template <typename T, int KIND, int BT_RV, int BT_RH, int RC = 0>
 __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile_x2(BoxParams P)
 {
+    pdl_wait();  // launched with programmatic serialization: earlier kernels are complete here
     constexpr int NP = (KIND == KIND_MEAN2) ? 1 : 2;  // float2 pairs
     // uint8 input (KIND 1): the samples are integers J, P <= 1020 and J^2, J P <= 1020^2 < 2^24, so the
     // unshifted FP32 column sums of at most 2 r' + 2 <= 10 rows are exact; they are staged as uint32 and the
@@ -789,6 +798,7 @@ __global__ void __launch_bounds__(BT_NT_MAX) k_box_tile_x2(BoxParams P)
             }
         }
     }
+    pdl_trigger();
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -854,6 +864,7 @@ __device__ __forceinline__ void ld4<uint8_t>(const uint8_t *p, bool vec, int val
 template <typename TI, typename TQ, int CC, bool VEC>
 __global__ void __launch_bounds__(UP_NT) k_upsample_output(UpParams P)
 {
+    pdl_wait();  // launched with programmatic serialization: earlier kernels are complete here
     extern __shared__ float tap[];  // [CC][2][LRmax][LCmax] low-res tap tile (mean_a, mean_b)
     const int Xb = blockIdx.x * UP_BAND;
     const int Yb = max(blockIdx.y * P.R, P.Yw0), Ye = min(min(blockIdx.y * P.R + P.R, P.H), P.Yw1);
@@ -981,6 +992,7 @@ __global__ void __launch_bounds__(UP_NT) k_upsample_output(UpParams P)
             }
         }
     }
+    pdl_trigger();
 }
 
 // s = 4 or 8, 4-aligned rows (one guide channel for all of p, or one per channel).  Full-res row S*j + S/2 + k (k = 0 .. S-1) samples low-res
@@ -993,6 +1005,7 @@ __global__ void __launch_bounds__(UP_NT) k_upsample_output(UpParams P)
 template <typename TI, typename TQ, int S>
 __global__ void __launch_bounds__(UP_NT, 8) k_upsample_output_s4x(UpParams P)
 {
+    pdl_wait();  // launched with programmatic serialization: earlier kernels are complete here
     extern __shared__ float tap[];  // [2][LRmax][LCmax]: mean_a, mean_b at low-res rows jb-1 .. jb+nb, clamped
     const int nb = P.R / S;         // low-res rows (bands) per CTA
     const int jb = blockIdx.y * nb;
@@ -1115,11 +1128,13 @@ __global__ void __launch_bounds__(UP_NT, 8) k_upsample_output_s4x(UpParams P)
         }
     }
     cp_async_wait_all();
+    pdl_trigger();
 }
 
 template <typename TI, typename TQ, int CC, bool VEC>
 __global__ void __launch_bounds__(UP_NT) k_output_s1(UpParams P)
 {
+    pdl_wait();  // launched with programmatic serialization: earlier kernels are complete here
     const int X0 = (blockIdx.x * UP_NT + threadIdx.x) * 4;
     if (X0 >= P.W) return;
     const int valid = min(4, P.W - X0);
@@ -1151,6 +1166,7 @@ __global__ void __launch_bounds__(UP_NT) k_output_s1(UpParams P)
             st4<TQ>((TQ *)P.q + (size_t)(n * P.C + c) * HW + (size_t)Y * P.W + X0, vec, valid, out);
         }
     }
+    pdl_trigger();
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -1186,10 +1202,10 @@ template <typename T>
 void launch_sub_t(const SubParams &sp, dim3 grid, cudaStream_t st)
 {
     switch (sp.mode) {
-    case GF_SUB_NEAREST: k_subsample<T, GF_SUB_NEAREST><<<grid, SUB_NT, 0, st>>>(sp); break;
-    case GF_SUB_BILINEAR: k_subsample<T, GF_SUB_BILINEAR><<<grid, SUB_NT, 0, st>>>(sp); break;
-    case GF_SUB_BOX: k_subsample<T, GF_SUB_BOX><<<grid, SUB_NT, 0, st>>>(sp); break;
-    default: k_subsample_aa<T><<<grid, SUB_NT, 0, st>>>(sp); break;
+    case GF_SUB_NEAREST: launch_pdl(k_subsample<T, GF_SUB_NEAREST>, grid, dim3(SUB_NT), 0, st, sp); break;
+    case GF_SUB_BILINEAR: launch_pdl(k_subsample<T, GF_SUB_BILINEAR>, grid, dim3(SUB_NT), 0, st, sp); break;
+    case GF_SUB_BOX: launch_pdl(k_subsample<T, GF_SUB_BOX>, grid, dim3(SUB_NT), 0, st, sp); break;
+    default: launch_pdl(k_subsample_aa<T>, grid, dim3(SUB_NT), 0, st, sp); break;
     }
 }
 
@@ -1204,7 +1220,7 @@ cudaError_t launch_box_v(const BoxParams &bp, int planes, cudaStream_t st)
     // one phase-1 item (column segment) per thread when it fits; phase 2 needs BT_TH * BT_TW / RH <= 256
     const int items = (BT_TW + 2 * bp.r) * (BT_TH / RV);
     const int nt = std::min(BT_NT_MAX, std::max(256, (items + 31) / 32 * 32));
-    k_box_tile<T, KIND, COMP, RV, RH><<<grid, nt, smem, st>>>(bp);
+    launch_pdl(k_box_tile<T, KIND, COMP, RV, RH>, grid, dim3(nt), smem, st, bp);
     return cudaGetLastError();
 }
 
@@ -1222,7 +1238,7 @@ cudaError_t launch_box_x2(const BoxParams &bp, int planes, cudaStream_t st)
     dim3 grid((bp.w + BT_TW - 1) / BT_TW, (bp.h + BT_TH - 1) / BT_TH, planes);
     const int items = (BT_TW + 2 * bp.r) * (BT_TH / RV);
     const int nt = std::min(BT_NT_MAX, std::max(256, (items + 31) / 32 * 32));
-    k_box_tile_x2<T, KIND, RV, RH, RC><<<grid, nt, smem, st>>>(bp);
+    launch_pdl(k_box_tile_x2<T, KIND, RV, RH, RC>, grid, dim3(nt), smem, st, bp);
     return cudaGetLastError();
 }
 
@@ -1262,7 +1278,7 @@ void launch_up_t(UpParams up, int N, int CC, bool vec, cudaStream_t st)
     const int bands = (up.W + UP_BAND - 1) / UP_BAND;
     if (s1) {
         dim3 grid(bands, (up.H + up.R - 1) / up.R, N * up.CG);
-#define GF_S1(cc, v) k_output_s1<TI, TQ, cc, v><<<grid, UP_NT, 0, st>>>(up)
+#define GF_S1(cc, v) launch_pdl(k_output_s1<TI, TQ, cc, v>, grid, dim3(UP_NT), 0, st, up)
         if (CC == 3) { if (vec) GF_S1(3, true); else GF_S1(3, false); }
         else { if (vec) GF_S1(1, true); else GF_S1(1, false); }
 #undef GF_S1
@@ -1282,8 +1298,8 @@ void launch_up_t(UpParams up, int N, int CC, bool vec, cudaStream_t st)
         up.LCmax = (up.LCmax + 1) & ~1;  // 2 * LRmax * LCmax floats is then a multiple of 16 bytes
         dim3 grid(bands * up.C, (up.H + up.R - 1) / up.R, N);
         const size_t smem = (size_t)2 * up.LRmax * up.LCmax * sizeof(float) + (size_t)UP_NST * 4 * UP_NT * 4 * sizeof(TI);
-        if (up.s == 4) k_upsample_output_s4x<TI, TQ, 4><<<grid, UP_NT, smem, st>>>(up);
-        else k_upsample_output_s4x<TI, TQ, 8><<<grid, UP_NT, smem, st>>>(up);
+        if (up.s == 4) launch_pdl(k_upsample_output_s4x<TI, TQ, 4>, grid, dim3(UP_NT), smem, st, up);
+        else launch_pdl(k_upsample_output_s4x<TI, TQ, 8>, grid, dim3(UP_NT), smem, st, up);
         return;
     }
     up.LRmax = (up.R * up.sd + up.sn - 1) / up.sn + 2;  // ceil(R / s) + 2 tap rows under R full-res rows
@@ -1293,7 +1309,7 @@ void launch_up_t(UpParams up, int N, int CC, bool vec, cudaStream_t st)
 #define GF_UP(cc, v)                                                                 \
     do {                                                                             \
         if (opt_in_smem(k_upsample_output<TI, TQ, cc, v>, smem) == cudaSuccess)      \
-            k_upsample_output<TI, TQ, cc, v><<<grid, UP_NT, smem, st>>>(up);         \
+            launch_pdl(k_upsample_output<TI, TQ, cc, v>, grid, dim3(UP_NT), smem, st, up);         \
     } while (0)
     if (CC == 3) { if (vec) GF_UP(3, true); else GF_UP(3, false); }
     else { if (vec) GF_UP(1, true); else GF_UP(1, false); }
@@ -1469,7 +1485,7 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
 #undef GF_SV
         } else if (aligned_fp32_wide_subsample(P)) {
             dim3 grid((P.w + SUB_NT - 1) / SUB_NT, (P.h + SUB_JB - 1) / SUB_JB, nz);
-#define GF_SW(m, ss) k_subsample_wide<m, ss><<<grid, SUB_NT, 0, st>>>(sp)
+#define GF_SW(m, ss) launch_pdl(k_subsample_wide<m, ss>, grid, dim3(SUB_NT), 0, st, sp)
             if (P.mode == GF_SUB_BOX) {
                 if (P.s == 2) GF_SW(GF_SUB_BOX, 2); else if (P.s == 4) GF_SW(GF_SUB_BOX, 4); else GF_SW(GF_SUB_BOX, 8);
             } else {

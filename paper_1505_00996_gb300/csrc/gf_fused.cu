@@ -190,8 +190,10 @@ __device__ __forceinline__ void fused_tile(const FusedParams &P, int bx, int by,
 template <typename TI, typename TQ, int MODE>
 __global__ void __launch_bounds__(FU_NT) k_fgf_fused(FusedParams P)
 {
+    pdl_wait();  // launched with programmatic serialization: earlier kernels are complete here
     extern __shared__ float sm[];
     fused_tile<TI, TQ, MODE>(P, blockIdx.x, blockIdx.y, blockIdx.z, sm);
+    pdl_trigger();
 }
 
 // The tile-queue form: one launch for the tiles of up to FUSED_QUEUE_MAX requests of the same storage types
@@ -208,12 +210,14 @@ struct FusedQueue {
 template <typename TI, typename TQ, int MODE>
 __global__ void __launch_bounds__(FU_NT) k_fgf_fused_queue(const __grid_constant__ FusedQueue Q)
 {
+    pdl_wait();  // launched with programmatic serialization: earlier kernels are complete here
     extern __shared__ float sm[];
     const int t = blockIdx.x;
     int k = 0;
     while (k + 1 < Q.n && t >= Q.start[k + 1]) ++k;
     const int local = t - Q.start[k], gx = Q.gx[k], gy = Q.gy[k];
     fused_tile<TI, TQ, MODE>(Q.p[k], local % gx, (local / gx) % gy, local / (gx * gy), sm);
+    pdl_trigger();
 }
 
 // Upper bounds of the region sizes for a TH x TW tile (low-res rows / columns), and the shared memory.
@@ -302,7 +306,7 @@ cudaError_t launch_fused_queue(const FwdPlan *plans, int n, cudaStream_t st)
 #define GF_FQ(TI, TQ, M)                                                                     \
     do {                                                                                     \
         if ((e = opt_in_smem(k_fgf_fused_queue<TI, TQ, M>, smem)) != cudaSuccess) return e;  \
-        k_fgf_fused_queue<TI, TQ, M><<<(unsigned)total, FU_NT, smem, st>>>(Q);               \
+        launch_pdl(k_fgf_fused_queue<TI, TQ, M>, (unsigned)total, dim3(FU_NT), smem, st, Q);               \
     } while (0)
 #define GF_FQ_MODE(TI, TQ)                                                                   \
     do {                                                                                     \
@@ -333,7 +337,7 @@ cudaError_t launch_fused(const FwdPlan &P, cudaStream_t st)
 #define GF_FU(TI, TQ, M)                                                                     \
     do {                                                                                     \
         if ((e = opt_in_smem(k_fgf_fused<TI, TQ, M>, S.smem)) != cudaSuccess) return e;      \
-        k_fgf_fused<TI, TQ, M><<<grid, FU_NT, S.smem, st>>>(F);                              \
+        launch_pdl(k_fgf_fused<TI, TQ, M>, grid, dim3(FU_NT), S.smem, st, F);                              \
     } while (0)
 #define GF_FU_MODE(TI, TQ)                                                                   \
     do {                                                                                     \
