@@ -12,12 +12,13 @@
 // serves three channels, of all three (the guide's sums are then formed once per pixel).  Phase 1: one thread
 // per strip column (the 128 columns and the r halo on each side: 160 threads at r = 16) carries the vertical
 // window sums down the segment, adding the row that enters the window and subtracting the row that leaves it,
-// both read straight from global memory (the leaving row was read 2r + 1 rows earlier, so it comes from L2),
-// and writes the sums of a block of 10 rows to shared memory.  Phase 2: every thread takes a run of 8 outputs of
-// one row of the block, slides the horizontal window along the column sums, applies the epilogue and stores
-// with 128-bit stores.  A window is opened once per segment, not per tile, and both phases keep all threads
-// busy, which the tile form (gf_box.cu) cannot at large radii: its 2r halo rows and columns cost more there
-// than the outputs themselves.
+// both read straight from global memory (the leaving row was read 2r + 1 rows earlier, so it comes from L2)
+// and requested a block ahead, and writes the sums of a block of 10 rows to shared memory.  Phase 2: every
+// thread takes a run of 8 outputs of one row of the block; the 16 runs of a row share the sums of whole
+// 8-column blocks, each run slides its window along the column sums, applies the epilogue and stores with
+// 128-bit stores.  A window is opened once per segment, not per tile, and both phases keep all threads busy,
+// which the tile form (gf_box.cu) cannot at large radii: its 2r halo rows and columns cost more there than the
+// outputs themselves.
 //
 // Statistics are taken of values shifted by one sample of the segment (its first output pixel), so
 // E[I^2] - E[I]^2 is formed from terms near the local level; pairs of quantities travel as packed FP32x2.
@@ -230,10 +231,11 @@ __host__ __device__ constexpr size_t buf_bytes(int NQ)
 }
 
 // Phase-2 reads of one run: the column sums of walker columns c0 + i (c0 = 8 g) of row k of a block.
-//   float2 layout (NQ == 1): column c at c + c / 8, i.e. 9 g + i + i / 8 -- a constant offset from the run's base;
-//   float4 layout (NQ >= 2): column c at c ^ ((c / 8) mod 8).  The window's whole 8-column blocks are read slot
-//   by slot, lane g taking slot (e + g) mod 8 at step e (8 distinct banks across a quarter-warp, constant offsets
-//   from 8 per-thread bases); single columns take the swizzle: one XOR and one address per read.
+//   float2 layout (NQ == 1): column c at c + 2 (c / 8), i.e. 10 g + i + 2 (i / 8) -- a constant offset from the
+//   run's base, each even / odd pair of columns one aligned 16-byte word;
+//   float4 layout (NQ >= 2): column c at c ^ ((c / 8) mod 8).  A run's own 8-column block is read slot by slot,
+//   lane g taking slot (e + g) mod 8 at step e (8 distinct banks across a quarter-warp), since a block sum does
+//   not depend on the order; single columns take the swizzle: one XOR and one address per read.
 template <int NQ>
 struct RunReader {
     const float4 *pair2;  // NQ == 1: the run's base (column pairs c0 + i, c0 + i + 1 for even i)
