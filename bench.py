@@ -51,7 +51,7 @@ def parse_args():
                          "guides); precision: only the 12 MP workload stored as FP32, FP16 and uint8")
     ap.add_argument("--no-graph", action="store_true", help="launch every step eagerly instead of graph replay")
     ap.add_argument("--no-extras", action="store_true", help="skip the s sweep, e2e, cpu baseline")
-    ap.add_argument("--streams", type=int, default=2,
+    ap.add_argument("--streams", type=int, default=3,
                     help="independent images in flight, one stream (own scratch, own input copy) each")
     ap.add_argument("--shard", choices=["images", "rows"], default="images",
                     help="N > 1: every rank filters its own image (weak scaling), or one image split into row "
