@@ -150,11 +150,12 @@ __device__ __forceinline__ void put_sums(unsigned char *buf, int k, int j, const
 // window of output row yb + k and row yb + k - r leaves it after.  They are requested one block ahead (fetch
 // right after the previous block's column sums are written), so the loads are in flight during phase 2.  A row
 // outside the image reads as the shift value, whose shifted pair is exactly zero.  The three-channel statistics
-// (four planes) have no registers to spare for that and read their rows when they use them.
-template <int KIND, int NY>
+// (four planes) request their leaving rows ahead only at the radii 15 and 16 (PL), where a batch of 80 values a
+// thread and two CTAs per SM pay; elsewhere they read those rows when they use them, at three CTAs per SM.
+template <int KIND, int NY, bool PL>
 struct RowBatch {
     static constexpr int NS = Column<KIND, NY>::NS;
-    static constexpr bool PRE_L = (NS <= 2);  // the leaving rows too
+    static constexpr bool PRE_L = (NS <= 2) || PL;  // the leaving rows too
     float e[SP_CB][NS], l[PRE_L ? SP_CB : 1][NS];
     __device__ __forceinline__ static float ld_row(const Column<KIND, NY> &col, int t, int h, int k)
     {
@@ -183,8 +184,8 @@ struct RowBatch {
 // Phase 1 of one block for one walker column: the vertical window sums of rows yb .. yb + SP_CB - 1 from the
 // batch fetched for them.  S holds the sums of rows [yb - r, yb + r - 1] (clipped to the image) on entry and is
 // carried on to the next block.
-template <int KIND, int NY>
-__device__ __forceinline__ void walk_block(const Column<KIND, NY> &col, const RowBatch<KIND, NY> &B,
+template <int KIND, int NY, bool PL>
+__device__ __forceinline__ void walk_block(const Column<KIND, NY> &col, const RowBatch<KIND, NY, PL> &B,
                                            float2 (&S)[nq_of(KIND, NY)], int yb, int r, int h, unsigned char *buf,
                                            int j)
 {
@@ -194,12 +195,12 @@ __device__ __forceinline__ void walk_block(const Column<KIND, NY> &col, const Ro
     for (int k = 0; k < SP_CB; ++k) {
         float2 qe[NQ], ql[NQ];
         col.pairs(B.e[k], qe);
-        if constexpr (RowBatch<KIND, NY>::PRE_L) {
+        if constexpr (RowBatch<KIND, NY, PL>::PRE_L) {
             col.pairs(B.l[k], ql);
         } else {
             float vl[NS];
 #pragma unroll
-            for (int q = 0; q < NS; ++q) vl[q] = RowBatch<KIND, NY>::ld_row(col, yb + k - r, h, q);
+            for (int q = 0; q < NS; ++q) vl[q] = RowBatch<KIND, NY, PL>::ld_row(col, yb + k - r, h, q);
             col.pairs(vl, ql);
         }
 #pragma unroll
@@ -384,15 +385,24 @@ struct RunReader {
     }
 };
 
+// Whether the three-channel statistics request their leaving rows a block ahead: at the compile-time radii 15 and
+// 16 (12 MP, s = 1, r = 16: 158 us against 164 us).  At r' = 4 one call alone also gains, but with other images'
+// kernels in flight on other streams the 168-register CTAs leave them less room (190.4 k -> 186.1 k MP/s), and the
+// run-time radius form loses (r = 12: 179 us against 175 us).
+__host__ __device__ constexpr bool pl_of(int NQ, int RC) { return NQ == 4 && (RC == 15 || RC == 16); }
 // CTAs per SM the registers are sized for: four; three for the three-channel statistics, whose batch of entering
-// rows (four planes) needs the registers of a 3-CTA split, and for the box means + output, which also holds the
-// next block's guide row.
-__host__ __device__ constexpr int minb_of(int KIND, int NQ) { return (NQ == 4 || KIND == SK_MEAN2_OUT) ? 3 : 4; }
+// rows (four planes) needs the registers of a 3-CTA split (two where the batch holds the leaving rows too), and for
+// the box means + output, which also holds the next block's guide row.
+__host__ __device__ constexpr int minb_of(int KIND, int NQ, int RC)
+{
+    return pl_of(NQ, RC) ? 2 : ((NQ == 4 || KIND == SK_MEAN2_OUT) ? 3 : 4);
+}
 
 template <int KIND, int NY, int RC, typename TQ>
-__global__ void __launch_bounds__(SP_NT, minb_of(KIND, nq_of(KIND, NY))) k_box_strip(StripParams P)
+__global__ void __launch_bounds__(SP_NT, minb_of(KIND, nq_of(KIND, NY), RC)) k_box_strip(StripParams P)
 {
     constexpr int NQ = nq_of(KIND, NY);
+    constexpr bool PL = pl_of(NQ, RC);
     constexpr int NS = Column<KIND, NY>::NS;
     constexpr int NBUF = db_of(NQ) ? 2 : 1;
     const int r = RC >= 0 ? RC : P.r;
@@ -458,14 +468,14 @@ __global__ void __launch_bounds__(SP_NT, minb_of(KIND, nq_of(KIND, NY))) k_box_s
         }
     };
     if constexpr (KIND == SK_MEAN2_OUT) load_guide(y0 + pk, ivn);
-    RowBatch<KIND, NY> B;
+    RowBatch<KIND, NY, PL> B;
     if (colok) B.fetch(col, y0, r, h);
     for (int b = 0; b < nblocks; ++b) {
         const int yb = y0 + b * SP_CB;
         unsigned char *buf = sm + (NBUF == 2 ? (size_t)(b & 1) * buf_bytes(NQ) : 0);
         // ---- phase 1: vertical window sums of the block's rows; then the next block's rows are requested
         if (colok) {
-            walk_block<KIND, NY>(col, B, S, yb, r, h, buf, tid);
+            walk_block<KIND, NY, PL>(col, B, S, yb, r, h, buf, tid);
             if (b + 1 < nblocks) B.fetch(col, yb + SP_CB, r, h);
         } else if (walker) {  // a column outside the image contributes nothing
             const float2 Z[NQ] = {};
