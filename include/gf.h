@@ -187,8 +187,12 @@ gf_status gf_kernel_faults(int device, unsigned *flags, int clear);
 
 /* Number of kernels one gf_filter call with these arguments launches (host-only; -1 for invalid
  * arguments): 1 when the single fused kernel runs (gf_opts.fused); else 4 when s > 1 (subsample,
- * statistics + coefficients, box means of a and b, upsample + output), 3 when s = 1 (no subsample); 6 with
- * a colour guide (subsample, products, box means, coefficients, box means, upsample + output). */
+ * statistics + coefficients, box means of a and b, upsample + output), 3 when the subsample and the
+ * statistics run as one kernel (opt-in with the environment variable GF_SUB_STRIP=1: FP32, s = 4 or 8,
+ * nearest or bilinear, a gray guide for C a multiple of 3, r' = 4, which this count learns from
+ * opts->r_low; 16-byte aligned planes and no stats_out assumed); at s = 1, 2 (statistics, then the box
+ * means fused with the output; rows a multiple of 4 pixels) or 3; 6 with a colour guide (subsample,
+ * products, box means, coefficients, box means, upsample + output). */
 int gf_filter_kernel_count(int H, int W, int C, int s, gf_subsample_mode mode, const gf_opts *opts);
 
 /* Bytes of device scratch one gf_filter call with these arguments needs (host-only). */

@@ -113,6 +113,16 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int x, 
         : "memory");
 }
 
+// One 4-D tiled TMA load (box at element coordinates x, y, z, v; x * element size a multiple of 16 bytes).
+__device__ __forceinline__ void tma_load_4d(void *dst, const void *tmap, int x, int y, int z, int v, unsigned bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(x), "r"(y), "r"(z), "r"(v), "r"(bar)
+        : "memory");
+}
+
 // Upsampling taps along one axis at ratio s = sn / sd: full-res index X samples position
 // (X + 1/2)/s - 1/2 = ((2X + 1) sd - sn)/(2 sn), clamped to [0, n-1].  Integer arithmetic keeps the taps exact.
 __device__ __forceinline__ void up_taps_q(int X, int sn, int sd, int n, int &i0, int &i1, float &f)

@@ -1368,11 +1368,19 @@ bool s1_means_output_form(const Resolved &R)
            (R.dt_out == F32 || R.dt_out == F16) && R.W % 4 == 0 && R.r_low <= 16;
 }
 
+// Whether a call with this geometry takes the subsample and the box statistics as one kernel (k_box_strip_sub),
+// given 16-byte aligned planes and no window statistics asked for (gf_opts.stats_out).
+static bool sub_strip_form(const Resolved &R)
+{
+    return !R.color && !R.fused && !R.saved_forward && !R.int_stats &&
+           strip_sub_geometry(R.C, R.CI, R.H, R.W, R.h, R.w, R.s, R.sd, R.mode, R.r_low, R.dt_in, R.p_lowres);
+}
+
 int forward_kernel_count(const Resolved &R)
 {
     if (R.fused) return 1;
     if (R.color) return 6;
-    if (R.s > 1) return 4;
+    if (R.s > 1) return sub_strip_form(R) ? 3 : 4;
     return s1_means_output_form(R) ? 2 : 3;
 }
 
@@ -1454,7 +1462,21 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
     // A self-guided call (p is I, one guide channel per channel) subsamples once and uses I' as p'; the
     // backward keeps its own p' plane, so its forward recomputation subsamples both.
     const bool self_guided = (P.I == P.p) && (P.CI == P.C) && !P.p_lowres && !P.need_lowres;
-    if (P.s > 1 || P.color) {  // the colour stages read low-res planes only, so s = 1 copies
+    // The subsample and the box statistics as one kernel (k_box_strip_sub) where it takes the call: then I', p'
+    // are never written, so not when they are kept for the backward or the window statistics are asked for.
+    SubStripJob SJ{};
+    bool sub_strip = false;
+    if (!P.color && !P.need_lowres && !P.stats && !P.int_stats &&
+        strip_sub_geometry(P.C, P.CI, P.H, P.W, P.h, P.w, P.s, P.sd, P.mode, P.r_low, P.dt_in, P.p_lowres)) {
+        SJ.I = (const float *)P.I; SJ.p = (const float *)P.p; SJ.fps = P.fps;
+        SJ.N = P.N; SJ.C = P.C; SJ.H = P.H; SJ.W = P.W; SJ.h = P.h; SJ.w = P.w; SJ.s = P.s; SJ.mode = P.mode;
+        SJ.r = P.r_low; SJ.eps = P.eps;
+        SJ.a = P.a; SJ.b = P.b; SJ.ops = P.lps;
+        SJ.clear_word = clear_word;
+        SJ.fault = P.fault;
+        sub_strip = strip_sub_supported(SJ);
+    }
+    if ((P.s > 1 || P.color) && !sub_strip) {  // the colour stages read low-res planes only, so s = 1 copies
         SubParams sp;
         sp.h = P.h; sp.w = P.w; sp.mode = P.mode;
         // uint8 path: carry the subsampled values as exact integers J = k * (value in 1/255 units)
@@ -1510,7 +1532,12 @@ cudaError_t launch_forward(const FwdPlan &P, cudaStream_t st)
     if (P.color) return launch_color_chain(P, self_guided ? P.Il : P.pl, tm, st);
 
     // ---- Algorithm 2, box statistics + var/cov + coefficients a, b (Eq. 2-3)
-    {
+    if (sub_strip) {
+        tm.before();
+        err = launch_strip_sub(SJ, st);
+        tm.after();
+        if (err != cudaSuccess) return err;
+    } else {
         BoxParams bp{};
         bp.X = Xsrc; bp.Y = Ysrc;
         const bool lowres_src = (P.s > 1);

@@ -244,6 +244,28 @@ cudaError_t launch_box_tma(const BoxTmaJob &J, cudaStream_t st);
 // multiple of 4 outputs, 16-byte aligned outputs, no window statistics kept), and their launch.
 bool strip_box_supported(const BoxTmaJob &J);
 cudaError_t launch_strip_box(const BoxTmaJob &J, cudaStream_t st);
+// 4-D tensor map of the full-res rows a subsample at ratio S reads (gf_tma.cu): dims (W, S, h, planes), box
+// box_w columns x nph rows of one S-row block.  False when the encoder is unavailable or rejects it.
+bool encode_tmap_sampled_rows(CUtensorMap *map, const float *base, int W, int S, int h, int planes,
+                              size_t plane_stride, int box_w, int nph);
+// Algorithm 2's first two steps in one kernel (gf_strip.cu): the nearest or bilinear subsample of a gray guide
+// and three channels of p per group, fed by TMA, and the box statistics + coefficients a, b of the samples.
+// FP32 full-res planes (plane stride fps), H = s h and W = s w, s = 4 or 8; a, b as for BOX_JOB_STATS.
+struct SubStripJob {
+    const float *I, *p;  // N guide planes, N * C input planes
+    size_t fps;
+    int N, C, H, W, h, w, s, mode, r;
+    float eps;
+    float *a, *b;
+    size_t ops;
+    unsigned *clear_word;  // the call's fault word, zeroed by the kernel (the first of the chain), or NULL
+    FaultSink fault;
+};
+// Whether the geometry takes the fused form (no pointer checked); and whether these buffers do.
+bool strip_sub_geometry(int C, int CI, int H, int W, int h, int w, int s, int sd, int mode, int r_low, int dt_in,
+                        bool p_lowres);
+bool strip_sub_supported(const SubStripJob &J);
+cudaError_t launch_strip_sub(const SubStripJob &J, cudaStream_t st);
 
 // The single-kernel form (gf_fused.cu): whether it can run these arguments, and its launch.
 bool fused_supported(const Resolved &R, bool intermediates);

@@ -22,6 +22,7 @@
 //
 // Statistics are taken of values shifted by one sample of the segment (its first output pixel), so
 // E[I^2] - E[I]^2 is formed from terms near the local level; pairs of quantities travel as packed FP32x2.
+#include <algorithm>
 #include <atomic>
 #include <type_traits>
 
@@ -50,6 +51,7 @@ struct StripParams {
     int groups;          // CTAs across the channels of one image (C / NY)
     int h, w, r;         // plane size; radius (used when the kernel's RC < 0)
     int ylo, yhi, seg;   // output rows [ylo, yhi), seg rows per CTA (a multiple of SP_CB)
+    int seg_order;       // the grid's rows take the segments in the order (k mod seg_order, k / seg_order)
     float eps;
     float *out0, *out1;  // SK_STATS: a, b; SK_MEAN2: mean_a, mean_b (plane stride ops)
     size_t ops;
@@ -134,10 +136,9 @@ struct Column {
 };
 
 // Column sums of one row of a block into shared memory (walker column j).
-template <int NQ>
+template <int NQ, int VP = vp_of(NQ)>
 __device__ __forceinline__ void put_sums(unsigned char *buf, int k, int j, const float2 S[NQ])
 {
-    constexpr int VP = vp_of(NQ);
     if constexpr (NQ == 1) {
         reinterpret_cast<float2 *>(buf)[k * VP + vidx2(j)] = S[0];
     } else {
@@ -237,14 +238,13 @@ __host__ __device__ constexpr size_t buf_bytes(int NQ)
 //   float4 layout (NQ >= 2): column c at c ^ ((c / 8) mod 8).  A run's own 8-column block is read slot by slot,
 //   lane g taking slot (e + g) mod 8 at step e (8 distinct banks across a quarter-warp), since a block sum does
 //   not depend on the order; single columns take the swizzle: one XOR and one address per read.
-template <int NQ>
+template <int NQ, int VP = vp_of(NQ)>
 struct RunReader {
     const float4 *pair2;  // NQ == 1: the run's base (column pairs c0 + i, c0 + i + 1 for even i)
     const float4 *row4;   // NQ >= 2: the block's row
     int pg;
     __device__ __forceinline__ RunReader(const unsigned char *buf, int k, int g) : pg(g)
     {
-        constexpr int VP = vp_of(NQ);
         pair2 = reinterpret_cast<const float4 *>(reinterpret_cast<const float2 *>(buf) + k * VP + 10 * g);
         row4 = reinterpret_cast<const float4 *>(buf) + k * VP;
     }
@@ -309,7 +309,7 @@ struct RunReader {
         T[0] = add2(T[0], make_float2(a.x, a.y));
         T[1] = add2(T[1], make_float2(a.z, a.w));
         if constexpr (NQ == 4) {
-            const float4 b = p[SP_CB * vp_of(NQ)];
+            const float4 b = p[SP_CB * VP];
             T[2] = add2(T[2], make_float2(b.x, b.y));
             T[3] = add2(T[3], make_float2(b.z, b.w));
         }
@@ -320,7 +320,7 @@ struct RunReader {
         u[0] = make_float2(a.x, a.y);
         u[1] = make_float2(a.z, a.w);
         if constexpr (NQ == 4) {
-            const float4 b = p[SP_CB * vp_of(NQ)];
+            const float4 b = p[SP_CB * VP];
             u[2] = make_float2(b.x, b.y);
             u[3] = make_float2(b.z, b.w);
         }
@@ -390,6 +390,135 @@ struct RunReader {
 // kernels in flight on other streams the 168-register CTAs leave them less room (190.4 k -> 186.1 k MP/s), and the
 // run-time radius form loses (r = 12: 179 us against 175 us).
 __host__ __device__ constexpr bool pl_of(int NQ, int RC) { return NQ == 4 && (RC == 15 || RC == 16); }
+// Phase 2 of one block for one thread: the horizontal windows of its run (row pk of the block: outputs ox .. ox + 7 of
+// output row y) from the column sums in buf, the epilogue and the 128-bit stores.  bs holds the block sums the
+// runs of a row share.  Every one of the CTA's 160 threads calls it, live run or not (the block sums synchronise
+// each half-warp).  shift: the values subtracted from every plane (statistics); iv: the guide under the run
+// (box means + output).
+template <int KIND, int NY, int RC, typename TQ, int VP = vp_of(nq_of(KIND, NY))>
+__device__ __forceinline__ void run_block(const StripParams &P, const unsigned char *buf, unsigned char *bs,
+                                          const float (&shift)[Column<KIND, NY>::NS], const float (&iv)[8], int y,
+                                          bool live, int pk, int pg, int ox, int r, int h, int w, int n, int grp,
+                                          bool second, bool x_interior, float inv_full)
+{
+    constexpr int NQ = nq_of(KIND, NY);
+    const RunReader<NQ, VP> rd(buf, pk, pg);
+    float2 W8[NQ == 1 ? SP_RUN : 1];
+    float2 T[NQ];
+    {
+        if constexpr (NQ == 1) {
+            rd.template windows8_shared<RC>(r, reinterpret_cast<float2 *>(bs) + pk * SP_NBLK, W8);
+        } else {
+            float4 *bA = reinterpret_cast<float4 *>(bs) + pk * SP_NBLK;
+            rd.template window_shared<RC>(r, bA, bA + SP_CB * SP_NBLK, T);
+        }
+    }
+    if (live) {
+        const bool interior = x_interior && (y - r >= 0) && (y + r < h);
+        const int ny = min(h - 1, y + r) - max(0, y - r) + 1;
+        // output rows of this run
+        constexpr int NO = (KIND == SK_STATS) ? 2 * NY : (KIND == SK_MEAN2 ? 2 : 1);
+        float *dst0[NO / 2 > 0 ? NO / 2 : 1], *dst1[NO / 2 > 0 ? NO / 2 : 1];
+        TQ *dq = nullptr;
+        if constexpr (KIND == SK_MEAN2_OUT) {
+            dq = (TQ *)P.q + (size_t)(n * P.C + grp) * P.fps + (size_t)y * w + ox;
+        } else {
+#pragma unroll
+            for (int k = 0; k < NO / 2; ++k) {
+                const size_t off = (size_t)(n * P.C + grp * (NO / 2) + k) * P.ops + (size_t)y * w + ox;
+                dst0[k] = P.out0 + off;
+                dst1[k] = P.out1 + off;
+            }
+        }
+        auto run = [&](auto border_tag) {
+            constexpr bool BORDER = decltype(border_tag)::value;
+            float o[NO][4];
+#pragma unroll
+            for (int j = 0; j < SP_RUN; ++j) {
+                if constexpr (NQ == 1) T[0] = W8[j];
+                else if (j > 0) rd.template slide<RC>(j, r, T);
+                float inv = inv_full;
+                if constexpr (BORDER) {
+                    const int xx = ox + j;
+                    const int nx = min(w - 1, xx + r) - max(0, xx - r) + 1;
+                    inv = __fdividef(1.0f, (float)(nx * ny));
+                }
+                const float2 iv2 = make_float2(inv, inv);
+                const int jj = j & 3;
+                if constexpr (KIND == SK_STATS) {
+                    const float2 m0 = mul2(T[0], iv2);
+                    if constexpr (NY == 1) {
+                        const float2 m1 = mul2(T[1], iv2);
+                        // var_I, cov_Ip; exactly 0 for a one-sample window (r = 0), as in the tile kernels
+                        const float var = r ? fmaxf(fmaf(-m0.x, m0.x, m1.x), 0.0f) : 0.0f;
+                        const float cov = r ? fmaf(-m0.x, m0.y, m1.y) : 0.0f;
+                        const float a = __fdividef(cov, var + P.eps);            // a, Eq. (2)
+                        o[0][jj] = a;
+                        o[1][jj] = (m0.y + shift[1]) - a * (m0.x + shift[0]);    // b, Eq. (3)
+                    } else {
+                        const float2 m1 = mul2(T[1], iv2), m2 = mul2(T[2], iv2), m3 = mul2(T[3], iv2);
+                        const float var = r ? fmaxf(fmaf(-m0.x, m0.x, m2.x), 0.0f) : 0.0f;
+                        const float rv = __fdividef(1.0f, var + P.eps);
+                        const float mx = m0.x + shift[0];
+                        const float my[3] = {m0.y, m1.x, m1.y}, mxy[3] = {m2.y, m3.x, m3.y};
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            const float cov = r ? fmaf(-m0.x, my[k], mxy[k]) : 0.0f;
+                            const float a = cov * rv;                             // a, Eq. (2)
+                            o[2 * k][jj] = a;
+                            o[2 * k + 1][jj] = (my[k] + shift[1 + k]) - a * mx;   // b, Eq. (3)
+                        }
+                    }
+                } else if constexpr (KIND == SK_MEAN2) {
+                    o[0][jj] = T[0].x * inv;  // mean_a
+                    o[1][jj] = T[0].y * inv;  // mean_b
+                } else {
+                    o[0][jj] = fmaf(T[0].x * inv, iv[j], T[0].y * inv);  // Eq. (4)
+                }
+                if (jj == 3 && (j == 3 || second)) {  // a float4 of every output plane
+                    const int xs = j - 3;
+                    if constexpr (KIND == SK_MEAN2_OUT) {
+                        if (P.detail != 0.0f) {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) o[0][e] = fmaf(P.detail, iv[xs + e] - o[0][e], o[0][e]);
+                        }
+                        store4q<TQ>(dq + xs, o[0]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < NO / 2; ++k) {
+                            const float4 va = make_float4(o[2 * k][0], o[2 * k][1], o[2 * k][2], o[2 * k][3]);
+                            const float4 vb =
+                                make_float4(o[2 * k + 1][0], o[2 * k + 1][1], o[2 * k + 1][2], o[2 * k + 1][3]);
+                            if (P.stream_out) {  // planes larger than L2: streamed
+                                __stcs(reinterpret_cast<float4 *>(dst0[k] + xs), va);
+                                __stcs(reinterpret_cast<float4 *>(dst1[k] + xs), vb);
+                            } else {             // small planes stay in L2 for the next kernel
+                                *reinterpret_cast<float4 *>(dst0[k] + xs) = va;
+                                *reinterpret_cast<float4 *>(dst1[k] + xs) = vb;
+                            }
+                        }
+                    }
+                }
+            }
+        };
+        if (interior) run(std::false_type{});
+        else run(std::true_type{});
+    }
+}
+
+// The segment of grid row p (of n): the rows take the segments in the order (k mod m, k / m).  With m the waves
+// of resident CTAs an image's grid fills, segment k + 1 then starts in the wave after segment k's, about when
+// segment k ends, so the 2r rows that open its window (the last ones segment k read) are still in L2.
+__device__ __forceinline__ int seg_of(int p, int n, int m)
+{
+    for (int j = 0; j < m - 1; ++j) {
+        const int c = (n - j + m - 1) / m;  // segments k < n with k mod m == j
+        if (p < c) return j + m * p;
+        p -= c;
+    }
+    return (m - 1) + m * p;
+}
+
 // CTAs per SM the registers are sized for: four; three for the three-channel statistics, whose batch of entering
 // rows (four planes) needs the registers of a 3-CTA split (two where the batch holds the leaving rows too), and for
 // the box means + output, which also holds the next block's guide row.
@@ -409,7 +538,7 @@ __global__ void __launch_bounds__(SP_NT, minb_of(KIND, nq_of(KIND, NY), RC)) k_b
     const int h = P.h, w = P.w, tid = threadIdx.x;
     const int grp = blockIdx.x % P.groups, sx = blockIdx.x / P.groups, n = blockIdx.z;
     const int x0 = sx * SP_TW;
-    const int y0 = P.ylo + blockIdx.y * P.seg, yend = min(y0 + P.seg, P.yhi);
+    const int y0 = P.ylo + seg_of(blockIdx.y, gridDim.y, P.seg_order) * P.seg, yend = min(y0 + P.seg, P.yhi);
     extern __shared__ __align__(16) unsigned char sm[];
     pdl_wait();  // launched with programmatic serialization: the previous kernel's planes are complete here
 
@@ -493,112 +622,230 @@ __global__ void __launch_bounds__(SP_NT, minb_of(KIND, nq_of(KIND, NY), RC)) k_b
             for (int e = 0; e < 8; ++e) iv[e] = ivn[e];
             if (b + 1 < nblocks) load_guide(y + SP_CB, ivn);
         }
-        const RunReader<NQ> rd(buf, pk, pg);
-        float2 W8[NQ == 1 ? SP_RUN : 1];
-        float2 T[NQ];
-        {
-            unsigned char *bs = sm + NBUF * buf_bytes(NQ);
-            if constexpr (NQ == 1) {
-                rd.template windows8_shared<RC>(r, reinterpret_cast<float2 *>(bs) + pk * SP_NBLK, W8);
-            } else {
-                float4 *bA = reinterpret_cast<float4 *>(bs) + pk * SP_NBLK;
-                rd.template window_shared<RC>(r, bA, bA + SP_CB * SP_NBLK, T);
-            }
-        }
-        if (live) {
-            const bool interior = x_interior && (y - r >= 0) && (y + r < h);
-            const int ny = min(h - 1, y + r) - max(0, y - r) + 1;
-            // output rows of this run
-            constexpr int NO = (KIND == SK_STATS) ? 2 * NY : (KIND == SK_MEAN2 ? 2 : 1);
-            float *dst0[NO / 2 > 0 ? NO / 2 : 1], *dst1[NO / 2 > 0 ? NO / 2 : 1];
-            TQ *dq = nullptr;
-            if constexpr (KIND == SK_MEAN2_OUT) {
-                dq = (TQ *)P.q + (size_t)(n * P.C + grp) * P.fps + (size_t)y * w + ox;
-            } else {
-#pragma unroll
-                for (int k = 0; k < NO / 2; ++k) {
-                    const size_t off = (size_t)(n * P.C + grp * (NO / 2) + k) * P.ops + (size_t)y * w + ox;
-                    dst0[k] = P.out0 + off;
-                    dst1[k] = P.out1 + off;
-                }
-            }
-            auto run = [&](auto border_tag) {
-                constexpr bool BORDER = decltype(border_tag)::value;
-                float o[NO][4];
-#pragma unroll
-                for (int j = 0; j < SP_RUN; ++j) {
-                    if constexpr (NQ == 1) T[0] = W8[j];
-                    else if (j > 0) rd.template slide<RC>(j, r, T);
-                    float inv = inv_full;
-                    if constexpr (BORDER) {
-                        const int xx = ox + j;
-                        const int nx = min(w - 1, xx + r) - max(0, xx - r) + 1;
-                        inv = __fdividef(1.0f, (float)(nx * ny));
-                    }
-                    const float2 iv2 = make_float2(inv, inv);
-                    const int jj = j & 3;
-                    if constexpr (KIND == SK_STATS) {
-                        const float2 m0 = mul2(T[0], iv2);
-                        if constexpr (NY == 1) {
-                            const float2 m1 = mul2(T[1], iv2);
-                            // var_I, cov_Ip; exactly 0 for a one-sample window (r = 0), as in the tile kernels
-                            const float var = r ? fmaxf(fmaf(-m0.x, m0.x, m1.x), 0.0f) : 0.0f;
-                            const float cov = r ? fmaf(-m0.x, m0.y, m1.y) : 0.0f;
-                            const float a = __fdividef(cov, var + P.eps);            // a, Eq. (2)
-                            o[0][jj] = a;
-                            o[1][jj] = (m0.y + col.c[1]) - a * (m0.x + col.c[0]);    // b, Eq. (3)
-                        } else {
-                            const float2 m1 = mul2(T[1], iv2), m2 = mul2(T[2], iv2), m3 = mul2(T[3], iv2);
-                            const float var = r ? fmaxf(fmaf(-m0.x, m0.x, m2.x), 0.0f) : 0.0f;
-                            const float rv = __fdividef(1.0f, var + P.eps);
-                            const float mx = m0.x + col.c[0];
-                            const float my[3] = {m0.y, m1.x, m1.y}, mxy[3] = {m2.y, m3.x, m3.y};
-#pragma unroll
-                            for (int k = 0; k < 3; ++k) {
-                                const float cov = r ? fmaf(-m0.x, my[k], mxy[k]) : 0.0f;
-                                const float a = cov * rv;                             // a, Eq. (2)
-                                o[2 * k][jj] = a;
-                                o[2 * k + 1][jj] = (my[k] + col.c[1 + k]) - a * mx;   // b, Eq. (3)
-                            }
-                        }
-                    } else if constexpr (KIND == SK_MEAN2) {
-                        o[0][jj] = T[0].x * inv;  // mean_a
-                        o[1][jj] = T[0].y * inv;  // mean_b
-                    } else {
-                        o[0][jj] = fmaf(T[0].x * inv, iv[j], T[0].y * inv);  // Eq. (4)
-                    }
-                    if (jj == 3 && (j == 3 || second)) {  // a float4 of every output plane
-                        const int xs = j - 3;
-                        if constexpr (KIND == SK_MEAN2_OUT) {
-                            if (P.detail != 0.0f) {
-#pragma unroll
-                                for (int e = 0; e < 4; ++e) o[0][e] = fmaf(P.detail, iv[xs + e] - o[0][e], o[0][e]);
-                            }
-                            store4q<TQ>(dq + xs, o[0]);
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < NO / 2; ++k) {
-                                const float4 va = make_float4(o[2 * k][0], o[2 * k][1], o[2 * k][2], o[2 * k][3]);
-                                const float4 vb =
-                                    make_float4(o[2 * k + 1][0], o[2 * k + 1][1], o[2 * k + 1][2], o[2 * k + 1][3]);
-                                if (P.stream_out) {  // planes larger than L2: streamed
-                                    __stcs(reinterpret_cast<float4 *>(dst0[k] + xs), va);
-                                    __stcs(reinterpret_cast<float4 *>(dst1[k] + xs), vb);
-                                } else {             // small planes stay in L2 for the next kernel
-                                    *reinterpret_cast<float4 *>(dst0[k] + xs) = va;
-                                    *reinterpret_cast<float4 *>(dst1[k] + xs) = vb;
-                                }
-                            }
-                        }
-                    }
-                }
-            };
-            if (interior) run(std::false_type{});
-            else run(std::true_type{});
-        }
+        run_block<KIND, NY, RC, TQ>(P, buf, sm + NBUF * buf_bytes(NQ), col.c, iv, y, live, pk, pg, ox, r, h, w, n,
+                                    grp, second, x_interior, inv_full);
         if (NBUF == 1 && b + 1 < nblocks) __syncthreads();  // the column sums are rewritten by the next block
     }
     pdl_trigger();  // this CTA's outputs are written: the next kernel may be scheduled
+}
+
+// ------------------------------------------------------------------------------------------------------
+// k_box_strip_sub: Algorithm 2's first two steps in one kernel, for a gray guide serving three channels (the
+// statistics of k_box_strip<SK_STATS, 3>) at s = 4 or 8 with nearest or bilinear subsampling.  The low-res
+// samples are never written: a producer warp streams, for each low-res row t of the CTA's strip, the full-res
+// rows the samples read (S t + S/2 - 1 and S t + S/2 for bilinear, S t + S/2 for nearest) of the guide and the
+// three input planes into a ring of shared-memory stages by TMA (4-D view: column, row within the S-row block,
+// block, plane; S boxes of 128 + 2r full-res columns per plane, 128 / S + 2r / S walker columns each).  Each walker forms its
+// column's sample of the four planes from the stage (the subsample's arithmetic), adds it to the window sums,
+// and keeps it in a ring of the last 2r + 1 samples of its column in shared memory, from which the leaving row
+// is taken.  Phase 2 (the runs, the epilogue of Eq. 2-3) is k_box_strip's, on column sums of pitch 128 + 2r.
+// At s = 4 two CTAs fit an SM (two stages each); at s = 8 one (three stages).
+//
+// Waits are bounded like the TMA output kernel's: a wait that gives up reports FAULT_BOX_TMA and the thread
+// stops waiting (its results are not valid; the call reports the fault); the producer drains its loads before
+// the CTA exits.
+// ------------------------------------------------------------------------------------------------------
+constexpr int SS_NT = SP_NT + 32;  // the 160 walkers / runs, then one producer warp
+
+__host__ __device__ constexpr int ss_nph(int MODE) { return MODE == GF_SUB_BILINEAR ? 2 : 1; }
+// walker columns (the column-sum pitch) and the full-res columns of one box: 128 + 2r
+__host__ __device__ constexpr int ss_vp(int r) { return SP_TW + 2 * r; }
+// bytes of one box (its nph rows) as loaded, and as laid out (128-byte aligned starts)
+__host__ __device__ constexpr int ss_box_bytes(int MODE, int r) { return ss_nph(MODE) * ss_vp(r) * 4; }
+__host__ __device__ constexpr int ss_box_pitch(int MODE, int r) { return (ss_box_bytes(MODE, r) + 127) / 128 * 128; }
+// one ring stage: the sampled full-res rows of one low-res row, 4 planes x S boxes
+__host__ __device__ constexpr int ss_stage_bytes(int S, int MODE, int r) { return 4 * S * ss_box_pitch(MODE, r); }
+__host__ __device__ constexpr int ss_nst(int S) { return S == 4 ? 2 : 3; }  // stages (low-res rows in flight)
+// column sums (pitch 128 + 2r) and block sums, the sample ring, the stages, the full / empty mbarriers
+__host__ __device__ constexpr size_t ss_sums_bytes(int r) { return (size_t)SP_CB * ss_vp(r) * 32; }
+__host__ __device__ constexpr size_t ss_smem(int S, int MODE, int r)
+{
+    return ss_sums_bytes(r) + bsum_bytes(4) + (size_t)(2 * r + 1) * ss_vp(r) * 16 +
+           (size_t)ss_nst(S) * ss_stage_bytes(S, MODE, r) + (size_t)2 * ss_nst(S) * 8;
+}
+
+struct SubStripParams {
+    StripParams P;  // X, Y unused; h, w low-res; CX = 1, groups = C / 3
+    int H, W;       // full-res plane size
+    unsigned *clear_word;
+    FaultSink fault;
+};
+
+// The bilinear (or nearest) sample of one plane from its two (one) stage rows: the walker's S-column block
+// starts at float `c` of each row, rows BW floats apart.
+template <int S, int MODE, int BW>
+__device__ __forceinline__ float stage_sample(const float *row, int c)
+{
+    if constexpr (MODE == GF_SUB_BILINEAR) {
+        float t0, t1, b0, b1;  // columns S/2 - 1, S/2 of the two rows
+        if constexpr (S == 4) {
+            const float4 t = *reinterpret_cast<const float4 *>(row + c);
+            const float4 b = *reinterpret_cast<const float4 *>(row + BW + c);
+            t0 = t.y; t1 = t.z; b0 = b.y; b1 = b.z;
+        } else {
+            t0 = row[c + S / 2 - 1]; t1 = row[c + S / 2];
+            b0 = row[BW + c + S / 2 - 1]; b1 = row[BW + c + S / 2];
+        }
+        return 0.5f * (0.5f * t0 + 0.5f * t1) + 0.5f * (0.5f * b0 + 0.5f * b1);
+    } else {
+        return row[c + S / 2];
+    }
+}
+// The same sample straight from global memory (the CTA's shift; the row pointer is that of block row 0).
+template <int S, int MODE>
+__device__ __forceinline__ float global_sample(const float *blk, int W)
+{
+    if constexpr (MODE == GF_SUB_BILINEAR) {
+        const float *t = blk + (size_t)(S / 2 - 1) * W, *b = t + W;
+        return 0.5f * (0.5f * __ldg(t + S / 2 - 1) + 0.5f * __ldg(t + S / 2)) +
+               0.5f * (0.5f * __ldg(b + S / 2 - 1) + 0.5f * __ldg(b + S / 2));
+    } else {
+        return __ldg(blk + (size_t)(S / 2) * W + S / 2);
+    }
+}
+
+template <int S, int MODE, int RC>
+__global__ void __launch_bounds__(SS_NT, S == 4 ? 2 : 1)
+    k_box_strip_sub(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmP,
+                    const __grid_constant__ SubStripParams Q)
+{
+    constexpr int NY = 3, NQ = 4, NST = ss_nst(S);
+    constexpr int VP = ss_vp(RC);                         // walker columns; full-res columns of a box
+    constexpr int STAGE = ss_stage_bytes(S, MODE, RC);
+    constexpr int BOXF = ss_box_pitch(MODE, RC) / 4;      // floats from one box to the next
+    constexpr int STAGE_TX = 4 * S * ss_box_bytes(MODE, RC);  // bytes the loads of one stage bring
+    constexpr int WPB = VP / S;                           // walker columns per box
+    constexpr int R = 2 * RC + 1;                         // sample ring rows
+    static_assert(VP % 8 == 0 && VP % S == 0 && VP <= 256, "box geometry");
+    static_assert((ss_sums_bytes(RC) + bsum_bytes(4) + (size_t)R * VP * 16) % 128 == 0, "stages start 128-byte aligned");
+    const StripParams &P = Q.P;
+    const int r = RC, h = P.h, w = P.w, tid = threadIdx.x;
+    const int grp = blockIdx.x % P.groups, sx = blockIdx.x / P.groups, n = blockIdx.z;
+    const int x0 = sx * SP_TW;
+    const int y0 = P.ylo + seg_of(blockIdx.y, gridDim.y, P.seg_order) * P.seg, yend = min(y0 + P.seg, P.yhi);
+    const int tstart = max(y0 - r, 0), tend = min(yend + r, h);  // the low-res rows streamed, in order
+    extern __shared__ __align__(128) unsigned char smx[];
+    unsigned char *bsx = smx + ss_sums_bytes(RC);                          // block sums of phase 2
+    float4 *ring = reinterpret_cast<float4 *>(bsx + bsum_bytes(NQ));      // [R][VP]: (I, p0, p1, p2) samples
+    unsigned char *stages = reinterpret_cast<unsigned char *>(ring + R * VP);
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(stages + (size_t)NST * STAGE);
+    const unsigned full0 = smem_u32(bars), empty0 = smem_u32(bars + NST);
+    pdl_wait();  // launched with programmatic serialization: the previous call's kernels are complete here
+    // the call's fault word starts at zero; a wait gives up only after FaultSink::limit polls, long after this
+    // CTA (the first scheduled) has run this line
+    if (Q.clear_word && (blockIdx.x | blockIdx.y | blockIdx.z | tid) == 0) *Q.clear_word = 0u;
+    if (tid == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, SP_NT / 32);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    const int plane_I = n, plane_p = n * P.C + grp * NY;
+    if (tid >= SP_NT) {  // ---- producer warp: one lane streams the rows
+        if (tid == SP_NT) {
+            const int xf = S * (x0 - r);  // first full-res column of box 0 (a multiple of 4: 16-byte aligned)
+            int issued = 0;
+            for (int u = 0; u < tend - tstart; ++u) {
+                const int st = u % NST;
+                if (u >= NST && !mbar_wait(empty0 + 8 * st, ((u / NST) - 1) & 1, Q.fault, FAULT_BOX_TMA)) break;
+                const unsigned fb = full0 + 8 * st;
+                mbar_expect_tx(fb, STAGE_TX);
+                float *dst = reinterpret_cast<float *>(stages + (size_t)st * STAGE);
+                const int t = tstart + u;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int k = 0; k < S; ++k)
+                        tma_load_4d(dst + (q * S + k) * BOXF, q == 0 ? (const void *)&tmI : (const void *)&tmP,
+                                    xf + VP * k, MODE == GF_SUB_BILINEAR ? S / 2 - 1 : S / 2, t,
+                                    q == 0 ? plane_I : plane_p + q - 1, fb);
+                issued = u + 1;
+            }
+            // every load issued has landed before the CTA may exit
+            for (int u = max(0, issued - NST); u < issued; ++u)
+                mbar_wait(full0 + 8 * (u % NST), (u / NST) & 1, Q.fault, FAULT_BOX_TMA);
+        }
+        pdl_trigger();
+        return;
+    }
+
+    // ---- the shift: every plane's sample at the first output pixel (y0, x0)
+    Column<SK_STATS, NY> col;
+    {
+        const size_t off = (size_t)S * y0 * Q.W + (size_t)S * x0;
+        col.c[0] = global_sample<S, MODE>(P.X + (size_t)plane_I * P.xps + off, Q.W);
+#pragma unroll
+        for (int k = 0; k < NY; ++k) col.c[1 + k] = global_sample<S, MODE>(P.Y + (size_t)(plane_p + k) * P.yps + off, Q.W);
+    }
+    const int xc = x0 - r + tid;  // this thread's walker column
+    const bool walker = tid < SP_TW + 2 * r;
+    const bool colok = walker && xc >= 0 && xc < w;
+    const int lane = tid & 31, wbox = tid / WPB, wcol = S * (tid % WPB);
+    const float4 shift4 = make_float4(col.c[0], col.c[1], col.c[2], col.c[3]);
+    bool waiting = true;  // false once a wait gave up
+    // the samples of low-res row t at this column, kept in the ring; rows outside the image read as the shift
+    auto enter = [&](int t) -> float4 {
+        float4 v = shift4;
+        if (t >= tstart && t < tend) {
+            const int u = t - tstart, st = u % NST;
+            if (waiting && !mbar_wait(full0 + 8 * st, (u / NST) & 1, Q.fault, FAULT_BOX_TMA)) waiting = false;
+            if (waiting && colok) {
+                const float *sb = reinterpret_cast<const float *>(stages + (size_t)st * STAGE) + wbox * BOXF;
+                v.x = stage_sample<S, MODE, VP>(sb, wcol);
+                v.y = stage_sample<S, MODE, VP>(sb + S * BOXF, wcol);
+                v.z = stage_sample<S, MODE, VP>(sb + 2 * S * BOXF, wcol);
+                v.w = stage_sample<S, MODE, VP>(sb + 3 * S * BOXF, wcol);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty0 + 8 * st);
+        }
+        if (walker) ring[((t + R) % R) * VP + tid] = v;
+        return v;
+    };
+    auto add = [&](float2 (&S2)[NQ], const float4 &v, bool sub) {
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+        float2 q[NQ];
+        col.pairs(vv, q);
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) S2[k] = sub ? sub2(S2[k], q[k]) : add2(S2[k], q[k]);
+    };
+
+    // ---- the window of the segment's first row, less its last row: rows [y0 - r, y0 + r - 1]
+    float2 Sw[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) Sw[q] = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+    for (int t = y0 - r; t < y0 + r; ++t) add(Sw, enter(t), false);
+
+    const int pk = tid >> 4, pg = tid & 15;
+    const int ox = x0 + pg * SP_RUN;
+    const bool second = ox + 4 < w;
+    const float inv_full = 1.0f / (float)((2 * r + 1) * (2 * r + 1));
+    const bool x_interior = (ox - r >= 0) && (ox + SP_RUN - 1 + r < w);
+    const int nblocks = (yend - y0 + SP_CB - 1) / SP_CB;
+    const float iv[8] = {};
+    for (int b = 0; b < nblocks; ++b) {
+        const int yb = y0 + b * SP_CB;
+        // ---- phase 1: row yb + k + r enters the window of output row yb + k, row yb + k - r leaves after
+#pragma unroll 1
+        for (int k = 0; k < SP_CB; ++k) {
+            add(Sw, enter(yb + k + r), false);
+            if (walker) {
+                put_sums<NQ, VP>(smx, k, tid, Sw);
+                add(Sw, ring[((yb + k - r + R) % R) * VP + tid], true);
+            }
+        }
+        asm volatile("bar.sync 1, %0;\n" ::"r"(SP_NT) : "memory");  // walkers / runs only
+        // ---- phase 2
+        const int y = yb + pk;
+        run_block<SK_STATS, NY, RC, float, VP>(P, smx, bsx, col.c, iv, y, (y < yend) && (ox < w), pk, pg, ox, r, h, w,
+                                               n, grp, second, x_interior, inv_full);
+        if (b + 1 < nblocks) asm volatile("bar.sync 1, %0;\n" ::"r"(SP_NT) : "memory");
+    }
+    pdl_trigger();
 }
 
 // SMs of the current device (cached per device ordinal).
@@ -651,8 +898,12 @@ cudaError_t launch_strip(StripParams P, int N, cudaStream_t st)
     }
     const int strips = (P.w + SP_TW - 1) / SP_TW;
     const long long tasks = (long long)strips * P.groups * N;
-    P.seg = segment_rows(P.yhi - P.ylo, P.r, tasks, (long long)per_sm * sm_count());
-    const dim3 grid((unsigned)(strips * P.groups), (unsigned)((P.yhi - P.ylo + P.seg - 1) / P.seg), (unsigned)N);
+    const long long resident = (long long)per_sm * sm_count();
+    P.seg = segment_rows(P.yhi - P.ylo, P.r, tasks, resident);
+    const int nseg = (P.yhi - P.ylo + P.seg - 1) / P.seg;
+    const long long waves = ((long long)strips * P.groups * nseg + resident - 1) / resident;  // of one image
+    P.seg_order = (int)std::min<long long>(std::max<long long>(waves, 1), nseg);
+    const dim3 grid((unsigned)(strips * P.groups), (unsigned)nseg, (unsigned)N);
     if ((e = launch_pdl(kern, grid, dim3(SP_NT), smem, st, P)) != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -730,6 +981,91 @@ cudaError_t launch_strip_box(const BoxTmaJob &J, cudaStream_t st)
         if (J.dt_out == F16) return launch_radius<SK_MEAN2_OUT, 1, __half>(P, J.N, st);
         return launch_radius<SK_MEAN2_OUT, 1, float>(P, J.N, st);
     }
+}
+
+namespace {
+
+template <int S, int MODE, int RC>
+cudaError_t launch_ss(const CUtensorMap &mI, const CUtensorMap &mP, SubStripParams Q, int N, cudaStream_t st)
+{
+    auto kern = k_box_strip_sub<S, MODE, RC>;
+    constexpr size_t smem = ss_smem(S, MODE, RC);
+    cudaError_t e = opt_in_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    static std::atomic<int> per_sm_cached{0};
+    int per_sm = per_sm_cached.load(std::memory_order_relaxed);
+    if (per_sm == 0) {
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SS_NT, smem)) != cudaSuccess) return e;
+        per_sm = per_sm > 0 ? per_sm : 1;
+        per_sm_cached.store(per_sm, std::memory_order_relaxed);
+    }
+    StripParams &P = Q.P;
+    const int strips = (P.w + SP_TW - 1) / SP_TW;
+    const long long tasks = (long long)strips * P.groups * N;
+    const long long resident = (long long)per_sm * sm_count();
+    P.seg = segment_rows(P.yhi - P.ylo, RC, tasks, resident);
+    const int nseg = (P.yhi - P.ylo + P.seg - 1) / P.seg;
+    const long long waves = ((long long)strips * P.groups * nseg + resident - 1) / resident;
+    P.seg_order = (int)std::min<long long>(std::max<long long>(waves, 1), nseg);
+    const dim3 grid((unsigned)(strips * P.groups), (unsigned)nseg, (unsigned)N);
+    if ((e = launch_pdl(kern, grid, dim3(SS_NT), smem, st, mI, mP, Q)) != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool strip_sub_geometry(int C, int CI, int H, int W, int h, int w, int s, int sd, int mode, int r_low, int dt_in,
+                        bool p_lowres)
+{
+    if (!getenv("GF_SUB_STRIP")) return false;
+    return dt_in == F32 && !p_lowres && sd == 1 && (s == 4 || s == 8) &&
+           (mode == GF_SUB_BILINEAR || mode == GF_SUB_NEAREST) && CI == 1 && C % 3 == 0 && H == s * h &&
+           W == s * w && W % 4 == 0 && w % 4 == 0 && r_low == 4 && (long long)H * W < (1LL << 31) &&
+           h <= 65535 * SP_CB;
+}
+
+bool strip_sub_supported(const SubStripJob &J)
+{
+    return strip_sub_geometry(J.C, 1, J.H, J.W, J.h, J.w, J.s, 1, J.mode, J.r, F32, false) && J.N >= 1 &&
+           J.N <= 65535 && aligned16s(J.I) && aligned16s(J.p) && J.fps % 4 == 0 && aligned16s(J.a) &&
+           aligned16s(J.b) && J.ops % 4 == 0 && (long long)((J.w + SP_TW - 1) / SP_TW) * (J.C / 3) < (1LL << 31);
+}
+
+cudaError_t launch_strip_sub(const SubStripJob &J, cudaStream_t st)
+{
+    const int nph = J.mode == GF_SUB_BILINEAR ? 2 : 1;
+    CUtensorMap mI, mP;
+    if (!encode_tmap_sampled_rows(&mI, J.I, J.W, J.s, J.h, J.N, J.fps, ss_vp(J.r), nph) ||
+        !encode_tmap_sampled_rows(&mP, J.p, J.W, J.s, J.h, J.N * J.C, J.fps, ss_vp(J.r), nph))
+        return cudaErrorInvalidValue;
+    SubStripParams Q{};
+    StripParams &P = Q.P;
+    P.X = J.I;
+    P.Y = J.p;
+    P.xps = P.yps = J.fps;
+    P.C = J.C;
+    P.CX = 1;
+    P.groups = J.C / 3;
+    P.h = J.h;
+    P.w = J.w;
+    P.r = J.r;
+    P.ylo = 0;
+    P.yhi = J.h;
+    P.eps = J.eps;
+    P.out0 = J.a;
+    P.out1 = J.b;
+    P.ops = J.ops;
+    P.stream_out = (double)J.N * J.C * J.h * J.w * 2 * sizeof(float) > 64e6;
+    Q.H = J.H;
+    Q.W = J.W;
+    Q.clear_word = J.clear_word;
+    Q.fault = J.fault;
+    if (J.s == 4) {
+        return J.mode == GF_SUB_BILINEAR ? launch_ss<4, GF_SUB_BILINEAR, 4>(mI, mP, Q, J.N, st)
+                                         : launch_ss<4, GF_SUB_NEAREST, 4>(mI, mP, Q, J.N, st);
+    }
+    return J.mode == GF_SUB_BILINEAR ? launch_ss<8, GF_SUB_BILINEAR, 4>(mI, mP, Q, J.N, st)
+                                     : launch_ss<8, GF_SUB_NEAREST, 4>(mI, mP, Q, J.N, st);
 }
 
 }  // namespace gfk

@@ -234,6 +234,23 @@ bool encode_tmap_3d(CUtensorMap *map, int dt, const void *base, int w, int h, in
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The rows a subsample at ratio S reads, as a 4-D FP32 tensor (column, row within the S-row block, block,
+// plane): dims (W, S, h, planes) for planes of H = S h rows of W floats, plane_stride floats apart.  A box is
+// box_w columns of nph consecutive rows of one block: the two rows a bilinear sample reads (nph = 2), or the
+// one of a nearest sample.
+bool encode_tmap_sampled_rows(CUtensorMap *map, const float *base, int W, int S, int h, int planes,
+                              size_t plane_stride, int box_w, int nph)
+{
+    EncodeFn enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)W, (cuuint64_t)S, (cuuint64_t)h, (cuuint64_t)planes};
+    const cuuint64_t strides[3] = {(cuuint64_t)W * 4, (cuuint64_t)S * W * 4, (cuuint64_t)plane_stride * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)box_w, (cuuint32_t)nph, 1, 1}, estr[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // The sticky word's device address, looked up once per CUDA context (a context made after cudaDeviceReset
 // gets its own lookup, so no stale address is used).
 unsigned *sticky_fault_word()

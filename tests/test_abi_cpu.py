@@ -108,7 +108,7 @@ def test_product_package_does_not_use_the_oracle():
                 assert "gf_oracle" not in text and "libgforacle" not in text, f
 
 
-def test_kernel_count(lib):
+def test_kernel_count(lib, monkeypatch):
     from paper_1505_00996_gb300 import binding
     o = binding.opts_init()
     count = lambda H, W, s, mode: lib.gf_filter_kernel_count(H, W, 3, s, mode, ctypes.byref(o))
@@ -118,6 +118,15 @@ def test_kernel_count(lib):
     assert count(3000, 4000, 1, binding.GF_SUB_BILINEAR) == 2
     assert count(3000, 4001, 1, binding.GF_SUB_BILINEAR) == 3
     assert count(0, 4000, 4, binding.GF_SUB_BILINEAR) == -1
+    # the subsample and the statistics as one kernel: opt-in, at r' = 4 (given through opts.r_low)
+    o.r_low = 4
+    assert count(3000, 4000, 4, binding.GF_SUB_BILINEAR) == 4
+    monkeypatch.setenv("GF_SUB_STRIP", "1")
+    assert count(3000, 4000, 4, binding.GF_SUB_BILINEAR) == 3
+    assert count(3000, 4000, 8, binding.GF_SUB_NEAREST) == 3
+    assert count(3000, 4000, 2, binding.GF_SUB_BILINEAR) == 4  # s = 2: not taken
+    o.r_low = 3
+    assert count(3000, 4000, 4, binding.GF_SUB_BILINEAR) == 4  # r' = 3: not taken
 
 
 def test_host_strips(lib):
