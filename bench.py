@@ -332,6 +332,25 @@ def run_native(args, world, rank, local):
         out["speedup_s4_vs_s1"] = round(sweep["1"]["ms_per_step"] / ms, 3)
         out["speedup_s4_vs_s1_serial"] = round(sweep["1"]["serial_ms_per_step"] / ms_serial, 3)
 
+        # ---- the headline with no input re-read by consecutive calls of a stream: each stream alternates
+        #      between two copies of I and p, so what one call's output kernel leaves of I in L2 is not the next
+        #      call's input (the headline above refilters the same copy, which its 320 MB per step allows)
+        def filt_alt(s, lane):
+            spare = (lane["I"].clone(), lane["p"].clone())
+            count = [0]
+
+            def call():
+                Ik, pk = (lane["I"], lane["p"]) if count[0] % 2 == 0 else spare
+                count[0] += 1
+                return gf.fast_guided_filter(Ik, pk, R, EPS, s, MODE, out=lane["q"], stream=lane["stream"],
+                                             ctx=lane["ctx"], rows=strip)
+            return call
+        alt = [(ln["stream"], filt_alt(S, ln)) for ln in lanes]
+        ms_alt = time_steps(alt, k_sweep, args.warmup, world, graph_steps, use_graph)
+        out["headline_distinct_inputs"] = {"ms_per_step": round(ms_alt, 5),
+                                           "mp_per_s": round(world * mp / (ms_alt / 1e3), 1), "steps": k_sweep,
+                                           "inputs": "two copies of I and p per stream, alternating call by call"}
+
         # ---- end to end through the host-buffer entry point: copies in, filter, copy out, every step
         I_h = torch.from_numpy(I_np).pin_memory()
         p_h = torch.from_numpy(p_np).pin_memory()
