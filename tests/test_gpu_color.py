@@ -54,6 +54,7 @@ CASES = [  # (N, C, H, W, r, eps, s, mode, p_lowres)
     (2, 3, 96, 128, 0, 1e-2, 4, "box", True),
     (1, 4, 257, 1030, 24, 1e-4, 8, "bilinear", False),
     (1, 3, 136, 264, 16, 1e-3, 8, "bilinear", False),    # s = 8 run form of the output, C = 3
+    (1, 3, 300, 1100, 16, 1e-3, 4, "bilinear", False),   # 3 output bands (the last 76 pixels), h = 75 ragged
     (1, 1, 7, 5, 4, 1e-2, 2, "bilinear", False),
 ]
 
