@@ -70,7 +70,6 @@ public:
     {
         free_.clear();
         if (size) free_[0] = size;
-        size_ = size;
     }
     bool alloc(size_t bytes, size_t *off)
     {
@@ -105,12 +104,11 @@ public:
             }
         }
     }
-    size_t size() const { return size_; }
     size_t in_use() const { return in_use_; }
 
 private:
     std::map<size_t, size_t> free_;  // offset -> length
-    size_t size_ = 0, in_use_ = 0;
+    size_t in_use_ = 0;
 };
 
 enum ReqState { QUEUED, RUNNING, DONE, FAILED, CANCELED };
