@@ -85,10 +85,24 @@ __device__ __forceinline__ int vidx2(int c) { return c + 2 * (c >> 3); }
 // arrays when NQ >= 2).
 constexpr int SP_NBLK = SP_NT / 8;
 __host__ __device__ constexpr size_t bsum_bytes(int NQ) { return (size_t)SP_CB * SP_NBLK * 8 * NQ; }
-__host__ __device__ constexpr size_t strip_smem(int NQ)
+// The column-sum pitch at a compile-time radius r <= 8: just the 128 + 2r walker columns, in whole 8-column
+// blocks for the float4 swizzle; for float2, past the padded index of the last column and 8 mod 16.  Rows then
+// keep the bank offset of the full pitch (0 banks for float4, 16 for float2), and the smaller CTAs fit beside
+// other kernels' CTAs on an SM.  Larger and run-time radii keep the pitch of r = 16.
+__host__ __device__ constexpr int vp2_need(int RC) { return (SP_TW + 2 * RC - 1) + 2 * ((SP_TW + 2 * RC - 1) >> 3) + 1; }
+__host__ __device__ constexpr int vp_rc(int NQ, int RC)
 {
-    return (size_t)(db_of(NQ) ? 2 : 1) * SP_CB * vp_of(NQ) * (NQ == 1 ? 8 : 16) * (NQ == 1 ? 1 : NQ / 2) +
-           bsum_bytes(NQ);
+    return (RC < 0 || RC > 8) ? vp_of(NQ)
+                              : (NQ == 1 ? vp2_need(RC) + (24 - vp2_need(RC) % 16) % 16
+                                         : ((SP_TW + 2 * RC + 7) & ~7));
+}
+__host__ __device__ constexpr size_t buf_bytes_rc(int NQ, int RC)
+{
+    return (size_t)SP_CB * vp_rc(NQ, RC) * (NQ == 1 ? 8 : 16) * (NQ == 1 ? 1 : NQ / 2);
+}
+__host__ __device__ constexpr size_t strip_smem_rc(int NQ, int RC)
+{
+    return (size_t)(db_of(NQ) ? 2 : 1) * buf_bytes_rc(NQ, RC) + bsum_bytes(NQ);
 }
 
 // One strip column's sources: the planes it reads (statistics: the guide, then NY inputs; box means: a, b),
@@ -185,7 +199,7 @@ struct RowBatch {
 // Phase 1 of one block for one walker column: the vertical window sums of rows yb .. yb + SP_CB - 1 from the
 // batch fetched for them.  S holds the sums of rows [yb - r, yb + r - 1] (clipped to the image) on entry and is
 // carried on to the next block.
-template <int KIND, int NY, bool PL>
+template <int KIND, int NY, bool PL, int VP>
 __device__ __forceinline__ void walk_block(const Column<KIND, NY> &col, const RowBatch<KIND, NY, PL> &B,
                                            float2 (&S)[nq_of(KIND, NY)], int yb, int r, int h, unsigned char *buf,
                                            int j)
@@ -206,7 +220,7 @@ __device__ __forceinline__ void walk_block(const Column<KIND, NY> &col, const Ro
         }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) S[q] = add2(S[q], qe[q]);
-        put_sums<NQ>(buf, k, j, S);
+        put_sums<NQ, VP>(buf, k, j, S);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) S[q] = sub2(S[q], ql[q]);
     }
@@ -227,10 +241,6 @@ __device__ __forceinline__ void store4q<__half>(__half *p, const float v[4])
         make_uint2(*reinterpret_cast<const unsigned *>(&lo), *reinterpret_cast<const unsigned *>(&hi));
 }
 
-__host__ __device__ constexpr size_t buf_bytes(int NQ)
-{
-    return (size_t)SP_CB * vp_of(NQ) * (NQ == 1 ? 8 : 16) * (NQ == 1 ? 1 : NQ / 2);
-}
 
 // Phase-2 reads of one run: the column sums of walker columns c0 + i (c0 = 8 g) of row k of a block.
 //   float2 layout (NQ == 1): column c at c + 2 (c / 8), i.e. 10 g + i + 2 (i / 8) -- a constant offset from the
@@ -532,6 +542,7 @@ __global__ void __launch_bounds__(SP_NT, minb_of(KIND, nq_of(KIND, NY), RC)) k_b
 {
     constexpr int NQ = nq_of(KIND, NY);
     constexpr bool PL = pl_of(NQ, RC);
+    constexpr int VP = vp_rc(NQ, RC);  // column-sum pitch
     constexpr int NS = Column<KIND, NY>::NS;
     constexpr int NBUF = db_of(NQ) ? 2 : 1;
     const int r = RC >= 0 ? RC : P.r;
@@ -601,15 +612,15 @@ __global__ void __launch_bounds__(SP_NT, minb_of(KIND, nq_of(KIND, NY), RC)) k_b
     if (colok) B.fetch(col, y0, r, h);
     for (int b = 0; b < nblocks; ++b) {
         const int yb = y0 + b * SP_CB;
-        unsigned char *buf = sm + (NBUF == 2 ? (size_t)(b & 1) * buf_bytes(NQ) : 0);
+        unsigned char *buf = sm + (NBUF == 2 ? (size_t)(b & 1) * buf_bytes_rc(NQ, RC) : 0);
         // ---- phase 1: vertical window sums of the block's rows; then the next block's rows are requested
         if (colok) {
-            walk_block<KIND, NY, PL>(col, B, S, yb, r, h, buf, tid);
+            walk_block<KIND, NY, PL, VP>(col, B, S, yb, r, h, buf, tid);
             if (b + 1 < nblocks) B.fetch(col, yb + SP_CB, r, h);
         } else if (walker) {  // a column outside the image contributes nothing
             const float2 Z[NQ] = {};
 #pragma unroll 1
-            for (int k = 0; k < SP_CB; ++k) put_sums<NQ>(buf, k, tid, Z);
+            for (int k = 0; k < SP_CB; ++k) put_sums<NQ, VP>(buf, k, tid, Z);
         }
         __syncthreads();
 
@@ -622,7 +633,7 @@ __global__ void __launch_bounds__(SP_NT, minb_of(KIND, nq_of(KIND, NY), RC)) k_b
             for (int e = 0; e < 8; ++e) iv[e] = ivn[e];
             if (b + 1 < nblocks) load_guide(y + SP_CB, ivn);
         }
-        run_block<KIND, NY, RC, TQ>(P, buf, sm + NBUF * buf_bytes(NQ), col.c, iv, y, live, pk, pg, ox, r, h, w, n,
+        run_block<KIND, NY, RC, TQ, VP>(P, buf, sm + NBUF * buf_bytes_rc(NQ, RC), col.c, iv, y, live, pk, pg, ox, r, h, w, n,
                                     grp, second, x_interior, inv_full);
         if (NBUF == 1 && b + 1 < nblocks) __syncthreads();  // the column sums are rewritten by the next block
     }
@@ -886,7 +897,7 @@ template <int KIND, int NY, int RC, typename TQ>
 cudaError_t launch_strip(StripParams P, int N, cudaStream_t st)
 {
     auto kern = k_box_strip<KIND, NY, RC, TQ>;
-    constexpr size_t smem = strip_smem(nq_of(KIND, NY));
+    constexpr size_t smem = strip_smem_rc(nq_of(KIND, NY), RC);
     cudaError_t e = opt_in_smem(kern, smem);
     if (e != cudaSuccess) return e;
     static std::atomic<int> per_sm_cached{0};  // CTAs per SM of this instantiation
