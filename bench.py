@@ -15,6 +15,7 @@ its own image (weak scaling, no collective on the data path; the timing is max-r
 ``--impl reference`` times the FP64 CPU oracle on the same workload instead (rank 0 only).
 """
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -569,7 +570,10 @@ def run_small_images(dev, stream, ctx, world, calls=200):
                 e1.record(stream)
             torch.cuda.synchronize()
             row[name] = {"graph_us": round(ms_g * 1e3, 2), "eager_us": round(e0.elapsed_time(e1) / calls * 1e3, 2)}
-        row["auto"] = "fused" if gf.load_library().gf_filter_kernel_count(Hh, Ww, Cc, 4, 1, None) == 1 else "chain"
+        o = gf.binding.opts_init()
+        o.r_low = gf.lowres_geometry(Hh, Ww, 4, r)[2]
+        row["auto"] = ("fused" if gf.load_library().gf_filter_kernel_count(Hh, Ww, Cc, 4, 1, ctypes.byref(o)) == 1
+                       else "chain")
         res["%dx%d_C%d_r%d" % (Hh, Ww, Cc, r)] = row
     return res
 

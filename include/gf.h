@@ -107,7 +107,8 @@ typedef struct gf_ctx gf_ctx;
  *                   bilinear or antialiased subsampling, FP32 or FP16 storage, a gray or depthwise guide,
  *                   no row range; forward only.
  *   fused           0: run the whole filter as one kernel (each CTA recomputes its halo) for a subsampled
- *                   call (s > 1) on a small image (N*C*H*W <= GF_FUSED_AUTO_PIXELS), where the four-kernel
+ *                   call (s > 1) on a small image (N*C*H*W <= GF_FUSED_AUTO_PIXELS, and N*C*H*W weighed by
+ *                   (1 + r'/4)^2 for the halo at most 2.1 GF_FUSED_AUTO_PIXELS), where the four-kernel
  *                   chain is dominated by per-kernel fixed costs; 1: always (GF_EINVAL where unsupported);
  *                   -1: never.  The single
  *                   kernel takes FP32 or FP16 storage, a gray or depthwise guide, any subsample mode and

@@ -206,9 +206,12 @@ gf_status resolve(int H, int W, int C, int r, float eps, int s, int mode, const 
             return fail(GF_EINVAL, "the fused kernel does not take these arguments (colour guide, uint8, "
                                    "intermediate outputs or too large a radius)");
         // automatic: subsampled calls up to GF_FUSED_AUTO_PIXELS pixel-channels, where the single kernel was
-        // measured faster than the chain launched call by call (at s = 1 its direct window sums lose)
-        R.fused = ok && (o->fused > 0 || (o->fused == 0 && R.s > 1 &&
-                                          (long long)R.N * C * H * W <= GF_FUSED_AUTO_PIXELS));
+        // measured faster than the chain (at s = 1 its direct window sums lose).  Its cost grows with the halo
+        // each tile recomputes, so the pixel-channels are weighed by (1 + r'/4)^2 against 2.1 GF_FUSED_AUTO_PIXELS
+        // (measured crossings: r' = 2 between 896^2 and 1024^2 single-channel images, r' = 4 near 600 x 800)
+        const double pc = (double)R.N * C * H * W, grow = 1.0 + R.r_low / 4.0;
+        R.fused = ok && (o->fused > 0 || (o->fused == 0 && R.s > 1 && pc <= GF_FUSED_AUTO_PIXELS &&
+                                          pc * grow * grow <= 2.1 * GF_FUSED_AUTO_PIXELS));
     }
     const long long planes = (long long)R.N * (R.CI + C);
     if (planes > 65535) return fail(GF_EINVAL, "batch * (guide channels + C) must be <= 65535");

@@ -127,6 +127,23 @@ def test_kernel_count(lib, monkeypatch):
     assert count(3000, 4000, 2, binding.GF_SUB_BILINEAR) == 4  # s = 2: not taken
     o.r_low = 3
     assert count(3000, 4000, 4, binding.GF_SUB_BILINEAR) == 4  # r' = 3: not taken
+    monkeypatch.delenv("GF_SUB_STRIP")
+
+
+def test_automatic_single_kernel_weighs_the_halo(lib):
+    """gf_opts.fused = 0 takes the single kernel while N C H W (1 + r'/4)^2 <= 2.1 * 2^20 (and N C H W <=
+    2^20): the measured crossings against the chain move to smaller images as r' grows."""
+    from paper_1505_00996_gb300 import binding
+    o = binding.opts_init()
+    count = lambda H, W, C: lib.gf_filter_kernel_count(H, W, C, 4, binding.GF_SUB_BILINEAR, ctypes.byref(o))
+    o.r_low = 1
+    assert count(1024, 1024, 1) == 1 and count(480, 640, 3) == 1
+    o.r_low = 2
+    assert count(896, 896, 1) == 1 and count(480, 640, 3) == 1
+    assert count(1024, 1024, 1) == 4
+    o.r_low = 4
+    assert count(640, 640, 1) == 1 and count(600, 800, 1) == 1
+    assert count(768, 768, 1) == 4 and count(512, 512, 3) == 4
 
 
 def test_host_strips(lib):
