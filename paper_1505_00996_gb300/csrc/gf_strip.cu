@@ -4,7 +4,8 @@
 //                fused with var_I, cov_Ip and the coefficients a (Eq. 2) and b (Eq. 3);
 //   SK_MEAN2     box means of a and b;
 //   SK_MEAN2_OUT box means of a and b fused with q = mean_a I + mean_b (Eq. 4), at s = 1 only, where the
-//                upsample is the identity.
+//                upsample is the identity;
+// and k_box_strip_sub (further down), Algorithm 2's subsample and statistics in one kernel, its rows fed by TMA.
 //
 // f_mean is the box mean over the window clipped to the image, divided by the window's in-image count.
 //
